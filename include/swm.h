@@ -1,0 +1,195 @@
+/*
+ * swm.h -- C ABI of the GB300 (sm_103a) sparsified thin-wire method-of-moments solver.
+ *
+ * The library computes the electric currents induced on a cloud of straight, thin, perfectly
+ * conducting wires ("chaffs") by plane waves, and the radar cross section (RCS) they scatter,
+ * following arXiv 2410.03060 ("Fast algorithm for full-wave EM scattering analysis of large-scale
+ * chaff cloud ..."):
+ *
+ *   - Sec. II-A, Eq. (current_expression) and its footnote: each wire p is cut into n_s(p) equal
+ *     segments; the n_s(p) - 1 interior vertices carry rooftop unknowns.  Unknowns are numbered
+ *     wire by wire in the caller's wire order: unknown (p, i) has index off_p + i, i = 0..n_s(p)-2,
+ *     off_p = sum over wires q < p of (n_s(q) - 1).
+ *   - Sec. II-A, Eqs. (TW_EFIE_MOM), (4)-(8): Galerkin testing of the thin-wire EFIE.  The library
+ *     solves the scaled system Z jt = b with
+ *         b_m  = int Lambda_m(s) t_m . E_inc(r(s)) ds,
+ *         Z_mn = (t_m.t_n) int int Lambda_m Lambda_n G - (1/k^2) int int Lambda_m' Lambda_n' G,
+ *     G = exp(-j k R)/(4 pi R), R = sqrt(|r - r'|^2 + a^2) (reduced thin-wire kernel).  This is the
+ *     paper's Z j = v multiplied by j*omega*mu0, so the physical current in amperes is
+ *     jt / (j omega mu0) = -j jt / (k eta0).  Time convention exp(+j omega t).
+ *   - Sec. II-B, Eq. (neardef) (S-NFC): the block Z_pq is kept iff the centroid distance
+ *     |c_p - c_q| <= r_c (inclusive), every other block is zero.
+ *   - Sec. II-B (after Eq. neardef): the block-sparse system is solved iteratively with a
+ *     block-diagonal preconditioner; this library uses restarted GMRES, right-preconditioned by
+ *     the inverses of the self blocks Z_pp.
+ *   - Sec. III-A, III-B: bistatic and monostatic RCS from the far field of the currents.
+ *
+ * Quadrature (the paper names only "analytic singularity extraction" and "Gaussian quadrature"):
+ * different wires use tensor Gauss-Legendre with 4 points per segment (8 when the two wires come
+ * closer than the longer segment length); segments of one wire use an exact reduction of the
+ * double integral to one dimension, 8 Gauss points per half, and a closed-form static part for
+ * coincident or touching segments.  The mutual radius is a^2 = (a_p^2 + a_q^2)/2.
+ *
+ * Conventions.  Lengths in metres (any unit works if k is in radians per that unit); k in rad/m.
+ * Incident plane waves have amplitude 1 V/m.  An incidence is (theta, phi, psi) in radians: the
+ * wave ARRIVES from the direction u = (sin th cos ph, sin th sin ph, cos th), i.e. it propagates
+ * along -u, and its polarisation is cos(psi) theta_hat + sin(psi) phi_hat of the spherical frame
+ * at (theta, phi).  An observation is (theta, phi).  sigma = |e_s . F|^2 / (4 pi) where F is the
+ * radiation vector of the currents and e_s is theta_hat (index 0) or phi_hat (index 1) at the
+ * observation direction; RCS is in m^2.
+ *
+ * Memory.  Pointers tagged SWM_HOST are ordinary host memory; SWM_DEVICE pointers are device
+ * memory of the context's device (e.g. torch data_ptr()).  The library copies every input it
+ * keeps; the caller keeps ownership of every buffer it passes.  Work runs on the context's CUDA
+ * stream; calls return after their results are complete in the output buffers.
+ *
+ * Errors.  Every int-returning call returns SWM_OK (0), a positive warning, or a negative error.
+ * On an error the context keeps its previous valid state where possible and swm_last_error()
+ * describes the failure.  Nothing throws across the ABI.  A context is not thread-safe: use one
+ * context per host thread.
+ */
+#ifndef SWM_H
+#define SWM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SWM_OK 0
+#define SWM_ENOTCONV 1 /* warning: GMRES hit max_iter before tol; outputs hold the last iterate */
+#define SWM_EINVAL (-1) /* invalid argument (bad size, NaN, non-unit direction, ...) */
+#define SWM_ENOMEM (-2) /* device allocation failed */
+#define SWM_ECUDA (-3)  /* a CUDA runtime call or kernel failed */
+#define SWM_ESTATE (-4) /* call out of order (e.g. solve before build) */
+
+/* memory kinds */
+#define SWM_HOST 0
+#define SWM_DEVICE 1
+
+/* precision of the fill, the stored blocks and the Krylov vectors */
+#define SWM_C128 0 /* plain path: FP64 kernel evaluation, complex128 blocks, complex128 GMRES */
+#define SWM_C64 1  /* fast path: FP64 per-block geometry, FP32 kernel evaluation, complex64 blocks
+                      and vectors, FP64 dot products, norms, Hessenberg and rotations */
+
+/* limits */
+#define SWM_MAX_SEG 16  /* segments per wire: 2 <= n_s <= SWM_MAX_SEG */
+#define SWM_MAX_RESTART 128
+
+typedef struct swm_ctx swm_ctx;
+
+typedef struct swm_stats {
+  int64_t nw;          /* wires */
+  int64_t n;           /* unknowns */
+  int64_t nb;          /* kept blocks, full storage, diagonal included */
+  int64_t nnz;         /* stored complex entries of Z */
+  int n_rhs;           /* incidences of the last solve */
+  int iterations;      /* GMRES iterations (matrix-vector products) of the last solve */
+  int restarts;        /* restart cycles of the last solve */
+  int converged;       /* 1 if every right-hand side reached tol */
+  double rel_residual; /* max over right-hand sides of ||b - Z x|| / ||b|| at exit */
+  double ms_neighbour; /* phase times of the last build / solve / rcs call (CUDA events) */
+  double ms_fill;
+  double ms_precond;
+  double ms_rhs;
+  double ms_solve;
+  double ms_rcs;
+  int64_t kernel_launches; /* kernels launched by this context since its creation */
+} swm_stats;
+
+/* Create a context on CUDA device `device` that issues all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context. */
+int swm_create(swm_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer of the context and the context itself.  NULL is ignored. */
+void swm_destroy(swm_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none).  Valid until the next call. */
+const char* swm_last_error(const swm_ctx* ctx);
+
+/* Route the context's device allocations through caller-supplied functions (e.g. a caching
+ * allocator).  alloc returns device memory of at least `bytes` usable on `stream` or NULL; free
+ * releases it.  Must be called before swm_set_cloud.  Passing NULL functions restores
+ * cudaMallocAsync / cudaFreeAsync on the context stream. */
+typedef void* (*swm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*swm_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+int swm_set_allocator(swm_ctx* ctx, swm_alloc_fn alloc, swm_free_fn free_fn, void* user);
+
+/* Load a wire cloud (Sec. II-A).  nw >= 1 wires:
+ *   centres  nw x 3 float64 (row-major), wire centroids c_p;
+ *   dirs     nw x 3 float64, unit directions t_p (|t_p| = 1 within 1e-9);
+ *   lengths  nw float64 > 0;
+ *   radii    nw float64 > 0;
+ *   nseg     nw int32 segment counts, 2 <= nseg <= SWM_MAX_SEG (unknowns per wire = nseg - 1).
+ * All five pointers have the same memory kind `mem_kind`.  Replaces any previous cloud and
+ * invalidates any built matrix.  SWM_EINVAL on a NaN, a non-unit direction, a non-positive
+ * length or radius, or a segment count out of range (checked on the device for SWM_DEVICE). */
+int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double* dirs,
+                  const double* lengths, const double* radii, const int32_t* nseg, int mem_kind);
+
+/* Build the S-NFC system (Sec. II-B): neighbour search with coupling radius r_c (r_c <= 0 or
+ * infinite = entire coupling, every block kept), fill of every kept block at wavenumber k > 0
+ * (Eqs. (5)-(8)), and the block-Jacobi preconditioner.  precision is SWM_C128 or SWM_C64.
+ * Device memory: about 16 (c128) or 8 (c64) bytes per stored entry, twice (Z and Z times the
+ * preconditioner), plus O(nw + nb) index arrays. */
+int swm_build(swm_ctx* ctx, double k, double r_c, int precision);
+
+/* Solve Z jt = b for n_inc >= 1 incidences (Eq. (4) right-hand sides), inc = n_inc x 3 float64
+ * (theta, phi, psi) in host memory.  Restarted GMRES(restart), 1 <= restart <= SWM_MAX_RESTART,
+ * stops when every relative residual ||b - Z x||/||b|| <= tol or after max_iter iterations
+ * (SWM_ENOTCONV, last iterate kept).  The currents stay in the context for the RCS calls; if
+ * currents_out is not NULL they are also written there as n_inc x N complex128 (interleaved
+ * re, im; incidence-major, caller's unknown order), in memory of kind out_kind. */
+int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restart, int max_iter,
+              double* currents_out, int out_kind);
+
+/* Bistatic RCS (Sec. III-A) of the currents of the last solve at n_obs >= 1 observation
+ * directions obs = n_obs x 2 float64 (theta, phi), host memory.  sigma_out receives
+ * n_inc x n_obs x 2 float64 (theta- and phi-received), memory of kind out_kind. */
+int swm_rcs_bistatic(swm_ctx* ctx, int n_obs, const double* obs, double* sigma_out, int out_kind);
+
+/* Monostatic RCS (Sec. III-B): each incidence observed back along its arrival direction.
+ * sigma_out receives n_inc x 2 float64, memory of kind out_kind. */
+int swm_rcs_monostatic(swm_ctx* ctx, double* sigma_out, int out_kind);
+
+/* Counters and phase times of the context. */
+int swm_get_stats(const swm_ctx* ctx, swm_stats* out);
+
+/* Kept block pattern of the last build (Eq. neardef) as nb x 2 int64 (p, q) pairs in the
+ * caller's wire numbering, host memory of at least 2 * stats.nb entries, rows sorted by p then q. */
+int swm_get_pattern(swm_ctx* ctx, int64_t* pairs_out);
+
+/* Block Z_pq (caller's wire numbering) as m_p x m_q complex128, row-major, interleaved re/im,
+ * host memory.  SWM_EINVAL if the block was not kept. */
+int swm_get_block(swm_ctx* ctx, int64_t p, int64_t q, double* re_im_out);
+
+/* Right-hand sides b of the last solve, n_inc x N complex128 as in swm_solve, host memory. */
+int swm_get_rhs(swm_ctx* ctx, double* re_im_out);
+
+/* Stateless far-field RCS of given currents (Sec. III-A), all pointers device memory:
+ *   centres, dirs (nw x 3), lengths (nw), nseg (nw) as in swm_set_cloud; off (nw + 1) int64
+ *   unknown offsets off_p (off_0 = 0, off_{p+1} = off_p + nseg_p - 1);
+ *   currents n_rhs x N complex128 (interleaved); obs n_obs x 2 (theta, phi);
+ *   sigma_out n_rhs x n_obs x 2 float64 (theta- and phi-received).
+ * Runs on `cuda_stream` and returns when sigma_out is complete.  Allocates device scratch of
+ * about 48 * n_rhs * n_obs * ceil(nw / 256) bytes with cudaMallocAsync and frees it before
+ * returning.  Error text (if any) is returned by swm_stateless_error(). */
+int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const double* dirs,
+                  const double* lengths, const int32_t* nseg, const int64_t* off, double k,
+                  int n_rhs, const double* currents, int n_obs, const double* obs,
+                  double* sigma_out);
+
+/* Message of the last failed stateless call on this host thread ("" if none). */
+const char* swm_stateless_error(void);
+
+/* Library version string. */
+const char* swm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWM_H */

@@ -1,0 +1,528 @@
+// C-ABI entry points of the swm library (declared and documented in include/swm.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace swm {
+
+int dalloc(swm_ctx* ctx, std::vector<Buf>& group, void** out, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  void* p = nullptr;
+  if (ctx->user_alloc) {
+    p = ctx->user_alloc(bytes, (void*)ctx->stream, ctx->user_arg);
+    if (!p) return ctx->fail(SWM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return ctx->fail(SWM_ENOMEM, "cudaMallocAsync(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+  }
+  group.push_back(Buf{p, bytes});
+  *out = p;
+  return SWM_OK;
+}
+
+void dfree_group(swm_ctx* ctx, std::vector<Buf>& group) {
+  for (auto& b : group) {
+    if (ctx->user_free)
+      ctx->user_free(b.p, b.bytes, (void*)ctx->stream, ctx->user_arg);
+    else
+      cudaFreeAsync(b.p, ctx->stream);
+  }
+  group.clear();
+}
+
+namespace {
+
+// Per-wire input checks; flags: 1 NaN/Inf, 2 non-unit direction, 4 length, 8 radius, 16 segments.
+__global__ void k_validate(int64_t nw, const double* __restrict__ c, const double* __restrict__ t,
+                           const double* __restrict__ L, const double* __restrict__ a, const int32_t* __restrict__ ns,
+                           int* __restrict__ flags, int* __restrict__ max_ns) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  int f = 0;
+  for (int d = 0; d < 3; ++d)
+    if (!isfinite(c[3 * i + d]) || !isfinite(t[3 * i + d])) f |= 1;
+  if (!isfinite(L[i]) || !isfinite(a[i])) f |= 1;
+  const double tn = t[3 * i] * t[3 * i] + t[3 * i + 1] * t[3 * i + 1] + t[3 * i + 2] * t[3 * i + 2];
+  if (!(fabs(tn - 1.0) <= 2e-9)) f |= 2;
+  if (!(L[i] > 0.0)) f |= 4;
+  if (!(a[i] > 0.0)) f |= 8;
+  if (ns[i] < 2 || ns[i] > kMaxSeg) f |= 16;
+  if (f) atomicOr(flags, f);
+  atomicMax(max_ns, ns[i]);
+}
+
+// Internal [R][N] currents (any precision) -> caller [R][N] complex128 in caller unknown order.
+template <typename TV>
+__global__ void k_to_user(int64_t N, int R, const int32_t* __restrict__ rowwire, const int64_t* __restrict__ off,
+                          const int64_t* __restrict__ uoff, const cplx<TV>* __restrict__ X, c128* __restrict__ out) {
+  const int r = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int p = rowwire[n];
+  out[(int64_t)r * N + uoff[p] + (n - off[p])] = ccast<double>(X[(int64_t)r * N + n]);
+}
+
+// Incidence frames: k_hat (propagation, = -arrival) and polarisation e, 6 doubles each.
+void frames_host(const double* inc, int n, std::vector<double>& out) {
+  out.resize(6 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const double th = inc[3 * i], ph = inc[3 * i + 1], ps = inc[3 * i + 2];
+    const double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
+    const double u[3] = {st * cp, st * sp, ct};
+    const double tht[3] = {ct * cp, ct * sp, -st};
+    const double pht[3] = {-sp, cp, 0.0};
+    for (int d = 0; d < 3; ++d) {
+      out[6 * i + d] = -u[d];
+      out[6 * i + 3 + d] = std::cos(ps) * tht[d] + std::sin(ps) * pht[d];
+    }
+  }
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double stop() {
+    float ms = 0.f;
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+int copy_in(swm_ctx* ctx, void* dst, const void* src, size_t bytes, int kind) {
+  SWM_CK(cudaMemcpyAsync(dst, src, bytes, kind == SWM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         ctx->stream));
+  return SWM_OK;
+}
+
+int set_device(swm_ctx* ctx) {
+  SWM_CK(cudaSetDevice(ctx->device));
+  return SWM_OK;
+}
+
+thread_local std::string g_stateless_err;
+
+}  // namespace
+}  // namespace swm
+
+using namespace swm;
+
+extern "C" {
+
+const char* swm_version(void) { return "swm 0.1 (sm_103a)"; }
+
+int swm_create(swm_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SWM_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SWM_EINVAL;
+  }
+  swm_ctx* ctx = new (std::nothrow) swm_ctx();
+  if (!ctx) return SWM_ENOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return SWM_ECUDA;
+  }
+  *out = ctx;
+  return SWM_OK;
+}
+
+void swm_destroy(swm_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  dfree_group(ctx, ctx->solve_bufs);
+  dfree_group(ctx, ctx->build_bufs);
+  dfree_group(ctx, ctx->cloud_bufs);
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+const char* swm_last_error(const swm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int swm_set_allocator(swm_ctx* ctx, swm_alloc_fn alloc, swm_free_fn free_fn, void* user) {
+  if (!ctx) return SWM_EINVAL;
+  if (!ctx->cloud_bufs.empty() || !ctx->build_bufs.empty() || !ctx->solve_bufs.empty())
+    return ctx->fail(SWM_ESTATE, "swm_set_allocator must precede swm_set_cloud");
+  if ((alloc == nullptr) != (free_fn == nullptr)) return ctx->fail(SWM_EINVAL, "alloc and free must both be set");
+  ctx->user_alloc = alloc;
+  ctx->user_free = free_fn;
+  ctx->user_arg = user;
+  return SWM_OK;
+}
+
+int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double* dirs, const double* lengths,
+                  const double* radii, const int32_t* nseg, int mem_kind) {
+  if (!ctx) return SWM_EINVAL;
+  ctx->err.clear();
+  if (nw < 1 || nw > (int64_t)INT32_MAX / 2) return ctx->fail(SWM_EINVAL, "nw out of range");
+  if (!centres || !dirs || !lengths || !radii || !nseg) return ctx->fail(SWM_EINVAL, "null input pointer");
+  if (mem_kind != SWM_HOST && mem_kind != SWM_DEVICE) return ctx->fail(SWM_EINVAL, "bad mem_kind");
+  SWM_TRY(set_device(ctx));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, ctx->solve_bufs);
+  dfree_group(ctx, ctx->build_bufs);
+  dfree_group(ctx, ctx->cloud_bufs);
+  ctx->built = ctx->solved = false;
+  ctx->rowwire = nullptr;
+  ctx->nw = nw;
+  auto& G = ctx->cloud_bufs;
+  SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_c, sizeof(double) * 3 * nw));
+  SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_t, sizeof(double) * 3 * nw));
+  SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_L, sizeof(double) * nw));
+  SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_a, sizeof(double) * nw));
+  SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_ns, sizeof(int32_t) * nw));
+  SWM_TRY(copy_in(ctx, ctx->u_c, centres, sizeof(double) * 3 * nw, mem_kind));
+  SWM_TRY(copy_in(ctx, ctx->u_t, dirs, sizeof(double) * 3 * nw, mem_kind));
+  SWM_TRY(copy_in(ctx, ctx->u_L, lengths, sizeof(double) * nw, mem_kind));
+  SWM_TRY(copy_in(ctx, ctx->u_a, radii, sizeof(double) * nw, mem_kind));
+  SWM_TRY(copy_in(ctx, ctx->u_ns, nseg, sizeof(int32_t) * nw, mem_kind));
+  std::vector<Buf> tmp;
+  int* flags = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&flags, 2 * sizeof(int)));
+  SWM_CK(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx->stream));
+  k_validate<<<(unsigned)ceil_div(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a,
+                                                                   ctx->u_ns, flags, flags + 1);
+  SWM_LAUNCHED();
+  int hf[2] = {0, 0};
+  SWM_CK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, tmp);
+  if (hf[0]) {
+    std::string m = "invalid cloud:";
+    if (hf[0] & 1) m += " non-finite value;";
+    if (hf[0] & 2) m += " direction not of unit length;";
+    if (hf[0] & 4) m += " length <= 0;";
+    if (hf[0] & 8) m += " radius <= 0;";
+    if (hf[0] & 16) m += " segment count outside [2, " + std::to_string(kMaxSeg) + "];";
+    dfree_group(ctx, ctx->cloud_bufs);
+    ctx->nw = 0;
+    return ctx->fail(SWM_EINVAL, m);
+  }
+  ctx->max_ns = hf[1];
+  ctx->stats = swm_stats{};
+  ctx->stats.nw = nw;
+  return SWM_OK;
+}
+
+int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
+  if (!ctx) return SWM_EINVAL;
+  ctx->err.clear();
+  if (ctx->nw < 1) return ctx->fail(SWM_ESTATE, "swm_build before swm_set_cloud");
+  if (!(k > 0.0) || !std::isfinite(k)) return ctx->fail(SWM_EINVAL, "k must be positive and finite");
+  if (std::isnan(r_c)) return ctx->fail(SWM_EINVAL, "r_c is NaN");
+  if (precision != SWM_C128 && precision != SWM_C64) return ctx->fail(SWM_EINVAL, "bad precision");
+  SWM_TRY(set_device(ctx));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, ctx->solve_bufs);
+  dfree_group(ctx, ctx->build_bufs);
+  ctx->built = ctx->solved = false;
+  ctx->rowwire = nullptr;
+  ctx->k = k;
+  ctx->rc = r_c;
+  ctx->dense = !(r_c > 0.0) || std::isinf(r_c);
+  ctx->prec = precision;
+  {
+    Timer t(ctx->stream);
+    SWM_TRY(build_pattern(ctx));
+    ctx->stats.ms_neighbour = t.stop();
+  }
+  {
+    Timer t(ctx->stream);
+    SWM_TRY(fill_blocks(ctx));
+    ctx->stats.ms_fill = t.stop();
+  }
+  {
+    Timer t(ctx->stream);
+    SWM_TRY(build_precond(ctx));
+    ctx->stats.ms_precond = t.stop();
+  }
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  SWM_CK(cudaGetLastError());
+  ctx->stats.n = ctx->N;
+  ctx->stats.nb = ctx->nb;
+  ctx->stats.nnz = ctx->full.nval;
+  ctx->built = true;
+  return SWM_OK;
+}
+
+int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restart, int max_iter,
+              double* currents_out, int out_kind) {
+  if (!ctx) return SWM_EINVAL;
+  ctx->err.clear();
+  if (!ctx->built) return ctx->fail(SWM_ESTATE, "swm_solve before swm_build");
+  if (n_inc < 1 || n_inc > 65535 || !inc) return ctx->fail(SWM_EINVAL, "bad incidence list");
+  if (!(tol > 0.0) || restart < 1 || restart > SWM_MAX_RESTART || max_iter < 0)
+    return ctx->fail(SWM_EINVAL, "bad solver parameters");
+  if (currents_out && out_kind != SWM_HOST && out_kind != SWM_DEVICE) return ctx->fail(SWM_EINVAL, "bad out_kind");
+  for (int i = 0; i < 3 * n_inc; ++i)
+    if (!std::isfinite(inc[i])) return ctx->fail(SWM_EINVAL, "non-finite incidence angle");
+  SWM_TRY(set_device(ctx));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, ctx->solve_bufs);
+  ctx->solved = false;
+  ctx->n_rhs = n_inc;
+  const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
+  auto& S = ctx->solve_bufs;
+  SWM_TRY(dalloc(ctx, S, &ctx->Bv, esz * n_inc * ctx->N));
+  SWM_TRY(dalloc(ctx, S, &ctx->Xv, esz * n_inc * ctx->N));
+  SWM_TRY(dalloc(ctx, S, (void**)&ctx->inc_dev, sizeof(double) * 3 * n_inc));
+  double* frames = nullptr;
+  SWM_TRY(dalloc(ctx, S, (void**)&frames, sizeof(double) * 6 * n_inc));
+  std::vector<double> fh;
+  frames_host(inc, n_inc, fh);
+  SWM_CK(cudaMemcpyAsync(ctx->inc_dev, inc, sizeof(double) * 3 * n_inc, cudaMemcpyHostToDevice, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(frames, fh.data(), sizeof(double) * 6 * n_inc, cudaMemcpyHostToDevice, ctx->stream));
+  {
+    Timer t(ctx->stream);
+    SWM_TRY(compute_rhs(ctx, n_inc, frames));
+    ctx->stats.ms_rhs = t.stop();
+  }
+  int rc;
+  {
+    Timer t(ctx->stream);
+    rc = gmres_solve(ctx, tol, restart, max_iter);
+    ctx->stats.ms_solve = t.stop();
+  }
+  if (rc < 0) return rc;
+  ctx->stats.n_rhs = n_inc;
+  ctx->solved = true;
+  if (currents_out) {
+    const int64_t N = ctx->N;
+    c128* dst = nullptr;
+    std::vector<Buf> tmp;
+    if (out_kind == SWM_DEVICE)
+      dst = (c128*)currents_out;
+    else
+      SWM_TRY(dalloc(ctx, tmp, (void**)&dst, sizeof(c128) * n_inc * N));
+    const dim3 grid((unsigned)ceil_div(N, 256), n_inc);
+    if (ctx->prec == SWM_C128)
+      k_to_user<double><<<grid, 256, 0, ctx->stream>>>(N, n_inc, ctx->rowwire, ctx->off, ctx->uoff, (const c128*)ctx->Xv,
+                                                       dst);
+    else
+      k_to_user<float><<<grid, 256, 0, ctx->stream>>>(N, n_inc, ctx->rowwire, ctx->off, ctx->uoff, (const c64*)ctx->Xv,
+                                                      dst);
+    SWM_LAUNCHED();
+    if (out_kind == SWM_HOST)
+      SWM_CK(cudaMemcpyAsync(currents_out, dst, sizeof(c128) * n_inc * N, cudaMemcpyDeviceToHost, ctx->stream));
+    SWM_CK(cudaStreamSynchronize(ctx->stream));
+    dfree_group(ctx, tmp);
+  }
+  return rc;
+}
+
+static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, double* sigma_out, int out_kind) {
+  if (!ctx) return SWM_EINVAL;
+  ctx->err.clear();
+  if (!ctx->solved) return ctx->fail(SWM_ESTATE, "RCS requested before swm_solve");
+  if (!sigma_out || (out_kind != SWM_HOST && out_kind != SWM_DEVICE)) return ctx->fail(SWM_EINVAL, "bad output");
+  if (!mono) {
+    if (n_obs < 1 || !obs) return ctx->fail(SWM_EINVAL, "bad observation list");
+    for (int i = 0; i < 2 * n_obs; ++i)
+      if (!std::isfinite(obs[i])) return ctx->fail(SWM_EINVAL, "non-finite observation angle");
+  }
+  SWM_TRY(set_device(ctx));
+  Timer t(ctx->stream);
+  const int R = ctx->n_rhs;
+  const int64_t npairs = mono ? R : (int64_t)R * n_obs;
+  std::vector<Buf> tmp;
+  double* obs_dev = ctx->inc_dev;
+  int stride = 3;
+  if (!mono) {
+    SWM_TRY(dalloc(ctx, tmp, (void**)&obs_dev, sizeof(double) * 2 * n_obs));
+    SWM_CK(cudaMemcpyAsync(obs_dev, obs, sizeof(double) * 2 * n_obs, cudaMemcpyHostToDevice, ctx->stream));
+    stride = 2;
+  }
+  const size_t sb = far_field_scratch_bytes(ctx->nw, npairs);
+  void* scratch = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, &scratch, sb));
+  double* sig = nullptr;
+  if (out_kind == SWM_DEVICE)
+    sig = sigma_out;
+  else
+    SWM_TRY(dalloc(ctx, tmp, (void**)&sig, sizeof(double) * 2 * npairs));
+  std::string err;
+  int rc = far_field_launch(ctx->stream, &ctx->launches, ctx->prec == SWM_C64, ctx->prec == SWM_C128, ctx->Xv, ctx->nw,
+                            ctx->N, nullptr, nullptr, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L,
+                            ctx->ns, ctx->off, true, ctx->k, R, mono ? R : n_obs, obs_dev, stride, mono, sig, scratch,
+                            sb, &err);
+  if (rc < 0) return ctx->fail(rc, err);
+  if (out_kind == SWM_HOST)
+    SWM_CK(cudaMemcpyAsync(sigma_out, sig, sizeof(double) * 2 * npairs, cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, tmp);
+  ctx->stats.ms_rcs = t.stop();
+  return SWM_OK;
+}
+
+int swm_rcs_bistatic(swm_ctx* ctx, int n_obs, const double* obs, double* sigma_out, int out_kind) {
+  return rcs_common(ctx, n_obs, obs, false, sigma_out, out_kind);
+}
+
+int swm_rcs_monostatic(swm_ctx* ctx, double* sigma_out, int out_kind) {
+  return rcs_common(ctx, 0, nullptr, true, sigma_out, out_kind);
+}
+
+int swm_get_stats(const swm_ctx* ctx, swm_stats* out) {
+  if (!ctx || !out) return SWM_EINVAL;
+  *out = ctx->stats;
+  out->kernel_launches = ctx->launches;
+  return SWM_OK;
+}
+
+int swm_get_pattern(swm_ctx* ctx, int64_t* pairs_out) {
+  if (!ctx || !pairs_out) return SWM_EINVAL;
+  if (!ctx->built) return ctx->fail(SWM_ESTATE, "no built system");
+  SWM_TRY(set_device(ctx));
+  const int64_t nw = ctx->nw, nb = ctx->nb;
+  std::vector<int64_t> rp(nw + 1);
+  std::vector<int32_t> col(nb), perm(nw);
+  SWM_CK(cudaMemcpyAsync(rp.data(), ctx->row_ptr, sizeof(int64_t) * (nw + 1), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(col.data(), ctx->col, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(perm.data(), ctx->perm, sizeof(int32_t) * nw, cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<std::pair<int64_t, int64_t>> pr;
+  pr.reserve(nb);
+  for (int64_t p = 0; p < nw; ++p)
+    for (int64_t b = rp[p]; b < rp[p + 1]; ++b) pr.emplace_back(perm[p], perm[col[b]]);
+  std::sort(pr.begin(), pr.end());
+  for (int64_t i = 0; i < nb; ++i) {
+    pairs_out[2 * i] = pr[i].first;
+    pairs_out[2 * i + 1] = pr[i].second;
+  }
+  return SWM_OK;
+}
+
+int swm_get_block(swm_ctx* ctx, int64_t p, int64_t q, double* re_im_out) {
+  if (!ctx || !re_im_out) return SWM_EINVAL;
+  if (!ctx->built) return ctx->fail(SWM_ESTATE, "no built system");
+  if (p < 0 || q < 0 || p >= ctx->nw || q >= ctx->nw) return ctx->fail(SWM_EINVAL, "wire index out of range");
+  SWM_TRY(set_device(ctx));
+  int32_t ip = 0, iq = 0;
+  SWM_CK(cudaMemcpyAsync(&ip, ctx->iperm + p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(&iq, ctx->iperm + q, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  int64_t rp[2];
+  int32_t mp = 0, mq = 0, K = 0;
+  int64_t rowbase = 0;
+  SWM_CK(cudaMemcpyAsync(rp, ctx->row_ptr + ip, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(&mp, ctx->m + ip, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(&mq, ctx->m + iq, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(&K, ctx->full.K + ip, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(&rowbase, ctx->full.rowbase + ip, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<int32_t> cols(rp[1] - rp[0]), cps(rp[1] - rp[0]);
+  SWM_CK(cudaMemcpyAsync(cols.data(), ctx->col + rp[0], sizeof(int32_t) * cols.size(), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  SWM_CK(cudaMemcpyAsync(cps.data(), ctx->full.colpos + rp[0], sizeof(int32_t) * cps.size(), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  int64_t b = -1;
+  for (size_t i = 0; i < cols.size(); ++i)
+    if (cols[i] == iq) b = (int64_t)i;
+  if (b < 0) return ctx->fail(SWM_EINVAL, "block not kept");
+  const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
+  std::vector<unsigned char> row(esz * mq);
+  for (int i = 0; i < mp; ++i) {
+    const int64_t o = rowbase + (int64_t)i * K + cps[b];
+    SWM_CK(cudaMemcpyAsync(row.data(), (unsigned char*)ctx->Z + esz * o, esz * mq, cudaMemcpyDeviceToHost, ctx->stream));
+    SWM_CK(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < mq; ++j) {
+      if (ctx->prec == SWM_C128) {
+        c128 z;
+        std::memcpy(&z, row.data() + esz * j, sizeof(z));
+        re_im_out[2 * (i * mq + j)] = z.re;
+        re_im_out[2 * (i * mq + j) + 1] = z.im;
+      } else {
+        c64 z;
+        std::memcpy(&z, row.data() + esz * j, sizeof(z));
+        re_im_out[2 * (i * mq + j)] = z.re;
+        re_im_out[2 * (i * mq + j) + 1] = z.im;
+      }
+    }
+  }
+  return SWM_OK;
+}
+
+int swm_get_rhs(swm_ctx* ctx, double* re_im_out) {
+  if (!ctx || !re_im_out) return SWM_EINVAL;
+  if (!ctx->solved) return ctx->fail(SWM_ESTATE, "no solve yet");
+  SWM_TRY(set_device(ctx));
+  const int64_t N = ctx->N;
+  const int R = ctx->n_rhs;
+  std::vector<Buf> tmp;
+  c128* dst = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&dst, sizeof(c128) * R * N));
+  const dim3 grid((unsigned)ceil_div(N, 256), R);
+  if (ctx->prec == SWM_C128)
+    k_to_user<double><<<grid, 256, 0, ctx->stream>>>(N, R, ctx->rowwire, ctx->off, ctx->uoff, (const c128*)ctx->Bv, dst);
+  else
+    k_to_user<float><<<grid, 256, 0, ctx->stream>>>(N, R, ctx->rowwire, ctx->off, ctx->uoff, (const c64*)ctx->Bv, dst);
+  SWM_LAUNCHED();
+  SWM_CK(cudaMemcpyAsync(re_im_out, dst, sizeof(c128) * R * N, cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, tmp);
+  return SWM_OK;
+}
+
+const char* swm_stateless_error(void) { return g_stateless_err.c_str(); }
+
+int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const double* dirs, const double* lengths,
+                  const int32_t* nseg, const int64_t* off, double k, int n_rhs, const double* currents, int n_obs,
+                  const double* obs, double* sigma_out) {
+  g_stateless_err.clear();
+  if (nw < 1 || n_rhs < 1 || n_obs < 1 || n_rhs > 65535 || !centres || !dirs || !lengths || !nseg || !off ||
+      !currents || !obs || !sigma_out || !(k > 0.0)) {
+    g_stateless_err = "swm_far_field: bad argument";
+    return SWM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int64_t N = 0;
+  if (cudaMemcpyAsync(&N, off + nw, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    g_stateless_err = "swm_far_field: cannot read off[nw]";
+    return SWM_ECUDA;
+  }
+  const int64_t npairs = (int64_t)n_rhs * n_obs;
+  const size_t sb = far_field_scratch_bytes(nw, npairs);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, sb, st) != cudaSuccess) {
+    cudaGetLastError();
+    g_stateless_err = "swm_far_field: scratch allocation failed";
+    return SWM_ENOMEM;
+  }
+  int rc = far_field_launch(st, nullptr, false, true, currents, nw, N, centres, dirs, nullptr, nullptr, nullptr,
+                            nullptr, nullptr, nullptr, lengths, nseg, off, false, k, n_rhs, n_obs, obs, 2, false,
+                            sigma_out, scratch, sb, &g_stateless_err);
+  cudaFreeAsync(scratch, st);
+  if (rc < 0) return rc;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    g_stateless_err = std::string("swm_far_field: ") + cudaGetErrorString(cudaGetLastError());
+    return SWM_ECUDA;
+  }
+  return SWM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Host-side state of a swm context and the internal launcher interfaces between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "swm.h"
+
+namespace swm {
+
+// Variable-block-row layout of a block-sparse matrix.  Block-row p holds m_p scalar rows; each
+// scalar row is stored contiguously as the concatenation of the block rows of its kept blocks in
+// column order, so block-row p occupies m_p * K_p entries starting at rowbase[p] with row stride
+// K_p.  Entry (i, j) of block b = (p, q) sits at rowbase[p] + i * K_p + colpos[b] + j.  colmap
+// lists, per block-row, the scalar column (internal unknown index) of each of its K_p positions.
+struct Layout {
+  int32_t* K = nullptr;        // [nw]
+  int64_t* rowbase = nullptr;  // [nw + 1]
+  int64_t* cmbase = nullptr;   // [nw + 1]
+  int32_t* colpos = nullptr;   // [nb], -1 when the block is not stored in this layout
+  int32_t* colmap = nullptr;   // [ncm]
+  int64_t nval = 0;
+  int64_t ncm = 0;
+};
+
+// Device state of the Krylov solver (one copy in device memory).
+struct KrylovDev {
+  int j;              // Arnoldi step inside the current cycle
+  int cycle_done;     // no right-hand side is active in this cycle any more
+  int all_converged;  // every right-hand side has met tol
+  int iters;          // total Arnoldi steps
+  unsigned int counter[4];  // arrival counters of the last-block reductions
+};
+
+struct Buf {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace swm
+
+struct swm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  swm_alloc_fn user_alloc = nullptr;
+  swm_free_fn user_free = nullptr;
+  void* user_arg = nullptr;
+  std::vector<swm::Buf> cloud_bufs, build_bufs, solve_bufs;
+  int64_t launches = 0;
+
+  // cloud, caller order, device
+  int64_t nw = 0;
+  double *u_c = nullptr, *u_t = nullptr, *u_L = nullptr, *u_a = nullptr;
+  int32_t* u_ns = nullptr;
+  int max_ns = 0;
+
+  // built system
+  bool built = false;
+  double k = 0.0, rc = 0.0;
+  int prec = SWM_C128;
+  bool dense = false;
+  double *cx = nullptr, *cy = nullptr, *cz = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr;
+  double *L = nullptr, *a = nullptr;
+  int32_t* ns = nullptr;     // segments per internal wire
+  int32_t* m = nullptr;      // unknowns per internal wire
+  int32_t* perm = nullptr;   // internal wire -> caller wire
+  int32_t* iperm = nullptr;  // caller wire -> internal wire
+  int64_t* off = nullptr;    // internal unknown offsets [nw + 1]
+  int64_t* uoff = nullptr;   // caller-order unknown offset of internal wire p [nw]
+  int64_t* uoff_user = nullptr;  // caller-order unknown offsets by caller wire [nw + 1]
+  int64_t N = 0;
+  int64_t nb = 0, nup = 0;
+  int64_t* row_ptr = nullptr;  // [nw + 1]
+  int32_t* col = nullptr;      // [nb]
+  int64_t* bt = nullptr;       // [nb] index of the transposed block
+  int64_t* diag_b = nullptr;   // [nw] index of block (p, p)
+  int64_t* ublk = nullptr;     // [nup] blocks (p, q) with q > p
+  int64_t* minv_off = nullptr; // [nw + 1] offsets of the m_p x m_p inverse blocks
+  int32_t* rowwire = nullptr;  // [N] internal wire of each scalar row
+  swm::Layout full, offd;
+  void* Z = nullptr;     // values of Z in layout `full`
+  void* Zp = nullptr;    // values of Z * blockdiag(Z)^-1 without its identity diagonal, layout `offd`
+  void* Minv = nullptr;  // inverses of the self blocks
+
+  // last solve
+  int n_rhs = 0;
+  void* Bv = nullptr;  // right-hand sides [n_rhs][N] (internal order)
+  void* Xv = nullptr;  // currents [n_rhs][N] (internal order)
+  double* inc_dev = nullptr;
+  bool solved = false;
+
+  swm_stats stats{};
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+};
+
+namespace swm {
+
+// allocation helpers (api.cu)
+int dalloc(swm_ctx* ctx, std::vector<Buf>& group, void** out, size_t bytes);
+void dfree_group(swm_ctx* ctx, std::vector<Buf>& group);
+
+#define SWM_CK(call)                                                                 \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return ctx->fail(SWM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define SWM_LAUNCHED()                                                                   \
+  do {                                                                                   \
+    ctx->launches++;                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess)                                                               \
+      return ctx->fail(SWM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define SWM_TRY(expr)      \
+  do {                     \
+    int rc_ = (expr);      \
+    if (rc_ < 0) return rc_; \
+  } while (0)
+
+// neighbour.cu: a0 + a1 (sort by cell, numbering, S-NFC pattern, layouts)
+int build_pattern(swm_ctx* ctx);
+// scan.cu
+int exclusive_scan_i64(swm_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);
+int exclusive_scan_i32_to_i64(swm_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host);
+// fill.cu: a2 + a3
+int fill_blocks(swm_ctx* ctx);
+// precond.cu: a5
+int build_precond(swm_ctx* ctx);
+// rhs_ff.cu: a4 + a7
+int compute_rhs(swm_ctx* ctx, int n_inc, const double* inc_dev);
+size_t far_field_scratch_bytes(int64_t nw, int64_t npairs);
+int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64, const void* cur, int64_t nw,
+                     int64_t N, const double* c3, const double* t3, const double* cx, const double* cy,
+                     const double* cz, const double* tx, const double* ty, const double* tz, const double* Ls,
+                     const int32_t* ns, const int64_t* off, bool soa, double k, int n_rhs, int n_obs,
+                     const double* obs, int obs_stride, bool mono, double* sigma, void* scratch, size_t scratch_bytes,
+                     std::string* err);
+// krylov.cu: a6
+int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
+
+}  // namespace swm

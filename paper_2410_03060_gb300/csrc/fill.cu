@@ -1,0 +1,521 @@
+// Fill of the kept blocks of Z (Sec. II-A, Eqs. (5)-(8); analytic singularity extraction and
+// Gaussian quadrature as named after Eq. (8)).
+//
+// Z_pq[i][j] = (t_p.t_q) sum_{u,v} I_{a b}(u, v) - 1/(k^2 D_p D_q) sum_{u,v} s_a s_b I_G(u, v),
+// where basis i (vertex i+1) rises on segment i (slope +1/D) and falls on segment i+1 (slope
+// -1/D), I_ab(u, v) is the integral of the two linear shapes against G over segments u of p and
+// v of q, and I_G = sum of the four.
+//
+// Self blocks (p = q), float64, one warp per wire: the double integral over two segments of one
+// straight wire depends only on s - s', so with offset d = u - v it is exactly
+// D^2 int_{-1}^{1} W_ab(w) G(D (d + w)) dw, W_ab the convolution of the two shapes (piecewise
+// cubic).  Each half uses 8 Gauss points; for |d| <= 1 the static 1/(4 pi R) part is integrated
+// in closed form.  The block is Toeplitz in i - j.
+//
+// Mutual blocks (p < q), one CTA per batch of blocks: one thread per block sets up the block's
+// geometry in float64 (centre difference, near/far decision), then threads share the batch's
+// segment pairs (tensor Gauss-Legendre, 4 points per segment, 8 for near wires), accumulate
+// their four shape integrals in shared memory, and finally assemble the m_p x m_q entries,
+// writing Z_pq and Z_qp = Z_pq^T.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace swm {
+
+struct GLTable {
+  double x4[4], w4[4], x8[8], w8[8];
+};
+
+// Gauss-Legendre nodes and weights on [0, 1] by Newton iteration on P_n.
+static void gauss_legendre01(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+      }
+      dp = n * (z * p0 - p1) / (z * z - 1.0);
+      const double dz = p0 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[n - 1 - i] = 0.5 * (1.0 + z);
+    w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);  // (2/((1-z^2) P'^2)) / 2
+  }
+}
+
+static GLTable make_gl() {
+  GLTable t;
+  gauss_legendre01(4, t.x4, t.w4);
+  gauss_legendre01(8, t.x8, t.w8);
+  return t;
+}
+
+// ------------------------------------------------------------------------------------------------
+// self blocks
+
+// Convolution W_ab(w) of shape a on the test segment with shape b on the source segment
+// (a, b: 0 = rise x, 1 = fall 1 - x), as cubic coefficients in w for half 0 (w in [-1, 0]) and
+// half 1 (w in [0, 1]).  Derived from W_ab(w) = int phi_a(x) phi_b(x - w) dx.
+__device__ __constant__ double c_self_poly[2][4][4] = {
+    // half 0: rr, rf, fr, ff
+    {{1.0 / 3.0, 0.5, 0.0, -1.0 / 6.0},
+     {1.0 / 6.0, 0.5, 0.5, 1.0 / 6.0},
+     {1.0 / 6.0, -0.5, -0.5, 1.0 / 6.0},
+     {1.0 / 3.0, 0.5, 0.0, -1.0 / 6.0}},
+    // half 1
+    {{1.0 / 3.0, -0.5, 0.0, 1.0 / 6.0},
+     {1.0 / 6.0, 0.5, -0.5, -1.0 / 6.0},
+     {1.0 / 6.0, -0.5, 0.5, -1.0 / 6.0},
+     {1.0 / 3.0, -0.5, 0.0, 1.0 / 6.0}},
+};
+
+// Antiderivatives of t^n / sqrt(t^2 + al^2), n = 0..3, at t.
+__device__ __forceinline__ void static_prims(double t, double al, double out[4]) {
+  const double r = sqrt(t * t + al * al);
+  const double as = asinh(t / al);
+  out[0] = as;
+  out[1] = r;
+  out[2] = 0.5 * (t * r - al * al * as);
+  out[3] = (t * t - 2.0 * al * al) * r / 3.0;
+}
+
+// I[ab] for segment offset d >= 0 of a wire with segment length D and radius a (times 4 pi).
+__device__ void self_offset(int d, double D, double a, double k, const GLTable& gl, c128 out[4]) {
+  for (int ab = 0; ab < 4; ++ab) out[ab] = mkc(0.0, 0.0);
+  const double al = a / D;
+  for (int half = 0; half < 2; ++half) {
+    const double w0 = half ? 0.0 : -1.0;
+    for (int g = 0; g < 8; ++g) {
+      const double w = w0 + gl.x8[g];
+      const double t = d + w;
+      const double R = sqrt(D * D * t * t + a * a);
+      double s, c;
+      sincos(k * R, &s, &c);
+      // full kernel exp(-jkR)/R, or the smooth remainder (exp(-jkR) - 1)/R for |d| <= 1
+      const double re = (d <= 1 ? (c - 1.0) : c) / R, im = -s / R;
+      const double ww = gl.w8[g];
+      for (int ab = 0; ab < 4; ++ab) {
+        const double* P = c_self_poly[half][ab];
+        const double W = ((P[3] * w + P[2]) * w + P[1]) * w + P[0];
+        out[ab].re += ww * W * re;
+        out[ab].im += ww * W * im;
+      }
+    }
+    if (d <= 1) {
+      // static part: int W(t - d) / (D sqrt(t^2 + al^2)) dt over t in [w0 + d, w0 + 1 + d]
+      double A0[4], A1[4];
+      static_prims(w0 + d, al, A0);
+      static_prims(w0 + 1.0 + d, al, A1);
+      for (int ab = 0; ab < 4; ++ab) {
+        const double* P = c_self_poly[half][ab];
+        // coefficients of W(t - d) in powers of t
+        const double dd = (double)d;
+        const double q0 = P[0] - P[1] * dd + P[2] * dd * dd - P[3] * dd * dd * dd;
+        const double q1 = P[1] - 2.0 * P[2] * dd + 3.0 * P[3] * dd * dd;
+        const double q2 = P[2] - 3.0 * P[3] * dd;
+        const double q3 = P[3];
+        const double st = q0 * (A1[0] - A0[0]) + q1 * (A1[1] - A0[1]) + q2 * (A1[2] - A0[2]) + q3 * (A1[3] - A0[3]);
+        out[ab].re += st / D;
+      }
+    }
+  }
+  for (int ab = 0; ab < 4; ++ab) out[ab] = (D * D) * out[ab];
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(128) k_self_blocks(int64_t nw, const double* __restrict__ Ls, const double* __restrict__ as,
+                                                    const int32_t* __restrict__ ns, double k, GLTable gl,
+                                                    const int64_t* __restrict__ diag_b, Layout lay,
+                                                    cplx<TV>* __restrict__ Z) {
+  __shared__ c128 sI[4][kMaxSeg][4];  // per warp: offset d >= 0, ab
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * 4 + wl;
+  if (p >= nw) return;
+  const int n = ns[p];
+  const double D = Ls[p] / n, a = as[p];
+  if (lane < n) {
+    c128 I[4];
+    self_offset(lane, D, a, k, gl, I);
+    for (int ab = 0; ab < 4; ++ab) sI[wl][lane][ab] = I[ab];
+  }
+  __syncwarp();
+  const int m = n - 1;
+  const int K = lay.K[p];
+  const int64_t base = lay.rowbase[p] + lay.colpos[diag_b[p]];
+  const double sc = 1.0 / (k * k * D * D);
+  // I_ab at offset e (any sign): I_ab(-e) = I_ba(e)
+  auto get = [&](int e, int ab) -> c128 {
+    if (e >= 0) return sI[wl][e][ab];
+    const int ba = (ab == 1) ? 2 : (ab == 2 ? 1 : ab);
+    return sI[wl][-e][ba];
+  };
+  auto IG = [&](int e) -> c128 { return get(e, 0) + get(e, 1) + get(e, 2) + get(e, 3); };
+  for (int it = lane; it < m * m; it += 32) {
+    const int i = it / m, j = it % m;
+    const int d = i - j;
+    // rise(i) x rise(j): offset d; rise x fall(j+1): d - 1; fall(i+1) x rise: d + 1; fall x fall: d
+    c128 vec = get(d, 0) + get(d - 1, 1) + get(d + 1, 2) + get(d, 3);
+    c128 sca = IG(d) - IG(d - 1) - IG(d + 1) + IG(d);
+    c128 z = mkc((vec.re - sc * sca.re) / kFourPi, (vec.im - sc * sca.im) / kFourPi);
+    Z[base + (int64_t)i * K + j] = ccast<TV>(z);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// mutual blocks
+
+struct BlockGeo {
+  float D[3], tp[3], tq[3];  // FP32 copies (fast path); the FP64 path re-reads FP64 geometry
+  float Lp, Lq, a2, tpq;
+  int nsp, nsq, nq, item0;   // item0: first segment pair of this block in the batch
+  int out0;                  // first output entry of this block in the batch
+  int p, q;
+  int64_t bpq, bqp;          // value offsets of Z_pq[0][0] and Z_qp[0][0]
+  int Kp, Kq;
+};
+
+// Shortest distance between two finite segments (float64): convex quadratic over a rectangle,
+// interior stationary point if it lies inside, else the best clamped optimum on the four edges.
+__device__ double seg_dist(const double D[3], const double tp[3], double hp, const double tq[3], double hq) {
+  const double b = tp[0] * tq[0] + tp[1] * tq[1] + tp[2] * tq[2];
+  const double dp = D[0] * tp[0] + D[1] * tp[1] + D[2] * tp[2];
+  const double dq = D[0] * tq[0] + D[1] * tq[1] + D[2] * tq[2];
+  auto d2 = [&](double s, double sq) {
+    double v0 = D[0] + s * tp[0] - sq * tq[0], v1 = D[1] + s * tp[1] - sq * tq[1], v2 = D[2] + s * tp[2] - sq * tq[2];
+    return v0 * v0 + v1 * v1 + v2 * v2;
+  };
+  double best = INFINITY;
+  const double det = 1.0 - b * b;
+  if (det > 1e-12) {
+    const double s = (b * dq - dp) / det, sq = (dq - b * dp) / det;
+    if (fabs(s) <= hp && fabs(sq) <= hq) best = d2(s, sq);
+  }
+  for (int e = 0; e < 2; ++e) {
+    const double s = e ? hp : -hp;
+    const double sq = fmin(fmax(dq + b * s, -hq), hq);
+    best = fmin(best, d2(s, sq));
+  }
+  for (int e = 0; e < 2; ++e) {
+    const double sq = e ? hq : -hq;
+    const double s = fmin(fmax(b * sq - dp, -hp), hp);
+    best = fmin(best, d2(s, sq));
+  }
+  return sqrt(best);
+}
+
+template <typename R>
+struct SegI {
+  cplx<R> rr, rf, fr, ff;
+};
+
+// Shape integrals of one segment pair (without the 1/(4 pi) D_p D_q factor).
+template <int NQ>
+__device__ __forceinline__ void seg_pair_f32(const BlockGeo& G, int u, int v, float k, const float* xg, const float* wg,
+                                             SegI<float>& out) {
+  float Ex[NQ], Ey[NQ], Ez[NQ], Qx[NQ], Qy[NQ], Qz[NQ];
+  const float Dp = G.Lp / G.nsp, Dq = G.Lq / G.nsq;
+#pragma unroll
+  for (int g = 0; g < NQ; ++g) {
+    const float sp = -0.5f * G.Lp + ((float)u + xg[g]) * Dp;
+    Ex[g] = G.D[0] + sp * G.tp[0];
+    Ey[g] = G.D[1] + sp * G.tp[1];
+    Ez[g] = G.D[2] + sp * G.tp[2];
+    const float sq = -0.5f * G.Lq + ((float)v + xg[g]) * Dq;
+    Qx[g] = sq * G.tq[0];
+    Qy[g] = sq * G.tq[1];
+    Qz[g] = sq * G.tq[2];
+  }
+  float rrr = 0.f, rri = 0.f, rfr = 0.f, rfi = 0.f, frr = 0.f, fri = 0.f, ffr = 0.f, ffi = 0.f;
+#pragma unroll
+  for (int g = 0; g < NQ; ++g) {
+    float Ar = 0.f, Ai = 0.f, Br = 0.f, Bi = 0.f;
+#pragma unroll
+    for (int h = 0; h < NQ; ++h) {
+      const float dx = Ex[g] - Qx[h], dy = Ey[g] - Qy[h], dz = Ez[g] - Qz[h];
+      const float R2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, G.a2)));
+      const float ri = rsqrtf(R2);
+      const float Rr = R2 * ri;
+      float s, c;
+      __sincosf(k * Rr, &s, &c);
+      const float gr = c * ri, gi = -s * ri;
+      const float wh = wg[h], wxh = wg[h] * xg[h];
+      Ar = fmaf(wh, gr, Ar);
+      Ai = fmaf(wh, gi, Ai);
+      Br = fmaf(wxh, gr, Br);
+      Bi = fmaf(wxh, gi, Bi);
+    }
+    const float wr = wg[g] * xg[g], wf = wg[g] - wr;
+    const float Cr = Ar - Br, Ci = Ai - Bi;
+    rrr = fmaf(wr, Br, rrr);
+    rri = fmaf(wr, Bi, rri);
+    rfr = fmaf(wr, Cr, rfr);
+    rfi = fmaf(wr, Ci, rfi);
+    frr = fmaf(wf, Br, frr);
+    fri = fmaf(wf, Bi, fri);
+    ffr = fmaf(wf, Cr, ffr);
+    ffi = fmaf(wf, Ci, ffi);
+  }
+  out.rr = mkc(rrr, rri);
+  out.rf = mkc(rfr, rfi);
+  out.fr = mkc(frr, fri);
+  out.ff = mkc(ffr, ffi);
+}
+
+template <int NQ>
+__device__ __forceinline__ void seg_pair_f64(const double* __restrict__ cx, const double* __restrict__ cy,
+                                             const double* __restrict__ cz, const double* __restrict__ tx,
+                                             const double* __restrict__ ty, const double* __restrict__ tz,
+                                             const double* __restrict__ Ls, const double* __restrict__ as,
+                                             const BlockGeo& G, int u, int v, double k, const double* xg,
+                                             const double* wg, SegI<double>& out) {
+  const int p = G.p, q = G.q;
+  const double D[3] = {cx[p] - cx[q], cy[p] - cy[q], cz[p] - cz[q]};
+  const double tp[3] = {tx[p], ty[p], tz[p]}, tq[3] = {tx[q], ty[q], tz[q]};
+  const double Lp = Ls[p], Lq = Ls[q];
+  const double a2 = 0.5 * (as[p] * as[p] + as[q] * as[q]);
+  const double Dp = Lp / G.nsp, Dq = Lq / G.nsq;
+  double rrr = 0, rri = 0, rfr = 0, rfi = 0, frr = 0, fri = 0, ffr = 0, ffi = 0;
+  for (int g = 0; g < NQ; ++g) {
+    const double sp = -0.5 * Lp + (u + xg[g]) * Dp;
+    const double Ex = D[0] + sp * tp[0], Ey = D[1] + sp * tp[1], Ez = D[2] + sp * tp[2];
+    double Ar = 0, Ai = 0, Br = 0, Bi = 0;
+    for (int h = 0; h < NQ; ++h) {
+      const double sq = -0.5 * Lq + (v + xg[h]) * Dq;
+      const double dx = Ex - sq * tq[0], dy = Ey - sq * tq[1], dz = Ez - sq * tq[2];
+      const double R = sqrt(dx * dx + dy * dy + dz * dz + a2);
+      double s, c;
+      sincos(k * R, &s, &c);
+      const double gr = c / R, gi = -s / R;
+      Ar += wg[h] * gr;
+      Ai += wg[h] * gi;
+      Br += wg[h] * xg[h] * gr;
+      Bi += wg[h] * xg[h] * gi;
+    }
+    const double wr = wg[g] * xg[g], wf = wg[g] - wr;
+    rrr += wr * Br;
+    rri += wr * Bi;
+    rfr += wr * (Ar - Br);
+    rfi += wr * (Ai - Bi);
+    frr += wf * Br;
+    fri += wf * Bi;
+    ffr += wf * (Ar - Br);
+    ffi += wf * (Ai - Bi);
+  }
+  out.rr = mkc(rrr, rri);
+  out.rf = mkc(rfr, rfi);
+  out.fr = mkc(frr, fri);
+  out.ff = mkc(ffr, ffi);
+}
+
+constexpr int kFillThreads = 256;
+
+__host__ __device__ constexpr size_t round16(size_t x) { return (x + 15) / 16 * 16; }
+
+// One CTA per batch of `nbatch` upper blocks.  Shared memory: BlockGeo[nbatch], item and output
+// prefix arrays, and SegI<R> for every segment pair of the batch (capacity `cap`).
+template <typename R, typename TV>
+__global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
+    int64_t nup, const int64_t* __restrict__ ublk, const int32_t* __restrict__ col, const int64_t* __restrict__ bt,
+    const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
+    const double* __restrict__ tx, const double* __restrict__ ty, const double* __restrict__ tz,
+    const double* __restrict__ Ls, const double* __restrict__ as, const int32_t* __restrict__ ns, double k,
+    GLTable gl, Layout lay, int nbatch, cplx<TV>* __restrict__ Z) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t o_item = round16(sizeof(BlockGeo) * nbatch);
+  const size_t o_out = o_item + round16(sizeof(int) * (nbatch + 1));
+  const size_t o_seg = o_out + round16(sizeof(int) * (nbatch + 1));
+  BlockGeo* geo = reinterpret_cast<BlockGeo*>(smem);
+  int* item_pre = reinterpret_cast<int*>(smem + o_item);  // nbatch + 1
+  int* out_pre = reinterpret_cast<int*>(smem + o_out);    // nbatch + 1
+  SegI<R>* seg = reinterpret_cast<SegI<R>*>(smem + o_seg);
+  __shared__ float xs4[4], ws4[4], xs8[8], ws8[8];
+
+  const int tid = threadIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.x * nbatch;
+  const int nb_here = (int)min((int64_t)nbatch, nup - b0);
+  if (tid < 4) {
+    xs4[tid] = (float)gl.x4[tid];
+    ws4[tid] = (float)gl.w4[tid];
+  }
+  if (tid < 8) {
+    xs8[tid] = (float)gl.x8[tid];
+    ws8[tid] = (float)gl.w8[tid];
+  }
+  // --- per-block setup, float64, one thread per block
+  if (tid < nb_here) {
+    const int64_t b = ublk[b0 + tid];
+    const int q = col[b];
+    const int64_t bq = bt[b];
+    const int p = col[bq];
+    BlockGeo G;
+    const double D[3] = {cx[p] - cx[q], cy[p] - cy[q], cz[p] - cz[q]};
+    const double tp[3] = {tx[p], ty[p], tz[p]}, tq[3] = {tx[q], ty[q], tz[q]};
+    const double Lp = Ls[p], Lq = Ls[q];
+    const int nsp = ns[p], nsq = ns[q];
+    const double dmax = fmax(Lp / nsp, Lq / nsq);
+    // near rule: exact segment distance < longer segment length; skipped when the centroid
+    // distance already exceeds half the two lengths plus that length
+    int nq = 4;
+    const double reach = 0.5 * (Lp + Lq) + dmax;
+    const double cd2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+    if (cd2 < reach * reach * (1.0 + 1e-12)) {
+      if (seg_dist(D, tp, 0.5 * Lp, tq, 0.5 * Lq) < dmax) nq = 8;
+    }
+    for (int c = 0; c < 3; ++c) {
+      G.D[c] = (float)D[c];
+      G.tp[c] = (float)tp[c];
+      G.tq[c] = (float)tq[c];
+    }
+    G.Lp = (float)Lp;
+    G.Lq = (float)Lq;
+    G.a2 = (float)(0.5 * (as[p] * as[p] + as[q] * as[q]));
+    G.tpq = (float)(tp[0] * tq[0] + tp[1] * tq[1] + tp[2] * tq[2]);
+    G.nsp = nsp;
+    G.nsq = nsq;
+    G.nq = nq;
+    G.p = p;
+    G.q = q;
+    G.Kp = lay.K[p];
+    G.Kq = lay.K[q];
+    G.bpq = lay.rowbase[p] + lay.colpos[b];
+    G.bqp = lay.rowbase[q] + lay.colpos[bq];
+    geo[tid] = G;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int it = 0, ot = 0;
+    for (int t = 0; t < nb_here; ++t) {
+      item_pre[t] = it;
+      out_pre[t] = ot;
+      geo[t].item0 = it;
+      geo[t].out0 = ot;
+      it += geo[t].nsp * geo[t].nsq;
+      ot += (geo[t].nsp - 1) * (geo[t].nsq - 1);
+    }
+    item_pre[nb_here] = it;
+    out_pre[nb_here] = ot;
+  }
+  __syncthreads();
+
+  // --- segment pairs
+  const int nitems = item_pre[nb_here];
+  for (int it = tid; it < nitems; it += kFillThreads) {
+    int lo = 0, hi = nb_here - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (item_pre[mid] <= it)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const BlockGeo& G = geo[lo];
+    const int local = it - G.item0;
+    const int u = local / G.nsq, v = local % G.nsq;
+    SegI<R> s;
+    if constexpr (sizeof(R) == 4) {
+      if (G.nq == 4)
+        seg_pair_f32<4>(G, u, v, (float)k, xs4, ws4, s);
+      else
+        seg_pair_f32<8>(G, u, v, (float)k, xs8, ws8, s);
+    } else {
+      if (G.nq == 4)
+        seg_pair_f64<4>(cx, cy, cz, tx, ty, tz, Ls, as, G, u, v, k, gl.x4, gl.w4, s);
+      else
+        seg_pair_f64<8>(cx, cy, cz, tx, ty, tz, Ls, as, G, u, v, k, gl.x8, gl.w8, s);
+    }
+    seg[it] = s;
+  }
+  __syncthreads();
+
+  // --- assembly of the m_p x m_q entries, written to Z_pq and Z_qp
+  const int nout = out_pre[nb_here];
+  for (int ot = tid; ot < nout; ot += kFillThreads) {
+    int lo = 0, hi = nb_here - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (out_pre[mid] <= ot)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const BlockGeo& G = geo[lo];
+    const int mq = G.nsq - 1;
+    const int local = ot - G.out0;
+    const int i = local / mq, j = local % mq;
+    const SegI<R>* S = seg + G.item0;
+    const int nsq = G.nsq;
+    // basis i rises on segment i and falls on segment i + 1 (same for j on wire q)
+    const SegI<R> a00 = S[i * nsq + j], a01 = S[i * nsq + j + 1], a10 = S[(i + 1) * nsq + j],
+                  a11 = S[(i + 1) * nsq + j + 1];
+    const cplx<R> vec = a00.rr + a01.rf + a10.fr + a11.ff;
+    auto IG = [](const SegI<R>& x) { return x.rr + x.rf + x.fr + x.ff; };
+    const cplx<R> sca = IG(a00) - IG(a01) - IG(a10) + IG(a11);
+    double Dp, Dq, tpq;
+    if constexpr (sizeof(R) == 4) {
+      Dp = (double)G.Lp / G.nsp;
+      Dq = (double)G.Lq / G.nsq;
+      tpq = G.tpq;
+    } else {
+      Dp = Ls[G.p] / G.nsp;
+      Dq = Ls[G.q] / G.nsq;
+      tpq = tx[G.p] * tx[G.q] + ty[G.p] * ty[G.q] + tz[G.p] * tz[G.q];
+    }
+    const R f = (R)(Dp * Dq / kFourPi);
+    const R sc = (R)(1.0 / (k * k * Dp * Dq));
+    const cplx<R> z = mkc<R>(f * ((R)tpq * vec.re - sc * sca.re), f * ((R)tpq * vec.im - sc * sca.im));
+    const cplx<TV> zt = ccast<TV>(z);
+    Z[G.bpq + (int64_t)i * G.Kp + j] = zt;
+    Z[G.bqp + (int64_t)j * G.Kq + i] = zt;
+  }
+}
+
+template <typename R, typename TV>
+int launch_fill(swm_ctx* ctx, const GLTable& gl) {
+  const int ms = ctx->max_ns;
+  const int items_per_block = ms * ms;
+  // shared budget for segment pairs: 48 KB (float) or 64 KB (double)
+  const int cap_bytes = sizeof(R) == 4 ? 48 * 1024 : 64 * 1024;
+  int nbatch = std::max(1, cap_bytes / (int)(items_per_block * sizeof(SegI<R>)));
+  nbatch = std::min(nbatch, kFillThreads);
+  const size_t smem = round16(sizeof(BlockGeo) * nbatch) + 2 * round16(sizeof(int) * (nbatch + 1)) +
+                      sizeof(SegI<R>) * nbatch * items_per_block;
+  SWM_CK(cudaFuncSetAttribute(k_mutual_blocks<R, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (ctx->nup > 0) {
+    const int64_t grid = ceil_div(ctx->nup, nbatch);
+    k_mutual_blocks<R, TV><<<(unsigned)grid, kFillThreads, smem, ctx->stream>>>(
+        ctx->nup, ctx->ublk, ctx->col, ctx->bt, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->a,
+        ctx->ns, ctx->k, gl, ctx->full, nbatch, reinterpret_cast<cplx<TV>*>(ctx->Z));
+    SWM_LAUNCHED();
+  }
+  return SWM_OK;
+}
+
+int fill_blocks(swm_ctx* ctx) {
+  static const GLTable gl = make_gl();
+  const int64_t nw = ctx->nw;
+  const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Z, esz * std::max<int64_t>(1, ctx->full.nval)));
+  const unsigned grid_self = (unsigned)ceil_div(nw, 4);
+  if (ctx->prec == SWM_C128) {
+    k_self_blocks<double><<<grid_self, 128, 0, ctx->stream>>>(nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b,
+                                                               ctx->full, reinterpret_cast<c128*>(ctx->Z));
+    SWM_LAUNCHED();
+    SWM_TRY((launch_fill<double, double>(ctx, gl)));
+  } else {
+    k_self_blocks<float><<<grid_self, 128, 0, ctx->stream>>>(nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b,
+                                                              ctx->full, reinterpret_cast<c64*>(ctx->Z));
+    SWM_LAUNCHED();
+    SWM_TRY((launch_fill<float, float>(ctx, gl)));
+  }
+  return SWM_OK;
+}
+
+}  // namespace swm

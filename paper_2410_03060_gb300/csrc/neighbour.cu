@@ -1,0 +1,401 @@
+// S-NFC neighbour search (Sec. II-B, Eq. neardef) and the numbering of unknowns (Sec. II-A).
+//
+// Wires are binned into a uniform grid of cell side h >= r_c and renumbered by (cell, caller
+// index); a wire's S-NFC partners then lie in the 27 surrounding cells, whose wires occupy nine
+// contiguous index ranges.  One warp per wire tests 32 candidates at a time in float64 and
+// compacts the kept ones with a ballot, so each block-row comes out sorted by column.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace swm {
+
+namespace {
+
+constexpr int64_t kMaxCells = int64_t(1) << 24;
+
+struct Grid {
+  double x0, y0, z0, h;
+  int nx, ny, nz;
+};
+
+__global__ void k_bbox_partial(const double* __restrict__ c, int64_t nw, double* __restrict__ part) {
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double v = c[3 * i + d];
+      mn[d] = fmin(mn[d], v);
+      mx[d] = fmax(mx[d], v);
+    }
+  }
+  __shared__ double s[6][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+      mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+    }
+    if (lane == 0) {
+      s[d][w] = mn[d];
+      s[3 + d][w] = mx[d];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int d = threadIdx.x;
+    double v = s[d][0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = d < 3 ? fmin(v, s[d][k]) : fmax(v, s[d][k]);
+    part[blockIdx.x * 6 + d] = v;
+  }
+}
+
+__global__ void k_bbox_final(const double* __restrict__ part, int np, double* __restrict__ out) {
+  if (threadIdx.x < 6) {
+    const int d = threadIdx.x;
+    double v = part[d];
+    for (int k = 1; k < np; ++k) v = d < 3 ? fmin(v, part[k * 6 + d]) : fmax(v, part[k * 6 + d]);
+    out[d] = v;
+  }
+}
+
+__device__ __forceinline__ int cell_coord(double v, double v0, double h, int n) {
+  int i = (int)floor((v - v0) / h);
+  return min(max(i, 0), n - 1);
+}
+
+__global__ void k_cell_ids(const double* __restrict__ c, int64_t nw, Grid g, int32_t* __restrict__ cid,
+                           int32_t* __restrict__ cnt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  const int ix = cell_coord(c[3 * i], g.x0, g.h, g.nx);
+  const int iy = cell_coord(c[3 * i + 1], g.y0, g.h, g.ny);
+  const int iz = cell_coord(c[3 * i + 2], g.z0, g.h, g.nz);
+  const int id = (iz * g.ny + iy) * g.nx + ix;
+  cid[i] = id;
+  atomicAdd(&cnt[id], 1);
+}
+
+__global__ void k_scatter_unordered(const int32_t* __restrict__ cid, int64_t nw, const int64_t* __restrict__ cstart,
+                                    int32_t* __restrict__ fill, int32_t* __restrict__ tmp) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  const int id = cid[i];
+  const int64_t pos = cstart[id] + atomicAdd(&fill[id], 1);
+  tmp[pos] = (int32_t)i;
+}
+
+// Deterministic order inside a cell: a wire's rank is the number of wires of its cell with a
+// smaller caller index.
+__global__ void k_rank_in_cell(const int32_t* __restrict__ cid, int64_t nw, const int64_t* __restrict__ cstart,
+                               const int32_t* __restrict__ tmp, int32_t* __restrict__ perm,
+                               int32_t* __restrict__ iperm, int32_t* __restrict__ cid_sorted) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  const int id = cid[i];
+  const int64_t s = cstart[id], e = cstart[id + 1];
+  int64_t r = 0;
+  for (int64_t t = s; t < e; ++t) r += (tmp[t] < (int32_t)i);
+  perm[s + r] = (int32_t)i;
+  iperm[i] = (int32_t)(s + r);
+  cid_sorted[s + r] = id;
+}
+
+__global__ void k_gather_geometry(int64_t nw, const int32_t* __restrict__ perm, const double* __restrict__ uc,
+                                  const double* __restrict__ ut, const double* __restrict__ uL,
+                                  const double* __restrict__ ua, const int32_t* __restrict__ uns,
+                                  double* cx, double* cy, double* cz, double* tx, double* ty, double* tz, double* L,
+                                  double* a, int32_t* ns, int32_t* m) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nw) return;
+  const int64_t u = perm[p];
+  cx[p] = uc[3 * u];
+  cy[p] = uc[3 * u + 1];
+  cz[p] = uc[3 * u + 2];
+  tx[p] = ut[3 * u];
+  ty[p] = ut[3 * u + 1];
+  tz[p] = ut[3 * u + 2];
+  L[p] = uL[u];
+  a[p] = ua[u];
+  ns[p] = uns[u];
+  m[p] = uns[u] - 1;
+}
+
+__global__ void k_user_m(int64_t nw, const int32_t* __restrict__ uns, int32_t* __restrict__ um) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nw) um[i] = uns[i] - 1;
+}
+
+__global__ void k_uoff_by_internal(int64_t nw, const int32_t* __restrict__ perm, const int64_t* __restrict__ uoff_user,
+                                   int64_t* __restrict__ uoff) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < nw) uoff[p] = uoff_user[perm[p]];
+}
+
+// mode 0: count kept partners per wire; mode 1: write them (sorted) into col.
+__global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double* __restrict__ cy,
+                        const double* __restrict__ cz, const int32_t* __restrict__ cid, const int64_t* __restrict__ cstart,
+                        Grid g, double rc2, int dense, int mode, int32_t* __restrict__ row_cnt,
+                        const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col) {
+  const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= nw) return;
+  const int id = cid[p];
+  const int ix = id % g.nx, iy = (id / g.nx) % g.ny, iz = id / (g.nx * g.ny);
+  const double px = cx[p], py = cy[p], pz = cz[p];
+  int64_t count = 0;
+  const int64_t base = mode ? row_ptr[p] : 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = iz + dz;
+    if (z < 0 || z >= g.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = iy + dy;
+      if (y < 0 || y >= g.ny) continue;
+      const int x0 = max(ix - 1, 0), x1 = min(ix + 1, g.nx - 1);
+      const int64_t c0 = ((int64_t)z * g.ny + y) * g.nx + x0;
+      const int64_t c1 = ((int64_t)z * g.ny + y) * g.nx + x1;
+      const int64_t q0 = cstart[c0], q1 = cstart[c1 + 1];
+      for (int64_t qb = q0; qb < q1; qb += 32) {
+        const int64_t q = qb + lane;
+        bool keep = false;
+        if (q < q1) {
+          if (dense) {
+            keep = true;
+          } else {
+            const double dx = px - cx[q], dyy = py - cy[q], dzz = pz - cz[q];
+            // (dx*dx + dy*dy) + dz*dz, each operation rounded separately (no contraction)
+            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dyy, dyy)), __dmul_rn(dzz, dzz));
+            keep = d2 <= rc2;
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (mode && keep) col[base + count + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
+        count += __popc(bal);
+      }
+    }
+  }
+  if (!mode && lane == 0) row_cnt[p] = (int32_t)count;
+}
+
+__device__ __forceinline__ int64_t find_in_row(const int32_t* __restrict__ col, int64_t b, int64_t e, int32_t key) {
+  while (b < e) {
+    const int64_t mid = (b + e) >> 1;
+    if (col[mid] < key)
+      b = mid + 1;
+    else
+      e = mid;
+  }
+  return b;
+}
+
+__global__ void k_row_meta(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ m, int64_t* __restrict__ diag_b, int64_t* __restrict__ ucnt,
+                           int32_t* __restrict__ colpos_f, int32_t* __restrict__ K_f, int32_t* __restrict__ colpos_o,
+                           int32_t* __restrict__ K_o, int64_t* __restrict__ ent_f, int64_t* __restrict__ ent_o) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nw) return;
+  const int64_t b0 = row_ptr[p], b1 = row_ptr[p + 1];
+  const int64_t d = find_in_row(col, b0, b1, (int32_t)p);
+  diag_b[p] = d;
+  ucnt[p] = b1 - d - 1;
+  int32_t kf = 0, ko = 0;
+  for (int64_t b = b0; b < b1; ++b) {
+    const int32_t mq = m[col[b]];
+    colpos_f[b] = kf;
+    kf += mq;
+    if (col[b] == (int32_t)p) {
+      colpos_o[b] = -1;
+    } else {
+      colpos_o[b] = ko;
+      ko += mq;
+    }
+  }
+  K_f[p] = kf;
+  K_o[p] = ko;
+  ent_f[p] = (int64_t)m[p] * kf;
+  ent_o[p] = (int64_t)m[p] * ko;
+}
+
+__global__ void k_transpose_and_upper(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                      const int64_t* __restrict__ diag_b, const int64_t* __restrict__ ubase,
+                                      int64_t* __restrict__ bt, int64_t* __restrict__ ublk) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nw) return;
+  const int64_t b0 = row_ptr[p], b1 = row_ptr[p + 1];
+  for (int64_t b = b0; b < b1; ++b) {
+    const int32_t q = col[b];
+    bt[b] = find_in_row(col, row_ptr[q], row_ptr[q + 1], (int32_t)p);
+  }
+  int64_t u = ubase[p];
+  for (int64_t b = diag_b[p] + 1; b < b1; ++b) ublk[u++] = b;
+}
+
+__global__ void k_colmap(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                         const int32_t* __restrict__ m, const int64_t* __restrict__ off, const int32_t* __restrict__ colpos,
+                         const int64_t* __restrict__ cmbase, int32_t* __restrict__ colmap) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nw) return;
+  for (int64_t b = row_ptr[p]; b < row_ptr[p + 1]; ++b) {
+    const int32_t cp = colpos[b];
+    if (cp < 0) continue;
+    const int32_t q = col[b];
+    for (int j = 0; j < m[q]; ++j) colmap[cmbase[p] + cp + j] = (int32_t)(off[q] + j);
+  }
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, ceil_div(n, t)); }
+
+int build_layout(swm_ctx* ctx, Layout& lay, int32_t* K, int32_t* colpos, int64_t* ent, const int32_t* m) {
+  const int64_t nw = ctx->nw;
+  lay.K = K;
+  lay.colpos = colpos;
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.rowbase, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.cmbase, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(exclusive_scan_i64(ctx, ent, lay.rowbase, nw, &lay.nval));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, K, lay.cmbase, nw, &lay.ncm));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.colmap, sizeof(int32_t) * std::max<int64_t>(1, lay.ncm)));
+  k_colmap<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, colpos, lay.cmbase,
+                                                     lay.colmap);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+}  // namespace
+
+int build_pattern(swm_ctx* ctx) {
+  const int64_t nw = ctx->nw;
+  cudaStream_t st = ctx->stream;
+  std::vector<Buf> tmp;
+  auto& B = ctx->build_bufs;
+
+  // --- bounding box of the centres
+  const int nbb = (int)std::min<int64_t>(1024, nblk(nw, 256));
+  double *part = nullptr, *bb = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * 6 * nbb));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&bb, sizeof(double) * 6));
+  k_bbox_partial<<<nbb, 256, 0, st>>>(ctx->u_c, nw, part);
+  SWM_LAUNCHED();
+  k_bbox_final<<<1, 32, 0, st>>>(part, nbb, bb);
+  SWM_LAUNCHED();
+  double hb[6];
+  SWM_CK(cudaMemcpyAsync(hb, bb, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  SWM_CK(cudaStreamSynchronize(st));
+
+  // --- grid (cell side slightly above r_c so a pair at exactly r_c is never two cells apart)
+  Grid g;
+  g.x0 = hb[0];
+  g.y0 = hb[1];
+  g.z0 = hb[2];
+  const double ext = std::max({hb[3] - hb[0], hb[4] - hb[1], hb[5] - hb[2], 0.0});
+  if (ctx->dense) {
+    g.h = ext * 2.0 + 1.0;
+  } else {
+    g.h = ctx->rc * (1.0 + 1e-9) + 1e-300;
+  }
+  auto dims = [&](double h, int64_t& nx, int64_t& ny, int64_t& nz) {
+    nx = (int64_t)std::floor((hb[3] - hb[0]) / h) + 1;
+    ny = (int64_t)std::floor((hb[4] - hb[1]) / h) + 1;
+    nz = (int64_t)std::floor((hb[5] - hb[2]) / h) + 1;
+  };
+  int64_t nx, ny, nz;
+  dims(g.h, nx, ny, nz);
+  while ((double)nx * (double)ny * (double)nz > (double)kMaxCells) {
+    g.h *= 1.25 * std::cbrt((double)nx * ny * nz / (double)kMaxCells);
+    dims(g.h, nx, ny, nz);
+  }
+  g.nx = (int)nx;
+  g.ny = (int)ny;
+  g.nz = (int)nz;
+  const int64_t ncell = nx * ny * nz;
+
+  // --- bin and renumber by (cell, caller index)
+  int32_t *cid = nullptr, *cnt = nullptr, *fill = nullptr, *tmpidx = nullptr, *cid_s = nullptr;
+  int64_t* cstart = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&cid, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&cnt, sizeof(int32_t) * ncell));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&fill, sizeof(int32_t) * ncell));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&tmpidx, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&cid_s, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&cstart, sizeof(int64_t) * (ncell + 1)));
+  SWM_CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ncell, st));
+  SWM_CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * ncell, st));
+  k_cell_ids<<<nblk(nw, 256), 256, 0, st>>>(ctx->u_c, nw, g, cid, cnt);
+  SWM_LAUNCHED();
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, cnt, cstart, ncell, nullptr));
+  k_scatter_unordered<<<nblk(nw, 256), 256, 0, st>>>(cid, nw, cstart, fill, tmpidx);
+  SWM_LAUNCHED();
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->perm, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->iperm, sizeof(int32_t) * nw));
+  k_rank_in_cell<<<nblk(nw, 256), 256, 0, st>>>(cid, nw, cstart, tmpidx, ctx->perm, ctx->iperm, cid_s);
+  SWM_LAUNCHED();
+
+  // --- geometry in internal order, numbering of unknowns (a0)
+  double** geo[8] = {&ctx->cx, &ctx->cy, &ctx->cz, &ctx->tx, &ctx->ty, &ctx->tz, &ctx->L, &ctx->a};
+  for (auto pp : geo) SWM_TRY(dalloc(ctx, B, (void**)pp, sizeof(double) * nw));
+  int32_t *m = nullptr, *um = nullptr;
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->ns, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, B, (void**)&m, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&um, sizeof(int32_t) * nw));
+  k_gather_geometry<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->perm, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a,
+                                                   ctx->u_ns, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty,
+                                                   ctx->tz, ctx->L, ctx->a, ctx->ns, m);
+  SWM_LAUNCHED();
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->off, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, m, ctx->off, nw, &ctx->N));
+  k_user_m<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->u_ns, um);
+  SWM_LAUNCHED();
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->uoff_user, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, um, ctx->uoff_user, nw, nullptr));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->uoff, sizeof(int64_t) * nw));
+  k_uoff_by_internal<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->perm, ctx->uoff_user, ctx->uoff);
+  SWM_LAUNCHED();
+
+  // --- S-NFC pairs (a1): count, scan, write
+  int32_t* rcnt = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&rcnt, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->row_ptr, sizeof(int64_t) * (nw + 1)));
+  const double rc2 = ctx->dense ? 0.0 : ctx->rc * ctx->rc;
+  k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
+                                              ctx->dense ? 1 : 0, 0, rcnt, nullptr, nullptr);
+  SWM_LAUNCHED();
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, rcnt, ctx->row_ptr, nw, &ctx->nb));
+  if (ctx->nb > INT32_MAX / 2) return ctx->fail(SWM_EINVAL, "too many kept blocks for 32-bit positions");
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->col, sizeof(int32_t) * ctx->nb));
+  k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
+                                              ctx->dense ? 1 : 0, 1, nullptr, ctx->row_ptr, ctx->col);
+  SWM_LAUNCHED();
+
+  // --- per-row metadata, transpose map, upper-triangle block list, layouts
+  int64_t *ucnt = nullptr, *ubase = nullptr, *ent_f = nullptr, *ent_o = nullptr;
+  int32_t *Kf = nullptr, *Ko = nullptr, *cpf = nullptr, *cpo = nullptr;
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->diag_b, sizeof(int64_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&ucnt, sizeof(int64_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&ubase, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&ent_f, sizeof(int64_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&ent_o, sizeof(int64_t) * nw));
+  SWM_TRY(dalloc(ctx, B, (void**)&Kf, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, B, (void**)&Ko, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, B, (void**)&cpf, sizeof(int32_t) * ctx->nb));
+  SWM_TRY(dalloc(ctx, B, (void**)&cpo, sizeof(int32_t) * ctx->nb));
+  k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, ucnt, cpf, Kf, cpo, Ko,
+                                            ent_f, ent_o);
+  SWM_LAUNCHED();
+  SWM_TRY(exclusive_scan_i64(ctx, ucnt, ubase, nw, &ctx->nup));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->bt, sizeof(int64_t) * ctx->nb));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->ublk, sizeof(int64_t) * std::max<int64_t>(1, ctx->nup)));
+  k_transpose_and_upper<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, ctx->diag_b, ubase, ctx->bt,
+                                                       ctx->ublk);
+  SWM_LAUNCHED();
+  SWM_TRY(build_layout(ctx, ctx->full, Kf, cpf, ent_f, m));
+  SWM_TRY(build_layout(ctx, ctx->offd, Ko, cpo, ent_o, m));
+
+  ctx->m = m;
+  SWM_CK(cudaStreamSynchronize(st));
+  dfree_group(ctx, tmp);
+  return SWM_OK;
+}
+
+}  // namespace swm

@@ -1,0 +1,152 @@
+// Block-diagonal (block-Jacobi) preconditioner named with the solver after Eq. (neardef):
+// M = blockdiag(Z_pp).  GMRES runs on the right-preconditioned operator Z M^-1 = I + E, where
+// E_pq = Z_pq Z_qq^-1 for the kept off-diagonal blocks; E is stored (layout `offd`) so that each
+// Krylov step is one block-sparse product plus the identity, and x = M^-1 y at the end.
+#include <algorithm>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace swm {
+
+namespace {
+
+__global__ void k_msq(int64_t nw, const int32_t* __restrict__ m, int64_t* __restrict__ out) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < nw) out[p] = (int64_t)m[p] * m[p];
+}
+
+// Gauss-Jordan inversion with partial pivoting of Z_pp (float64), one warp per wire.
+template <typename TV>
+__global__ void __launch_bounds__(128) k_invert_self(int64_t nw, const int32_t* __restrict__ m,
+                                                    const int64_t* __restrict__ diag_b, Layout lay,
+                                                    const cplx<TV>* __restrict__ Z, const int64_t* __restrict__ moff,
+                                                    cplx<TV>* __restrict__ Minv, int* __restrict__ singular) {
+  __shared__ c128 A[4][kMaxM][2 * kMaxM];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * 4 + wl;
+  if (p >= nw) return;
+  const int n = m[p];
+  const int K = lay.K[p];
+  const int64_t base = lay.rowbase[p] + lay.colpos[diag_b[p]];
+  c128(*a)[2 * kMaxM] = A[wl];
+  for (int e = lane; e < n * 2 * n; e += 32) {
+    const int i = e / (2 * n), j = e % (2 * n);
+    a[i][j] = j < n ? ccast<double>(Z[base + (int64_t)i * K + j]) : mkc(j - n == i ? 1.0 : 0.0, 0.0);
+  }
+  __syncwarp();
+  for (int c = 0; c < n; ++c) {
+    // pivot: largest |a[r][c]|, r >= c (ties: smallest r)
+    double best = -1.0;
+    int br = c;
+    for (int r = c; r < n; ++r) {
+      const double v = a[r][c].re * a[r][c].re + a[r][c].im * a[r][c].im;
+      if (v > best) {
+        best = v;
+        br = r;
+      }
+    }
+    if (best == 0.0) {
+      if (lane == 0) atomicExch(singular, 1);
+      return;
+    }
+    if (br != c) {
+      for (int j = lane; j < 2 * n; j += 32) {
+        const c128 t = a[c][j];
+        a[c][j] = a[br][j];
+        a[br][j] = t;
+      }
+      __syncwarp();
+    }
+    const c128 piv = a[c][c];
+    const double den = piv.re * piv.re + piv.im * piv.im;
+    const c128 inv = mkc(piv.re / den, -piv.im / den);
+    __syncwarp();
+    for (int j = lane; j < 2 * n; j += 32) a[c][j] = a[c][j] * inv;
+    __syncwarp();
+    for (int e = lane; e < n * 2 * n; e += 32) {
+      const int r = e / (2 * n), j = e % (2 * n);
+      if (r != c && j != c) a[r][j] = a[r][j] - a[r][c] * a[c][j];
+    }
+    __syncwarp();
+    for (int r = lane; r < n; r += 32)
+      if (r != c) a[r][c] = mkc(0.0, 0.0);
+    __syncwarp();
+  }
+  const int64_t mo = moff[p];
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e % n;
+    Minv[mo + e] = ccast<TV>(a[i][n + j]);
+  }
+}
+
+// E_pq = Z_pq Minv_q for every kept block with q != p; one warp per block.
+template <typename TV>
+__global__ void k_form_E(int64_t nb, const int32_t* __restrict__ col, const int64_t* __restrict__ bt,
+                         const int32_t* __restrict__ m, Layout full, Layout offd, const cplx<TV>* __restrict__ Z,
+                         const int64_t* __restrict__ moff, const cplx<TV>* __restrict__ Minv, cplx<TV>* __restrict__ E) {
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= nb) return;
+  const int q = col[b];
+  const int p = col[bt[b]];
+  if (p == q) return;
+  const int mp = m[p], mq = m[q];
+  const int Kf = full.K[p], Ko = offd.K[p];
+  const int64_t zb = full.rowbase[p] + full.colpos[b];
+  const int64_t eb = offd.rowbase[p] + offd.colpos[b];
+  const cplx<TV>* Mi = Minv + moff[q];
+  for (int e = lane; e < mp * mq; e += 32) {
+    const int i = e / mq, j = e % mq;
+    cplx<TV> acc = mkc<TV>(0, 0);
+    for (int l = 0; l < mq; ++l) cfma(acc, Z[zb + (int64_t)i * Kf + l], Mi[l * mq + j]);
+    E[eb + (int64_t)i * Ko + j] = acc;
+  }
+}
+
+}  // namespace
+
+int build_precond(swm_ctx* ctx) {
+  const int64_t nw = ctx->nw;
+  const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
+  std::vector<Buf> tmp;
+  int64_t* msq = nullptr;
+  int* sing = nullptr;
+  int64_t nminv = 0;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&msq, sizeof(int64_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&sing, sizeof(int)));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->minv_off, sizeof(int64_t) * (nw + 1)));
+  k_msq<<<(unsigned)ceil_div(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->m, msq);
+  SWM_LAUNCHED();
+  SWM_TRY(exclusive_scan_i64(ctx, msq, ctx->minv_off, nw, &nminv));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Minv, esz * std::max<int64_t>(1, nminv)));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Zp, esz * std::max<int64_t>(1, ctx->offd.nval)));
+  SWM_CK(cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream));
+  const unsigned g1 = (unsigned)ceil_div(nw, 4);
+  const unsigned g2 = (unsigned)std::max<int64_t>(1, ceil_div(ctx->nb * 32, 256));
+  if (ctx->prec == SWM_C128) {
+    k_invert_self<double><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
+                                                       ctx->minv_off, (c128*)ctx->Minv, sing);
+    SWM_LAUNCHED();
+    k_form_E<double><<<g2, 256, 0, ctx->stream>>>(ctx->nb, ctx->col, ctx->bt, ctx->m, ctx->full, ctx->offd,
+                                                  (const c128*)ctx->Z, ctx->minv_off, (const c128*)ctx->Minv,
+                                                  (c128*)ctx->Zp);
+    SWM_LAUNCHED();
+  } else {
+    k_invert_self<float><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c64*)ctx->Z,
+                                                      ctx->minv_off, (c64*)ctx->Minv, sing);
+    SWM_LAUNCHED();
+    k_form_E<float><<<g2, 256, 0, ctx->stream>>>(ctx->nb, ctx->col, ctx->bt, ctx->m, ctx->full, ctx->offd,
+                                                 (const c64*)ctx->Z, ctx->minv_off, (const c64*)ctx->Minv,
+                                                 (c64*)ctx->Zp);
+    SWM_LAUNCHED();
+  }
+  int hs = 0;
+  SWM_CK(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, tmp);
+  if (hs) return ctx->fail(SWM_EINVAL, "a self block is singular (degenerate wire geometry?)");
+  return SWM_OK;
+}
+
+}  // namespace swm

@@ -1,0 +1,299 @@
+// Right-hand sides (Eq. (4)) and far field / RCS (Sec. III-A, III-B), both in closed form.
+//
+// For a rooftop of half-width D centred at s_l on wire p (centre c, direction t):
+//   int Lambda(s) exp(j beta s) ds = D exp(j beta s_l) sinc^2(beta D / 2),  sinc(z) = sin z / z.
+// RHS:  b_{p,l} = (e.t) exp(-j k khat.c) D exp(-j k (khat.t) s_l) sinc^2(k (khat.t) D / 2)
+// far:  F(r) = sum_p t_p D_p exp(j k r.c_p) sinc^2(k (r.t_p) D_p / 2) sum_l j_{p,l} exp(j k (r.t_p) s_l)
+//       sigma_s = |e_s . F|^2 / (4 pi), e_s = theta_hat or phi_hat at r.
+// The exp(j beta s_l) factors along a wire are a geometric progression in l.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace swm {
+
+namespace {
+
+// x mod 2 pi in float64 (two-constant Cody-Waite split), result in [-pi, pi].
+__device__ __forceinline__ double reduce_2pi(double x) {
+  const double inv2pi = 0.15915494309189535;
+  const double c1 = 6.28318530717958623;      // 2 pi rounded to double
+  const double c2 = 2.4492935982947064e-16;   // 2 pi - c1
+  const double n = rint(x * inv2pi);
+  return fma(-n, c2, fma(-n, c1, x));
+}
+
+__device__ __forceinline__ double sinc_d(double z) { return fabs(z) < 1e-8 ? 1.0 - z * z / 6.0 : sin(z) / z; }
+__device__ __forceinline__ float sinc_f(float z) { return fabsf(z) < 1e-4f ? 1.0f - z * z / 6.0f : __sinf(z) / z; }
+
+// One thread per (wire, incidence).  frames: per incidence khat[3], e[3].
+template <typename TV>
+__global__ void k_rhs(int64_t nw, int n_inc, const double* __restrict__ cx, const double* __restrict__ cy,
+                      const double* __restrict__ cz, const double* __restrict__ tx, const double* __restrict__ ty,
+                      const double* __restrict__ tz, const double* __restrict__ Ls, const int32_t* __restrict__ ns,
+                      const int64_t* __restrict__ off, int64_t N, double k, const double* __restrict__ frames,
+                      cplx<TV>* __restrict__ B) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nw * n_inc) return;
+  const int64_t p = e % nw;
+  const int r = (int)(e / nw);
+  const double* f = frames + 6 * r;
+  const double kt = f[0] * tx[p] + f[1] * ty[p] + f[2] * tz[p];
+  const double et = f[3] * tx[p] + f[4] * ty[p] + f[5] * tz[p];
+  const double ph0 = -k * (f[0] * cx[p] + f[1] * cy[p] + f[2] * cz[p]);
+  const int n = ns[p];
+  const double D = Ls[p] / n;
+  const double beta = -k * kt;  // exp(j beta s)
+  const double s1 = -0.5 * Ls[p] + D;
+  cplx<TV>* out = B + (int64_t)r * N + off[p];
+  if constexpr (sizeof(TV) == 8) {
+    const double sc = sinc_d(0.5 * beta * D);
+    const double amp = et * D * sc * sc;
+    double sa, ca, sb, cb;
+    sincos(ph0 + beta * s1, &sa, &ca);
+    sincos(beta * D, &sb, &cb);
+    c128 z = mkc(amp * ca, amp * sa);
+    const c128 rat = mkc(cb, sb);
+    for (int l = 0; l < n - 1; ++l) {
+      out[l] = z;
+      z = z * rat;
+    }
+  } else {
+    const float sc = sinc_f((float)(0.5 * beta * D));
+    const float amp = (float)(et * D) * sc * sc;
+    float sa, ca, sb, cb;
+    __sincosf((float)reduce_2pi(ph0 + beta * s1), &sa, &ca);
+    __sincosf((float)(beta * D), &sb, &cb);
+    c64 z = mkc(amp * ca, amp * sa);
+    const c64 rat = mkc(cb, sb);
+    for (int l = 0; l < n - 1; ++l) {
+      out[l] = z;
+      z = z * rat;
+    }
+  }
+}
+
+// Geometry access: structure-of-arrays (internal) or caller arrays (centres/dirs as nw x 3).
+struct Geo {
+  const double *cx, *cy, *cz, *tx, *ty, *tz;  // SoA when soa
+  const double* c3;                           // AoS centres
+  const double* t3;                           // AoS dirs
+  const double* L;
+  const int32_t* ns;
+  const int64_t* off;
+  int soa;
+  __device__ __forceinline__ void get(int64_t p, double c[3], double t[3]) const {
+    if (soa) {
+      c[0] = cx[p];
+      c[1] = cy[p];
+      c[2] = cz[p];
+      t[0] = tx[p];
+      t[1] = ty[p];
+      t[2] = tz[p];
+    } else {
+      c[0] = c3[3 * p];
+      c[1] = c3[3 * p + 1];
+      c[2] = c3[3 * p + 2];
+      t[0] = t3[3 * p];
+      t[1] = t3[3 * p + 1];
+      t[2] = t3[3 * p + 2];
+    }
+  }
+};
+
+constexpr int kFFThreads = 128;
+
+__device__ __forceinline__ void obs_frame(const double* obs, int stride, int o, double r[3], double th[3], double ph[3]) {
+  double st, ct, sp, cp;
+  sincos(obs[(int64_t)o * stride], &st, &ct);
+  sincos(obs[(int64_t)o * stride + 1], &sp, &cp);
+  r[0] = st * cp;
+  r[1] = st * sp;
+  r[2] = ct;
+  th[0] = ct * cp;
+  th[1] = ct * sp;
+  th[2] = -st;
+  ph[0] = -sp;
+  ph[1] = cp;
+  ph[2] = 0.0;
+}
+
+// grid (ceil(npairs / kFFThreads), nchunks).  Pair e: bistatic (r = e / n_obs, o = e % n_obs),
+// monostatic (r = o = e).  partial[chunk][e][3] complex128.
+template <typename TC, bool F64>
+__global__ void __launch_bounds__(kFFThreads) k_far_partial(Geo geo, int64_t nw, int64_t N, double k, int n_rhs,
+                                                            const cplx<TC>* __restrict__ cur, int n_obs,
+                                                            const double* __restrict__ obs, int obs_stride, int mono,
+                                                            int64_t chunk, c128* __restrict__ partial) {
+  const int64_t npairs = mono ? n_rhs : (int64_t)n_rhs * n_obs;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p0 = blockIdx.y * chunk, p1 = min(nw, p0 + chunk);
+  if (e >= npairs) return;
+  const int r = mono ? (int)e : (int)(e / n_obs);
+  const int o = mono ? (int)e : (int)(e % n_obs);
+  double rh[3], th[3], ph[3];
+  obs_frame(obs, obs_stride, o, rh, th, ph);
+  const cplx<TC>* J = cur + (int64_t)r * N;
+  double F[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t p = p0; p < p1; ++p) {
+    double c[3], t[3];
+    geo.get(p, c, t);
+    const int n = geo.ns[p];
+    const double Lp = geo.L[p], D = Lp / n;
+    const double beta = k * (rh[0] * t[0] + rh[1] * t[1] + rh[2] * t[2]);
+    const double phc = k * (rh[0] * c[0] + rh[1] * c[1] + rh[2] * c[2]);
+    const double s1 = -0.5 * Lp + D;
+    const cplx<TC>* Jp = J + geo.off[p];
+    double Sr, Si;
+    if constexpr (F64) {
+      double sa, ca, sb, cb;
+      sincos(phc + beta * s1, &sa, &ca);
+      sincos(beta * D, &sb, &cb);
+      const double sc = sinc_d(0.5 * beta * D);
+      c128 z = mkc(ca, sa), acc = mkc(0.0, 0.0);
+      const c128 rat = mkc(cb, sb);
+      for (int l = 0; l < n - 1; ++l) {
+        cfma(acc, ccast<double>(Jp[l]), z);
+        z = z * rat;
+      }
+      const double amp = D * sc * sc;
+      Sr = amp * acc.re;
+      Si = amp * acc.im;
+    } else {
+      float sa, ca, sb, cb;
+      __sincosf((float)reduce_2pi(phc + beta * s1), &sa, &ca);
+      __sincosf((float)(beta * D), &sb, &cb);
+      const float sc = sinc_f((float)(0.5 * beta * D));
+      c64 z = mkc(ca, sa), acc = mkc(0.f, 0.f);
+      const c64 rat = mkc(cb, sb);
+      for (int l = 0; l < n - 1; ++l) {
+        cfma(acc, ccast<float>(Jp[l]), z);
+        z = z * rat;
+      }
+      const float amp = (float)D * sc * sc;
+      Sr = (double)(amp * acc.re);
+      Si = (double)(amp * acc.im);
+    }
+    F[0] += t[0] * Sr;
+    F[1] += t[0] * Si;
+    F[2] += t[1] * Sr;
+    F[3] += t[1] * Si;
+    F[4] += t[2] * Sr;
+    F[5] += t[2] * Si;
+  }
+  c128* out = partial + ((int64_t)blockIdx.y * npairs + e) * 3;
+  out[0] = mkc(F[0], F[1]);
+  out[1] = mkc(F[2], F[3]);
+  out[2] = mkc(F[4], F[5]);
+}
+
+__global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict__ partial, int n_obs,
+                             const double* __restrict__ obs, int obs_stride, int mono, double* __restrict__ sigma) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= npairs) return;
+  double F[6] = {0, 0, 0, 0, 0, 0};
+  for (int c = 0; c < nchunks; ++c) {
+    const c128* in = partial + ((int64_t)c * npairs + e) * 3;
+    for (int d = 0; d < 3; ++d) {
+      F[2 * d] += in[d].re;
+      F[2 * d + 1] += in[d].im;
+    }
+  }
+  const int o = mono ? (int)e : (int)(e % n_obs);
+  double rh[3], th[3], ph[3];
+  obs_frame(obs, obs_stride, o, rh, th, ph);
+  const double tr = th[0] * F[0] + th[1] * F[2] + th[2] * F[4], ti = th[0] * F[1] + th[1] * F[3] + th[2] * F[5];
+  const double pr = ph[0] * F[0] + ph[1] * F[2] + ph[2] * F[4], pi = ph[0] * F[1] + ph[1] * F[3] + ph[2] * F[5];
+  sigma[2 * e] = (tr * tr + ti * ti) / kFourPi;
+  sigma[2 * e + 1] = (pr * pr + pi * pi) / kFourPi;
+}
+
+}  // namespace
+
+int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
+  const int64_t tot = ctx->nw * (int64_t)n_inc;
+  const unsigned grid = (unsigned)ceil_div(tot, 256);
+  if (ctx->prec == SWM_C128)
+    k_rhs<double><<<grid, 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz,
+                                                 ctx->L, ctx->ns, ctx->off, ctx->N, ctx->k, frames_dev,
+                                                 (c128*)ctx->Bv);
+  else
+    k_rhs<float><<<grid, 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz,
+                                                ctx->L, ctx->ns, ctx->off, ctx->N, ctx->k, frames_dev, (c64*)ctx->Bv);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+// Launch shape shared by the scratch sizing and the launch itself.
+static void ff_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& chunk) {
+  const int64_t gx = ceil_div(npairs, kFFThreads);
+  nchunks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nw, 32), ceil_div(2 * 152, gx)));
+  nchunks = std::min<int64_t>(nchunks, 65535);
+  chunk = ceil_div(nw, nchunks);
+  nchunks = ceil_div(nw, chunk);
+}
+
+size_t far_field_scratch_bytes(int64_t nw, int64_t npairs) {
+  int64_t nchunks, chunk;
+  ff_shape(nw, npairs, nchunks, chunk);
+  return (size_t)nchunks * npairs * 3 * sizeof(c128);
+}
+
+// Far field + RCS.  Scratch must hold at least 3 * npairs complex128; with less than
+// far_field_scratch_bytes() the wire range is cut into fewer chunks.
+int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64, const void* cur, int64_t nw,
+                     int64_t N, const double* c3, const double* t3, const double* cx, const double* cy,
+                     const double* cz, const double* tx, const double* ty, const double* tz, const double* Ls,
+                     const int32_t* ns, const int64_t* off, bool soa, double k, int n_rhs, int n_obs,
+                     const double* obs, int obs_stride, bool mono, double* sigma, void* scratch, size_t scratch_bytes,
+                     std::string* err) {
+  const int64_t npairs = mono ? n_rhs : (int64_t)n_rhs * n_obs;
+  int64_t nchunks, chunk;
+  ff_shape(nw, npairs, nchunks, chunk);
+  const int64_t fit = (int64_t)(scratch_bytes / (3 * sizeof(c128) * (size_t)npairs));
+  if (fit < 1) {
+    *err = "far field: scratch too small for " + std::to_string(npairs) + " (incidence, observation) pairs";
+    return SWM_EINVAL;
+  }
+  if (nchunks > fit) {
+    nchunks = fit;
+    chunk = ceil_div(nw, nchunks);
+    nchunks = ceil_div(nw, chunk);
+  }
+  Geo g{cx, cy, cz, tx, ty, tz, c3, t3, Ls, ns, off, soa ? 1 : 0};
+  dim3 grid((unsigned)ceil_div(npairs, kFFThreads), (unsigned)nchunks);
+  c128* part = (c128*)scratch;
+  if (cur_c64) {
+    if (f64)
+      k_far_partial<float, true><<<grid, kFFThreads, 0, st>>>(g, nw, N, k, n_rhs, (const c64*)cur, n_obs, obs,
+                                                             obs_stride, mono, chunk, part);
+    else
+      k_far_partial<float, false><<<grid, kFFThreads, 0, st>>>(g, nw, N, k, n_rhs, (const c64*)cur, n_obs, obs,
+                                                              obs_stride, mono, chunk, part);
+  } else {
+    if (f64)
+      k_far_partial<double, true><<<grid, kFFThreads, 0, st>>>(g, nw, N, k, n_rhs, (const c128*)cur, n_obs, obs,
+                                                              obs_stride, mono, chunk, part);
+    else
+      k_far_partial<double, false><<<grid, kFFThreads, 0, st>>>(g, nw, N, k, n_rhs, (const c128*)cur, n_obs, obs,
+                                                               obs_stride, mono, chunk, part);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = std::string("far field launch: ") + cudaGetErrorString(e);
+    return SWM_ECUDA;
+  }
+  k_far_reduce<<<(unsigned)ceil_div(npairs, 128), 128, 0, st>>>(npairs, (int)nchunks, part, n_obs, obs, obs_stride,
+                                                                mono, sigma);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = std::string("far field reduce launch: ") + cudaGetErrorString(e);
+    return SWM_ECUDA;
+  }
+  if (launches) *launches += 2;
+  return SWM_OK;
+}
+
+}  // namespace swm

@@ -1,0 +1,128 @@
+// Exclusive prefix sums on the device (tile sums, one-CTA scan of the tile sums, tile rescan).
+#include "common.cuh"
+#include "ctx.h"
+
+namespace swm {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kTile = kScanThreads * kScanItems;
+
+// Inclusive block scan of one value per thread; returns the block total in *total.
+__device__ int64_t block_incl_scan(int64_t v, int64_t* total) {
+  __shared__ int64_t warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) warp_tot[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int64_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t n = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += n;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  if (w > 0) v += warp_tot[w - 1];
+  *total = warp_tot[kScanThreads / 32 - 1];
+  __syncthreads();
+  return v;
+}
+
+template <typename TIn>
+__global__ void k_tile_sums(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  int64_t s = 0;
+  for (int t = threadIdx.x; t < kTile; t += kScanThreads) {
+    int64_t i = base + t;
+    if (i < n) s += (int64_t)in[i];
+  }
+  int64_t tot;
+  block_incl_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// One CTA: exclusive scan of nt tile sums in place; grand total to sums[nt].
+__global__ void k_scan_sums(int64_t* sums, int64_t nt) {
+  const int64_t per = ceil_div(nt, kScanThreads);
+  const int64_t b = threadIdx.x * per, e = min(nt, b + per);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += sums[i];
+  int64_t tot;
+  int64_t incl = block_incl_scan(s, &tot);
+  int64_t run = incl - s;
+  for (int64_t i = b; i < e; ++i) {
+    int64_t v = sums[i];
+    sums[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) sums[nt] = tot;
+}
+
+template <typename TIn>
+__global__ void k_tile_rescan(const TIn* __restrict__ in, int64_t n, const int64_t* __restrict__ sums,
+                              int64_t* __restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    int64_t i = base + t;
+    v[t] = i < n ? (int64_t)in[i] : 0;
+    s += v[t];
+  }
+  int64_t tot;
+  int64_t run = block_incl_scan(s, &tot) - s + sums[blockIdx.x];
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    int64_t i = base + t;
+    if (i < n) out[i] = run;
+    run += v[t];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = sums[gridDim.x];
+}
+
+template <typename TIn>
+int scan_impl(swm_ctx* ctx, const TIn* in, int64_t* out, int64_t n, int64_t* total_host) {
+  // out has n + 1 entries; out[n] = total.
+  if (n == 0) {
+    SWM_CK(cudaMemsetAsync(out, 0, sizeof(int64_t), ctx->stream));
+    if (total_host) *total_host = 0;
+    return SWM_OK;
+  }
+  const int64_t nt = ceil_div(n, kTile);
+  std::vector<Buf> tmp;
+  int64_t* sums = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&sums, sizeof(int64_t) * (nt + 1)));
+  k_tile_sums<TIn><<<(unsigned)nt, kScanThreads, 0, ctx->stream>>>(in, n, sums);
+  SWM_LAUNCHED();
+  k_scan_sums<<<1, kScanThreads, 0, ctx->stream>>>(sums, nt);
+  SWM_LAUNCHED();
+  k_tile_rescan<TIn><<<(unsigned)nt, kScanThreads, 0, ctx->stream>>>(in, n, sums, out);
+  SWM_LAUNCHED();
+  if (total_host) {
+    SWM_CK(cudaMemcpyAsync(total_host, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SWM_CK(cudaStreamSynchronize(ctx->stream));
+  }
+  dfree_group(ctx, tmp);
+  return SWM_OK;
+}
+
+}  // namespace
+
+int exclusive_scan_i64(swm_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host) {
+  return scan_impl<int64_t>(ctx, in, out, n, total_host);
+}
+int exclusive_scan_i32_to_i64(swm_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host) {
+  return scan_impl<int32_t>(ctx, in, out, n, total_host);
+}
+
+}  // namespace swm

@@ -1,0 +1,274 @@
+"""Thin Python binding of the swm C ABI (include/swm.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Inputs may be NumPy arrays (host
+memory) or CUDA torch tensors (device memory); outputs are written into caller-provided arrays or
+tensors, or returned as new NumPy arrays by the ``swm_get_*`` helpers.  Negative status codes
+raise :class:`SwmError`; SWM_ENOTCONV is returned as a warning code.  There is no fallback: if
+the CUDA library cannot be built or loaded, every call fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SWM_OK, SWM_ENOTCONV = 0, 1
+SWM_EINVAL, SWM_ENOMEM, SWM_ECUDA, SWM_ESTATE = -1, -2, -3, -4
+SWM_HOST, SWM_DEVICE = 0, 1
+SWM_C128, SWM_C64 = 0, 1
+SWM_MAX_SEG = 16
+SWM_MAX_RESTART = 128
+
+_lib = None
+
+
+class SwmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"swm error {code}: {msg}")
+        self.code = code
+
+
+class swm_stats(C.Structure):
+    _fields_ = [("nw", C.c_int64), ("n", C.c_int64), ("nb", C.c_int64), ("nnz", C.c_int64),
+                ("n_rhs", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("rel_residual", C.c_double), ("ms_neighbour", C.c_double), ("ms_fill", C.c_double),
+                ("ms_precond", C.c_double), ("ms_rhs", C.c_double), ("ms_solve", C.c_double),
+                ("ms_rcs", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_P = C.c_void_p
+_SIGS = {
+    "swm_version": (C.c_char_p, []),
+    "swm_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "swm_destroy": (None, [_P]),
+    "swm_last_error": (C.c_char_p, [_P]),
+    "swm_set_allocator": (C.c_int, [_P, ALLOC_FN, FREE_FN, _P]),
+    "swm_set_cloud": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_int]),
+    "swm_build": (C.c_int, [_P, C.c_double, C.c_double, C.c_int]),
+    "swm_solve": (C.c_int, [_P, C.c_int, _P, C.c_double, C.c_int, C.c_int, _P, C.c_int]),
+    "swm_rcs_bistatic": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
+    "swm_rcs_monostatic": (C.c_int, [_P, _P, C.c_int]),
+    "swm_get_stats": (C.c_int, [_P, C.POINTER(swm_stats)]),
+    "swm_get_pattern": (C.c_int, [_P, _P]),
+    "swm_get_block": (C.c_int, [_P, C.c_int64, C.c_int64, _P]),
+    "swm_get_rhs": (C.c_int, [_P, _P]),
+    "swm_far_field": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P, C.c_int, _P, _P]),
+    "swm_stateless_error": (C.c_char_p, []),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def load(build: bool = True):
+    """Load libswm.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: the CUDA library was not built")
+        lib = C.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+# ------------------------------------------------------------------------------ marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype, shape=None, name="array"):
+    """(pointer, mem_kind, keepalive) of a contiguous host NumPy array or CUDA torch tensor."""
+    if _is_torch(x):
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64,
+               np.complex128: torch.complex128}[dtype]
+        if x.dtype != tdt or not x.is_contiguous() or not x.is_cuda:
+            raise TypeError(f"{name}: need a contiguous CUDA tensor of {tdt}")
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError(f"{name}: shape {tuple(x.shape)} != {tuple(shape)}")
+        return C.c_void_p(x.data_ptr()), SWM_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if shape is not None and a.shape != tuple(shape):
+        raise ValueError(f"{name}: shape {a.shape} != {tuple(shape)}")
+    return a.ctypes.data_as(C.c_void_p), SWM_HOST, a
+
+
+def _out_ptr(x, dtype, shape, name):
+    if _is_torch(x):
+        return _ptr(x, dtype, shape, name)
+    if not (isinstance(x, np.ndarray) and x.dtype == dtype and x.flags.c_contiguous and x.shape == tuple(shape)):
+        raise TypeError(f"{name}: need a C-contiguous {np.dtype(dtype).name} array of shape {tuple(shape)}")
+    return x.ctypes.data_as(C.c_void_p), SWM_HOST, x
+
+
+def _check(ctx, rc):
+    if rc < 0:
+        raise SwmError(rc, swm_last_error(ctx))
+    return rc
+
+
+def _torch_stream_handle():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ------------------------------------------------------------------------------ context API
+class Ctx:
+    """Opaque context handle plus the Python objects that must outlive it."""
+
+    def __init__(self, handle, device, stream):
+        self.handle = handle
+        self.device = device
+        self.stream = stream
+        self._keep = []
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def swm_version() -> str:
+    return load().swm_version().decode()
+
+
+def swm_create(device: int = 0, stream=None, torch_allocator: bool = True) -> Ctx:
+    """Create a context on ``device`` issuing work on ``stream`` (a cudaStream_t handle; default:
+    torch's current stream).  With ``torch_allocator`` the device memory comes from torch's
+    caching allocator."""
+    lib = load()
+    if stream is None:
+        stream = _torch_stream_handle()
+    h = C.c_void_p()
+    rc = lib.swm_create(C.byref(h), int(device), C.c_void_p(stream))
+    if rc < 0:
+        raise SwmError(rc, "swm_create failed (no CUDA device?)")
+    ctx = Ctx(h, device, stream)
+    if torch_allocator:
+        swm_set_allocator(ctx)
+    return ctx
+
+
+def swm_destroy(ctx: Ctx) -> None:
+    if ctx is not None and ctx.handle:
+        load().swm_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def swm_last_error(ctx) -> str:
+    h = ctx.handle if isinstance(ctx, Ctx) else ctx
+    return load().swm_last_error(h).decode()
+
+
+def swm_set_allocator(ctx: Ctx) -> int:
+    """Route the context's device allocations through torch's caching allocator."""
+    import torch
+
+    dev = ctx.device
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+    ctx._keep += [fa, ff]
+    return _check(ctx, load().swm_set_allocator(ctx.handle, fa, ff, None))
+
+
+def swm_set_cloud(ctx: Ctx, centres, dirs, lengths, radii, nseg) -> int:
+    nw = len(lengths)
+    pc, k1, a1 = _ptr(centres, np.float64, (nw, 3), "centres")
+    pt, k2, a2 = _ptr(dirs, np.float64, (nw, 3), "dirs")
+    pl, k3, a3 = _ptr(lengths, np.float64, (nw,), "lengths")
+    pr, k4, a4 = _ptr(radii, np.float64, (nw,), "radii")
+    pn, k5, a5 = _ptr(nseg, np.int32, (nw,), "nseg")
+    if len({k1, k2, k3, k4, k5}) != 1:
+        raise TypeError("swm_set_cloud: all inputs must be host arrays or all device tensors")
+    return _check(ctx, load().swm_set_cloud(ctx.handle, nw, pc, pt, pl, pr, pn, k1))
+
+
+def swm_build(ctx: Ctx, k: float, r_c: float, precision: int = SWM_C128) -> int:
+    return _check(ctx, load().swm_build(ctx.handle, float(k), float(r_c), int(precision)))
+
+
+def swm_solve(ctx: Ctx, inc, tol: float = 1e-6, restart: int = 50, max_iter: int = 1000, currents_out=None) -> int:
+    inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+    n_inc = inc.shape[0]
+    if currents_out is None:
+        pc, kind = None, SWM_HOST
+    else:
+        n = swm_get_stats(ctx)["n"]
+        pc, kind, _ = _out_ptr(currents_out, np.complex128, (n_inc, n), "currents_out")
+    return _check(ctx, load().swm_solve(ctx.handle, n_inc, inc.ctypes.data_as(C.c_void_p), float(tol), int(restart),
+                                        int(max_iter), pc, kind))
+
+
+def swm_rcs_bistatic(ctx: Ctx, obs, sigma_out) -> int:
+    obs = np.ascontiguousarray(np.atleast_2d(obs), dtype=np.float64)
+    n_inc = swm_get_stats(ctx)["n_rhs"]
+    ps, kind, _ = _out_ptr(sigma_out, np.float64, (n_inc, obs.shape[0], 2), "sigma_out")
+    return _check(ctx, load().swm_rcs_bistatic(ctx.handle, obs.shape[0], obs.ctypes.data_as(C.c_void_p), ps, kind))
+
+
+def swm_rcs_monostatic(ctx: Ctx, sigma_out) -> int:
+    n_inc = swm_get_stats(ctx)["n_rhs"]
+    ps, kind, _ = _out_ptr(sigma_out, np.float64, (n_inc, 2), "sigma_out")
+    return _check(ctx, load().swm_rcs_monostatic(ctx.handle, ps, kind))
+
+
+def swm_get_stats(ctx: Ctx) -> dict:
+    s = swm_stats()
+    _check(ctx, load().swm_get_stats(ctx.handle, C.byref(s)))
+    return {name: getattr(s, name) for name, _ in swm_stats._fields_}
+
+
+def swm_get_pattern(ctx: Ctx) -> np.ndarray:
+    nb = swm_get_stats(ctx)["nb"]
+    out = np.zeros((nb, 2), dtype=np.int64)
+    _check(ctx, load().swm_get_pattern(ctx.handle, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def swm_get_block(ctx: Ctx, p: int, q: int, mp: int, mq: int) -> np.ndarray:
+    out = np.zeros((mp, mq), dtype=np.complex128)
+    _check(ctx, load().swm_get_block(ctx.handle, int(p), int(q), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def swm_get_rhs(ctx: Ctx) -> np.ndarray:
+    st = swm_get_stats(ctx)
+    out = np.zeros((st["n_rhs"], st["n"]), dtype=np.complex128)
+    _check(ctx, load().swm_get_rhs(ctx.handle, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out) -> int:
+    """Stateless far-field RCS; every array a CUDA torch tensor (see include/swm.h)."""
+    nw = lengths.shape[0]
+    n_rhs, n_obs = currents.shape[0], obs.shape[0]
+    args = [_ptr(centres, np.float64, (nw, 3), "centres")[0], _ptr(dirs, np.float64, (nw, 3), "dirs")[0],
+            _ptr(lengths, np.float64, (nw,), "lengths")[0], _ptr(nseg, np.int32, (nw,), "nseg")[0],
+            _ptr(off, np.int64, (nw + 1,), "off")[0]]
+    pc = _ptr(currents, np.complex128, None, "currents")[0]
+    po = _ptr(obs, np.float64, (n_obs, 2), "obs")[0]
+    ps = _ptr(sigma_out, np.float64, (n_rhs, n_obs, 2), "sigma_out")[0]
+    if stream is None:
+        stream = _torch_stream_handle()
+    lib = load()
+    rc = lib.swm_far_field(C.c_void_p(stream), nw, *args, float(k), n_rhs, pc, n_obs, po, ps)
+    if rc < 0:
+        raise SwmError(rc, lib.swm_stateless_error().decode())
+    return rc

@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: S-NFC pattern bit-exact; FP64 blocks and right-hand sides to 1e-10 relative; FP64 currents
+to 1e-5 relative; RCS within 0.1 dB; the complex64 path (FP32 kernel evaluation) to 2e-5
+relative per block and 0.1 dB in RCS.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import K, assert_rcs_db, block_errors, run_gpu
+from synth import CONFIGS, Cloud, cloud_small, cloud_uniform_cube, observations_phi_cut
+
+pytestmark = pytest.mark.gpu
+
+C128, C64 = 0, 1
+BLOCK_TOL = {C128: 1e-10, C64: 2e-5}
+
+
+def _mixed_cloud(nw=48, side=2.5, seed=31):
+    """Tight cloud with every segment count 2..16 and near-touching wires (8-point rule)."""
+    rng = np.random.default_rng(seed)
+    c = cloud_uniform_cube(nw, side, seed=seed)
+    c.nseg = (2 + np.arange(nw) % 15).astype(np.int32)
+    c.lengths = rng.uniform(0.2, 0.7, nw)
+    c.radii = rng.uniform(5e-4, 2e-3, nw)
+    # two almost touching wires
+    c.centres[1] = c.centres[0] + 0.03 * np.cross(c.dirs[0], [0.0, 0.0, 1.0]) / max(
+        1e-9, np.linalg.norm(np.cross(c.dirs[0], [0.0, 0.0, 1.0])))
+    return c
+
+
+def _ties_cloud():
+    rng = np.random.default_rng(21)
+    nw = 150
+    c = np.round(rng.uniform(-3, 3, size=(nw, 3)) * 4) / 4
+    d = rng.standard_normal((nw, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return Cloud(c, d, np.full(nw, 0.4), np.full(nw, 1e-3), np.full(nw, 5, np.int32), "ties")
+
+
+# ------------------------------------------------------------------------------------- a1 pattern
+@pytest.mark.parametrize("case", ["small", "ties", "mixed", "single"])
+def test_pattern_bit_exact(case):
+    if case == "small":
+        cl, r_c = cloud_small(), 3.0
+    elif case == "ties":
+        cl, r_c = _ties_cloud(), 1.5
+    elif case == "mixed":
+        cl, r_c = _mixed_cloud(), 0.9
+    else:
+        cl, r_c = cloud_uniform_cube(1, 1.0, seed=1), 2.0
+    out = run_gpu(cl, K, r_c, C128, np.array([[0.0, 0.0, 0.0]]))
+    ref = O.neighbour_pairs(cl.centres, r_c)
+    assert np.array_equal(out["pattern"], ref)
+
+
+def test_dense_mode_keeps_every_pair():
+    cl = cloud_uniform_cube(30, 40.0, seed=3)
+    out = run_gpu(cl, K, 0.0, C128, np.array([[0.0, 0.0, 0.0]]))
+    assert out["stats"]["nb"] == 30 * 30
+
+
+# ------------------------------------------------------------------------------------- a2/a3 fill
+@pytest.mark.parametrize("prec", [C128, C64])
+def test_blocks_match_oracle(prec):
+    cl = _mixed_cloud()
+    out = run_gpu(cl, K, 0.9, prec, np.array([[0.3, 0.2, 0.1]]))
+    pairs = out["pattern"]
+    near = [(p, q) for p, q in pairs if p != q and O.mutual_order(cl, p, q) == O.NQ_NEAR]
+    assert len(near) > 0
+    err = block_errors(out["ctx"], cl, K, pairs)
+    assert err < BLOCK_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [C128, C64])
+def test_self_blocks_all_segment_counts(prec):
+    cl = cloud_uniform_cube(15, 60.0, seed=4)
+    cl.nseg = np.arange(2, 17, dtype=np.int32)
+    out = run_gpu(cl, K, 0.5, prec, np.array([[0.0, 0.0, 0.0]]))
+    assert len(out["pattern"]) == 15  # isolated wires
+    assert block_errors(out["ctx"], cl, K, out["pattern"]) < BLOCK_TOL[prec]
+
+
+# ------------------------------------------------------------------------------------- a4 rhs
+@pytest.mark.parametrize("prec", [C128, C64])
+def test_rhs_matches_oracle(prec):
+    cl = _mixed_cloud(seed=5)
+    rng = np.random.default_rng(0)
+    inc = np.stack([rng.uniform(0, math.pi, 7), rng.uniform(0, 2 * math.pi, 7), rng.uniform(0, math.pi, 7)], 1)
+    out = run_gpu(cl, K, 0.9, prec, inc)
+    ref = O.rhs(cl, K, inc)
+    tol = 1e-12 if prec == C128 else 2e-6
+    assert np.max(np.abs(out["rhs"] - ref)) / np.max(np.abs(ref)) < tol
+
+
+# ------------------------------------------------------------------------------------- a5-a7 solve + RCS
+def test_currents_and_rcs_fp64_vs_oracle_lu():
+    cl = cloud_uniform_cube(80, 5.0, seed=41)
+    inc = np.array([[0.0, 0.0, 0.0], [1.1, 0.7, 0.5], [2.5, 4.0, 1.2]])
+    obs = observations_phi_cut(90)
+    for r_c in (1.5, 0.0):
+        out = run_gpu(cl, K, r_c, C128, inc, obs=obs, tol=1e-12, mono=True)
+        Z = O.assemble(cl, K, r_c if r_c > 0 else None, sparse=False)
+        X = O.solve_lu(Z, O.rhs(cl, K, inc))
+        rel = np.linalg.norm(out["currents"] - X) / np.linalg.norm(X)
+        assert rel < 1e-5, rel
+        assert out["rc"] == 0 and out["stats"]["converged"] == 1
+        s_ref = O.rcs_bistatic(cl, K, X, obs)
+        assert np.max(np.abs(out["sigma"] - s_ref)) / np.max(s_ref) < 1e-8
+        assert np.allclose(out["sigma_mono"], O.rcs_monostatic(cl, K, X, inc), rtol=1e-7, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["dense", "sparse"])
+def test_small_config_fp64_and_c64(mode):
+    """The small workload (200 wires, N = 1400) in both precisions against the oracle."""
+    cfg = CONFIGS["small"]
+    cl = cloud_small()
+    r_c = cfg["r_c"] if mode == "sparse" else 0.0
+    inc, obs = cfg["inc"](), cfg["obs"]()
+    Z = O.assemble(cl, K, r_c if mode == "sparse" else None, sparse=False)
+    X = O.solve_lu(Z, O.rhs(cl, K, inc))
+    s_ref = O.rcs_bistatic(cl, K, X, obs)[0, :, 0]
+    g64 = run_gpu(cl, K, r_c, C128, inc, obs=obs, tol=1e-11)
+    assert np.linalg.norm(g64["currents"] - X) / np.linalg.norm(X) < 1e-5
+    assert_rcs_db(g64["sigma"][0, :, 0], s_ref, db=1e-4)
+    g32 = run_gpu(cl, K, r_c, C64, inc, obs=obs, tol=1e-6)
+    assert np.linalg.norm(g32["currents"] - X) / np.linalg.norm(X) < 1e-4
+    assert_rcs_db(g32["sigma"][0, :, 0], s_ref, db=0.1)
+
+
+def test_far_field_stateless_matches_oracle():
+    import torch
+    from paper_2410_03060_gb300 import swm
+
+    cl = _mixed_cloud(seed=9)
+    m, off = O.numbering(cl.nseg)
+    rng = np.random.default_rng(2)
+    cur = rng.standard_normal((3, off[-1])) + 1j * rng.standard_normal((3, off[-1]))
+    obs = np.stack([rng.uniform(0, math.pi, 33), rng.uniform(0, 2 * math.pi, 33)], 1)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sig = torch.zeros((3, 33, 2), dtype=torch.float64, device="cuda")
+    swm.swm_far_field(None, t(cl.centres), t(cl.dirs), t(cl.lengths), t(cl.nseg), t(off), K, t(cur), t(obs), sig)
+    torch.cuda.synchronize()
+    ref = np.transpose(O.rcs_from_far_field(O.far_field(cl, K, cur.T, _rhat(obs)), obs), (2, 0, 1))
+    assert np.max(np.abs(sig.cpu().numpy() - ref)) / np.max(ref) < 1e-10
+
+
+def _rhat(obs):
+    th, ph = obs[:, 0], obs[:, 1]
+    return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+
+
+# ------------------------------------------------------------------------------------- edge cases
+def test_edge_single_wire_and_two_segment_wires():
+    cl = cloud_uniform_cube(1, 1.0, seed=2, nseg=2)
+    out = run_gpu(cl, K, 3.0, C128, np.array([[0.4, 0.0, 0.0]]), tol=1e-12)
+    X = O.solve_lu(O.assemble(cl, K, None, sparse=False), O.rhs(cl, K, np.array([[0.4, 0.0, 0.0]])))
+    assert np.allclose(out["currents"], X, rtol=1e-9)
+    cl = cloud_uniform_cube(40, 3.0, seed=3, nseg=2)
+    out = run_gpu(cl, K, 1.0, C128, np.array([[0.4, 0.0, 0.0]]), tol=1e-12)
+    X = O.solve_lu(O.assemble(cl, K, 1.0, sparse=False), O.rhs(cl, K, np.array([[0.4, 0.0, 0.0]])))
+    assert np.linalg.norm(out["currents"] - X) / np.linalg.norm(X) < 1e-8
+
+
+def test_edge_isolated_limit_converges_at_once():
+    cl = cloud_uniform_cube(50, 50.0, seed=6)
+    out = run_gpu(cl, K, 1e-3, C128, np.array([[0.0, 0.0, 0.0]]), tol=1e-10)
+    assert out["stats"]["nb"] == 50 and out["stats"]["iterations"] <= 1
+    X = O.solve_lu(O.assemble(cl, K, 1e-3, sparse=False), O.rhs(cl, K, np.array([[0.0, 0.0, 0.0]])))
+    assert np.allclose(out["currents"], X, rtol=1e-9, atol=1e-15)
+
+
+def test_edge_restart_one_and_max_iter():
+    cl = cloud_uniform_cube(60, 4.0, seed=7)
+    inc = np.array([[0.0, 0.0, 0.0]])
+    X = O.solve_lu(O.assemble(cl, K, 2.0, sparse=False), O.rhs(cl, K, inc))
+    out = run_gpu(cl, K, 2.0, C128, inc, tol=1e-10, restart=1)
+    assert np.linalg.norm(out["currents"] - X) / np.linalg.norm(X) < 1e-6
+    out = run_gpu(cl, K, 2.0, C128, inc, tol=1e-14, max_iter=2)
+    assert out["rc"] == 1 and out["stats"]["iterations"] == 2 and out["stats"]["converged"] == 0
+
+
+def test_device_inputs_equal_host_inputs():
+    cl = _mixed_cloud(seed=12)
+    a = run_gpu(cl, K, 0.9, C128, np.array([[0.2, 0.3, 0.0]]))
+    b = run_gpu(cl, K, 0.9, C128, np.array([[0.2, 0.3, 0.0]]), device_inputs=True)
+    assert np.array_equal(a["currents"], b["currents"])
+
+
+def test_invalid_inputs_rejected():
+    from paper_2410_03060_gb300 import swm
+
+    cl = cloud_uniform_cube(5, 2.0, seed=1)
+    ctx = swm.swm_create(0)
+    bad = cl.dirs.copy()
+    bad[2] *= 1.01
+    with pytest.raises(swm.SwmError) as e:
+        swm.swm_set_cloud(ctx, cl.centres, bad, cl.lengths, cl.radii, cl.nseg)
+    assert "unit" in str(e.value)
+    ns = cl.nseg.copy()
+    ns[0] = 17
+    with pytest.raises(swm.SwmError):
+        swm.swm_set_cloud(ctx, cl.centres, cl.dirs, cl.lengths, cl.radii, ns)
+    with pytest.raises(swm.SwmError):
+        swm.swm_build(ctx, K, 1.0, 0)  # no cloud loaded
+    swm.swm_set_cloud(ctx, cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)
+    with pytest.raises(swm.SwmError):
+        swm.swm_solve(ctx, [[0.0, 0.0, 0.0]])  # not built
+    with pytest.raises(swm.SwmError):
+        swm.swm_build(ctx, -1.0, 1.0, 0)
+    swm.swm_build(ctx, K, 1.0, 0)
+    with pytest.raises(swm.SwmError):
+        swm.swm_solve(ctx, [[0.0, 0.0, 0.0]], restart=0)
+    swm.swm_destroy(ctx)
