@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Throughput of the sparsified thin-wire MoM hot path on GB300: unknowns x incidences solved per
+second, RCS checked against the plain FP64 path.
+
+One step = the whole hot path on one cloud: load the wire cloud, S-NFC neighbour search, block
+fill, block-Jacobi preconditioner, right-hand side, GMRES(50) to 1e-6, and the 720-angle bistatic
+RCS.  Workload: 10,000 wires (lengths U[0.3, 0.6] wavelengths, <= 0.08-wavelength segments,
+radius 1e-3, Gaussian centres sigma = 30 wavelengths, random directions), r_c = 3 wavelengths, one
+plane wave arriving from +z, theta-polarised.  Inputs are seeded and synthetic.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own cloud (seed 1 + rank): weak scaling, no data-path
+collective; the timing is the max over ranks.  ``--impl reference`` times the FP64 CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import cloud_mid, incidences_single_minus_z, observations_phi_cut  # noqa: E402
+
+METRIC = "unknowns×incidences solved/sec at ≤0.1 dB RCS error vs plain FP64 path"
+UNIT = "unknowns*incidences/s"
+K0 = 2.0 * math.pi
+R_C = 3.0
+TOL = 1e-6
+RESTART = 50
+N_OBS = 720
+FP32_FLOPS_PER_EVAL = 29  # algorithmic FP32 operations of one kernel evaluation of the fill
+N_SM = 152
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def rcs_db_error(s, ref, floor_db=30.0):
+    s, ref = np.asarray(s).ravel(), np.asarray(ref).ravel()
+    keep = ref >= ref.max() * 10 ** (-floor_db / 10)
+    return float(np.max(np.abs(10 * np.log10(s[keep] / ref[keep]))))
+
+
+def slab_sample(cloud, n_target):
+    """The wires of the centre slab |x| < w holding about n_target wires (local density kept)."""
+    x = np.abs(cloud.centres[:, 0])
+    w = np.sort(x)[min(len(x) - 1, n_target)]
+    return cloud.subset(np.nonzero(x < w)[0])
+
+
+def oracle_step(cloud, inc, obs):
+    """The whole path on the FP64 CPU oracle (test infrastructure, timed as the CPU baseline)."""
+    import oracle as O
+
+    Z = O.assemble(cloud, K0, R_C, sparse=True)
+    Mi = O.block_jacobi(cloud, K0)
+    m, off = O.numbering(cloud.nseg)
+    b = O.rhs(cloud, K0, inc)
+    X = np.zeros_like(b)
+    for i in range(b.shape[1]):
+        X[:, i], _, _ = O.gmres(Z, b[:, i], Mi, off, TOL, RESTART, 1000)
+    return O.rcs_bistatic(cloud, K0, X, obs)
+
+
+def cpu_baseline(n_wires=1000):
+    cl = slab_sample(cloud_mid(), n_wires)
+    inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
+    t = time.perf_counter()
+    oracle_step(cl, inc, obs)
+    dt = time.perf_counter() - t
+    return {"value": cl.n_unknowns * inc.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"centre slab of the 10,000-wire cloud: {cl.nw} wires, N={cl.n_unknowns}, full path "
+                      f"(pairs, fill, block-Jacobi, RHS, GMRES(50) 1e-6, 720-angle RCS) in {dt:.1f} s; "
+                      f"single-threaded NumPy"}
+
+
+# ---------------------------------------------------------------------------------- our arm
+def kernel_roofline(cls, st, prof_ms, launches, prec, n_rhs, pk, clocks):
+    """Achieved algorithmic rate of one kernel class over the timed region."""
+    esz = 16 if prec == "c128" else 8
+    N, nw = st["n"], st["nw"]
+    if prof_ms <= 0 or launches <= 0:
+        return None
+    per_launch_ms = prof_ms / launches
+    if cls == "apply":
+        # E values + column map + x + y + V row + per-row metadata, per product
+        byts = (st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 3 * N * esz * n_rhs + 4 * N + 28 * nw)
+        work = byts * st["_applies"]
+        return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
+                "unit": "GB/s", "per_launch_bytes": byts, "per_launch_ms": per_launch_ms}
+    if cls in ("dots", "update", "finish"):
+        vec = N * esz * n_rhs
+        work = sum((j + 1) * vec + 2 * vec for j in st["_steps"]) * st["_cycles_mult"]
+        return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
+                "unit": "GB/s", "per_launch_bytes": work / max(1, len(st["_steps"])), "per_launch_ms": per_launch_ms}
+    if cls == "fill_mutual":
+        flops = st["fill_evals"] * FP32_FLOPS_PER_EVAL
+        mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = N_SM * 128 * 2 * mhz * 1e6 / 1e12 if prec == "c64" else 1.25
+        return {"bound": "alu", "achieved": flops / (per_launch_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "per_launch_flops": flops, "per_launch_ms": per_launch_ms,
+                "note": ("FP32 peak = 152 SMs x 128 lanes x 2 flops x max SM clock" if prec == "c64"
+                         else "nominal FP64 peak")}
+    return {"bound": "other", "per_launch_ms": per_launch_ms}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_03060_gb300 import swm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec_id = swm.SWM_C64 if args.precision == "c64" else swm.SWM_C128
+    cl = cloud_mid(seed=1 + rank)
+    inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
+    N = cl.n_unknowns
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+           (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
+    sigma = torch.zeros((1, N_OBS, 2), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    ctx = swm.swm_create(local)
+
+    def step(prec=prec_id, inputs=dev, out=sigma):
+        swm.swm_set_cloud(ctx, *inputs)
+        swm.swm_build(ctx, K0, R_C, prec)
+        swm.swm_solve(ctx, inc, TOL, RESTART, 1000)
+        swm.swm_rcs_bistatic(ctx, obs, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st0 = swm.swm_get_stats(ctx)
+    # accuracy gate against the plain FP64 path (untimed)
+    s_fast = sigma.cpu().numpy()[0, :, 0].copy()
+    sig64 = torch.zeros_like(sigma)
+    step(prec=swm.SWM_C128, out=sig64)
+    torch.cuda.synchronize()
+    err_db = rcs_db_error(s_fast, sig64.cpu().numpy()[0, :, 0])
+
+    # dominant kernel class: one profiled step per class (untimed)
+    classes = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "rhs", "apply", "dots", "update",
+               "finish", "far"]
+    share = {}
+    for c in classes:
+        swm.swm_profile(ctx, c)
+        step()
+        torch.cuda.synchronize()
+        share[c] = swm.swm_get_stats(ctx)["prof_ms"]
+    dominant = max(share, key=share.get)
+    swm.swm_profile(ctx, dominant)
+
+    # timed region
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = swm.swm_get_stats(ctx)["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    st = swm.swm_get_stats(ctx)
+    launches = (st["kernel_launches"] - l0) // max(1, args.steps)
+    ms_step = float(np.mean(ms))
+    prof_ms, prof_n = st["prof_ms"], st["prof_launches"]
+    swm.swm_profile(ctx, "none")
+
+    # e2e through the public API with pinned host buffers (copies inside the timed region)
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in
+               (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
+    sig_host = torch.zeros((1, N_OBS, 2), dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 50))
+    e2e = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        step(inputs=host_in, out=sig_host)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t)
+    e2e_ms = 1e3 * float(np.mean(e2e))
+    h2d = int(sum(a.nbytes for a in host_in))
+    d2h = int(sig_host.nbytes)
+
+    # plain FP64 path on the same GPU
+    f64 = []
+    for _ in range(max(1, min(args.steps, 20))):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(prec=swm.SWM_C128, out=sig64)
+        b.record()
+        f64.append((a, b))
+    torch.cuda.synchronize()
+    ms64 = float(np.mean([a.elapsed_time(b) for a, b in f64]))
+    swm.swm_destroy(ctx)
+
+    # max over ranks, units over all ranks
+    tm = torch.tensor([ms_step, e2e_ms, ms64], dtype=torch.float64, device="cuda")
+    units = torch.tensor([float(N)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    ms_step, e2e_ms, ms64 = tm.tolist()
+    total_units = units.item() * inc.shape[0]
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    # reconstruct the Arnoldi step indices of one solve for the Gram-Schmidt byte counts
+    it = st["iterations"]
+    steps_j = []
+    while it > 0:
+        c = min(RESTART, it)
+        steps_j += list(range(c))
+        it -= c
+    st["_steps"] = steps_j
+    st["_cycles_mult"] = args.steps
+    st["_applies"] = (st["iterations"] + st["restarts"] + 1) * args.steps
+    roof = kernel_roofline(dominant, st, prof_ms, prof_n, args.precision, 1, pk, clk)
+    if roof and roof.get("peak"):
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["peak_source"] = "of measured (MEASURED_PEAKS.json)" if roof["unit"] == "GB/s" else roof.get("note")
+    if roof is not None:
+        roof["traffic"] = None
+        roof["kernel"] = dominant
+    out = {
+        "metric": METRIC, "value": total_units / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64" if args.precision == "c64" else "c128",
+        "data": "synthetic (seeded wire clouds)",
+        "config": {"workload": "mid: 10,000 wires, Gaussian sigma 30, r_c 3, GMRES(50) 1e-6, 1 incidence, "
+                               "720-angle bistatic RCS", "nw": cl.nw, "unknowns": N, "blocks": st["nb"],
+                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"{world} independent clouds (one per GPU)"},
+        "gpu_launches": int(launches),
+        "e2e": {"value": total_units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "rcs_err_db_vs_fp64": err_db,
+        "fp64_path": {"value": total_units / (ms64 * 1e-3), "ms_per_step": ms64,
+                      "speedup_of_value": ms64 / ms_step},
+        "iterations": st["iterations"],
+        "phase_ms": {k: st[k] for k in ("ms_neighbour", "ms_fill", "ms_precond", "ms_rhs", "ms_solve", "ms_rcs")},
+        "kernel_share_ms_per_step": share,
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # sample size keeps the whole run within a few minutes (about 8 ms of oracle time per wire)
+    n_wires = int(min(1000, max(100, 150.0 / ((args.steps + args.warmup) * 0.008))))
+    cl = slab_sample(cloud_mid(), n_wires)
+    inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
+    for _ in range(args.warmup):
+        oracle_step(cl, inc, obs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(cl, inc, obs)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    v = cl.n_unknowns * inc.shape[0] / dt
+    sample = (f"centre slab of the 10,000-wire cloud: {cl.nw} wires, N={cl.n_unknowns}; full path on the FP64 "
+              f"NumPy oracle, single-threaded")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded wire clouds)",
+        "config": {"workload": "mid (sampled): 10,000-wire cloud statistics, r_c 3, GMRES(50) 1e-6, 1 incidence, "
+                               "720-angle bistatic RCS", "nw": cl.nw, "unknowns": cl.n_unknowns},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

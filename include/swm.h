@@ -98,7 +98,27 @@ typedef struct swm_stats {
   double ms_solve;
   double ms_rcs;
   int64_t kernel_launches; /* kernels launched by this context since its creation */
+  int64_t fill_evals;      /* kernel evaluations of the mutual fill (sum over blocks p < q of
+                              n_s(p) n_s(q) n_q^2) in the last build */
+  int64_t nnz_offd;        /* stored entries of Z M^-1 without its diagonal blocks */
+  int64_t ncm_offd;        /* column-map entries of that matrix (sum over block-rows of K_p) */
+  double prof_ms;          /* summed device time of the profiled kernel class (swm_profile) */
+  int64_t prof_launches;   /* launches of the profiled kernel class */
 } swm_stats;
+
+/* kernel classes for swm_profile */
+#define SWM_K_NONE 0
+#define SWM_K_PAIRS 1       /* S-NFC pair count and write passes */
+#define SWM_K_FILL_SELF 2   /* self blocks */
+#define SWM_K_FILL_MUTUAL 3 /* mutual blocks */
+#define SWM_K_INVERT 4      /* self-block inverses */
+#define SWM_K_FORM_E 5      /* Z_pq Z_qq^-1 */
+#define SWM_K_RHS 6         /* right-hand sides */
+#define SWM_K_APPLY 7       /* block-sparse product (GMRES step and residual) */
+#define SWM_K_DOTS 8        /* first Gram-Schmidt pass */
+#define SWM_K_UPDATE 9      /* second Gram-Schmidt pass */
+#define SWM_K_FINISH 10     /* norm, Hessenberg column, rotation */
+#define SWM_K_FAR 11        /* far field: partial sums and their reduction to RCS */
 
 /* Create a context on CUDA device `device` that issues all work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context. */
@@ -157,6 +177,11 @@ int swm_rcs_monostatic(swm_ctx* ctx, double* sigma_out, int out_kind);
 
 /* Counters and phase times of the context. */
 int swm_get_stats(const swm_ctx* ctx, swm_stats* out);
+
+/* Time every launch of one kernel class (SWM_K_*) with CUDA events on the context stream from now
+ * on, adding to stats.prof_ms / stats.prof_launches (both reset by this call).  SWM_K_NONE stops.
+ * The events cost a few microseconds of device time per launch of that class only. */
+int swm_profile(swm_ctx* ctx, int kernel_class);
 
 /* Kept block pattern of the last build (Eq. neardef) as nb x 2 int64 (p, q) pairs in the
  * caller's wire numbering, host memory of at least 2 * stats.nb entries, rows sorted by p then q. */

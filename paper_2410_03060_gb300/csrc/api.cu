@@ -153,6 +153,10 @@ void swm_destroy(swm_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (auto& e : ctx->prof_ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   dfree_group(ctx, ctx->solve_bufs);
   dfree_group(ctx, ctx->build_bufs);
   dfree_group(ctx, ctx->cloud_bufs);
@@ -264,7 +268,10 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->stats.n = ctx->N;
   ctx->stats.nb = ctx->nb;
   ctx->stats.nnz = ctx->full.nval;
+  ctx->stats.nnz_offd = ctx->offd.nval;
+  ctx->stats.ncm_offd = ctx->offd.ncm;
   ctx->built = true;
+  ctx->prof_flush();
   return SWM_OK;
 }
 
@@ -306,6 +313,7 @@ int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restar
     rc = gmres_solve(ctx, tol, restart, max_iter);
     ctx->stats.ms_solve = t.stop();
   }
+  ctx->prof_flush();
   if (rc < 0) return rc;
   ctx->stats.n_rhs = n_inc;
   ctx->solved = true;
@@ -364,16 +372,19 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
   else
     SWM_TRY(dalloc(ctx, tmp, (void**)&sig, sizeof(double) * 2 * npairs));
   std::string err;
+  ctx->prof_begin(SWM_K_FAR);
   int rc = far_field_launch(ctx->stream, &ctx->launches, ctx->prec == SWM_C64, ctx->prec == SWM_C128, ctx->Xv, ctx->nw,
                             ctx->N, nullptr, nullptr, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L,
                             ctx->ns, ctx->off, true, ctx->k, R, mono ? R : n_obs, obs_dev, stride, mono, sig, scratch,
                             sb, &err);
+  ctx->prof_end(SWM_K_FAR);
   if (rc < 0) return ctx->fail(rc, err);
   if (out_kind == SWM_HOST)
     SWM_CK(cudaMemcpyAsync(sigma_out, sig, sizeof(double) * 2 * npairs, cudaMemcpyDeviceToHost, ctx->stream));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   dfree_group(ctx, tmp);
   ctx->stats.ms_rcs = t.stop();
+  ctx->prof_flush();
   return SWM_OK;
 }
 
@@ -389,6 +400,20 @@ int swm_get_stats(const swm_ctx* ctx, swm_stats* out) {
   if (!ctx || !out) return SWM_EINVAL;
   *out = ctx->stats;
   out->kernel_launches = ctx->launches;
+  out->prof_ms = ctx->prof_ms;
+  out->prof_launches = ctx->prof_n;
+  return SWM_OK;
+}
+
+int swm_profile(swm_ctx* ctx, int kernel_class) {
+  if (!ctx) return SWM_EINVAL;
+  if (kernel_class < SWM_K_NONE || kernel_class > SWM_K_FAR) return ctx->fail(SWM_EINVAL, "bad kernel class");
+  SWM_TRY(set_device(ctx));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof_flush();
+  ctx->prof_cls = kernel_class;
+  ctx->prof_ms = 0.0;
+  ctx->prof_n = 0;
   return SWM_OK;
 }
 

@@ -95,6 +95,38 @@ struct swm_ctx {
 
   swm_stats stats{};
 
+  // per-kernel-class event timing (swm_profile)
+  int prof_cls = SWM_K_NONE;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  size_t prof_used = 0;
+  double prof_ms = 0.0;
+  int64_t prof_n = 0;
+  void prof_begin(int cls) {
+    if (cls != prof_cls) return;
+    if (prof_used == prof_ev.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      prof_ev.emplace_back(a, b);
+    }
+    cudaEventRecord(prof_ev[prof_used].first, stream);
+  }
+  void prof_end(int cls) {
+    if (cls != prof_cls) return;
+    cudaEventRecord(prof_ev[prof_used].second, stream);
+    ++prof_used;
+  }
+  // add the recorded intervals (the stream must have been synchronised)
+  void prof_flush() {
+    for (size_t i = 0; i < prof_used; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, prof_ev[i].first, prof_ev[i].second) == cudaSuccess) prof_ms += ms;
+    }
+    prof_n += (int64_t)prof_used;
+    prof_used = 0;
+    cudaGetLastError();
+  }
+
   int fail(int code, const std::string& msg) {
     err = msg;
     return code;

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
     const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
     const double* __restrict__ tx, const double* __restrict__ ty, const double* __restrict__ tz,
     const double* __restrict__ Ls, const double* __restrict__ as, const int32_t* __restrict__ ns, double k,
-    GLTable gl, Layout lay, int nbatch, cplx<TV>* __restrict__ Z) {
+    GLTable gl, Layout lay, int nbatch, cplx<TV>* __restrict__ Z, unsigned long long* __restrict__ evals) {
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t o_item = round16(sizeof(BlockGeo) * nbatch);
   const size_t o_out = o_item + round16(sizeof(int) * (nbatch + 1));
@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
   int* out_pre = reinterpret_cast<int*>(smem + o_out);    // nbatch + 1
   SegI<R>* seg = reinterpret_cast<SegI<R>*>(smem + o_seg);
   __shared__ float xs4[4], ws4[4], xs8[8], ws8[8];
+  __shared__ unsigned long long cta_evals;
 
   const int tid = threadIdx.x;
   const int64_t b0 = (int64_t)blockIdx.x * nbatch;
@@ -349,6 +350,8 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
     xs8[tid] = (float)gl.x8[tid];
     ws8[tid] = (float)gl.w8[tid];
   }
+  if (tid == 0) cta_evals = 0;
+  __syncthreads();
   // --- per-block setup, float64, one thread per block
   if (tid < nb_here) {
     const int64_t b = ublk[b0 + tid];
@@ -388,6 +391,7 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
     G.bpq = lay.rowbase[p] + lay.colpos[b];
     G.bqp = lay.rowbase[q] + lay.colpos[bq];
     geo[tid] = G;
+    atomicAdd(&cta_evals, (unsigned long long)(nsp * nsq * nq * nq));
   }
   __syncthreads();
   if (tid == 0) {
@@ -402,6 +406,7 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
     }
     item_pre[nb_here] = it;
     out_pre[nb_here] = ot;
+    atomicAdd(evals, cta_evals);
   }
   __syncthreads();
 
@@ -478,7 +483,7 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
 }
 
 template <typename R, typename TV>
-int launch_fill(swm_ctx* ctx, const GLTable& gl) {
+int launch_fill(swm_ctx* ctx, const GLTable& gl, unsigned long long* evals) {
   const int ms = ctx->max_ns;
   const int items_per_block = ms * ms;
   // shared budget for segment pairs: 48 KB (float) or 64 KB (double)
@@ -490,9 +495,11 @@ int launch_fill(swm_ctx* ctx, const GLTable& gl) {
   SWM_CK(cudaFuncSetAttribute(k_mutual_blocks<R, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (ctx->nup > 0) {
     const int64_t grid = ceil_div(ctx->nup, nbatch);
+    ctx->prof_begin(SWM_K_FILL_MUTUAL);
     k_mutual_blocks<R, TV><<<(unsigned)grid, kFillThreads, smem, ctx->stream>>>(
         ctx->nup, ctx->ublk, ctx->col, ctx->bt, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->a,
-        ctx->ns, ctx->k, gl, ctx->full, nbatch, reinterpret_cast<cplx<TV>*>(ctx->Z));
+        ctx->ns, ctx->k, gl, ctx->full, nbatch, reinterpret_cast<cplx<TV>*>(ctx->Z), evals);
+    ctx->prof_end(SWM_K_FILL_MUTUAL);
     SWM_LAUNCHED();
   }
   return SWM_OK;
@@ -503,18 +510,29 @@ int fill_blocks(swm_ctx* ctx) {
   const int64_t nw = ctx->nw;
   const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Z, esz * std::max<int64_t>(1, ctx->full.nval)));
+  std::vector<Buf> tmp;
+  unsigned long long* evals = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&evals, sizeof(unsigned long long)));
+  SWM_CK(cudaMemsetAsync(evals, 0, sizeof(unsigned long long), ctx->stream));
   const unsigned grid_self = (unsigned)ceil_div(nw, 4);
-  if (ctx->prec == SWM_C128) {
+  ctx->prof_begin(SWM_K_FILL_SELF);
+  if (ctx->prec == SWM_C128)
     k_self_blocks<double><<<grid_self, 128, 0, ctx->stream>>>(nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b,
                                                                ctx->full, reinterpret_cast<c128*>(ctx->Z));
-    SWM_LAUNCHED();
-    SWM_TRY((launch_fill<double, double>(ctx, gl)));
-  } else {
+  else
     k_self_blocks<float><<<grid_self, 128, 0, ctx->stream>>>(nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b,
                                                               ctx->full, reinterpret_cast<c64*>(ctx->Z));
-    SWM_LAUNCHED();
-    SWM_TRY((launch_fill<float, float>(ctx, gl)));
-  }
+  ctx->prof_end(SWM_K_FILL_SELF);
+  SWM_LAUNCHED();
+  if (ctx->prec == SWM_C128)
+    SWM_TRY((launch_fill<double, double>(ctx, gl, evals)));
+  else
+    SWM_TRY((launch_fill<float, float>(ctx, gl, evals)));
+  unsigned long long he = 0;
+  SWM_CK(cudaMemcpyAsync(&he, evals, sizeof(he), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, tmp);
+  ctx->stats.fill_evals = (int64_t)he;
   return SWM_OK;
 }
 

@@ -474,7 +474,9 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   bool first = true;
   while (true) {
     // residual of the current y and the start of a cycle
+    ctx->prof_begin(SWM_K_APPLY);
     k_apply<TV><<<g_rows, kRows, 0, st>>>(1, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
+    ctx->prof_end(SWM_K_APPLY);
     SWM_LAUNCHED();
     k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, W0, first ? 1 : 0);
     SWM_LAUNCHED();
@@ -484,13 +486,21 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     if (hs.all_conv || hs.numeric || hs.iters >= max_iter) break;
     const int steps = std::min(restart, max_iter - hs.iters);
     for (int s = 0; s < steps; ++s) {
+      ctx->prof_begin(SWM_K_APPLY);
       k_apply<TV><<<g_rows, kRows, 0, st>>>(0, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
+      ctx->prof_end(SWM_K_APPLY);
       SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_DOTS);
       k_dots<TV><<<g_chunk, kRows, sm, st>>>(P, W0, W1, V);
+      ctx->prof_end(SWM_K_DOTS);
       SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_UPDATE);
       k_update<TV><<<g_chunk, kRows, sm, st>>>(P, W0, W1, V);
+      ctx->prof_end(SWM_K_UPDATE);
       SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_FINISH);
       k_finish<TV><<<g_chunk, kRows, sm, st>>>(P, W0, W1, V);
+      ctx->prof_end(SWM_K_FINISH);
       SWM_LAUNCHED();
       // poll every 8 steps so a converged cycle does not queue many empty steps
       if ((s & 7) == 7 && s + 1 < steps) {

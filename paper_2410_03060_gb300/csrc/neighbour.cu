@@ -358,14 +358,18 @@ int build_pattern(swm_ctx* ctx) {
   SWM_TRY(dalloc(ctx, tmp, (void**)&rcnt, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->row_ptr, sizeof(int64_t) * (nw + 1)));
   const double rc2 = ctx->dense ? 0.0 : ctx->rc * ctx->rc;
+  ctx->prof_begin(SWM_K_PAIRS);
   k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
                                               ctx->dense ? 1 : 0, 0, rcnt, nullptr, nullptr);
+  ctx->prof_end(SWM_K_PAIRS);
   SWM_LAUNCHED();
   SWM_TRY(exclusive_scan_i32_to_i64(ctx, rcnt, ctx->row_ptr, nw, &ctx->nb));
   if (ctx->nb > INT32_MAX / 2) return ctx->fail(SWM_EINVAL, "too many kept blocks for 32-bit positions");
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->col, sizeof(int32_t) * ctx->nb));
+  ctx->prof_begin(SWM_K_PAIRS);
   k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
                                               ctx->dense ? 1 : 0, 1, nullptr, ctx->row_ptr, ctx->col);
+  ctx->prof_end(SWM_K_PAIRS);
   SWM_LAUNCHED();
 
   // --- per-row metadata, transpose map, upper-triangle block list, layouts

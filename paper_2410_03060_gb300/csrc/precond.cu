@@ -125,20 +125,28 @@ int build_precond(swm_ctx* ctx) {
   const unsigned g1 = (unsigned)ceil_div(nw, 4);
   const unsigned g2 = (unsigned)std::max<int64_t>(1, ceil_div(ctx->nb * 32, 256));
   if (ctx->prec == SWM_C128) {
+    ctx->prof_begin(SWM_K_INVERT);
     k_invert_self<double><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
                                                        ctx->minv_off, (c128*)ctx->Minv, sing);
+    ctx->prof_end(SWM_K_INVERT);
     SWM_LAUNCHED();
+    ctx->prof_begin(SWM_K_FORM_E);
     k_form_E<double><<<g2, 256, 0, ctx->stream>>>(ctx->nb, ctx->col, ctx->bt, ctx->m, ctx->full, ctx->offd,
                                                   (const c128*)ctx->Z, ctx->minv_off, (const c128*)ctx->Minv,
                                                   (c128*)ctx->Zp);
+    ctx->prof_end(SWM_K_FORM_E);
     SWM_LAUNCHED();
   } else {
+    ctx->prof_begin(SWM_K_INVERT);
     k_invert_self<float><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c64*)ctx->Z,
                                                       ctx->minv_off, (c64*)ctx->Minv, sing);
+    ctx->prof_end(SWM_K_INVERT);
     SWM_LAUNCHED();
+    ctx->prof_begin(SWM_K_FORM_E);
     k_form_E<float><<<g2, 256, 0, ctx->stream>>>(ctx->nb, ctx->col, ctx->bt, ctx->m, ctx->full, ctx->offd,
                                                  (const c64*)ctx->Z, ctx->minv_off, (const c64*)ctx->Minv,
                                                  (c64*)ctx->Zp);
+    ctx->prof_end(SWM_K_FORM_E);
     SWM_LAUNCHED();
   }
   int hs = 0;

@@ -26,7 +26,13 @@ __device__ __forceinline__ double reduce_2pi(double x) {
 }
 
 __device__ __forceinline__ double sinc_d(double z) { return fabs(z) < 1e-8 ? 1.0 - z * z / 6.0 : sin(z) / z; }
-__device__ __forceinline__ float sinc_f(float z) { return fabsf(z) < 1e-4f ? 1.0f - z * z / 6.0f : __sinf(z) / z; }
+// sin(z)/z in float: Taylor series to z^6 on |z| <= 0.5 (truncation below 2e-8 relative), else
+// the correctly rounded-to-a-few-ulp sinf; the fast __sinf has only absolute accuracy.
+__device__ __forceinline__ float sinc_f(float z) {
+  const float z2 = z * z;
+  if (z2 <= 0.25f) return 1.0f + z2 * (-1.0f / 6.0f + z2 * (1.0f / 120.0f + z2 * (-1.0f / 5040.0f)));
+  return sinf(z) / z;
+}
 
 // One thread per (wire, incidence).  frames: per incidence khat[3], e[3].
 template <typename TV>
@@ -64,8 +70,8 @@ __global__ void k_rhs(int64_t nw, int n_inc, const double* __restrict__ cx, cons
     const float sc = sinc_f((float)(0.5 * beta * D));
     const float amp = (float)(et * D) * sc * sc;
     float sa, ca, sb, cb;
-    __sincosf((float)reduce_2pi(ph0 + beta * s1), &sa, &ca);
-    __sincosf((float)(beta * D), &sb, &cb);
+    sincosf((float)reduce_2pi(ph0 + beta * s1), &sa, &ca);
+    sincosf((float)(beta * D), &sb, &cb);
     c64 z = mkc(amp * ca, amp * sa);
     const c64 rat = mkc(cb, sb);
     for (int l = 0; l < n - 1; ++l) {
@@ -163,8 +169,8 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial(Geo geo, int64_t nw,
       Si = amp * acc.im;
     } else {
       float sa, ca, sb, cb;
-      __sincosf((float)reduce_2pi(phc + beta * s1), &sa, &ca);
-      __sincosf((float)(beta * D), &sb, &cb);
+      sincosf((float)reduce_2pi(phc + beta * s1), &sa, &ca);
+      sincosf((float)(beta * D), &sb, &cb);
       const float sc = sinc_f((float)(0.5 * beta * D));
       c64 z = mkc(ca, sa), acc = mkc(0.f, 0.f);
       const c64 rat = mkc(cb, sb);
@@ -215,6 +221,7 @@ __global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
   const int64_t tot = ctx->nw * (int64_t)n_inc;
   const unsigned grid = (unsigned)ceil_div(tot, 256);
+  ctx->prof_begin(SWM_K_RHS);
   if (ctx->prec == SWM_C128)
     k_rhs<double><<<grid, 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz,
                                                  ctx->L, ctx->ns, ctx->off, ctx->N, ctx->k, frames_dev,
@@ -222,6 +229,7 @@ int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
   else
     k_rhs<float><<<grid, 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz,
                                                 ctx->L, ctx->ns, ctx->off, ctx->N, ctx->k, frames_dev, (c64*)ctx->Bv);
+  ctx->prof_end(SWM_K_RHS);
   SWM_LAUNCHED();
   return SWM_OK;
 }

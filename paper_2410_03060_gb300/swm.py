@@ -36,7 +36,9 @@ class swm_stats(C.Structure):
                 ("n_rhs", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("rel_residual", C.c_double), ("ms_neighbour", C.c_double), ("ms_fill", C.c_double),
                 ("ms_precond", C.c_double), ("ms_rhs", C.c_double), ("ms_solve", C.c_double),
-                ("ms_rcs", C.c_double), ("kernel_launches", C.c_int64)]
+                ("ms_rcs", C.c_double), ("kernel_launches", C.c_int64), ("fill_evals", C.c_int64),
+                ("nnz_offd", C.c_int64), ("ncm_offd", C.c_int64), ("prof_ms", C.c_double),
+                ("prof_launches", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -54,6 +56,7 @@ _SIGS = {
     "swm_rcs_bistatic": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "swm_rcs_monostatic": (C.c_int, [_P, _P, C.c_int]),
     "swm_get_stats": (C.c_int, [_P, C.POINTER(swm_stats)]),
+    "swm_profile": (C.c_int, [_P, C.c_int]),
     "swm_get_pattern": (C.c_int, [_P, _P]),
     "swm_get_block": (C.c_int, [_P, C.c_int64, C.c_int64, _P]),
     "swm_get_rhs": (C.c_int, [_P, _P]),
@@ -233,6 +236,16 @@ def swm_get_stats(ctx: Ctx) -> dict:
     s = swm_stats()
     _check(ctx, load().swm_get_stats(ctx.handle, C.byref(s)))
     return {name: getattr(s, name) for name, _ in swm_stats._fields_}
+
+
+SWM_K = {"none": 0, "pairs": 1, "fill_self": 2, "fill_mutual": 3, "invert": 4, "form_e": 5, "rhs": 6,
+         "apply": 7, "dots": 8, "update": 9, "finish": 10, "far": 11}
+
+
+def swm_profile(ctx: Ctx, kernel_class) -> int:
+    """Time every launch of one kernel class (name from SWM_K or its number) with CUDA events."""
+    kc = SWM_K[kernel_class] if isinstance(kernel_class, str) else int(kernel_class)
+    return _check(ctx, load().swm_profile(ctx.handle, kc))
 
 
 def swm_get_pattern(ctx: Ctx) -> np.ndarray:

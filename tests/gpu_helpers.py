@@ -43,18 +43,30 @@ def run_gpu(cloud, k, r_c, prec, inc, obs=None, tol=1e-10, restart=50, max_iter=
         raise
 
 
-def block_errors(ctx, cloud, k, pairs):
-    """max |Z_gpu - Z_oracle| / max |Z_oracle| over the given blocks."""
+def block_errors(ctx, cloud, k, pairs, scaled=False):
+    """Worst block error over the given blocks: max |Z_gpu - Z_oracle| / max |Z_oracle| per block,
+    or, with ``scaled``, divided instead by sqrt(max|Z_pp| max|Z_qq|), the scale of the two self
+    blocks the block couples.  Returns (worst, (p, q) of the worst block)."""
     import oracle as O
     from paper_2410_03060_gb300 import swm
 
-    worst = 0.0
+    worst, where = 0.0, None
     m = cloud.nseg - 1
+    diag = {}
+
+    def dmax(p):
+        if p not in diag:
+            diag[p] = float(np.max(np.abs(O.self_block(cloud, k, p))))
+        return diag[p]
     for p, q in pairs:
-        zg = swm.swm_get_block(ctx, int(p), int(q), int(m[p]), int(m[q]))
-        zo = O.block(cloud, k, int(p), int(q))
-        worst = max(worst, float(np.max(np.abs(zg - zo)) / np.max(np.abs(zo))))
-    return worst
+        p, q = int(p), int(q)
+        zg = swm.swm_get_block(ctx, p, q, int(m[p]), int(m[q]))
+        zo = O.block(cloud, k, p, q)
+        scale = math.sqrt(dmax(p) * dmax(q)) if scaled else float(np.max(np.abs(zo)))
+        e = float(np.max(np.abs(zg - zo)) / scale)
+        if e > worst:
+            worst, where = e, (p, q)
+    return worst, where
 
 
 def assert_rcs_db(s_gpu, s_ref, db=0.1, floor_db=30.0):
