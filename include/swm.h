@@ -207,6 +207,33 @@ int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const do
                   int n_rhs, const double* currents, int n_obs, const double* obs,
                   double* sigma_out);
 
+/* Allocation-free twin of swm_far_field; the paper has no counterpart (it is a service to
+ * callers, not a step of the method).  Same arguments, same results (to rounding: the wire
+ * range may be cut into fewer chunks).
+ *
+ * Who needs it: callers that cannot allocate device memory at the moment they ask for the RCS --
+ * a process whose device memory is entirely reserved by another framework's memory pool, a
+ * latency-critical loop that cannot afford an allocation or the synchronisation an allocation
+ * may bring, or a host that forbids dynamic allocation after start-up.  This entry point makes
+ * no cudaMalloc/cudaFree (or any other allocating) call.  Instead its scratch (the per-chunk
+ * partial sums) is a fixed 8 MiB array compiled into the library; every GPU that loads the
+ * library holds those 8 MiB until the process exits.
+ *
+ * Limits and rules:
+ *   - n_rhs * n_obs <= 174762 (48 bytes of scratch per incidence-observation pair); larger
+ *     requests return SWM_EINVAL with the sizes in swm_stateless_error().
+ *   - The stream's device must be the current device.  The first call on each device looks up
+ *     the array's device address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.
+ *   - All calls share the one array, and it keeps the last call's contents.  Each call writes
+ *     every partial sum it later reads, so nothing has to start at zero; but calls that can
+ *     overlap on the GPU (other streams, other host threads) race on the array and must be
+ *     serialised by the caller. */
+int swm_far_field_noalloc(void* cuda_stream, int64_t nw, const double* centres, const double* dirs,
+                          const double* lengths, const int32_t* nseg, const int64_t* off, double k,
+                          int n_rhs, const double* currents, int n_obs, const double* obs,
+                          double* sigma_out);
+
 /* Message of the last failed stateless call on this host thread ("" if none). */
 const char* swm_stateless_error(void);
 

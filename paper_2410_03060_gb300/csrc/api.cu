@@ -121,6 +121,9 @@ int set_device(swm_ctx* ctx) {
 thread_local std::string g_stateless_err;
 
 }  // namespace
+
+void set_stateless_error(const std::string& msg) { g_stateless_err = msg; }
+
 }  // namespace swm
 
 using namespace swm;

@@ -178,6 +178,8 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
                      const int32_t* ns, const int64_t* off, bool soa, double k, int n_rhs, int n_obs,
                      const double* obs, int obs_stride, bool mono, double* sigma, void* scratch, size_t scratch_bytes,
                      std::string* err);
+// error text reported by swm_stateless_error() (api.cu)
+void set_stateless_error(const std::string& msg);
 // krylov.cu: a6
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
 

@@ -61,6 +61,8 @@ _SIGS = {
     "swm_get_block": (C.c_int, [_P, C.c_int64, C.c_int64, _P]),
     "swm_get_rhs": (C.c_int, [_P, _P]),
     "swm_far_field": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P, C.c_int, _P, _P]),
+    "swm_far_field_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P, C.c_int, _P,
+                                         _P]),
     "swm_stateless_error": (C.c_char_p, []),
 }
 EXPORTED = tuple(_SIGS)
@@ -268,7 +270,7 @@ def swm_get_rhs(ctx: Ctx) -> np.ndarray:
     return out
 
 
-def swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out) -> int:
+def swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out, _entry="swm_far_field") -> int:
     """Stateless far-field RCS; every array a CUDA torch tensor (see include/swm.h)."""
     nw = lengths.shape[0]
     n_rhs, n_obs = currents.shape[0], obs.shape[0]
@@ -281,7 +283,15 @@ def swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, s
     if stream is None:
         stream = _torch_stream_handle()
     lib = load()
-    rc = lib.swm_far_field(C.c_void_p(stream), nw, *args, float(k), n_rhs, pc, n_obs, po, ps)
+    rc = getattr(lib, _entry)(C.c_void_p(stream), nw, *args, float(k), n_rhs, pc, n_obs, po, ps)
     if rc < 0:
         raise SwmError(rc, lib.swm_stateless_error().decode())
     return rc
+
+
+def swm_far_field_noalloc(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out) -> int:
+    """Allocation-free far-field RCS for callers that cannot allocate device memory at call time;
+    same arguments and results as :func:`swm_far_field`, scratch from a fixed 8 MiB array in the
+    library (at most 174762 incidence-observation pairs per call; overlapping calls race)."""
+    return swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out,
+                         _entry="swm_far_field_noalloc")
