@@ -114,8 +114,9 @@ typedef struct swm_stats {
 #define SWM_K_INVERT 4      /* self-block inverses */
 #define SWM_K_FORM_E 5      /* Z_pq Z_qq^-1 */
 #define SWM_K_RHS 6         /* right-hand sides */
-#define SWM_K_APPLY 7       /* block-sparse product (GMRES step and residual) */
-#define SWM_K_DOTS 8        /* first Gram-Schmidt pass */
+#define SWM_K_APPLY 7       /* block-sparse product fused with the first Gram-Schmidt pass, and
+                               the residual product at each restart */
+#define SWM_K_DOTS 8        /* reserved (the first pass is part of SWM_K_APPLY) */
 #define SWM_K_UPDATE 9      /* second Gram-Schmidt pass */
 #define SWM_K_FINISH 10     /* norm, Hessenberg column, rotation */
 #define SWM_K_FAR 11        /* far field: partial sums and their reduction to RCS */

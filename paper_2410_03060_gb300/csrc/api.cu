@@ -11,7 +11,19 @@
 namespace swm {
 
 int dalloc(swm_ctx* ctx, std::vector<Buf>& group, void** out, size_t bytes) {
-  bytes = std::max<size_t>(bytes, 16);
+  bytes = std::max<size_t>((bytes + 255) / 256 * 256, 256);
+  // reuse the smallest released buffer that fits without wasting more than half of it
+  int best = -1;
+  for (int i = 0; i < (int)ctx->free_list.size(); ++i) {
+    const size_t b = ctx->free_list[i].bytes;
+    if (b >= bytes && b <= 2 * bytes + (size_t(1) << 20) && (best < 0 || b < ctx->free_list[best].bytes)) best = i;
+  }
+  if (best >= 0) {
+    group.push_back(ctx->free_list[best]);
+    ctx->free_list.erase(ctx->free_list.begin() + best);
+    *out = group.back().p;
+    return SWM_OK;
+  }
   void* p = nullptr;
   if (ctx->user_alloc) {
     p = ctx->user_alloc(bytes, (void*)ctx->stream, ctx->user_arg);
@@ -29,13 +41,21 @@ int dalloc(swm_ctx* ctx, std::vector<Buf>& group, void** out, size_t bytes) {
 }
 
 void dfree_group(swm_ctx* ctx, std::vector<Buf>& group) {
-  for (auto& b : group) {
+  for (auto& b : group) ctx->free_list.push_back(b);
+  group.clear();
+}
+
+static void release_all(swm_ctx* ctx) {
+  dfree_group(ctx, ctx->solve_bufs);
+  dfree_group(ctx, ctx->build_bufs);
+  dfree_group(ctx, ctx->cloud_bufs);
+  for (auto& b : ctx->free_list) {
     if (ctx->user_free)
       ctx->user_free(b.p, b.bytes, (void*)ctx->stream, ctx->user_arg);
     else
       cudaFreeAsync(b.p, ctx->stream);
   }
-  group.clear();
+  ctx->free_list.clear();
 }
 
 namespace {
@@ -86,26 +106,6 @@ void frames_host(const double* inc, int n, std::vector<double>& out) {
   }
 }
 
-struct Timer {
-  cudaEvent_t a = nullptr, b = nullptr;
-  cudaStream_t s;
-  explicit Timer(cudaStream_t st) : s(st) {
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, s);
-  }
-  double stop() {
-    float ms = 0.f;
-    cudaEventRecord(b, s);
-    cudaEventSynchronize(b);
-    cudaEventElapsedTime(&ms, a, b);
-    return ms;
-  }
-  ~Timer() {
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-  }
-};
 
 int copy_in(swm_ctx* ctx, void* dst, const void* src, size_t bytes, int kind) {
   SWM_CK(cudaMemcpyAsync(dst, src, bytes, kind == SWM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -160,9 +160,15 @@ void swm_destroy(swm_ctx* ctx) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
-  dfree_group(ctx, ctx->solve_bufs);
-  dfree_group(ctx, ctx->build_bufs);
-  dfree_group(ctx, ctx->cloud_bufs);
+  for (auto& e : ctx->ph_ev)
+    for (auto ev : e)
+      if (ev) cudaEventDestroy(ev);
+  for (auto ev : ctx->poll_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->pinned_state) cudaFreeHost(ctx->pinned_state);
+  if (ctx->gm_exec) cudaGraphExecDestroy(ctx->gm_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  release_all(ctx);
   cudaStreamSynchronize(ctx->stream);
   delete ctx;
 }
@@ -171,7 +177,7 @@ const char* swm_last_error(const swm_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int swm_set_allocator(swm_ctx* ctx, swm_alloc_fn alloc, swm_free_fn free_fn, void* user) {
   if (!ctx) return SWM_EINVAL;
-  if (!ctx->cloud_bufs.empty() || !ctx->build_bufs.empty() || !ctx->solve_bufs.empty())
+  if (!ctx->cloud_bufs.empty() || !ctx->build_bufs.empty() || !ctx->solve_bufs.empty() || !ctx->free_list.empty())
     return ctx->fail(SWM_ESTATE, "swm_set_allocator must precede swm_set_cloud");
   if ((alloc == nullptr) != (free_fn == nullptr)) return ctx->fail(SWM_EINVAL, "alloc and free must both be set");
   ctx->user_alloc = alloc;
@@ -251,22 +257,19 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->rc = r_c;
   ctx->dense = !(r_c > 0.0) || std::isinf(r_c);
   ctx->prec = precision;
-  {
-    Timer t(ctx->stream);
-    SWM_TRY(build_pattern(ctx));
-    ctx->stats.ms_neighbour = t.stop();
-  }
-  {
-    Timer t(ctx->stream);
-    SWM_TRY(fill_blocks(ctx));
-    ctx->stats.ms_fill = t.stop();
-  }
-  {
-    Timer t(ctx->stream);
-    SWM_TRY(build_precond(ctx));
-    ctx->stats.ms_precond = t.stop();
-  }
+  ctx->phase_begin(swm_ctx::PH_NEIGHBOUR);
+  SWM_TRY(build_pattern(ctx));
+  ctx->phase_end(swm_ctx::PH_NEIGHBOUR);
+  ctx->phase_begin(swm_ctx::PH_FILL);
+  SWM_TRY(fill_blocks(ctx));
+  ctx->phase_end(swm_ctx::PH_FILL);
+  ctx->phase_begin(swm_ctx::PH_PRECOND);
+  SWM_TRY(build_precond(ctx));
+  ctx->phase_end(swm_ctx::PH_PRECOND);
+  SWM_TRY(prepare_far_field(ctx));
+  SWM_TRY(finish_build(ctx));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
+  ctx->phase_collect();
   SWM_CK(cudaGetLastError());
   ctx->stats.n = ctx->N;
   ctx->stats.nb = ctx->nb;
@@ -305,17 +308,14 @@ int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restar
   frames_host(inc, n_inc, fh);
   SWM_CK(cudaMemcpyAsync(ctx->inc_dev, inc, sizeof(double) * 3 * n_inc, cudaMemcpyHostToDevice, ctx->stream));
   SWM_CK(cudaMemcpyAsync(frames, fh.data(), sizeof(double) * 6 * n_inc, cudaMemcpyHostToDevice, ctx->stream));
-  {
-    Timer t(ctx->stream);
-    SWM_TRY(compute_rhs(ctx, n_inc, frames));
-    ctx->stats.ms_rhs = t.stop();
-  }
-  int rc;
-  {
-    Timer t(ctx->stream);
-    rc = gmres_solve(ctx, tol, restart, max_iter);
-    ctx->stats.ms_solve = t.stop();
-  }
+  ctx->phase_begin(swm_ctx::PH_RHS);
+  SWM_TRY(compute_rhs(ctx, n_inc, frames));
+  ctx->phase_end(swm_ctx::PH_RHS);
+  ctx->phase_begin(swm_ctx::PH_SOLVE);
+  int rc = gmres_solve(ctx, tol, restart, max_iter);
+  ctx->phase_end(swm_ctx::PH_SOLVE);
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  ctx->phase_collect();
   ctx->prof_flush();
   if (rc < 0) return rc;
   ctx->stats.n_rhs = n_inc;
@@ -355,7 +355,7 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
       if (!std::isfinite(obs[i])) return ctx->fail(SWM_EINVAL, "non-finite observation angle");
   }
   SWM_TRY(set_device(ctx));
-  Timer t(ctx->stream);
+  ctx->phase_begin(swm_ctx::PH_RCS);
   const int R = ctx->n_rhs;
   const int64_t npairs = mono ? R : (int64_t)R * n_obs;
   std::vector<Buf> tmp;
@@ -376,17 +376,23 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
     SWM_TRY(dalloc(ctx, tmp, (void**)&sig, sizeof(double) * 2 * npairs));
   std::string err;
   ctx->prof_begin(SWM_K_FAR);
-  int rc = far_field_launch(ctx->stream, &ctx->launches, ctx->prec == SWM_C64, ctx->prec == SWM_C128, ctx->Xv, ctx->nw,
-                            ctx->N, nullptr, nullptr, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L,
-                            ctx->ns, ctx->off, true, ctx->k, R, mono ? R : n_obs, obs_dev, stride, mono, sig, scratch,
-                            sb, &err);
+  int rc;
+  if (ctx->prec == SWM_C64) {
+    rc = far_field_f32_launch(ctx, mono ? R : n_obs, obs_dev, stride, mono, sig, scratch, sb);
+  } else {
+    rc = far_field_launch(ctx->stream, &ctx->launches, false, true, ctx->Xv, ctx->nw, ctx->N, nullptr, nullptr, ctx->cx,
+                          ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns, ctx->off, true, ctx->k, R,
+                          mono ? R : n_obs, obs_dev, stride, mono, sig, scratch, sb, &err);
+    if (rc < 0) ctx->fail(rc, err);
+  }
   ctx->prof_end(SWM_K_FAR);
-  if (rc < 0) return ctx->fail(rc, err);
+  if (rc < 0) return rc;
   if (out_kind == SWM_HOST)
     SWM_CK(cudaMemcpyAsync(sigma_out, sig, sizeof(double) * 2 * npairs, cudaMemcpyDeviceToHost, ctx->stream));
+  ctx->phase_end(swm_ctx::PH_RCS);
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   dfree_group(ctx, tmp);
-  ctx->stats.ms_rcs = t.stop();
+  ctx->phase_collect();
   ctx->prof_flush();
   return SWM_OK;
 }

@@ -50,7 +50,37 @@ struct swm_ctx {
   swm_free_fn user_free = nullptr;
   void* user_arg = nullptr;
   std::vector<swm::Buf> cloud_bufs, build_bufs, solve_bufs;
+  // buffers released by a group wait here for reuse by later allocations on the same stream
+  // (stream order makes the reuse safe); they are returned to the allocator by swm_destroy
+  std::vector<swm::Buf> free_list;
   int64_t launches = 0;
+
+  // phase timing with CUDA events, read after the call's final synchronisation
+  enum { PH_NEIGHBOUR, PH_FILL, PH_PRECOND, PH_RHS, PH_SOLVE, PH_RCS, PH_N };
+  cudaEvent_t ph_ev[PH_N][2] = {};
+  bool ph_rec[PH_N] = {};
+  void phase_begin(int i) {
+    if (!ph_ev[i][0]) {
+      cudaEventCreate(&ph_ev[i][0]);
+      cudaEventCreate(&ph_ev[i][1]);
+    }
+    cudaEventRecord(ph_ev[i][0], stream);
+  }
+  void phase_end(int i) {
+    cudaEventRecord(ph_ev[i][1], stream);
+    ph_rec[i] = true;
+  }
+  void phase_collect() {
+    double* dst[PH_N] = {&stats.ms_neighbour, &stats.ms_fill, &stats.ms_precond, &stats.ms_rhs, &stats.ms_solve,
+                         &stats.ms_rcs};
+    for (int i = 0; i < PH_N; ++i) {
+      if (!ph_rec[i]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ph_ev[i][0], ph_ev[i][1]) == cudaSuccess) *dst[i] = ms;
+      ph_rec[i] = false;
+    }
+    cudaGetLastError();
+  }
 
   // cloud, caller order, device
   int64_t nw = 0;
@@ -81,6 +111,15 @@ struct swm_ctx {
   int64_t* ublk = nullptr;     // [nup] blocks (p, q) with q > p
   int64_t* minv_off = nullptr; // [nw + 1] offsets of the m_p x m_p inverse blocks
   int32_t* rowwire = nullptr;  // [N] internal wire of each scalar row
+  int64_t nminv = 0;           // entries of the packed self-block inverses
+  unsigned long long* d_evals = nullptr;  // fill evaluation counter (device)
+  int* d_sing = nullptr;                  // singular self block flag (device)
+  void* pinned_state = nullptr;           // two pinned slots for the Krylov state poll
+  void* ffw = nullptr;                    // per-wire float32 far-field data (complex64 path)
+  cudaGraphExec_t gm_exec = nullptr;      // captured chunk of GMRES steps and its argument key
+  std::vector<unsigned char> gm_key;
+  cudaStream_t cap_stream = nullptr;      // private stream for graph capture
+  cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   swm::Layout full, offd;
   void* Z = nullptr;     // values of Z in layout `full`
   void* Zp = nullptr;    // values of Z * blockdiag(Z)^-1 without its identity diagonal, layout `offd`
@@ -162,6 +201,10 @@ void dfree_group(swm_ctx* ctx, std::vector<Buf>& group);
 
 // neighbour.cu: a0 + a1 (sort by cell, numbering, S-NFC pattern, layouts)
 int build_pattern(swm_ctx* ctx);
+// copy n device int64 values to the host with one synchronisation
+int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst);
+// precond.cu: read the build's deferred device flags and counters
+int finish_build(swm_ctx* ctx);
 // scan.cu
 int exclusive_scan_i64(swm_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);
 int exclusive_scan_i32_to_i64(swm_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host);
@@ -172,6 +215,9 @@ int build_precond(swm_ctx* ctx);
 // rhs_ff.cu: a4 + a7
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* inc_dev);
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs);
+int prepare_far_field(swm_ctx* ctx);
+int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_stride, bool mono, double* sigma,
+                         void* scratch, size_t scratch_bytes);
 int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64, const void* cur, int64_t nw,
                      int64_t N, const double* c3, const double* t3, const double* cx, const double* cy,
                      const double* cz, const double* tx, const double* ty, const double* tz, const double* Ls,

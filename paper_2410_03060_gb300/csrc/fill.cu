@@ -78,51 +78,56 @@ __device__ __constant__ double c_self_poly[2][4][4] = {
 };
 
 // Antiderivatives of t^n / sqrt(t^2 + al^2), n = 0..3, at t.
-__device__ __forceinline__ void static_prims(double t, double al, double out[4]) {
-  const double r = sqrt(t * t + al * al);
-  const double as = asinh(t / al);
+template <typename R>
+__device__ __forceinline__ void static_prims(R t, R al, R out[4]) {
+  const R r = sqrt(t * t + al * al);
+  const R as = asinh(t / al);
   out[0] = as;
   out[1] = r;
-  out[2] = 0.5 * (t * r - al * al * as);
-  out[3] = (t * t - 2.0 * al * al) * r / 3.0;
+  out[2] = R(0.5) * (t * r - al * al * as);
+  out[3] = (t * t - R(2) * al * al) * r / R(3);
 }
 
-// I[ab] for segment offset d >= 0 of a wire with segment length D and radius a (times 4 pi).
-__device__ void self_offset(int d, double D, double a, double k, const GLTable& gl, c128 out[4]) {
-  for (int ab = 0; ab < 4; ++ab) out[ab] = mkc(0.0, 0.0);
-  const double al = a / D;
+// I[ab] for segment offset d >= 0 of a wire with segment length D and radius a (without 1/(4 pi)),
+// in precision R.  xg, wg: 8-point Gauss-Legendre rule on [0, 1].
+template <typename R>
+__device__ void self_offset(int d, R D, R a, R k, const R* xg, const R* wg, cplx<R> out[4]) {
+  for (int ab = 0; ab < 4; ++ab) out[ab] = mkc<R>(0, 0);
+  const R al = a / D;
   for (int half = 0; half < 2; ++half) {
-    const double w0 = half ? 0.0 : -1.0;
+    const R w0 = half ? R(0) : R(-1);
     for (int g = 0; g < 8; ++g) {
-      const double w = w0 + gl.x8[g];
-      const double t = d + w;
-      const double R = sqrt(D * D * t * t + a * a);
-      double s, c;
-      sincos(k * R, &s, &c);
+      const R w = w0 + xg[g];
+      const R t = R(d) + w;
+      const R Rr = sqrt(D * D * t * t + a * a);
+      // half-angle form keeps cos(kR) - 1 accurate when kR is small
+      R sh, ch;
+      sincos(R(0.5) * k * Rr, &sh, &ch);
+      const R cm1 = R(-2) * sh * sh, sn = R(2) * sh * ch;
       // full kernel exp(-jkR)/R, or the smooth remainder (exp(-jkR) - 1)/R for |d| <= 1
-      const double re = (d <= 1 ? (c - 1.0) : c) / R, im = -s / R;
-      const double ww = gl.w8[g];
+      const R re = (d <= 1 ? cm1 : R(1) + cm1) / Rr, im = -sn / Rr;
+      const R ww = wg[g];
       for (int ab = 0; ab < 4; ++ab) {
         const double* P = c_self_poly[half][ab];
-        const double W = ((P[3] * w + P[2]) * w + P[1]) * w + P[0];
+        const R W = ((R(P[3]) * w + R(P[2])) * w + R(P[1])) * w + R(P[0]);
         out[ab].re += ww * W * re;
         out[ab].im += ww * W * im;
       }
     }
     if (d <= 1) {
       // static part: int W(t - d) / (D sqrt(t^2 + al^2)) dt over t in [w0 + d, w0 + 1 + d]
-      double A0[4], A1[4];
-      static_prims(w0 + d, al, A0);
-      static_prims(w0 + 1.0 + d, al, A1);
+      R A0[4], A1[4];
+      static_prims<R>(w0 + R(d), al, A0);
+      static_prims<R>(w0 + R(1) + R(d), al, A1);
       for (int ab = 0; ab < 4; ++ab) {
         const double* P = c_self_poly[half][ab];
         // coefficients of W(t - d) in powers of t
-        const double dd = (double)d;
-        const double q0 = P[0] - P[1] * dd + P[2] * dd * dd - P[3] * dd * dd * dd;
-        const double q1 = P[1] - 2.0 * P[2] * dd + 3.0 * P[3] * dd * dd;
-        const double q2 = P[2] - 3.0 * P[3] * dd;
-        const double q3 = P[3];
-        const double st = q0 * (A1[0] - A0[0]) + q1 * (A1[1] - A0[1]) + q2 * (A1[2] - A0[2]) + q3 * (A1[3] - A0[3]);
+        const R dd = (R)d;
+        const R q0 = R(P[0]) - R(P[1]) * dd + R(P[2]) * dd * dd - R(P[3]) * dd * dd * dd;
+        const R q1 = R(P[1]) - R(2) * R(P[2]) * dd + R(3) * R(P[3]) * dd * dd;
+        const R q2 = R(P[2]) - R(3) * R(P[3]) * dd;
+        const R q3 = R(P[3]);
+        const R st = q0 * (A1[0] - A0[0]) + q1 * (A1[1] - A0[1]) + q2 * (A1[2] - A0[2]) + q3 * (A1[3] - A0[3]);
         out[ab].re += st / D;
       }
     }
@@ -130,42 +135,69 @@ __device__ void self_offset(int d, double D, double a, double k, const GLTable& 
   for (int ab = 0; ab < 4; ++ab) out[ab] = (D * D) * out[ab];
 }
 
-template <typename TV>
-__global__ void __launch_bounds__(128) k_self_blocks(int64_t nw, const double* __restrict__ Ls, const double* __restrict__ as,
-                                                    const int32_t* __restrict__ ns, double k, GLTable gl,
-                                                    const int64_t* __restrict__ diag_b, Layout lay,
-                                                    cplx<TV>* __restrict__ Z) {
-  __shared__ c128 sI[4][kMaxSeg][4];  // per warp: offset d >= 0, ab
-  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t p = (int64_t)blockIdx.x * 4 + wl;
-  if (p >= nw) return;
-  const int n = ns[p];
-  const double D = Ls[p] / n, a = as[p];
-  if (lane < n) {
-    c128 I[4];
-    self_offset(lane, D, a, k, gl, I);
-    for (int ab = 0; ab < 4; ++ab) sI[wl][lane][ab] = I[ab];
+constexpr int kSelfThreads = 128;
+
+// One thread per (wire, segment offset d >= 0): S slots per wire (S a power of two >= max n_s),
+// kSelfThreads / S wires per CTA; then the CTA writes the Toeplitz blocks of its wires.
+template <typename R, typename TV>
+__global__ void __launch_bounds__(kSelfThreads) k_self_blocks(int64_t nw, const double* __restrict__ Ls,
+                                                             const double* __restrict__ as,
+                                                             const int32_t* __restrict__ ns, double k, GLTable gl,
+                                                             const int64_t* __restrict__ diag_b, Layout lay, int S,
+                                                             cplx<TV>* __restrict__ Z) {
+  __shared__ cplx<R> sI[kSelfThreads][4];
+  __shared__ int obase[kSelfThreads + 1];
+  __shared__ R xg[8], wg[8];
+  const int wpc = kSelfThreads / S;
+  const int64_t p0 = (int64_t)blockIdx.x * wpc;
+  const int tid = threadIdx.x;
+  if (tid < 8) {
+    xg[tid] = (R)gl.x8[tid];
+    wg[tid] = (R)gl.w8[tid];
   }
-  __syncwarp();
-  const int m = n - 1;
-  const int K = lay.K[p];
-  const int64_t base = lay.rowbase[p] + lay.colpos[diag_b[p]];
-  const double sc = 1.0 / (k * k * D * D);
-  // I_ab at offset e (any sign): I_ab(-e) = I_ba(e)
-  auto get = [&](int e, int ab) -> c128 {
-    if (e >= 0) return sI[wl][e][ab];
-    const int ba = (ab == 1) ? 2 : (ab == 2 ? 1 : ab);
-    return sI[wl][-e][ba];
-  };
-  auto IG = [&](int e) -> c128 { return get(e, 0) + get(e, 1) + get(e, 2) + get(e, 3); };
-  for (int it = lane; it < m * m; it += 32) {
-    const int i = it / m, j = it % m;
+  __syncthreads();
+  {
+    const int lw = tid / S, d = tid % S;
+    const int64_t p = p0 + lw;
+    if (p < nw && d < ns[p]) {
+      cplx<R> I[4];
+      self_offset<R>(d, (R)(Ls[p] / ns[p]), (R)as[p], (R)k, xg, wg, I);
+      for (int ab = 0; ab < 4; ++ab) sI[tid][ab] = I[ab];
+    }
+  }
+  if (tid == 0) {
+    int acc = 0;
+    for (int w = 0; w < wpc; ++w) {
+      obase[w] = acc;
+      if (p0 + w < nw) acc += (ns[p0 + w] - 1) * (ns[p0 + w] - 1);
+    }
+    obase[wpc] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < obase[wpc]; e += kSelfThreads) {
+    int w = 0;
+    while (obase[w + 1] <= e) ++w;
+    const int64_t p = p0 + w;
+    const int n = ns[p], m = n - 1;
+    const int local = e - obase[w];
+    const int i = local / m, j = local % m;
     const int d = i - j;
+    const cplx<R>* T = &sI[w * S][0];
+    // I_ab at offset x (any sign): I_ab(-x) = I_ba(x)
+    auto get = [&](int x, int ab) -> cplx<R> {
+      if (x >= 0) return T[4 * x + ab];
+      const int ba = (ab == 1) ? 2 : (ab == 2 ? 1 : ab);
+      return T[4 * (-x) + ba];
+    };
+    auto IG = [&](int x) -> cplx<R> { return get(x, 0) + get(x, 1) + get(x, 2) + get(x, 3); };
     // rise(i) x rise(j): offset d; rise x fall(j+1): d - 1; fall(i+1) x rise: d + 1; fall x fall: d
-    c128 vec = get(d, 0) + get(d - 1, 1) + get(d + 1, 2) + get(d, 3);
-    c128 sca = IG(d) - IG(d - 1) - IG(d + 1) + IG(d);
-    c128 z = mkc((vec.re - sc * sca.re) / kFourPi, (vec.im - sc * sca.im) / kFourPi);
-    Z[base + (int64_t)i * K + j] = ccast<TV>(z);
+    const cplx<R> vec = get(d, 0) + get(d - 1, 1) + get(d + 1, 2) + get(d, 3);
+    const cplx<R> sca = IG(d) - IG(d - 1) - IG(d + 1) + IG(d);
+    const R D = (R)(Ls[p] / n);
+    const R sc = R(1) / ((R)k * (R)k * D * D);
+    const R f = R(1.0 / kFourPi);
+    const cplx<R> z = mkc<R>(f * (vec.re - sc * sca.re), f * (vec.im - sc * sca.im));
+    Z[lay.rowbase[p] + lay.colpos[diag_b[p]] + (int64_t)i * lay.K[p] + j] = ccast<TV>(z);
   }
 }
 
@@ -510,29 +542,24 @@ int fill_blocks(swm_ctx* ctx) {
   const int64_t nw = ctx->nw;
   const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Z, esz * std::max<int64_t>(1, ctx->full.nval)));
-  std::vector<Buf> tmp;
-  unsigned long long* evals = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&evals, sizeof(unsigned long long)));
-  SWM_CK(cudaMemsetAsync(evals, 0, sizeof(unsigned long long), ctx->stream));
-  const unsigned grid_self = (unsigned)ceil_div(nw, 4);
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->d_evals, sizeof(unsigned long long)));
+  SWM_CK(cudaMemsetAsync(ctx->d_evals, 0, sizeof(unsigned long long), ctx->stream));
+  int S = 2;
+  while (S < ctx->max_ns) S <<= 1;
+  const unsigned grid_self = (unsigned)ceil_div(nw, kSelfThreads / S);
   ctx->prof_begin(SWM_K_FILL_SELF);
   if (ctx->prec == SWM_C128)
-    k_self_blocks<double><<<grid_self, 128, 0, ctx->stream>>>(nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b,
-                                                               ctx->full, reinterpret_cast<c128*>(ctx->Z));
+    k_self_blocks<double, double><<<grid_self, kSelfThreads, 0, ctx->stream>>>(
+        nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b, ctx->full, S, reinterpret_cast<c128*>(ctx->Z));
   else
-    k_self_blocks<float><<<grid_self, 128, 0, ctx->stream>>>(nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b,
-                                                              ctx->full, reinterpret_cast<c64*>(ctx->Z));
+    k_self_blocks<float, float><<<grid_self, kSelfThreads, 0, ctx->stream>>>(
+        nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b, ctx->full, S, reinterpret_cast<c64*>(ctx->Z));
   ctx->prof_end(SWM_K_FILL_SELF);
   SWM_LAUNCHED();
   if (ctx->prec == SWM_C128)
-    SWM_TRY((launch_fill<double, double>(ctx, gl, evals)));
+    SWM_TRY((launch_fill<double, double>(ctx, gl, ctx->d_evals)));
   else
-    SWM_TRY((launch_fill<float, float>(ctx, gl, evals)));
-  unsigned long long he = 0;
-  SWM_CK(cudaMemcpyAsync(&he, evals, sizeof(he), cudaMemcpyDeviceToHost, ctx->stream));
-  SWM_CK(cudaStreamSynchronize(ctx->stream));
-  dfree_group(ctx, tmp);
-  ctx->stats.fill_evals = (int64_t)he;
+    SWM_TRY((launch_fill<float, float>(ctx, gl, ctx->d_evals)));
   return SWM_OK;
 }
 

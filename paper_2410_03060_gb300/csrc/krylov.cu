@@ -4,17 +4,19 @@
 //
 // The operator is A = Z M^-1 = I + E (E stored, see precond.cu); GMRES finds y with A y = b and
 // the currents are x = M^-1 y.  Several right-hand sides (incidences) run as independent GMRES
-// instances that share every pass over E.  One Arnoldi step is four kernels:
-//   k_apply  : v_j = w / |w| (row owners) and w' = A v_j
-//   k_dots   : h = V^H w'                        (classical Gram-Schmidt, first pass)
-//   k_update : w' -= V h, h2 = V^H w'            (second pass)
+// instances that share every pass over E.  One Arnoldi step is three kernels, each over chunks of
+// rows:
+//   k_step   : v_j = w / |w| (row owners), w' = A v_j, h = V^H w'  (classical Gram-Schmidt, pass 1)
+//   k_update : w' -= V h, h2 = V^H w'                              (pass 2)
 //   k_finish : w' -= V h2, |w'|, Hessenberg column, Givens rotation, residual estimate
 // Reductions end in the last CTA to arrive (no spin-waits).  Every kernel reads the step index
-// and the activity flags from device memory, so the host issues identical launches every step
-// and checks convergence once per restart cycle.  Vectors are stored right-hand-side major:
+// and the activity flags from device memory, so the host issues identical launches every step;
+// it keeps one chunk of steps queued ahead of the convergence flag it is reading, so the GPU
+// does not wait for the host inside a restart cycle.  Vectors are stored right-hand-side major:
 // V[j][r][n].  Dot products, norms, the Hessenberg matrix and the rotations are float64.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
 #include "ctx.h"
@@ -152,17 +154,51 @@ __device__ void reduce_dots(const KPtr& P, int j, int r, c128* __restrict__ dst)
   if (threadIdx.x == 0) P.counter[r] = 0;
 }
 
+// Normalise, multiply by A = I + E and take the first Gram-Schmidt dots, over one chunk of rows.
+// Eight lanes share a scalar row; the 32 row groups of the CTA sweep the chunk.
 template <typename TV>
-__global__ void __launch_bounds__(kRows) k_dots(KPtr P, cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
-                                                const cplx<TV>* __restrict__ V) {
+__global__ void __launch_bounds__(kRows) k_step(KPtr P, const int32_t* __restrict__ rowwire,
+                                                const int64_t* __restrict__ off, Layout lay,
+                                                const cplx<TV>* __restrict__ E, cplx<TV>* __restrict__ W0,
+                                                cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ V) {
   if (P.st->cycle_done) return;
   const int j = P.st->j, r = blockIdx.y;
+  const int64_t N = P.N;
   const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
-  const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
-  const cplx<TV>* w = ((j & 1) ? W0 : W1) + (int64_t)r * P.N + n0;
+  const int cnt = (int)min((int64_t)P.chunk, N - n0);
+  const cplx<TV>* src = ((j & 1) ? W1 : W0) + (int64_t)r * N;
+  cplx<TV>* dst = ((j & 1) ? W0 : W1) + (int64_t)r * N;
+  const bool act = P.active[r];
+  const TV s = (TV)P.inv_h[r];
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
-  for (int t = threadIdx.x; t < cnt; t += kRows) w_sm[t] = w[t];
+  const int g = threadIdx.x / kG, sub = threadIdx.x % kG;
+  for (int rb = 0; rb < cnt; rb += kRows / kG) {
+    const int row = rb + g;
+    const bool valid = row < cnt;
+    const int64_t n = n0 + row;
+    cplx<TV> acc = mkc<TV>(0, 0);
+    if (valid && act) {
+      const int64_t p = rowwire[n];
+      const int i = (int)(n - off[p]);
+      const int K = lay.K[p];
+      const int64_t vb = lay.rowbase[p] + (int64_t)i * K;
+      const int32_t* cm = lay.colmap + lay.cmbase[p];
+      for (int c = sub; c < K; c += kG) cfma(acc, E[vb + c], src[cm[c]]);
+    }
+#pragma unroll
+    for (int o = kG / 2; o > 0; o >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (valid && sub == 0) {
+      const cplx<TV> x = act ? s * src[n] : mkc<TV>(0, 0);
+      const cplx<TV> y = act ? x + s * acc : mkc<TV>(0, 0);
+      V[((int64_t)j * P.R + r) * N + n] = x;
+      dst[n] = y;
+      w_sm[row] = y;
+    }
+  }
   __syncthreads();
   cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nchunk + blockIdx.x) * (P.restart + 1));
   if (last_cta(P, r)) reduce_dots(P, j, r, P.hc);
@@ -465,13 +501,81 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   const dim3 g_chunk((unsigned)P.nchunk, R);
   const size_t sm = sizeof(cplx<TV>) * P.chunk;
   if (sm > 48 * 1024) {
-    SWM_CK(cudaFuncSetAttribute(k_dots<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SWM_CK(cudaFuncSetAttribute(k_step<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SWM_CK(cudaFuncSetAttribute(k_update<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SWM_CK(cudaFuncSetAttribute(k_finish<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   }
   KState hs{};
   int cycles = 0;
   bool first = true;
+  if (!ctx->pinned_state) {
+    SWM_CK(cudaMallocHost(&ctx->pinned_state, 2 * sizeof(KState)));
+    SWM_CK(cudaEventCreateWithFlags(&ctx->poll_ev[0], cudaEventDisableTiming));
+    SWM_CK(cudaEventCreateWithFlags(&ctx->poll_ev[1], cudaEventDisableTiming));
+  }
+  KState* slot = reinterpret_cast<KState*>(ctx->pinned_state);
+  constexpr int kChunkSteps = 4;
+  auto launch_steps = [&](cudaStream_t s, int n) -> int {
+    for (int i = 0; i < n; ++i) {
+      ctx->prof_begin(SWM_K_APPLY);
+      k_step<TV><<<g_chunk, kRows, sm, s>>>(P, ctx->rowwire, ctx->off, ctx->offd, E, W0, W1, V);
+      ctx->prof_end(SWM_K_APPLY);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_UPDATE);
+      k_update<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
+      ctx->prof_end(SWM_K_UPDATE);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_FINISH);
+      k_finish<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
+      ctx->prof_end(SWM_K_FINISH);
+      SWM_LAUNCHED();
+    }
+    return SWM_OK;
+  };
+  // A chunk of Arnoldi steps is a CUDA graph (the launches are identical every step), captured on
+  // a private stream and reused while the kernel arguments stay the same.  Profiling a GMRES kernel
+  // class uses direct launches so its events time each launch.
+  const bool use_graph = ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_UPDATE &&
+                         ctx->prof_cls != SWM_K_FINISH;
+  if (use_graph) {
+    struct Key {
+      KPtr P;
+      const void* ptr[6];
+      Layout lay;
+      size_t sm;
+      unsigned gx, gy, bits;
+    } key;
+    std::memset(&key, 0, sizeof(key));
+    key.P = P;
+    const void* ptrs[6] = {ctx->rowwire, ctx->off, E, W0, W1, V};
+    for (int i = 0; i < 6; ++i) key.ptr[i] = ptrs[i];
+    key.lay = ctx->offd;
+    key.sm = sm;
+    key.gx = g_chunk.x;
+    key.gy = g_chunk.y;
+    key.bits = sizeof(TV);
+    const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
+    std::vector<unsigned char> kv(kb, kb + sizeof(key));
+    if (!ctx->gm_exec || kv != ctx->gm_key) {
+      if (!ctx->cap_stream) SWM_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+      const int64_t launches0 = ctx->launches;
+      SWM_CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = launch_steps(ctx->cap_stream, kChunkSteps);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+      ctx->launches = launches0;
+      if (rc < 0) return rc;
+      SWM_CK(ce);
+      if (ctx->gm_exec) {
+        cudaGraphExecDestroy(ctx->gm_exec);
+        ctx->gm_exec = nullptr;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&ctx->gm_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SWM_CK(ie);
+      ctx->gm_key = kv;
+    }
+  }
   while (true) {
     // residual of the current y and the start of a cycle
     ctx->prof_begin(SWM_K_APPLY);
@@ -485,28 +589,21 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     SWM_CK(cudaStreamSynchronize(st));
     if (hs.all_conv || hs.numeric || hs.iters >= max_iter) break;
     const int steps = std::min(restart, max_iter - hs.iters);
-    for (int s = 0; s < steps; ++s) {
-      ctx->prof_begin(SWM_K_APPLY);
-      k_apply<TV><<<g_rows, kRows, 0, st>>>(0, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
-      ctx->prof_end(SWM_K_APPLY);
-      SWM_LAUNCHED();
-      ctx->prof_begin(SWM_K_DOTS);
-      k_dots<TV><<<g_chunk, kRows, sm, st>>>(P, W0, W1, V);
-      ctx->prof_end(SWM_K_DOTS);
-      SWM_LAUNCHED();
-      ctx->prof_begin(SWM_K_UPDATE);
-      k_update<TV><<<g_chunk, kRows, sm, st>>>(P, W0, W1, V);
-      ctx->prof_end(SWM_K_UPDATE);
-      SWM_LAUNCHED();
-      ctx->prof_begin(SWM_K_FINISH);
-      k_finish<TV><<<g_chunk, kRows, sm, st>>>(P, W0, W1, V);
-      ctx->prof_end(SWM_K_FINISH);
-      SWM_LAUNCHED();
-      // poll every 8 steps so a converged cycle does not queue many empty steps
-      if ((s & 7) == 7 && s + 1 < steps) {
-        SWM_CK(cudaMemcpyAsync(&hs, P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
-        SWM_CK(cudaStreamSynchronize(st));
-        if (hs.cycle_done) break;
+    // chunks of steps; the host reads the flag of chunk c - 1 while chunk c is queued
+    int c = 0;
+    for (int s0 = 0; s0 < steps; s0 += kChunkSteps, ++c) {
+      const int n = std::min(steps - s0, kChunkSteps);
+      if (use_graph && n == kChunkSteps) {
+        SWM_CK(cudaGraphLaunch(ctx->gm_exec, st));
+        ctx->launches += 3 * kChunkSteps;
+      } else {
+        SWM_TRY(launch_steps(st, n));
+      }
+      SWM_CK(cudaMemcpyAsync(&slot[c & 1], P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
+      SWM_CK(cudaEventRecord(ctx->poll_ev[c & 1], st));
+      if (c >= 1) {
+        SWM_CK(cudaEventSynchronize(ctx->poll_ev[(c - 1) & 1]));
+        if (slot[(c - 1) & 1].cycle_done) break;
       }
     }
     k_backsolve<<<(unsigned)ceil_div(R, 64), 64, 0, st>>>(P);
@@ -514,8 +611,6 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     k_update_y<TV><<<dim3((unsigned)ceil_div(N, 256), R), 256, 0, st>>>(P, V, Y);
     SWM_LAUNCHED();
     ++cycles;
-    // the step counter restarts with the next cycle
-    SWM_CK(cudaMemsetAsync(&P.st->cycle_done, 0, sizeof(int), st));
   }
   // x = M^-1 y
   k_apply_minv<TV><<<dim3((unsigned)ceil_div(N, 256), R), 256, 0, st>>>(N, R, ctx->rowwire, ctx->off, ctx->m,

@@ -194,7 +194,8 @@ __device__ __forceinline__ int64_t find_in_row(const int32_t* __restrict__ col, 
 __global__ void k_row_meta(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                            const int32_t* __restrict__ m, int64_t* __restrict__ diag_b, int64_t* __restrict__ ucnt,
                            int32_t* __restrict__ colpos_f, int32_t* __restrict__ K_f, int32_t* __restrict__ colpos_o,
-                           int32_t* __restrict__ K_o, int64_t* __restrict__ ent_f, int64_t* __restrict__ ent_o) {
+                           int32_t* __restrict__ K_o, int64_t* __restrict__ ent_f, int64_t* __restrict__ ent_o,
+                           int64_t* __restrict__ msq) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= nw) return;
   const int64_t b0 = row_ptr[p], b1 = row_ptr[p + 1];
@@ -217,6 +218,7 @@ __global__ void k_row_meta(int64_t nw, const int64_t* __restrict__ row_ptr, cons
   K_o[p] = ko;
   ent_f[p] = (int64_t)m[p] * kf;
   ent_o[p] = (int64_t)m[p] * ko;
+  msq[p] = (int64_t)m[p] * m[p];
 }
 
 __global__ void k_transpose_and_upper(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -248,22 +250,31 @@ __global__ void k_colmap(int64_t nw, const int64_t* __restrict__ row_ptr, const 
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, ceil_div(n, t)); }
 
-int build_layout(swm_ctx* ctx, Layout& lay, int32_t* K, int32_t* colpos, int64_t* ent, const int32_t* m) {
-  const int64_t nw = ctx->nw;
+int alloc_layout(swm_ctx* ctx, Layout& lay, int32_t* K, int32_t* colpos) {
   lay.K = K;
   lay.colpos = colpos;
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.rowbase, sizeof(int64_t) * (nw + 1)));
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.cmbase, sizeof(int64_t) * (nw + 1)));
-  SWM_TRY(exclusive_scan_i64(ctx, ent, lay.rowbase, nw, &lay.nval));
-  SWM_TRY(exclusive_scan_i32_to_i64(ctx, K, lay.cmbase, nw, &lay.ncm));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.rowbase, sizeof(int64_t) * (ctx->nw + 1)));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.cmbase, sizeof(int64_t) * (ctx->nw + 1)));
+  return SWM_OK;
+}
+
+int fill_colmap(swm_ctx* ctx, Layout& lay, const int32_t* m) {
+  const int64_t nw = ctx->nw;
   SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.colmap, sizeof(int32_t) * std::max<int64_t>(1, lay.ncm)));
-  k_colmap<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, colpos, lay.cmbase,
+  k_colmap<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, lay.colpos, lay.cmbase,
                                                      lay.colmap);
   SWM_LAUNCHED();
   return SWM_OK;
 }
 
 }  // namespace
+
+int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst) {
+  for (int i = 0; i < n; ++i)
+    SWM_CK(cudaMemcpyAsync(dst + i, src[i], sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  return SWM_OK;
+}
 
 int build_pattern(swm_ctx* ctx) {
   const int64_t nw = ctx->nw;
@@ -344,7 +355,7 @@ int build_pattern(swm_ctx* ctx) {
                                                    ctx->tz, ctx->L, ctx->a, ctx->ns, m);
   SWM_LAUNCHED();
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->off, sizeof(int64_t) * (nw + 1)));
-  SWM_TRY(exclusive_scan_i32_to_i64(ctx, m, ctx->off, nw, &ctx->N));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, m, ctx->off, nw, nullptr));
   k_user_m<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->u_ns, um);
   SWM_LAUNCHED();
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->uoff_user, sizeof(int64_t) * (nw + 1)));
@@ -363,7 +374,14 @@ int build_pattern(swm_ctx* ctx) {
                                               ctx->dense ? 1 : 0, 0, rcnt, nullptr, nullptr);
   ctx->prof_end(SWM_K_PAIRS);
   SWM_LAUNCHED();
-  SWM_TRY(exclusive_scan_i32_to_i64(ctx, rcnt, ctx->row_ptr, nw, &ctx->nb));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, rcnt, ctx->row_ptr, nw, nullptr));
+  {
+    const int64_t* src[2] = {ctx->off + nw, ctx->row_ptr + nw};
+    int64_t v[2];
+    SWM_TRY(read_i64(ctx, 2, src, v));
+    ctx->N = v[0];
+    ctx->nb = v[1];
+  }
   if (ctx->nb > INT32_MAX / 2) return ctx->fail(SWM_EINVAL, "too many kept blocks for 32-bit positions");
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->col, sizeof(int32_t) * ctx->nb));
   ctx->prof_begin(SWM_K_PAIRS);
@@ -373,31 +391,51 @@ int build_pattern(swm_ctx* ctx) {
   SWM_LAUNCHED();
 
   // --- per-row metadata, transpose map, upper-triangle block list, layouts
-  int64_t *ucnt = nullptr, *ubase = nullptr, *ent_f = nullptr, *ent_o = nullptr;
+  int64_t *ucnt = nullptr, *ubase = nullptr, *ent_f = nullptr, *ent_o = nullptr, *msq = nullptr;
   int32_t *Kf = nullptr, *Ko = nullptr, *cpf = nullptr, *cpo = nullptr;
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->diag_b, sizeof(int64_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&ucnt, sizeof(int64_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&ubase, sizeof(int64_t) * (nw + 1)));
   SWM_TRY(dalloc(ctx, tmp, (void**)&ent_f, sizeof(int64_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&ent_o, sizeof(int64_t) * nw));
+  SWM_TRY(dalloc(ctx, tmp, (void**)&msq, sizeof(int64_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&Kf, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&Ko, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&cpf, sizeof(int32_t) * ctx->nb));
   SWM_TRY(dalloc(ctx, B, (void**)&cpo, sizeof(int32_t) * ctx->nb));
   k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, ucnt, cpf, Kf, cpo, Ko,
-                                            ent_f, ent_o);
+                                            ent_f, ent_o, msq);
   SWM_LAUNCHED();
-  SWM_TRY(exclusive_scan_i64(ctx, ucnt, ubase, nw, &ctx->nup));
+  // the S-NFC pattern is symmetric, so the blocks above the diagonal are half the off-diagonal ones
+  ctx->nup = (ctx->nb - nw) / 2;
+  SWM_TRY(exclusive_scan_i64(ctx, ucnt, ubase, nw, nullptr));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->bt, sizeof(int64_t) * ctx->nb));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->ublk, sizeof(int64_t) * std::max<int64_t>(1, ctx->nup)));
   k_transpose_and_upper<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, ctx->diag_b, ubase, ctx->bt,
                                                        ctx->ublk);
   SWM_LAUNCHED();
-  SWM_TRY(build_layout(ctx, ctx->full, Kf, cpf, ent_f, m));
-  SWM_TRY(build_layout(ctx, ctx->offd, Ko, cpo, ent_o, m));
-
+  SWM_TRY(alloc_layout(ctx, ctx->full, Kf, cpf));
+  SWM_TRY(alloc_layout(ctx, ctx->offd, Ko, cpo));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->minv_off, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(exclusive_scan_i64(ctx, ent_f, ctx->full.rowbase, nw, nullptr));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, Kf, ctx->full.cmbase, nw, nullptr));
+  SWM_TRY(exclusive_scan_i64(ctx, ent_o, ctx->offd.rowbase, nw, nullptr));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, Ko, ctx->offd.cmbase, nw, nullptr));
+  SWM_TRY(exclusive_scan_i64(ctx, msq, ctx->minv_off, nw, nullptr));
+  {
+    const int64_t* src[5] = {ctx->full.rowbase + nw, ctx->full.cmbase + nw, ctx->offd.rowbase + nw,
+                             ctx->offd.cmbase + nw, ctx->minv_off + nw};
+    int64_t v[5];
+    SWM_TRY(read_i64(ctx, 5, src, v));
+    ctx->full.nval = v[0];
+    ctx->full.ncm = v[1];
+    ctx->offd.nval = v[2];
+    ctx->offd.ncm = v[3];
+    ctx->nminv = v[4];
+  }
+  SWM_TRY(fill_colmap(ctx, ctx->full, m));
+  SWM_TRY(fill_colmap(ctx, ctx->offd, m));
   ctx->m = m;
-  SWM_CK(cudaStreamSynchronize(st));
   dfree_group(ctx, tmp);
   return SWM_OK;
 }

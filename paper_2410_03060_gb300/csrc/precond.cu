@@ -11,56 +11,52 @@ namespace swm {
 
 namespace {
 
-__global__ void k_msq(int64_t nw, const int32_t* __restrict__ m, int64_t* __restrict__ out) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p < nw) out[p] = (int64_t)m[p] * m[p];
-}
 
-// Gauss-Jordan inversion with partial pivoting of Z_pp (float64), one warp per wire.
-template <typename TV>
+// Gauss-Jordan inversion with partial pivoting of Z_pp in precision R, one warp per wire.
+template <typename R, typename TV>
 __global__ void __launch_bounds__(128) k_invert_self(int64_t nw, const int32_t* __restrict__ m,
                                                     const int64_t* __restrict__ diag_b, Layout lay,
                                                     const cplx<TV>* __restrict__ Z, const int64_t* __restrict__ moff,
                                                     cplx<TV>* __restrict__ Minv, int* __restrict__ singular) {
-  __shared__ c128 A[4][kMaxM][2 * kMaxM];
+  __shared__ cplx<R> A[4][kMaxM][2 * kMaxM];
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * 4 + wl;
   if (p >= nw) return;
   const int n = m[p];
   const int K = lay.K[p];
   const int64_t base = lay.rowbase[p] + lay.colpos[diag_b[p]];
-  c128(*a)[2 * kMaxM] = A[wl];
+  cplx<R>(*a)[2 * kMaxM] = A[wl];
   for (int e = lane; e < n * 2 * n; e += 32) {
     const int i = e / (2 * n), j = e % (2 * n);
-    a[i][j] = j < n ? ccast<double>(Z[base + (int64_t)i * K + j]) : mkc(j - n == i ? 1.0 : 0.0, 0.0);
+    a[i][j] = j < n ? ccast<R>(Z[base + (int64_t)i * K + j]) : mkc<R>(j - n == i ? R(1) : R(0), R(0));
   }
   __syncwarp();
   for (int c = 0; c < n; ++c) {
     // pivot: largest |a[r][c]|, r >= c (ties: smallest r)
-    double best = -1.0;
+    R best = -1;
     int br = c;
     for (int r = c; r < n; ++r) {
-      const double v = a[r][c].re * a[r][c].re + a[r][c].im * a[r][c].im;
+      const R v = a[r][c].re * a[r][c].re + a[r][c].im * a[r][c].im;
       if (v > best) {
         best = v;
         br = r;
       }
     }
-    if (best == 0.0) {
+    if (best == R(0)) {
       if (lane == 0) atomicExch(singular, 1);
       return;
     }
     if (br != c) {
       for (int j = lane; j < 2 * n; j += 32) {
-        const c128 t = a[c][j];
+        const cplx<R> t = a[c][j];
         a[c][j] = a[br][j];
         a[br][j] = t;
       }
       __syncwarp();
     }
-    const c128 piv = a[c][c];
-    const double den = piv.re * piv.re + piv.im * piv.im;
-    const c128 inv = mkc(piv.re / den, -piv.im / den);
+    const cplx<R> piv = a[c][c];
+    const R den = piv.re * piv.re + piv.im * piv.im;
+    const cplx<R> inv = mkc<R>(piv.re / den, -piv.im / den);
     __syncwarp();
     for (int j = lane; j < 2 * n; j += 32) a[c][j] = a[c][j] * inv;
     __syncwarp();
@@ -70,7 +66,7 @@ __global__ void __launch_bounds__(128) k_invert_self(int64_t nw, const int32_t* 
     }
     __syncwarp();
     for (int r = lane; r < n; r += 32)
-      if (r != c) a[r][c] = mkc(0.0, 0.0);
+      if (r != c) a[r][c] = mkc<R>(0, 0);
     __syncwarp();
   }
   const int64_t mo = moff[p];
@@ -109,25 +105,16 @@ __global__ void k_form_E(int64_t nb, const int32_t* __restrict__ col, const int6
 int build_precond(swm_ctx* ctx) {
   const int64_t nw = ctx->nw;
   const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
-  std::vector<Buf> tmp;
-  int64_t* msq = nullptr;
-  int* sing = nullptr;
-  int64_t nminv = 0;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&msq, sizeof(int64_t) * nw));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&sing, sizeof(int)));
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->minv_off, sizeof(int64_t) * (nw + 1)));
-  k_msq<<<(unsigned)ceil_div(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->m, msq);
-  SWM_LAUNCHED();
-  SWM_TRY(exclusive_scan_i64(ctx, msq, ctx->minv_off, nw, &nminv));
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Minv, esz * std::max<int64_t>(1, nminv)));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Minv, esz * std::max<int64_t>(1, ctx->nminv)));
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Zp, esz * std::max<int64_t>(1, ctx->offd.nval)));
-  SWM_CK(cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->d_sing, sizeof(int)));
+  SWM_CK(cudaMemsetAsync(ctx->d_sing, 0, sizeof(int), ctx->stream));
   const unsigned g1 = (unsigned)ceil_div(nw, 4);
   const unsigned g2 = (unsigned)std::max<int64_t>(1, ceil_div(ctx->nb * 32, 256));
   if (ctx->prec == SWM_C128) {
     ctx->prof_begin(SWM_K_INVERT);
-    k_invert_self<double><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
-                                                       ctx->minv_off, (c128*)ctx->Minv, sing);
+    k_invert_self<double, double><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
+                                                               ctx->minv_off, (c128*)ctx->Minv, ctx->d_sing);
     ctx->prof_end(SWM_K_INVERT);
     SWM_LAUNCHED();
     ctx->prof_begin(SWM_K_FORM_E);
@@ -138,8 +125,8 @@ int build_precond(swm_ctx* ctx) {
     SWM_LAUNCHED();
   } else {
     ctx->prof_begin(SWM_K_INVERT);
-    k_invert_self<float><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c64*)ctx->Z,
-                                                      ctx->minv_off, (c64*)ctx->Minv, sing);
+    k_invert_self<float, float><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c64*)ctx->Z,
+                                                             ctx->minv_off, (c64*)ctx->Minv, ctx->d_sing);
     ctx->prof_end(SWM_K_INVERT);
     SWM_LAUNCHED();
     ctx->prof_begin(SWM_K_FORM_E);
@@ -149,11 +136,17 @@ int build_precond(swm_ctx* ctx) {
     ctx->prof_end(SWM_K_FORM_E);
     SWM_LAUNCHED();
   }
-  int hs = 0;
-  SWM_CK(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  return SWM_OK;
+}
+
+int finish_build(swm_ctx* ctx) {
+  unsigned long long evals = 0;
+  int sing = 0;
+  SWM_CK(cudaMemcpyAsync(&evals, ctx->d_evals, sizeof(evals), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(&sing, ctx->d_sing, sizeof(sing), cudaMemcpyDeviceToHost, ctx->stream));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
-  dfree_group(ctx, tmp);
-  if (hs) return ctx->fail(SWM_EINVAL, "a self block is singular (degenerate wire geometry?)");
+  ctx->stats.fill_evals = (int64_t)evals;
+  if (sing) return ctx->fail(SWM_EINVAL, "a self block is singular (degenerate wire geometry?)");
   return SWM_OK;
 }
 

@@ -27,7 +27,7 @@ __device__ __forceinline__ double reduce_2pi(double x) {
 
 __device__ __forceinline__ double sinc_d(double z) { return fabs(z) < 1e-8 ? 1.0 - z * z / 6.0 : sin(z) / z; }
 // sin(z)/z in float: Taylor series to z^6 on |z| <= 0.5 (truncation below 2e-8 relative), else
-// the correctly rounded-to-a-few-ulp sinf; the fast __sinf has only absolute accuracy.
+// sinf(z)/z; the fast __sinf is avoided because its error is absolute, not relative.
 __device__ __forceinline__ float sinc_f(float z) {
   const float z2 = z * z;
   if (z2 <= 0.25f) return 1.0f + z2 * (-1.0f / 6.0f + z2 * (1.0f / 120.0f + z2 * (-1.0f / 5040.0f)));
@@ -143,17 +143,16 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial(Geo geo, int64_t nw,
   obs_frame(obs, obs_stride, o, rh, th, ph);
   const cplx<TC>* J = cur + (int64_t)r * N;
   double F[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t p = p0; p < p1; ++p) {
-    double c[3], t[3];
-    geo.get(p, c, t);
-    const int n = geo.ns[p];
-    const double Lp = geo.L[p], D = Lp / n;
-    const double beta = k * (rh[0] * t[0] + rh[1] * t[1] + rh[2] * t[2]);
-    const double phc = k * (rh[0] * c[0] + rh[1] * c[1] + rh[2] * c[2]);
-    const double s1 = -0.5 * Lp + D;
-    const cplx<TC>* Jp = J + geo.off[p];
-    double Sr, Si;
-    if constexpr (F64) {
+  if constexpr (F64) {
+    for (int64_t p = p0; p < p1; ++p) {
+      double c[3], t[3];
+      geo.get(p, c, t);
+      const int n = geo.ns[p];
+      const double Lp = geo.L[p], D = Lp / n;
+      const double beta = k * (rh[0] * t[0] + rh[1] * t[1] + rh[2] * t[2]);
+      const double phc = k * (rh[0] * c[0] + rh[1] * c[1] + rh[2] * c[2]);
+      const double s1 = -0.5 * Lp + D;
+      const cplx<TC>* Jp = J + geo.off[p];
       double sa, ca, sb, cb;
       sincos(phc + beta * s1, &sa, &ca);
       sincos(beta * D, &sb, &cb);
@@ -165,29 +164,49 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial(Geo geo, int64_t nw,
         z = z * rat;
       }
       const double amp = D * sc * sc;
-      Sr = amp * acc.re;
-      Si = amp * acc.im;
-    } else {
+      const double Sr = amp * acc.re, Si = amp * acc.im;
+      F[0] += t[0] * Sr;
+      F[1] += t[0] * Si;
+      F[2] += t[1] * Sr;
+      F[3] += t[1] * Si;
+      F[4] += t[2] * Sr;
+      F[5] += t[2] * Si;
+    }
+  } else {
+    // float32 everywhere except the wire-centre phase k r.c, formed and reduced mod 2 pi in float64
+    const float kf = (float)k;
+    const float rf[3] = {(float)rh[0], (float)rh[1], (float)rh[2]};
+    float Ff[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t p = p0; p < p1; ++p) {
+      double c[3], t[3];
+      geo.get(p, c, t);
+      const float tf[3] = {(float)t[0], (float)t[1], (float)t[2]};
+      const int n = geo.ns[p];
+      const float Lp = (float)geo.L[p], D = Lp / (float)n;
+      const float beta = kf * (rf[0] * tf[0] + rf[1] * tf[1] + rf[2] * tf[2]);
+      const float phc = (float)reduce_2pi(k * (rh[0] * c[0] + rh[1] * c[1] + rh[2] * c[2]));
+      const float s1 = -0.5f * Lp + D;
+      const cplx<TC>* Jp = J + geo.off[p];
       float sa, ca, sb, cb;
-      sincosf((float)reduce_2pi(phc + beta * s1), &sa, &ca);
-      sincosf((float)(beta * D), &sb, &cb);
-      const float sc = sinc_f((float)(0.5 * beta * D));
+      sincosf(phc + beta * s1, &sa, &ca);
+      sincosf(beta * D, &sb, &cb);
+      const float sc = sinc_f(0.5f * beta * D);
       c64 z = mkc(ca, sa), acc = mkc(0.f, 0.f);
       const c64 rat = mkc(cb, sb);
       for (int l = 0; l < n - 1; ++l) {
         cfma(acc, ccast<float>(Jp[l]), z);
         z = z * rat;
       }
-      const float amp = (float)D * sc * sc;
-      Sr = (double)(amp * acc.re);
-      Si = (double)(amp * acc.im);
+      const float amp = D * sc * sc;
+      const float Sr = amp * acc.re, Si = amp * acc.im;
+      Ff[0] = fmaf(tf[0], Sr, Ff[0]);
+      Ff[1] = fmaf(tf[0], Si, Ff[1]);
+      Ff[2] = fmaf(tf[1], Sr, Ff[2]);
+      Ff[3] = fmaf(tf[1], Si, Ff[3]);
+      Ff[4] = fmaf(tf[2], Sr, Ff[4]);
+      Ff[5] = fmaf(tf[2], Si, Ff[5]);
     }
-    F[0] += t[0] * Sr;
-    F[1] += t[0] * Si;
-    F[2] += t[1] * Sr;
-    F[3] += t[1] * Si;
-    F[4] += t[2] * Sr;
-    F[5] += t[2] * Si;
+    for (int i = 0; i < 6; ++i) F[i] = Ff[i];
   }
   c128* out = partial + ((int64_t)blockIdx.y * npairs + e) * 3;
   out[0] = mkc(F[0], F[1]);
@@ -216,7 +235,145 @@ __global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict
   sigma[2 * e + 1] = (pr * pr + pi * pi) / kFourPi;
 }
 
+// Per-wire data of the float32 far field: the centre in cycles, c k / (2 pi), split into a float
+// and its float remainder, the direction and the length.
+struct FFWire {
+  float ch[3], cl[3], t[3], L;
+};
+
+__global__ void k_ff_wires(int64_t nw, const double* __restrict__ cx, const double* __restrict__ cy,
+                           const double* __restrict__ cz, const double* __restrict__ tx, const double* __restrict__ ty,
+                           const double* __restrict__ tz, const double* __restrict__ Ls, double k,
+                           FFWire* __restrict__ out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nw) return;
+  const double s = k / (2.0 * kPi);
+  const double c[3] = {cx[p] * s, cy[p] * s, cz[p] * s};
+  FFWire w;
+  for (int i = 0; i < 3; ++i) {
+    w.ch[i] = (float)c[i];
+    w.cl[i] = (float)(c[i] - (double)w.ch[i]);
+  }
+  w.t[0] = (float)tx[p];
+  w.t[1] = (float)ty[p];
+  w.t[2] = (float)tz[p];
+  w.L = (float)Ls[p];
+  out[p] = w;
+}
+
+// float32 far field.  The centre phase k r.c = 2 pi (r . c k / 2 pi) is formed modulo one cycle
+// from the hi/lo splits of r and of the centre in cycles: each hi*hi product is split exactly
+// into p + e with an FMA, and p - rint(p) is exact, so the phase keeps ~1e-7 cycles however far
+// the wire is from the origin.
+__global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __restrict__ wires,
+                                                                const int32_t* __restrict__ ns,
+                                                                const int64_t* __restrict__ off, int64_t nw, int64_t N,
+                                                                float k, int n_rhs, const c64* __restrict__ cur,
+                                                                int n_obs, const double* __restrict__ obs,
+                                                                int obs_stride, int mono, int64_t chunk,
+                                                                c128* __restrict__ partial) {
+  const int64_t npairs = mono ? n_rhs : (int64_t)n_rhs * n_obs;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p0 = blockIdx.y * chunk, p1 = min(nw, p0 + chunk);
+  if (e >= npairs) return;
+  const int r = mono ? (int)e : (int)(e / n_obs);
+  const int o = mono ? (int)e : (int)(e % n_obs);
+  double rh[3], th[3], ph[3];
+  obs_frame(obs, obs_stride, o, rh, th, ph);
+  float rhi[3], rlo[3];
+  for (int i = 0; i < 3; ++i) {
+    rhi[i] = (float)rh[i];
+    rlo[i] = (float)(rh[i] - (double)rhi[i]);
+  }
+  const float two_pi = 6.28318530717958647692f;
+  const c64* J = cur + (int64_t)r * N;
+  float F[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t p = p0; p < p1; ++p) {
+    const FFWire w = wires[p];
+    float fr = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float pr = rhi[i] * w.ch[i];
+      const float er = fmaf(rhi[i], w.ch[i], -pr);
+      fr += pr - rintf(pr);
+      fr += er + rhi[i] * w.cl[i] + rlo[i] * w.ch[i];
+    }
+    fr -= rintf(fr);
+    const int n = ns[p];
+    const float D = w.L / (float)n;
+    const float beta = k * (rhi[0] * w.t[0] + rhi[1] * w.t[1] + rhi[2] * w.t[2]);
+    const float s1 = -0.5f * w.L + D;
+    float sa, ca, sb, cb;
+    __sincosf(fmaf(two_pi, fr, beta * s1), &sa, &ca);
+    __sincosf(beta * D, &sb, &cb);
+    const float sc = sinc_f(0.5f * beta * D);
+    const c64* Jp = J + off[p];
+    c64 z = mkc(ca, sa), acc = mkc(0.f, 0.f);
+    const c64 rat = mkc(cb, sb);
+    for (int l = 0; l < n - 1; ++l) {
+      cfma(acc, Jp[l], z);
+      z = z * rat;
+    }
+    const float amp = D * sc * sc;
+    const float Sr = amp * acc.re, Si = amp * acc.im;
+    F[0] = fmaf(w.t[0], Sr, F[0]);
+    F[1] = fmaf(w.t[0], Si, F[1]);
+    F[2] = fmaf(w.t[1], Sr, F[2]);
+    F[3] = fmaf(w.t[1], Si, F[3]);
+    F[4] = fmaf(w.t[2], Sr, F[4]);
+    F[5] = fmaf(w.t[2], Si, F[5]);
+  }
+  c128* out = partial + ((int64_t)blockIdx.y * npairs + e) * 3;
+  out[0] = mkc((double)F[0], (double)F[1]);
+  out[1] = mkc((double)F[2], (double)F[3]);
+  out[2] = mkc((double)F[4], (double)F[5]);
+}
+
 }  // namespace
+
+// Launch shape shared by the scratch sizing and the launch itself.
+static void ff_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& chunk) {
+  // about eight CTAs per SM, chunks of at least 16 wires
+  const int64_t gx = ceil_div(npairs, kFFThreads);
+  nchunks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nw, 16), ceil_div(8 * 152, gx)));
+  nchunks = std::min<int64_t>(nchunks, 65535);
+  chunk = ceil_div(nw, nchunks);
+  nchunks = ceil_div(nw, chunk);
+}
+
+int prepare_far_field(swm_ctx* ctx) {
+  if (ctx->prec != SWM_C64) return SWM_OK;
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->ffw, sizeof(FFWire) * ctx->nw));
+  k_ff_wires<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, ctx->stream>>>(ctx->nw, ctx->cx, ctx->cy, ctx->cz, ctx->tx,
+                                                                        ctx->ty, ctx->tz, ctx->L, ctx->k,
+                                                                        (FFWire*)ctx->ffw);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_stride, bool mono, double* sigma,
+                         void* scratch, size_t scratch_bytes) {
+  const int R = ctx->n_rhs;
+  const int64_t npairs = mono ? R : (int64_t)R * n_obs;
+  int64_t nchunks, chunk;
+  ff_shape(ctx->nw, npairs, nchunks, chunk);
+  const int64_t fit = (int64_t)(scratch_bytes / (3 * sizeof(c128) * (size_t)npairs));
+  if (fit < 1) return ctx->fail(SWM_EINVAL, "far field: scratch too small");
+  if (nchunks > fit) {
+    nchunks = fit;
+    chunk = ceil_div(ctx->nw, nchunks);
+    nchunks = ceil_div(ctx->nw, chunk);
+  }
+  dim3 grid((unsigned)ceil_div(npairs, kFFThreads), (unsigned)nchunks);
+  k_far_partial_f32<<<grid, kFFThreads, 0, ctx->stream>>>((const FFWire*)ctx->ffw, ctx->ns, ctx->off, ctx->nw, ctx->N,
+                                                          (float)ctx->k, R, (const c64*)ctx->Xv, n_obs, obs,
+                                                          obs_stride, mono, chunk, (c128*)scratch);
+  SWM_LAUNCHED();
+  k_far_reduce<<<(unsigned)ceil_div(npairs, 128), 128, 0, ctx->stream>>>(npairs, (int)nchunks, (c128*)scratch, n_obs,
+                                                                         obs, obs_stride, mono, sigma);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
 
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
   const int64_t tot = ctx->nw * (int64_t)n_inc;
@@ -232,15 +389,6 @@ int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
   ctx->prof_end(SWM_K_RHS);
   SWM_LAUNCHED();
   return SWM_OK;
-}
-
-// Launch shape shared by the scratch sizing and the launch itself.
-static void ff_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& chunk) {
-  const int64_t gx = ceil_div(npairs, kFFThreads);
-  nchunks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nw, 32), ceil_div(2 * 152, gx)));
-  nchunks = std::min<int64_t>(nchunks, 65535);
-  chunk = ceil_div(nw, nchunks);
-  nchunks = ceil_div(nw, chunk);
 }
 
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs) {

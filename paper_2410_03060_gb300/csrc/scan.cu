@@ -90,12 +90,38 @@ __global__ void k_tile_rescan(const TIn* __restrict__ in, int64_t n, const int64
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = sums[gridDim.x];
 }
 
+// Whole scan in one CTA for short arrays (one launch instead of three).
+template <typename TIn>
+__global__ void k_scan_single(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
+  const int64_t per = ceil_div(n, kScanThreads);
+  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += (int64_t)in[i];
+  int64_t tot;
+  int64_t run = block_incl_scan(s, &tot) - s;
+  for (int64_t i = b; i < e; ++i) {
+    const int64_t v = (int64_t)in[i];
+    out[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) out[n] = tot;
+}
+
 template <typename TIn>
 int scan_impl(swm_ctx* ctx, const TIn* in, int64_t* out, int64_t n, int64_t* total_host) {
   // out has n + 1 entries; out[n] = total.
   if (n == 0) {
     SWM_CK(cudaMemsetAsync(out, 0, sizeof(int64_t), ctx->stream));
     if (total_host) *total_host = 0;
+    return SWM_OK;
+  }
+  if (n <= 4 * kTile) {
+    k_scan_single<TIn><<<1, kScanThreads, 0, ctx->stream>>>(in, n, out);
+    SWM_LAUNCHED();
+    if (total_host) {
+      SWM_CK(cudaMemcpyAsync(total_host, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+      SWM_CK(cudaStreamSynchronize(ctx->stream));
+    }
     return SWM_OK;
   }
   const int64_t nt = ceil_div(n, kTile);
