@@ -1,6 +1,7 @@
 // C-ABI entry points of the swm library (declared and documented in include/swm.h).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -46,6 +47,9 @@ void dfree_group(swm_ctx* ctx, std::vector<Buf>& group) {
 }
 
 static void release_all(swm_ctx* ctx) {
+  dfree_group(ctx, ctx->kry_bufs);
+  std::free(ctx->kry_ws);
+  ctx->kry_ws = nullptr;
   dfree_group(ctx, ctx->solve_bufs);
   dfree_group(ctx, ctx->build_bufs);
   dfree_group(ctx, ctx->cloud_bufs);
@@ -219,8 +223,12 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   k_validate<<<(unsigned)ceil_div(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a,
                                                                    ctx->u_ns, flags, flags + 1);
   SWM_LAUNCHED();
+  double* bb = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&bb, sizeof(double) * 6));
+  SWM_TRY(cloud_bbox_async(ctx, bb, tmp));
   int hf[2] = {0, 0};
   SWM_CK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(ctx->bbox, bb, sizeof(ctx->bbox), cudaMemcpyDeviceToHost, ctx->stream));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   dfree_group(ctx, tmp);
   if (hf[0]) {
@@ -321,6 +329,7 @@ int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restar
   ctx->stats.n_rhs = n_inc;
   ctx->solved = true;
   if (currents_out) {
+    SWM_TRY(ensure_user_offsets(ctx));
     const int64_t N = ctx->N;
     c128* dst = nullptr;
     std::vector<Buf> tmp;
@@ -366,7 +375,8 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
     SWM_CK(cudaMemcpyAsync(obs_dev, obs, sizeof(double) * 2 * n_obs, cudaMemcpyHostToDevice, ctx->stream));
     stride = 2;
   }
-  const size_t sb = far_field_scratch_bytes(ctx->nw, npairs);
+  const size_t sb = ctx->prec == SWM_C64 ? far_field_f32_scratch_bytes(ctx->nw, npairs)
+                                        : far_field_scratch_bytes(ctx->nw, npairs);
   void* scratch = nullptr;
   SWM_TRY(dalloc(ctx, tmp, &scratch, sb));
   double* sig = nullptr;
@@ -504,6 +514,7 @@ int swm_get_rhs(swm_ctx* ctx, double* re_im_out) {
   if (!ctx || !re_im_out) return SWM_EINVAL;
   if (!ctx->solved) return ctx->fail(SWM_ESTATE, "no solve yet");
   SWM_TRY(set_device(ctx));
+  SWM_TRY(ensure_user_offsets(ctx));
   const int64_t N = ctx->N;
   const int R = ctx->n_rhs;
   std::vector<Buf> tmp;

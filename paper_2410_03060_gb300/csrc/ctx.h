@@ -53,6 +53,9 @@ struct swm_ctx {
   // buffers released by a group wait here for reuse by later allocations on the same stream
   // (stream order makes the reuse safe); they are returned to the allocator by swm_destroy
   std::vector<swm::Buf> free_list;
+  std::vector<swm::Buf> kry_bufs;  // Krylov workspace, kept while the problem size stays the same
+  void* kry_ws = nullptr;          // host record of that workspace (krylov.cu)
+  size_t kry_ws_bytes = 0;
   int64_t launches = 0;
 
   // phase timing with CUDA events, read after the call's final synchronisation
@@ -87,6 +90,7 @@ struct swm_ctx {
   double *u_c = nullptr, *u_t = nullptr, *u_L = nullptr, *u_a = nullptr;
   int32_t* u_ns = nullptr;
   int max_ns = 0;
+  double bbox[6] = {0, 0, 0, 0, 0, 0};  // min xyz, max xyz of the centres
 
   // built system
   bool built = false;
@@ -111,6 +115,7 @@ struct swm_ctx {
   int64_t* ublk = nullptr;     // [nup] blocks (p, q) with q > p
   int64_t* minv_off = nullptr; // [nw + 1] offsets of the m_p x m_p inverse blocks
   int32_t* rowwire = nullptr;  // [N] internal wire of each scalar row
+  void* rowinfo = nullptr;     // [N] row descriptors of E (value offset, column-map offset, length)
   int64_t nminv = 0;           // entries of the packed self-block inverses
   unsigned long long* d_evals = nullptr;  // fill evaluation counter (device)
   int* d_sing = nullptr;                  // singular self block flag (device)
@@ -203,11 +208,18 @@ void dfree_group(swm_ctx* ctx, std::vector<Buf>& group);
 int build_pattern(swm_ctx* ctx);
 // copy n device int64 values to the host with one synchronisation
 int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst);
+// launch the bounding-box reduction of the caller centres into out6 (device)
+int cloud_bbox_async(swm_ctx* ctx, double* out6, std::vector<Buf>& tmp);
+// caller-order unknown offsets, made on first use
+int ensure_user_offsets(swm_ctx* ctx);
 // precond.cu: read the build's deferred device flags and counters
 int finish_build(swm_ctx* ctx);
 // scan.cu
 int exclusive_scan_i64(swm_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);
 int exclusive_scan_i32_to_i64(swm_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host);
+// up to six scans of the same length (one launch when short); inputs int64 (is64) or int32
+int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const int* is64, int64_t* const* out,
+                         int64_t n);
 // fill.cu: a2 + a3
 int fill_blocks(swm_ctx* ctx);
 // precond.cu: a5
@@ -215,6 +227,7 @@ int build_precond(swm_ctx* ctx);
 // rhs_ff.cu: a4 + a7
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* inc_dev);
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs);
+size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs);
 int prepare_far_field(swm_ctx* ctx);
 int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_stride, bool mono, double* sigma,
                          void* scratch, size_t scratch_bytes);

@@ -16,6 +16,7 @@
 // V[j][r][n].  Dot products, norms, the Hessenberg matrix and the rotations are float64.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -52,6 +53,7 @@ struct KPtr {
   c128* part;         // [R][nchunk][restart + 1]
   double* partn;      // [R][nchunk]
   int R, restart, nchunk, chunk;
+  int nschunk, schunk;  // chunks of the fused step kernel (finer, for more CTAs)
   int64_t N;
   double tol;
 };
@@ -136,36 +138,72 @@ __device__ bool last_cta(const KPtr& P, int r) {
   return last;
 }
 
-__device__ void reduce_dots(const KPtr& P, int j, int r, c128* __restrict__ dst) {
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const c128* part = P.part + (int64_t)r * P.nchunk * (P.restart + 1);
-  for (int i = wp; i <= j; i += kRows / 32) {
-    double re = 0, im = 0;
-    for (int c = lane; c < P.nchunk; c += 32) {
-      // written by other CTAs of this launch: read through L2
-      const double2 v = __ldcg(reinterpret_cast<const double2*>(part + (int64_t)c * (P.restart + 1) + i));
-      re += v.x;
-      im += v.y;
+// Sum of a strided column of partials, read through L2 with eight loads in flight per lane.
+__device__ __forceinline__ c128 sum_partials_c(const c128* __restrict__ base, int stride, int n, int lane) {
+  double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+  int c = lane;
+  for (; c + 7 * 32 < n; c += 8 * 32) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(reinterpret_cast<const double2*>(base + (int64_t)(c + u * 32) * stride));
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      re[u & 3] += v[u].x;
+      im[u & 3] += v[u].y;
     }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) dst[(int64_t)r * (P.restart + 1) + i] = mkc(re, im);
+  }
+  for (; c < n; c += 32) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(base + (int64_t)c * stride));
+    re[0] += v.x;
+    im[0] += v.y;
+  }
+  return mkc(warp_sum((re[0] + re[1]) + (re[2] + re[3])), warp_sum((im[0] + im[1]) + (im[2] + im[3])));
+}
+
+__device__ __forceinline__ double sum_partials_d(const double* __restrict__ base, int n, int lane) {
+  double a[4] = {0, 0, 0, 0};
+  int c = lane;
+  for (; c + 7 * 32 < n; c += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(base + c + u * 32);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u & 3] += v[u];
+  }
+  for (; c < n; c += 32) a[0] += __ldcg(base + c);
+  return warp_sum((a[0] + a[1]) + (a[2] + a[3]));
+}
+
+__device__ void reduce_dots(const KPtr& P, int j, int r, c128* __restrict__ dst, int nchunk) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const c128* part = P.part + (int64_t)r * nchunk * (P.restart + 1);
+  for (int i = wp; i <= j; i += kRows / 32) {
+    const c128 v = sum_partials_c(part + i, P.restart + 1, nchunk, lane);
+    if (lane == 0) dst[(int64_t)r * (P.restart + 1) + i] = v;
   }
   if (threadIdx.x == 0) P.counter[r] = 0;
 }
 
-// Normalise, multiply by A = I + E and take the first Gram-Schmidt dots, over one chunk of rows.
-// Eight lanes share a scalar row; the 32 row groups of the CTA sweep the chunk.
+// Row descriptor of the stored matrix E: first value, first column-map entry, row length.
+struct alignas(16) RowInfo {
+  int64_t vb;
+  int32_t cmb;
+  int32_t K;
+};
+
+// Normalise, multiply by A = I + E and take the first Gram-Schmidt dots, over one chunk of rows
+// (P.schunk rows, a multiple of 32).  Eight lanes share a scalar row; the 32 row groups of the
+// CTA take the chunk's rows in turn, with their descriptors loaded up front.
 template <typename TV>
-__global__ void __launch_bounds__(kRows) k_step(KPtr P, const int32_t* __restrict__ rowwire,
-                                                const int64_t* __restrict__ off, Layout lay,
-                                                const cplx<TV>* __restrict__ E, cplx<TV>* __restrict__ W0,
-                                                cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ V) {
+__global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restrict__ rinfo,
+                                                const int32_t* __restrict__ colmap, const cplx<TV>* __restrict__ E,
+                                                cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
+                                                cplx<TV>* __restrict__ V) {
   if (P.st->cycle_done) return;
   const int j = P.st->j, r = blockIdx.y;
   const int64_t N = P.N;
-  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
-  const int cnt = (int)min((int64_t)P.chunk, N - n0);
+  const int64_t n0 = (int64_t)blockIdx.x * P.schunk;
+  const int cnt = (int)min((int64_t)P.schunk, N - n0);
   const cplx<TV>* src = ((j & 1) ? W1 : W0) + (int64_t)r * N;
   cplx<TV>* dst = ((j & 1) ? W0 : W1) + (int64_t)r * N;
   const bool act = P.active[r];
@@ -173,25 +211,29 @@ __global__ void __launch_bounds__(kRows) k_step(KPtr P, const int32_t* __restric
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
   const int g = threadIdx.x / kG, sub = threadIdx.x % kG;
-  for (int rb = 0; rb < cnt; rb += kRows / kG) {
-    const int row = rb + g;
-    const bool valid = row < cnt;
-    const int64_t n = n0 + row;
+  constexpr int kMaxRowsPerGroup = 4;
+  RowInfo ri[kMaxRowsPerGroup];
+#pragma unroll
+  for (int t = 0; t < kMaxRowsPerGroup; ++t) {
+    const int row = g + 32 * t;
+    ri[t] = (row < cnt) ? rinfo[n0 + row] : RowInfo{0, 0, 0};
+  }
+#pragma unroll
+  for (int t = 0; t < kMaxRowsPerGroup; ++t) {
+    const int row = g + 32 * t;
+    if (32 * t >= cnt) break;  // uniform across the CTA
     cplx<TV> acc = mkc<TV>(0, 0);
-    if (valid && act) {
-      const int64_t p = rowwire[n];
-      const int i = (int)(n - off[p]);
-      const int K = lay.K[p];
-      const int64_t vb = lay.rowbase[p] + (int64_t)i * K;
-      const int32_t* cm = lay.colmap + lay.cmbase[p];
-      for (int c = sub; c < K; c += kG) cfma(acc, E[vb + c], src[cm[c]]);
+    if (act) {
+      const int32_t* cm = colmap + ri[t].cmb;
+      for (int c = sub; c < ri[t].K; c += kG) cfma(acc, E[ri[t].vb + c], src[cm[c]]);
     }
 #pragma unroll
     for (int o = kG / 2; o > 0; o >>= 1) {
       acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
       acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
     }
-    if (valid && sub == 0) {
+    if (row < cnt && sub == 0) {
+      const int64_t n = n0 + row;
       const cplx<TV> x = act ? s * src[n] : mkc<TV>(0, 0);
       const cplx<TV> y = act ? x + s * acc : mkc<TV>(0, 0);
       V[((int64_t)j * P.R + r) * N + n] = x;
@@ -200,8 +242,8 @@ __global__ void __launch_bounds__(kRows) k_step(KPtr P, const int32_t* __restric
     }
   }
   __syncthreads();
-  cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nchunk + blockIdx.x) * (P.restart + 1));
-  if (last_cta(P, r)) reduce_dots(P, j, r, P.hc);
+  cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nschunk + blockIdx.x) * (P.restart + 1));
+  if (last_cta(P, r)) reduce_dots(P, j, r, P.hc, P.nschunk);
 }
 
 // w -= sum_i V_i h_i over the CTA's rows; result kept in shared memory and written back.
@@ -213,6 +255,7 @@ __device__ void cta_update(const KPtr& P, int j, int r, const cplx<TV>* __restri
   __syncthreads();
   for (int t = threadIdx.x; t < cnt; t += kRows) {
     cplx<TV> x = w[t];
+#pragma unroll 4
     for (int i = 0; i <= j; ++i) {
       const cplx<TV> v = V[((int64_t)i * P.R + r) * P.N + n0 + t];
       const cplx<TV> hh = hs[i];
@@ -237,7 +280,7 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
   cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
   cta_update<TV>(P, j, r, V, P.hc, w, w_sm, n0, cnt);
   cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nchunk + blockIdx.x) * (P.restart + 1));
-  if (last_cta(P, r)) reduce_dots(P, j, r, P.hc2);
+  if (last_cta(P, r)) reduce_dots(P, j, r, P.hc2, P.nchunk);
 }
 
 // Second update, norm, and (last CTA) the Hessenberg column, Givens rotation and residual.
@@ -268,38 +311,49 @@ __global__ void __launch_bounds__(kRows) k_finish(KPtr P, cplx<TV>* __restrict__
     P.partn[(int64_t)r * P.nchunk + blockIdx.x] = t;
   }
   if (!last_cta(P, r)) return;
-  // ---- last CTA of right-hand side r
+  // ---- last CTA of right-hand side r: the Hessenberg column, its rotations and the residual
+  // estimate are worked in shared memory (loaded and stored by all threads) so the one thread
+  // that applies the rotations in order never waits on global memory.
   __shared__ double nrm2;
+  __shared__ c128 col[SWM_MAX_RESTART + 1];
+  __shared__ double scs[SWM_MAX_RESTART];
+  __shared__ c128 ssn[SWM_MAX_RESTART];
+  __shared__ int act_r;
+  __shared__ c128 g_j;
+  __shared__ double bnorm_r;
+  const int R1 = P.restart + 1;
+  c128* Hr = P.H + (int64_t)r * R1 * P.restart;  // H[i][j] at i * restart + j
   if (threadIdx.x < 32) {
-    double t = 0;
-    for (int c = threadIdx.x; c < P.nchunk; c += 32) t += __ldcg(P.partn + (int64_t)r * P.nchunk + c);
-    t = warp_sum(t);
-    if (threadIdx.x == 0) nrm2 = t;
+    const double t = sum_partials_d(P.partn + (int64_t)r * P.nchunk, P.nchunk, threadIdx.x);
+    if (threadIdx.x == 0) {
+      nrm2 = t;
+      act_r = P.active[r];
+      g_j = P.g[(int64_t)r * R1 + j];
+      bnorm_r = P.bnorm[r];
+    }
+  }
+  for (int i = threadIdx.x; i <= j; i += kRows)
+    col[i] = P.hc[(int64_t)r * R1 + i] + P.hc2[(int64_t)r * R1 + i];
+  for (int i = threadIdx.x; i < j; i += kRows) {
+    scs[i] = P.cs[(int64_t)r * P.restart + i];
+    ssn[i] = P.sn[(int64_t)r * P.restart + i];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     P.counter[r] = 0;
-    const int R1 = P.restart + 1;
-    if (P.active[r]) {
+    if (act_r) {
       const double hn = sqrt(nrm2);
-      c128* Hr = P.H + (int64_t)r * R1 * P.restart;  // H[i][j] at i * restart + j
-      c128* hc = P.hc + (int64_t)r * R1;
-      c128* hc2 = P.hc2 + (int64_t)r * R1;
-      double* cs = P.cs + (int64_t)r * P.restart;
-      c128* sn = P.sn + (int64_t)r * P.restart;
-      c128* g = P.g + (int64_t)r * R1;
-      for (int i = 0; i <= j; ++i) Hr[i * P.restart + j] = hc[i] + hc2[i];
       // previous rotations
       for (int i = 0; i < j; ++i) {
-        const c128 a = Hr[i * P.restart + j], b = Hr[(i + 1) * P.restart + j];
-        const c128 sc = sn[i];
-        Hr[i * P.restart + j] = cs[i] * a + sc * b;
-        Hr[(i + 1) * P.restart + j] = mkc(-sc.re, sc.im) * a + cs[i] * b;  // -conj(s) a + c b
+        const c128 a = col[i], b = col[i + 1];
+        const c128 sc = ssn[i];
+        col[i] = scs[i] * a + sc * b;
+        col[i + 1] = mkc(-sc.re, sc.im) * a + scs[i] * b;  // -conj(s) a + c b
       }
       // new rotation zeroing the subdiagonal hn (real, >= 0)
-      const c128 a = Hr[j * P.restart + j];
-      const double aa = hypot(a.re, a.im);
-      const double nu = hypot(aa, hn);
+      const c128 a = col[j];
+      const double aa = sqrt(a.re * a.re + a.im * a.im);
+      const double nu = sqrt(aa * aa + hn * hn);
       double c;
       c128 sv;
       if (aa == 0.0) {
@@ -309,13 +363,15 @@ __global__ void __launch_bounds__(kRows) k_finish(KPtr P, cplx<TV>* __restrict__
         c = aa / nu;
         sv = mkc(a.re / aa * hn / nu, a.im / aa * hn / nu);
       }
-      cs[j] = c;
-      sn[j] = sv;
-      Hr[j * P.restart + j] = c * a + hn * sv;
-      const c128 gj = g[j];
-      g[j + 1] = mkc(-sv.re, sv.im) * gj;
+      P.cs[(int64_t)r * P.restart + j] = c;
+      P.sn[(int64_t)r * P.restart + j] = sv;
+      col[j] = c * a + hn * sv;
+      c128* g = P.g + (int64_t)r * R1;
+      const c128 gj = g_j;
+      const c128 gn = mkc(-sv.re, sv.im) * gj;
+      g[j + 1] = gn;
       g[j] = c * gj;
-      const double res = hypot(g[j + 1].re, g[j + 1].im) / P.bnorm[r];
+      const double res = sqrt(gn.re * gn.re + gn.im * gn.im) / bnorm_r;
       P.resid[r] = res;
       P.jlast[r] = j + 1;
       if (!isfinite(hn) || !isfinite(res)) {
@@ -326,6 +382,11 @@ __global__ void __launch_bounds__(kRows) k_finish(KPtr P, cplx<TV>* __restrict__
       }
       P.inv_h[r] = hn > 0.0 ? 1.0 / hn : 0.0;
     }
+  }
+  __syncthreads();
+  if (act_r)
+    for (int i = threadIdx.x; i <= j; i += kRows) Hr[i * P.restart + j] = col[i];
+  if (threadIdx.x == 0) {
     // the CTA that finishes the last right-hand side advances the step
     __threadfence();
     const unsigned done = atomicAdd(&P.counter[P.R], 1u);
@@ -361,9 +422,7 @@ __global__ void __launch_bounds__(kRows) k_cycle_start(KPtr P, const cplx<TV>* _
   if (!last_cta(P, r)) return;
   __shared__ double nrm2;
   if (threadIdx.x < 32) {
-    double t = 0;
-    for (int c = threadIdx.x; c < P.nchunk; c += 32) t += __ldcg(P.partn + (int64_t)r * P.nchunk + c);
-    t = warp_sum(t);
+    const double t = sum_partials_d(P.partn + (int64_t)r * P.nchunk, P.nchunk, threadIdx.x);
     if (threadIdx.x == 0) nrm2 = t;
   }
   __syncthreads();
@@ -392,23 +451,48 @@ __global__ void __launch_bounds__(kRows) k_cycle_start(KPtr P, const cplx<TV>* _
   }
 }
 
-// Back substitution H y = g per right-hand side (one thread each).
-__global__ void k_backsolve(KPtr P) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= P.R) return;
+// Back substitution H y = g, one CTA per right-hand side.  The triangle is staged in shared memory
+// (dynamic, restart^2 entries) when it fits, the diagonal reciprocals are formed in parallel, and
+// warp 0 substitutes upward with a warp reduction per row.
+__global__ void __launch_bounds__(kRows) k_backsolve(KPtr P, int smem_tri) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ c128 yv[SWM_MAX_RESTART], gv[SWM_MAX_RESTART], dinv[SWM_MAX_RESTART];
+  const int r = blockIdx.x;
   const int n = P.jlast[r];
-  const int R1 = P.restart + 1;
-  const c128* Hr = P.H + (int64_t)r * R1 * P.restart;
-  const c128* g = P.g + (int64_t)r * R1;
-  c128* y = P.coef + (int64_t)r * P.restart;
-  for (int i = n - 1; i >= 0; --i) {
-    c128 s = g[i];
-    for (int l = i + 1; l < n; ++l) s = s - Hr[i * P.restart + l] * y[l];
-    const c128 d = Hr[i * P.restart + i];
+  const int R1 = P.restart + 1, RS = P.restart;
+  const c128* Hg = P.H + (int64_t)r * R1 * RS;
+  c128* Hs = reinterpret_cast<c128*>(sm_raw);
+  const c128* H = smem_tri ? Hs : Hg;
+  if (smem_tri)
+    for (int e = threadIdx.x; e < n * n; e += kRows) {
+      const int i = e / n, l = e % n;
+      if (l >= i) Hs[i * RS + l] = Hg[i * RS + l];
+    }
+  for (int i = threadIdx.x; i < n; i += kRows) {
+    gv[i] = P.g[(int64_t)r * R1 + i];
+    const c128 d = Hg[i * RS + i];
     const double den = d.re * d.re + d.im * d.im;
-    y[i] = den > 0.0 ? mkc((s.re * d.re + s.im * d.im) / den, (s.im * d.re - s.re * d.im) / den) : mkc(0.0, 0.0);
+    dinv[i] = den > 0.0 ? mkc(d.re / den, -d.im / den) : mkc(0.0, 0.0);
   }
-  for (int i = n; i < P.restart; ++i) y[i] = mkc(0.0, 0.0);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = n - 1; i >= 0; --i) {
+      double sr = 0.0, si = 0.0;
+      for (int l = i + 1 + lane; l < n; l += 32) {
+        const c128 h = H[i * RS + l], y = yv[l];
+        sr += h.re * y.re - h.im * y.im;
+        si += h.re * y.im + h.im * y.re;
+      }
+      sr = warp_sum(sr);
+      si = warp_sum(si);
+      if (lane == 0) yv[i] = (gv[i] - mkc(sr, si)) * dinv[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  c128* y = P.coef + (int64_t)r * RS;
+  for (int i = threadIdx.x; i < RS; i += kRows) y[i] = i < n ? yv[i] : mkc(0.0, 0.0);
 }
 
 // Y += V coef.
@@ -443,10 +527,15 @@ __global__ void k_apply_minv(int64_t N, int R, const int32_t* __restrict__ rowwi
   X[(int64_t)r * N + n] = ccast<TV>(acc);
 }
 
-__global__ void k_rowwire(int64_t nw, const int64_t* __restrict__ off, int32_t* __restrict__ rowwire) {
+__global__ void k_rowwire(int64_t nw, const int64_t* __restrict__ off, Layout lay, int32_t* __restrict__ rowwire,
+                          RowInfo* __restrict__ rinfo) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= nw) return;
-  for (int64_t n = off[p]; n < off[p + 1]; ++n) rowwire[n] = (int32_t)p;
+  const int K = lay.K[p];
+  for (int64_t n = off[p]; n < off[p + 1]; ++n) {
+    rowwire[n] = (int32_t)p;
+    rinfo[n] = RowInfo{lay.rowbase[p] + (n - off[p]) * K, (int32_t)lay.cmbase[p], K};
+  }
 }
 
 template <typename TV>
@@ -457,8 +546,11 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   std::vector<Buf>& S = ctx->solve_bufs;
   std::vector<Buf> tmp;
   if (!ctx->rowwire) {
+    if (ctx->offd.ncm > INT32_MAX) return ctx->fail(SWM_EINVAL, "column map too large for 32-bit offsets");
     SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->rowwire, sizeof(int32_t) * std::max<int64_t>(1, N)));
-    k_rowwire<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, st>>>(ctx->nw, ctx->off, ctx->rowwire);
+    SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->rowinfo, sizeof(RowInfo) * std::max<int64_t>(1, N)));
+    k_rowwire<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, st>>>(ctx->nw, ctx->off, ctx->offd, ctx->rowwire,
+                                                               (RowInfo*)ctx->rowinfo);
     SWM_LAUNCHED();
   }
   KPtr P{};
@@ -468,28 +560,56 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   P.tol = tol;
   P.chunk = (int)std::max<int64_t>(kRows, ceil_div(ceil_div(N, 512), kRows) * kRows);
   P.nchunk = (int)ceil_div(N, P.chunk);
+  // the fused step kernel: 64..128 rows per CTA, at most 2048 chunks
+  P.schunk = (int)std::min<int64_t>(128, std::max<int64_t>(128, ceil_div(ceil_div(N, 2048), 32) * 32));
+  P.nschunk = (int)ceil_div(N, P.schunk);
   const int R1 = restart + 1;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.st, sizeof(KState)));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.counter, sizeof(unsigned) * (R + 1)));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.active, sizeof(int) * R));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.jlast, sizeof(int) * R));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.inv_h, sizeof(double) * R));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.bnorm, sizeof(double) * R));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.resid, sizeof(double) * R));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.H, sizeof(c128) * R * R1 * restart));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.cs, sizeof(double) * R * restart));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.sn, sizeof(c128) * R * restart));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.g, sizeof(c128) * R * R1));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.hc, sizeof(c128) * R * R1));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.hc2, sizeof(c128) * R * R1));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.coef, sizeof(c128) * R * restart));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.part, sizeof(c128) * (size_t)R * P.nchunk * R1));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&P.partn, sizeof(double) * (size_t)R * P.nchunk));
-  cplx<TV> *Y = nullptr, *W0 = nullptr, *W1 = nullptr, *V = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&Y, sizeof(cplx<TV>) * R * N));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&W0, sizeof(cplx<TV>) * R * N));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&W1, sizeof(cplx<TV>) * R * N));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&V, sizeof(cplx<TV>) * (size_t)R1 * R * N));
+  // The workspace persists across solves of the same size, so buffer addresses (and the captured
+  // graph that bakes them in) stay the same from one solve to the next.
+  struct Workspace {
+    int64_t key[4];
+    KPtr P;
+    cplx<TV> *Y, *W0, *W1, *V;
+  };
+  const int64_t key[4] = {R, N, restart, (int64_t)sizeof(TV)};
+  Workspace* ws = reinterpret_cast<Workspace*>(ctx->kry_ws);
+  if (!ws || std::memcmp(ws->key, key, sizeof(key)) != 0 || ctx->kry_ws_bytes != sizeof(Workspace)) {
+    dfree_group(ctx, ctx->kry_bufs);
+    std::free(ctx->kry_ws);
+    ctx->kry_ws = nullptr;
+    ws = reinterpret_cast<Workspace*>(std::calloc(1, sizeof(Workspace)));
+    if (!ws) return ctx->fail(SWM_ENOMEM, "host allocation failed");
+    ctx->kry_ws = ws;
+    ctx->kry_ws_bytes = sizeof(Workspace);
+    std::memcpy(ws->key, key, sizeof(key));
+    auto& K = ctx->kry_bufs;
+    SWM_TRY(dalloc(ctx, K, (void**)&P.st, sizeof(KState)));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.counter, sizeof(unsigned) * (R + 1)));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.active, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.jlast, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.inv_h, sizeof(double) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.bnorm, sizeof(double) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.resid, sizeof(double) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.H, sizeof(c128) * R * R1 * restart));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.cs, sizeof(double) * R * restart));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.sn, sizeof(c128) * R * restart));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.g, sizeof(c128) * R * R1));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.hc, sizeof(c128) * R * R1));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.hc2, sizeof(c128) * R * R1));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.coef, sizeof(c128) * R * restart));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.part, sizeof(c128) * (size_t)R * std::max(P.nchunk, P.nschunk) * R1));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.partn, sizeof(double) * (size_t)R * P.nchunk));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->Y, sizeof(cplx<TV>) * R * N));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->W0, sizeof(cplx<TV>) * R * N));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->W1, sizeof(cplx<TV>) * R * N));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->V, sizeof(cplx<TV>) * (size_t)R1 * R * N));
+    ws->P = P;
+  } else {
+    const double tol_now = P.tol;
+    P = ws->P;
+    P.tol = tol_now;
+  }
+  cplx<TV> *Y = ws->Y, *W0 = ws->W0, *W1 = ws->W1, *V = ws->V;
   SWM_CK(cudaMemsetAsync(P.st, 0, sizeof(KState), st));
   SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));
   SWM_CK(cudaMemsetAsync(Y, 0, sizeof(cplx<TV>) * R * N, st));
@@ -499,12 +619,18 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   const cplx<TV>* Bv = (const cplx<TV>*)ctx->Bv;
   const dim3 g_rows((unsigned)ceil_div(N * kG, kRows), R);
   const dim3 g_chunk((unsigned)P.nchunk, R);
+  const dim3 g_schunk((unsigned)P.nschunk, R);
   const size_t sm = sizeof(cplx<TV>) * P.chunk;
+  const size_t ssm = sizeof(cplx<TV>) * P.schunk;
   if (sm > 48 * 1024) {
-    SWM_CK(cudaFuncSetAttribute(k_step<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SWM_CK(cudaFuncSetAttribute(k_update<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SWM_CK(cudaFuncSetAttribute(k_finish<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   }
+  // back substitution stages the triangle in shared memory when it fits
+  size_t bs_smem = sizeof(c128) * (size_t)restart * restart;
+  if (bs_smem > 160 * 1024) bs_smem = 0;
+  if (bs_smem > 0)
+    SWM_CK(cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
   KState hs{};
   int cycles = 0;
   bool first = true;
@@ -518,7 +644,7 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   auto launch_steps = [&](cudaStream_t s, int n) -> int {
     for (int i = 0; i < n; ++i) {
       ctx->prof_begin(SWM_K_APPLY);
-      k_step<TV><<<g_chunk, kRows, sm, s>>>(P, ctx->rowwire, ctx->off, ctx->offd, E, W0, W1, V);
+      k_step<TV><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
       ctx->prof_end(SWM_K_APPLY);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_UPDATE);
@@ -547,7 +673,7 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     } key;
     std::memset(&key, 0, sizeof(key));
     key.P = P;
-    const void* ptrs[6] = {ctx->rowwire, ctx->off, E, W0, W1, V};
+    const void* ptrs[6] = {ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V};
     for (int i = 0; i < 6; ++i) key.ptr[i] = ptrs[i];
     key.lay = ctx->offd;
     key.sm = sm;
@@ -606,7 +732,7 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
         if (slot[(c - 1) & 1].cycle_done) break;
       }
     }
-    k_backsolve<<<(unsigned)ceil_div(R, 64), 64, 0, st>>>(P);
+    k_backsolve<<<(unsigned)R, kRows, bs_smem, st>>>(P, bs_smem > 0 ? 1 : 0);
     SWM_LAUNCHED();
     k_update_y<TV><<<dim3((unsigned)ceil_div(N, 256), R), 256, 0, st>>>(P, V, Y);
     SWM_LAUNCHED();

@@ -235,16 +235,19 @@ __global__ void k_transpose_and_upper(int64_t nw, const int64_t* __restrict__ ro
   for (int64_t b = diag_b[p] + 1; b < b1; ++b) ublk[u++] = b;
 }
 
+// Column maps of both layouts (with and without the diagonal blocks), one thread per block-row.
 __global__ void k_colmap(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                         const int32_t* __restrict__ m, const int64_t* __restrict__ off, const int32_t* __restrict__ colpos,
-                         const int64_t* __restrict__ cmbase, int32_t* __restrict__ colmap) {
+                         const int32_t* __restrict__ m, const int64_t* __restrict__ off, Layout a, Layout b2) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= nw) return;
   for (int64_t b = row_ptr[p]; b < row_ptr[p + 1]; ++b) {
-    const int32_t cp = colpos[b];
-    if (cp < 0) continue;
     const int32_t q = col[b];
-    for (int j = 0; j < m[q]; ++j) colmap[cmbase[p] + cp + j] = (int32_t)(off[q] + j);
+    const int32_t ca = a.colpos[b], cb = b2.colpos[b];
+    for (int j = 0; j < m[q]; ++j) {
+      const int32_t v = (int32_t)(off[q] + j);
+      if (ca >= 0) a.colmap[a.cmbase[p] + ca + j] = v;
+      if (cb >= 0) b2.colmap[b2.cmbase[p] + cb + j] = v;
+    }
   }
 }
 
@@ -258,16 +261,36 @@ int alloc_layout(swm_ctx* ctx, Layout& lay, int32_t* K, int32_t* colpos) {
   return SWM_OK;
 }
 
-int fill_colmap(swm_ctx* ctx, Layout& lay, const int32_t* m) {
+}  // namespace
+
+int cloud_bbox_async(swm_ctx* ctx, double* out6, std::vector<Buf>& tmp) {
   const int64_t nw = ctx->nw;
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.colmap, sizeof(int32_t) * std::max<int64_t>(1, lay.ncm)));
-  k_colmap<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, lay.colpos, lay.cmbase,
-                                                     lay.colmap);
+  const int nbb = (int)std::min<int64_t>(1024, nblk(nw, 256));
+  double* part = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * 6 * nbb));
+  k_bbox_partial<<<nbb, 256, 0, ctx->stream>>>(ctx->u_c, nw, part);
+  SWM_LAUNCHED();
+  k_bbox_final<<<1, 32, 0, ctx->stream>>>(part, nbb, out6);
   SWM_LAUNCHED();
   return SWM_OK;
 }
 
-}  // namespace
+int ensure_user_offsets(swm_ctx* ctx) {
+  if (ctx->uoff) return SWM_OK;
+  const int64_t nw = ctx->nw;
+  std::vector<Buf> tmp;
+  int32_t* um = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&um, sizeof(int32_t) * nw));
+  k_user_m<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->u_ns, um);
+  SWM_LAUNCHED();
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->uoff_user, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(exclusive_scan_i32_to_i64(ctx, um, ctx->uoff_user, nw, nullptr));
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->uoff, sizeof(int64_t) * nw));
+  k_uoff_by_internal<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->perm, ctx->uoff_user, ctx->uoff);
+  SWM_LAUNCHED();
+  dfree_group(ctx, tmp);
+  return SWM_OK;
+}
 
 int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst) {
   for (int i = 0; i < n; ++i)
@@ -282,18 +305,8 @@ int build_pattern(swm_ctx* ctx) {
   std::vector<Buf> tmp;
   auto& B = ctx->build_bufs;
 
-  // --- bounding box of the centres
-  const int nbb = (int)std::min<int64_t>(1024, nblk(nw, 256));
-  double *part = nullptr, *bb = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * 6 * nbb));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&bb, sizeof(double) * 6));
-  k_bbox_partial<<<nbb, 256, 0, st>>>(ctx->u_c, nw, part);
-  SWM_LAUNCHED();
-  k_bbox_final<<<1, 32, 0, st>>>(part, nbb, bb);
-  SWM_LAUNCHED();
-  double hb[6];
-  SWM_CK(cudaMemcpyAsync(hb, bb, sizeof(hb), cudaMemcpyDeviceToHost, st));
-  SWM_CK(cudaStreamSynchronize(st));
+  // --- bounding box of the centres (computed when the cloud was loaded)
+  const double* hb = ctx->bbox;
 
   // --- grid (cell side slightly above r_c so a pair at exactly r_c is never two cells apart)
   Grid g;
@@ -313,8 +326,10 @@ int build_pattern(swm_ctx* ctx) {
   };
   int64_t nx, ny, nz;
   dims(g.h, nx, ny, nz);
-  while ((double)nx * (double)ny * (double)nz > (double)kMaxCells) {
-    g.h *= 1.25 * std::cbrt((double)nx * ny * nz / (double)kMaxCells);
+  // at most about four cells per wire (larger cells only add candidates to the distance test)
+  const double max_cells = std::min<double>((double)kMaxCells, std::max<double>(4096.0, 4.0 * (double)nw));
+  while ((double)nx * (double)ny * (double)nz > max_cells) {
+    g.h *= 1.05 * std::cbrt((double)nx * ny * nz / max_cells);
     dims(g.h, nx, ny, nz);
   }
   g.nx = (int)nx;
@@ -346,23 +361,17 @@ int build_pattern(swm_ctx* ctx) {
   // --- geometry in internal order, numbering of unknowns (a0)
   double** geo[8] = {&ctx->cx, &ctx->cy, &ctx->cz, &ctx->tx, &ctx->ty, &ctx->tz, &ctx->L, &ctx->a};
   for (auto pp : geo) SWM_TRY(dalloc(ctx, B, (void**)pp, sizeof(double) * nw));
-  int32_t *m = nullptr, *um = nullptr;
+  int32_t* m = nullptr;
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->ns, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&m, sizeof(int32_t) * nw));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&um, sizeof(int32_t) * nw));
   k_gather_geometry<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->perm, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a,
                                                    ctx->u_ns, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty,
                                                    ctx->tz, ctx->L, ctx->a, ctx->ns, m);
   SWM_LAUNCHED();
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->off, sizeof(int64_t) * (nw + 1)));
   SWM_TRY(exclusive_scan_i32_to_i64(ctx, m, ctx->off, nw, nullptr));
-  k_user_m<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->u_ns, um);
-  SWM_LAUNCHED();
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->uoff_user, sizeof(int64_t) * (nw + 1)));
-  SWM_TRY(exclusive_scan_i32_to_i64(ctx, um, ctx->uoff_user, nw, nullptr));
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->uoff, sizeof(int64_t) * nw));
-  k_uoff_by_internal<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->perm, ctx->uoff_user, ctx->uoff);
-  SWM_LAUNCHED();
+  ctx->uoff = nullptr;  // caller-order offsets are made on first use (ensure_user_offsets)
+  ctx->uoff_user = nullptr;
 
   // --- S-NFC pairs (a1): count, scan, write
   int32_t* rcnt = nullptr;
@@ -408,20 +417,21 @@ int build_pattern(swm_ctx* ctx) {
   SWM_LAUNCHED();
   // the S-NFC pattern is symmetric, so the blocks above the diagonal are half the off-diagonal ones
   ctx->nup = (ctx->nb - nw) / 2;
-  SWM_TRY(exclusive_scan_i64(ctx, ucnt, ubase, nw, nullptr));
+  SWM_TRY(alloc_layout(ctx, ctx->full, Kf, cpf));
+  SWM_TRY(alloc_layout(ctx, ctx->offd, Ko, cpo));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->minv_off, sizeof(int64_t) * (nw + 1)));
+  {
+    const void* in[6] = {ucnt, ent_f, Kf, ent_o, Ko, msq};
+    const int is64[6] = {1, 1, 0, 1, 0, 1};
+    int64_t* out[6] = {ubase, ctx->full.rowbase, ctx->full.cmbase, ctx->offd.rowbase, ctx->offd.cmbase,
+                       ctx->minv_off};
+    SWM_TRY(exclusive_scan_multi(ctx, 6, in, is64, out, nw));
+  }
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->bt, sizeof(int64_t) * ctx->nb));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->ublk, sizeof(int64_t) * std::max<int64_t>(1, ctx->nup)));
   k_transpose_and_upper<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, ctx->diag_b, ubase, ctx->bt,
                                                        ctx->ublk);
   SWM_LAUNCHED();
-  SWM_TRY(alloc_layout(ctx, ctx->full, Kf, cpf));
-  SWM_TRY(alloc_layout(ctx, ctx->offd, Ko, cpo));
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->minv_off, sizeof(int64_t) * (nw + 1)));
-  SWM_TRY(exclusive_scan_i64(ctx, ent_f, ctx->full.rowbase, nw, nullptr));
-  SWM_TRY(exclusive_scan_i32_to_i64(ctx, Kf, ctx->full.cmbase, nw, nullptr));
-  SWM_TRY(exclusive_scan_i64(ctx, ent_o, ctx->offd.rowbase, nw, nullptr));
-  SWM_TRY(exclusive_scan_i32_to_i64(ctx, Ko, ctx->offd.cmbase, nw, nullptr));
-  SWM_TRY(exclusive_scan_i64(ctx, msq, ctx->minv_off, nw, nullptr));
   {
     const int64_t* src[5] = {ctx->full.rowbase + nw, ctx->full.cmbase + nw, ctx->offd.rowbase + nw,
                              ctx->offd.cmbase + nw, ctx->minv_off + nw};
@@ -433,8 +443,10 @@ int build_pattern(swm_ctx* ctx) {
     ctx->offd.ncm = v[3];
     ctx->nminv = v[4];
   }
-  SWM_TRY(fill_colmap(ctx, ctx->full, m));
-  SWM_TRY(fill_colmap(ctx, ctx->offd, m));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->full.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->full.ncm)));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->offd.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->offd.ncm)));
+  k_colmap<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, ctx->full, ctx->offd);
+  SWM_LAUNCHED();
   ctx->m = m;
   dfree_group(ctx, tmp);
   return SWM_OK;

@@ -214,18 +214,22 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial(Geo geo, int64_t nw,
   out[2] = mkc(F[4], F[5]);
 }
 
+// One warp per (incidence, observation) pair: sum the chunk partials, then sigma.
 __global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict__ partial, int n_obs,
                              const double* __restrict__ obs, int obs_stride, int mono, double* __restrict__ sigma) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (e >= npairs) return;
   double F[6] = {0, 0, 0, 0, 0, 0};
-  for (int c = 0; c < nchunks; ++c) {
+  for (int c = lane; c < nchunks; c += 32) {
     const c128* in = partial + ((int64_t)c * npairs + e) * 3;
     for (int d = 0; d < 3; ++d) {
       F[2 * d] += in[d].re;
       F[2 * d + 1] += in[d].im;
     }
   }
+  for (int d = 0; d < 6; ++d) F[d] = warp_sum(F[d]);
+  if (lane != 0) return;
   const int o = mono ? (int)e : (int)(e % n_obs);
   double rh[3], th[3], ph[3];
   obs_frame(obs, obs_stride, o, rh, th, ph);
@@ -240,6 +244,8 @@ __global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict
 struct FFWire {
   float ch[3], cl[3], t[3], L;
 };
+constexpr int kFFChunkMax = 64;   // wires per chunk of the float32 far field
+constexpr int kFFCurMax = 1024;   // staged currents per chunk
 
 __global__ void k_ff_wires(int64_t nw, const double* __restrict__ cx, const double* __restrict__ cy,
                            const double* __restrict__ cz, const double* __restrict__ tx, const double* __restrict__ ty,
@@ -275,9 +281,9 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
   const int64_t npairs = mono ? n_rhs : (int64_t)n_rhs * n_obs;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t p0 = blockIdx.y * chunk, p1 = min(nw, p0 + chunk);
-  if (e >= npairs) return;
-  const int r = mono ? (int)e : (int)(e / n_obs);
-  const int o = mono ? (int)e : (int)(e % n_obs);
+  const int64_t ec = e < npairs ? e : npairs - 1;  // threads past the end help stage, then leave
+  const int r = mono ? (int)ec : (int)(ec / n_obs);
+  const int o = mono ? (int)ec : (int)(ec % n_obs);
   double rh[3], th[3], ph[3];
   obs_frame(obs, obs_stride, o, rh, th, ph);
   float rhi[3], rlo[3];
@@ -286,10 +292,28 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
     rlo[i] = (float)(rh[i] - (double)rhi[i]);
   }
   const float two_pi = 6.28318530717958647692f;
-  const c64* J = cur + (int64_t)r * N;
+  // the chunk's wires and their currents, staged once per CTA
+  __shared__ FFWire sw[kFFChunkMax];
+  __shared__ int sn[kFFChunkMax];
+  __shared__ int soff[kFFChunkMax + 1];
+  __shared__ c64 sJ[kFFCurMax];
+  const int nwc = (int)(p1 - p0);
+  const int64_t o0 = off[p0];
+  const int ncur = (int)(off[p1] - o0);
+  const bool stage_cur = mono == 0 && n_rhs == 1 && ncur <= kFFCurMax;
+  for (int t = threadIdx.x; t < nwc; t += blockDim.x) {
+    sw[t] = wires[p0 + t];
+    sn[t] = ns[p0 + t];
+    soff[t] = (int)(off[p0 + t] - o0);
+  }
+  if (stage_cur)
+    for (int t = threadIdx.x; t < ncur; t += blockDim.x) sJ[t] = cur[o0 + t];
+  __syncthreads();
+  if (e >= npairs) return;
+  const c64* J = cur + (int64_t)r * N + o0;
   float F[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int64_t p = p0; p < p1; ++p) {
-    const FFWire w = wires[p];
+  for (int q = 0; q < nwc; ++q) {
+    const FFWire& w = sw[q];
     float fr = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -299,7 +323,7 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
       fr += er + rhi[i] * w.cl[i] + rlo[i] * w.ch[i];
     }
     fr -= rintf(fr);
-    const int n = ns[p];
+    const int n = sn[q];
     const float D = w.L / (float)n;
     const float beta = k * (rhi[0] * w.t[0] + rhi[1] * w.t[1] + rhi[2] * w.t[2]);
     const float s1 = -0.5f * w.L + D;
@@ -307,7 +331,7 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
     __sincosf(fmaf(two_pi, fr, beta * s1), &sa, &ca);
     __sincosf(beta * D, &sb, &cb);
     const float sc = sinc_f(0.5f * beta * D);
-    const c64* Jp = J + off[p];
+    const c64* Jp = stage_cur ? sJ + soff[q] : J + soff[q];
     c64 z = mkc(ca, sa), acc = mkc(0.f, 0.f);
     const c64 rat = mkc(cb, sb);
     for (int l = 0; l < n - 1; ++l) {
@@ -357,20 +381,19 @@ int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_str
   const int64_t npairs = mono ? R : (int64_t)R * n_obs;
   int64_t nchunks, chunk;
   ff_shape(ctx->nw, npairs, nchunks, chunk);
-  const int64_t fit = (int64_t)(scratch_bytes / (3 * sizeof(c128) * (size_t)npairs));
-  if (fit < 1) return ctx->fail(SWM_EINVAL, "far field: scratch too small");
-  if (nchunks > fit) {
-    nchunks = fit;
-    chunk = ceil_div(ctx->nw, nchunks);
+  if (chunk > kFFChunkMax) {
+    chunk = kFFChunkMax;
     nchunks = ceil_div(ctx->nw, chunk);
   }
+  if ((size_t)nchunks * npairs * 3 * sizeof(c128) > scratch_bytes)
+    return ctx->fail(SWM_EINVAL, "far field: scratch too small");
   dim3 grid((unsigned)ceil_div(npairs, kFFThreads), (unsigned)nchunks);
   k_far_partial_f32<<<grid, kFFThreads, 0, ctx->stream>>>((const FFWire*)ctx->ffw, ctx->ns, ctx->off, ctx->nw, ctx->N,
                                                           (float)ctx->k, R, (const c64*)ctx->Xv, n_obs, obs,
                                                           obs_stride, mono, chunk, (c128*)scratch);
   SWM_LAUNCHED();
-  k_far_reduce<<<(unsigned)ceil_div(npairs, 128), 128, 0, ctx->stream>>>(npairs, (int)nchunks, (c128*)scratch, n_obs,
-                                                                         obs, obs_stride, mono, sigma);
+  k_far_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, ctx->stream>>>(npairs, (int)nchunks, (c128*)scratch,
+                                                                              n_obs, obs, obs_stride, mono, sigma);
   SWM_LAUNCHED();
   return SWM_OK;
 }
@@ -389,6 +412,13 @@ int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
   ctx->prof_end(SWM_K_RHS);
   SWM_LAUNCHED();
   return SWM_OK;
+}
+
+size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs) {
+  int64_t nchunks, chunk;
+  ff_shape(nw, npairs, nchunks, chunk);
+  if (chunk > kFFChunkMax) nchunks = ceil_div(nw, kFFChunkMax);
+  return (size_t)nchunks * npairs * 3 * sizeof(c128);
 }
 
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs) {
@@ -441,8 +471,8 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
     *err = std::string("far field launch: ") + cudaGetErrorString(e);
     return SWM_ECUDA;
   }
-  k_far_reduce<<<(unsigned)ceil_div(npairs, 128), 128, 0, st>>>(npairs, (int)nchunks, part, n_obs, obs, obs_stride,
-                                                                mono, sigma);
+  k_far_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, st>>>(npairs, (int)nchunks, part, n_obs, obs,
+                                                                     obs_stride, mono, sigma);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("far field reduce launch: ") + cudaGetErrorString(e);

@@ -142,7 +142,58 @@ int scan_impl(swm_ctx* ctx, const TIn* in, int64_t* out, int64_t n, int64_t* tot
   return SWM_OK;
 }
 
+struct MultiScanArgs {
+  const void* in[6];
+  int is64[6];
+  int64_t* out[6];
+  int narr;
+};
+
+// Several exclusive scans of the same short length in one CTA.
+__global__ void k_scan_multi(MultiScanArgs a, int64_t n) {
+  const int64_t per = ceil_div(n, kScanThreads);
+  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+  for (int k = 0; k < a.narr; ++k) {
+    const int64_t* i64 = (const int64_t*)a.in[k];
+    const int32_t* i32 = (const int32_t*)a.in[k];
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += a.is64[k] ? i64[i] : (int64_t)i32[i];
+    int64_t tot;
+    int64_t run = block_incl_scan(s, &tot) - s;
+    int64_t* out = a.out[k];
+    for (int64_t i = b; i < e; ++i) {
+      const int64_t v = a.is64[k] ? i64[i] : (int64_t)i32[i];
+      out[i] = run;
+      run += v;
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+  }
+}
+
 }  // namespace
+
+int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const int* is64, int64_t* const* out,
+                         int64_t n) {
+  if (n <= 4 * kTile && n > 0) {
+    MultiScanArgs a{};
+    a.narr = narr;
+    for (int k = 0; k < narr; ++k) {
+      a.in[k] = in[k];
+      a.is64[k] = is64[k];
+      a.out[k] = out[k];
+    }
+    k_scan_multi<<<1, kScanThreads, 0, ctx->stream>>>(a, n);
+    SWM_LAUNCHED();
+    return SWM_OK;
+  }
+  for (int k = 0; k < narr; ++k) {
+    if (is64[k])
+      SWM_TRY(scan_impl<int64_t>(ctx, (const int64_t*)in[k], out[k], n, nullptr));
+    else
+      SWM_TRY(scan_impl<int32_t>(ctx, (const int32_t*)in[k], out[k], n, nullptr));
+  }
+  return SWM_OK;
+}
 
 int exclusive_scan_i64(swm_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host) {
   return scan_impl<int64_t>(ctx, in, out, n, total_host);
