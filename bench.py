@@ -29,7 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import cloud_mid, incidences_single_minus_z, observations_phi_cut  # noqa: E402
+from synth import (cloud_batching_snapshot, cloud_learned, cloud_mid, cloud_precision,  # noqa: E402
+                   incidences_monostatic, incidences_single_minus_z, observations_phi_cut)
 
 METRIC = "unknowns×incidences solved/sec at ≤0.1 dB RCS error vs plain FP64 path"
 UNIT = "unknowns*incidences/s"
@@ -334,6 +335,106 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------------- larger workloads
+SCALE = {
+    "learned": dict(cloud=cloud_learned, r_c=3.0, n_inc=37,
+                    text="1,000,000 wires in 8 Gaussian clusters (sigma 40) in a 600-wavelength cube, r_c 3"),
+    "precision": dict(cloud=cloud_precision, r_c=4.0, n_inc=91,
+                      text="200,000 wires in a 350-wavelength cube, lengths 0.35/0.45/0.5, r_c 4"),
+    "batching0": dict(cloud=lambda nw=None: cloud_batching_snapshot(0, nw), r_c=3.0, n_inc=181,
+                      text="batching snapshot 0 (0.005 wires per cubic wavelength), r_c 3"),
+}
+
+
+def run_scale(args):
+    """One larger workload: the step (cloud, build, solve, monostatic RCS) in complex64, with the fill
+    measured against the FP32 peak and the block-sparse product against HBM bandwidth.  Prints a
+    JSON line of kind "scale"; it is a measurement record, not the benchmark line."""
+    import torch
+
+    from paper_2410_03060_gb300 import swm
+
+    w = SCALE[args.workload]
+    torch.cuda.set_device(0)
+    cl = w["cloud"](nw=args.nw) if args.nw else w["cloud"]()
+    n_inc = args.inc or w["n_inc"]
+    inc = incidences_monostatic(n_inc)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
+    mono = torch.zeros((n_inc, 2), dtype=torch.float64, device="cuda")
+    ctx = swm.swm_create(0)
+    restart = args.restart
+
+    def step():
+        swm.swm_set_cloud(ctx, *dev)
+        swm.swm_build(ctx, K0, w["r_c"], swm.SWM_C64)
+        rc = swm.swm_solve(ctx, inc, TOL, restart, 2000)
+        swm.swm_rcs_monostatic(ctx, mono)
+        return rc
+
+    step()
+    torch.cuda.synchronize()
+    res = {}
+    for cls in ("fill_mutual", "apply", "dots", "update", "finish", "far", "pairs", "fill_self"):
+        swm.swm_profile(ctx, cls)
+        step()
+        torch.cuda.synchronize()
+        st = swm.swm_get_stats(ctx)
+        res[cls] = (st["prof_ms"], st["prof_launches"])
+    swm.swm_profile(ctx, "none")
+    ts = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rc = step()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t)
+    st = swm.swm_get_stats(ctx)
+    pk = peaks()
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = N_SM * 128 * 2 * mhz * 1e6 / 1e12
+    fill_ms, _ = res["fill_mutual"]
+    fill_tf = st["fill_evals"] * FP32_FLOPS_PER_EVAL / (fill_ms * 1e-3) / 1e12
+    # block-sparse product: E (+ column map, row descriptors) once per block of 8 right-hand sides,
+    # x/V/y rows and the fused first Gram-Schmidt pass per right-hand side
+    esz, N, R = 8, st["n"], n_inc
+    it = st["iterations"]
+    steps_j = []
+    while it > 0:
+        c = min(restart, it)
+        steps_j += list(range(c))
+        it -= c
+    nblk = -(-R // 8) if R > 1 else 1
+    mat = (st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N) * nblk
+    split = N >= (1 << 19)  # the library's default split of the Arnoldi step
+    # split: the product alone (x read, V and y written); fused: plus the V rows of the first dots
+    apply_bytes = sum(mat + R * N * esz * (3 + (0 if split else j + 1)) for j in steps_j)
+    apply_ms, apply_n = res["apply"]
+    # the residual products of the restarts are timed with the class too: count their bytes
+    apply_bytes += (st["restarts"] + 1) * (st["nnz_offd"] * esz + st["ncm_offd"] * 4) * R
+    gbs = apply_bytes / (apply_ms * 1e-3) / 1e9
+    out = {
+        "kind": "scale", "workload": args.workload, "description": w["text"], "nw": cl.nw, "unknowns": N,
+        "blocks": st["nb"], "nnz": st["nnz"], "incidences": n_inc, "restart": restart, "iterations": st["iterations"],
+        "converged": st["converged"], "rel_residual": st["rel_residual"], "rc": rc,
+        "ms_per_step": 1e3 * float(np.median(ts)),
+        "value": N * n_inc / float(np.median(ts)), "unit": UNIT,
+        "phase_ms": {k: st[k] for k in ("ms_neighbour", "ms_fill", "ms_precond", "ms_rhs", "ms_solve", "ms_rcs")},
+        "fill_roofline": {"bound": "alu", "kernel": "k_mutual_blocks<float>", "evals": st["fill_evals"],
+                          "flops_per_eval": FP32_FLOPS_PER_EVAL, "ms": fill_ms, "achieved": fill_tf,
+                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": fill_tf / fp32_peak,
+                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"},
+        "apply_roofline": {"bound": "hbm",
+                           "kernel": "k_spmv (block-sparse product)" if split else
+                           "k_step (block-sparse product + first Gram-Schmidt pass)",
+                           "launches": apply_n, "ms": apply_ms, "bytes": apply_bytes, "achieved": gbs,
+                           "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                           "frac": gbs / pk.get("hbm_gbs", 6800.0), "peak_source": "of measured (MEASURED_PEAKS.json)"},
+        "kernel_ms_per_step": {k: v[0] for k, v in res.items()},
+    }
+    print(json.dumps(out))
+    swm.swm_destroy(ctx)
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -371,8 +472,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["mid"] + sorted(SCALE), default="mid")
+    ap.add_argument("--inc", type=int, default=0, help="incidences of a larger workload (default: its own)")
+    ap.add_argument("--restart", type=int, default=RESTART)
+    ap.add_argument("--nw", type=int, default=0, help="wire count of a larger workload (default: its own)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.workload != "mid" and args.impl == "ours":
+        run_scale(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

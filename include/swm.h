@@ -114,15 +114,19 @@ typedef struct swm_stats {
 #define SWM_K_INVERT 4      /* self-block inverses */
 #define SWM_K_FORM_E 5      /* Z_pq Z_qq^-1 */
 #define SWM_K_RHS 6         /* right-hand sides */
-#define SWM_K_APPLY 7       /* block-sparse product fused with the first Gram-Schmidt pass, and
-                               the residual product at each restart */
-#define SWM_K_DOTS 8        /* reserved (the first pass is part of SWM_K_APPLY) */
+#define SWM_K_APPLY 7       /* block-sparse product (fused with the first Gram-Schmidt pass when
+                               N < 2^19), and the residual product at each restart */
+#define SWM_K_DOTS 8        /* first Gram-Schmidt pass when it runs on its own (N >= 2^19);
+                               below that it is part of SWM_K_APPLY */
 #define SWM_K_UPDATE 9      /* second Gram-Schmidt pass */
 #define SWM_K_FINISH 10     /* norm, Hessenberg column, rotation */
 #define SWM_K_FAR 11        /* far field: partial sums and their reduction to RCS */
 
 /* Create a context on CUDA device `device` that issues all work on `cuda_stream`
- * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context. */
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context.
+ * Environment: SWM_SPLIT_ROWS (default 524288) -- systems with at least this many unknowns run
+ * each GMRES step as a streaming block-sparse product plus separate dot products, smaller ones
+ * as one fused kernel; read when the context is created. */
 int swm_create(swm_ctx** out, int device, void* cuda_stream);
 
 /* Free every device buffer of the context and the context itself.  NULL is ignored. */

@@ -148,6 +148,7 @@ int swm_create(swm_ctx** out, int device, void* cuda_stream) {
   if (!ctx) return SWM_ENOMEM;
   ctx->device = device;
   ctx->stream = (cudaStream_t)cuda_stream;
+  if (const char* e = std::getenv("SWM_SPLIT_ROWS")) ctx->split_rows = std::max<long long>(0, std::atoll(e));
   if (cudaSetDevice(device) != cudaSuccess) {
     delete ctx;
     return SWM_ECUDA;

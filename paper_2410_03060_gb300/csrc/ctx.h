@@ -124,6 +124,9 @@ struct swm_ctx {
   cudaGraphExec_t gm_exec = nullptr;      // captured chunk of GMRES steps and its argument key
   std::vector<unsigned char> gm_key;
   cudaStream_t cap_stream = nullptr;      // private stream for graph capture
+  // systems with at least this many unknowns run the Arnoldi step as a streaming product plus
+  // separate dots (bandwidth); smaller ones as one fused kernel (latency).  SWM_SPLIT_ROWS overrides.
+  int64_t split_rows = int64_t(1) << 19;
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   swm::Layout full, offd;
   void* Z = nullptr;     // values of Z in layout `full`

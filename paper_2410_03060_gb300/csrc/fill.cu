@@ -207,6 +207,8 @@ __global__ void __launch_bounds__(kSelfThreads) k_self_blocks(int64_t nw, const 
 struct BlockGeo {
   float D[3], tp[3], tq[3];  // FP32 copies (fast path); the FP64 path re-reads FP64 geometry
   float Lp, Lq, a2, tpq;
+  float f, sc;               // D_p D_q / (4 pi) and 1 / (k^2 D_p D_q), formed in float64
+  double fd, scd, tpqd;      // the same in float64 for the float64 path
   int nsp, nsq, nq, item0;   // item0: first segment pair of this block in the batch
   int out0;                  // first output entry of this block in the batch
   int p, q;
@@ -354,7 +356,7 @@ __host__ __device__ constexpr size_t round16(size_t x) { return (x + 15) / 16 * 
 // One CTA per batch of `nbatch` upper blocks.  Shared memory: BlockGeo[nbatch], item and output
 // prefix arrays, and SegI<R> for every segment pair of the batch (capacity `cap`).
 template <typename R, typename TV>
-__global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
+__global__ void __launch_bounds__(kFillThreads, sizeof(R) == 4 ? 3 : 1) k_mutual_blocks(
     int64_t nup, const int64_t* __restrict__ ublk, const int32_t* __restrict__ col, const int64_t* __restrict__ bt,
     const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
     const double* __restrict__ tx, const double* __restrict__ ty, const double* __restrict__ tz,
@@ -412,7 +414,15 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
     G.Lp = (float)Lp;
     G.Lq = (float)Lq;
     G.a2 = (float)(0.5 * (as[p] * as[p] + as[q] * as[q]));
-    G.tpq = (float)(tp[0] * tq[0] + tp[1] * tq[1] + tp[2] * tq[2]);
+    G.tpqd = tp[0] * tq[0] + tp[1] * tq[1] + tp[2] * tq[2];
+    G.tpq = (float)G.tpqd;
+    {
+      const double Dp = Lp / nsp, Dq = Lq / nsq;
+      G.fd = Dp * Dq / kFourPi;
+      G.scd = 1.0 / (k * k * Dp * Dq);
+      G.f = (float)G.fd;
+      G.sc = (float)G.scd;
+    }
     G.nsp = nsp;
     G.nsq = nsq;
     G.nq = nq;
@@ -495,19 +505,17 @@ __global__ void __launch_bounds__(kFillThreads) k_mutual_blocks(
     const cplx<R> vec = a00.rr + a01.rf + a10.fr + a11.ff;
     auto IG = [](const SegI<R>& x) { return x.rr + x.rf + x.fr + x.ff; };
     const cplx<R> sca = IG(a00) - IG(a01) - IG(a10) + IG(a11);
-    double Dp, Dq, tpq;
+    R f, sc, tpq;
     if constexpr (sizeof(R) == 4) {
-      Dp = (double)G.Lp / G.nsp;
-      Dq = (double)G.Lq / G.nsq;
+      f = G.f;
+      sc = G.sc;
       tpq = G.tpq;
     } else {
-      Dp = Ls[G.p] / G.nsp;
-      Dq = Ls[G.q] / G.nsq;
-      tpq = tx[G.p] * tx[G.q] + ty[G.p] * ty[G.q] + tz[G.p] * tz[G.q];
+      f = G.fd;
+      sc = G.scd;
+      tpq = G.tpqd;
     }
-    const R f = (R)(Dp * Dq / kFourPi);
-    const R sc = (R)(1.0 / (k * k * Dp * Dq));
-    const cplx<R> z = mkc<R>(f * ((R)tpq * vec.re - sc * sca.re), f * ((R)tpq * vec.im - sc * sca.im));
+    const cplx<R> z = mkc<R>(f * (tpq * vec.re - sc * sca.re), f * (tpq * vec.im - sc * sca.im));
     const cplx<TV> zt = ccast<TV>(z);
     Z[G.bpq + (int64_t)i * G.Kp + j] = zt;
     Z[G.bqp + (int64_t)j * G.Kq + i] = zt;

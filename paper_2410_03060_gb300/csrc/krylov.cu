@@ -118,7 +118,21 @@ __device__ void cta_dots(const KPtr& P, int j, int r, const cplx<TV>* __restrict
   for (int i = wp; i <= j; i += kRows / 32) {
     const cplx<TV>* vi = V + ((int64_t)i * P.R + r) * P.N + n0;
     cplx<TV> acc = mkc<TV>(0, 0);
-    for (int t = lane; t < cnt; t += 32) {
+    int t = lane;
+    for (; t + 96 < cnt; t += 128) {
+      cplx<TV> v[4], w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u] = vi[t + 32 * u];
+        w[u] = w_sm[t + 32 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc.re = fma(v[u].re, w[u].re, fma(v[u].im, w[u].im, acc.re));
+        acc.im = fma(v[u].re, w[u].im, fma(-v[u].im, w[u].re, acc.im));
+      }
+    }
+    for (; t < cnt; t += 32) {
       const cplx<TV> v = vi[t], w = w_sm[t];
       acc.re = fma(v.re, w.re, fma(v.im, w.im, acc.re));
       acc.im = fma(v.re, w.im, fma(-v.im, w.re, acc.im));
@@ -181,7 +195,6 @@ __device__ void reduce_dots(const KPtr& P, int j, int r, c128* __restrict__ dst,
     const c128 v = sum_partials_c(part + i, P.restart + 1, nchunk, lane);
     if (lane == 0) dst[(int64_t)r * (P.restart + 1) + i] = v;
   }
-  if (threadIdx.x == 0) P.counter[r] = 0;
 }
 
 // Row descriptor of the stored matrix E: first value, first column-map entry, row length.
@@ -192,24 +205,34 @@ struct alignas(16) RowInfo {
 };
 
 // Normalise, multiply by A = I + E and take the first Gram-Schmidt dots, over one chunk of rows
-// (P.schunk rows, a multiple of 32).  Eight lanes share a scalar row; the 32 row groups of the
-// CTA take the chunk's rows in turn, with their descriptors loaded up front.
-template <typename TV>
+// (P.schunk rows, a multiple of 32) and a block of RB right-hand sides that share every read of E.
+// Eight lanes share a scalar row; the 32 row groups of the CTA take the chunk's rows in turn, with
+// their descriptors loaded up front.
+template <typename TV, int RB>
 __global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restrict__ rinfo,
                                                 const int32_t* __restrict__ colmap, const cplx<TV>* __restrict__ E,
                                                 cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
                                                 cplx<TV>* __restrict__ V) {
   if (P.st->cycle_done) return;
-  const int j = P.st->j, r = blockIdx.y;
+  const int j = P.st->j, rblk = blockIdx.y;
+  const int r0 = rblk * RB;
+  const int nr = min(RB, P.R - r0);
   const int64_t N = P.N;
   const int64_t n0 = (int64_t)blockIdx.x * P.schunk;
   const int cnt = (int)min((int64_t)P.schunk, N - n0);
-  const cplx<TV>* src = ((j & 1) ? W1 : W0) + (int64_t)r * N;
-  cplx<TV>* dst = ((j & 1) ? W0 : W1) + (int64_t)r * N;
-  const bool act = P.active[r];
-  const TV s = (TV)P.inv_h[r];
+  const cplx<TV>* src = ((j & 1) ? W1 : W0);
+  cplx<TV>* dst = ((j & 1) ? W0 : W1);
+  bool act[RB];
+  TV sc[RB];
+  bool any = false;
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    act[b] = b < nr && P.active[r0 + b];
+    sc[b] = b < nr ? (TV)P.inv_h[r0 + b] : TV(0);
+    any |= act[b];
+  }
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
+  cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);  // [RB][schunk]
   const int g = threadIdx.x / kG, sub = threadIdx.x % kG;
   constexpr int kMaxRowsPerGroup = 4;
   RowInfo ri[kMaxRowsPerGroup];
@@ -222,28 +245,142 @@ __global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restric
   for (int t = 0; t < kMaxRowsPerGroup; ++t) {
     const int row = g + 32 * t;
     if (32 * t >= cnt) break;  // uniform across the CTA
-    cplx<TV> acc = mkc<TV>(0, 0);
-    if (act) {
+    cplx<TV> acc[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) acc[b] = mkc<TV>(0, 0);
+    if (any) {
       const int32_t* cm = colmap + ri[t].cmb;
-      for (int c = sub; c < ri[t].K; c += kG) cfma(acc, E[ri[t].vb + c], src[cm[c]]);
+      for (int c = sub; c < ri[t].K; c += kG) {
+        const cplx<TV> e = E[ri[t].vb + c];
+        const int64_t col = cm[c];
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+          if (b < nr) cfma(acc[b], e, src[(int64_t)(r0 + b) * N + col]);
+      }
     }
 #pragma unroll
-    for (int o = kG / 2; o > 0; o >>= 1) {
-      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
-      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    for (int b = 0; b < RB; ++b) {
+#pragma unroll
+      for (int o = kG / 2; o > 0; o >>= 1) {
+        acc[b].re += __shfl_xor_sync(0xffffffffu, acc[b].re, o);
+        acc[b].im += __shfl_xor_sync(0xffffffffu, acc[b].im, o);
+      }
     }
     if (row < cnt && sub == 0) {
       const int64_t n = n0 + row;
-      const cplx<TV> x = act ? s * src[n] : mkc<TV>(0, 0);
-      const cplx<TV> y = act ? x + s * acc : mkc<TV>(0, 0);
-      V[((int64_t)j * P.R + r) * N + n] = x;
-      dst[n] = y;
-      w_sm[row] = y;
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        if (b >= nr) break;
+        const int64_t off_r = (int64_t)(r0 + b) * N;
+        const cplx<TV> x = act[b] ? sc[b] * src[off_r + n] : mkc<TV>(0, 0);
+        const cplx<TV> y = act[b] ? x + sc[b] * acc[b] : mkc<TV>(0, 0);
+        V[((int64_t)j * P.R + r0 + b) * N + n] = x;
+        dst[off_r + n] = y;
+        w_sm[b * P.schunk + row] = y;
+      }
     }
   }
   __syncthreads();
-  cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nschunk + blockIdx.x) * (P.restart + 1));
-  if (last_cta(P, r)) reduce_dots(P, j, r, P.hc, P.nschunk);
+  for (int b = 0; b < nr; ++b)
+    cta_dots<TV>(P, j, r0 + b, V, w_sm + b * P.schunk, n0, cnt,
+                 P.part + ((int64_t)(r0 + b) * P.nschunk + blockIdx.x) * (P.restart + 1));
+  if (last_cta(P, rblk)) {
+    for (int b = 0; b < nr; ++b) reduce_dots(P, j, r0 + b, P.hc, P.nschunk);
+    __syncthreads();
+    if (threadIdx.x == 0) P.counter[rblk] = 0;
+  }
+}
+
+// Large-N form of the step, part 1: normalise and multiply by A = I + E, streaming.  One scalar row
+// per group of eight lanes, no shared memory and no barrier, so many rows' loads are in flight.
+template <typename TV, int RB>
+__global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restrict__ rinfo,
+                                                const int32_t* __restrict__ colmap, const cplx<TV>* __restrict__ E,
+                                                cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
+                                                cplx<TV>* __restrict__ V) {
+  if (P.st->cycle_done) return;
+  const int j = P.st->j;
+  const int r0 = blockIdx.y * RB;
+  const int nr = min(RB, P.R - r0);
+  const int64_t N = P.N;
+  const int64_t n = (blockIdx.x * (int64_t)kRows + threadIdx.x) / kG;
+  const int sub = threadIdx.x % kG;
+  const cplx<TV>* src = ((j & 1) ? W1 : W0);
+  cplx<TV>* dst = ((j & 1) ? W0 : W1);
+  bool act[RB];
+  TV sc[RB];
+  bool any = false;
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    act[b] = b < nr && P.active[r0 + b];
+    sc[b] = b < nr ? (TV)P.inv_h[r0 + b] : TV(0);
+    any |= act[b];
+  }
+  cplx<TV> acc[RB];
+#pragma unroll
+  for (int b = 0; b < RB; ++b) acc[b] = mkc<TV>(0, 0);
+  if (n < N && any) {
+    const RowInfo ri = rinfo[n];
+    const int32_t* cm = colmap + ri.cmb;
+    int c = sub;
+    for (; c + kG < ri.K; c += 2 * kG) {
+      const cplx<TV> e0 = E[ri.vb + c], e1 = E[ri.vb + c + kG];
+      const int64_t c0 = cm[c], c1 = cm[c + kG];
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+        if (b < nr) {
+          const cplx<TV>* x = src + (int64_t)(r0 + b) * N;
+          const cplx<TV> x0 = x[c0], x1 = x[c1];
+          cfma(acc[b], e0, x0);
+          cfma(acc[b], e1, x1);
+        }
+    }
+    if (c < ri.K) {
+      const cplx<TV> e0 = E[ri.vb + c];
+      const int64_t c0 = cm[c];
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+        if (b < nr) cfma(acc[b], e0, src[(int64_t)(r0 + b) * N + c0]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+#pragma unroll
+    for (int o = kG / 2; o > 0; o >>= 1) {
+      acc[b].re += __shfl_xor_sync(0xffffffffu, acc[b].re, o);
+      acc[b].im += __shfl_xor_sync(0xffffffffu, acc[b].im, o);
+    }
+  }
+  if (n < N && sub == 0) {
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      if (b >= nr) break;
+      const int64_t off_r = (int64_t)(r0 + b) * N;
+      const cplx<TV> x = act[b] ? sc[b] * src[off_r + n] : mkc<TV>(0, 0);
+      V[((int64_t)j * P.R + r0 + b) * N + n] = x;
+      dst[off_r + n] = act[b] ? x + sc[b] * acc[b] : mkc<TV>(0, 0);
+    }
+  }
+}
+
+// Large-N form of the step, part 2: h = V^H w over chunks of rows (first Gram-Schmidt pass).
+template <typename TV>
+__global__ void __launch_bounds__(kRows) k_dots_big(KPtr P, cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
+                                                    const cplx<TV>* __restrict__ V) {
+  if (P.st->cycle_done) return;
+  const int j = P.st->j, r = blockIdx.y;
+  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
+  const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
+  const cplx<TV>* w = ((j & 1) ? W0 : W1) + (int64_t)r * P.N + n0;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
+  for (int t = threadIdx.x; t < cnt; t += kRows) w_sm[t] = w[t];
+  __syncthreads();
+  cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nchunk + blockIdx.x) * (P.restart + 1));
+  if (last_cta(P, r)) {
+    reduce_dots(P, j, r, P.hc, P.nchunk);
+    if (threadIdx.x == 0) P.counter[r] = 0;
+  }
 }
 
 // w -= sum_i V_i h_i over the CTA's rows; result kept in shared memory and written back.
@@ -280,7 +417,10 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
   cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
   cta_update<TV>(P, j, r, V, P.hc, w, w_sm, n0, cnt);
   cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nchunk + blockIdx.x) * (P.restart + 1));
-  if (last_cta(P, r)) reduce_dots(P, j, r, P.hc2, P.nchunk);
+  if (last_cta(P, r)) {
+    reduce_dots(P, j, r, P.hc2, P.nchunk);
+    if (threadIdx.x == 0) P.counter[r] = 0;
+  }
 }
 
 // Second update, norm, and (last CTA) the Hessenberg column, Givens rotation and residual.
@@ -619,11 +759,16 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   const cplx<TV>* Bv = (const cplx<TV>*)ctx->Bv;
   const dim3 g_rows((unsigned)ceil_div(N * kG, kRows), R);
   const dim3 g_chunk((unsigned)P.nchunk, R);
-  const dim3 g_schunk((unsigned)P.nschunk, R);
+  constexpr int kRB = 8;
+  const bool multi = R > 1;
+  // large systems: streaming product and separate dots (bandwidth); small: one fused kernel (latency)
+  const bool split = N >= ctx->split_rows;
+  const dim3 g_schunk((unsigned)P.nschunk, multi ? (unsigned)ceil_div(R, kRB) : 1u);
   const size_t sm = sizeof(cplx<TV>) * P.chunk;
-  const size_t ssm = sizeof(cplx<TV>) * P.schunk;
+  const size_t ssm = sizeof(cplx<TV>) * P.schunk * (multi ? kRB : 1);
   if (sm > 48 * 1024) {
     SWM_CK(cudaFuncSetAttribute(k_update<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SWM_CK(cudaFuncSetAttribute(k_dots_big<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SWM_CK(cudaFuncSetAttribute(k_finish<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   }
   // back substitution stages the triangle in shared memory when it fits
@@ -644,8 +789,24 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   auto launch_steps = [&](cudaStream_t s, int n) -> int {
     for (int i = 0; i < n; ++i) {
       ctx->prof_begin(SWM_K_APPLY);
-      k_step<TV><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
-      ctx->prof_end(SWM_K_APPLY);
+      if (split) {
+        const dim3 gsp((unsigned)ceil_div(N * kG, kRows), multi ? (unsigned)ceil_div(R, kRB) : 1u);
+        if (multi)
+          k_spmv<TV, kRB><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+        else
+          k_spmv<TV, 1><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+        ctx->prof_end(SWM_K_APPLY);
+        SWM_LAUNCHED();
+        ctx->prof_begin(SWM_K_DOTS);
+        k_dots_big<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
+        ctx->prof_end(SWM_K_DOTS);
+      } else if (multi) {
+        k_step<TV, kRB><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+        ctx->prof_end(SWM_K_APPLY);
+      } else {
+        k_step<TV, 1><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+        ctx->prof_end(SWM_K_APPLY);
+      }
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_UPDATE);
       k_update<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
@@ -661,8 +822,8 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   // A chunk of Arnoldi steps is a CUDA graph (the launches are identical every step), captured on
   // a private stream and reused while the kernel arguments stay the same.  Profiling a GMRES kernel
   // class uses direct launches so its events time each launch.
-  const bool use_graph = ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_UPDATE &&
-                         ctx->prof_cls != SWM_K_FINISH;
+  const bool use_graph = ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_DOTS &&
+                         ctx->prof_cls != SWM_K_UPDATE && ctx->prof_cls != SWM_K_FINISH;
   if (use_graph) {
     struct Key {
       KPtr P;

@@ -221,3 +221,19 @@ def test_invalid_inputs_rejected():
     with pytest.raises(swm.SwmError):
         swm.swm_solve(ctx, [[0.0, 0.0, 0.0]], restart=0)
     swm.swm_destroy(ctx)
+
+
+def test_split_step_path_matches_oracle(monkeypatch):
+    """The large-system form of the GMRES step (streaming product + separate dots), forced on a
+    small system, against the oracle's LU solution, for one and for several incidences."""
+    monkeypatch.setenv("SWM_SPLIT_ROWS", "0")
+    cl = cloud_uniform_cube(80, 5.0, seed=43)
+    obs = observations_phi_cut(60)
+    for inc in (np.array([[0.2, 0.1, 0.0]]), np.array([[0.0, 0.0, 0.0], [1.1, 0.7, 0.5], [2.5, 4.0, 1.2]] * 3)):
+        for prec, tol in ((C128, 1e-5), (C64, 1e-3)):
+            out = run_gpu(cl, K, 1.5, prec, inc, obs=obs, tol=1e-11 if prec == C128 else 1e-6)
+            X = O.solve_lu(O.assemble(cl, K, 1.5, sparse=False), O.rhs(cl, K, inc))
+            assert np.linalg.norm(out["currents"] - X) / np.linalg.norm(X) < tol
+            s_ref = O.rcs_bistatic(cl, K, X, obs)
+            for i in range(inc.shape[0]):
+                assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
