@@ -522,6 +522,177 @@ __global__ void __launch_bounds__(kFillThreads, sizeof(R) == 4 ? 3 : 1) k_mutual
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// mutual blocks, float32 path without CTA barriers: each warp takes a batch of kWarpBlocks blocks.
+// Lanes 0..kWarpBlocks-1 set up one block each (float32 geometry from a float64 centre difference;
+// the exact float64 segment distance only when the wires may be near), then every lane evaluates
+// segment pairs and adds each pair's four contributions straight into the block's entries in shared
+// memory, and finally the warp writes Z_pq and Z_qp = Z_pq^T.
+
+constexpr int kWarpBlocks = 8;
+constexpr int kFillF32Threads = 256;
+
+struct WarpGeo {
+  float D[3], tp[3], tq[3];
+  float Lp, Lq, a2, tpq, f, sc;
+  int nsp, nsq, nq, item0, acc0;
+  int Kp, Kq;
+  int64_t bpq, bqp;
+};
+
+__global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
+    int64_t nup, const int64_t* __restrict__ ublk, const int32_t* __restrict__ col, const int64_t* __restrict__ bt,
+    const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
+    const double* __restrict__ tx, const double* __restrict__ ty, const double* __restrict__ tz,
+    const double* __restrict__ Ls, const double* __restrict__ as, const int32_t* __restrict__ ns, double k,
+    GLTable gl, Layout lay, int acc_per_block, c64* __restrict__ Z, unsigned long long* __restrict__ evals) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float xs4[4], ws4[4], xs8[8], ws8[8];
+  __shared__ WarpGeo geo_all[kFillF32Threads / 32][kWarpBlocks];
+  __shared__ int pre_all[kFillF32Threads / 32][kWarpBlocks + 1];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  if (threadIdx.x < 4) {
+    xs4[threadIdx.x] = (float)gl.x4[threadIdx.x];
+    ws4[threadIdx.x] = (float)gl.w4[threadIdx.x];
+  }
+  if (threadIdx.x < 8) {
+    xs8[threadIdx.x] = (float)gl.x8[threadIdx.x];
+    ws8[threadIdx.x] = (float)gl.w8[threadIdx.x];
+  }
+  __syncthreads();  // the only CTA-wide barrier: the quadrature tables
+  WarpGeo* geo = geo_all[wl];
+  int* pre = pre_all[wl];
+  float2* acc = reinterpret_cast<float2*>(smem) + (size_t)wl * kWarpBlocks * acc_per_block;
+  const int64_t b0 = ((int64_t)blockIdx.x * (kFillF32Threads / 32) + wl) * kWarpBlocks;
+  if (b0 >= nup) return;  // whole warp
+  const int nb_here = (int)min((int64_t)kWarpBlocks, nup - b0);
+  const float kf = (float)k;
+  // --- set-up, one lane per block
+  int items = 0;
+  unsigned long long ev = 0;
+  if (lane < nb_here) {
+    const int64_t b = ublk[b0 + lane];
+    const int q = col[b];
+    const int64_t bq = bt[b];
+    const int p = col[bq];
+    WarpGeo G;
+    const double Dd[3] = {cx[p] - cx[q], cy[p] - cy[q], cz[p] - cz[q]};
+    const double tpd[3] = {tx[p], ty[p], tz[p]}, tqd[3] = {tx[q], ty[q], tz[q]};
+    for (int c = 0; c < 3; ++c) {
+      G.D[c] = (float)Dd[c];
+      G.tp[c] = (float)tpd[c];
+      G.tq[c] = (float)tqd[c];
+    }
+    const int nsp = ns[p], nsq = ns[q];
+    G.Lp = (float)Ls[p];
+    G.Lq = (float)Ls[q];
+    const float Dp = G.Lp / nsp, Dq = G.Lq / nsq;
+    const float ap = (float)as[p], aq = (float)as[q];
+    G.a2 = 0.5f * (ap * ap + aq * aq);
+    G.tpq = G.tp[0] * G.tq[0] + G.tp[1] * G.tq[1] + G.tp[2] * G.tq[2];
+    G.f = Dp * Dq * (float)(1.0 / kFourPi);
+    G.sc = 1.0f / (kf * kf * Dp * Dq);
+    // near rule, decided in float64 like the reference: only when the wires may come within
+    // the longer segment length (the float32 screen has a wide margin)
+    const float dmax = fmaxf(Dp, Dq);
+    const float reach = 0.5f * (G.Lp + G.Lq) + dmax;
+    const float cd2 = G.D[0] * G.D[0] + G.D[1] * G.D[1] + G.D[2] * G.D[2];
+    int nq = 4;
+    if (cd2 < reach * reach * 1.001f + 1e-6f) {
+      const double Lpd = Ls[p], Lqd = Ls[q];
+      const double dmaxd = fmax(Lpd / nsp, Lqd / nsq);
+      if (seg_dist(Dd, tpd, 0.5 * Lpd, tqd, 0.5 * Lqd) < dmaxd) nq = 8;
+    }
+    G.nsp = nsp;
+    G.nsq = nsq;
+    G.nq = nq;
+    G.Kp = lay.K[p];
+    G.Kq = lay.K[q];
+    G.bpq = lay.rowbase[p] + lay.colpos[b];
+    G.bqp = lay.rowbase[q] + lay.colpos[bq];
+    items = nsp * nsq;
+    ev = (unsigned long long)items * nq * nq;
+    geo[lane] = G;
+  }
+  // prefix of items over the batch
+  int incl = items;
+#pragma unroll
+  for (int o = 1; o < kWarpBlocks; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane < kWarpBlocks) pre[lane + 1] = incl;
+  if (lane == 0) pre[0] = 0;
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+  if (lane == 0) atomicAdd(evals, ev);
+  // clear the accumulators of the batch
+  for (int e = lane; e < kWarpBlocks * acc_per_block; e += 32) acc[e] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const int nitems = pre[nb_here];
+  for (int it = lane; it < nitems; it += 32) {
+    int bl = 0;
+    while (pre[bl + 1] <= it) ++bl;
+    const WarpGeo& G = geo[bl];
+    const int local = it - pre[bl];
+    const int u = local / G.nsq, v = local % G.nsq;
+    BlockGeo B;
+    for (int c = 0; c < 3; ++c) {
+      B.D[c] = G.D[c];
+      B.tp[c] = G.tp[c];
+      B.tq[c] = G.tq[c];
+    }
+    B.Lp = G.Lp;
+    B.Lq = G.Lq;
+    B.a2 = G.a2;
+    B.nsp = G.nsp;
+    B.nsq = G.nsq;
+    SegI<float> S;
+    if (G.nq == 4)
+      seg_pair_f32<4>(B, u, v, kf, xs4, ws4, S);
+    else
+      seg_pair_f32<8>(B, u, v, kf, xs8, ws8, S);
+    const c64 IG = S.rr + S.rf + S.fr + S.ff;
+    // segment u rises for basis u and falls for basis u - 1 (same on wire q with v)
+    const int mp = G.nsp - 1, mq = G.nsq - 1;
+    float2* A = acc + bl * acc_per_block;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int i = a == 0 ? u : u - 1;
+      if (i < 0 || i >= mp) continue;
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb) {
+        const int jj = bb == 0 ? v : v - 1;
+        if (jj < 0 || jj >= mq) continue;
+        const c64 I = a == 0 ? (bb == 0 ? S.rr : S.rf) : (bb == 0 ? S.fr : S.ff);
+        const float sgn = (a == bb) ? 1.f : -1.f;
+        const float re = G.f * (G.tpq * I.re - G.sc * sgn * IG.re);
+        const float im = G.f * (G.tpq * I.im - G.sc * sgn * IG.im);
+        atomicAdd(&A[i * mq + jj].x, re);
+        atomicAdd(&A[i * mq + jj].y, im);
+      }
+    }
+  }
+  __syncwarp();
+  // write Z_pq and Z_qp = Z_pq^T
+  int outs[kWarpBlocks + 1];
+  outs[0] = 0;
+#pragma unroll
+  for (int bl = 0; bl < kWarpBlocks; ++bl)
+    outs[bl + 1] = outs[bl] + (bl < nb_here ? (geo[bl].nsp - 1) * (geo[bl].nsq - 1) : 0);
+  for (int e = lane; e < outs[nb_here]; e += 32) {
+    int bl = 0;
+    while (outs[bl + 1] <= e) ++bl;
+    const WarpGeo& G = geo[bl];
+    const int mq = G.nsq - 1;
+    const int local = e - outs[bl];
+    const int i = local / mq, jj = local % mq;
+    const float2 z = acc[bl * acc_per_block + i * mq + jj];
+    const c64 zc = mkc(z.x, z.y);
+    Z[G.bpq + (int64_t)i * G.Kp + jj] = zc;
+    Z[G.bqp + (int64_t)jj * G.Kq + i] = zc;
+  }
+}
+
 template <typename R, typename TV>
 int launch_fill(swm_ctx* ctx, const GLTable& gl, unsigned long long* evals) {
   const int ms = ctx->max_ns;
@@ -564,10 +735,22 @@ int fill_blocks(swm_ctx* ctx) {
         nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b, ctx->full, S, reinterpret_cast<c64*>(ctx->Z));
   ctx->prof_end(SWM_K_FILL_SELF);
   SWM_LAUNCHED();
-  if (ctx->prec == SWM_C128)
+  if (ctx->prec == SWM_C128) {
     SWM_TRY((launch_fill<double, double>(ctx, gl, ctx->d_evals)));
-  else
-    SWM_TRY((launch_fill<float, float>(ctx, gl, ctx->d_evals)));
+  } else if (ctx->nup > 0) {
+    const int mm = ctx->max_ns - 1;
+    const int acc_per_block = std::max(1, mm * mm);
+    const size_t smem = sizeof(float2) * (size_t)(kFillF32Threads / 32) * kWarpBlocks * acc_per_block;
+    if (smem > 48 * 1024)
+      SWM_CK(cudaFuncSetAttribute(k_mutual_blocks_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks_per_cta = (int64_t)(kFillF32Threads / 32) * kWarpBlocks;
+    ctx->prof_begin(SWM_K_FILL_MUTUAL);
+    k_mutual_blocks_f32<<<(unsigned)ceil_div(ctx->nup, blocks_per_cta), kFillF32Threads, smem, ctx->stream>>>(
+        ctx->nup, ctx->ublk, ctx->col, ctx->bt, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->a,
+        ctx->ns, ctx->k, gl, ctx->full, acc_per_block, reinterpret_cast<c64*>(ctx->Z), ctx->d_evals);
+    ctx->prof_end(SWM_K_FILL_MUTUAL);
+    SWM_LAUNCHED();
+  }
   return SWM_OK;
 }
 
