@@ -139,6 +139,30 @@ def cpu_baseline(n_wires=1000):
                       f"single-threaded NumPy"}
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per working launch, mid workload, from ncu
+MEASURED_TRAFFIC = {("apply", "c64"): 7.0e6}
+
+
+# ---------------------------------------------------------------------------------- ranks
+def rank_seed(rank: int) -> int:
+    """Each rank solves its own cloud of the same statistics (weak scaling): seed 1 + rank."""
+    return 1 + rank
+
+
+def aggregate_over_ranks(times_ms, units, device, world):
+    """Max of each time over the ranks and the sum of the units they processed (whole-job
+    throughput = summed units / slowest rank).  A timing reduction only: no solver data moves."""
+    import torch
+    import torch.distributed as dist
+
+    tm = torch.tensor([float(t) for t in times_ms], dtype=torch.float64, device=device)
+    un = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(un, op=dist.ReduceOp.SUM)
+    return tm.tolist(), un.item()
+
+
 # ---------------------------------------------------------------------------------- our arm
 def kernel_roofline(cls, st, prof_ms, launches, prec, n_rhs, pk, clocks):
     """Achieved algorithmic rate of one kernel class over the timed region."""
@@ -185,7 +209,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prec_id = swm.SWM_C64 if args.precision == "c64" else swm.SWM_C128
-    cl = cloud_mid(seed=1 + rank)
+    cl = cloud_mid(seed=rank_seed(rank))
     inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
     N = cl.n_unknowns
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
@@ -279,13 +303,8 @@ def run_ours(args):
     swm.swm_destroy(ctx)
 
     # max over ranks, units over all ranks
-    tm = torch.tensor([ms_step, e2e_ms, ms64], dtype=torch.float64, device="cuda")
-    units = torch.tensor([float(N)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        dist.all_reduce(units, op=dist.ReduceOp.SUM)
-    ms_step, e2e_ms, ms64 = tm.tolist()
-    total_units = units.item() * inc.shape[0]
+    (ms_step, e2e_ms, ms64), total_units = aggregate_over_ranks([ms_step, e2e_ms, ms64], N * inc.shape[0],
+                                                                "cuda", world)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -305,7 +324,9 @@ def run_ours(args):
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["peak_source"] = "of measured (MEASURED_PEAKS.json)" if roof["unit"] == "GB/s" else roof.get("note")
     if roof is not None:
-        roof["traffic"] = None
+        # DRAM bytes per launch from one ncu capture of this kernel at this workload
+        # (profiles/k_step_mid_traffic.md); null for a kernel without a capture of its current code
+        roof["traffic"] = MEASURED_TRAFFIC.get((dominant, args.precision))
         roof["kernel"] = dominant
     out = {
         "metric": METRIC, "value": total_units / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world,

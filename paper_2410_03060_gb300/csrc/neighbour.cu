@@ -326,8 +326,9 @@ int build_pattern(swm_ctx* ctx) {
   };
   int64_t nx, ny, nz;
   dims(g.h, nx, ny, nz);
-  // at most about four cells per wire (larger cells only add candidates to the distance test)
-  const double max_cells = std::min<double>((double)kMaxCells, std::max<double>(4096.0, 4.0 * (double)nw));
+  // at most 64 cells per wire (larger cells only add candidates to the distance test, more cells
+  // only add empty ones to scan)
+  const double max_cells = std::min<double>((double)kMaxCells, std::max<double>(4096.0, 64.0 * (double)nw));
   while ((double)nx * (double)ny * (double)nz > max_cells) {
     g.h *= 1.05 * std::cbrt((double)nx * ny * nz / max_cells);
     dims(g.h, nx, ny, nz);

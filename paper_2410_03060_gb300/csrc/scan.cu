@@ -149,11 +149,12 @@ struct MultiScanArgs {
   int narr;
 };
 
-// Several exclusive scans of the same short length in one CTA.
+// Several exclusive scans of the same short length, one CTA per array.
 __global__ void k_scan_multi(MultiScanArgs a, int64_t n) {
   const int64_t per = ceil_div(n, kScanThreads);
   const int64_t b = threadIdx.x * per, e = min(n, b + per);
-  for (int k = 0; k < a.narr; ++k) {
+  {
+    const int k = blockIdx.x;
     const int64_t* i64 = (const int64_t*)a.in[k];
     const int32_t* i32 = (const int32_t*)a.in[k];
     int64_t s = 0;
@@ -182,7 +183,7 @@ int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const in
       a.is64[k] = is64[k];
       a.out[k] = out[k];
     }
-    k_scan_multi<<<1, kScanThreads, 0, ctx->stream>>>(a, n);
+    k_scan_multi<<<narr, kScanThreads, 0, ctx->stream>>>(a, n);
     SWM_LAUNCHED();
     return SWM_OK;
   }
