@@ -180,6 +180,18 @@ def kernel_roofline(cls, st, prof_ms, launches, prec, n_rhs, pk, clocks):
         work = per_solve * st["_cycles_mult"]
         return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
                 "unit": "GB/s", "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms}
+    if cls == "gmres":
+        # the persistent solve, one launch per solve.  Per Arnoldi step j: E values + column map +
+        # row descriptors, the gathered and written vectors, V_j, and two Gram-Schmidt passes over
+        # V_0..V_j; per restart cycle: the residual product and the update of y by the basis.
+        mat = st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N
+        vec = N * esz * n_rhs
+        per_solve = sum(mat + 3 * vec + 2 * (j + 1) * vec for j in st["_steps"])
+        per_solve += (st["restarts"] + 1) * (mat + 3 * vec) + sum(st["_cycle_len"]) * vec
+        work = per_solve * st["_cycles_mult"]
+        return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
+                "unit": "GB/s", "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms,
+                "note": "latency-bound at this size (E and the basis stay on chip or in L2)"}
     if cls in ("dots", "update", "finish"):
         vec = N * esz * n_rhs
         work = sum((j + 1) * vec + 2 * vec for j in st["_steps"]) * st["_cycles_mult"]
@@ -236,7 +248,8 @@ def run_ours(args):
     err_db = rcs_db_error(s_fast, sig64.cpu().numpy()[0, :, 0])
 
     # dominant kernel class: one profiled step per class (untimed)
-    classes = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "rhs", "apply", "update", "finish", "far"]
+    classes = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "rhs", "apply", "update", "finish", "far",
+               "gmres"]
     share = {}
     for c in classes:
         swm.swm_profile(ctx, c)
@@ -312,12 +325,14 @@ def run_ours(args):
     pk = peaks()
     # reconstruct the Arnoldi step indices of one solve for the Gram-Schmidt byte counts
     it = st["iterations"]
-    steps_j = []
+    steps_j, cycle_len = [], []
     while it > 0:
         c = min(RESTART, it)
         steps_j += list(range(c))
+        cycle_len.append(c)
         it -= c
     st["_steps"] = steps_j
+    st["_cycle_len"] = cycle_len
     st["_cycles_mult"] = args.steps
     roof = kernel_roofline(dominant, st, prof_ms, prof_n, args.precision, 1, pk, clk)
     if roof and roof.get("peak"):

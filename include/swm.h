@@ -65,6 +65,8 @@ extern "C" {
 #define SWM_ENOMEM (-2) /* device allocation failed */
 #define SWM_ECUDA (-3)  /* a CUDA runtime call or kernel failed */
 #define SWM_ESTATE (-4) /* call out of order (e.g. solve before build) */
+#define SWM_ETIMEOUT (-5) /* a bounded device-side wait ran out (grid barrier of the persistent
+                             GMRES kernel, limit 1 s); the context stays usable */
 
 /* memory kinds */
 #define SWM_HOST 0
@@ -121,12 +123,17 @@ typedef struct swm_stats {
 #define SWM_K_UPDATE 9      /* second Gram-Schmidt pass */
 #define SWM_K_FINISH 10     /* norm, Hessenberg column, rotation */
 #define SWM_K_FAR 11        /* far field: partial sums and their reduction to RCS */
+#define SWM_K_GMRES 12      /* the whole solve as one persistent cooperative kernel (systems below
+                               SWM_SPLIT_ROWS unknowns with at most 8 right-hand sides); the
+                               per-step classes 7-10 then launch nothing */
 
 /* Create a context on CUDA device `device` that issues all work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context.
  * Environment: SWM_SPLIT_ROWS (default 524288) -- systems with at least this many unknowns run
  * each GMRES step as a streaming block-sparse product plus separate dot products, smaller ones
- * as one fused kernel; read when the context is created. */
+ * as one fused kernel; SWM_PERSIST (default 1) -- 0 solves small systems with one launch per
+ * kernel of each GMRES step instead of the persistent cooperative kernel; both read when the
+ * context is created. */
 int swm_create(swm_ctx** out, int device, void* cuda_stream);
 
 /* Free every device buffer of the context and the context itself.  NULL is ignored. */

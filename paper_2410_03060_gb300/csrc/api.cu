@@ -149,7 +149,12 @@ int swm_create(swm_ctx** out, int device, void* cuda_stream) {
   ctx->device = device;
   ctx->stream = (cudaStream_t)cuda_stream;
   if (const char* e = std::getenv("SWM_SPLIT_ROWS")) ctx->split_rows = std::max<long long>(0, std::atoll(e));
-  if (cudaSetDevice(device) != cudaSuccess) {
+  if (const char* e = std::getenv("SWM_PERSIST")) ctx->persist = std::atoi(e) != 0;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+    cudaGetLastError();
     delete ctx;
     return SWM_ECUDA;
   }
@@ -427,7 +432,7 @@ int swm_get_stats(const swm_ctx* ctx, swm_stats* out) {
 
 int swm_profile(swm_ctx* ctx, int kernel_class) {
   if (!ctx) return SWM_EINVAL;
-  if (kernel_class < SWM_K_NONE || kernel_class > SWM_K_FAR) return ctx->fail(SWM_EINVAL, "bad kernel class");
+  if (kernel_class < SWM_K_NONE || kernel_class > SWM_K_GMRES) return ctx->fail(SWM_EINVAL, "bad kernel class");
   SWM_TRY(set_device(ctx));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->prof_flush();

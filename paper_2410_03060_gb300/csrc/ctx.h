@@ -127,6 +127,15 @@ struct swm_ctx {
   // systems with at least this many unknowns run the Arnoldi step as a streaming product plus
   // separate dots (bandwidth); smaller ones as one fused kernel (latency).  SWM_SPLIT_ROWS overrides.
   int64_t split_rows = int64_t(1) << 19;
+  // systems below split_rows with at most 8 right-hand sides solve in one persistent cooperative
+  // kernel (SWM_PERSIST=0 turns it off); SM count and cooperative-launch support of the device
+  bool persist = true;
+  int nsm = 0;
+  int coop = 0;
+  int smem_optin = 0;  // shared memory a CTA may opt in to (bytes)
+  // chunk size of the persistent solve and the largest E / column-map slice of a chunk
+  int pslice_rows = -1;
+  int64_t pslice_e = 0, pslice_c = 0;
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   swm::Layout full, offd;
   void* Z = nullptr;     // values of Z in layout `full`

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 SWM_OK, SWM_ENOTCONV = 0, 1
-SWM_EINVAL, SWM_ENOMEM, SWM_ECUDA, SWM_ESTATE = -1, -2, -3, -4
+SWM_EINVAL, SWM_ENOMEM, SWM_ECUDA, SWM_ESTATE, SWM_ETIMEOUT = -1, -2, -3, -4, -5
 SWM_HOST, SWM_DEVICE = 0, 1
 SWM_C128, SWM_C64 = 0, 1
 SWM_MAX_SEG = 16
@@ -241,7 +241,7 @@ def swm_get_stats(ctx: Ctx) -> dict:
 
 
 SWM_K = {"none": 0, "pairs": 1, "fill_self": 2, "fill_mutual": 3, "invert": 4, "form_e": 5, "rhs": 6,
-         "apply": 7, "dots": 8, "update": 9, "finish": 10, "far": 11}
+         "apply": 7, "dots": 8, "update": 9, "finish": 10, "far": 11, "gmres": 12}
 
 
 def swm_profile(ctx: Ctx, kernel_class) -> int:

@@ -237,3 +237,50 @@ def test_split_step_path_matches_oracle(monkeypatch):
             s_ref = O.rcs_bistatic(cl, K, X, obs)
             for i in range(inc.shape[0]):
                 assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
+
+
+def test_per_kernel_step_path_matches_oracle(monkeypatch):
+    """With the persistent solve turned off, small systems run one launch per kernel of each GMRES
+    step (fused product and first dots, second pass, finish); same check as above."""
+    monkeypatch.setenv("SWM_PERSIST", "0")
+    cl = cloud_uniform_cube(80, 5.0, seed=44)
+    obs = observations_phi_cut(60)
+    for inc in (np.array([[0.2, 0.1, 0.0]]), np.array([[0.0, 0.0, 0.0], [1.1, 0.7, 0.5], [2.5, 4.0, 1.2]] * 3)):
+        for prec, tol in ((C128, 1e-5), (C64, 1e-3)):
+            out = run_gpu(cl, K, 1.5, prec, inc, obs=obs, tol=1e-11 if prec == C128 else 1e-6)
+            X = O.solve_lu(O.assemble(cl, K, 1.5, sparse=False), O.rhs(cl, K, inc))
+            assert np.linalg.norm(out["currents"] - X) / np.linalg.norm(X) < tol
+            s_ref = O.rcs_bistatic(cl, K, X, obs)
+            for i in range(inc.shape[0]):
+                assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
+
+
+@pytest.mark.parametrize("n_inc", [1, 2, 8])
+def test_persistent_solve_matches_oracle_and_launches_once(n_inc):
+    """The persistent cooperative solve (default for small systems with at most 8 incidences):
+    currents against the oracle's LU solution, several restart cycles (restart 5), and a single
+    GMRES launch per solve besides the final block-diagonal product."""
+    from paper_2410_03060_gb300 import swm
+
+    cl = cloud_uniform_cube(150, 6.0, seed=45)
+    rng = np.random.default_rng(9)
+    inc = np.stack([rng.uniform(0, np.pi, n_inc), rng.uniform(0, 2 * np.pi, n_inc), rng.uniform(0, np.pi, n_inc)], 1)
+    X = O.solve_lu(O.assemble(cl, K, 2.0, sparse=False), O.rhs(cl, K, inc))
+    for prec, tol in ((C128, 1e-6), (C64, 1e-3)):
+        out = run_gpu(cl, K, 2.0, prec, inc, tol=1e-12 if prec == C128 else 1e-6, restart=5)
+        try:
+            st = out["stats"]
+            assert st["converged"] == 1 and st["restarts"] >= 2
+            assert np.linalg.norm(out["currents"] - X) / np.linalg.norm(X) < tol
+            ctx = out["ctx"]
+            cur = np.zeros((n_inc, X.shape[0]), dtype=np.complex128)
+            l0 = swm.swm_get_stats(ctx)["kernel_launches"]
+            swm.swm_profile(ctx, "gmres")
+            swm.swm_solve(ctx, inc, 1e-12 if prec == C128 else 1e-6, 5, 3000, cur)
+            st2 = swm.swm_get_stats(ctx)
+            swm.swm_profile(ctx, "none")
+            assert st2["prof_launches"] == 1
+            assert st2["iterations"] == st["iterations"]
+            assert np.array_equal(cur.T, out["currents"])  # deterministic
+        finally:
+            swm.swm_destroy(out["ctx"])
