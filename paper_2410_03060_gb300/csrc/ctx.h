@@ -133,9 +133,6 @@ struct swm_ctx {
   int nsm = 0;
   int coop = 0;
   int smem_optin = 0;  // shared memory a CTA may opt in to (bytes)
-  // chunk size of the persistent solve and the largest E / column-map slice of a chunk
-  int pslice_rows = -1;
-  int64_t pslice_e = 0, pslice_c = 0;
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   swm::Layout full, offd;
   void* Z = nullptr;     // values of Z in layout `full`

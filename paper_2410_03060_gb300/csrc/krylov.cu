@@ -1358,18 +1358,6 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
   }
 }
 
-// Largest E and column-map slice over the persistent kernel's chunks of `rows` rows.
-__global__ void k_slice_max(const RowInfo* __restrict__ rinfo, int64_t N, int rows, int G,
-                            unsigned long long* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= G) return;
-  const int64_t n0 = (int64_t)c * rows;
-  const int64_t n1 = min(N, n0 + rows) - 1;
-  const RowInfo f = rinfo[n0], l = rinfo[n1];
-  atomicMax(out, (unsigned long long)(l.vb + l.K - f.vb));
-  atomicMax(out + 1, (unsigned long long)((int64_t)l.cmb + l.K - f.cmb));
-}
-
 template <typename TV>
 int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   cudaStream_t st = ctx->stream;
@@ -1384,7 +1372,6 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     k_rowwire<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, st>>>(ctx->nw, ctx->off, ctx->offd, ctx->rowwire,
                                                                (RowInfo*)ctx->rowinfo);
     SWM_LAUNCHED();
-    ctx->pslice_rows = -1;
   }
   KPtr P{};
   P.R = R;
@@ -1467,35 +1454,27 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   if (ctx->persist && ctx->coop && ws->sync && N > 0 && N < ctx->split_rows &&
       prows <= kPersistMaxRowsPerThread * kPT) {
     const int G = (int)ceil_div(N, prows);
-    if (ctx->pslice_rows != prows) {
-      // largest E and column-map slice of a chunk, for the shared-memory copies
-      unsigned long long* d = nullptr;
-      SWM_TRY(dalloc(ctx, tmp, (void**)&d, 2 * sizeof(unsigned long long)));
-      SWM_CK(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st));
-      k_slice_max<<<(unsigned)ceil_div(G, 128), 128, 0, st>>>((const RowInfo*)ctx->rowinfo, N, prows, G, d);
-      SWM_LAUNCHED();
-      unsigned long long hv[2];
-      SWM_CK(cudaMemcpyAsync(hv, d, sizeof(hv), cudaMemcpyDeviceToHost, st));
-      SWM_CK(cudaStreamSynchronize(st));
-      ctx->pslice_rows = prows;
-      ctx->pslice_e = (int64_t)hv[0];
-      ctx->pslice_c = (int64_t)hv[1];
-    }
     const int RB = R == 1 ? 1 : kPersistMaxR;
     const void* fn = R == 1 ? (const void*)k_gmres_persist<TV, 1> : (const void*)k_gmres_persist<TV, kPersistMaxR>;
     cudaFuncAttributes fa{};
     SWM_CK(cudaFuncGetAttributes(&fa, fn));
     const size_t limit = (size_t)std::max(0, ctx->smem_optin - (int)fa.sharedSizeBytes - 1024);
-    // V and E slices in shared memory when they fit, V first (it is read four times a step)
-    int vsm = 0, esm = 0;
-    size_t smem = 0;
-    bool fits = false;
-    for (int pick = 0; pick < 4 && !fits; ++pick) {
-      vsm = pick < 2 ? 1 : 0;
-      esm = (pick == 0 || pick == 2) ? 1 : 0;
-      smem = persist_layout(RB, R, restart, prows, sizeof(cplx<TV>), vsm, esm, ctx->pslice_e, ctx->pslice_c).total;
-      fits = smem <= limit;
+    const size_t cb = sizeof(cplx<TV>);
+    // V in shared memory when it fits (it is read four times a step); then as large an E slice as
+    // the rest holds (column map + gathered vector about a third of the E entries: the rows of a
+    // wire share their column map).  A CTA whose slice is larger reads E from global memory.
+    int vsm = persist_layout(RB, R, restart, prows, cb, 1, 0, 0, 0).total <= limit ? 1 : 0;
+    const size_t base = persist_layout(RB, R, restart, prows, cb, vsm, 1, 0, 0).total + 64;
+    const int64_t mean_e = ceil_div(ctx->offd.nval, G);
+    int64_t emax = 0, cmax = 0;
+    if (base < limit) {
+      emax = (int64_t)((limit - base) / (cb + (4 + cb * R) / 3.0));
+      cmax = emax / 3;
     }
+    const int esm = emax >= mean_e && emax > 0 ? 1 : 0;
+    if (!esm) emax = cmax = 0;
+    const size_t smem = persist_layout(RB, R, restart, prows, cb, vsm, esm, emax, cmax).total;
+    const bool fits = smem <= limit;
     int occ = 0;
     if (fits) {
       SWM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1520,8 +1499,8 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
       pa.max_iter = max_iter;
       pa.vsm = vsm;
       pa.esm = esm;
-      pa.emax = ctx->pslice_e;
-      pa.cmax = ctx->pslice_c;
+      pa.emax = emax;
+      pa.cmax = cmax;
       SWM_CK(cudaMemsetAsync(ws->sync, 0, sizeof(PSync), st));
       void* args[] = {&pa};
       ctx->prof_begin(SWM_K_GMRES);

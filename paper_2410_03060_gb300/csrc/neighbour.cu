@@ -135,10 +135,24 @@ __global__ void k_uoff_by_internal(int64_t nw, const int32_t* __restrict__ perm,
   if (p < nw) uoff[p] = uoff_user[perm[p]];
 }
 
-// mode 0: count kept partners per wire; mode 1: write them (sorted) into col.
+// Per-row sizes gathered by the counting pass of k_pairs: kept blocks, kept blocks above the
+// diagonal, and the row lengths and entry counts of both layouts (with and without the diagonal
+// block), so that one read-back after one scan sizes every pattern array.
+struct RowCounts {
+  int32_t* cnt;    // kept partners
+  int64_t* ucnt;   // partners q > p
+  int32_t* K_f;    // sum of m_q over kept q
+  int32_t* K_o;    // the same without q = p
+  int64_t* ent_f;  // m_p K_f
+  int64_t* ent_o;  // m_p K_o
+  int64_t* msq;    // m_p^2
+};
+
+// mode 0: count kept partners per wire (and the sizes in RowCounts); mode 1: write them (sorted)
+// into col.
 __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double* __restrict__ cy,
                         const double* __restrict__ cz, const int32_t* __restrict__ cid, const int64_t* __restrict__ cstart,
-                        Grid g, double rc2, int dense, int mode, int32_t* __restrict__ row_cnt,
+                        Grid g, double rc2, int dense, int mode, RowCounts rc, const int32_t* __restrict__ m,
                         const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col) {
   const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -147,6 +161,7 @@ __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double*
   const int ix = id % g.nx, iy = (id / g.nx) % g.ny, iz = id / (g.nx * g.ny);
   const double px = cx[p], py = cy[p], pz = cz[p];
   int64_t count = 0;
+  int32_t msum = 0, nup = 0;  // this lane's kept m_q and kept q > p (counting pass)
   const int64_t base = mode ? row_ptr[p] : 0;
   for (int dz = -1; dz <= 1; ++dz) {
     const int z = iz + dz;
@@ -173,11 +188,31 @@ __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double*
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (mode && keep) col[base + count + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
+        if (!mode && keep) {
+          msum += m[q];
+          nup += q > p ? 1 : 0;
+        }
         count += __popc(bal);
       }
     }
   }
-  if (!mode && lane == 0) row_cnt[p] = (int32_t)count;
+  if (!mode) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      msum += __shfl_xor_sync(0xffffffffu, msum, o);
+      nup += __shfl_xor_sync(0xffffffffu, nup, o);
+    }
+    if (lane == 0) {
+      const int32_t mp = m[p];
+      rc.cnt[p] = (int32_t)count;
+      rc.ucnt[p] = nup;
+      rc.K_f[p] = msum;
+      rc.K_o[p] = msum - mp;  // the diagonal block (distance 0) is always kept
+      rc.ent_f[p] = (int64_t)mp * msum;
+      rc.ent_o[p] = (int64_t)mp * (msum - mp);
+      rc.msq[p] = (int64_t)mp * mp;
+    }
+  }
 }
 
 __device__ __forceinline__ int64_t find_in_row(const int32_t* __restrict__ col, int64_t b, int64_t e, int32_t key) {
@@ -191,17 +226,14 @@ __device__ __forceinline__ int64_t find_in_row(const int32_t* __restrict__ col, 
   return b;
 }
 
+// Diagonal block and column positions of every block in both layouts.
 __global__ void k_row_meta(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ m, int64_t* __restrict__ diag_b, int64_t* __restrict__ ucnt,
-                           int32_t* __restrict__ colpos_f, int32_t* __restrict__ K_f, int32_t* __restrict__ colpos_o,
-                           int32_t* __restrict__ K_o, int64_t* __restrict__ ent_f, int64_t* __restrict__ ent_o,
-                           int64_t* __restrict__ msq) {
+                           const int32_t* __restrict__ m, int64_t* __restrict__ diag_b, int32_t* __restrict__ colpos_f,
+                           int32_t* __restrict__ colpos_o) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= nw) return;
   const int64_t b0 = row_ptr[p], b1 = row_ptr[p + 1];
-  const int64_t d = find_in_row(col, b0, b1, (int32_t)p);
-  diag_b[p] = d;
-  ucnt[p] = b1 - d - 1;
+  diag_b[p] = find_in_row(col, b0, b1, (int32_t)p);
   int32_t kf = 0, ko = 0;
   for (int64_t b = b0; b < b1; ++b) {
     const int32_t mq = m[col[b]];
@@ -214,11 +246,6 @@ __global__ void k_row_meta(int64_t nw, const int64_t* __restrict__ row_ptr, cons
       ko += mq;
     }
   }
-  K_f[p] = kf;
-  K_o[p] = ko;
-  ent_f[p] = (int64_t)m[p] * kf;
-  ent_o[p] = (int64_t)m[p] * ko;
-  msq[p] = (int64_t)m[p] * m[p];
 }
 
 __global__ void k_transpose_and_upper(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -374,36 +401,10 @@ int build_pattern(swm_ctx* ctx) {
   ctx->uoff = nullptr;  // caller-order offsets are made on first use (ensure_user_offsets)
   ctx->uoff_user = nullptr;
 
-  // --- S-NFC pairs (a1): count, scan, write
-  int32_t* rcnt = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&rcnt, sizeof(int32_t) * nw));
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->row_ptr, sizeof(int64_t) * (nw + 1)));
-  const double rc2 = ctx->dense ? 0.0 : ctx->rc * ctx->rc;
-  ctx->prof_begin(SWM_K_PAIRS);
-  k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
-                                              ctx->dense ? 1 : 0, 0, rcnt, nullptr, nullptr);
-  ctx->prof_end(SWM_K_PAIRS);
-  SWM_LAUNCHED();
-  SWM_TRY(exclusive_scan_i32_to_i64(ctx, rcnt, ctx->row_ptr, nw, nullptr));
-  {
-    const int64_t* src[2] = {ctx->off + nw, ctx->row_ptr + nw};
-    int64_t v[2];
-    SWM_TRY(read_i64(ctx, 2, src, v));
-    ctx->N = v[0];
-    ctx->nb = v[1];
-  }
-  if (ctx->nb > INT32_MAX / 2) return ctx->fail(SWM_EINVAL, "too many kept blocks for 32-bit positions");
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->col, sizeof(int32_t) * ctx->nb));
-  ctx->prof_begin(SWM_K_PAIRS);
-  k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
-                                              ctx->dense ? 1 : 0, 1, nullptr, ctx->row_ptr, ctx->col);
-  ctx->prof_end(SWM_K_PAIRS);
-  SWM_LAUNCHED();
-
-  // --- per-row metadata, transpose map, upper-triangle block list, layouts
+  // --- S-NFC pairs (a1): count (with the per-row sizes), one merged scan, one read-back, write
   int64_t *ucnt = nullptr, *ubase = nullptr, *ent_f = nullptr, *ent_o = nullptr, *msq = nullptr;
-  int32_t *Kf = nullptr, *Ko = nullptr, *cpf = nullptr, *cpo = nullptr;
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->diag_b, sizeof(int64_t) * nw));
+  int32_t *rcnt = nullptr, *Kf = nullptr, *Ko = nullptr, *cpf = nullptr, *cpo = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&rcnt, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&ucnt, sizeof(int64_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&ubase, sizeof(int64_t) * (nw + 1)));
   SWM_TRY(dalloc(ctx, tmp, (void**)&ent_f, sizeof(int64_t) * nw));
@@ -411,39 +412,60 @@ int build_pattern(swm_ctx* ctx) {
   SWM_TRY(dalloc(ctx, tmp, (void**)&msq, sizeof(int64_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&Kf, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&Ko, sizeof(int32_t) * nw));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->row_ptr, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->diag_b, sizeof(int64_t) * nw));
+  SWM_TRY(alloc_layout(ctx, ctx->full, Kf, nullptr));
+  SWM_TRY(alloc_layout(ctx, ctx->offd, Ko, nullptr));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->minv_off, sizeof(int64_t) * (nw + 1)));
+  const double rc2 = ctx->dense ? 0.0 : ctx->rc * ctx->rc;
+  RowCounts rcs{rcnt, ucnt, Kf, Ko, ent_f, ent_o, msq};
+  ctx->prof_begin(SWM_K_PAIRS);
+  k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
+                                              ctx->dense ? 1 : 0, 0, rcs, m, nullptr, nullptr);
+  ctx->prof_end(SWM_K_PAIRS);
+  SWM_LAUNCHED();
+  {
+    const void* in[7] = {rcnt, ucnt, ent_f, Kf, ent_o, Ko, msq};
+    const int is64[7] = {0, 1, 1, 0, 1, 0, 1};
+    int64_t* out[7] = {ctx->row_ptr, ubase, ctx->full.rowbase, ctx->full.cmbase, ctx->offd.rowbase,
+                       ctx->offd.cmbase, ctx->minv_off};
+    SWM_TRY(exclusive_scan_multi(ctx, 7, in, is64, out, nw));
+  }
+  {
+    const int64_t* src[7] = {ctx->off + nw, ctx->row_ptr + nw, ctx->full.rowbase + nw, ctx->full.cmbase + nw,
+                             ctx->offd.rowbase + nw, ctx->offd.cmbase + nw, ctx->minv_off + nw};
+    int64_t v[7];
+    SWM_TRY(read_i64(ctx, 7, src, v));
+    ctx->N = v[0];
+    ctx->nb = v[1];
+    ctx->full.nval = v[2];
+    ctx->full.ncm = v[3];
+    ctx->offd.nval = v[4];
+    ctx->offd.ncm = v[5];
+    ctx->nminv = v[6];
+  }
+  if (ctx->nb > INT32_MAX / 2) return ctx->fail(SWM_EINVAL, "too many kept blocks for 32-bit positions");
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->col, sizeof(int32_t) * ctx->nb));
   SWM_TRY(dalloc(ctx, B, (void**)&cpf, sizeof(int32_t) * ctx->nb));
   SWM_TRY(dalloc(ctx, B, (void**)&cpo, sizeof(int32_t) * ctx->nb));
-  k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, ucnt, cpf, Kf, cpo, Ko,
-                                            ent_f, ent_o, msq);
+  ctx->full.colpos = cpf;
+  ctx->offd.colpos = cpo;
+  ctx->prof_begin(SWM_K_PAIRS);
+  k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
+                                              ctx->dense ? 1 : 0, 1, rcs, m, ctx->row_ptr, ctx->col);
+  ctx->prof_end(SWM_K_PAIRS);
+  SWM_LAUNCHED();
+
+  // --- diagonal blocks and column positions, transpose map, upper-triangle block list, layouts
+  k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, cpf, cpo);
   SWM_LAUNCHED();
   // the S-NFC pattern is symmetric, so the blocks above the diagonal are half the off-diagonal ones
   ctx->nup = (ctx->nb - nw) / 2;
-  SWM_TRY(alloc_layout(ctx, ctx->full, Kf, cpf));
-  SWM_TRY(alloc_layout(ctx, ctx->offd, Ko, cpo));
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->minv_off, sizeof(int64_t) * (nw + 1)));
-  {
-    const void* in[6] = {ucnt, ent_f, Kf, ent_o, Ko, msq};
-    const int is64[6] = {1, 1, 0, 1, 0, 1};
-    int64_t* out[6] = {ubase, ctx->full.rowbase, ctx->full.cmbase, ctx->offd.rowbase, ctx->offd.cmbase,
-                       ctx->minv_off};
-    SWM_TRY(exclusive_scan_multi(ctx, 6, in, is64, out, nw));
-  }
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->bt, sizeof(int64_t) * ctx->nb));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->ublk, sizeof(int64_t) * std::max<int64_t>(1, ctx->nup)));
   k_transpose_and_upper<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, ctx->diag_b, ubase, ctx->bt,
                                                        ctx->ublk);
   SWM_LAUNCHED();
-  {
-    const int64_t* src[5] = {ctx->full.rowbase + nw, ctx->full.cmbase + nw, ctx->offd.rowbase + nw,
-                             ctx->offd.cmbase + nw, ctx->minv_off + nw};
-    int64_t v[5];
-    SWM_TRY(read_i64(ctx, 5, src, v));
-    ctx->full.nval = v[0];
-    ctx->full.ncm = v[1];
-    ctx->offd.nval = v[2];
-    ctx->offd.ncm = v[3];
-    ctx->nminv = v[4];
-  }
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->full.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->full.ncm)));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->offd.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->offd.ncm)));
   k_colmap<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, ctx->full, ctx->offd);

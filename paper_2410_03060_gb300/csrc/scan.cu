@@ -90,21 +90,67 @@ __global__ void k_tile_rescan(const TIn* __restrict__ in, int64_t n, const int64
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = sums[gridDim.x];
 }
 
-// Whole scan in one CTA for short arrays (one launch instead of three).
+// Whole scan in one CTA of kSingleThreads for short arrays (one launch instead of three).  Each
+// thread owns up to kSingleItems consecutive entries, loaded together before they are summed, so
+// the scan costs one memory round trip instead of one per entry.
+constexpr int kSingleThreads = 1024;
+constexpr int kSingleItems = 16;
+constexpr int64_t kSingleMax = (int64_t)kSingleThreads * kSingleItems;
+
+__device__ int64_t block_incl_scan_1024(int64_t v, int64_t* total) {
+  __shared__ int64_t warp_tot[kSingleThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) warp_tot[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int64_t t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t n = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += n;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  if (w > 0) v += warp_tot[w - 1];
+  *total = warp_tot[kSingleThreads / 32 - 1];
+  __syncthreads();
+  return v;
+}
+
 template <typename TIn>
-__global__ void k_scan_single(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
-  const int64_t per = ceil_div(n, kScanThreads);
-  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+__device__ void cta_scan_short(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
+  const int64_t per = ceil_div(n, kSingleThreads);  // <= kSingleItems
+  const int64_t b = threadIdx.x * per;
+  int64_t v[kSingleItems];
   int64_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += (int64_t)in[i];
+#pragma unroll
+  for (int t = 0; t < kSingleItems; ++t) {
+    const int64_t i = b + t;
+    v[t] = (t < per && i < n) ? (int64_t)in[i] : 0;
+  }
+#pragma unroll
+  for (int t = 0; t < kSingleItems; ++t) s += v[t];
   int64_t tot;
-  int64_t run = block_incl_scan(s, &tot) - s;
-  for (int64_t i = b; i < e; ++i) {
-    const int64_t v = (int64_t)in[i];
-    out[i] = run;
-    run += v;
+  int64_t run = block_incl_scan_1024(s, &tot) - s;
+#pragma unroll
+  for (int t = 0; t < kSingleItems; ++t) {
+    const int64_t i = b + t;
+    if (t < per && i < n) out[i] = run;
+    run += v[t];
   }
   if (threadIdx.x == 0) out[n] = tot;
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(kSingleThreads) k_scan_single(const TIn* __restrict__ in, int64_t n,
+                                                                int64_t* __restrict__ out) {
+  cta_scan_short<TIn>(in, n, out);
 }
 
 template <typename TIn>
@@ -115,8 +161,8 @@ int scan_impl(swm_ctx* ctx, const TIn* in, int64_t* out, int64_t n, int64_t* tot
     if (total_host) *total_host = 0;
     return SWM_OK;
   }
-  if (n <= 4 * kTile) {
-    k_scan_single<TIn><<<1, kScanThreads, 0, ctx->stream>>>(in, n, out);
+  if (n <= kSingleMax) {
+    k_scan_single<TIn><<<1, kSingleThreads, 0, ctx->stream>>>(in, n, out);
     SWM_LAUNCHED();
     if (total_host) {
       SWM_CK(cudaMemcpyAsync(total_host, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -142,40 +188,28 @@ int scan_impl(swm_ctx* ctx, const TIn* in, int64_t* out, int64_t n, int64_t* tot
   return SWM_OK;
 }
 
+constexpr int kMaxMultiScan = 8;
 struct MultiScanArgs {
-  const void* in[6];
-  int is64[6];
-  int64_t* out[6];
+  const void* in[kMaxMultiScan];
+  int is64[kMaxMultiScan];
+  int64_t* out[kMaxMultiScan];
   int narr;
 };
 
 // Several exclusive scans of the same short length, one CTA per array.
-__global__ void k_scan_multi(MultiScanArgs a, int64_t n) {
-  const int64_t per = ceil_div(n, kScanThreads);
-  const int64_t b = threadIdx.x * per, e = min(n, b + per);
-  {
-    const int k = blockIdx.x;
-    const int64_t* i64 = (const int64_t*)a.in[k];
-    const int32_t* i32 = (const int32_t*)a.in[k];
-    int64_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += a.is64[k] ? i64[i] : (int64_t)i32[i];
-    int64_t tot;
-    int64_t run = block_incl_scan(s, &tot) - s;
-    int64_t* out = a.out[k];
-    for (int64_t i = b; i < e; ++i) {
-      const int64_t v = a.is64[k] ? i64[i] : (int64_t)i32[i];
-      out[i] = run;
-      run += v;
-    }
-    if (threadIdx.x == 0) out[n] = tot;
-  }
+__global__ void __launch_bounds__(kSingleThreads) k_scan_multi(MultiScanArgs a, int64_t n) {
+  const int k = blockIdx.x;
+  if (a.is64[k])
+    cta_scan_short<int64_t>((const int64_t*)a.in[k], n, a.out[k]);
+  else
+    cta_scan_short<int32_t>((const int32_t*)a.in[k], n, a.out[k]);
 }
 
 }  // namespace
 
 int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const int* is64, int64_t* const* out,
                          int64_t n) {
-  if (n <= 4 * kTile && n > 0) {
+  if (n <= kSingleMax && n > 0 && narr <= kMaxMultiScan) {
     MultiScanArgs a{};
     a.narr = narr;
     for (int k = 0; k < narr; ++k) {
@@ -183,7 +217,7 @@ int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const in
       a.is64[k] = is64[k];
       a.out[k] = out[k];
     }
-    k_scan_multi<<<narr, kScanThreads, 0, ctx->stream>>>(a, n);
+    k_scan_multi<<<narr, kSingleThreads, 0, ctx->stream>>>(a, n);
     SWM_LAUNCHED();
     return SWM_OK;
   }
