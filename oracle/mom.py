@@ -53,7 +53,7 @@ __all__ = [
     "assemble_block", "mutual_block", "self_block", "block",
     "neighbour_pairs", "block_pattern", "assemble", "block_jacobi",
     "incidence_frames", "triangle_ft", "rhs", "far_field", "rcs_from_far_field",
-    "rcs_bistatic", "rcs_monostatic", "solve_lu", "gmres", "solve",
+    "rcs_bistatic", "rcs_monostatic", "solve_lu", "gmres", "gcr", "solve",
 ]
 
 
@@ -472,12 +472,13 @@ def solve_lu(Z, b):
 
 
 def gmres(A, b: np.ndarray, Minv_blocks, off, tol: float = 1e-6, restart: int = 50,
-          max_iter: int = 1000, x0=None):
+          max_iter: int = 1000, x0=None, history=None):
     """Restarted GMRES with right block-Jacobi preconditioning, modified Gram-Schmidt and complex
     Givens rotations, in float64.  Solves A x = b for one right-hand side.  The paper uses GCR
     with a block-diagonal preconditioner (after Eq. neardef); GMRES minimises the same residual
     over the same Krylov space and reaches the same solution to tolerance.
-    Returns (x, iterations, relative residual estimate)."""
+    Returns (x, iterations, relative residual estimate); ``history`` (a list) receives the
+    residual estimate after every iteration."""
     b = np.asarray(b, dtype=np.complex128)
     N = b.shape[0]
 
@@ -533,6 +534,8 @@ def gmres(A, b: np.ndarray, Minv_blocks, off, tol: float = 1e-6, restart: int = 
             it += 1
             jlast = j
             rel = abs(g[j + 1]) / bnorm
+            if history is not None:
+                history.append(rel)
             if rel <= tol or it >= max_iter or H[j, j] == 0.0:
                 break
         n = jlast + 1
@@ -542,10 +545,68 @@ def gmres(A, b: np.ndarray, Minv_blocks, off, tol: float = 1e-6, restart: int = 
         x = x + Minv(V[:n].T @ y)
 
 
+def gcr(A, b: np.ndarray, Minv_blocks, off, tol: float = 1e-6, restart: int = 50,
+        max_iter: int = 1000, x0=None, history=None):
+    """Restarted GCR, the Krylov method the paper names (Sec. II-B, after Eq. neardef), with right
+    block-Jacobi preconditioning, in float64, for one right-hand side of A x = b.
+
+    Each step takes the search direction p = M^-1 r from the current residual and its image
+    q = A p, makes q orthogonal to the earlier images q_i (modified Gram-Schmidt, with the same
+    combination applied to p so that q = A p still holds), scales both so |q| = 1, and then moves
+    x along p by the coefficient alpha = q^H r that removes the q-component of the residual:
+    x += alpha p, r -= alpha q.  After k steps r is the smallest residual over the Krylov space of
+    dimension k, as in GMRES.  Every ``restart`` steps the bases are dropped and r is recomputed
+    as b - A x.  Returns (x, iterations, relative residual); ``history`` receives |r|/|b| after
+    every step."""
+    b = np.asarray(b, dtype=np.complex128)
+    N = b.shape[0]
+
+    def Minv(v):
+        z = np.empty_like(v)
+        for p, Mi in enumerate(Minv_blocks):
+            z[off[p]:off[p + 1]] = Mi @ v[off[p]:off[p + 1]]
+        return z
+
+    x = np.zeros(N, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, 0.0
+    it = 0
+    while True:
+        r = b - A @ x
+        rel = np.linalg.norm(r) / bnorm
+        if rel <= tol or it >= max_iter:
+            return x, it, rel
+        P, Q = [], []
+        for _ in range(restart):
+            p = Minv(r)
+            q = A @ p
+            for pi, qi in zip(P, Q):
+                beta = np.vdot(qi, q)
+                q = q - beta * qi
+                p = p - beta * pi
+            nq = np.linalg.norm(q)
+            if nq == 0.0:
+                break
+            q, p = q / nq, p / nq
+            alpha = np.vdot(q, r)
+            x = x + alpha * p
+            r = r - alpha * q
+            P.append(p)
+            Q.append(q)
+            it += 1
+            rel = np.linalg.norm(r) / bnorm
+            if history is not None:
+                history.append(rel)
+            if rel <= tol or it >= max_iter:
+                break
+
+
 def solve(cloud, k: float, inc: np.ndarray, r_c: float | None = None, method: str = "lu",
           tol: float = 1e-6, restart: int = 50, max_iter: int = 1000):
-    """Currents jt (N x n_inc) of Z jt = b for each incidence.  ``method`` 'lu' or 'gmres'."""
-    Z = assemble(cloud, k, r_c, sparse=(method == "gmres"))
+    """Currents jt (N x n_inc) of Z jt = b for each incidence.  ``method`` 'lu', 'gmres' or
+    'gcr'."""
+    Z = assemble(cloud, k, r_c, sparse=(method != "lu"))
     b = rhs(cloud, k, inc)
     if method == "lu":
         return solve_lu(Z, b), {"iterations": 0}
@@ -554,6 +615,7 @@ def solve(cloud, k: float, inc: np.ndarray, r_c: float | None = None, method: st
     X = np.zeros_like(b)
     its = []
     for i in range(b.shape[1]):
-        X[:, i], it, rel = gmres(Z, b[:, i], Mi, off, tol, restart, max_iter)
+        krylov = gcr if method == "gcr" else gmres
+        X[:, i], it, rel = krylov(Z, b[:, i], Mi, off, tol, restart, max_iter)
         its.append(it)
     return X, {"iterations": its}

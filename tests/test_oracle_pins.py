@@ -399,6 +399,60 @@ def test_gmres_matches_lu_and_stops_at_tolerance():
     assert np.linalg.norm(x1 - x_lu) / np.linalg.norm(x_lu) < 1e-8
 
 
+def test_gcr_matches_lu_and_restarts():
+    """The paper's solver (GCR, Sec. II-B) reaches the LU solution, with and without restarts."""
+    cl = cloud_uniform_cube(40, 4.0, seed=16)
+    inc = np.array([[0.0, 0.0, 0.0]])
+    Z = O.assemble(cl, K, 2.0, sparse=True)
+    b = O.rhs(cl, K, inc)[:, 0]
+    x_lu = O.solve_lu(Z, b)
+    m, off = O.numbering(cl.nseg)
+    Mi = O.block_jacobi(cl, K)
+    for restart in (50, 4, 1):
+        x, it, rel = O.gcr(Z, b, Mi, off, tol=1e-12, restart=restart, max_iter=3000)
+        assert rel <= 1e-12
+        assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-9
+        assert np.linalg.norm(b - Z @ x) / np.linalg.norm(b) < 1e-11
+
+
+def test_gcr_residual_is_the_krylov_least_squares_minimum():
+    """After k steps (no restart) the GCR iterate is x_k = M^-1 z_k with z_k minimising
+    |b - A M^-1 z| over the Krylov space K_k(A M^-1, b): checked against that definition solved by
+    least squares on an explicit, orthonormalised Krylov basis (iterate and residual); GMRES's
+    residual estimates are the same numbers."""
+    cl = cloud_uniform_cube(30, 4.0, seed=21)
+    inc = np.array([[0.4, 1.0, 0.3]])
+    Z = O.assemble(cl, K, 2.0, sparse=False)
+    b = O.rhs(cl, K, inc)[:, 0]
+    m, off = O.numbering(cl.nseg)
+    Mi = O.block_jacobi(cl, K)
+    N = b.shape[0]
+    Mfull = np.zeros((N, N), dtype=complex)
+    for p, B in enumerate(Mi):
+        Mfull[off[p]:off[p + 1], off[p]:off[p + 1]] = B
+    Ap = Z @ Mfull
+    kmax = 8
+    hist_gcr, hist_gmres = [], []
+    O.gcr(Z, b, Mi, off, tol=1e-300, restart=kmax, max_iter=kmax, history=hist_gcr)
+    O.gmres(Z, b, Mi, off, tol=1e-300, restart=kmax, max_iter=kmax, history=hist_gmres)
+    basis = []
+    v = b.copy()
+    for k in range(1, kmax + 1):
+        for u in basis:  # orthonormal basis of span{b, A'b, ..., A'^(k-1) b}
+            v = v - np.vdot(u, v) * u
+        basis.append(v / np.linalg.norm(v))
+        Kb = np.stack(basis, 1)
+        c = np.linalg.lstsq(Ap @ Kb, b, rcond=None)[0]
+        rmin = np.linalg.norm(b - Ap @ (Kb @ c)) / np.linalg.norm(b)
+        assert abs(hist_gcr[k - 1] - rmin) <= 1e-9 * max(rmin, 1e-3)
+        assert abs(hist_gmres[k - 1] - rmin) <= 1e-9 * max(rmin, 1e-3)
+        xk, _, _ = O.gcr(Z, b, Mi, off, tol=1e-300, restart=kmax, max_iter=k)
+        x_ls = Mfull @ (Kb @ c)
+        assert np.linalg.norm(xk - x_ls) <= 1e-8 * np.linalg.norm(x_ls)
+        v = Ap @ basis[-1]
+    assert hist_gcr[-1] < hist_gcr[0] < 1.0
+
+
 def test_rcs_error_shrinks_as_rc_grows():
     """Sparsified RCS approaches the entire-coupling RCS as the coupling radius grows (Sec. III-B)."""
     cl = cloud_uniform_cube(60, 5.0, seed=17, length=0.475, nseg=8)
