@@ -106,6 +106,8 @@ typedef struct swm_stats {
   int64_t ncm_offd;        /* column-map entries of that matrix (sum over block-rows of K_p) */
   double prof_ms;          /* summed device time of the profiled kernel class (swm_profile) */
   int64_t prof_launches;   /* launches of the profiled kernel class */
+  int pattern_reused;      /* 1 if the last build kept the previous S-NFC pattern (same cloud and
+                              r_c, e.g. a frequency sweep) and only refilled the values */
 } swm_stats;
 
 /* kernel classes for swm_profile */
@@ -165,14 +167,28 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
 /* Build the S-NFC system (Sec. II-B): neighbour search with coupling radius r_c (r_c <= 0 or
  * infinite = entire coupling, every block kept), fill of every kept block at wavenumber k > 0
  * (Eqs. (5)-(8)), and the block-Jacobi preconditioner.  precision is SWM_C128 or SWM_C64.
+ * The pattern depends on the cloud and r_c only: a build with the same r_c as the previous one
+ * on the same cloud (a frequency sweep: only k changes) keeps the pattern, its index arrays and
+ * the wire order, and refills the values (swm_stats.pattern_reused = 1).
  * Device memory: about 16 (c128) or 8 (c64) bytes per stored entry, twice (Z and Z times the
  * preconditioner), plus O(nw + nb) index arrays. */
 int swm_build(swm_ctx* ctx, double k, double r_c, int precision);
 
+/* Krylov method of swm_solve (both right-preconditioned by the inverses of the self blocks and
+ * minimising the residual over the same Krylov space, restarted every `restart` steps):
+ * SWM_SOLVER_GMRES (default) -- restarted GMRES, Hessenberg least squares by Givens rotations;
+ * SWM_SOLVER_GCR -- restarted GCR, the method the paper names (Sec. II-B, after Eq. neardef):
+ * per step one product, two Gram-Schmidt passes over the stored images A p_i, and an update of
+ * the iterate and of the residual, whose norm is then exact; it stores two bases (p_i and A p_i).
+ * Applies to the following swm_solve calls of this context; SWM_EINVAL for another value. */
+#define SWM_SOLVER_GMRES 0
+#define SWM_SOLVER_GCR 1
+int swm_set_solver(swm_ctx* ctx, int method);
+
 /* Solve Z jt = b for n_inc >= 1 incidences (Eq. (4) right-hand sides), inc = n_inc x 3 float64
- * (theta, phi, psi) in host memory.  Restarted GMRES(restart), 1 <= restart <= SWM_MAX_RESTART,
- * stops when every relative residual ||b - Z x||/||b|| <= tol or after max_iter iterations
- * (SWM_ENOTCONV, last iterate kept).  The currents stay in the context for the RCS calls; if
+ * (theta, phi, psi) in host memory.  Restarted GMRES(restart) or GCR(restart) (swm_set_solver),
+ * 1 <= restart <= SWM_MAX_RESTART, stops when every relative residual ||b - Z x||/||b|| <= tol or
+ * after max_iter iterations (SWM_ENOTCONV, last iterate kept).  The currents stay in the context for the RCS calls; if
  * currents_out is not NULL they are also written there as n_inc x N complex128 (interleaved
  * re, im; incidence-major, caller's unknown order), in memory of kind out_kind. */
 int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restart, int max_iter,

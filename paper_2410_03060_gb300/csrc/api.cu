@@ -52,6 +52,7 @@ static void release_all(swm_ctx* ctx) {
   ctx->kry_ws = nullptr;
   dfree_group(ctx, ctx->solve_bufs);
   dfree_group(ctx, ctx->build_bufs);
+  dfree_group(ctx, ctx->pattern_bufs);
   dfree_group(ctx, ctx->cloud_bufs);
   for (auto& b : ctx->free_list) {
     if (ctx->user_free)
@@ -187,7 +188,8 @@ const char* swm_last_error(const swm_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int swm_set_allocator(swm_ctx* ctx, swm_alloc_fn alloc, swm_free_fn free_fn, void* user) {
   if (!ctx) return SWM_EINVAL;
-  if (!ctx->cloud_bufs.empty() || !ctx->build_bufs.empty() || !ctx->solve_bufs.empty() || !ctx->free_list.empty())
+  if (!ctx->cloud_bufs.empty() || !ctx->pattern_bufs.empty() || !ctx->build_bufs.empty() ||
+      !ctx->solve_bufs.empty() || !ctx->free_list.empty())
     return ctx->fail(SWM_ESTATE, "swm_set_allocator must precede swm_set_cloud");
   if ((alloc == nullptr) != (free_fn == nullptr)) return ctx->fail(SWM_EINVAL, "alloc and free must both be set");
   ctx->user_alloc = alloc;
@@ -207,8 +209,10 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   dfree_group(ctx, ctx->solve_bufs);
   dfree_group(ctx, ctx->build_bufs);
+  dfree_group(ctx, ctx->pattern_bufs);
   dfree_group(ctx, ctx->cloud_bufs);
   ctx->built = ctx->solved = false;
+  ctx->pattern_ok = false;
   ctx->rowwire = nullptr;
   ctx->nw = nw;
   auto& G = ctx->cloud_bufs;
@@ -266,13 +270,27 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   dfree_group(ctx, ctx->solve_bufs);
   dfree_group(ctx, ctx->build_bufs);
   ctx->built = ctx->solved = false;
-  ctx->rowwire = nullptr;
+  const bool dense = !(r_c > 0.0) || std::isinf(r_c);
+  // the pattern depends on the cloud and r_c only (Eq. neardef), not on k: a build at a new
+  // frequency with the same r_c refills the values on the kept pattern
+  const bool reuse = ctx->pattern_ok && ctx->pattern_dense == dense && (dense || ctx->pattern_rc == r_c);
   ctx->k = k;
   ctx->rc = r_c;
-  ctx->dense = !(r_c > 0.0) || std::isinf(r_c);
+  ctx->dense = dense;
   ctx->prec = precision;
   ctx->phase_begin(swm_ctx::PH_NEIGHBOUR);
-  SWM_TRY(build_pattern(ctx));
+  if (!reuse) {
+    dfree_group(ctx, ctx->pattern_bufs);
+    ctx->pattern_ok = false;
+    ctx->rowwire = nullptr;
+    ctx->uoff = nullptr;
+    ctx->uoff_user = nullptr;
+    SWM_TRY(build_pattern(ctx));
+    ctx->pattern_ok = true;
+    ctx->pattern_rc = r_c;
+    ctx->pattern_dense = dense;
+  }
+  ctx->stats.pattern_reused = reuse ? 1 : 0;
   ctx->phase_end(swm_ctx::PH_NEIGHBOUR);
   ctx->phase_begin(swm_ctx::PH_FILL);
   SWM_TRY(fill_blocks(ctx));
@@ -292,6 +310,13 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->stats.ncm_offd = ctx->offd.ncm;
   ctx->built = true;
   ctx->prof_flush();
+  return SWM_OK;
+}
+
+int swm_set_solver(swm_ctx* ctx, int method) {
+  if (!ctx) return SWM_EINVAL;
+  if (method != SWM_SOLVER_GMRES && method != SWM_SOLVER_GCR) return ctx->fail(SWM_EINVAL, "bad solver");
+  ctx->solver = method;
   return SWM_OK;
 }
 
@@ -326,7 +351,8 @@ int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restar
   SWM_TRY(compute_rhs(ctx, n_inc, frames));
   ctx->phase_end(swm_ctx::PH_RHS);
   ctx->phase_begin(swm_ctx::PH_SOLVE);
-  int rc = gmres_solve(ctx, tol, restart, max_iter);
+  int rc = ctx->solver == SWM_SOLVER_GCR ? gcr_solve(ctx, tol, restart, max_iter)
+                                         : gmres_solve(ctx, tol, restart, max_iter);
   ctx->phase_end(swm_ctx::PH_SOLVE);
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->phase_collect();

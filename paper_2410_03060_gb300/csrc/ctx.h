@@ -26,13 +26,11 @@ struct Layout {
   int64_t ncm = 0;
 };
 
-// Device state of the Krylov solver (one copy in device memory).
-struct KrylovDev {
-  int j;              // Arnoldi step inside the current cycle
-  int cycle_done;     // no right-hand side is active in this cycle any more
-  int all_converged;  // every right-hand side has met tol
-  int iters;          // total Arnoldi steps
-  unsigned int counter[4];  // arrival counters of the last-block reductions
+// Row descriptor of the stored matrix E: first value, first column-map entry, row length.
+struct alignas(16) RowInfo {
+  int64_t vb;
+  int32_t cmb;
+  int32_t K;
 };
 
 struct Buf {
@@ -49,7 +47,13 @@ struct swm_ctx {
   swm_alloc_fn user_alloc = nullptr;
   swm_free_fn user_free = nullptr;
   void* user_arg = nullptr;
-  std::vector<swm::Buf> cloud_bufs, build_bufs, solve_bufs;
+  // device buffers by lifetime: the cloud; the S-NFC pattern and everything indexed by it (kept
+  // across builds at the same r_c: frequency sweeps refill only the values); the values at one k;
+  // one solve
+  std::vector<swm::Buf> cloud_bufs, pattern_bufs, build_bufs, solve_bufs;
+  bool pattern_ok = false;  // pattern_bufs hold the pattern of (pattern_rc, pattern_dense)
+  double pattern_rc = 0.0;
+  bool pattern_dense = false;
   // buffers released by a group wait here for reuse by later allocations on the same stream
   // (stream order makes the reuse safe); they are returned to the allocator by swm_destroy
   std::vector<swm::Buf> free_list;
@@ -120,6 +124,7 @@ struct swm_ctx {
   unsigned long long* d_evals = nullptr;  // fill evaluation counter (device)
   int* d_sing = nullptr;                  // singular self block flag (device)
   void* pinned_state = nullptr;           // two pinned slots for the Krylov state poll
+  int solver = 0;                         // SWM_SOLVER_GMRES or SWM_SOLVER_GCR
   void* ffw = nullptr;                    // per-wire float32 far-field data (complex64 path)
   cudaGraphExec_t gm_exec = nullptr;      // captured chunk of GMRES steps and its argument key
   std::vector<unsigned char> gm_key;
@@ -250,5 +255,13 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
 void set_stateless_error(const std::string& msg);
 // krylov.cu: a6
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
+// row descriptors of E (built once per build) and x = M^-1 y into ctx->Xv
+int ensure_rowinfo(swm_ctx* ctx);
+// two pinned host slots (kPollSlotBytes in all) for polling the solvers' device state
+constexpr size_t kPollSlotBytes = 128;
+int ensure_poll_slots(swm_ctx* ctx);
+int apply_minv(swm_ctx* ctx, const void* Y);
+// gcr.cu: the paper's GCR solver (alternative to GMRES)
+int gcr_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
 
 }  // namespace swm

@@ -198,13 +198,6 @@ __device__ void reduce_dots(const KPtr& P, int j, int r, c128* __restrict__ dst,
   }
 }
 
-// Row descriptor of the stored matrix E: first value, first column-map entry, row length.
-struct alignas(16) RowInfo {
-  int64_t vb;
-  int32_t cmb;
-  int32_t K;
-};
-
 // Normalise, multiply by A = I + E and take the first Gram-Schmidt dots, over one chunk of rows
 // (P.schunk rows, a multiple of 32) and a block of RB right-hand sides that share every read of E.
 // Eight lanes share a scalar row; the 32 row groups of the CTA take the chunk's rows in turn, with
@@ -1365,14 +1358,7 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   const int64_t N = ctx->N;
   std::vector<Buf>& S = ctx->solve_bufs;
   std::vector<Buf> tmp;
-  if (!ctx->rowwire) {
-    if (ctx->offd.ncm > INT32_MAX) return ctx->fail(SWM_EINVAL, "column map too large for 32-bit offsets");
-    SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->rowwire, sizeof(int32_t) * std::max<int64_t>(1, N)));
-    SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->rowinfo, sizeof(RowInfo) * std::max<int64_t>(1, N)));
-    k_rowwire<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, st>>>(ctx->nw, ctx->off, ctx->offd, ctx->rowwire,
-                                                               (RowInfo*)ctx->rowinfo);
-    SWM_LAUNCHED();
-  }
+  SWM_TRY(ensure_rowinfo(ctx));
   KPtr P{};
   P.R = R;
   P.restart = restart;
@@ -1536,11 +1522,8 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   if (bs_smem > 0)
     SWM_CK(cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
   bool first = true;
-  if (!ctx->pinned_state) {
-    SWM_CK(cudaMallocHost(&ctx->pinned_state, 2 * sizeof(KState)));
-    SWM_CK(cudaEventCreateWithFlags(&ctx->poll_ev[0], cudaEventDisableTiming));
-    SWM_CK(cudaEventCreateWithFlags(&ctx->poll_ev[1], cudaEventDisableTiming));
-  }
+  SWM_TRY(ensure_poll_slots(ctx));
+  static_assert(2 * sizeof(KState) <= kPollSlotBytes, "poll slots");
   KState* slot = reinterpret_cast<KState*>(ctx->pinned_state);
   constexpr int kChunkSteps = 4;
   auto launch_steps = [&](cudaStream_t s, int n) -> int {
@@ -1657,10 +1640,7 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     ++cycles;
   }
   // x = M^-1 y
-  k_apply_minv<TV><<<dim3((unsigned)ceil_div(N, 256), R), 256, 0, st>>>(N, R, ctx->rowwire, ctx->off, ctx->m,
-                                                                        ctx->minv_off, (const cplx<TV>*)ctx->Minv, Y,
-                                                                        (cplx<TV>*)ctx->Xv);
-  SWM_LAUNCHED();
+  SWM_TRY(apply_minv(ctx, Y));
   std::vector<double> res(R);
   SWM_CK(cudaMemcpyAsync(res.data(), P.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
   SWM_CK(cudaStreamSynchronize(st));
@@ -1676,6 +1656,40 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
 }
 
 }  // namespace
+
+int ensure_poll_slots(swm_ctx* ctx) {
+  if (ctx->pinned_state) return SWM_OK;
+  SWM_CK(cudaMallocHost(&ctx->pinned_state, kPollSlotBytes));
+  SWM_CK(cudaEventCreateWithFlags(&ctx->poll_ev[0], cudaEventDisableTiming));
+  SWM_CK(cudaEventCreateWithFlags(&ctx->poll_ev[1], cudaEventDisableTiming));
+  return SWM_OK;
+}
+
+int ensure_rowinfo(swm_ctx* ctx) {
+  if (ctx->rowwire) return SWM_OK;
+  const int64_t N = ctx->N;
+  if (ctx->offd.ncm > INT32_MAX) return ctx->fail(SWM_EINVAL, "column map too large for 32-bit offsets");
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&ctx->rowwire, sizeof(int32_t) * std::max<int64_t>(1, N)));
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, &ctx->rowinfo, sizeof(RowInfo) * std::max<int64_t>(1, N)));
+  k_rowwire<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, ctx->stream>>>(ctx->nw, ctx->off, ctx->offd, ctx->rowwire,
+                                                                      (RowInfo*)ctx->rowinfo);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+int apply_minv(swm_ctx* ctx, const void* Y) {
+  const int64_t N = ctx->N;
+  const int R = ctx->n_rhs;
+  const dim3 grid((unsigned)ceil_div(N, 256), R);
+  if (ctx->prec == SWM_C128)
+    k_apply_minv<double><<<grid, 256, 0, ctx->stream>>>(N, R, ctx->rowwire, ctx->off, ctx->m, ctx->minv_off,
+                                                         (const c128*)ctx->Minv, (const c128*)Y, (c128*)ctx->Xv);
+  else
+    k_apply_minv<float><<<grid, 256, 0, ctx->stream>>>(N, R, ctx->rowwire, ctx->off, ctx->m, ctx->minv_off,
+                                                        (const c64*)ctx->Minv, (const c64*)Y, (c64*)ctx->Xv);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
 
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter) {
   if (ctx->prec == SWM_C128) return gmres_impl<double>(ctx, tol, restart, max_iter);

@@ -283,8 +283,8 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, c
 int alloc_layout(swm_ctx* ctx, Layout& lay, int32_t* K, int32_t* colpos) {
   lay.K = K;
   lay.colpos = colpos;
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.rowbase, sizeof(int64_t) * (ctx->nw + 1)));
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&lay.cmbase, sizeof(int64_t) * (ctx->nw + 1)));
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&lay.rowbase, sizeof(int64_t) * (ctx->nw + 1)));
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&lay.cmbase, sizeof(int64_t) * (ctx->nw + 1)));
   return SWM_OK;
 }
 
@@ -310,9 +310,9 @@ int ensure_user_offsets(swm_ctx* ctx) {
   SWM_TRY(dalloc(ctx, tmp, (void**)&um, sizeof(int32_t) * nw));
   k_user_m<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->u_ns, um);
   SWM_LAUNCHED();
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->uoff_user, sizeof(int64_t) * (nw + 1)));
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&ctx->uoff_user, sizeof(int64_t) * (nw + 1)));
   SWM_TRY(exclusive_scan_i32_to_i64(ctx, um, ctx->uoff_user, nw, nullptr));
-  SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->uoff, sizeof(int64_t) * nw));
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&ctx->uoff, sizeof(int64_t) * nw));
   k_uoff_by_internal<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->perm, ctx->uoff_user, ctx->uoff);
   SWM_LAUNCHED();
   dfree_group(ctx, tmp);
@@ -330,7 +330,7 @@ int build_pattern(swm_ctx* ctx) {
   const int64_t nw = ctx->nw;
   cudaStream_t st = ctx->stream;
   std::vector<Buf> tmp;
-  auto& B = ctx->build_bufs;
+  auto& B = ctx->pattern_bufs;
 
   // --- bounding box of the centres (computed when the cloud was loaded)
   const double* hb = ctx->bbox;

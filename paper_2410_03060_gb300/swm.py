@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 SWM_OK, SWM_ENOTCONV = 0, 1
+SWM_SOLVER_GMRES, SWM_SOLVER_GCR = 0, 1
 SWM_EINVAL, SWM_ENOMEM, SWM_ECUDA, SWM_ESTATE, SWM_ETIMEOUT = -1, -2, -3, -4, -5
 SWM_HOST, SWM_DEVICE = 0, 1
 SWM_C128, SWM_C64 = 0, 1
@@ -38,7 +39,7 @@ class swm_stats(C.Structure):
                 ("ms_precond", C.c_double), ("ms_rhs", C.c_double), ("ms_solve", C.c_double),
                 ("ms_rcs", C.c_double), ("kernel_launches", C.c_int64), ("fill_evals", C.c_int64),
                 ("nnz_offd", C.c_int64), ("ncm_offd", C.c_int64), ("prof_ms", C.c_double),
-                ("prof_launches", C.c_int64)]
+                ("prof_launches", C.c_int64), ("pattern_reused", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -52,6 +53,7 @@ _SIGS = {
     "swm_set_allocator": (C.c_int, [_P, ALLOC_FN, FREE_FN, _P]),
     "swm_set_cloud": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_int]),
     "swm_build": (C.c_int, [_P, C.c_double, C.c_double, C.c_int]),
+    "swm_set_solver": (C.c_int, [_P, C.c_int]),
     "swm_solve": (C.c_int, [_P, C.c_int, _P, C.c_double, C.c_int, C.c_int, _P, C.c_int]),
     "swm_rcs_bistatic": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "swm_rcs_monostatic": (C.c_int, [_P, _P, C.c_int]),
@@ -207,6 +209,12 @@ def swm_set_cloud(ctx: Ctx, centres, dirs, lengths, radii, nseg) -> int:
 
 def swm_build(ctx: Ctx, k: float, r_c: float, precision: int = SWM_C128) -> int:
     return _check(ctx, load().swm_build(ctx.handle, float(k), float(r_c), int(precision)))
+
+
+def swm_set_solver(ctx: Ctx, method) -> int:
+    """Krylov method of the following solves: "gmres" / SWM_SOLVER_GMRES or "gcr" / SWM_SOLVER_GCR."""
+    m = {"gmres": SWM_SOLVER_GMRES, "gcr": SWM_SOLVER_GCR}[method] if isinstance(method, str) else int(method)
+    return _check(ctx, load().swm_set_solver(ctx.handle, m))
 
 
 def swm_solve(ctx: Ctx, inc, tol: float = 1e-6, restart: int = 50, max_iter: int = 1000, currents_out=None) -> int:
