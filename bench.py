@@ -139,8 +139,9 @@ def cpu_baseline(n_wires=1000):
                       f"single-threaded NumPy"}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per working launch, mid workload, from ncu
-MEASURED_TRAFFIC = {("apply", "c64"): 7.0e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, mid workload, from one ncu capture of
+# the kernel's current code (profiles/gmres_persist_mid.md)
+MEASURED_TRAFFIC = {("gmres", "c64"): 3.98e6}
 
 
 # ---------------------------------------------------------------------------------- ranks
@@ -471,6 +472,60 @@ def run_scale(args):
     swm.swm_destroy(ctx)
 
 
+def run_compare(args):
+    """One larger workload solved in the three precisions (float64, complex64, bfloat16 storage with
+    float64 refinement): time per step and the monostatic RCS error of each against the float64
+    path.  Prints a JSON line of kind "precision_compare" (a measurement record)."""
+    import torch
+
+    from paper_2410_03060_gb300 import swm
+
+    w = SCALE[args.workload]
+    torch.cuda.set_device(0)
+    cl = w["cloud"](nw=args.nw) if args.nw else w["cloud"]()
+    n_inc = args.inc or w["n_inc"]
+    inc = incidences_monostatic(n_inc)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
+    res = {}
+    ref = None
+    for name, prec in (("c128", swm.SWM_C128), ("c64", swm.SWM_C64), ("bf16", swm.SWM_BF16)):
+        ctx = swm.swm_create(0)
+        mono = torch.zeros((n_inc, 2), dtype=torch.float64, device="cuda")
+
+        def step():
+            swm.swm_set_cloud(ctx, *dev)
+            swm.swm_build(ctx, K0, w["r_c"], prec)
+            rc = swm.swm_solve(ctx, inc, TOL, args.restart, 2000)
+            swm.swm_rcs_monostatic(ctx, mono)
+            return rc
+
+        step()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            rc = step()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+        st = swm.swm_get_stats(ctx)
+        sig = mono.cpu().numpy()[:, 0].copy()
+        if ref is None:
+            ref = sig
+        ms = 1e3 * float(np.median(ts))
+        res[name] = {"ms_per_step": ms, "value": st["n"] * n_inc / (ms * 1e-3), "iterations": st["iterations"],
+                     "outer_or_restarts": st["restarts"], "rel_residual": st["rel_residual"], "rc": rc,
+                     "phase_ms": {k: st[k] for k in ("ms_neighbour", "ms_fill", "ms_precond", "ms_rhs", "ms_solve",
+                                                     "ms_rcs")},
+                     "rcs_err_db_vs_c128": rcs_db_error(sig, ref)}
+        swm.swm_destroy(ctx)
+    for name in res:
+        res[name]["speedup_vs_c128"] = res["c128"]["ms_per_step"] / res[name]["ms_per_step"]
+    print(json.dumps({"kind": "precision_compare", "workload": args.workload, "description": w["text"],
+                      "nw": cl.nw, "incidences": n_inc, "restart": args.restart, "tol": TOL, "unit": UNIT,
+                      "paths": res}))
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -512,10 +567,15 @@ def main():
     ap.add_argument("--inc", type=int, default=0, help="incidences of a larger workload (default: its own)")
     ap.add_argument("--restart", type=int, default=RESTART)
     ap.add_argument("--nw", type=int, default=0, help="wire count of a larger workload (default: its own)")
+    ap.add_argument("--compare-precisions", action="store_true",
+                    help="larger workload: time the float64, complex64 and bfloat16-refinement paths")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.workload != "mid" and args.impl == "ours":
-        run_scale(args)
+        if args.compare_precisions:
+            run_compare(args)
+        else:
+            run_scale(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -75,7 +75,14 @@ extern "C" {
 /* precision of the fill, the stored blocks and the Krylov vectors */
 #define SWM_C128 0 /* plain path: FP64 kernel evaluation, complex128 blocks, complex128 GMRES */
 #define SWM_C64 1  /* fast path: FP64 per-block geometry, FP32 kernel evaluation, complex64 blocks
-                      and vectors, FP64 dot products, norms, Hessenberg and rotations */
+                      and vectors; FP64 dot products, norms, Hessenberg and rotations, except in
+                      the persistent solve of small systems, which keeps them in FP32 */
+#define SWM_BF16 2 /* mixed path: the SWM_C64 fill and blocks, plus Z M^-1 rounded to complex
+                      bfloat16 for the Krylov products; swm_solve runs FP64 iterative refinement
+                      (residuals b - Z x with the complex64 blocks, FP64 vectors) around GMRES on
+                      the bfloat16 blocks (complex64 vectors; inner tolerance 2e-3, loosened on the
+                      last refinement steps to what tol still needs); the GMRES
+                      solver is used whatever swm_set_solver chose; currents stored complex64 */
 
 /* limits */
 #define SWM_MAX_SEG 16  /* segments per wire: 2 <= n_s <= SWM_MAX_SEG */
@@ -134,8 +141,10 @@ typedef struct swm_stats {
  * Environment: SWM_SPLIT_ROWS (default 524288) -- systems with at least this many unknowns run
  * each GMRES step as a streaming block-sparse product plus separate dot products, smaller ones
  * as one fused kernel; SWM_PERSIST (default 1) -- 0 solves small systems with one launch per
- * kernel of each GMRES step instead of the persistent cooperative kernel; both read when the
- * context is created. */
+ * kernel of each GMRES step instead of the persistent cooperative kernel;
+ * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the
+ * persistent solve wait for n arrivals that never come, so each wait runs out (after 1 s) and the
+ * solve returns SWM_ETIMEOUT; all read when the context is created. */
 int swm_create(swm_ctx** out, int device, void* cuda_stream);
 
 /* Free every device buffer of the context and the context itself.  NULL is ignored. */

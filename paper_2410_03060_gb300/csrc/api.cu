@@ -151,6 +151,7 @@ int swm_create(swm_ctx** out, int device, void* cuda_stream) {
   ctx->stream = (cudaStream_t)cuda_stream;
   if (const char* e = std::getenv("SWM_SPLIT_ROWS")) ctx->split_rows = std::max<long long>(0, std::atoll(e));
   if (const char* e = std::getenv("SWM_PERSIST")) ctx->persist = std::atoi(e) != 0;
+  if (const char* e = std::getenv("SWM_TEST_BARRIER_EXTRA")) ctx->test_barrier_extra = std::max(0, std::atoi(e));
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
@@ -264,7 +265,8 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   if (ctx->nw < 1) return ctx->fail(SWM_ESTATE, "swm_build before swm_set_cloud");
   if (!(k > 0.0) || !std::isfinite(k)) return ctx->fail(SWM_EINVAL, "k must be positive and finite");
   if (std::isnan(r_c)) return ctx->fail(SWM_EINVAL, "r_c is NaN");
-  if (precision != SWM_C128 && precision != SWM_C64) return ctx->fail(SWM_EINVAL, "bad precision");
+  if (precision != SWM_C128 && precision != SWM_C64 && precision != SWM_BF16)
+    return ctx->fail(SWM_EINVAL, "bad precision");
   SWM_TRY(set_device(ctx));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   dfree_group(ctx, ctx->solve_bufs);
@@ -277,7 +279,10 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->k = k;
   ctx->rc = r_c;
   ctx->dense = dense;
-  ctx->prec = precision;
+  // SWM_BF16 fills and preconditions as SWM_C64 and then adds the bfloat16 copy of E
+  ctx->prec = precision == SWM_BF16 ? SWM_C64 : precision;
+  ctx->bf16 = precision == SWM_BF16;
+  ctx->E16 = nullptr;
   ctx->phase_begin(swm_ctx::PH_NEIGHBOUR);
   if (!reuse) {
     dfree_group(ctx, ctx->pattern_bufs);
@@ -297,6 +302,7 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->phase_end(swm_ctx::PH_FILL);
   ctx->phase_begin(swm_ctx::PH_PRECOND);
   SWM_TRY(build_precond(ctx));
+  if (ctx->bf16) SWM_TRY(make_e16(ctx));
   ctx->phase_end(swm_ctx::PH_PRECOND);
   SWM_TRY(prepare_far_field(ctx));
   SWM_TRY(finish_build(ctx));
@@ -351,8 +357,9 @@ int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restar
   SWM_TRY(compute_rhs(ctx, n_inc, frames));
   ctx->phase_end(swm_ctx::PH_RHS);
   ctx->phase_begin(swm_ctx::PH_SOLVE);
-  int rc = ctx->solver == SWM_SOLVER_GCR ? gcr_solve(ctx, tol, restart, max_iter)
-                                         : gmres_solve(ctx, tol, restart, max_iter);
+  int rc = ctx->bf16 ? refine_solve(ctx, frames, tol, restart, max_iter)
+           : ctx->solver == SWM_SOLVER_GCR ? gcr_solve(ctx, tol, restart, max_iter)
+                                           : gmres_solve(ctx, tol, restart, max_iter);
   ctx->phase_end(swm_ctx::PH_SOLVE);
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->phase_collect();

@@ -135,6 +135,9 @@ struct swm_ctx {
   // systems below split_rows with at most 8 right-hand sides solve in one persistent cooperative
   // kernel (SWM_PERSIST=0 turns it off); SM count and cooperative-launch support of the device
   bool persist = true;
+  // test hook (SWM_TEST_BARRIER_EXTRA): grid barriers of the persistent solve wait for this many
+  // arrivals more than there are CTAs, so every wait runs out and the solve reports SWM_ETIMEOUT
+  int test_barrier_extra = 0;
   int nsm = 0;
   int coop = 0;
   int smem_optin = 0;  // shared memory a CTA may opt in to (bytes)
@@ -143,6 +146,8 @@ struct swm_ctx {
   void* Z = nullptr;     // values of Z in layout `full`
   void* Zp = nullptr;    // values of Z * blockdiag(Z)^-1 without its identity diagonal, layout `offd`
   void* Minv = nullptr;  // inverses of the self blocks
+  void* E16 = nullptr;   // precision SWM_BF16: E as complex bfloat16 (inner products of the refinement)
+  bool bf16 = false;     // the last build was SWM_BF16 (values complex64, plus E16)
 
   // last solve
   int n_rhs = 0;
@@ -263,5 +268,13 @@ int ensure_poll_slots(swm_ctx* ctx);
 int apply_minv(swm_ctx* ctx, const void* Y);
 // gcr.cu: the paper's GCR solver (alternative to GMRES)
 int gcr_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
+// krylov.cu: GMRES on the bfloat16 copy of E (inner solve of the refinement); y-space result
+int gmres_inner_bf16(swm_ctx* ctx, double tol, int restart, int max_iter, void** y_out, int* iters);
+// rhs_ff.cu: right-hand sides in float64 into `out` ([n_inc][N], internal order)
+int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out);
+// refine.cu: float64 iterative refinement around bfloat16-storage GMRES (precision SWM_BF16)
+int refine_solve(swm_ctx* ctx, const double* frames_dev, double tol, int restart, int max_iter);
+// precond.cu: bfloat16 copy of E (ctx->E16) for precision SWM_BF16
+int make_e16(swm_ctx* ctx);
 
 }  // namespace swm

@@ -21,43 +21,11 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "krylov_common.cuh"
 
 namespace swm {
 
 namespace {
-
-struct KState {
-  int j;          // Arnoldi step inside the cycle
-  int cycle_done; // no active right-hand side left in this cycle
-  int all_conv;   // every right-hand side met tol at the start of this cycle
-  int iters;      // total Arnoldi steps
-  int numeric;    // a NaN/Inf appeared
-  int cycles;     // restart cycles (persistent solve)
-  int pad[2];
-};
-
-struct KPtr {
-  KState* st;
-  unsigned* counter;  // [R]
-  int* active;        // [R]
-  int* jlast;         // [R]
-  double* inv_h;      // [R]
-  double* bnorm;      // [R]
-  double* resid;      // [R]
-  c128* H;            // [R][(restart + 1) * restart]
-  double* cs;         // [R][restart]
-  c128* sn;           // [R][restart]
-  c128* g;            // [R][restart + 1]
-  c128* hc;           // [R][restart + 1]
-  c128* hc2;          // [R][restart + 1]
-  c128* coef;         // [R][restart]
-  c128* part;         // [R][nchunk][restart + 1]
-  double* partn;      // [R][nchunk]
-  int R, restart, nchunk, chunk;
-  int nschunk, schunk;  // chunks of the fused step kernel (finer, for more CTAs)
-  int64_t N;
-  double tol;
-};
 
 constexpr int kRows = 256;  // CTA width of the vector kernels
 constexpr int kG = 8;       // lanes per scalar row in the block-sparse product
@@ -69,10 +37,10 @@ __device__ __forceinline__ bool finite_c(cplx<T> z) {
 
 // mode 0 (Arnoldi): x = W_src * inv_h; V[j] = x (row owners); W_dst = x + E x.
 // mode 1 (residual): W_dst = B - (Y + E Y).
-template <typename TV>
+template <typename TV, typename TE>
 __global__ void __launch_bounds__(kRows) k_apply(int mode, KPtr P, const int32_t* __restrict__ rowwire,
                                                  const int64_t* __restrict__ off, Layout lay,
-                                                 const cplx<TV>* __restrict__ E, const cplx<TV>* __restrict__ B,
+                                                 const TE* __restrict__ E, const cplx<TV>* __restrict__ B,
                                                  cplx<TV>* __restrict__ Y, cplx<TV>* __restrict__ W0,
                                                  cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ V) {
   if (mode == 0 && P.st->cycle_done) return;
@@ -92,7 +60,7 @@ __global__ void __launch_bounds__(kRows) k_apply(int mode, KPtr P, const int32_t
     const int K = lay.K[p];
     const int64_t vb = lay.rowbase[p] + (int64_t)i * K;
     const int32_t* cm = lay.colmap + lay.cmbase[p];
-    for (int c = sub; c < K; c += kG) cfma(acc, E[vb + c], src[cm[c]]);
+    for (int c = sub; c < K; c += kG) cfma(acc, ELoad<TV, TE>::ld(E + vb + c), src[cm[c]]);
   }
 #pragma unroll
   for (int o = kG / 2; o > 0; o >>= 1) {
@@ -202,9 +170,9 @@ __device__ void reduce_dots(const KPtr& P, int j, int r, c128* __restrict__ dst,
 // (P.schunk rows, a multiple of 32) and a block of RB right-hand sides that share every read of E.
 // Eight lanes share a scalar row; the 32 row groups of the CTA take the chunk's rows in turn, with
 // their descriptors loaded up front.
-template <typename TV, int RB>
+template <typename TV, typename TE, int RB>
 __global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restrict__ rinfo,
-                                                const int32_t* __restrict__ colmap, const cplx<TV>* __restrict__ E,
+                                                const int32_t* __restrict__ colmap, const TE* __restrict__ E,
                                                 cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
                                                 cplx<TV>* __restrict__ V) {
   if (P.st->cycle_done) return;
@@ -245,7 +213,7 @@ __global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restric
     if (any) {
       const int32_t* cm = colmap + ri[t].cmb;
       for (int c = sub; c < ri[t].K; c += kG) {
-        const cplx<TV> e = E[ri[t].vb + c];
+        const cplx<TV> e = ELoad<TV, TE>::ld(E + ri[t].vb + c);
         const int64_t col = cm[c];
 #pragma unroll
         for (int b = 0; b < RB; ++b)
@@ -287,9 +255,9 @@ __global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restric
 
 // Large-N form of the step, part 1: normalise and multiply by A = I + E, streaming.  One scalar row
 // per group of eight lanes, no shared memory and no barrier, so many rows' loads are in flight.
-template <typename TV, int RB>
+template <typename TV, typename TE, int RB>
 __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restrict__ rinfo,
-                                                const int32_t* __restrict__ colmap, const cplx<TV>* __restrict__ E,
+                                                const int32_t* __restrict__ colmap, const TE* __restrict__ E,
                                                 cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
                                                 cplx<TV>* __restrict__ V) {
   if (P.st->cycle_done) return;
@@ -318,7 +286,7 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
     const int32_t* cm = colmap + ri.cmb;
     int c = sub;
     for (; c + kG < ri.K; c += 2 * kG) {
-      const cplx<TV> e0 = E[ri.vb + c], e1 = E[ri.vb + c + kG];
+      const cplx<TV> e0 = ELoad<TV, TE>::ld(E + ri.vb + c), e1 = ELoad<TV, TE>::ld(E + ri.vb + c + kG);
       const int64_t c0 = cm[c], c1 = cm[c + kG];
 #pragma unroll
       for (int b = 0; b < RB; ++b)
@@ -330,7 +298,7 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
         }
     }
     if (c < ri.K) {
-      const cplx<TV> e0 = E[ri.vb + c];
+      const cplx<TV> e0 = ELoad<TV, TE>::ld(E + ri.vb + c);
       const int64_t c0 = cm[c];
 #pragma unroll
       for (int b = 0; b < RB; ++b)
@@ -672,687 +640,10 @@ __global__ void k_rowwire(int64_t nw, const int64_t* __restrict__ off, Layout la
   }
 }
 
-// ------------------------------------------------------------------------------------------------
-// Persistent solve: the whole restarted GMRES in one cooperative launch, for systems of up to a
-// few hundred thousand unknowns with at most 8 right-hand sides.  There one Arnoldi step moves
-// only a few megabytes, so launch gaps, host polls and dependent latencies (L2 round trips,
-// float64 divides and square roots) set its time, not bandwidth.  Every CTA owns a contiguous
-// chunk of rows and keeps in shared memory, when they fit: its slice of the current Krylov
-// vector, its rows of the basis V, and its rows of E with their column map and row descriptors
-// (loaded once).  The product first gathers the vector at the CTA's column-map slice (the rows
-// of one wire share their block-row's column map) into shared memory, all loads in flight at
-// once, and then forms each row's sum from shared memory.  One Arnoldi step has four phases
-// separated by three grid barriers:
-//   A: v_j = w / |w| (own rows), u = A v_j, first dots V^H u
-//   B: sum of the dot partials, u -= V h1, second dots V^H u
-//   C: sum, u -= V h2, w = u written for the next gather, |w|^2 partials
-//   D: sum of the norms, Hessenberg column, Givens rotation, residual estimate and activity
-// Phase D and every partial sum are computed by every CTA from the same partials in the same
-// order, so all CTAs reach identical decisions and run identical barrier sequences.  The dot
-// products, their sums over the CTAs (in a fixed pairwise order), the rotations and the
-// triangular solve run in the precision of the vectors: float64 on the complex128 path, float32 on
-// the complex64 path, whose vectors carry float32 rounding anyway (on this GPU a float64 warp
-// instruction issues about sixteen times slower than a float32 one, which would otherwise set
-// the step time).  The initial residual norm and the relative residual estimate are float64.
-// A barrier waits at most kBarrierNs; a CTA that gives up raises an abort flag that the other
-// CTAs also poll, every CTA then returns, and the host reports SWM_ETIMEOUT.
-constexpr int kPT = 512;              // threads of a persistent-solve CTA
-constexpr int kPWarps = kPT / 32;
-constexpr int kPersistMaxR = 8;       // right-hand sides of one persistent solve
-constexpr int kPersistMaxRowsPerThread = 4;
-constexpr unsigned long long kBarrierNs = 1000000000ull;  // 1 s
-
-struct PSync {
-  unsigned count;  // arrivals at grid barriers since the launch
-  int abort;       // a barrier ran out of time
-  int pad[30];
-};
-
-struct PArgs {
-  KPtr P;                  // st, jlast, resid, H, coef, R, restart, N, tol
-  PSync* sync;
-  const RowInfo* rinfo;
-  const int32_t* colmap;
-  const void* E;
-  const void* B;
-  void* Y;
-  void* W;                 // current unnormalised Krylov vector, all rows [R][N]
-  void* V;                 // basis [restart + 1][R][N] (unused when it lives in shared memory)
-  void* part1;             // [R][restart + 1][G] first dots (vector precision)
-  void* part2;             // [R][restart + 1][G] second dots
-  void* partn;             // [R][G] squared norms
-  int G, rows, max_iter;
-  int vsm, esm;            // V / E slices in shared memory
-  int64_t emax, cmax;      // largest E and column-map slice of a CTA (entries)
-};
-
-// Byte offsets of the shared-memory arrays of the persistent kernel.
-struct PLayout {
-  size_t h1, h2, yv, gg, sn, col, ri, ys, vs, es, xg, cs, cm, total;
-};
-__host__ __device__ inline size_t p_align16(size_t x) { return (x + 15) & ~size_t(15); }
-__host__ __device__ inline PLayout persist_layout(int RB, int R, int restart, int rows, size_t cb, int vsm, int esm,
-                                                  int64_t emax, int64_t cmax) {
-  PLayout L;
-  const size_t R1 = restart + 1;
-  size_t o = 0;
-  L.yv = o; o += sizeof(c128) * RB * restart;
-  L.h1 = o; o += p_align16(cb * RB * R1);  // coefficients and rotations in the vector precision
-  L.h2 = o; o += p_align16(cb * RB * R1);
-  L.gg = o; o += p_align16(cb * RB * R1);
-  L.sn = o; o += p_align16(cb * RB * restart);
-  L.col = o; o += p_align16(cb * RB * R1);
-  L.ri = o; o += esm ? 16 * (size_t)rows : 0;
-  L.ys = o; o += p_align16(cb * RB * rows);
-  L.vs = o; o += vsm ? p_align16(cb * R1 * R * rows) : 0;
-  L.es = o; o += esm ? p_align16(cb * (size_t)emax) : 0;
-  L.xg = o; o += esm ? p_align16(cb * (size_t)R * cmax) : 0;
-  L.cs = o; o += p_align16(cb / 2 * RB * restart);
-  L.cm = o; o += esm ? 4 * (size_t)cmax : 0;
-  L.total = p_align16(o);
-  return L;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-template <typename TV>
-__device__ __forceinline__ cplx<TV> ldcg_c(const cplx<TV>* p);
-template <>
-__device__ __forceinline__ cplx<float> ldcg_c<float>(const cplx<float>* p) {
-  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-  return mkc<float>(v.x, v.y);
-}
-template <>
-__device__ __forceinline__ cplx<double> ldcg_c<double>(const cplx<double>* p) {
-  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
-  return mkc<double>(v.x, v.y);
-}
-
-// Grid barrier with a time limit.  Returns false (in every thread of the CTA) if this CTA gave up
-// or saw another CTA give up.
-__device__ bool grid_sync(PSync* s, unsigned G, unsigned* epoch, int* ok_sm) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned target = (*epoch + 1u) * G;
-    *epoch += 1u;
-    __threadfence();
-    atomicAdd(&s->count, 1u);
-    int ok = 1;
-    const unsigned long long t0 = global_ns();
-    while (ld_acquire_u32(&s->count) < target) {
-      if (*(volatile int*)&s->abort) {
-        ok = 0;
-        break;
-      }
-      if (global_ns() - t0 > kBarrierNs) {
-        atomicExch(&s->abort, 1);
-        ok = 0;
-        break;
-      }
-      __nanosleep(20);
-    }
-    __threadfence();
-    *ok_sm = ok;
-  }
-  __syncthreads();
-  return *ok_sm != 0;
-}
-
-// Sum of G partials (contiguous, read through L2), all of a lane's loads issued together, added
-// pairwise in the same order in every CTA.
-template <typename T>
-__device__ __forceinline__ T ldcg_s(const T* p) {
-  return __ldcg(p);
-}
-template <typename T>
-__device__ __forceinline__ cplx<T> sum_g_c(const cplx<T>* __restrict__ p, int G, int lane) {
-  T re = 0, im = 0;
-  for (int c0 = 0; c0 < G; c0 += 256) {
-    cplx<T> v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int c = c0 + lane + 32 * u;
-      v[u] = c < G ? ldcg_c<T>(p + c) : mkc<T>(0, 0);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = v[u] + v[u + 4];
-    v[0] = v[0] + v[2];
-    v[1] = v[1] + v[3];
-    re += v[0].re + v[1].re;
-    im += v[0].im + v[1].im;
-  }
-  return mkc<T>(warp_sum(re), warp_sum(im));
-}
-template <typename T>
-__device__ __forceinline__ T sum_g_d(const T* __restrict__ p, int G, int lane) {
-  T s = 0;
-  for (int c0 = 0; c0 < G; c0 += 256) {
-    T v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int c = c0 + lane + 32 * u;
-      v[u] = c < G ? ldcg_s<T>(p + c) : T(0);
-    }
-    s += ((v[0] + v[4]) + (v[2] + v[6])) + ((v[1] + v[5]) + (v[3] + v[7]));
-  }
-  return warp_sum(s);
-}
-
-// dst[b][i] (shared) = sum over the G CTAs of part[(b * R1 + i) * G + c], for active b, i <= j.
-template <typename T>
-__device__ void p_reduce(const cplx<T>* __restrict__ part, int G, int R, int R1, int j, const int* act, cplx<T>* dst) {
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int nt = R * (j + 1);
-  for (int k = wp; k < nt; k += kPWarps) {
-    const int b = k / (j + 1), i = k % (j + 1);
-    if (!act[b]) continue;
-    const cplx<T> v = sum_g_c<T>(part + (int64_t)(b * R1 + i) * G, G, lane);
-    if (lane == 0) dst[b * R1 + i] = v;
-  }
-}
-
-// Rows of V: row t of basis vector i, right-hand side b is at(i, b)[t].
-template <typename TV>
-struct VRows {
-  cplx<TV>* base;
-  int64_t stride;
-  int R;
-  __device__ __forceinline__ cplx<TV>* at(int i, int b) const { return base + ((int64_t)i * R + b) * stride; }
-};
-
-// Partial dots conj(V_i[b]) . ys[b] over the CTA's rows, for active b and i <= j.
-template <typename TV>
-__device__ void p_dots(const VRows<TV>& V, const cplx<TV>* ys, int rows, int cnt, int R, int R1, int j, int G,
-                       const int* act, cplx<TV>* __restrict__ part) {
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int nt = R * (j + 1);
-  for (int k = wp; k < nt; k += kPWarps) {
-    const int b = k / (j + 1), i = k % (j + 1);
-    if (!act[b]) continue;
-    const cplx<TV>* vi = V.at(i, b);
-    const cplx<TV>* w = ys + b * rows;
-    cplx<TV> acc = mkc<TV>(0, 0);
-    int t = lane;
-    for (; t + 96 < cnt; t += 128) {
-      cplx<TV> v[4], x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        v[u] = vi[t + 32 * u];
-        x[u] = w[t + 32 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        acc.re = fma(v[u].re, x[u].re, fma(v[u].im, x[u].im, acc.re));
-        acc.im = fma(v[u].re, x[u].im, fma(-v[u].im, x[u].re, acc.im));
-      }
-    }
-    for (; t < cnt; t += 32) {
-      const cplx<TV> v = vi[t], x = w[t];
-      acc.re = fma(v.re, x.re, fma(v.im, x.im, acc.re));
-      acc.im = fma(v.re, x.im, fma(-v.im, x.re, acc.im));
-    }
-    const TV re = warp_sum(acc.re), im = warp_sum(acc.im);
-    if (lane == 0) part[(int64_t)(b * R1 + i) * G + blockIdx.x] = mkc<TV>(re, im);
-  }
-}
-
-// Block sums of per-thread values nrm[b] to partn[b][blockIdx.x] (warp sums, then warp 0 sums
-// the warps' values as a tree).
-template <typename T, int RB>
-__device__ void p_norm_partials(const T* nrm, int R, int G, T* __restrict__ partn, T (*red)[RB]) {
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-#pragma unroll
-  for (int b = 0; b < RB; ++b) {
-    const T s = warp_sum(nrm[b]);
-    if (lane == 0) red[wp][b] = s;
-  }
-  __syncthreads();
-  if (wp == 0) {
-#pragma unroll
-    for (int b = 0; b < RB; ++b) {
-      if (b >= R) break;
-      const T s = warp_sum(lane < kPWarps ? red[lane][b] : T(0));
-      if (lane == 0) partn[(int64_t)b * G + blockIdx.x] = s;
-    }
-  }
-}
-
-// ys[b] -= sum_{i <= j} V_i[b] h[b][i] over the CTA's rows, for active b.  With W non-null the
-// result also goes to the global vector and the squared norms of the CTA's rows go to partn.
-template <typename TV, int RB>
-__device__ void p_update(const VRows<TV>& V, cplx<TV>* ys, int rows, int cnt, int64_t n0, int64_t N, int R, int R1,
-                         int j, const int* act, const cplx<TV>* h, cplx<TV>* __restrict__ W, TV* __restrict__ partn,
-                         int G, TV (*red)[RB]) {
-  TV nrm[RB];
-#pragma unroll
-  for (int b = 0; b < RB; ++b) nrm[b] = 0;
-#pragma unroll
-  for (int b = 0; b < RB; ++b) {
-    if (b >= R) break;
-    if (!act[b]) continue;
-    const cplx<TV>* hb = h + b * R1;
-    for (int t = threadIdx.x; t < cnt; t += kPT) {
-      cplx<TV> x = ys[b * rows + t];
-      int i = 0;
-      for (; i + 3 <= j; i += 4) {
-        cplx<TV> v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = V.at(i + u, b)[t];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const cplx<TV> hh = hb[i + u];
-          x.re = fma(-v[u].re, hh.re, fma(v[u].im, hh.im, x.re));
-          x.im = fma(-v[u].re, hh.im, fma(-v[u].im, hh.re, x.im));
-        }
-      }
-      for (; i <= j; ++i) {
-        const cplx<TV> v0 = V.at(i, b)[t];
-        const cplx<TV> hh = hb[i];
-        x.re = fma(-v0.re, hh.re, fma(v0.im, hh.im, x.re));
-        x.im = fma(-v0.re, hh.im, fma(-v0.im, hh.re, x.im));
-      }
-      ys[b * rows + t] = x;
-      if (W) {
-        W[(int64_t)b * N + n0 + t] = x;
-        nrm[b] = fma(x.re, x.re, fma(x.im, x.im, nrm[b]));
-      }
-    }
-  }
-  if (W) p_norm_partials<TV, RB>(nrm, R, G, partn, red);
-}
-
-// The CTA's slice of E: values, column map, row descriptors, and the gathered vector entries.
-template <typename TV>
-struct ESlice {
-  const cplx<TV>* e;
-  const int32_t* cm;
-  const RowInfo* ri;
-  int64_t ebase, cbase;  // subtracted from the descriptors' offsets
-  cplx<TV>* xg;          // [R][cstride] gathered vector at the column-map slice (shared) or null
-  int clen, cstride;
-};
-
-// Rows of the CTA times A = I + E for the R right-hand sides of `src`.
-// mode 0 (Arnoldi): x = ys * inv (the normalised v_j, stored in V_j), ys = x + inv * E src.
-// mode 1 (residual): ys = W = B - (Y + E Y), squared norms to partn.
-template <typename TV, int RB>
-__device__ void p_product(int mode, const PArgs& a, const ESlice<TV>& S, const cplx<TV>* __restrict__ src,
-                          cplx<TV>* ys, int cnt, int64_t n0, const VRows<TV>& V, int j, const int* act,
-                          const TV* inv, const cplx<TV>* __restrict__ B, cplx<TV>* __restrict__ W,
-                          TV (*red)[RB]) {
-  const int R = a.P.R;
-  const int64_t N = a.P.N;
-  bool on[RB];
-  TV sc[RB];
-  TV nrm[RB];
-#pragma unroll
-  for (int b = 0; b < RB; ++b) {
-    on[b] = b < R && (mode == 1 || act[b]);
-    sc[b] = b < R ? inv[b] : TV(0);
-    nrm[b] = 0;
-  }
-  if (S.xg) {
-    // gather src at the column-map slice: every load in flight at once
-#pragma unroll 4
-    for (int q = threadIdx.x; q < S.clen; q += kPT) {
-      const int64_t col = S.cm[q];
-#pragma unroll
-      for (int b = 0; b < RB; ++b)
-        if (on[b]) S.xg[b * S.cstride + q] = ldcg_c<TV>(src + (int64_t)b * N + col);
-    }
-    __syncthreads();
-  }
-  for (int t = threadIdx.x; t < cnt; t += kPT) {
-    const RowInfo ri = S.ri[t];
-    const cplx<TV>* e = S.e + (ri.vb - S.ebase);
-    cplx<TV> acc[RB];
-#pragma unroll
-    for (int b = 0; b < RB; ++b) acc[b] = mkc<TV>(0, 0);
-    if (S.xg) {
-      const cplx<TV>* xq = S.xg + (ri.cmb - S.cbase);
-      int c = 0;
-      for (; c + 1 < ri.K; c += 2) {
-        const cplx<TV> e0 = e[c], e1 = e[c + 1];
-#pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) {
-            cfma(acc[b], e0, xq[b * S.cstride + c]);
-            cfma(acc[b], e1, xq[b * S.cstride + c + 1]);
-          }
-      }
-      if (c < ri.K) {
-        const cplx<TV> e0 = e[c];
-#pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) cfma(acc[b], e0, xq[b * S.cstride + c]);
-      }
-    } else {
-      const int32_t* cm = S.cm + (ri.cmb - S.cbase);
-      int c = 0;
-      for (; c + 3 < ri.K; c += 4) {
-        cplx<TV> ev[4];
-        int64_t col[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          ev[u] = e[c + u];
-          col[u] = cm[c + u];
-        }
-#pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) {
-            cplx<TV> x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = ldcg_c<TV>(src + (int64_t)b * N + col[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) cfma(acc[b], ev[u], x[u]);
-          }
-      }
-      for (; c < ri.K; ++c) {
-        const cplx<TV> ev = e[c];
-        const int64_t col = cm[c];
-#pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) cfma(acc[b], ev, ldcg_c<TV>(src + (int64_t)b * N + col));
-      }
-    }
-    const int64_t n = n0 + t;
-#pragma unroll
-    for (int b = 0; b < RB; ++b) {
-      if (!on[b]) continue;
-      if (mode == 0) {
-        const cplx<TV> x = sc[b] * ys[b * a.rows + t];
-        V.at(j, b)[t] = x;
-        ys[b * a.rows + t] = x + sc[b] * acc[b];
-      } else {
-        const cplx<TV> y = src[(int64_t)b * N + n];  // own row of Y, written by this CTA
-        const cplx<TV> r = B[(int64_t)b * N + n] - (y + acc[b]);
-        ys[b * a.rows + t] = r;
-        W[(int64_t)b * N + n] = r;
-        nrm[b] = fma(r.re, r.re, fma(r.im, r.im, nrm[b]));
-      }
-    }
-  }
-  if (mode == 1) p_norm_partials<TV, RB>(nrm, R, a.G, (TV*)a.partn, red);
-}
-
-template <typename TV, int RB>
-__global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
-  using C = cplx<TV>;
-  const KPtr& P = a.P;
-  const int R = P.R, RS = P.restart, R1 = RS + 1, G = a.G;
-  const int64_t N = P.N;
-  const int64_t n0 = (int64_t)blockIdx.x * a.rows;
-  const int cnt = N > n0 ? (int)(N - n0 < (int64_t)a.rows ? N - n0 : (int64_t)a.rows) : 0;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const C* B = (const C*)a.B;
-  C* Y = (C*)a.Y;
-  C* W = (C*)a.W;
-
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const PLayout L = persist_layout(RB, R, RS, a.rows, sizeof(C), a.vsm, a.esm, a.emax, a.cmax);
-  C* h1 = reinterpret_cast<C*>(sm_raw + L.h1);         // [RB][R1] first-pass coefficients
-  C* h2 = reinterpret_cast<C*>(sm_raw + L.h2);         // [RB][R1] second-pass coefficients
-  c128* yv = reinterpret_cast<c128*>(sm_raw + L.yv);   // [RB][RS] back-solve / coefficients
-  C* part1 = (C*)a.part1;
-  C* part2 = (C*)a.part2;
-  TV* partn = (TV*)a.partn;
-  C* gg = reinterpret_cast<C*>(sm_raw + L.gg);         // [RB][R1] rotated residual
-  C* sn = reinterpret_cast<C*>(sm_raw + L.sn);         // [RB][RS] rotation sines
-  C* colv = reinterpret_cast<C*>(sm_raw + L.col);      // [RB][R1] Hessenberg column
-  TV* cs = reinterpret_cast<TV*>(sm_raw + L.cs);       // [RB][RS] rotation cosines
-  C* ys = reinterpret_cast<C*>(sm_raw + L.ys);         // [RB][rows]
-  VRows<TV> V;
-  V.R = R;
-  if (a.vsm) {
-    V.base = reinterpret_cast<C*>(sm_raw + L.vs);
-    V.stride = a.rows;
-  } else {
-    V.base = (C*)a.V + n0;
-    V.stride = N;
-  }
-  ESlice<TV> S;
-  S.e = (const C*)a.E;
-  S.cm = a.colmap;
-  S.ri = a.rinfo + n0;
-  S.ebase = 0;
-  S.cbase = 0;
-  S.xg = nullptr;
-  S.clen = 0;
-  S.cstride = 0;
-  if (a.esm && cnt > 0) {
-    RowInfo* ri_s = reinterpret_cast<RowInfo*>(sm_raw + L.ri);
-    C* e_s = reinterpret_cast<C*>(sm_raw + L.es);
-    int32_t* cm_s = reinterpret_cast<int32_t*>(sm_raw + L.cm);
-    const RowInfo first = a.rinfo[n0], last = a.rinfo[n0 + cnt - 1];
-    const int64_t elen = last.vb + last.K - first.vb;
-    const int64_t clen = (int64_t)last.cmb + last.K - first.cmb;
-    if (elen <= a.emax && clen <= a.cmax) {  // always true for the host's slice bounds
-      for (int t = threadIdx.x; t < cnt; t += kPT) ri_s[t] = a.rinfo[n0 + t];
-      for (int64_t i = threadIdx.x; i < elen; i += kPT) e_s[i] = S.e[first.vb + i];
-      for (int64_t i = threadIdx.x; i < clen; i += kPT) cm_s[i] = a.colmap[first.cmb + i];
-      S.e = e_s;
-      S.cm = cm_s;
-      S.ri = ri_s;
-      S.ebase = first.vb;
-      S.cbase = first.cmb;
-      S.xg = reinterpret_cast<C*>(sm_raw + L.xg);
-      S.clen = (int)clen;
-      S.cstride = (int)a.cmax;
-    }
-  }
-  __shared__ double bnorm[RB], resid[RB];
-  __shared__ TV inv[RB], nrm2[RB];
-  __shared__ TV red[kPWarps][RB];
-  __shared__ int act[RB], jl[RB];
-  __shared__ int s_j, s_iters, s_done, s_conv, s_numeric, s_cycles, s_ok;
-  __shared__ unsigned s_epoch;
-  if (threadIdx.x == 0) {
-    s_epoch = 0;
-    s_iters = 0;
-    s_numeric = 0;
-    s_cycles = 0;
-    s_conv = 0;
-  }
-  if (threadIdx.x < RB) {
-    act[threadIdx.x] = 0;
-    inv[threadIdx.x] = 0;
-    jl[threadIdx.x] = 0;
-  }
-  __syncthreads();
-  bool first = true;
-  bool ok = true;
-  while (true) {
-    if (!first) {
-      // ---- end of a cycle: CTA 0 solves the triangular systems (one warp per right-hand side)
-      if (blockIdx.x == 0 && wp < R) {
-        const int b = wp, n = jl[b];
-        const c128* Hb = P.H + (int64_t)b * R1 * RS;
-        C* y = reinterpret_cast<C*>(yv) + b * RS;
-        for (int i = n - 1; i >= 0; --i) {
-          TV sr = 0, si = 0;
-          for (int l = i + 1 + lane; l < n; l += 32) {
-            const C h = ccast<TV>(Hb[i * RS + l]), v = y[l];
-            sr += h.re * v.re - h.im * v.im;
-            si += h.re * v.im + h.im * v.re;
-          }
-          sr = warp_sum(sr);
-          si = warp_sum(si);
-          if (lane == 0) {
-            const C d = ccast<TV>(Hb[i * RS + i]);
-            const TV den = d.re * d.re + d.im * d.im;
-            const TV iden = den > TV(0) ? TV(1) / den : TV(0);
-            y[i] = (gg[b * R1 + i] - mkc<TV>(sr, si)) * mkc<TV>(d.re * iden, -d.im * iden);
-          }
-          __syncwarp();
-        }
-        for (int i = lane; i < RS; i += 32) P.coef[(int64_t)b * RS + i] = i < n ? ccast<double>(y[i]) : mkc(0.0, 0.0);
-      }
-      if (!(ok = grid_sync(a.sync, G, &s_epoch, &s_ok))) break;
-      // ---- Y += V coef on the CTA's rows
-      C* yc = reinterpret_cast<C*>(yv);
-      for (int k = threadIdx.x; k < R * RS; k += kPT) yc[k] = ccast<TV>(ldcg_c<double>(P.coef + k));
-      __syncthreads();
-      for (int k = threadIdx.x; cnt > 0 && k < R * cnt; k += kPT) {
-        const int b = k / cnt, t = k % cnt;
-        const int n = jl[b];
-        if (n == 0) continue;
-        const int64_t row = (int64_t)b * N + n0 + t;
-        C acc = Y[row];
-        for (int i = 0; i < n; ++i) cfma(acc, V.at(i, b)[t], yc[b * RS + i]);
-        Y[row] = acc;
-      }
-      if (!(ok = grid_sync(a.sync, G, &s_epoch, &s_ok))) break;
-    }
-    // ---- residual W = B - A Y on the CTA's rows, its squared norms
-    p_product<TV, RB>(1, a, S, Y, ys, cnt, n0, V, 0, act, inv, B, W, red);
-    if (!(ok = grid_sync(a.sync, G, &s_epoch, &s_ok))) break;
-    // ---- start of a cycle (every CTA)
-    if (wp < R) {
-      const TV t = sum_g_d<TV>(partn + (int64_t)wp * G, G, lane);
-      if (lane == 0) nrm2[wp] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < R) {
-      const int b = threadIdx.x;
-      const double beta = sqrt((double)nrm2[b]);
-      if (first) bnorm[b] = beta > 0.0 ? beta : 1.0;
-      const double res = beta / bnorm[b];
-      resid[b] = res;
-      jl[b] = 0;
-      const bool ac = isfinite(res) && res > P.tol;
-      if (!isfinite(res)) s_numeric = 1;
-      act[b] = ac ? 1 : 0;
-      inv[b] = beta > 0.0 ? (TV)(1.0 / beta) : TV(0);
-      gg[b * R1] = mkc<TV>((TV)beta, TV(0));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int any = 0;
-      for (int b = 0; b < R; ++b) any |= act[b];
-      s_conv = any ? 0 : 1;
-      s_j = 0;
-      s_done = (!any || s_iters >= a.max_iter) ? 1 : 0;
-      if (!first) s_cycles += 1;
-    }
-    __syncthreads();
-    first = false;
-    if (s_conv || s_numeric || s_iters >= a.max_iter) break;
-    // ---- Arnoldi steps
-    while (!s_done) {
-      const int j = s_j;
-      // A: v_j and u = A v_j on own rows, first dots
-      p_product<TV, RB>(0, a, S, W, ys, cnt, n0, V, j, act, inv, B, W, red);
-      __syncthreads();
-      p_dots<TV>(V, ys, a.rows, cnt, R, R1, j, G, act, part1);
-      if (!(ok = grid_sync(a.sync, G, &s_epoch, &s_ok))) break;
-      // B: h1, u -= V h1, second dots
-      p_reduce<TV>(part1, G, R, R1, j, act, h1);
-      __syncthreads();
-      p_update<TV, RB>(V, ys, a.rows, cnt, n0, N, R, R1, j, act, h1, nullptr, nullptr, G, red);
-      __syncthreads();
-      p_dots<TV>(V, ys, a.rows, cnt, R, R1, j, G, act, part2);
-      if (!(ok = grid_sync(a.sync, G, &s_epoch, &s_ok))) break;
-      // C: h2, w = u - V h2 to global, squared norms
-      p_reduce<TV>(part2, G, R, R1, j, act, h2);
-      __syncthreads();
-      p_update<TV, RB>(V, ys, a.rows, cnt, n0, N, R, R1, j, act, h2, W, partn, G, red);
-      if (!(ok = grid_sync(a.sync, G, &s_epoch, &s_ok))) break;
-      // D: norms, Hessenberg column, rotations, residual estimate (every CTA, same values)
-      if (wp < R && act[wp]) {
-        const TV t = sum_g_d<TV>(partn + (int64_t)wp * G, G, lane);
-        if (lane == 0) nrm2[wp] = t;
-      }
-      for (int k = threadIdx.x; k < R * (j + 1); k += kPT) {
-        const int b = k / (j + 1), i = k % (j + 1);
-        if (act[b]) colv[b * R1 + i] = h1[b * R1 + i] + h2[b * R1 + i];
-      }
-      __syncthreads();
-      if (threadIdx.x < R && act[threadIdx.x]) {
-        const int b = threadIdx.x;
-        C* col = colv + b * R1;
-        const TV h = sqrt(nrm2[b]);
-        for (int i = 0; i < j; ++i) {
-          const C x0 = col[i], x1 = col[i + 1];
-          const C s = sn[b * RS + i];
-          const TV c = cs[b * RS + i];
-          col[i] = c * x0 + s * x1;
-          col[i + 1] = mkc<TV>(-s.re, s.im) * x0 + c * x1;
-        }
-        const C x = col[j];
-        const TV ax2 = x.re * x.re + x.im * x.im;
-        const TV aa = sqrt(ax2);
-        const TV nu = sqrt(ax2 + h * h);
-        const TV inu = TV(1) / nu;
-        TV c;
-        C sv;
-        if (aa == TV(0)) {
-          c = TV(0);
-          sv = mkc<TV>(1, 0);
-        } else {
-          c = aa * inu;
-          const TV f = h * inu / aa;
-          sv = mkc<TV>(x.re * f, x.im * f);
-        }
-        cs[b * RS + j] = c;
-        sn[b * RS + j] = sv;
-        col[j] = c * x + h * sv;
-        const C gj = gg[b * R1 + j];
-        gg[b * R1 + j + 1] = mkc<TV>(-sv.re, sv.im) * gj;
-        gg[b * R1 + j] = c * gj;
-        // |g_{j+1}| = |s_j| |g_j| with |s_j| = h / nu
-        const double res = resid[b] * (double)(h * inu);
-        resid[b] = res;
-        jl[b] = j + 1;
-        if (!isfinite(h) || !isfinite(res)) {
-          s_numeric = 1;
-          act[b] = 0;
-        } else if (res <= P.tol || h == TV(0)) {
-          act[b] = 0;
-        }
-        inv[b] = h > TV(0) ? TV(1) / h : TV(0);
-      }
-      __syncthreads();
-      if (blockIdx.x == 0)
-        for (int k = threadIdx.x; k < R * (j + 1); k += kPT) {
-          const int b = k / (j + 1), i = k % (j + 1);
-          if (jl[b] == j + 1) P.H[(int64_t)b * R1 * RS + i * RS + j] = ccast<double>(colv[b * R1 + i]);
-        }
-      if (threadIdx.x == 0) {
-        int any = 0;
-        for (int b = 0; b < R; ++b) any |= act[b];
-        s_j = j + 1;
-        s_iters += 1;
-        s_done = (!any || j + 1 >= RS || s_iters >= a.max_iter) ? 1 : 0;
-      }
-      __syncthreads();
-    }
-    if (!ok) break;
-  }
-  // ---- results (CTA 0)
-  if (blockIdx.x == 0 && ok) {
-    if (threadIdx.x < R) {
-      P.resid[threadIdx.x] = resid[threadIdx.x];
-      P.jlast[threadIdx.x] = jl[threadIdx.x];
-    }
-    if (threadIdx.x == 0) {
-      P.st->iters = s_iters;
-      P.st->all_conv = s_conv;
-      P.st->numeric = s_numeric;
-      P.st->cycles = s_cycles;
-    }
-  }
-}
-
-template <typename TV>
-int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
+// Restarted GMRES on A = I + E with E stored as TE.  With y_out the result stays in y-space
+// (*y_out = the workspace's y, no M^-1 and no statistics); otherwise x = M^-1 y goes to ctx->Xv.
+template <typename TV, typename TE>
+int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter, void** y_out, KState* hs_out) {
   cudaStream_t st = ctx->stream;
   const int R = ctx->n_rhs;
   const int64_t N = ctx->N;
@@ -1430,77 +721,15 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   SWM_CK(cudaMemsetAsync(Y, 0, sizeof(cplx<TV>) * R * N, st));
   (void)S;
 
-  const cplx<TV>* E = (const cplx<TV>*)ctx->Zp;
   const cplx<TV>* Bv = (const cplx<TV>*)ctx->Bv;
   KState hs{};
   int cycles = 0;
   // small systems: the whole solve as one persistent cooperative kernel
   bool persisted = false;
-  const int prows = (int)(ceil_div(ceil_div(std::max<int64_t>(N, 1), ctx->nsm > 0 ? ctx->nsm : 1), 32) * 32);
-  if (ctx->persist && ctx->coop && ws->sync && N > 0 && N < ctx->split_rows &&
-      prows <= kPersistMaxRowsPerThread * kPT) {
-    const int G = (int)ceil_div(N, prows);
-    const int RB = R == 1 ? 1 : kPersistMaxR;
-    const void* fn = R == 1 ? (const void*)k_gmres_persist<TV, 1> : (const void*)k_gmres_persist<TV, kPersistMaxR>;
-    cudaFuncAttributes fa{};
-    SWM_CK(cudaFuncGetAttributes(&fa, fn));
-    const size_t limit = (size_t)std::max(0, ctx->smem_optin - (int)fa.sharedSizeBytes - 1024);
-    const size_t cb = sizeof(cplx<TV>);
-    // V in shared memory when it fits (it is read four times a step); then as large an E slice as
-    // the rest holds (column map + gathered vector about a third of the E entries: the rows of a
-    // wire share their column map).  A CTA whose slice is larger reads E from global memory.
-    int vsm = persist_layout(RB, R, restart, prows, cb, 1, 0, 0, 0).total <= limit ? 1 : 0;
-    const size_t base = persist_layout(RB, R, restart, prows, cb, vsm, 1, 0, 0).total + 64;
-    const int64_t mean_e = ceil_div(ctx->offd.nval, G);
-    int64_t emax = 0, cmax = 0;
-    if (base < limit) {
-      emax = (int64_t)((limit - base) / (cb + (4 + cb * R) / 3.0));
-      cmax = emax / 3;
-    }
-    const int esm = emax >= mean_e && emax > 0 ? 1 : 0;
-    if (!esm) emax = cmax = 0;
-    const size_t smem = persist_layout(RB, R, restart, prows, cb, vsm, esm, emax, cmax).total;
-    const bool fits = smem <= limit;
-    int occ = 0;
-    if (fits) {
-      SWM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      SWM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPT, smem));
-    }
-    if (occ >= 1 && G <= occ * ctx->nsm) {
-      PArgs pa{};
-      pa.P = P;
-      pa.sync = ws->sync;
-      pa.rinfo = (const RowInfo*)ctx->rowinfo;
-      pa.colmap = ctx->offd.colmap;
-      pa.E = E;
-      pa.B = Bv;
-      pa.Y = Y;
-      pa.W = W0;
-      pa.V = V;
-      pa.part1 = ws->pp1;
-      pa.part2 = ws->pp2;
-      pa.partn = ws->ppn;
-      pa.G = G;
-      pa.rows = prows;
-      pa.max_iter = max_iter;
-      pa.vsm = vsm;
-      pa.esm = esm;
-      pa.emax = emax;
-      pa.cmax = cmax;
-      SWM_CK(cudaMemsetAsync(ws->sync, 0, sizeof(PSync), st));
-      void* args[] = {&pa};
-      ctx->prof_begin(SWM_K_GMRES);
-      SWM_CK(cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kPT), args, smem, st));
-      ctx->prof_end(SWM_K_GMRES);
-      SWM_LAUNCHED();
-      PSync hsync{};
-      SWM_CK(cudaMemcpyAsync(&hs, P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
-      SWM_CK(cudaMemcpyAsync(&hsync, ws->sync, sizeof(PSync), cudaMemcpyDeviceToHost, st));
-      SWM_CK(cudaStreamSynchronize(st));
-      if (hsync.abort) return ctx->fail(SWM_ETIMEOUT, "GMRES: a grid barrier of the persistent solve timed out");
-      cycles = hs.cycles;
-      persisted = true;
-    }
+  {
+    PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V};
+    SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
+    if (persisted) cycles = hs.cycles;
   }
   const dim3 g_rows((unsigned)ceil_div(N * kG, kRows), R);
   const dim3 g_chunk((unsigned)P.nchunk, R);
@@ -1532,19 +761,19 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
       if (split) {
         const dim3 gsp((unsigned)ceil_div(N * kG, kRows), multi ? (unsigned)ceil_div(R, kRB) : 1u);
         if (multi)
-          k_spmv<TV, kRB><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+          k_spmv<TV, TE, kRB><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
         else
-          k_spmv<TV, 1><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+          k_spmv<TV, TE, 1><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
         ctx->prof_end(SWM_K_APPLY);
         SWM_LAUNCHED();
         ctx->prof_begin(SWM_K_DOTS);
         k_dots_big<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
         ctx->prof_end(SWM_K_DOTS);
       } else if (multi) {
-        k_step<TV, kRB><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+        k_step<TV, TE, kRB><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
         ctx->prof_end(SWM_K_APPLY);
       } else {
-        k_step<TV, 1><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+        k_step<TV, TE, 1><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
         ctx->prof_end(SWM_K_APPLY);
       }
       SWM_LAUNCHED();
@@ -1580,7 +809,7 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     key.sm = sm;
     key.gx = g_chunk.x;
     key.gy = g_chunk.y;
-    key.bits = sizeof(TV);
+    key.bits = (unsigned)(sizeof(TV) * 64 + sizeof(TE));
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
     std::vector<unsigned char> kv(kb, kb + sizeof(key));
     if (!ctx->gm_exec || kv != ctx->gm_key) {
@@ -1606,7 +835,7 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
   while (!persisted) {
     // residual of the current y and the start of a cycle
     ctx->prof_begin(SWM_K_APPLY);
-    k_apply<TV><<<g_rows, kRows, 0, st>>>(1, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
+    k_apply<TV, TE><<<g_rows, kRows, 0, st>>>(1, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
     ctx->prof_end(SWM_K_APPLY);
     SWM_LAUNCHED();
     k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, W0, first ? 1 : 0);
@@ -1638,6 +867,13 @@ int gmres_impl(swm_ctx* ctx, double tol, int restart, int max_iter) {
     k_update_y<TV><<<dim3((unsigned)ceil_div(N, 256), R), 256, 0, st>>>(P, V, Y);
     SWM_LAUNCHED();
     ++cycles;
+  }
+  if (hs_out) *hs_out = hs;
+  if (y_out) {  // inner solve of the refinement: the result stays in y-space
+    *y_out = Y;
+    dfree_group(ctx, tmp);
+    if (hs.numeric) return ctx->fail(SWM_ECUDA, "GMRES produced a non-finite value");
+    return hs.all_conv ? SWM_OK : SWM_ENOTCONV;
   }
   // x = M^-1 y
   SWM_TRY(apply_minv(ctx, Y));
@@ -1692,8 +928,17 @@ int apply_minv(swm_ctx* ctx, const void* Y) {
 }
 
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter) {
-  if (ctx->prec == SWM_C128) return gmres_impl<double>(ctx, tol, restart, max_iter);
-  return gmres_impl<float>(ctx, tol, restart, max_iter);
+  if (ctx->prec == SWM_C128)
+    return gmres_impl<double, c128>(ctx, (const c128*)ctx->Zp, tol, restart, max_iter, nullptr, nullptr);
+  return gmres_impl<float, c64>(ctx, (const c64*)ctx->Zp, tol, restart, max_iter, nullptr, nullptr);
+}
+
+int gmres_inner_bf16(swm_ctx* ctx, double tol, int restart, int max_iter, void** y_out, int* iters) {
+  KState hs{};
+  const int rc = gmres_impl<float, __nv_bfloat162>(ctx, (const __nv_bfloat162*)ctx->E16, tol, restart, max_iter,
+                                                   y_out, &hs);
+  *iters = hs.iters;
+  return rc;
 }
 
 }  // namespace swm

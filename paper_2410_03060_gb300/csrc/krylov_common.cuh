@@ -1,0 +1,81 @@
+// Device state shared by the GMRES kernels (krylov.cu, persist.cu) and the loaders of the stored
+// matrix E in its storage precisions.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace swm {
+
+struct KState {
+  int j;          // Arnoldi step inside the cycle
+  int cycle_done; // no active right-hand side left in this cycle
+  int all_conv;   // every right-hand side met tol at the start of this cycle
+  int iters;      // total Arnoldi steps
+  int numeric;    // a NaN/Inf appeared
+  int cycles;     // restart cycles (persistent solve)
+  int pad[2];
+};
+
+struct KPtr {
+  KState* st;
+  unsigned* counter;  // [R]
+  int* active;        // [R]
+  int* jlast;         // [R]
+  double* inv_h;      // [R]
+  double* bnorm;      // [R]
+  double* resid;      // [R]
+  c128* H;            // [R][(restart + 1) * restart]
+  double* cs;         // [R][restart]
+  c128* sn;           // [R][restart]
+  c128* g;            // [R][restart + 1]
+  c128* hc;           // [R][restart + 1]
+  c128* hc2;          // [R][restart + 1]
+  c128* coef;         // [R][restart]
+  c128* part;         // [R][nchunk][restart + 1]
+  double* partn;      // [R][nchunk]
+  int R, restart, nchunk, chunk;
+  int nschunk, schunk;  // chunks of the fused step kernel (finer, for more CTAs)
+  int64_t N;
+  double tol;
+};
+
+// Entry of E as the vector type: complex128 / complex64 storage as is, complex bfloat16 storage
+// (one __nv_bfloat162 per entry, real part first) widened to complex64.
+template <typename TV, typename TE>
+struct ELoad;
+template <typename TV>
+struct ELoad<TV, cplx<TV>> {
+  static __device__ __forceinline__ cplx<TV> ld(const cplx<TV>* p) { return *p; }
+};
+template <>
+struct ELoad<float, __nv_bfloat162> {
+  static __device__ __forceinline__ cplx<float> ld(const __nv_bfloat162* p) {
+    const float2 f = __bfloat1622float2(*p);
+    return mkc<float>(f.x, f.y);
+  }
+};
+
+// Buffers of the persistent solve (persist.cu) handed over by the GMRES driver (krylov.cu).
+struct PSync {
+  unsigned count;  // arrivals at grid barriers since the launch
+  int abort;       // a barrier ran out of time
+  int pad[30];
+};
+struct PBuffers {
+  PSync* sync;
+  void *part1, *part2, *partn;  // partial sums over the CTAs (at most ctx->nsm of them)
+  const void* E;                // E in its storage type
+  const void* B;
+  void *Y, *W, *V;
+};
+constexpr int kPersistMaxR = 8;  // right-hand sides of one persistent solve
+
+// Runs the whole restarted GMRES as one cooperative kernel when the system is small enough
+// (sets *done); otherwise leaves *done false and launches nothing.
+template <typename TV, typename TE>
+int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& B, int max_iter, KState* hs, bool* done);
+
+}  // namespace swm

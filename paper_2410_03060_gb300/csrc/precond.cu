@@ -4,6 +4,8 @@
 // Krylov step is one block-sparse product plus the identity, and x = M^-1 y at the end.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "ctx.h"
 
@@ -134,6 +136,23 @@ int build_precond(swm_ctx* ctx) {
                                                  (const c64*)ctx->Z, ctx->minv_off, (const c64*)ctx->Minv,
                                                  (c64*)ctx->Zp);
     ctx->prof_end(SWM_K_FORM_E);
+    SWM_LAUNCHED();
+  }
+  return SWM_OK;
+}
+
+// E rounded to complex bfloat16 (round to nearest even), one __nv_bfloat162 per entry.
+__global__ void k_to_bf16(int64_t n, const c64* __restrict__ src, __nv_bfloat162* __restrict__ dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float22bfloat162_rn(make_float2(src[i].re, src[i].im));
+}
+
+int make_e16(swm_ctx* ctx) {
+  const int64_t n = std::max<int64_t>(1, ctx->offd.nval);
+  SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->E16, sizeof(__nv_bfloat162) * n));
+  if (ctx->offd.nval > 0) {
+    k_to_bf16<<<(unsigned)ceil_div(ctx->offd.nval, 256), 256, 0, ctx->stream>>>(ctx->offd.nval, (const c64*)ctx->Zp,
+                                                                                 (__nv_bfloat162*)ctx->E16);
     SWM_LAUNCHED();
   }
   return SWM_OK;

@@ -414,6 +414,15 @@ int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
   return SWM_OK;
 }
 
+int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out) {
+  const int64_t tot = ctx->nw * (int64_t)n_inc;
+  k_rhs<double><<<(unsigned)ceil_div(tot, 256), 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz,
+                                                                     ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns,
+                                                                     ctx->off, ctx->N, ctx->k, frames_dev, out);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
 size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs) {
   int64_t nchunks, chunk;
   ff_shape(nw, npairs, nchunks, chunk);

@@ -19,7 +19,7 @@ SWM_OK, SWM_ENOTCONV = 0, 1
 SWM_SOLVER_GMRES, SWM_SOLVER_GCR = 0, 1
 SWM_EINVAL, SWM_ENOMEM, SWM_ECUDA, SWM_ESTATE, SWM_ETIMEOUT = -1, -2, -3, -4, -5
 SWM_HOST, SWM_DEVICE = 0, 1
-SWM_C128, SWM_C64 = 0, 1
+SWM_C128, SWM_C64, SWM_BF16 = 0, 1, 2
 SWM_MAX_SEG = 16
 SWM_MAX_RESTART = 128
 

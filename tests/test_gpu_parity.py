@@ -284,3 +284,35 @@ def test_persistent_solve_matches_oracle_and_launches_once(n_inc):
             assert np.array_equal(cur.T, out["currents"])  # deterministic
         finally:
             swm.swm_destroy(out["ctx"])
+
+
+def test_persistent_barrier_wait_runs_out_and_reports_etimeout(monkeypatch):
+    """Failure detection without a GPU fault: with the test hook every grid barrier of the
+    persistent solve waits for one CTA that does not exist, so each wait runs out after its 1 s
+    limit, every CTA returns, and the solve reports SWM_ETIMEOUT; the GPU and a new context then
+    solve normally."""
+    import time
+
+    from paper_2410_03060_gb300 import swm
+
+    cl = cloud_uniform_cube(60, 4.0, seed=47)
+    inc = np.array([[0.3, 0.1, 0.0]])
+    monkeypatch.setenv("SWM_TEST_BARRIER_EXTRA", "1")
+    ctx = swm.swm_create(0)
+    try:
+        swm.swm_set_cloud(ctx, cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)
+        swm.swm_build(ctx, K, 2.0, C64)
+        t0 = time.perf_counter()
+        with pytest.raises(swm.SwmError) as e:
+            swm.swm_solve(ctx, inc, 1e-6, 20, 100)
+        dt = time.perf_counter() - t0
+        assert e.value.code == swm.SWM_ETIMEOUT and "timed out" in str(e.value)
+        assert 0.9 < dt < 30.0
+    finally:
+        swm.swm_destroy(ctx)
+    monkeypatch.delenv("SWM_TEST_BARRIER_EXTRA")
+    out = run_gpu(cl, K, 2.0, C64, inc, tol=1e-6)
+    try:
+        assert out["rc"] == 0 and out["stats"]["converged"] == 1
+    finally:
+        swm.swm_destroy(out["ctx"])
