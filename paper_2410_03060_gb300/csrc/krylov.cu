@@ -197,16 +197,17 @@ __global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restric
   cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);  // [RB][schunk]
   const int g = threadIdx.x / kG, sub = threadIdx.x % kG;
   constexpr int kMaxRowsPerGroup = 4;
+  for (int tb = 0; tb < cnt; tb += 32 * kMaxRowsPerGroup) {  // same trip count in every lane
   RowInfo ri[kMaxRowsPerGroup];
 #pragma unroll
   for (int t = 0; t < kMaxRowsPerGroup; ++t) {
-    const int row = g + 32 * t;
+    const int row = tb + g + 32 * t;
     ri[t] = (row < cnt) ? rinfo[n0 + row] : RowInfo{0, 0, 0};
   }
 #pragma unroll
   for (int t = 0; t < kMaxRowsPerGroup; ++t) {
-    const int row = g + 32 * t;
-    if (32 * t >= cnt) break;  // uniform across the CTA
+    const int row = tb + g + 32 * t;
+    if (tb + 32 * t >= cnt) break;  // uniform across the CTA
     cplx<TV> acc[RB];
 #pragma unroll
     for (int b = 0; b < RB; ++b) acc[b] = mkc<TV>(0, 0);
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restric
         w_sm[b * P.schunk + row] = y;
       }
     }
+  }
   }
   __syncthreads();
   for (int b = 0; b < nr; ++b)
@@ -657,8 +659,15 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   P.tol = tol;
   P.chunk = (int)std::max<int64_t>(kRows, ceil_div(ceil_div(N, 512), kRows) * kRows);
   P.nchunk = (int)ceil_div(N, P.chunk);
-  // the fused step kernel: 64..128 rows per CTA, at most 2048 chunks
-  P.schunk = (int)std::min<int64_t>(128, std::max<int64_t>(128, ceil_div(ceil_div(N, 2048), 32) * 32));
+  // the fused step kernel: 128 rows per CTA for one right-hand side; with several, chunks as large as
+  // keep about four CTAs per SM busy over the blocks of 8 right-hand sides (at most 1024 rows), so
+  // the partial dot products the last CTA sums stay few
+  {
+    const int64_t nrb = ceil_div(R, 8);
+    const int64_t want = std::max<int64_t>(1, 4 * std::max(ctx->nsm, 1) / std::max<int64_t>(1, nrb));
+    P.schunk = R > 1 ? (int)std::min<int64_t>(1024, std::max<int64_t>(128, ceil_div(ceil_div(N, want), 32) * 32))
+                     : 128;
+  }
   P.nschunk = (int)ceil_div(N, P.schunk);
   const int R1 = restart + 1;
   // The workspace persists across solves of the same size, so buffer addresses (and the captured
@@ -740,6 +749,10 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   const dim3 g_schunk((unsigned)P.nschunk, multi ? (unsigned)ceil_div(R, kRB) : 1u);
   const size_t sm = sizeof(cplx<TV>) * P.chunk;
   const size_t ssm = sizeof(cplx<TV>) * P.schunk * (multi ? kRB : 1);
+  if (ssm > 48 * 1024) {
+    SWM_CK(cudaFuncSetAttribute(k_step<TV, TE, kRB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    SWM_CK(cudaFuncSetAttribute(k_step<TV, TE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+  }
   if (sm > 48 * 1024) {
     SWM_CK(cudaFuncSetAttribute(k_update<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SWM_CK(cudaFuncSetAttribute(k_dots_big<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

@@ -14,7 +14,9 @@ namespace swm {
 namespace {
 
 
-// Gauss-Jordan inversion with partial pivoting of Z_pp in precision R, one warp per wire.
+// Gauss-Jordan inversion with partial pivoting of Z_pp in precision R, one warp per wire: lane j
+// owns column j of the augmented matrix [Z_pp | I] (2 m_p <= 30 columns) and sweeps the rows, so no
+// lane divides indices; the pivot row is the warp's arg-max of |a[r][c]| (ties: smallest r).
 template <typename R, typename TV>
 __global__ void __launch_bounds__(128) k_invert_self(int64_t nw, const int32_t* __restrict__ m,
                                                     const int64_t* __restrict__ diag_b, Layout lay,
@@ -28,53 +30,56 @@ __global__ void __launch_bounds__(128) k_invert_self(int64_t nw, const int32_t* 
   const int K = lay.K[p];
   const int64_t base = lay.rowbase[p] + lay.colpos[diag_b[p]];
   cplx<R>(*a)[2 * kMaxM] = A[wl];
-  for (int e = lane; e < n * 2 * n; e += 32) {
-    const int i = e / (2 * n), j = e % (2 * n);
-    a[i][j] = j < n ? ccast<R>(Z[base + (int64_t)i * K + j]) : mkc<R>(j - n == i ? R(1) : R(0), R(0));
-  }
+  const int j = lane;
+  const bool col = j < 2 * n;
+  if (col)
+    for (int i = 0; i < n; ++i)
+      a[i][j] = j < n ? ccast<R>(Z[base + (int64_t)i * K + j]) : mkc<R>(j - n == i ? R(1) : R(0), R(0));
   __syncwarp();
   for (int c = 0; c < n; ++c) {
-    // pivot: largest |a[r][c]|, r >= c (ties: smallest r)
-    R best = -1;
-    int br = c;
-    for (int r = c; r < n; ++r) {
-      const R v = a[r][c].re * a[r][c].re + a[r][c].im * a[r][c].im;
-      if (v > best) {
-        best = v;
-        br = r;
+    // pivot: lane r (c <= r < n) offers |a[r][c]|^2; warp arg-max, smallest r on ties
+    R v = R(-1);
+    int br = lane;
+    if (lane >= c && lane < n) v = a[lane][c].re * a[lane][c].re + a[lane][c].im * a[lane][c].im;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      const int b2 = __shfl_xor_sync(0xffffffffu, br, o);
+      if (v2 > v || (v2 == v && b2 < br)) {
+        v = v2;
+        br = b2;
       }
     }
-    if (best == R(0)) {
+    if (!(v > R(0))) {
       if (lane == 0) atomicExch(singular, 1);
       return;
     }
-    if (br != c) {
-      for (int j = lane; j < 2 * n; j += 32) {
-        const cplx<R> t = a[c][j];
-        a[c][j] = a[br][j];
-        a[br][j] = t;
-      }
-      __syncwarp();
+    if (br != c && col) {
+      const cplx<R> t = a[c][j];
+      a[c][j] = a[br][j];
+      a[br][j] = t;
     }
+    __syncwarp();
     const cplx<R> piv = a[c][c];
     const R den = piv.re * piv.re + piv.im * piv.im;
     const cplx<R> inv = mkc<R>(piv.re / den, -piv.im / den);
+    cplx<R> f[kMaxM];
+#pragma unroll
+    for (int r = 0; r < kMaxM; ++r) f[r] = r < n ? a[r][c] : mkc<R>(0, 0);  // column c before the sweep
     __syncwarp();
-    for (int j = lane; j < 2 * n; j += 32) a[c][j] = a[c][j] * inv;
-    __syncwarp();
-    for (int e = lane; e < n * 2 * n; e += 32) {
-      const int r = e / (2 * n), j = e % (2 * n);
-      if (r != c && j != c) a[r][j] = a[r][j] - a[r][c] * a[c][j];
+    if (col) {
+      const cplx<R> pc = a[c][j] * inv;
+      a[c][j] = pc;
+#pragma unroll
+      for (int r = 0; r < kMaxM; ++r)
+        if (r < n && r != c) a[r][j] = a[r][j] - f[r] * pc;
     }
-    __syncwarp();
-    for (int r = lane; r < n; r += 32)
-      if (r != c) a[r][c] = mkc<R>(0, 0);
     __syncwarp();
   }
   const int64_t mo = moff[p];
   for (int e = lane; e < n * n; e += 32) {
-    const int i = e / n, j = e % n;
-    Minv[mo + e] = ccast<TV>(a[i][n + j]);
+    const int i = e / n, jj = e % n;
+    Minv[mo + e] = ccast<TV>(a[i][n + jj]);
   }
 }
 
