@@ -22,7 +22,7 @@ def _case(seed=5, nw=12, side=3.0, r_c=2.0):
 
 
 def test_param_count_and_layout():
-    assert n_params() == sum(i * o + o for i, o in NL.LAYERS) == 112966
+    assert n_params() == sum(i * o + o for i, o in NL.LAYERS) == 93720
     Ws = NL.unpack(init_params(0))
     assert [w.shape for w, _ in Ws] == [(i, o) for i, o in NL.LAYERS]
 
@@ -32,9 +32,14 @@ def test_backward_matches_central_differences():
     xi = NL.isolated_currents(cl, K, inc)
     rng = np.random.default_rng(1)
     params = init_params(3).astype(np.float64)
-    params[-(256 * 6 + 6):] *= 100.0
+    params *= 1.0
+    o = 0
+    for li, (i, n) in enumerate(NL.LAYERS):  # undo the small initial scale of the two last layers
+        if li in (2, 5):
+            params[o:o + i * n] *= 100.0
+        o += i * n + n
     xt = xi + 0.1 * np.abs(xi).mean() * (rng.standard_normal(xi.shape) + 1j * rng.standard_normal(xi.shape))
-    L, g, _ = NL.loss_and_grad(params, cl, K, inc, Xe, Xs, xi, xt)
+    L, g, _ = NL.loss_and_grad(params, cl, K, inc, Xe, Xs, xi, xt, nbr)
     # a few entries of every weight matrix and bias vector
     o, idx = 0, []
     for i, n in NL.LAYERS:
@@ -44,11 +49,11 @@ def test_backward_matches_central_differences():
         h = 1e-6 * max(1.0, abs(params[j]))
         pp = params.copy()
         pp[j] += h
-        Lp = NL.loss_and_grad(pp, cl, K, inc, Xe, Xs, xi, xt)[0]
+        Lp = NL.loss_and_grad(pp, cl, K, inc, Xe, Xs, xi, xt, nbr)[0]
         pp[j] -= 2 * h
-        Lm = NL.loss_and_grad(pp, cl, K, inc, Xe, Xs, xi, xt)[0]
+        Lm = NL.loss_and_grad(pp, cl, K, inc, Xe, Xs, xi, xt, nbr)[0]
         fd = (Lp - Lm) / (2 * h)
-        assert abs(fd - g[j]) <= 1e-5 * (abs(fd) + abs(g[j])) + 1e-12, (j, fd, g[j])
+        assert abs(fd - g[j]) <= 1e-5 * (abs(fd) + abs(g[j])) + 1e-9, (j, fd, g[j])
 
 
 def _rotate(cl, inc, Rm):
@@ -77,10 +82,9 @@ def test_features_and_prediction_are_rotation_invariant():
     assert np.array_equal(nbr, nbr2)
     Xe2, Xs2 = NL.features(cl2, K, inc2, 2.0, nbr2)
     assert np.allclose(Xe, Xe2, atol=1e-10) and np.allclose(Xs, Xs2, atol=1e-12)
-    params = init_params(2).astype(np.float64)
-    params[-(256 * 6 + 6):] *= 100.0
-    x0, _ = NL.forward(params, cl, K, inc, Xe, Xs, NL.isolated_currents(cl, K, inc))
-    x02, _ = NL.forward(params, cl2, K, inc2, Xe2, Xs2, NL.isolated_currents(cl2, K, inc2))
+    params = init_params(2).astype(np.float64) * 5.0
+    x0, _ = NL.forward(params, cl, K, inc, Xe, Xs, NL.isolated_currents(cl, K, inc), nbr)
+    x02, _ = NL.forward(params, cl2, K, inc2, Xe2, Xs2, NL.isolated_currents(cl2, K, inc2), nbr2)
     assert np.allclose(x0, x02, rtol=1e-8, atol=1e-12 * np.abs(x0).max())
 
 
@@ -98,12 +102,34 @@ def test_neighbour_lists_match_kdtree_query():
         assert got == keep
 
 
+def test_mode_amplitudes_reproduce_sine_shaped_currents():
+    """The amplitudes are the discrete sine transform of the isolated currents: a current made of
+    the three modes is recovered exactly (times the wire's incident phase)."""
+    cl, inc, nbr, Xe, Xs = _case(seed=13)
+    m, off = O.numbering(cl.nseg)
+    _, khat, _ = O.incidence_frames(inc)
+    rng = np.random.default_rng(2)
+    want = rng.standard_normal((2, cl.nw, 3)) + 1j * rng.standard_normal((2, cl.nw, 3))
+    x = np.zeros((int(off[-1]), 2), dtype=complex)
+    for r in range(2):
+        for p in range(cl.nw):
+            i = np.arange(1, cl.nseg[p])[:, None]
+            phi = np.sin(np.arange(1, 4)[None, :] * np.pi * i / cl.nseg[p])
+            x[off[p]:off[p + 1], r] = np.exp(-1j * K * (khat[r] @ cl.centres[p])) * (phi @ want[r, p])
+    a = NL.amplitudes(cl, K, inc, x)
+    assert np.allclose(a, want, rtol=1e-12, atol=1e-12)
+
+
 def test_untrained_output_layer_zero_gives_isolated_currents():
     cl, inc, nbr, Xe, Xs = _case(seed=11)
     params = init_params(0).astype(np.float64)
-    params[-(256 * 6 + 6):] = 0.0
+    o = 0
+    for li, (i, n) in enumerate(NL.LAYERS):  # zero the last layer of both MLPs: no correction
+        if li in (2, 5):
+            params[o:o + i * n + n] = 0.0
+        o += i * n + n
     xi = NL.isolated_currents(cl, K, inc)
-    x0, _ = NL.forward(params, cl, K, inc, Xe, Xs, xi)
+    x0, _ = NL.forward(params, cl, K, inc, Xe, Xs, xi, nbr)
     assert np.array_equal(x0, xi)
     # the isolated currents solve the block-diagonal part of the system exactly
     Z = O.assemble(cl, K, None, sparse=False)
