@@ -203,6 +203,44 @@ int swm_set_solver(swm_ctx* ctx, int method);
 int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restart, int max_iter,
               double* currents_out, int out_kind);
 
+/* swm_solve from an initial guess x0 (n_inc x N complex128, interleaved re, im; incidence-major,
+ * caller's unknown order, memory of kind x0_kind): the Krylov iteration starts from y0 = M x0
+ * (M = blockdiag(Z_pp), the right preconditioner) instead of zero; tol stays relative to |b|.
+ * No counterpart in the paper: it serves the learned warm start (swm_net_predict).  Otherwise as
+ * swm_solve. */
+int swm_solve_guess(swm_ctx* ctx, int n_inc, const double* inc, const double* x0, int x0_kind, double tol,
+                    int restart, int max_iter, double* currents_out, int out_kind);
+
+/* Learned warm start (no counterpart in the paper): a rotation-invariant neighbourhood network
+ * that predicts each wire's current as the isolated-wire current Z_pp^-1 b_p plus three complex
+ * sine modes along the wire.  For each of the wire's up to 16 nearest S-NFC partners an MLP
+ * (16-128-128-18, SiLU) maps 16 invariant features in the wire's frame (offsets along and across
+ * the wire / r_c, direction cosines, lengths / wavelength, the incident polarisation and direction
+ * projected on both wires, the incident phase difference, the propagation phase over the
+ * distance, a presence flag) to a complex 3 x 3 coupling matrix, applied to the partner's
+ * isolated-current mode amplitudes; their sum h and an output MLP (20-256-256-6, SiLU) on
+ * [h, 8 own features, own amplitudes] give the mode corrections h + o.  93,720 float32 parameters
+ * (W[in][out] then b, layer by layer).  Forward, backward and Adam are the library's kernels.  A
+ * network belongs to one device; it reads the geometry, pattern, k, r_c (finite) and block-Jacobi
+ * inverses of a built context.  Workspace: about 3 KB per wire-incidence sample (training) on
+ * the context's device. */
+typedef struct swm_net swm_net;
+int64_t swm_net_num_params(void);
+int swm_net_create(swm_net** out, int device, void* cuda_stream);
+void swm_net_destroy(swm_net* net);
+const char* swm_net_last_error(const swm_net* net);
+/* parameters in or out (host or device pointer of swm_net_num_params() float32); setting them
+ * resets the Adam moments */
+int swm_net_set_params(swm_net* net, const float* params, int mem_kind);
+int swm_net_get_params(swm_net* net, float* params, int mem_kind);
+/* predicted currents x0 (n_inc x N complex128, caller order) for the context's built system */
+int swm_net_predict(swm_net* net, swm_ctx* ctx, int n_inc, const double* inc, double* x0_out, int out_kind);
+/* one training step on targets x_true (n_inc x N complex128, caller order): loss
+ * sum|x0 - x_true|^2 / sum|x_true|^2 to *loss_out, its gradient to grad_out (optional, float32),
+ * and with lr > 0 an Adam update (beta 0.9, 0.999, eps 1e-8) of the parameters */
+int swm_net_train_step(swm_net* net, swm_ctx* ctx, int n_inc, const double* inc, const double* x_true, int xt_kind,
+                       float lr, double* loss_out, float* grad_out);
+
 /* Bistatic RCS (Sec. III-A) of the currents of the last solve at n_obs >= 1 observation
  * directions obs = n_obs x 2 float64 (theta, phi), host memory.  sigma_out receives
  * n_inc x n_obs x 2 float64 (theta- and phi-received), memory of kind out_kind. */

@@ -95,21 +95,6 @@ __global__ void k_to_user(int64_t N, int R, const int32_t* __restrict__ rowwire,
   out[(int64_t)r * N + uoff[p] + (n - off[p])] = ccast<double>(X[(int64_t)r * N + n]);
 }
 
-// Incidence frames: k_hat (propagation, = -arrival) and polarisation e, 6 doubles each.
-void frames_host(const double* inc, int n, std::vector<double>& out) {
-  out.resize(6 * (size_t)n);
-  for (int i = 0; i < n; ++i) {
-    const double th = inc[3 * i], ph = inc[3 * i + 1], ps = inc[3 * i + 2];
-    const double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
-    const double u[3] = {st * cp, st * sp, ct};
-    const double tht[3] = {ct * cp, ct * sp, -st};
-    const double pht[3] = {-sp, cp, 0.0};
-    for (int d = 0; d < 3; ++d) {
-      out[6 * i + d] = -u[d];
-      out[6 * i + 3 + d] = std::cos(ps) * tht[d] + std::sin(ps) * pht[d];
-    }
-  }
-}
 
 
 int copy_in(swm_ctx* ctx, void* dst, const void* src, size_t bytes, int kind) {
@@ -126,6 +111,49 @@ int set_device(swm_ctx* ctx) {
 thread_local std::string g_stateless_err;
 
 }  // namespace
+
+// Caller-order [R][N] complex128 -> internal order.
+__global__ void k_from_user(int64_t N, const int32_t* __restrict__ rowwire, const int64_t* __restrict__ off,
+                            const int64_t* __restrict__ uoff, const c128* __restrict__ in, c128* __restrict__ out) {
+  const int r = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int p = rowwire[n];
+  out[(int64_t)r * N + n] = in[(int64_t)r * N + uoff[p] + (n - off[p])];
+}
+
+// y = blockdiag(Z_pp) x (the right preconditioner applied forward), float64 arithmetic.
+template <typename TZ>
+__global__ void k_mult_diag(int64_t N, const int32_t* __restrict__ rowwire, const int64_t* __restrict__ off,
+                            const int32_t* __restrict__ m, const int64_t* __restrict__ diag_b, Layout full,
+                            const cplx<TZ>* __restrict__ Z, const c128* __restrict__ x, c128* __restrict__ y) {
+  const int r = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int p = rowwire[n];
+  const int64_t o = off[p];
+  const int i = (int)(n - o), mp = m[p];
+  const cplx<TZ>* zr = Z + full.rowbase[p] + (int64_t)i * full.K[p] + full.colpos[diag_b[p]];
+  c128 acc = mkc(0.0, 0.0);
+  for (int l = 0; l < mp; ++l) cfma(acc, ccast<double>(zr[l]), x[(int64_t)r * N + o + l]);
+  y[(int64_t)r * N + n] = acc;
+}
+
+// Incidence frames: k_hat (propagation, = -arrival) and polarisation e, 6 doubles each.
+void frames_host(const double* inc, int n, std::vector<double>& out) {
+  out.resize(6 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const double th = inc[3 * i], ph = inc[3 * i + 1], ps = inc[3 * i + 2];
+    const double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
+    const double u[3] = {st * cp, st * sp, ct};
+    const double tht[3] = {ct * cp, ct * sp, -st};
+    const double pht[3] = {-sp, cp, 0.0};
+    for (int d = 0; d < 3; ++d) {
+      out[6 * i + d] = -u[d];
+      out[6 * i + 3 + d] = std::cos(ps) * tht[d] + std::sin(ps) * pht[d];
+    }
+  }
+}
 
 void set_stateless_error(const std::string& msg) { g_stateless_err = msg; }
 
@@ -326,8 +354,23 @@ int swm_set_solver(swm_ctx* ctx, int method) {
   return SWM_OK;
 }
 
+static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restart, int max_iter,
+                      double* currents_out, int out_kind, const double* x0, int x0_kind);
+
 int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restart, int max_iter,
               double* currents_out, int out_kind) {
+  return solve_impl(ctx, n_inc, inc, tol, restart, max_iter, currents_out, out_kind, nullptr, SWM_HOST);
+}
+
+int swm_solve_guess(swm_ctx* ctx, int n_inc, const double* inc, const double* x0, int x0_kind, double tol,
+                    int restart, int max_iter, double* currents_out, int out_kind) {
+  if (!ctx) return SWM_EINVAL;
+  if (!x0 || (x0_kind != SWM_HOST && x0_kind != SWM_DEVICE)) return ctx->fail(SWM_EINVAL, "bad initial guess");
+  return solve_impl(ctx, n_inc, inc, tol, restart, max_iter, currents_out, out_kind, x0, x0_kind);
+}
+
+static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restart, int max_iter,
+                      double* currents_out, int out_kind, const double* x0, int x0_kind) {
   if (!ctx) return SWM_EINVAL;
   ctx->err.clear();
   if (!ctx->built) return ctx->fail(SWM_ESTATE, "swm_solve before swm_build");
@@ -356,11 +399,38 @@ int swm_solve(swm_ctx* ctx, int n_inc, const double* inc, double tol, int restar
   ctx->phase_begin(swm_ctx::PH_RHS);
   SWM_TRY(compute_rhs(ctx, n_inc, frames));
   ctx->phase_end(swm_ctx::PH_RHS);
+  ctx->guess = nullptr;
+  if (x0) {
+    // y0 = M x0 in internal order: the solvers start from it instead of zero
+    SWM_TRY(ensure_rowinfo(ctx));
+    SWM_TRY(ensure_user_offsets(ctx));
+    const int64_t N = ctx->N;
+    c128 *xin = nullptr, *y0 = nullptr;
+    SWM_TRY(dalloc(ctx, S, (void**)&xin, sizeof(c128) * n_inc * N));
+    SWM_TRY(dalloc(ctx, S, (void**)&y0, sizeof(c128) * n_inc * N));
+    const c128* src = (const c128*)x0;
+    if (x0_kind == SWM_HOST) {
+      SWM_CK(cudaMemcpyAsync(y0, x0, sizeof(c128) * n_inc * N, cudaMemcpyHostToDevice, ctx->stream));
+      src = y0;
+    }
+    const dim3 g((unsigned)ceil_div(N, 256), n_inc);
+    k_from_user<<<g, 256, 0, ctx->stream>>>(N, ctx->rowwire, ctx->off, ctx->uoff, src, xin);
+    SWM_LAUNCHED();
+    if (ctx->prec == SWM_C128)
+      k_mult_diag<double><<<g, 256, 0, ctx->stream>>>(N, ctx->rowwire, ctx->off, ctx->m, ctx->diag_b, ctx->full,
+                                                      (const c128*)ctx->Z, xin, y0);
+    else
+      k_mult_diag<float><<<g, 256, 0, ctx->stream>>>(N, ctx->rowwire, ctx->off, ctx->m, ctx->diag_b, ctx->full,
+                                                     (const c64*)ctx->Z, xin, y0);
+    SWM_LAUNCHED();
+    ctx->guess = y0;
+  }
   ctx->phase_begin(swm_ctx::PH_SOLVE);
   int rc = ctx->bf16 ? refine_solve(ctx, frames, tol, restart, max_iter)
            : ctx->solver == SWM_SOLVER_GCR ? gcr_solve(ctx, tol, restart, max_iter)
                                            : gmres_solve(ctx, tol, restart, max_iter);
   ctx->phase_end(swm_ctx::PH_SOLVE);
+  ctx->guess = nullptr;
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->phase_collect();
   ctx->prof_flush();

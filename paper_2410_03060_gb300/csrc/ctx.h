@@ -125,6 +125,7 @@ struct swm_ctx {
   int* d_sing = nullptr;                  // singular self block flag (device)
   void* pinned_state = nullptr;           // two pinned slots for the Krylov state poll
   int solver = 0;                         // SWM_SOLVER_GMRES or SWM_SOLVER_GCR
+  const void* guess = nullptr;            // during swm_solve_guess: y0 = M x0, complex128 [n_rhs][N]
   void* ffw = nullptr;                    // per-wire float32 far-field data (complex64 path)
   cudaGraphExec_t gm_exec = nullptr;      // captured chunk of GMRES steps and its argument key
   std::vector<unsigned char> gm_key;
@@ -256,12 +257,18 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
                      const int32_t* ns, const int64_t* off, bool soa, double k, int n_rhs, int n_obs,
                      const double* obs, int obs_stride, bool mono, double* sigma, void* scratch, size_t scratch_bytes,
                      std::string* err);
+// incidence frames on the host: k_hat (propagation, = -arrival) then polarisation e, 6 doubles each
+void frames_host(const double* inc, int n, std::vector<double>& out);
 // error text reported by swm_stateless_error() (api.cu)
 void set_stateless_error(const std::string& msg);
 // krylov.cu: a6
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
 // row descriptors of E (built once per build) and x = M^-1 y into ctx->Xv
 int ensure_rowinfo(swm_ctx* ctx);
+// y = y0 (ctx->guess, complex128) or 0 at the start of a solve, in the vector precision
+int init_y(swm_ctx* ctx, void* Y, bool f64);
+// |b_r| of the [n_rhs][N] right-hand sides into bnorm_dev (device), 1 for a zero one
+int norms_of_b(swm_ctx* ctx, const void* B, bool f64, double* bnorm_dev);
 // two pinned host slots (kPollSlotBytes in all) for polling the solvers' device state
 constexpr size_t kPollSlotBytes = 128;
 int ensure_poll_slots(swm_ctx* ctx);

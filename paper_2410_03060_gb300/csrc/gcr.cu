@@ -403,7 +403,8 @@ int gcr_impl(swm_ctx* ctx, double tol, int m, int max_iter) {
   SWM_TRY(dalloc(ctx, S, (void**)&Pb, sizeof(C) * (size_t)m * R * N));
   SWM_CK(cudaMemsetAsync(P.st, 0, sizeof(GState), st));
   SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));
-  SWM_CK(cudaMemsetAsync(Y, 0, sizeof(C) * R * N, st));
+  SWM_TRY(init_y(ctx, Y, sizeof(TV) == sizeof(double)));
+  if (ctx->guess) SWM_TRY(norms_of_b(ctx, ctx->Bv, sizeof(TV) == sizeof(double), P.bnorm));
   const C* E = (const C*)ctx->Zp;
   const C* Bv = (const C*)ctx->Bv;
   const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
@@ -420,7 +421,7 @@ int gcr_impl(swm_ctx* ctx, double tol, int m, int max_iter) {
   constexpr int kChunkSteps = 4;
   GState hs{};
   int cycles = 0;
-  bool first = true;
+  bool first = !ctx->guess;
   while (true) {
     ctx->prof_begin(SWM_K_APPLY);
     k_gcr_residual<TV><<<grid, kT, 0, st>>>(P, first ? 1 : 0, ri, ctx->offd.colmap, E, Bv, Y, Rv);

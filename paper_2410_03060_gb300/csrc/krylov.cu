@@ -727,7 +727,13 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   cplx<TV> *Y = ws->Y, *W0 = ws->W0, *W1 = ws->W1, *V = ws->V;
   SWM_CK(cudaMemsetAsync(P.st, 0, sizeof(KState), st));
   SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));
-  SWM_CK(cudaMemsetAsync(Y, 0, sizeof(cplx<TV>) * R * N, st));
+  // with an initial guess the tolerance stays relative to |b|, so |b| is measured first
+  const bool given_b = ctx->guess && !y_out;
+  if (y_out)  // inner solve of the refinement: the correction starts from zero
+    SWM_CK(cudaMemsetAsync(Y, 0, sizeof(cplx<TV>) * R * N, st));
+  else
+    SWM_TRY(init_y(ctx, Y, sizeof(TV) == sizeof(double)));
+  if (given_b) SWM_TRY(norms_of_b(ctx, ctx->Bv, sizeof(TV) == sizeof(double), P.bnorm));
   (void)S;
 
   const cplx<TV>* Bv = (const cplx<TV>*)ctx->Bv;
@@ -736,7 +742,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   // small systems: the whole solve as one persistent cooperative kernel
   bool persisted = false;
   {
-    PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V};
+    PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0};
     SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
     if (persisted) cycles = hs.cycles;
   }
@@ -763,7 +769,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   if (bs_smem > 160 * 1024) bs_smem = 0;
   if (bs_smem > 0)
     SWM_CK(cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
-  bool first = true;
+  bool first = !given_b;
   SWM_TRY(ensure_poll_slots(ctx));
   static_assert(2 * sizeof(KState) <= kPollSlotBytes, "poll slots");
   KState* slot = reinterpret_cast<KState*>(ctx->pinned_state);
@@ -905,6 +911,55 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
 }
 
 }  // namespace
+
+template <typename TV>
+__global__ void k_init_y(int64_t n, const c128* __restrict__ g, cplx<TV>* __restrict__ Y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) Y[i] = ccast<TV>(g[i]);
+}
+
+// |b_r| per right-hand side (one CTA each, float64), 1 for a zero right-hand side.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_bnorm(int64_t N, const cplx<TV>* __restrict__ B, double* __restrict__ out) {
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += 256) {
+    const cplx<TV> v = B[(int64_t)r * N + n];
+    s += (double)v.re * v.re + (double)v.im * v.im;
+  }
+  __shared__ double red[8];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    out[r] = t > 0.0 ? sqrt(t) : 1.0;
+  }
+}
+
+int norms_of_b(swm_ctx* ctx, const void* B, bool f64, double* bnorm_dev) {
+  if (f64)
+    k_bnorm<double><<<(unsigned)ctx->n_rhs, 256, 0, ctx->stream>>>(ctx->N, (const c128*)B, bnorm_dev);
+  else
+    k_bnorm<float><<<(unsigned)ctx->n_rhs, 256, 0, ctx->stream>>>(ctx->N, (const c64*)B, bnorm_dev);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+int init_y(swm_ctx* ctx, void* Y, bool f64) {
+  const int64_t n = (int64_t)ctx->n_rhs * ctx->N;
+  if (!ctx->guess) {
+    SWM_CK(cudaMemsetAsync(Y, 0, (f64 ? sizeof(c128) : sizeof(c64)) * n, ctx->stream));
+    return SWM_OK;
+  }
+  if (f64)
+    k_init_y<double><<<(unsigned)ceil_div(n, 256), 256, 0, ctx->stream>>>(n, (const c128*)ctx->guess, (c128*)Y);
+  else
+    k_init_y<float><<<(unsigned)ceil_div(n, 256), 256, 0, ctx->stream>>>(n, (const c128*)ctx->guess, (c64*)Y);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
 
 int ensure_poll_slots(swm_ctx* ctx) {
   if (ctx->pinned_state) return SWM_OK;

@@ -70,6 +70,7 @@ struct PBuffers {
   const void* E;                // E in its storage type
   const void* B;
   void *Y, *W, *V;
+  int bnorm_given;              // P.bnorm already holds |b| (solve from an initial guess)
 };
 constexpr int kPersistMaxR = 8;  // right-hand sides of one persistent solve
 

@@ -55,6 +55,7 @@ struct PArgs {
   unsigned arrivals;       // arrivals a grid barrier waits for (G; more only in the timeout test)
   int vsm, esm;            // V / E slices in shared memory
   int64_t emax, cmax;      // largest E and column-map slice of a CTA (entries)
+  int bnorm_given;         // P.bnorm holds |b| (else the first residual norm is |b|)
 };
 
 // Byte offsets of the shared-memory arrays of the persistent kernel.
@@ -555,7 +556,7 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
     if (threadIdx.x < R) {
       const int b = threadIdx.x;
       const double beta = sqrt((double)nrm2[b]);
-      if (first) bnorm[b] = beta > 0.0 ? beta : 1.0;
+      if (first) bnorm[b] = a.bnorm_given ? P.bnorm[b] : (beta > 0.0 ? beta : 1.0);
       const double res = beta / bnorm[b];
       resid[b] = res;
       jl[b] = 0;
@@ -743,6 +744,7 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   pa.esm = esm;
   pa.emax = emax;
   pa.cmax = cmax;
+  pa.bnorm_given = Bf.bnorm_given;
   SWM_CK(cudaMemsetAsync(Bf.sync, 0, sizeof(PSync), st));
   void* args[] = {&pa};
   ctx->prof_begin(SWM_K_GMRES);

@@ -120,9 +120,25 @@ int refine_solve(swm_ctx* ctx, const double* frames_dev, double tol, int restart
   SWM_TRY(dalloc(ctx, S, (void**)&dscale, sizeof(double) * R));
   SWM_TRY(dalloc(ctx, S, (void**)&dgain, sizeof(double) * R));
   SWM_TRY(compute_rhs_f64(ctx, R, frames_dev, B64));
-  SWM_CK(cudaMemsetAsync(Y64, 0, sizeof(c128) * R * N, st));
+  SWM_TRY(init_y(ctx, Y64, true));
   const dim3 gres((unsigned)nchunk, (unsigned)R), gvec((unsigned)ceil_div(N, 256), (unsigned)R);
   std::vector<double> hp((size_t)R * nchunk), bn(R, 1.0), rn(R), rel(R), scale(R), gain(R);
+  {
+    // |b| per right-hand side: the residual of y = 0
+    c128* y0 = nullptr;
+    SWM_TRY(dalloc(ctx, S, (void**)&y0, sizeof(c128) * R * N));
+    SWM_CK(cudaMemsetAsync(y0, 0, sizeof(c128) * R * N, st));
+    k_ir_residual<<<gres, kT, 0, st>>>(N, chunk, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, (const c64*)ctx->Zp,
+                                       B64, y0, Rr, part);
+    SWM_LAUNCHED();
+    SWM_CK(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+    SWM_CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r) {
+      double t = 0.0;
+      for (int c = 0; c < nchunk; ++c) t += hp[(size_t)r * nchunk + c];
+      bn[r] = t > 0.0 ? std::sqrt(t) : 1.0;
+    }
+  }
   int total = 0, outer = 0, rc_inner = SWM_OK;
   bool conv = false;
   while (true) {
@@ -138,7 +154,6 @@ int refine_solve(swm_ctx* ctx, const double* frames_dev, double tol, int restart
       double t = 0.0;
       for (int c = 0; c < nchunk; ++c) t += hp[(size_t)r * nchunk + c];
       rn[r] = std::sqrt(t);
-      if (outer == 0) bn[r] = rn[r] > 0.0 ? rn[r] : 1.0;
       rel[r] = rn[r] / bn[r];
       if (!std::isfinite(rel[r])) return ctx->fail(SWM_ECUDA, "refinement produced a non-finite residual");
       conv = conv && rel[r] <= tol;

@@ -66,6 +66,15 @@ _SIGS = {
     "swm_far_field_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P, C.c_int, _P,
                                          _P]),
     "swm_stateless_error": (C.c_char_p, []),
+    "swm_solve_guess": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _P, C.c_int]),
+    "swm_net_num_params": (C.c_int64, []),
+    "swm_net_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "swm_net_destroy": (None, [_P]),
+    "swm_net_last_error": (C.c_char_p, [_P]),
+    "swm_net_set_params": (C.c_int, [_P, _P, C.c_int]),
+    "swm_net_get_params": (C.c_int, [_P, _P, C.c_int]),
+    "swm_net_predict": (C.c_int, [_P, _P, C.c_int, _P, _P, C.c_int]),
+    "swm_net_train_step": (C.c_int, [_P, _P, C.c_int, _P, _P, C.c_int, C.c_float, _P, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -227,6 +236,102 @@ def swm_solve(ctx: Ctx, inc, tol: float = 1e-6, restart: int = 50, max_iter: int
         pc, kind, _ = _out_ptr(currents_out, np.complex128, (n_inc, n), "currents_out")
     return _check(ctx, load().swm_solve(ctx.handle, n_inc, inc.ctypes.data_as(C.c_void_p), float(tol), int(restart),
                                         int(max_iter), pc, kind))
+
+
+def swm_solve_guess(ctx: Ctx, inc, x0, tol: float = 1e-6, restart: int = 50, max_iter: int = 1000,
+                    currents_out=None) -> int:
+    """swm_solve starting from the initial guess x0 (n_inc x N complex128, caller order)."""
+    inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+    n_inc = inc.shape[0]
+    n = swm_get_stats(ctx)["n"]
+    if _is_torch(x0):
+        px, xk, _ = _ptr(x0, np.complex128, (n_inc, n), "x0")
+    else:
+        x0 = np.ascontiguousarray(x0, dtype=np.complex128).reshape(n_inc, n)
+        px, xk = x0.ctypes.data_as(C.c_void_p), SWM_HOST
+    if currents_out is None:
+        pc, kind = None, SWM_HOST
+    else:
+        pc, kind, _ = _out_ptr(currents_out, np.complex128, (n_inc, n), "currents_out")
+    return _check(ctx, load().swm_solve_guess(ctx.handle, n_inc, inc.ctypes.data_as(C.c_void_p), px, xk, float(tol),
+                                              int(restart), int(max_iter), pc, kind))
+
+
+class Net:
+    """Handle of the warm-start network (see swm_net_* in include/swm.h)."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+
+
+def _net_check(net, rc):
+    if rc < 0:
+        raise SwmError(rc, load().swm_net_last_error(net.handle).decode())
+    return rc
+
+
+def swm_net_num_params() -> int:
+    return int(load().swm_net_num_params())
+
+
+def swm_net_create(device: int = 0, stream=None) -> Net:
+    lib = load()
+    if stream is None:
+        stream = _torch_stream_handle()
+    h = C.c_void_p()
+    rc = lib.swm_net_create(C.byref(h), int(device), C.c_void_p(stream))
+    if rc < 0:
+        raise SwmError(rc, "swm_net_create failed")
+    return Net(h, device)
+
+
+def swm_net_destroy(net: Net) -> None:
+    if net is not None and net.handle:
+        load().swm_net_destroy(net.handle)
+        net.handle = None
+
+
+def swm_net_set_params(net: Net, params) -> int:
+    p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+    if p.size != swm_net_num_params():
+        raise ValueError("wrong parameter count")
+    return _net_check(net, load().swm_net_set_params(net.handle, p.ctypes.data_as(C.c_void_p), SWM_HOST))
+
+
+def swm_net_get_params(net: Net) -> np.ndarray:
+    p = np.zeros(swm_net_num_params(), dtype=np.float32)
+    _net_check(net, load().swm_net_get_params(net.handle, p.ctypes.data_as(C.c_void_p), SWM_HOST))
+    return p
+
+
+def swm_net_predict(net: Net, ctx: Ctx, inc, x0_out=None):
+    """Predicted currents (n_inc x N complex128, caller order); into x0_out if given."""
+    inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+    n_inc, n = inc.shape[0], swm_get_stats(ctx)["n"]
+    if x0_out is None:
+        x0_out = np.zeros((n_inc, n), dtype=np.complex128)
+    px, kind, _ = _out_ptr(x0_out, np.complex128, (n_inc, n), "x0_out")
+    _net_check(net, load().swm_net_predict(net.handle, ctx.handle, n_inc, inc.ctypes.data_as(C.c_void_p), px, kind))
+    return x0_out
+
+
+def swm_net_train_step(net: Net, ctx: Ctx, inc, x_true, lr: float = 0.0, want_grad: bool = False):
+    """Loss of the prediction against x_true (n_inc x N complex128, caller order); with lr > 0 one
+    Adam step.  Returns (loss, gradient or None)."""
+    inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+    n_inc, n = inc.shape[0], swm_get_stats(ctx)["n"]
+    if _is_torch(x_true):
+        pt, kind, _ = _ptr(x_true, np.complex128, (n_inc, n), "x_true")
+    else:
+        x_true = np.ascontiguousarray(x_true, dtype=np.complex128).reshape(n_inc, n)
+        pt, kind = x_true.ctypes.data_as(C.c_void_p), SWM_HOST
+    loss = C.c_double()
+    g = np.zeros(swm_net_num_params(), dtype=np.float32) if want_grad else None
+    pg = g.ctypes.data_as(C.c_void_p) if want_grad else None
+    _net_check(net, load().swm_net_train_step(net.handle, ctx.handle, n_inc, inc.ctypes.data_as(C.c_void_p), pt, kind,
+                                              float(lr), C.byref(loss), pg))
+    return loss.value, g
 
 
 def swm_rcs_bistatic(ctx: Ctx, obs, sigma_out) -> int:
