@@ -141,7 +141,7 @@ def cpu_baseline(n_wires=1000):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, mid workload, from one ncu capture of
 # the kernel's current code (profiles/gmres_persist_mid.md)
-MEASURED_TRAFFIC = {("gmres", "c64"): 3.98e6}
+MEASURED_TRAFFIC = {("gmres", "c64"): 3.975e6}
 
 
 # ---------------------------------------------------------------------------------- ranks
@@ -526,6 +526,163 @@ def run_compare(args):
                       "paths": res}))
 
 
+def run_warm(args):
+    """Learned warm start on the mid workload: train the network on clouds of the same statistics
+    (other seeds, 8 random incidences each, currents solved to 1e-8), then time the step with and
+    without it on the benchmark cloud.  Prints a JSON line of kind "warm_start" (a measurement
+    record; the network's training is outside the timed steps)."""
+    import torch
+
+    from paper_2410_03060_gb300 import swm
+    from synth.netinit import init_params
+
+    torch.cuda.set_device(0)
+    g = np.random.default_rng(5)
+
+    def incs(n):
+        return np.stack([np.arccos(g.uniform(-1, 1, n)), g.uniform(0, 2 * math.pi, n), g.uniform(0, math.pi, n)], 1)
+
+    train = []
+    for seed in range(11, 11 + args.train_clouds):
+        c = cloud_mid(seed=seed)
+        ctx = swm.swm_create(0)
+        swm.swm_set_cloud(ctx, c.centres, c.dirs, c.lengths, c.radii, c.nseg)
+        swm.swm_build(ctx, K0, R_C, swm.SWM_C64)
+        inc = incs(8)
+        X = np.zeros((8, c.n_unknowns), dtype=np.complex128)
+        swm.swm_solve(ctx, inc, 1e-8, RESTART, 2000, X)
+        train.append((ctx, inc, X))
+    net = swm.swm_net_create(0)
+    swm.swm_net_set_params(net, init_params(0))
+    t0 = time.perf_counter()
+    losses = []
+    for it in range(args.train_steps):
+        ctx, inc, X = train[it % len(train)]
+        losses.append(swm.swm_net_train_step(net, ctx, inc, X, 3e-4)[0])
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    for ctx, _, _ in train:
+        swm.swm_destroy(ctx)
+    cl = cloud_mid(seed=1)
+    inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
+    sig = torch.zeros((1, N_OBS, 2), dtype=torch.float64, device="cuda")
+    x0 = torch.zeros((1, cl.n_unknowns), dtype=torch.complex128, device="cuda")
+    ctx = swm.swm_create(0)
+
+    def step(warm):
+        swm.swm_set_cloud(ctx, *dev)
+        swm.swm_build(ctx, K0, R_C, swm.SWM_C64)
+        if warm:
+            swm.swm_net_predict(net, ctx, inc, x0)
+            swm.swm_solve_guess(ctx, inc, x0, TOL, RESTART, 1000)
+        else:
+            swm.swm_solve(ctx, inc, TOL, RESTART, 1000)
+        swm.swm_rcs_bistatic(ctx, obs, sig)
+
+    res = {}
+    for warm in (False, True):
+        for _ in range(3):
+            step(warm)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step(warm)
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        st = swm.swm_get_stats(ctx)
+        res["warm" if warm else "cold"] = {"ms_per_step": ms, "value": cl.n_unknowns / (ms * 1e-3),
+                                           "iterations": st["iterations"], "ms_solve": st["ms_solve"],
+                                           "rcs": sig.cpu().numpy()[0, :, 0].copy()}
+    # quality of the initial guess on this (unseen) cloud, against its converged currents
+    X = torch.zeros((1, cl.n_unknowns), dtype=torch.complex128, device="cuda")
+    swm.swm_set_cloud(ctx, *dev)
+    swm.swm_build(ctx, K0, R_C, swm.SWM_C64)
+    swm.swm_solve(ctx, inc, 1e-8, RESTART, 2000, X)
+    loss_net = swm.swm_net_train_step(net, ctx, inc, X, 0.0)[0]
+    swm.swm_net_set_params(net, init_params(0) * 0)
+    loss_iso = swm.swm_net_train_step(net, ctx, inc, X, 0.0)[0]
+    out = {"kind": "warm_start", "workload": "mid (10,000 wires), 1 incidence, 720-angle RCS",
+           "train": {"clouds": args.train_clouds, "incidences_each": 8, "steps": args.train_steps, "seconds": train_s,
+                     "loss_first_100": float(np.mean(losses[:100])), "loss_last_100": float(np.mean(losses[-100:]))},
+           "initial_guess_rel_sq_error": {"isolated_wires": loss_iso, "network": loss_net},
+           "rcs_err_db_warm_vs_cold": rcs_db_error(res["warm"]["rcs"], res["cold"]["rcs"]),
+           "cold": {k: v for k, v in res["cold"].items() if k != "rcs"},
+           "warm": {k: v for k, v in res["warm"].items() if k != "rcs"}}
+    print(json.dumps(out))
+    swm.swm_net_destroy(net)
+    swm.swm_destroy(ctx)
+
+
+def run_batch(args):
+    """The batching workload: 64 cloud snapshots of 2,000-50,000 wires (log-uniform sizes, 0.005
+    wires per cubic wavelength), each solved for 181 monostatic incidences (complex64, GMRES to 1e-6)
+    with its monostatic RCS.  Snapshots run concurrently on --streams contexts, each on its own CUDA
+    stream and host thread.  Prints a JSON line of kind "batch" (a measurement record)."""
+    import threading
+
+    import torch
+
+    from paper_2410_03060_gb300 import swm
+    from synth import batching_sizes
+
+    torch.cuda.set_device(0)
+    n_snap = args.snapshots
+    sizes = batching_sizes(n_snap)
+    clouds = [cloud_batching_snapshot(i) for i in range(n_snap)]
+    n_inc = args.inc or 181
+    inc = incidences_monostatic(n_inc)
+    dev = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (c.centres, c.dirs, c.lengths, c.radii, c.nseg)]
+           for c in clouds]
+    n_str = max(1, args.streams)
+    streams = [torch.cuda.Stream() for _ in range(n_str)]
+    ctxs = [swm.swm_create(0, stream=s.cuda_stream) for s in streams]
+    monos = [torch.zeros((n_inc, 2), dtype=torch.float64, device="cuda") for _ in range(n_str)]
+    its = [0] * n_snap
+
+    def worker(w, order):
+        with torch.cuda.stream(streams[w]):
+            for i in order:
+                ctx = ctxs[w]
+                swm.swm_set_cloud(ctx, *dev[i])
+                swm.swm_build(ctx, K0, R_C, swm.SWM_C64)
+                swm.swm_solve(ctx, inc, TOL, args.restart, 2000)
+                swm.swm_rcs_monostatic(ctx, monos[w])
+                its[i] = swm.swm_get_stats(ctx)["iterations"]
+
+    # largest snapshots first, dealt round-robin to the streams
+    order = list(np.argsort(-sizes))
+    plan = [order[w::n_str] for w in range(n_str)]
+
+    def run_all():
+        th = [threading.Thread(target=worker, args=(w, plan[w])) for w in range(n_str)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        torch.cuda.synchronize()
+
+    run_all()  # warm-up (allocations, the step kernel's block size per shape)
+    ts = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        run_all()
+        ts.append(time.perf_counter() - t0)
+    units = float(sum(c.n_unknowns for c in clouds)) * n_inc
+    sec = float(np.median(ts))
+    print(json.dumps({"kind": "batch", "snapshots": n_snap, "wires": int(sum(c.nw for c in clouds)),
+                      "unknowns": int(sum(c.n_unknowns for c in clouds)), "incidences_each": n_inc,
+                      "streams": n_str, "restart": args.restart, "seconds_per_batch": sec,
+                      "value": units / sec, "unit": UNIT, "iterations_min_max": [int(min(its)), int(max(its))],
+                      "step_rhs_block_last": [swm.swm_get_stats(c)["step_rhs_block"] for c in ctxs]}))
+    for c in ctxs:
+        swm.swm_destroy(c)
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -567,6 +724,14 @@ def main():
     ap.add_argument("--inc", type=int, default=0, help="incidences of a larger workload (default: its own)")
     ap.add_argument("--restart", type=int, default=RESTART)
     ap.add_argument("--nw", type=int, default=0, help="wire count of a larger workload (default: its own)")
+    ap.add_argument("--batch", action="store_true",
+                    help="the 64-snapshot batching workload, snapshots spread over --streams contexts")
+    ap.add_argument("--snapshots", type=int, default=64)
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--warm-start", action="store_true",
+                    help="mid workload with and without the learned warm start (trains the network first)")
+    ap.add_argument("--train-clouds", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--compare-precisions", action="store_true",
                     help="larger workload: time the float64, complex64 and bfloat16-refinement paths")
     args = ap.parse_args()
@@ -576,6 +741,12 @@ def main():
             run_compare(args)
         else:
             run_scale(args)
+        return
+    if args.batch and args.impl == "ours":
+        run_batch(args)
+        return
+    if args.warm_start and args.impl == "ours":
+        run_warm(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -115,6 +115,9 @@ typedef struct swm_stats {
   int64_t prof_launches;   /* launches of the profiled kernel class */
   int pattern_reused;      /* 1 if the last build kept the previous S-NFC pattern (same cloud and
                               r_c, e.g. a frequency sweep) and only refilled the values */
+  int step_rhs_block;      /* incidences sharing each read of the blocks in the last solve's
+                              per-kernel GMRES step (1, or 4 / 8 / 16 as timed on the system the
+                              first time a shape was solved on this context) */
 } swm_stats;
 
 /* kernel classes for swm_profile */

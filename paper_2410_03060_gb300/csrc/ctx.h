@@ -125,6 +125,13 @@ struct swm_ctx {
   int* d_sing = nullptr;                  // singular self block flag (device)
   void* pinned_state = nullptr;           // two pinned slots for the Krylov state poll
   int solver = 0;                         // SWM_SOLVER_GMRES or SWM_SOLVER_GCR
+  // right-hand sides per block of the fused multi-incidence GMRES step, measured per system shape
+  // (N, n_rhs, vector and matrix entry sizes, chunk, restart)
+  struct Tuned {
+    int64_t shape[6];
+    int rb;
+  };
+  std::vector<Tuned> tuned;
   const void* guess = nullptr;            // during swm_solve_guess: y0 = M x0, complex128 [n_rhs][N]
   void* ffw = nullptr;                    // per-wire float32 far-field data (complex64 path)
   cudaGraphExec_t gm_exec = nullptr;      // captured chunk of GMRES steps and its argument key

@@ -748,17 +748,37 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   }
   const dim3 g_rows((unsigned)ceil_div(N * kG, kRows), R);
   const dim3 g_chunk((unsigned)P.nchunk, R);
-  constexpr int kRB = 8;
+  constexpr int kRB = 8;  // right-hand sides sharing each read of E in the streaming product
   const bool multi = R > 1;
   // large systems: streaming product and separate dots (bandwidth); small: one fused kernel (latency)
   const bool split = N >= ctx->split_rows;
-  const dim3 g_schunk((unsigned)P.nschunk, multi ? (unsigned)ceil_div(R, kRB) : 1u);
   const size_t sm = sizeof(cplx<TV>) * P.chunk;
-  const size_t ssm = sizeof(cplx<TV>) * P.schunk * (multi ? kRB : 1);
-  if (ssm > 48 * 1024) {
-    SWM_CK(cudaFuncSetAttribute(k_step<TV, TE, kRB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
-    SWM_CK(cudaFuncSetAttribute(k_step<TV, TE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
-  }
+  // Fused step with several right-hand sides: how many share each read of E (4, 8 or 16) is
+  // measured on this system the first time its shape is seen, and kept.
+  int rb = multi ? 8 : 1;
+  auto ssm_of = [&](int b) { return sizeof(cplx<TV>) * (size_t)P.schunk * b; };
+  auto step_fn = [&](int b) -> const void* {
+    switch (b) {
+      case 1: return (const void*)k_step<TV, TE, 1>;
+      case 4: return (const void*)k_step<TV, TE, 4>;
+      case 16: return (const void*)k_step<TV, TE, 16>;
+      default: return (const void*)k_step<TV, TE, 8>;
+    }
+  };
+  auto launch_step = [&](cudaStream_t s, int b) {
+    const dim3 gs((unsigned)P.nschunk, (unsigned)ceil_div(R, b));
+    const size_t sz = ssm_of(b);
+    const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
+    switch (b) {
+      case 1: k_step<TV, TE, 1><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
+      case 4: k_step<TV, TE, 4><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
+      case 16: k_step<TV, TE, 16><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
+      default: k_step<TV, TE, 8><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
+    }
+  };
+  for (int b : {1, 4, 8, 16})
+    if (ssm_of(b) > 48 * 1024 && ssm_of(b) <= 200 * 1024)
+      SWM_CK(cudaFuncSetAttribute(step_fn(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm_of(b)));
   if (sm > 48 * 1024) {
     SWM_CK(cudaFuncSetAttribute(k_update<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SWM_CK(cudaFuncSetAttribute(k_dots_big<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -788,11 +808,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
         ctx->prof_begin(SWM_K_DOTS);
         k_dots_big<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
         ctx->prof_end(SWM_K_DOTS);
-      } else if (multi) {
-        k_step<TV, TE, kRB><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
-        ctx->prof_end(SWM_K_APPLY);
       } else {
-        k_step<TV, TE, 1><<<g_schunk, kRows, ssm, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
+        launch_step(s, rb);
         ctx->prof_end(SWM_K_APPLY);
       }
       SWM_LAUNCHED();
@@ -810,6 +827,50 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   // A chunk of Arnoldi steps is a CUDA graph (the launches are identical every step), captured on
   // a private stream and reused while the kernel arguments stay the same.  Profiling a GMRES kernel
   // class uses direct launches so its events time each launch.
+  if (!persisted && multi && !split) {
+    const int64_t shape[6] = {N, R, (int64_t)sizeof(TV), (int64_t)sizeof(TE), P.schunk, restart};
+    int found = 0;
+    for (const auto& t : ctx->tuned)
+      if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
+    if (found) {
+      rb = found;
+    } else {
+      // first cycle's residual and start (the loop below repeats them; both are idempotent), then
+      // each candidate step once untimed and once timed; the step is idempotent at a fixed j
+      k_apply<TV, TE><<<g_rows, kRows, 0, st>>>(1, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
+      SWM_LAUNCHED();
+      k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, W0, first ? 1 : 0);
+      SWM_LAUNCHED();
+      cudaEvent_t e0, e1;
+      SWM_CK(cudaEventCreate(&e0));
+      SWM_CK(cudaEventCreate(&e1));
+      float best = 0.f;
+      for (int b : {4, 8, 16}) {
+        if (ssm_of(b) > 200 * 1024) continue;
+        if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
+        launch_step(st, b);
+        SWM_CK(cudaEventRecord(e0, st));
+        launch_step(st, b);
+        SWM_CK(cudaEventRecord(e1, st));
+        ctx->launches += 2;
+        SWM_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SWM_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best == 0.f || ms < best) {
+          best = ms;
+          rb = b;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      SWM_CK(cudaGetLastError());
+      swm_ctx::Tuned t{};
+      std::memcpy(t.shape, shape, sizeof(shape));
+      t.rb = rb;
+      ctx->tuned.push_back(t);
+    }
+  }
+  ctx->stats.step_rhs_block = rb;
   const bool use_graph = !persisted && ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_DOTS &&
                          ctx->prof_cls != SWM_K_UPDATE && ctx->prof_cls != SWM_K_FINISH;
   if (use_graph) {
@@ -828,7 +889,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     key.sm = sm;
     key.gx = g_chunk.x;
     key.gy = g_chunk.y;
-    key.bits = (unsigned)(sizeof(TV) * 64 + sizeof(TE));
+    key.bits = (unsigned)(sizeof(TV) * 64 + sizeof(TE) + 4096 * rb);
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
     std::vector<unsigned char> kv(kb, kb + sizeof(key));
     if (!ctx->gm_exec || kv != ctx->gm_key) {

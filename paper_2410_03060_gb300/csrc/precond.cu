@@ -14,9 +14,75 @@ namespace swm {
 namespace {
 
 
-// Gauss-Jordan inversion with partial pivoting of Z_pp in precision R, one warp per wire: lane j
-// owns column j of the augmented matrix [Z_pp | I] (2 m_p <= 30 columns) and sweeps the rows, so no
-// lane divides indices; the pivot row is the warp's arg-max of |a[r][c]| (ties: smallest r).
+// Gauss-Jordan inversion with partial pivoting of Z_pp in precision R, one warp per wire, the
+// lanes spread over the (row, column) entries of each elimination step: the float64 form (a
+// lane-per-column sweep would chain m float64 operations per lane, slow on this GPU's float64 pipe).
+template <typename R, typename TV>
+__global__ void __launch_bounds__(128) k_invert_self_entries(int64_t nw, const int32_t* __restrict__ m,
+                                                    const int64_t* __restrict__ diag_b, Layout lay,
+                                                    const cplx<TV>* __restrict__ Z, const int64_t* __restrict__ moff,
+                                                    cplx<TV>* __restrict__ Minv, int* __restrict__ singular) {
+  __shared__ cplx<R> A[4][kMaxM][2 * kMaxM];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * 4 + wl;
+  if (p >= nw) return;
+  const int n = m[p];
+  const int K = lay.K[p];
+  const int64_t base = lay.rowbase[p] + lay.colpos[diag_b[p]];
+  cplx<R>(*a)[2 * kMaxM] = A[wl];
+  for (int e = lane; e < n * 2 * n; e += 32) {
+    const int i = e / (2 * n), j = e % (2 * n);
+    a[i][j] = j < n ? ccast<R>(Z[base + (int64_t)i * K + j]) : mkc<R>(j - n == i ? R(1) : R(0), R(0));
+  }
+  __syncwarp();
+  for (int c = 0; c < n; ++c) {
+    // pivot: largest |a[r][c]|, r >= c (ties: smallest r)
+    R best = -1;
+    int br = c;
+    for (int r = c; r < n; ++r) {
+      const R v = a[r][c].re * a[r][c].re + a[r][c].im * a[r][c].im;
+      if (v > best) {
+        best = v;
+        br = r;
+      }
+    }
+    if (best == R(0)) {
+      if (lane == 0) atomicExch(singular, 1);
+      return;
+    }
+    if (br != c) {
+      for (int j = lane; j < 2 * n; j += 32) {
+        const cplx<R> t = a[c][j];
+        a[c][j] = a[br][j];
+        a[br][j] = t;
+      }
+      __syncwarp();
+    }
+    const cplx<R> piv = a[c][c];
+    const R den = piv.re * piv.re + piv.im * piv.im;
+    const cplx<R> inv = mkc<R>(piv.re / den, -piv.im / den);
+    __syncwarp();
+    for (int j = lane; j < 2 * n; j += 32) a[c][j] = a[c][j] * inv;
+    __syncwarp();
+    for (int e = lane; e < n * 2 * n; e += 32) {
+      const int r = e / (2 * n), j = e % (2 * n);
+      if (r != c && j != c) a[r][j] = a[r][j] - a[r][c] * a[c][j];
+    }
+    __syncwarp();
+    for (int r = lane; r < n; r += 32)
+      if (r != c) a[r][c] = mkc<R>(0, 0);
+    __syncwarp();
+  }
+  const int64_t mo = moff[p];
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e % n;
+    Minv[mo + e] = ccast<TV>(a[i][n + j]);
+  }
+}
+
+// The same inversion, float32 form: lane j owns column j of the augmented matrix [Z_pp | I]
+// (2 m_p <= 30 columns) and sweeps the rows, so no lane divides indices; the pivot row is the
+// warp's arg-max of |a[r][c]| (ties: smallest r).
 template <typename R, typename TV>
 __global__ void __launch_bounds__(128) k_invert_self(int64_t nw, const int32_t* __restrict__ m,
                                                     const int64_t* __restrict__ diag_b, Layout lay,
@@ -120,7 +186,7 @@ int build_precond(swm_ctx* ctx) {
   const unsigned g2 = (unsigned)std::max<int64_t>(1, ceil_div(ctx->nb * 32, 256));
   if (ctx->prec == SWM_C128) {
     ctx->prof_begin(SWM_K_INVERT);
-    k_invert_self<double, double><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
+    k_invert_self_entries<double, double><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
                                                                ctx->minv_off, (c128*)ctx->Minv, ctx->d_sing);
     ctx->prof_end(SWM_K_INVERT);
     SWM_LAUNCHED();
