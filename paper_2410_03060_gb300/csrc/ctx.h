@@ -276,6 +276,16 @@ int ensure_rowinfo(swm_ctx* ctx);
 int init_y(swm_ctx* ctx, void* Y, bool f64);
 // |b_r| of the [n_rhs][N] right-hand sides into bnorm_dev (device), 1 for a zero one
 int norms_of_b(swm_ctx* ctx, const void* B, bool f64, double* bnorm_dev);
+// Lets kernel `fn` launch with as much dynamic shared memory as a CTA may have on the device
+// (smem_optin less its static shared memory).  Always the same value for a kernel, so contexts
+// driven from several host threads do not undo each other's setting of this process-wide
+// attribute; a launch that asks for less is unaffected.
+inline cudaError_t allow_max_dyn_smem(const void* fn, int smem_optin) {
+  cudaFuncAttributes fa{};
+  const cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)fa.sharedSizeBytes);
+}
 // two pinned host slots (kPollSlotBytes in all) for polling the solvers' device state
 constexpr size_t kPollSlotBytes = 128;
 int ensure_poll_slots(swm_ctx* ctx);

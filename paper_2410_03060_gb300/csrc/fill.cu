@@ -703,7 +703,7 @@ int launch_fill(swm_ctx* ctx, const GLTable& gl, unsigned long long* evals) {
   nbatch = std::min(nbatch, kFillThreads);
   const size_t smem = round16(sizeof(BlockGeo) * nbatch) + 2 * round16(sizeof(int) * (nbatch + 1)) +
                       sizeof(SegI<R>) * nbatch * items_per_block;
-  SWM_CK(cudaFuncSetAttribute(k_mutual_blocks<R, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SWM_CK(allow_max_dyn_smem((const void*)k_mutual_blocks<R, TV>, ctx->smem_optin));
   if (ctx->nup > 0) {
     const int64_t grid = ceil_div(ctx->nup, nbatch);
     ctx->prof_begin(SWM_K_FILL_MUTUAL);
@@ -742,7 +742,7 @@ int fill_blocks(swm_ctx* ctx) {
     const int acc_per_block = std::max(1, mm * mm);
     const size_t smem = sizeof(float2) * (size_t)(kFillF32Threads / 32) * kWarpBlocks * acc_per_block;
     if (smem > 48 * 1024)
-      SWM_CK(cudaFuncSetAttribute(k_mutual_blocks_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SWM_CK(allow_max_dyn_smem((const void*)k_mutual_blocks_f32, ctx->smem_optin));
     const int64_t blocks_per_cta = (int64_t)(kFillF32Threads / 32) * kWarpBlocks;
     ctx->prof_begin(SWM_K_FILL_MUTUAL);
     k_mutual_blocks_f32<<<(unsigned)ceil_div(ctx->nup, blocks_per_cta), kFillF32Threads, smem, ctx->stream>>>(

@@ -411,9 +411,9 @@ int gcr_impl(swm_ctx* ctx, double tol, int m, int max_iter) {
   const dim3 grid((unsigned)P.nchunk, (unsigned)R);
   const size_t sm = sizeof(C) * P.chunk;
   if (sm > 48 * 1024) {
-    SWM_CK(cudaFuncSetAttribute(k_gcr_product<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    SWM_CK(cudaFuncSetAttribute(k_gcr_pass2<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    SWM_CK(cudaFuncSetAttribute(k_gcr_coef<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SWM_CK(allow_max_dyn_smem((const void*)k_gcr_product<TV>, ctx->smem_optin));
+    SWM_CK(allow_max_dyn_smem((const void*)k_gcr_pass2<TV>, ctx->smem_optin));
+    SWM_CK(allow_max_dyn_smem((const void*)k_gcr_coef<TV>, ctx->smem_optin));
   }
   SWM_TRY(ensure_poll_slots(ctx));
   static_assert(2 * sizeof(GState) <= kPollSlotBytes, "poll slots");

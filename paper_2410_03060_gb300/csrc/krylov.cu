@@ -88,15 +88,15 @@ __device__ void cta_dots(const KPtr& P, int j, int r, const cplx<TV>* __restrict
     const cplx<TV>* vi = V + ((int64_t)i * P.R + r) * P.N + n0;
     cplx<TV> acc = mkc<TV>(0, 0);
     int t = lane;
-    for (; t + 96 < cnt; t += 128) {
-      cplx<TV> v[4], w[4];
+    for (; t + 224 < cnt; t += 256) {  // eight loads in flight per lane
+      cplx<TV> v[8], w[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         v[u] = vi[t + 32 * u];
         w[u] = w_sm[t + 32 * u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         acc.re = fma(v[u].re, w[u].re, fma(v[u].im, w[u].im, acc.re));
         acc.im = fma(v[u].re, w[u].im, fma(-v[u].im, w[u].re, acc.im));
       }
@@ -356,7 +356,7 @@ __device__ void cta_update(const KPtr& P, int j, int r, const cplx<TV>* __restri
   __syncthreads();
   for (int t = threadIdx.x; t < cnt; t += kRows) {
     cplx<TV> x = w[t];
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i <= j; ++i) {
       const cplx<TV> v = V[((int64_t)i * P.R + r) * P.N + n0 + t];
       const cplx<TV> hh = hs[i];
@@ -657,7 +657,9 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   P.restart = restart;
   P.N = N;
   P.tol = tol;
-  P.chunk = (int)std::max<int64_t>(kRows, ceil_div(ceil_div(N, 512), kRows) * kRows);
+  // rows per CTA of the Gram-Schmidt kernels: about 512 chunks per right-hand side, or 2048 for a
+  // single one (smaller chunks, less shared memory each, more CTAs and loads in flight per SM)
+  P.chunk = (int)std::max<int64_t>(kRows, ceil_div(ceil_div(N, R == 1 ? 2048 : 512), kRows) * kRows);
   P.nchunk = (int)ceil_div(N, P.chunk);
   // the fused step kernel: 128 rows per CTA for one right-hand side; with several, chunks as large as
   // keep about four CTAs per SM busy over the blocks of 8 right-hand sides (at most 1024 rows), so
@@ -778,17 +780,17 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   };
   for (int b : {1, 4, 8, 16})
     if (ssm_of(b) > 48 * 1024 && ssm_of(b) <= 200 * 1024)
-      SWM_CK(cudaFuncSetAttribute(step_fn(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm_of(b)));
+      SWM_CK(allow_max_dyn_smem(step_fn(b), ctx->smem_optin));
   if (sm > 48 * 1024) {
-    SWM_CK(cudaFuncSetAttribute(k_update<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    SWM_CK(cudaFuncSetAttribute(k_dots_big<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    SWM_CK(cudaFuncSetAttribute(k_finish<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SWM_CK(allow_max_dyn_smem((const void*)k_update<TV>, ctx->smem_optin));
+    SWM_CK(allow_max_dyn_smem((const void*)k_dots_big<TV>, ctx->smem_optin));
+    SWM_CK(allow_max_dyn_smem((const void*)k_finish<TV>, ctx->smem_optin));
   }
   // back substitution stages the triangle in shared memory when it fits
   size_t bs_smem = sizeof(c128) * (size_t)restart * restart;
   if (bs_smem > 160 * 1024) bs_smem = 0;
   if (bs_smem > 0)
-    SWM_CK(cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
+    SWM_CK(allow_max_dyn_smem((const void*)k_backsolve, ctx->smem_optin));
   bool first = !given_b;
   SWM_TRY(ensure_poll_slots(ctx));
   static_assert(2 * sizeof(KState) <= kPollSlotBytes, "poll slots");

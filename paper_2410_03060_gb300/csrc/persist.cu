@@ -720,7 +720,7 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   const size_t smem = persist_layout(RB, R, restart, prows, cb, eb, vsm, esm, emax, cmax).total;
   if (smem > limit) return SWM_OK;
   int occ = 0;
-  SWM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SWM_CK(allow_max_dyn_smem(fn, ctx->smem_optin));
   SWM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPT, smem));
   if (occ < 1 || G > occ * ctx->nsm) return SWM_OK;
   PArgs pa{};

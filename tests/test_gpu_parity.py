@@ -316,3 +316,61 @@ def test_persistent_barrier_wait_runs_out_and_reports_etimeout(monkeypatch):
         assert out["rc"] == 0 and out["stats"]["converged"] == 1
     finally:
         swm.swm_destroy(out["ctx"])
+
+
+def test_contexts_on_concurrent_host_threads():
+    """Contexts driven from several host threads at once (each on its own stream, with systems of
+    different sizes, so their kernels ask for different amounts of shared memory) give the same
+    currents as when run one after the other."""
+    import threading
+
+    import torch
+
+    from paper_2410_03060_gb300 import swm
+
+    # up to 150k unknowns: the fused step kernel then asks for more than 48 KB of shared memory
+    clouds = [cloud_uniform_cube(n, (n / 0.02) ** (1 / 3), seed=90 + i)
+              for i, n in enumerate((30000, 26000, 12000, 3000))]
+    inc = np.stack([np.linspace(0.1, 3.0, 9), np.linspace(0.0, 5.0, 9), np.zeros(9)], 1)
+
+    def solve(cl, ctx, out):
+        swm.swm_set_cloud(ctx, cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)
+        swm.swm_build(ctx, K, 2.0, C64)
+        cur = np.zeros((inc.shape[0], cl.n_unknowns), dtype=np.complex128)
+        swm.swm_solve(ctx, inc, 1e-6, 20, 500, cur)
+        out.append(cur)
+
+    seq = []
+    for cl in clouds:
+        ctx = swm.swm_create(0)
+        try:
+            solve(cl, ctx, seq)
+        finally:
+            swm.swm_destroy(ctx)
+    streams = [torch.cuda.Stream() for _ in clouds]
+    ctxs = [swm.swm_create(0, stream=s.cuda_stream) for s in streams]
+    outs = [[] for _ in clouds]
+    errors = []
+
+    def work(i):
+        try:
+            with torch.cuda.stream(streams[i]):
+                for _ in range(3):
+                    solve(clouds[i], ctxs[i], outs[i])
+        except Exception as e:  # reported below: a thread's exception does not reach pytest
+            errors.append(repr(e))
+
+    try:
+        th = [threading.Thread(target=work, args=(i,)) for i in range(len(clouds))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        torch.cuda.synchronize()
+        assert not errors, errors
+        for i in range(len(clouds)):
+            for cur in outs[i]:
+                assert np.linalg.norm(cur - seq[i]) <= 1e-12 * np.linalg.norm(seq[i])
+    finally:
+        for c in ctxs:
+            swm.swm_destroy(c)
