@@ -356,7 +356,7 @@ __device__ void cta_update(const KPtr& P, int j, int r, const cplx<TV>* __restri
   __syncthreads();
   for (int t = threadIdx.x; t < cnt; t += kRows) {
     cplx<TV> x = w[t];
-#pragma unroll 8
+#pragma unroll 4
     for (int i = 0; i <= j; ++i) {
       const cplx<TV> v = V[((int64_t)i * P.R + r) * P.N + n0 + t];
       const cplx<TV> hh = hs[i];
