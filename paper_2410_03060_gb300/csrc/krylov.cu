@@ -28,6 +28,8 @@ namespace swm {
 namespace {
 
 constexpr int kRows = 256;  // CTA width of the vector kernels
+constexpr int kMinorR = 12;  // right-hand sides from which the large-system product reads them
+                             // right-hand-side minor (one lane each)
 constexpr int kG = 8;       // lanes per scalar row in the block-sparse product
 
 template <typename T>
@@ -325,6 +327,75 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
       dst[off_r + n] = act[b] ? x + sc[b] * acc[b] : mkc<TV>(0, 0);
     }
   }
+}
+
+// Large-N form of the step with many right-hand sides, part 0: the current Krylov vectors
+// (right-hand-side major, [R][N]) copied to right-hand-side minor order Xt[N][R], through
+// shared-memory tiles of 32 rows x 32 right-hand sides, so that the product below reads the values
+// of all right-hand sides at a column as one contiguous run.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __restrict__ W0,
+                                                   const cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ Xt) {
+  if (P.st->cycle_done) return;
+  const cplx<TV>* src = (P.st->j & 1) ? W1 : W0;
+  __shared__ cplx<TV> tile[32][33];
+  const int64_t n0 = (int64_t)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k;
+    const int64_t n = n0 + tx;
+    if (r < P.R && n < P.N) tile[k][tx] = src[(int64_t)r * P.N + n];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t n = n0 + k;
+    const int r = r0 + tx;
+    if (r < P.R && n < P.N) Xt[n * P.R + r] = tile[tx][k];
+  }
+}
+
+// Large-N form of the step with many right-hand sides, part 1: normalise and multiply by
+// A = I + E with one lane per right-hand side: the RB lanes of a row group read each entry of E
+// once (the same address: one transaction) and the RB values of the gathered column as one
+// contiguous run of Xt.  E is read once per block of RB right-hand sides.
+template <typename TV, typename TE, int RB>
+__global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restrict__ rinfo,
+                                                const int32_t* __restrict__ colmap, const TE* __restrict__ E,
+                                                const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ W0,
+                                                cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ V) {
+  if (P.st->cycle_done) return;
+  const int j = P.st->j;
+  const int64_t N = P.N;
+  const int R = P.R;
+  const int64_t n = (blockIdx.x * (int64_t)256 + threadIdx.x) / RB;
+  const int r = blockIdx.y * RB + (int)(threadIdx.x % RB);
+  if (n >= N || r >= R) return;  // no collective operation below: lanes leave independently
+  cplx<TV>* dst = ((j & 1) ? W0 : W1) + (int64_t)r * N;
+  if (!P.active[r]) {
+    V[((int64_t)j * R + r) * N + n] = mkc<TV>(0, 0);
+    dst[n] = mkc<TV>(0, 0);
+    return;
+  }
+  const TV sc = (TV)P.inv_h[r];
+  const RowInfo ri = rinfo[n];
+  const int32_t* cm = colmap + ri.cmb;
+  cplx<TV> acc = mkc<TV>(0, 0);
+  int c = 0;
+  for (; c + 3 < ri.K; c += 4) {
+    cplx<TV> e[4], x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      e[u] = ELoad<TV, TE>::ld(E + ri.vb + c + u);
+      x[u] = Xt[(int64_t)cm[c + u] * R + r];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cfma(acc, e[u], x[u]);
+  }
+  for (; c < ri.K; ++c) cfma(acc, ELoad<TV, TE>::ld(E + ri.vb + c), Xt[(int64_t)cm[c] * R + r]);
+  const cplx<TV> x = sc * Xt[n * R + r];
+  V[((int64_t)j * R + r) * N + n] = x;
+  dst[n] = x + sc * acc;
 }
 
 // Large-N form of the step, part 2: h = V^H w over chunks of rows (first Gram-Schmidt pass).
@@ -678,6 +749,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     int64_t key[4];
     KPtr P;
     cplx<TV> *Y, *W0, *W1, *V;
+    cplx<TV>* Xt;         // many right-hand sides, large systems: the current vectors, [N][R]
     PSync* sync;          // persistent solve: barrier state and partial sums over its CTAs
     c128 *pp1, *pp2;
     double* ppn;
@@ -714,6 +786,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W0, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W1, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->V, sizeof(cplx<TV>) * (size_t)R1 * R * N));
+    if (R >= kMinorR && N >= ctx->split_rows)
+      SWM_TRY(dalloc(ctx, K, (void**)&ws->Xt, sizeof(cplx<TV>) * (size_t)R * N));
     if (R <= kPersistMaxR && ctx->nsm > 0) {
       SWM_TRY(dalloc(ctx, K, (void**)&ws->sync, sizeof(PSync)));
       SWM_TRY(dalloc(ctx, K, (void**)&ws->pp1, sizeof(c128) * (size_t)R * R1 * ctx->nsm));
@@ -801,7 +875,18 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       ctx->prof_begin(SWM_K_APPLY);
       if (split) {
         const dim3 gsp((unsigned)ceil_div(N * kG, kRows), multi ? (unsigned)ceil_div(R, kRB) : 1u);
-        if (multi)
+        if (ws->Xt) {
+          const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
+          k_rhs_minor<TV><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, W0, W1, ws->Xt);
+          SWM_LAUNCHED();
+          if (R >= 24) {
+            const dim3 g((unsigned)ceil_div(N * 32, 256), (unsigned)ceil_div(R, 32));
+            k_spmv_t<TV, TE, 32><<<g, 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, W0, W1, V);
+          } else {
+            const dim3 g((unsigned)ceil_div(N * 16, 256), (unsigned)ceil_div(R, 16));
+            k_spmv_t<TV, TE, 16><<<g, 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, W0, W1, V);
+          }
+        } else if (multi)
           k_spmv<TV, TE, kRB><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
         else
           k_spmv<TV, TE, 1><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
@@ -933,7 +1018,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       const int n = std::min(steps - s0, kChunkSteps);
       if (use_graph && n == kChunkSteps) {
         SWM_CK(cudaGraphLaunch(ctx->gm_exec, st));
-        ctx->launches += 3 * kChunkSteps;
+        ctx->launches += (split ? (ws->Xt ? 5 : 4) : 3) * kChunkSteps;
       } else {
         SWM_TRY(launch_steps(st, n));
       }

@@ -225,11 +225,16 @@ def test_invalid_inputs_rejected():
 
 def test_split_step_path_matches_oracle(monkeypatch):
     """The large-system form of the GMRES step (streaming product + separate dots), forced on a
-    small system, against the oracle's LU solution, for one and for several incidences."""
+    small system, against the oracle's LU solution, for one and for several incidences (with 12 or
+    more, the product reads the vectors incidence-minor, one lane per incidence)."""
     monkeypatch.setenv("SWM_SPLIT_ROWS", "0")
     cl = cloud_uniform_cube(80, 5.0, seed=43)
     obs = observations_phi_cut(60)
-    for inc in (np.array([[0.2, 0.1, 0.0]]), np.array([[0.0, 0.0, 0.0], [1.1, 0.7, 0.5], [2.5, 4.0, 1.2]] * 3)):
+    g = np.random.default_rng(7)
+    many = lambda n: np.stack([g.uniform(0, np.pi, n), g.uniform(0, 2 * np.pi, n), g.uniform(0, np.pi, n)], 1)
+    # 1 incidence; 9 (blocks of 8 share E); 13 and 30 (incidence-minor product, 16 and 32 lanes)
+    for inc in (np.array([[0.2, 0.1, 0.0]]), np.array([[0.0, 0.0, 0.0], [1.1, 0.7, 0.5], [2.5, 4.0, 1.2]] * 3),
+                many(13), many(30)):
         for prec, tol in ((C128, 1e-5), (C64, 1e-3)):
             out = run_gpu(cl, K, 1.5, prec, inc, obs=obs, tol=1e-11 if prec == C128 else 1e-6)
             X = O.solve_lu(O.assemble(cl, K, 1.5, sparse=False), O.rhs(cl, K, inc))
@@ -245,7 +250,11 @@ def test_per_kernel_step_path_matches_oracle(monkeypatch):
     monkeypatch.setenv("SWM_PERSIST", "0")
     cl = cloud_uniform_cube(80, 5.0, seed=44)
     obs = observations_phi_cut(60)
-    for inc in (np.array([[0.2, 0.1, 0.0]]), np.array([[0.0, 0.0, 0.0], [1.1, 0.7, 0.5], [2.5, 4.0, 1.2]] * 3)):
+    g = np.random.default_rng(7)
+    many = lambda n: np.stack([g.uniform(0, np.pi, n), g.uniform(0, 2 * np.pi, n), g.uniform(0, np.pi, n)], 1)
+    # 1 incidence; 9 (blocks of 8 share E); 13 and 30 (incidence-minor product, 16 and 32 lanes)
+    for inc in (np.array([[0.2, 0.1, 0.0]]), np.array([[0.0, 0.0, 0.0], [1.1, 0.7, 0.5], [2.5, 4.0, 1.2]] * 3),
+                many(13), many(30)):
         for prec, tol in ((C128, 1e-5), (C64, 1e-3)):
             out = run_gpu(cl, K, 1.5, prec, inc, obs=obs, tol=1e-11 if prec == C128 else 1e-6)
             X = O.solve_lu(O.assemble(cl, K, 1.5, sparse=False), O.rhs(cl, K, inc))
