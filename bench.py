@@ -431,8 +431,8 @@ def run_scale(args):
     fp32_peak = N_SM * 128 * 2 * mhz * 1e6 / 1e12
     fill_ms, _ = res["fill_mutual"]
     fill_tf = st["fill_evals"] * FP32_FLOPS_PER_EVAL / (fill_ms * 1e-3) / 1e12
-    # block-sparse product: E (+ column map, row descriptors) once per block of 8 right-hand sides,
-    # x/V/y rows and the fused first Gram-Schmidt pass per right-hand side
+    # block-sparse product: E (+ column map, row descriptors) once per block of right-hand sides
+    # sharing a read, x/V/y rows and the fused first Gram-Schmidt pass per right-hand side
     esz, N, R = 8, st["n"], n_inc
     it = st["iterations"]
     steps_j = []
@@ -440,9 +440,12 @@ def run_scale(args):
         c = min(restart, it)
         steps_j += list(range(c))
         it -= c
-    nblk = -(-R // 8) if R > 1 else 1
-    mat = (st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N) * nblk
     split = N >= (1 << 19)  # the library's default split of the Arnoldi step
+    # incidences sharing one read of E: one lane each on the large-system path from 12 incidences
+    # (16 or 32 per block), else the block size the library timed for this shape
+    rb = (32 if R >= 24 else 16) if (split and R >= 12) else max(1, st.get("step_rhs_block", 8) or 8)
+    nblk = -(-R // rb) if R > 1 else 1
+    mat = (st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N) * nblk
     # split: the product alone (x read, V and y written); fused: plus the V rows of the first dots
     apply_bytes = sum(mat + R * N * esz * (3 + (0 if split else j + 1)) for j in steps_j)
     apply_ms, apply_n = res["apply"]
@@ -461,7 +464,8 @@ def run_scale(args):
                           "peak": fp32_peak, "unit": "TFLOP/s", "frac": fill_tf / fp32_peak,
                           "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"},
         "apply_roofline": {"bound": "hbm",
-                           "kernel": "k_spmv (block-sparse product)" if split else
+                           "kernel": ("k_rhs_minor + k_spmv_t (block-sparse product, one lane per incidence)"
+                                      if R >= 12 else "k_spmv (block-sparse product)") if split else
                            "k_step (block-sparse product + first Gram-Schmidt pass)",
                            "launches": apply_n, "ms": apply_ms, "bytes": apply_bytes, "achieved": gbs,
                            "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",

@@ -358,44 +358,61 @@ __global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __res
 // Large-N form of the step with many right-hand sides, part 1: normalise and multiply by
 // A = I + E with one lane per right-hand side: the RB lanes of a row group read each entry of E
 // once (the same address: one transaction) and the RB values of the gathered column as one
-// contiguous run of Xt.  E is read once per block of RB right-hand sides.
+// contiguous run of Xt.  E is read once per block of RB right-hand sides.  A CTA covers 32 rows;
+// its results go through shared memory so that V_j and w are written right-hand-side major as
+// runs of 32 consecutive rows.
+constexpr int kTileRows = 32;
 template <typename TV, typename TE, int RB>
 __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restrict__ rinfo,
                                                 const int32_t* __restrict__ colmap, const TE* __restrict__ E,
                                                 const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ W0,
                                                 cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ V) {
   if (P.st->cycle_done) return;
+  __shared__ cplx<TV> xs[kTileRows][RB + 1], ys[kTileRows][RB + 1];
   const int j = P.st->j;
   const int64_t N = P.N;
   const int R = P.R;
-  const int64_t n = (blockIdx.x * (int64_t)256 + threadIdx.x) / RB;
-  const int r = blockIdx.y * RB + (int)(threadIdx.x % RB);
-  if (n >= N || r >= R) return;  // no collective operation below: lanes leave independently
-  cplx<TV>* dst = ((j & 1) ? W0 : W1) + (int64_t)r * N;
-  if (!P.active[r]) {
-    V[((int64_t)j * R + r) * N + n] = mkc<TV>(0, 0);
-    dst[n] = mkc<TV>(0, 0);
-    return;
-  }
-  const TV sc = (TV)P.inv_h[r];
-  const RowInfo ri = rinfo[n];
-  const int32_t* cm = colmap + ri.cmb;
-  cplx<TV> acc = mkc<TV>(0, 0);
-  int c = 0;
-  for (; c + 3 < ri.K; c += 4) {
-    cplx<TV> e[4], x[4];
+  const int64_t n0 = (int64_t)blockIdx.x * kTileRows;
+  const int lr = (int)(threadIdx.x % RB);          // right-hand side within the block
+  const int r = blockIdx.y * RB + lr;
+  const bool on = r < R && P.active[r];
+  const TV sc = r < R ? (TV)P.inv_h[r] : TV(0);
+  constexpr int kGroups = 256 / RB;                 // rows per pass
+  for (int t = (int)(threadIdx.x / RB); t < kTileRows; t += kGroups) {
+    const int64_t n = n0 + t;
+    cplx<TV> x = mkc<TV>(0, 0), y = mkc<TV>(0, 0);
+    if (n < N && on) {
+      const RowInfo ri = rinfo[n];
+      const int32_t* cm = colmap + ri.cmb;
+      cplx<TV> acc = mkc<TV>(0, 0);
+      int c = 0;
+      for (; c + 3 < ri.K; c += 4) {
+        cplx<TV> e[4], xv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      e[u] = ELoad<TV, TE>::ld(E + ri.vb + c + u);
-      x[u] = Xt[(int64_t)cm[c + u] * R + r];
+        for (int u = 0; u < 4; ++u) {
+          e[u] = ELoad<TV, TE>::ld(E + ri.vb + c + u);
+          xv[u] = Xt[(int64_t)cm[c + u] * R + r];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cfma(acc, e[u], xv[u]);
+      }
+      for (; c < ri.K; ++c) cfma(acc, ELoad<TV, TE>::ld(E + ri.vb + c), Xt[(int64_t)cm[c] * R + r]);
+      x = sc * Xt[n * R + r];
+      y = x + sc * acc;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) cfma(acc, e[u], x[u]);
+    xs[t][lr] = x;
+    ys[t][lr] = y;
   }
-  for (; c < ri.K; ++c) cfma(acc, ELoad<TV, TE>::ld(E + ri.vb + c), Xt[(int64_t)cm[c] * R + r]);
-  const cplx<TV> x = sc * Xt[n * R + r];
-  V[((int64_t)j * R + r) * N + n] = x;
-  dst[n] = x + sc * acc;
+  __syncthreads();
+  // write: warp w takes right-hand sides w, w + 8, ...; its lanes take the 32 rows
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t n = n0 + lane;
+  for (int b = w; b < RB; b += 8) {
+    const int rr = blockIdx.y * RB + b;
+    if (rr >= R || n >= N) continue;
+    V[((int64_t)j * R + rr) * N + n] = xs[lane][b];
+    ((j & 1) ? W0 : W1)[(int64_t)rr * N + n] = ys[lane][b];
+  }
 }
 
 // Large-N form of the step, part 2: h = V^H w over chunks of rows (first Gram-Schmidt pass).
@@ -879,13 +896,13 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
           const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
           k_rhs_minor<TV><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, W0, W1, ws->Xt);
           SWM_LAUNCHED();
-          if (R >= 24) {
-            const dim3 g((unsigned)ceil_div(N * 32, 256), (unsigned)ceil_div(R, 32));
-            k_spmv_t<TV, TE, 32><<<g, 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, W0, W1, V);
-          } else {
-            const dim3 g((unsigned)ceil_div(N * 16, 256), (unsigned)ceil_div(R, 16));
-            k_spmv_t<TV, TE, 16><<<g, 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, W0, W1, V);
-          }
+          const unsigned gx = (unsigned)ceil_div(N, kTileRows);
+          if (R >= 24)
+            k_spmv_t<TV, TE, 32><<<dim3(gx, (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E,
+                                                                                   ws->Xt, W0, W1, V);
+          else
+            k_spmv_t<TV, TE, 16><<<dim3(gx, (unsigned)ceil_div(R, 16)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E,
+                                                                                   ws->Xt, W0, W1, V);
         } else if (multi)
           k_spmv<TV, TE, kRB><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
         else
