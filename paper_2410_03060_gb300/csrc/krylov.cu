@@ -4,16 +4,21 @@
 //
 // The operator is A = Z M^-1 = I + E (E stored, see precond.cu); GMRES finds y with A y = b and
 // the currents are x = M^-1 y.  Several right-hand sides (incidences) run as independent GMRES
-// instances that share every pass over E.  One Arnoldi step is three kernels, each over chunks of
-// rows:
-//   k_step   : v_j = w / |w| (row owners), w' = A v_j, h = V^H w'  (classical Gram-Schmidt, pass 1)
-//   k_update : w' -= V h, h2 = V^H w'                              (pass 2)
-//   k_finish : w' -= V h2, |w'|, Hessenberg column, Givens rotation, residual estimate
-// Reductions end in the last CTA to arrive (no spin-waits).  Every kernel reads the step index
-// and the activity flags from device memory, so the host issues identical launches every step;
-// it keeps one chunk of steps queued ahead of the convergence flag it is reading, so the GPU
-// does not wait for the host inside a restart cycle.  Vectors are stored right-hand-side major:
-// V[j][r][n].  Dot products, norms, the Hessenberg matrix and the rotations are float64.
+// instances that share every pass over E.  The basis is orthogonalised by classical Gram-Schmidt
+// with one reorthogonalisation, the reorthogonalisation delayed by one step so that a step reads
+// the basis twice instead of four times: with Q = q_0..q_{j-1} final and u_j the pending vector
+// (one Gram-Schmidt pass done, not yet normalised), step j is
+//   product  : w = A u_j
+//   k_dots   : s = Q^H u_j, t = Q^H w, |u_j|^2, u_j^H w; the last CTA completes Hessenberg column
+//              j-1 (subdiagonal rho = |u_j - Q s|), its Givens rotation and residual estimate, and
+//              the first-pass coefficients of column j from these inner products
+//   k_update : q_j = (u_j - Q s) / rho, u_{j+1} = (w - Q t) / rho - (q_j^H w / rho) q_j
+// and a closing dots pass without product completes the last column of the cycle.  Reductions end
+// in the last CTA to arrive (no spin-waits).  Every kernel reads the step index and the activity
+// flags from device memory, so the host issues identical launches every step; it keeps one chunk
+// of steps queued ahead of the convergence flag it is reading, so the GPU does not wait for the
+// host inside a restart cycle.  Vectors are stored right-hand-side major: V[j][r][n].  Dot
+// products, norms, the Hessenberg matrix and the rotations are float64.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -31,33 +36,28 @@ constexpr int kRows = 256;  // CTA width of the vector kernels
 constexpr int kMinorR = 12;  // right-hand sides from which the large-system product reads them
                              // right-hand-side minor (one lane each)
 constexpr int kG = 8;       // lanes per scalar row in the block-sparse product
+constexpr int kMaxChunk = 2048;  // rows per CTA of the Gram-Schmidt kernels, at most
 
 template <typename T>
 __device__ __forceinline__ bool finite_c(cplx<T> z) {
   return isfinite((double)z.re) && isfinite((double)z.im);
 }
 
-// mode 0 (Arnoldi): x = W_src * inv_h; V[j] = x (row owners); W_dst = x + E x.
-// mode 1 (residual): W_dst = B - (Y + E Y).
+// Residual of the current y, the first vector of a cycle: U = B - (Y + E Y).
 template <typename TV, typename TE>
-__global__ void __launch_bounds__(kRows) k_apply(int mode, KPtr P, const int32_t* __restrict__ rowwire,
-                                                 const int64_t* __restrict__ off, Layout lay,
-                                                 const TE* __restrict__ E, const cplx<TV>* __restrict__ B,
-                                                 cplx<TV>* __restrict__ Y, cplx<TV>* __restrict__ W0,
-                                                 cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ V) {
-  if (mode == 0 && P.st->cycle_done) return;
+__global__ void __launch_bounds__(kRows) k_residual(KPtr P, const int32_t* __restrict__ rowwire,
+                                                    const int64_t* __restrict__ off, Layout lay,
+                                                    const TE* __restrict__ E, const cplx<TV>* __restrict__ B,
+                                                    const cplx<TV>* __restrict__ Y, cplx<TV>* __restrict__ U) {
   const int64_t n = (blockIdx.x * (int64_t)kRows + threadIdx.x) / kG;
   const int sub = threadIdx.x % kG;
   const int r = blockIdx.y;
   const int64_t N = P.N;
   const bool row_ok = n < N;
-  const int j = mode == 0 ? P.st->j : 0;
-  const cplx<TV>* src = mode == 0 ? ((j & 1) ? W1 : W0) + (int64_t)r * N : Y + (int64_t)r * N;
-  cplx<TV>* dst = (mode == 0 ? ((j & 1) ? W0 : W1) : W0) + (int64_t)r * N;
+  const cplx<TV>* src = Y + (int64_t)r * N;
   cplx<TV> acc = mkc<TV>(0, 0);
-  int64_t p = 0;
   if (row_ok) {
-    p = rowwire[n];
+    const int64_t p = rowwire[n];
     const int i = (int)(n - off[p]);
     const int K = lay.K[p];
     const int64_t vb = lay.rowbase[p] + (int64_t)i * K;
@@ -70,50 +70,10 @@ __global__ void __launch_bounds__(kRows) k_apply(int mode, KPtr P, const int32_t
     acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
   }
   if (!row_ok || sub != 0) return;
-  if (mode == 0) {
-    const bool act = P.active[r];
-    const TV s = (TV)P.inv_h[r];
-    const cplx<TV> x = act ? s * src[n] : mkc<TV>(0, 0);
-    V[((int64_t)j * P.R + r) * N + n] = x;
-    dst[n] = act ? x + s * acc : mkc<TV>(0, 0);
-  } else {
-    dst[n] = B[(int64_t)r * N + n] - (src[n] + acc);
-  }
+  U[(int64_t)r * N + n] = B[(int64_t)r * N + n] - (src[n] + acc);
 }
 
-// Partial dots conj(V_i) . w over the CTA's rows for i <= j, one warp per i, float64 results.
-template <typename TV>
-__device__ void cta_dots(const KPtr& P, int j, int r, const cplx<TV>* __restrict__ V, const cplx<TV>* w_sm, int64_t n0,
-                         int cnt, c128* __restrict__ out) {
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int i = wp; i <= j; i += kRows / 32) {
-    const cplx<TV>* vi = V + ((int64_t)i * P.R + r) * P.N + n0;
-    cplx<TV> acc = mkc<TV>(0, 0);
-    int t = lane;
-    for (; t + 224 < cnt; t += 256) {  // eight loads in flight per lane
-      cplx<TV> v[8], w[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        v[u] = vi[t + 32 * u];
-        w[u] = w_sm[t + 32 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        acc.re = fma(v[u].re, w[u].re, fma(v[u].im, w[u].im, acc.re));
-        acc.im = fma(v[u].re, w[u].im, fma(-v[u].im, w[u].re, acc.im));
-      }
-    }
-    for (; t < cnt; t += 32) {
-      const cplx<TV> v = vi[t], w = w_sm[t];
-      acc.re = fma(v.re, w.re, fma(v.im, w.im, acc.re));
-      acc.im = fma(v.re, w.im, fma(-v.im, w.re, acc.im));
-    }
-    const double re = warp_sum((double)acc.re), im = warp_sum((double)acc.im);
-    if (lane == 0) out[i] = mkc(re, im);
-  }
-}
-
-// Last CTA of right-hand side r to arrive sums the partial dots into dst[0..j].
+// Last CTA of right-hand side r to arrive at the end of a pass.
 __device__ bool last_cta(const KPtr& P, int r) {
   __shared__ bool last;
   __threadfence();
@@ -159,133 +119,31 @@ __device__ __forceinline__ double sum_partials_d(const double* __restrict__ base
   return warp_sum((a[0] + a[1]) + (a[2] + a[3]));
 }
 
-__device__ void reduce_dots(const KPtr& P, int j, int r, c128* __restrict__ dst, int nchunk) {
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const c128* part = P.part + (int64_t)r * nchunk * (P.restart + 1);
-  for (int i = wp; i <= j; i += kRows / 32) {
-    const c128 v = sum_partials_c(part + i, P.restart + 1, nchunk, lane);
-    if (lane == 0) dst[(int64_t)r * (P.restart + 1) + i] = v;
-  }
-}
-
-// Normalise, multiply by A = I + E and take the first Gram-Schmidt dots, over one chunk of rows
-// (P.schunk rows, a multiple of 32) and a block of RB right-hand sides that share every read of E.
-// Eight lanes share a scalar row; the 32 row groups of the CTA take the chunk's rows in turn, with
-// their descriptors loaded up front.
-template <typename TV, typename TE, int RB>
-__global__ void __launch_bounds__(kRows) k_step(KPtr P, const RowInfo* __restrict__ rinfo,
-                                                const int32_t* __restrict__ colmap, const TE* __restrict__ E,
-                                                cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
-                                                cplx<TV>* __restrict__ V) {
-  if (P.st->cycle_done) return;
-  const int j = P.st->j, rblk = blockIdx.y;
-  const int r0 = rblk * RB;
-  const int nr = min(RB, P.R - r0);
-  const int64_t N = P.N;
-  const int64_t n0 = (int64_t)blockIdx.x * P.schunk;
-  const int cnt = (int)min((int64_t)P.schunk, N - n0);
-  const cplx<TV>* src = ((j & 1) ? W1 : W0);
-  cplx<TV>* dst = ((j & 1) ? W0 : W1);
-  bool act[RB];
-  TV sc[RB];
-  bool any = false;
-#pragma unroll
-  for (int b = 0; b < RB; ++b) {
-    act[b] = b < nr && P.active[r0 + b];
-    sc[b] = b < nr ? (TV)P.inv_h[r0 + b] : TV(0);
-    any |= act[b];
-  }
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);  // [RB][schunk]
-  const int g = threadIdx.x / kG, sub = threadIdx.x % kG;
-  constexpr int kMaxRowsPerGroup = 4;
-  for (int tb = 0; tb < cnt; tb += 32 * kMaxRowsPerGroup) {  // same trip count in every lane
-  RowInfo ri[kMaxRowsPerGroup];
-#pragma unroll
-  for (int t = 0; t < kMaxRowsPerGroup; ++t) {
-    const int row = tb + g + 32 * t;
-    ri[t] = (row < cnt) ? rinfo[n0 + row] : RowInfo{0, 0, 0};
-  }
-#pragma unroll
-  for (int t = 0; t < kMaxRowsPerGroup; ++t) {
-    const int row = tb + g + 32 * t;
-    if (tb + 32 * t >= cnt) break;  // uniform across the CTA
-    cplx<TV> acc[RB];
-#pragma unroll
-    for (int b = 0; b < RB; ++b) acc[b] = mkc<TV>(0, 0);
-    if (any) {
-      const int32_t* cm = colmap + ri[t].cmb;
-      for (int c = sub; c < ri[t].K; c += kG) {
-        const cplx<TV> e = ELoad<TV, TE>::ld(E + ri[t].vb + c);
-        const int64_t col = cm[c];
-#pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (b < nr) cfma(acc[b], e, src[(int64_t)(r0 + b) * N + col]);
-      }
-    }
-#pragma unroll
-    for (int b = 0; b < RB; ++b) {
-#pragma unroll
-      for (int o = kG / 2; o > 0; o >>= 1) {
-        acc[b].re += __shfl_xor_sync(0xffffffffu, acc[b].re, o);
-        acc[b].im += __shfl_xor_sync(0xffffffffu, acc[b].im, o);
-      }
-    }
-    if (row < cnt && sub == 0) {
-      const int64_t n = n0 + row;
-#pragma unroll
-      for (int b = 0; b < RB; ++b) {
-        if (b >= nr) break;
-        const int64_t off_r = (int64_t)(r0 + b) * N;
-        const cplx<TV> x = act[b] ? sc[b] * src[off_r + n] : mkc<TV>(0, 0);
-        const cplx<TV> y = act[b] ? x + sc[b] * acc[b] : mkc<TV>(0, 0);
-        V[((int64_t)j * P.R + r0 + b) * N + n] = x;
-        dst[off_r + n] = y;
-        w_sm[b * P.schunk + row] = y;
-      }
-    }
-  }
-  }
-  __syncthreads();
-  for (int b = 0; b < nr; ++b)
-    cta_dots<TV>(P, j, r0 + b, V, w_sm + b * P.schunk, n0, cnt,
-                 P.part + ((int64_t)(r0 + b) * P.nschunk + blockIdx.x) * (P.restart + 1));
-  if (last_cta(P, rblk)) {
-    for (int b = 0; b < nr; ++b) reduce_dots(P, j, r0 + b, P.hc, P.nschunk);
-    __syncthreads();
-    if (threadIdx.x == 0) P.counter[rblk] = 0;
-  }
-}
-
-// Large-N form of the step, part 1: normalise and multiply by A = I + E, streaming.  One scalar row
-// per group of eight lanes, no shared memory and no barrier, so many rows' loads are in flight.
+// Product w = u + E u for the active right-hand sides, streaming: one scalar row per group of eight
+// lanes, RB right-hand sides sharing every read of E, no shared memory and no barrier, so many
+// rows' loads are in flight.
 template <typename TV, typename TE, int RB>
 __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restrict__ rinfo,
                                                 const int32_t* __restrict__ colmap, const TE* __restrict__ E,
-                                                cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
-                                                cplx<TV>* __restrict__ V) {
-  if (P.st->cycle_done) return;
-  const int j = P.st->j;
+                                                const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Wv) {
+  if (P.st->cycle_done || P.st->j >= P.st->jmax) return;
   const int r0 = blockIdx.y * RB;
   const int nr = min(RB, P.R - r0);
   const int64_t N = P.N;
   const int64_t n = (blockIdx.x * (int64_t)kRows + threadIdx.x) / kG;
   const int sub = threadIdx.x % kG;
-  const cplx<TV>* src = ((j & 1) ? W1 : W0);
-  cplx<TV>* dst = ((j & 1) ? W0 : W1);
   bool act[RB];
-  TV sc[RB];
   bool any = false;
 #pragma unroll
   for (int b = 0; b < RB; ++b) {
     act[b] = b < nr && P.active[r0 + b];
-    sc[b] = b < nr ? (TV)P.inv_h[r0 + b] : TV(0);
     any |= act[b];
   }
+  if (!any) return;  // the same for the whole CTA
   cplx<TV> acc[RB];
 #pragma unroll
   for (int b = 0; b < RB; ++b) acc[b] = mkc<TV>(0, 0);
-  if (n < N && any) {
+  if (n < N) {
     const RowInfo ri = rinfo[n];
     const int32_t* cm = colmap + ri.cmb;
     int c = sub;
@@ -294,8 +152,8 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
       const int64_t c0 = cm[c], c1 = cm[c + kG];
 #pragma unroll
       for (int b = 0; b < RB; ++b)
-        if (b < nr) {
-          const cplx<TV>* x = src + (int64_t)(r0 + b) * N;
+        if (act[b]) {
+          const cplx<TV>* x = U + (int64_t)(r0 + b) * N;
           const cplx<TV> x0 = x[c0], x1 = x[c1];
           cfma(acc[b], e0, x0);
           cfma(acc[b], e1, x1);
@@ -306,7 +164,7 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
       const int64_t c0 = cm[c];
 #pragma unroll
       for (int b = 0; b < RB; ++b)
-        if (b < nr) cfma(acc[b], e0, src[(int64_t)(r0 + b) * N + c0]);
+        if (act[b]) cfma(acc[b], e0, U[(int64_t)(r0 + b) * N + c0]);
     }
   }
 #pragma unroll
@@ -321,23 +179,19 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
       if (b >= nr) break;
-      const int64_t off_r = (int64_t)(r0 + b) * N;
-      const cplx<TV> x = act[b] ? sc[b] * src[off_r + n] : mkc<TV>(0, 0);
-      V[((int64_t)j * P.R + r0 + b) * N + n] = x;
-      dst[off_r + n] = act[b] ? x + sc[b] * acc[b] : mkc<TV>(0, 0);
+      const int64_t o = (int64_t)(r0 + b) * N + n;
+      if (act[b]) Wv[o] = U[o] + acc[b];
     }
   }
 }
 
-// Large-N form of the step with many right-hand sides, part 0: the current Krylov vectors
-// (right-hand-side major, [R][N]) copied to right-hand-side minor order Xt[N][R], through
-// shared-memory tiles of 32 rows x 32 right-hand sides, so that the product below reads the values
-// of all right-hand sides at a column as one contiguous run.
+// Product with many right-hand sides, part 0: the pending vectors U (right-hand-side major,
+// [R][N]) copied to right-hand-side minor order Xt[N][R] through shared-memory tiles of 32 rows x
+// 32 right-hand sides, so that the product below reads the values of all right-hand sides at a
+// column as one contiguous run.
 template <typename TV>
-__global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __restrict__ W0,
-                                                   const cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ Xt) {
-  if (P.st->cycle_done) return;
-  const cplx<TV>* src = (P.st->j & 1) ? W1 : W0;
+__global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Xt) {
+  if (P.st->cycle_done || P.st->j >= P.st->jmax) return;
   __shared__ cplx<TV> tile[32][33];
   const int64_t n0 = (int64_t)blockIdx.x * 32;
   const int r0 = blockIdx.y * 32;
@@ -345,7 +199,7 @@ __global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __res
   for (int k = ty; k < 32; k += 8) {
     const int r = r0 + k;
     const int64_t n = n0 + tx;
-    if (r < P.R && n < P.N) tile[k][tx] = src[(int64_t)r * P.N + n];
+    if (r < P.R && n < P.N) tile[k][tx] = U[(int64_t)r * P.N + n];
   }
   __syncthreads();
   for (int k = ty; k < 32; k += 8) {
@@ -355,32 +209,27 @@ __global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __res
   }
 }
 
-// Large-N form of the step with many right-hand sides, part 1: normalise and multiply by
-// A = I + E with one lane per right-hand side: the RB lanes of a row group read each entry of E
-// once (the same address: one transaction) and the RB values of the gathered column as one
-// contiguous run of Xt.  E is read once per block of RB right-hand sides.  A CTA covers 32 rows;
-// its results go through shared memory so that V_j and w are written right-hand-side major as
-// runs of 32 consecutive rows.
+// Product with many right-hand sides, part 1: w = u + E u with one lane per right-hand side: the RB
+// lanes of a row group read each entry of E once (the same address: one transaction) and the RB
+// values of the gathered column as one contiguous run of Xt.  A CTA covers 32 rows; its results go
+// through shared memory so that w is written right-hand-side major as runs of 32 consecutive rows.
 constexpr int kTileRows = 32;
 template <typename TV, typename TE, int RB>
 __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restrict__ rinfo,
                                                 const int32_t* __restrict__ colmap, const TE* __restrict__ E,
-                                                const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ W0,
-                                                cplx<TV>* __restrict__ W1, cplx<TV>* __restrict__ V) {
-  if (P.st->cycle_done) return;
-  __shared__ cplx<TV> xs[kTileRows][RB + 1], ys[kTileRows][RB + 1];
-  const int j = P.st->j;
+                                                const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ Wv) {
+  if (P.st->cycle_done || P.st->j >= P.st->jmax) return;
+  __shared__ cplx<TV> ys[kTileRows][RB + 1];
   const int64_t N = P.N;
   const int R = P.R;
   const int64_t n0 = (int64_t)blockIdx.x * kTileRows;
-  const int lr = (int)(threadIdx.x % RB);          // right-hand side within the block
+  const int lr = (int)(threadIdx.x % RB);  // right-hand side within the block
   const int r = blockIdx.y * RB + lr;
   const bool on = r < R && P.active[r];
-  const TV sc = r < R ? (TV)P.inv_h[r] : TV(0);
-  constexpr int kGroups = 256 / RB;                 // rows per pass
+  constexpr int kGroups = 256 / RB;  // rows per pass
   for (int t = (int)(threadIdx.x / RB); t < kTileRows; t += kGroups) {
     const int64_t n = n0 + t;
-    cplx<TV> x = mkc<TV>(0, 0), y = mkc<TV>(0, 0);
+    cplx<TV> y = mkc<TV>(0, 0);
     if (n < N && on) {
       const RowInfo ri = rinfo[n];
       const int32_t* cm = colmap + ri.cmb;
@@ -397,10 +246,8 @@ __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restric
         for (int u = 0; u < 4; ++u) cfma(acc, e[u], xv[u]);
       }
       for (; c < ri.K; ++c) cfma(acc, ELoad<TV, TE>::ld(E + ri.vb + c), Xt[(int64_t)cm[c] * R + r]);
-      x = sc * Xt[n * R + r];
-      y = x + sc * acc;
+      y = Xt[n * R + r] + acc;
     }
-    xs[t][lr] = x;
     ys[t][lr] = y;
   }
   __syncthreads();
@@ -409,197 +256,298 @@ __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restric
   const int64_t n = n0 + lane;
   for (int b = w; b < RB; b += 8) {
     const int rr = blockIdx.y * RB + b;
-    if (rr >= R || n >= N) continue;
-    V[((int64_t)j * R + rr) * N + n] = xs[lane][b];
-    ((j & 1) ? W0 : W1)[(int64_t)rr * N + n] = ys[lane][b];
+    if (rr >= R || n >= N || !P.active[rr]) continue;
+    Wv[(int64_t)rr * N + n] = ys[lane][b];
   }
 }
 
-// Large-N form of the step, part 2: h = V^H w over chunks of rows (first Gram-Schmidt pass).
-template <typename TV>
-__global__ void __launch_bounds__(kRows) k_dots_big(KPtr P, cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
-                                                    const cplx<TV>* __restrict__ V) {
-  if (P.st->cycle_done) return;
-  const int j = P.st->j, r = blockIdx.y;
-  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
-  const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
-  const cplx<TV>* w = ((j & 1) ? W0 : W1) + (int64_t)r * P.N + n0;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
-  for (int t = threadIdx.x; t < cnt; t += kRows) w_sm[t] = w[t];
-  __syncthreads();
-  cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nchunk + blockIdx.x) * (P.restart + 1));
-  if (last_cta(P, r)) {
-    reduce_dots(P, j, r, P.hc, P.nchunk);
-    if (threadIdx.x == 0) P.counter[r] = 0;
+// Arrival of one right-hand side at the end of the dots pass of step j; the last one advances the
+// step (and counts the Hessenberg column it completed) and ends the cycle when nothing is active
+// or the closing pass is done.
+__device__ void step_arrive(const KPtr& P, int j, bool closing) {
+  __threadfence();
+  const unsigned done = atomicAdd(&P.counter[P.R], 1u);
+  if (done == (unsigned)P.R - 1) {
+    P.counter[P.R] = 0;
+    int any = 0;
+    for (int q = 0; q < P.R; ++q) any |= __ldcg(P.active + q);
+    P.st->j = j + 1;
+    if (j >= 1) P.st->iters += 1;
+    if (!any || closing) P.st->cycle_done = 1;
   }
 }
 
-// w -= sum_i V_i h_i over the CTA's rows; result kept in shared memory and written back.
+// Last CTA of right-hand side r after the dots of step j (sums s_i = q_i^H u, t_i = q_i^H w for
+// i < j, alpha = |u|^2 and beta = u^H w in sv/tv[j]): completes Hessenberg column j-1 (first-pass
+// coefficients + reorthogonalisation s, subdiagonal rho = |u - Q s|), applies its Givens rotations
+// and the residual test, and, unless this is the closing pass or r stopped, forms the first-pass
+// coefficients of column j and the coefficients of the update pass.
 template <typename TV>
-__device__ void cta_update(const KPtr& P, int j, int r, const cplx<TV>* __restrict__ V, const c128* __restrict__ h,
-                           cplx<TV>* __restrict__ w, cplx<TV>* w_sm, int64_t n0, int cnt) {
-  __shared__ cplx<TV> hs[SWM_MAX_RESTART + 1];
-  for (int i = threadIdx.x; i <= j; i += kRows) hs[i] = ccast<TV>(h[(int64_t)r * (P.restart + 1) + i]);
-  __syncthreads();
-  for (int t = threadIdx.x; t < cnt; t += kRows) {
-    cplx<TV> x = w[t];
-#pragma unroll 4
-    for (int i = 0; i <= j; ++i) {
-      const cplx<TV> v = V[((int64_t)i * P.R + r) * P.N + n0 + t];
-      const cplx<TV> hh = hs[i];
-      x.re = fma(-v.re, hh.re, fma(v.im, hh.im, x.re));
-      x.im = fma(-v.re, hh.im, fma(-v.im, hh.re, x.im));
-    }
-    w[t] = x;
-    w_sm[t] = x;
-  }
-  __syncthreads();
-}
-
-template <typename TV>
-__global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
-                                                  const cplx<TV>* __restrict__ V) {
-  if (P.st->cycle_done) return;
-  const int j = P.st->j, r = blockIdx.y;
-  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
-  const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
-  cplx<TV>* w = ((j & 1) ? W0 : W1) + (int64_t)r * P.N + n0;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
-  cta_update<TV>(P, j, r, V, P.hc, w, w_sm, n0, cnt);
-  cta_dots<TV>(P, j, r, V, w_sm, n0, cnt, P.part + ((int64_t)r * P.nchunk + blockIdx.x) * (P.restart + 1));
-  if (last_cta(P, r)) {
-    reduce_dots(P, j, r, P.hc2, P.nchunk);
-    if (threadIdx.x == 0) P.counter[r] = 0;
-  }
-}
-
-// Second update, norm, and (last CTA) the Hessenberg column, Givens rotation and residual.
-template <typename TV>
-__global__ void __launch_bounds__(kRows) k_finish(KPtr P, cplx<TV>* __restrict__ W0, cplx<TV>* __restrict__ W1,
-                                                  const cplx<TV>* __restrict__ V) {
-  if (P.st->cycle_done) return;
-  const int j = P.st->j, r = blockIdx.y;
-  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
-  const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
-  cplx<TV>* w = ((j & 1) ? W0 : W1) + (int64_t)r * P.N + n0;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<TV>* w_sm = reinterpret_cast<cplx<TV>*>(sm_raw);
-  cta_update<TV>(P, j, r, V, P.hc2, w, w_sm, n0, cnt);
-  double s = 0.0;
-  {
-    TV a = 0;
-    for (int t = threadIdx.x; t < cnt; t += kRows) a += w_sm[t].re * w_sm[t].re + w_sm[t].im * w_sm[t].im;
-    s = (double)a;
-  }
-  __shared__ double red[kRows / 32];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int i = 0; i < kRows / 32; ++i) t += red[i];
-    P.partn[(int64_t)r * P.nchunk + blockIdx.x] = t;
-  }
-  if (!last_cta(P, r)) return;
-  // ---- last CTA of right-hand side r: the Hessenberg column, its rotations and the residual
-  // estimate are worked in shared memory (loaded and stored by all threads) so the one thread
-  // that applies the rotations in order never waits on global memory.
-  __shared__ double nrm2;
-  __shared__ c128 col[SWM_MAX_RESTART + 1];
+__device__ void dots_tail(const KPtr& P, int j, int r, bool closing) {
+  const int R1 = P.restart + 1, RS = P.restart;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  __shared__ c128 sv[SWM_MAX_RESTART + 1], tv[SWM_MAX_RESTART + 1], col[SWM_MAX_RESTART + 1];
   __shared__ double scs[SWM_MAX_RESTART];
   __shared__ c128 ssn[SWM_MAX_RESTART];
-  __shared__ int act_r;
-  __shared__ c128 g_j;
-  __shared__ double bnorm_r;
-  const int R1 = P.restart + 1;
-  c128* Hr = P.H + (int64_t)r * R1 * P.restart;  // H[i][j] at i * restart + j
-  if (threadIdx.x < 32) {
-    const double t = sum_partials_d(P.partn + (int64_t)r * P.nchunk, P.nchunk, threadIdx.x);
-    if (threadIdx.x == 0) {
-      nrm2 = t;
-      act_r = P.active[r];
-      g_j = P.g[(int64_t)r * R1 + j];
-      bnorm_r = P.bnorm[r];
+  __shared__ double rho_s;
+  __shared__ int go_on;
+  const c128* part = P.part + (int64_t)r * 2 * R1 * P.nchunk;
+  for (int i = wp; i < 2 * (j + 1); i += kRows / 32) {
+    if (closing && (i & 1)) continue;
+    const c128 v = sum_partials_c(part + (int64_t)i * P.nchunk, 1, P.nchunk, lane);
+    if (lane == 0) {
+      if (i & 1)
+        tv[i >> 1] = v;
+      else
+        sv[i >> 1] = v;
     }
   }
-  for (int i = threadIdx.x; i <= j; i += kRows)
-    col[i] = P.hc[(int64_t)r * R1 + i] + P.hc2[(int64_t)r * R1 + i];
-  for (int i = threadIdx.x; i < j; i += kRows) {
-    scs[i] = P.cs[(int64_t)r * P.restart + i];
-    ssn[i] = P.sn[(int64_t)r * P.restart + i];
+  for (int i = threadIdx.x; i < j; i += kRows) col[i] = P.hc[(int64_t)r * R1 + i];
+  for (int i = threadIdx.x; i + 1 < j; i += kRows) {
+    scs[i] = P.cs[(int64_t)r * RS + i];
+    ssn[i] = P.sn[(int64_t)r * RS + i];
   }
   __syncthreads();
+  if (wp == 0) {
+    double ss = 0.0;
+    for (int i = lane; i < j; i += 32) ss += sv[i].re * sv[i].re + sv[i].im * sv[i].im;
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      const double a = sv[j].re - ss;  // |u - Q s|^2 = |u|^2 - |s|^2 (Q orthonormal)
+      rho_s = !isfinite(a) ? a : (a > 0.0 ? sqrt(a) : 0.0);
+      P.counter[r] = 0;
+    }
+  }
+  __syncthreads();
+  const double rho = rho_s;
+  c128* Hraw = P.Hraw + (int64_t)r * R1 * RS;  // unrotated Hessenberg, [i][l] at i * restart + l
+  if (j >= 1)
+    for (int i = threadIdx.x; i <= j; i += kRows) {
+      const c128 v = i < j ? col[i] + sv[i] : mkc(rho, 0.0);
+      col[i] = v;
+      Hraw[i * RS + j - 1] = v;
+    }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    P.counter[r] = 0;
-    if (act_r) {
-      const double hn = sqrt(nrm2);
-      // previous rotations
-      for (int i = 0; i < j; ++i) {
+    int act = 1;
+    if (j >= 1) {
+      const int l = j - 1;  // the column being completed
+      for (int i = 0; i < l; ++i) {  // previous rotations
         const c128 a = col[i], b = col[i + 1];
         const c128 sc = ssn[i];
         col[i] = scs[i] * a + sc * b;
         col[i + 1] = mkc(-sc.re, sc.im) * a + scs[i] * b;  // -conj(s) a + c b
       }
-      // new rotation zeroing the subdiagonal hn (real, >= 0)
-      const c128 a = col[j];
+      // new rotation zeroing the subdiagonal rho (real, >= 0)
+      const c128 a = col[l];
       const double aa = sqrt(a.re * a.re + a.im * a.im);
-      const double nu = sqrt(aa * aa + hn * hn);
+      const double nu = sqrt(aa * aa + rho * rho);
       double c;
-      c128 sv;
+      c128 sg;
       if (aa == 0.0) {
         c = 0.0;
-        sv = mkc(1.0, 0.0);
+        sg = mkc(1.0, 0.0);
       } else {
         c = aa / nu;
-        sv = mkc(a.re / aa * hn / nu, a.im / aa * hn / nu);
+        sg = mkc(a.re / aa * rho / nu, a.im / aa * rho / nu);
       }
-      P.cs[(int64_t)r * P.restart + j] = c;
-      P.sn[(int64_t)r * P.restart + j] = sv;
-      col[j] = c * a + hn * sv;
+      P.cs[(int64_t)r * RS + l] = c;
+      P.sn[(int64_t)r * RS + l] = sg;
+      col[l] = c * a + rho * sg;
       c128* g = P.g + (int64_t)r * R1;
-      const c128 gj = g_j;
-      const c128 gn = mkc(-sv.re, sv.im) * gj;
-      g[j + 1] = gn;
-      g[j] = c * gj;
-      const double res = sqrt(gn.re * gn.re + gn.im * gn.im) / bnorm_r;
+      const c128 gl = g[l];
+      const c128 gn = mkc(-sg.re, sg.im) * gl;
+      g[l + 1] = gn;
+      g[l] = c * gl;
+      const double res = sqrt(gn.re * gn.re + gn.im * gn.im) / P.bnorm[r];
       P.resid[r] = res;
-      P.jlast[r] = j + 1;
-      if (!isfinite(hn) || !isfinite(res)) {
+      P.jlast[r] = j;
+      if (!isfinite(rho) || !isfinite(res)) {
         P.st->numeric = 1;
-        P.active[r] = 0;
-      } else if (res <= P.tol || hn == 0.0) {
-        P.active[r] = 0;
+        act = 0;
+      } else if (res <= P.tol || rho == 0.0) {
+        act = 0;
       }
-      P.inv_h[r] = hn > 0.0 ? 1.0 / hn : 0.0;
+    } else {
+      P.g[(int64_t)r * R1] = mkc(rho, 0.0);
+      if (!isfinite(rho)) P.st->numeric = 1;
+      if (!(rho > 0.0) || !isfinite(rho)) act = 0;
+    }
+    P.active[r] = act;
+    go_on = act && !closing;
+  }
+  __syncthreads();
+  c128* Hr = P.H + (int64_t)r * R1 * RS;
+  if (j >= 1)
+    for (int i = threadIdx.x; i < j; i += kRows) Hr[i * RS + j - 1] = col[i];
+  if (go_on) {
+    // A q_j = (w - A Q s) / rho and A Q s = Q (Hraw s) + q_j rho s_{j-1}; with Q orthonormal the
+    // first-pass coefficients of column j are (t - Hraw s) / rho and q_j^H w / rho - s_{j-1}, where
+    // q_j^H w = (beta - s^H t) / rho.
+    const double ir = 1.0 / rho;
+    for (int k = threadIdx.x; k < j; k += kRows) {
+      c128 c = mkc(0.0, 0.0);
+      for (int i = k > 0 ? k - 1 : 0; i < j; ++i) cfma(c, Hraw[k * RS + i], sv[i]);
+      P.hc[(int64_t)r * R1 + k] = ir * (tv[k] - c);
+      P.hc2[(int64_t)r * R1 + k] = sv[k];
+      P.ht[(int64_t)r * R1 + k] = tv[k];
+    }
+    if (wp == 0) {
+      double re = 0.0, im = 0.0;
+      for (int i = lane; i < j; i += 32) {
+        const c128 p = cmulc(sv[i], tv[i]);
+        re += p.re;
+        im += p.im;
+      }
+      re = warp_sum(re);
+      im = warp_sum(im);
+      if (lane == 0) {
+        const c128 gam = (ir * ir) * (tv[j] - mkc(re, im));  // q_j^H w / rho
+        P.gam[r] = gam;
+        P.hc[(int64_t)r * R1 + j] = j >= 1 ? gam - sv[j - 1] : gam;
+        P.inv_h[r] = ir;
+      }
     }
   }
   __syncthreads();
-  if (act_r)
-    for (int i = threadIdx.x; i <= j; i += kRows) Hr[i * P.restart + j] = col[i];
-  if (threadIdx.x == 0) {
-    // the CTA that finishes the last right-hand side advances the step
-    __threadfence();
-    const unsigned done = atomicAdd(&P.counter[P.R], 1u);
-    if (done == (unsigned)P.R - 1) {
-      P.counter[P.R] = 0;
-      int any = 0;
-      for (int q = 0; q < P.R; ++q) any |= __ldcg(P.active + q);
-      P.st->j = j + 1;
-      P.st->iters += 1;
-      if (!any || j + 1 >= P.restart) P.st->cycle_done = 1;
+  if (threadIdx.x == 0) step_arrive(P, j, closing);
+}
+
+// Dots of step j, one CTA per chunk of rows and right-hand side: for i < j the pairs
+// (q_i^H u, q_i^H w), and (|u|^2, u^H w), where u is the pending vector and w = A u; the closing
+// pass of a cycle (j = jmax, no product) takes only the first of each pair.  The chunk's rows of u
+// and w are staged in shared memory; the warps take (i, row slice) items, q_j standing for u itself,
+// with the rows split into S slices while j + 1 < 8 so that every warp streams, and eight loads in
+// flight per lane.  Slice sums are added in a fixed order (results do not depend on timing).
+template <typename TV>
+__global__ void __launch_bounds__(kRows) k_dots(KPtr P, const cplx<TV>* __restrict__ U,
+                                                const cplx<TV>* __restrict__ Wv, const cplx<TV>* __restrict__ V) {
+  if (P.st->cycle_done) return;
+  const int j = P.st->j, r = blockIdx.y;
+  const bool closing = j >= P.st->jmax;
+  if (!P.active[r]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) step_arrive(P, j, closing);
+    return;
+  }
+  const int R1 = P.restart + 1;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
+  const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<TV>* u_sm = reinterpret_cast<cplx<TV>*>(sm_raw);  // [chunk]
+  cplx<TV>* w_sm = u_sm + P.chunk;                       // [chunk]
+  __shared__ c128 slot[2 * (SWM_MAX_RESTART + 1)];
+  const cplx<TV>* u = U + (int64_t)r * P.N + n0;
+  const cplx<TV>* w = Wv + (int64_t)r * P.N + n0;
+  for (int t = threadIdx.x; t < cnt; t += kRows) {
+    u_sm[t] = u[t];
+    if (!closing) w_sm[t] = w[t];
+  }
+  __syncthreads();
+  constexpr int kWarps = kRows / 32;
+  const int S = j + 1 >= kWarps ? 1 : kWarps / (j + 1);  // row slices per i
+  const int len = ((cnt + S - 1) / S + 31) / 32 * 32;
+  for (int item = wp; item < (j + 1) * S; item += kWarps) {
+    const int i = item / S, sl = item % S;
+    const int lo = sl * len, hi = min(cnt, lo + len);
+    const cplx<TV>* vi = i < j ? V + ((int64_t)i * P.R + r) * P.N + n0 : u_sm;
+    cplx<TV> a = mkc<TV>(0, 0), b = mkc<TV>(0, 0);
+    int t = lo + lane;
+    for (; t + 224 < hi; t += 256) {
+      cplx<TV> v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = vi[t + 32 * k];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const cplx<TV> x = u_sm[t + 32 * k];
+        a.re = fma(v[k].re, x.re, fma(v[k].im, x.im, a.re));
+        a.im = fma(v[k].re, x.im, fma(-v[k].im, x.re, a.im));
+        if (!closing) {
+          const cplx<TV> y = w_sm[t + 32 * k];
+          b.re = fma(v[k].re, y.re, fma(v[k].im, y.im, b.re));
+          b.im = fma(v[k].re, y.im, fma(-v[k].im, y.re, b.im));
+        }
+      }
     }
+    for (; t < hi; t += 32) {
+      const cplx<TV> v = vi[t], x = u_sm[t];
+      a.re = fma(v.re, x.re, fma(v.im, x.im, a.re));
+      a.im = fma(v.re, x.im, fma(-v.im, x.re, a.im));
+      if (!closing) {
+        const cplx<TV> y = w_sm[t];
+        b.re = fma(v.re, y.re, fma(v.im, y.im, b.re));
+        b.im = fma(v.re, y.im, fma(-v.im, y.re, b.im));
+      }
+    }
+    const double ar = warp_sum((double)a.re), ai = warp_sum((double)a.im);
+    const double br = warp_sum((double)b.re), bi = warp_sum((double)b.im);
+    if (lane == 0) {
+      slot[2 * item] = mkc(ar, ai);
+      slot[2 * item + 1] = mkc(br, bi);
+    }
+  }
+  __syncthreads();
+  // partials laid out [r][2 i + k][chunk]: the last CTA reads each as one contiguous run
+  c128* part = P.part + (int64_t)r * 2 * R1 * P.nchunk;
+  for (int e = threadIdx.x; e < 2 * (j + 1); e += kRows) {
+    const int i = e >> 1, k = e & 1;
+    c128 v = slot[2 * (i * S) + k];
+    for (int sl = 1; sl < S; ++sl) v = v + slot[2 * (i * S + sl) + k];
+    part[(int64_t)e * P.nchunk + blockIdx.x] = v;
+  }
+  if (!last_cta(P, r)) return;
+  dots_tail<TV>(P, j, r, closing);
+}
+
+// Update of step j (after its dots): q_j = (u - Q s) / rho goes to V_j and the next pending vector
+// u' = (w - Q t) / rho - gamma q_j (the first Gram-Schmidt pass of A q_j) replaces u, in one read of
+// Q_{<j}; one thread per row.
+template <typename TV>
+__global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__ U, const cplx<TV>* __restrict__ Wv,
+                                                  cplx<TV>* __restrict__ V) {
+  if (P.st->cycle_done) return;
+  const int j = P.st->j - 1, r = blockIdx.y;
+  if (!P.active[r]) return;
+  const int R1 = P.restart + 1;
+  __shared__ cplx<TV> ss[SWM_MAX_RESTART], ts[SWM_MAX_RESTART];
+  for (int i = threadIdx.x; i < j; i += kRows) {
+    ss[i] = ccast<TV>(P.hc2[(int64_t)r * R1 + i]);
+    ts[i] = ccast<TV>(P.ht[(int64_t)r * R1 + i]);
+  }
+  const TV ih = (TV)P.inv_h[r];
+  const cplx<TV> gm = ccast<TV>(P.gam[r]);
+  __syncthreads();
+  const int64_t N = P.N;
+  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
+  const int cnt = (int)min((int64_t)P.chunk, N - n0);
+  cplx<TV>* u = U + (int64_t)r * N + n0;
+  const cplx<TV>* w = Wv + (int64_t)r * N + n0;
+  cplx<TV>* vj = V + ((int64_t)j * P.R + r) * N + n0;
+  for (int t = threadIdx.x; t < cnt; t += kRows) {
+    cplx<TV> x = u[t], y = w[t];
+#pragma unroll 4
+    for (int i = 0; i < j; ++i) {
+      const cplx<TV> v = V[((int64_t)i * P.R + r) * N + n0 + t];
+      const cplx<TV> a = ss[i], b = ts[i];
+      x.re = fma(-v.re, a.re, fma(v.im, a.im, x.re));
+      x.im = fma(-v.re, a.im, fma(-v.im, a.re, x.im));
+      y.re = fma(-v.re, b.re, fma(v.im, b.im, y.re));
+      y.im = fma(-v.re, b.im, fma(-v.im, b.re, y.im));
+    }
+    const cplx<TV> q = ih * x;
+    vj[t] = q;
+    u[t] = ih * y - q * gm;
   }
 }
 
-// Start of a cycle: norms of the residuals in W0, initial g, activity.
+// Start of a cycle: norms of the residuals in U, activity, and the number of columns this cycle
+// may take (restart, or what max_iter leaves).
 template <typename TV>
-__global__ void __launch_bounds__(kRows) k_cycle_start(KPtr P, const cplx<TV>* __restrict__ W0, int first) {
+__global__ void __launch_bounds__(kRows) k_cycle_start(KPtr P, const cplx<TV>* __restrict__ U, int first) {
   const int r = blockIdx.y;
   const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
   const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
-  const cplx<TV>* w = W0 + (int64_t)r * P.N + n0;
+  const cplx<TV>* w = U + (int64_t)r * P.N + n0;
   double s = 0.0;
   for (int t = threadIdx.x; t < cnt; t += kRows) s += (double)w[t].re * w[t].re + (double)w[t].im * w[t].im;
   __shared__ double red[kRows / 32];
@@ -628,7 +576,6 @@ __global__ void __launch_bounds__(kRows) k_cycle_start(KPtr P, const cplx<TV>* _
     const bool act = isfinite(res) && res > P.tol;
     if (!isfinite(res)) P.st->numeric = 1;
     P.active[r] = act ? 1 : 0;
-    P.inv_h[r] = beta > 0.0 ? 1.0 / beta : 0.0;
     P.g[(int64_t)r * (P.restart + 1)] = mkc(beta, 0.0);
     __threadfence();
     const unsigned done = atomicAdd(&P.counter[P.R], 1u);
@@ -637,6 +584,7 @@ __global__ void __launch_bounds__(kRows) k_cycle_start(KPtr P, const cplx<TV>* _
       int any = 0;
       for (int q = 0; q < P.R; ++q) any |= __ldcg(P.active + q);
       P.st->j = 0;
+      P.st->jmax = min(P.restart, P.max_iter - P.st->iters);
       P.st->cycle_done = any ? 0 : 1;
       P.st->all_conv = any ? 0 : 1;
     }
@@ -687,21 +635,25 @@ __global__ void __launch_bounds__(kRows) k_backsolve(KPtr P, int smem_tri) {
   for (int i = threadIdx.x; i < RS; i += kRows) y[i] = i < n ? yv[i] : mkc(0.0, 0.0);
 }
 
-// Y += V coef.
+// Y += V coef, in the precision of the vectors (float64 arithmetic issues far slower than float32
+// on this GPU, and the complex64 path stores y in complex64 anyway).
 template <typename TV>
-__global__ void k_update_y(KPtr P, const cplx<TV>* __restrict__ V, cplx<TV>* __restrict__ Y) {
+__global__ void __launch_bounds__(256) k_update_y(KPtr P, const cplx<TV>* __restrict__ V, cplx<TV>* __restrict__ Y) {
   const int r = blockIdx.y;
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= P.N) return;
   const int jl = P.jlast[r];
   if (jl == 0) return;
-  const c128* y = P.coef + (int64_t)r * P.restart;
-  c128 acc = ccast<double>(Y[(int64_t)r * P.N + n]);
-  for (int i = 0; i < jl; ++i) cfma(acc, ccast<double>(V[((int64_t)i * P.R + r) * P.N + n]), y[i]);
-  Y[(int64_t)r * P.N + n] = ccast<TV>(acc);
+  __shared__ cplx<TV> cf[SWM_MAX_RESTART];
+  for (int i = threadIdx.x; i < jl; i += blockDim.x) cf[i] = ccast<TV>(P.coef[(int64_t)r * P.restart + i]);
+  __syncthreads();
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= P.N) return;
+  cplx<TV> acc = mkc<TV>(0, 0);
+#pragma unroll 4
+  for (int i = 0; i < jl; ++i) cfma(acc, V[((int64_t)i * P.R + r) * P.N + n], cf[i]);
+  Y[(int64_t)r * P.N + n] = Y[(int64_t)r * P.N + n] + acc;
 }
 
-// x = M^-1 y, block by block.
+// x = M^-1 y, block by block, in the precision of the vectors.
 template <typename TV>
 __global__ void k_apply_minv(int64_t N, int R, const int32_t* __restrict__ rowwire, const int64_t* __restrict__ off,
                              const int32_t* __restrict__ m, const int64_t* __restrict__ moff,
@@ -714,9 +666,9 @@ __global__ void k_apply_minv(int64_t N, int R, const int32_t* __restrict__ rowwi
   const int i = (int)(n - o), mp = m[p];
   const cplx<TV>* Mi = Minv + moff[p] + (int64_t)i * mp;
   const cplx<TV>* y = Y + (int64_t)r * N + o;
-  c128 acc = mkc(0.0, 0.0);
-  for (int l = 0; l < mp; ++l) cfma(acc, ccast<double>(Mi[l]), ccast<double>(y[l]));
-  X[(int64_t)r * N + n] = ccast<TV>(acc);
+  cplx<TV> acc = mkc<TV>(0, 0);
+  for (int l = 0; l < mp; ++l) cfma(acc, Mi[l], y[l]);
+  X[(int64_t)r * N + n] = acc;
 }
 
 __global__ void k_rowwire(int64_t nw, const int64_t* __restrict__ off, Layout lay, int32_t* __restrict__ rowwire,
@@ -745,20 +697,12 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   P.restart = restart;
   P.N = N;
   P.tol = tol;
-  // rows per CTA of the Gram-Schmidt kernels: about 512 chunks per right-hand side, or 2048 for a
-  // single one (smaller chunks, less shared memory each, more CTAs and loads in flight per SM)
-  P.chunk = (int)std::max<int64_t>(kRows, ceil_div(ceil_div(N, R == 1 ? 2048 : 512), kRows) * kRows);
+  P.max_iter = max_iter;
+  // rows per CTA of the Gram-Schmidt kernels: about 16 CTAs per SM over all right-hand sides, at
+  // least kRows and at most kMaxChunk rows (the dots stage a chunk of u and w in shared memory)
+  P.chunk = (int)std::min<int64_t>(
+      kMaxChunk, std::max<int64_t>(kRows, ceil_div(ceil_div(N * R, 16 * std::max(ctx->nsm, 1)), kRows) * kRows));
   P.nchunk = (int)ceil_div(N, P.chunk);
-  // the fused step kernel: 128 rows per CTA for one right-hand side; with several, chunks as large as
-  // keep about four CTAs per SM busy over the blocks of 8 right-hand sides (at most 1024 rows), so
-  // the partial dot products the last CTA sums stay few
-  {
-    const int64_t nrb = ceil_div(R, 8);
-    const int64_t want = std::max<int64_t>(1, 4 * std::max(ctx->nsm, 1) / std::max<int64_t>(1, nrb));
-    P.schunk = R > 1 ? (int)std::min<int64_t>(1024, std::max<int64_t>(128, ceil_div(ceil_div(N, want), 32) * 32))
-                     : 128;
-  }
-  P.nschunk = (int)ceil_div(N, P.schunk);
   const int R1 = restart + 1;
   // The workspace persists across solves of the same size, so buffer addresses (and the captured
   // graph that bakes them in) stay the same from one solve to the next.
@@ -766,7 +710,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     int64_t key[4];
     KPtr P;
     cplx<TV> *Y, *W0, *W1, *V;
-    cplx<TV>* Xt;         // many right-hand sides, large systems: the current vectors, [N][R]
+    cplx<TV>* Xt;         // many right-hand sides: the pending vectors right-hand-side minor, [N][R]
     PSync* sync;          // persistent solve: barrier state and partial sums over its CTAs
     c128 *pp1, *pp2;
     double* ppn;
@@ -791,20 +735,22 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     SWM_TRY(dalloc(ctx, K, (void**)&P.bnorm, sizeof(double) * R));
     SWM_TRY(dalloc(ctx, K, (void**)&P.resid, sizeof(double) * R));
     SWM_TRY(dalloc(ctx, K, (void**)&P.H, sizeof(c128) * R * R1 * restart));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.Hraw, sizeof(c128) * R * R1 * restart));
     SWM_TRY(dalloc(ctx, K, (void**)&P.cs, sizeof(double) * R * restart));
     SWM_TRY(dalloc(ctx, K, (void**)&P.sn, sizeof(c128) * R * restart));
     SWM_TRY(dalloc(ctx, K, (void**)&P.g, sizeof(c128) * R * R1));
     SWM_TRY(dalloc(ctx, K, (void**)&P.hc, sizeof(c128) * R * R1));
     SWM_TRY(dalloc(ctx, K, (void**)&P.hc2, sizeof(c128) * R * R1));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.ht, sizeof(c128) * R * R1));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.gam, sizeof(c128) * R));
     SWM_TRY(dalloc(ctx, K, (void**)&P.coef, sizeof(c128) * R * restart));
-    SWM_TRY(dalloc(ctx, K, (void**)&P.part, sizeof(c128) * (size_t)R * std::max(P.nchunk, P.nschunk) * R1));
+    SWM_TRY(dalloc(ctx, K, (void**)&P.part, sizeof(c128) * (size_t)R * P.nchunk * 2 * R1));
     SWM_TRY(dalloc(ctx, K, (void**)&P.partn, sizeof(double) * (size_t)R * P.nchunk));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->Y, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W0, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W1, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->V, sizeof(cplx<TV>) * (size_t)R1 * R * N));
-    if (R >= kMinorR && N >= ctx->split_rows)
-      SWM_TRY(dalloc(ctx, K, (void**)&ws->Xt, sizeof(cplx<TV>) * (size_t)R * N));
+    if (R >= kMinorR) SWM_TRY(dalloc(ctx, K, (void**)&ws->Xt, sizeof(cplx<TV>) * (size_t)R * N));
     if (R <= kPersistMaxR && ctx->nsm > 0) {
       SWM_TRY(dalloc(ctx, K, (void**)&ws->sync, sizeof(PSync)));
       SWM_TRY(dalloc(ctx, K, (void**)&ws->pp1, sizeof(c128) * (size_t)R * R1 * ctx->nsm));
@@ -814,10 +760,14 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     ws->P = P;
   } else {
     const double tol_now = P.tol;
+    const int max_iter_now = P.max_iter;
     P = ws->P;
     P.tol = tol_now;
+    P.max_iter = max_iter_now;
   }
   cplx<TV> *Y = ws->Y, *W0 = ws->W0, *W1 = ws->W1, *V = ws->V;
+  // per-kernel path: W0 holds the pending vector u, W1 the product w = A u
+  cplx<TV> *U = W0, *Wv = W1;
   SWM_CK(cudaMemsetAsync(P.st, 0, sizeof(KState), st));
   SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));
   // with an initial guess the tolerance stays relative to |b|, so |b| is measured first
@@ -841,42 +791,36 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   }
   const dim3 g_rows((unsigned)ceil_div(N * kG, kRows), R);
   const dim3 g_chunk((unsigned)P.nchunk, R);
-  constexpr int kRB = 8;  // right-hand sides sharing each read of E in the streaming product
   const bool multi = R > 1;
-  // large systems: streaming product and separate dots (bandwidth); small: one fused kernel (latency)
-  const bool split = N >= ctx->split_rows;
-  const size_t sm = sizeof(cplx<TV>) * P.chunk;
-  // Fused step with several right-hand sides: how many share each read of E (4, 8 or 16) is
-  // measured on this system the first time its shape is seen, and kept.
+  const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
+  // The product: k_spmv with 1, 4, 8 or 16 right-hand sides sharing each read of E, or (kMinor)
+  // the right-hand-side-minor form; with several right-hand sides the form is timed on this system
+  // the first time its shape is solved, and kept.
+  constexpr int kMinor = 32;
   int rb = multi ? 8 : 1;
-  auto ssm_of = [&](int b) { return sizeof(cplx<TV>) * (size_t)P.schunk * b; };
-  auto step_fn = [&](int b) -> const void* {
+  auto launch_product = [&](cudaStream_t s, int b) -> int {
+    const dim3 gsp((unsigned)ceil_div(N * kG, kRows), (unsigned)ceil_div(R, std::min(b, 16)));
     switch (b) {
-      case 1: return (const void*)k_step<TV, TE, 1>;
-      case 4: return (const void*)k_step<TV, TE, 4>;
-      case 16: return (const void*)k_step<TV, TE, 16>;
-      default: return (const void*)k_step<TV, TE, 8>;
+      case 1: k_spmv<TV, TE, 1><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
+      case 4: k_spmv<TV, TE, 4><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
+      case 16: k_spmv<TV, TE, 16><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
+      case kMinor: {
+        k_rhs_minor<TV><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, U, ws->Xt);
+        SWM_LAUNCHED();
+        const unsigned gx = (unsigned)ceil_div(N, kTileRows);
+        if (R >= 24)
+          k_spmv_t<TV, TE, 32><<<dim3(gx, (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, Wv);
+        else
+          k_spmv_t<TV, TE, 16><<<dim3(gx, (unsigned)ceil_div(R, 16)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, Wv);
+        break;
+      }
+      default: k_spmv<TV, TE, 8><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
     }
+    SWM_LAUNCHED();
+    return SWM_OK;
   };
-  auto launch_step = [&](cudaStream_t s, int b) {
-    const dim3 gs((unsigned)P.nschunk, (unsigned)ceil_div(R, b));
-    const size_t sz = ssm_of(b);
-    const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
-    switch (b) {
-      case 1: k_step<TV, TE, 1><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
-      case 4: k_step<TV, TE, 4><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
-      case 16: k_step<TV, TE, 16><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
-      default: k_step<TV, TE, 8><<<gs, kRows, sz, s>>>(P, ri, ctx->offd.colmap, E, W0, W1, V); break;
-    }
-  };
-  for (int b : {1, 4, 8, 16})
-    if (ssm_of(b) > 48 * 1024 && ssm_of(b) <= 200 * 1024)
-      SWM_CK(allow_max_dyn_smem(step_fn(b), ctx->smem_optin));
-  if (sm > 48 * 1024) {
-    SWM_CK(allow_max_dyn_smem((const void*)k_update<TV>, ctx->smem_optin));
-    SWM_CK(allow_max_dyn_smem((const void*)k_dots_big<TV>, ctx->smem_optin));
-    SWM_CK(allow_max_dyn_smem((const void*)k_finish<TV>, ctx->smem_optin));
-  }
+  const size_t dots_smem = 2 * sizeof(cplx<TV>) * (size_t)P.chunk;
+  if (dots_smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_dots<TV>, ctx->smem_optin));
   // back substitution stages the triangle in shared memory when it fits
   size_t bs_smem = sizeof(c128) * (size_t)restart * restart;
   if (bs_smem > 160 * 1024) bs_smem = 0;
@@ -890,49 +834,21 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   auto launch_steps = [&](cudaStream_t s, int n) -> int {
     for (int i = 0; i < n; ++i) {
       ctx->prof_begin(SWM_K_APPLY);
-      if (split) {
-        const dim3 gsp((unsigned)ceil_div(N * kG, kRows), multi ? (unsigned)ceil_div(R, kRB) : 1u);
-        if (ws->Xt) {
-          const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
-          k_rhs_minor<TV><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, W0, W1, ws->Xt);
-          SWM_LAUNCHED();
-          const unsigned gx = (unsigned)ceil_div(N, kTileRows);
-          if (R >= 24)
-            k_spmv_t<TV, TE, 32><<<dim3(gx, (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E,
-                                                                                   ws->Xt, W0, W1, V);
-          else
-            k_spmv_t<TV, TE, 16><<<dim3(gx, (unsigned)ceil_div(R, 16)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E,
-                                                                                   ws->Xt, W0, W1, V);
-        } else if (multi)
-          k_spmv<TV, TE, kRB><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
-        else
-          k_spmv<TV, TE, 1><<<gsp, kRows, 0, s>>>(P, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V);
-        ctx->prof_end(SWM_K_APPLY);
-        SWM_LAUNCHED();
-        ctx->prof_begin(SWM_K_DOTS);
-        k_dots_big<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
-        ctx->prof_end(SWM_K_DOTS);
-      } else {
-        launch_step(s, rb);
-        ctx->prof_end(SWM_K_APPLY);
-      }
+      SWM_TRY(launch_product(s, rb));
+      ctx->prof_end(SWM_K_APPLY);
+      ctx->prof_begin(SWM_K_DOTS);
+      k_dots<TV><<<g_chunk, kRows, dots_smem, s>>>(P, U, Wv, V);
+      ctx->prof_end(SWM_K_DOTS);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_UPDATE);
-      k_update<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
+      k_update<TV><<<g_chunk, kRows, 0, s>>>(P, U, Wv, V);
       ctx->prof_end(SWM_K_UPDATE);
-      SWM_LAUNCHED();
-      ctx->prof_begin(SWM_K_FINISH);
-      k_finish<TV><<<g_chunk, kRows, sm, s>>>(P, W0, W1, V);
-      ctx->prof_end(SWM_K_FINISH);
       SWM_LAUNCHED();
     }
     return SWM_OK;
   };
-  // A chunk of Arnoldi steps is a CUDA graph (the launches are identical every step), captured on
-  // a private stream and reused while the kernel arguments stay the same.  Profiling a GMRES kernel
-  // class uses direct launches so its events time each launch.
-  if (!persisted && multi && !split) {
-    const int64_t shape[6] = {N, R, (int64_t)sizeof(TV), (int64_t)sizeof(TE), P.schunk, restart};
+  if (!persisted && multi) {
+    const int64_t shape[6] = {N, R, (int64_t)sizeof(TV), (int64_t)sizeof(TE), P.chunk, restart};
     int found = 0;
     for (const auto& t : ctx->tuned)
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
@@ -940,23 +856,22 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       rb = found;
     } else {
       // first cycle's residual and start (the loop below repeats them; both are idempotent), then
-      // each candidate step once untimed and once timed; the step is idempotent at a fixed j
-      k_apply<TV, TE><<<g_rows, kRows, 0, st>>>(1, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
+      // each candidate product once untimed and once timed; the product is idempotent
+      k_residual<TV, TE><<<g_rows, kRows, 0, st>>>(P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, U);
       SWM_LAUNCHED();
-      k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, W0, first ? 1 : 0);
+      k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, U, first ? 1 : 0);
       SWM_LAUNCHED();
       cudaEvent_t e0, e1;
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int b : {4, 8, 16}) {
-        if (ssm_of(b) > 200 * 1024) continue;
+      for (int b : {4, 8, 16, kMinor}) {
         if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
-        launch_step(st, b);
+        if (b == kMinor && !ws->Xt) continue;
+        SWM_TRY(launch_product(st, b));
         SWM_CK(cudaEventRecord(e0, st));
-        launch_step(st, b);
+        SWM_TRY(launch_product(st, b));
         SWM_CK(cudaEventRecord(e1, st));
-        ctx->launches += 2;
         SWM_CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         SWM_CK(cudaEventElapsedTime(&ms, e0, e1));
@@ -976,21 +891,19 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   }
   ctx->stats.step_rhs_block = rb;
   const bool use_graph = !persisted && ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_DOTS &&
-                         ctx->prof_cls != SWM_K_UPDATE && ctx->prof_cls != SWM_K_FINISH;
+                         ctx->prof_cls != SWM_K_UPDATE;
   if (use_graph) {
     struct Key {
       KPtr P;
-      const void* ptr[6];
+      const void* ptr[7];
       Layout lay;
-      size_t sm;
       unsigned gx, gy, bits;
     } key;
     std::memset(&key, 0, sizeof(key));
     key.P = P;
-    const void* ptrs[6] = {ctx->rowinfo, ctx->offd.colmap, E, W0, W1, V};
-    for (int i = 0; i < 6; ++i) key.ptr[i] = ptrs[i];
+    const void* ptrs[7] = {ctx->rowinfo, ctx->offd.colmap, E, U, Wv, V, ws->Xt};
+    for (int i = 0; i < 7; ++i) key.ptr[i] = ptrs[i];
     key.lay = ctx->offd;
-    key.sm = sm;
     key.gx = g_chunk.x;
     key.gy = g_chunk.y;
     key.bits = (unsigned)(sizeof(TV) * 64 + sizeof(TE) + 4096 * rb);
@@ -1016,26 +929,28 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       ctx->gm_key = kv;
     }
   }
+  const int launches_per_step = (rb == kMinor ? 2 : 1) + 2;
   while (!persisted) {
     // residual of the current y and the start of a cycle
     ctx->prof_begin(SWM_K_APPLY);
-    k_apply<TV, TE><<<g_rows, kRows, 0, st>>>(1, P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, W0, W1, V);
+    k_residual<TV, TE><<<g_rows, kRows, 0, st>>>(P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, U);
     ctx->prof_end(SWM_K_APPLY);
     SWM_LAUNCHED();
-    k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, W0, first ? 1 : 0);
+    k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, U, first ? 1 : 0);
     SWM_LAUNCHED();
     first = false;
     SWM_CK(cudaMemcpyAsync(&hs, P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
     SWM_CK(cudaStreamSynchronize(st));
     if (hs.all_conv || hs.numeric || hs.iters >= max_iter) break;
-    const int steps = std::min(restart, max_iter - hs.iters);
+    // the cycle's Arnoldi steps and its closing pass
+    const int steps = std::min(restart, max_iter - hs.iters) + 1;
     // chunks of steps; the host reads the flag of chunk c - 1 while chunk c is queued
     int c = 0;
     for (int s0 = 0; s0 < steps; s0 += kChunkSteps, ++c) {
       const int n = std::min(steps - s0, kChunkSteps);
       if (use_graph && n == kChunkSteps) {
         SWM_CK(cudaGraphLaunch(ctx->gm_exec, st));
-        ctx->launches += (split ? (ws->Xt ? 5 : 4) : 3) * kChunkSteps;
+        ctx->launches += launches_per_step * kChunkSteps;
       } else {
         SWM_TRY(launch_steps(st, n));
       }

@@ -16,7 +16,8 @@ struct KState {
   int iters;      // total Arnoldi steps
   int numeric;    // a NaN/Inf appeared
   int cycles;     // restart cycles (persistent solve)
-  int pad[2];
+  int jmax;       // Hessenberg columns of this cycle (per-kernel solve)
+  int pad;
 };
 
 struct KPtr {
@@ -27,17 +28,20 @@ struct KPtr {
   double* inv_h;      // [R]
   double* bnorm;      // [R]
   double* resid;      // [R]
-  c128* H;            // [R][(restart + 1) * restart]
+  c128* H;            // [R][(restart + 1) * restart], Givens-rotated
+  c128* Hraw;         // [R][(restart + 1) * restart], as formed (per-kernel solve)
   double* cs;         // [R][restart]
   c128* sn;           // [R][restart]
   c128* g;            // [R][restart + 1]
   c128* hc;           // [R][restart + 1]
   c128* hc2;          // [R][restart + 1]
+  c128* ht;           // [R][restart + 1]
+  c128* gam;          // [R]
   c128* coef;         // [R][restart]
-  c128* part;         // [R][nchunk][restart + 1]
+  c128* part;         // [R][2 (restart + 1)][nchunk]
   double* partn;      // [R][nchunk]
   int R, restart, nchunk, chunk;
-  int nschunk, schunk;  // chunks of the fused step kernel (finer, for more CTAs)
+  int max_iter;
   int64_t N;
   double tol;
 };
