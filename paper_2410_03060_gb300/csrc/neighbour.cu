@@ -149,7 +149,11 @@ struct RowCounts {
 };
 
 // mode 0: count kept partners per wire (and the sizes in RowCounts); mode 1: write them (sorted)
-// into col.
+// into col.  One warp per wire: lanes 0..8 look up the nine (z, y) rows of three cells around the
+// wire's cell at once (each a contiguous range of the renumbered wires), a warp scan lays the
+// ranges end to end, and the warp tests 32 candidates per pass, so a wire costs about three
+// dependent memory round trips whatever its cell occupancy.  Candidates are visited in increasing
+// index order (rows in cell order), so the ballot compaction writes each row's partners sorted.
 __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double* __restrict__ cy,
                         const double* __restrict__ cz, const int32_t* __restrict__ cid, const int64_t* __restrict__ cstart,
                         Grid g, double rc2, int dense, int mode, RowCounts rc, const int32_t* __restrict__ m,
@@ -159,42 +163,63 @@ __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double*
   if (p >= nw) return;
   const int id = cid[p];
   const int ix = id % g.nx, iy = (id / g.nx) % g.ny, iz = id / (g.nx * g.ny);
-  const double px = cx[p], py = cy[p], pz = cz[p];
-  int64_t count = 0;
-  int32_t msum = 0, nup = 0;  // this lane's kept m_q and kept q > p (counting pass)
-  const int64_t base = mode ? row_ptr[p] : 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int z = iz + dz;
-    if (z < 0 || z >= g.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = iy + dy;
-      if (y < 0 || y >= g.ny) continue;
+  // this lane's row range (lanes 0..8)
+  int64_t q0 = 0, len = 0;
+  if (lane < 9) {
+    const int z = iz + lane / 3 - 1, y = iy + lane % 3 - 1;
+    if (z >= 0 && z < g.nz && y >= 0 && y < g.ny) {
       const int x0 = max(ix - 1, 0), x1 = min(ix + 1, g.nx - 1);
       const int64_t c0 = ((int64_t)z * g.ny + y) * g.nx + x0;
       const int64_t c1 = ((int64_t)z * g.ny + y) * g.nx + x1;
-      const int64_t q0 = cstart[c0], q1 = cstart[c1 + 1];
-      for (int64_t qb = q0; qb < q1; qb += 32) {
-        const int64_t q = qb + lane;
-        bool keep = false;
-        if (q < q1) {
-          if (dense) {
-            keep = true;
-          } else {
-            const double dx = px - cx[q], dyy = py - cy[q], dzz = pz - cz[q];
-            // (dx*dx + dy*dy) + dz*dz, each operation rounded separately (no contraction)
-            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dyy, dyy)), __dmul_rn(dzz, dzz));
-            keep = d2 <= rc2;
-          }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (mode && keep) col[base + count + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
-        if (!mode && keep) {
-          msum += m[q];
-          nup += q > p ? 1 : 0;
-        }
-        count += __popc(bal);
+      q0 = cstart[c0];
+      len = cstart[c1 + 1] - q0;
+    }
+  }
+  const double px = cx[p], py = cy[p], pz = cz[p];
+  int64_t incl = len;
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) {
+    const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int64_t total = __shfl_sync(0xffffffffu, incl, 8);
+  // every lane keeps the nine ranges' starts in the flat order and their first indices
+  int64_t fs[9], qs[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const int64_t e = __shfl_sync(0xffffffffu, incl - len, r);
+    fs[r] = e;
+    qs[r] = __shfl_sync(0xffffffffu, q0, r) - e;  // q = f + qs[r] inside range r
+  }
+  int64_t count = 0;
+  int32_t msum = 0, nup = 0;  // this lane's kept m_q and kept q > p (counting pass)
+  const int64_t base = mode ? row_ptr[p] : 0;
+  for (int64_t fb = 0; fb < total; fb += 32) {
+    const int64_t f = fb + lane;
+    bool keep = false;
+    int64_t q = 0;
+    if (f < total) {
+      int64_t off = qs[0];
+#pragma unroll
+      for (int r = 1; r < 9; ++r)
+        if (f >= fs[r]) off = qs[r];  // empty ranges share their start with the next one
+      q = f + off;
+      if (dense) {
+        keep = true;
+      } else {
+        const double dx = px - cx[q], dyy = py - cy[q], dzz = pz - cz[q];
+        // (dx*dx + dy*dy) + dz*dz, each operation rounded separately (no contraction)
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dyy, dyy)), __dmul_rn(dzz, dzz));
+        keep = d2 <= rc2;
       }
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (mode && keep) col[base + count + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
+    if (!mode && keep) {
+      msum += m[q];
+      nup += q > p ? 1 : 0;
+    }
+    count += __popc(bal);
   }
   if (!mode) {
 #pragma unroll
