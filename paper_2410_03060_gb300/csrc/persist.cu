@@ -17,14 +17,19 @@ namespace {
 // vector, its rows of the basis V, and its rows of E with their column map and row descriptors
 // (loaded once).  The product first gathers the vector at the CTA's column-map slice (the rows
 // of one wire share their block-row's column map) into shared memory, all loads in flight at
-// once, and then forms each row's sum from shared memory.  One Arnoldi step has four phases
-// separated by three grid barriers:
-//   A: v_j = w / |w| (own rows), u = A v_j, first dots V^H u
-//   B: sum of the dot partials, u -= V h1, second dots V^H u
-//   C: sum, u -= V h2, w = u written for the next gather, |w|^2 partials
-//   D: sum of the norms, Hessenberg column, Givens rotation, residual estimate and activity
-// Phase D and every partial sum are computed by every CTA from the same partials in the same
-// order, so all CTAs reach identical decisions and run identical barrier sequences.  The dot
+// once, and then forms each row's sum from shared memory.  The basis is orthogonalised by
+// classical Gram-Schmidt with its second pass delayed by one step (as in the per-kernel solve),
+// so one Arnoldi step is two phases separated by two grid barriers:
+//   A: w = A u_j for the pending vector u_j (own rows), partial dots s = Q^H u_j, |u_j|^2,
+//      t = Q^H w, u_j^H w
+//   B: sums of the partials; rho = |u_j - Q s|, Hessenberg column j-1 completed (first-pass
+//      coefficients + s, subdiagonal rho), its Givens rotation, residual estimate and activity;
+//      the first-pass coefficients of column j (each CTA forms those of the Hessenberg rows it
+//      owns, from its rows of the unrotated matrix); q_j = (u_j - Q s) / rho to V_j and the next
+//      pending vector (w - Q t) / rho - (q_j^H w / rho) q_j, written for the next gather
+// and a closing phase A/B without product completes the last column of a cycle.  Phase B and
+// every partial sum are computed by every CTA from the same partials in the same order, so all
+// CTAs reach identical decisions and run identical barrier sequences.  The dot
 // products, their sums over the CTAs (in a fixed pairwise order), the rotations and the
 // triangular solve run in the precision of the vectors: float64 on the complex128 path, float32 on
 // the complex64 path, whose vectors carry float32 rounding anyway (on this GPU a float64 warp
@@ -60,11 +65,11 @@ struct PArgs {
 
 // Byte offsets of the shared-memory arrays of the persistent kernel.
 struct PLayout {
-  size_t h1, h2, yv, gg, sn, col, ri, ys, vs, es, xg, cs, cm, total;
+  size_t h1, h2, yv, gg, sn, col, hr, ri, ys, ws, vs, es, xg, cs, cm, total;
 };
 __host__ __device__ inline size_t p_align16(size_t x) { return (x + 15) & ~size_t(15); }
-__host__ __device__ inline PLayout persist_layout(int RB, int R, int restart, int rows, size_t cb, size_t eb,
-                                                  int vsm, int esm, int64_t emax, int64_t cmax) {
+__host__ __device__ inline PLayout persist_layout(int RB, int R, int restart, int rows, int hown, size_t cb,
+                                                  size_t eb, int vsm, int esm, int64_t emax, int64_t cmax) {
   PLayout L;
   const size_t R1 = restart + 1;
   size_t o = 0;
@@ -74,8 +79,10 @@ __host__ __device__ inline PLayout persist_layout(int RB, int R, int restart, in
   L.gg = o; o += p_align16(cb * RB * R1);
   L.sn = o; o += p_align16(cb * RB * restart);
   L.col = o; o += p_align16(cb * RB * R1);
+  L.hr = o; o += p_align16(cb * RB * (size_t)hown * restart);
   L.ri = o; o += esm ? 16 * (size_t)rows : 0;
   L.ys = o; o += p_align16(cb * RB * rows);
+  L.ws = o; o += p_align16(cb * RB * rows);
   L.vs = o; o += vsm ? p_align16(cb * R1 * R * rows) : 0;
   L.es = o; o += esm ? p_align16(eb * (size_t)emax) : 0;
   L.xg = o; o += esm ? p_align16(cb * (size_t)R * cmax) : 0;
@@ -179,16 +186,20 @@ __device__ __forceinline__ T sum_g_d(const T* __restrict__ p, int G, int lane) {
   return warp_sum(s);
 }
 
-// dst[b][i] (shared) = sum over the G CTAs of part[(b * R1 + i) * G + c], for active b, i <= j.
+// The sums of both partial arrays in one pass (every warp's loads of one item in flight together):
+// d1[b][i] from p1 and, unless closing, d2[b][i] from p2, for active b and i <= j.
 template <typename T>
-__device__ void p_reduce(const cplx<T>* __restrict__ part, int G, int R, int R1, int j, const int* act, cplx<T>* dst) {
+__device__ void p_reduce2(const cplx<T>* __restrict__ p1, const cplx<T>* __restrict__ p2, int G, int R, int R1, int j,
+                          const int* act, bool closing, cplx<T>* d1, cplx<T>* d2) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int nt = R * (j + 1);
+  const int per = R * (j + 1);
+  const int nt = closing ? per : 2 * per;
   for (int k = wp; k < nt; k += kPWarps) {
-    const int b = k / (j + 1), i = k % (j + 1);
+    const int which = k / per, rest = k % per;
+    const int b = rest / (j + 1), i = rest % (j + 1);
     if (!act[b]) continue;
-    const cplx<T> v = sum_g_c<T>(part + (int64_t)(b * R1 + i) * G, G, lane);
-    if (lane == 0) dst[b * R1 + i] = v;
+    const cplx<T> v = sum_g_c<T>((which ? p2 : p1) + (int64_t)(b * R1 + i) * G, G, lane);
+    if (lane == 0) (which ? d2 : d1)[b * R1 + i] = v;
   }
 }
 
@@ -201,39 +212,104 @@ struct VRows {
   __device__ __forceinline__ cplx<TV>* at(int i, int b) const { return base + ((int64_t)i * R + b) * stride; }
 };
 
-// Partial dots conj(V_i[b]) . ys[b] over the CTA's rows, for active b and i <= j.
+// Partial dots of the delayed Gram-Schmidt over the CTA's rows, for active b: part1[b][i] =
+// conj(V_i[b]) . u[b] and part2[b][i] = conj(V_i[b]) . w[b] for i < j, and at i = j the same with
+// u[b] in place of V_i[b] (|u|^2, u^H w); the closing pass (no product) fills part1 only.
 template <typename TV>
-__device__ void p_dots(const VRows<TV>& V, const cplx<TV>* ys, int rows, int cnt, int R, int R1, int j, int G,
-                       const int* act, cplx<TV>* __restrict__ part) {
+__device__ void p_dots2(const VRows<TV>& V, const cplx<TV>* ys, const cplx<TV>* ws, int rows, int cnt, int R, int R1,
+                        int j, int G, const int* act, bool closing, cplx<TV>* __restrict__ part1,
+                        cplx<TV>* __restrict__ part2) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int nt = R * (j + 1);
   for (int k = wp; k < nt; k += kPWarps) {
     const int b = k / (j + 1), i = k % (j + 1);
     if (!act[b]) continue;
-    const cplx<TV>* vi = V.at(i, b);
-    const cplx<TV>* w = ys + b * rows;
-    cplx<TV> acc = mkc<TV>(0, 0);
+    const cplx<TV>* u = ys + b * rows;
+    const cplx<TV>* w = ws + b * rows;
+    const cplx<TV>* vi = i < j ? V.at(i, b) : u;
+    cplx<TV> a = mkc<TV>(0, 0), c = mkc<TV>(0, 0);
     int t = lane;
     for (; t + 96 < cnt; t += 128) {
-      cplx<TV> v[4], x[4];
+      cplx<TV> v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        v[u] = vi[t + 32 * u];
-        x[u] = w[t + 32 * u];
-      }
+      for (int q = 0; q < 4; ++q) v[q] = vi[t + 32 * q];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        acc.re = fma(v[u].re, x[u].re, fma(v[u].im, x[u].im, acc.re));
-        acc.im = fma(v[u].re, x[u].im, fma(-v[u].im, x[u].re, acc.im));
+      for (int q = 0; q < 4; ++q) {
+        const cplx<TV> x = u[t + 32 * q];
+        a.re = fma(v[q].re, x.re, fma(v[q].im, x.im, a.re));
+        a.im = fma(v[q].re, x.im, fma(-v[q].im, x.re, a.im));
+        if (!closing) {
+          const cplx<TV> y = w[t + 32 * q];
+          c.re = fma(v[q].re, y.re, fma(v[q].im, y.im, c.re));
+          c.im = fma(v[q].re, y.im, fma(-v[q].im, y.re, c.im));
+        }
       }
     }
     for (; t < cnt; t += 32) {
-      const cplx<TV> v = vi[t], x = w[t];
-      acc.re = fma(v.re, x.re, fma(v.im, x.im, acc.re));
-      acc.im = fma(v.re, x.im, fma(-v.im, x.re, acc.im));
+      const cplx<TV> v = vi[t], x = u[t];
+      a.re = fma(v.re, x.re, fma(v.im, x.im, a.re));
+      a.im = fma(v.re, x.im, fma(-v.im, x.re, a.im));
+      if (!closing) {
+        const cplx<TV> y = w[t];
+        c.re = fma(v.re, y.re, fma(v.im, y.im, c.re));
+        c.im = fma(v.re, y.im, fma(-v.im, y.re, c.im));
+      }
     }
-    const TV re = warp_sum(acc.re), im = warp_sum(acc.im);
-    if (lane == 0) part[(int64_t)(b * R1 + i) * G + blockIdx.x] = mkc<TV>(re, im);
+    const TV are = warp_sum(a.re), aim = warp_sum(a.im);
+    const TV cre = warp_sum(c.re), cim = warp_sum(c.im);
+    if (lane == 0) {
+      part1[(int64_t)(b * R1 + i) * G + blockIdx.x] = mkc<TV>(are, aim);
+      if (!closing) part2[(int64_t)(b * R1 + i) * G + blockIdx.x] = mkc<TV>(cre, cim);
+    }
+  }
+}
+
+// The update of the delayed Gram-Schmidt over the CTA's rows, for active b: q = (u - sum_{i<j}
+// V_i s_i) / rho goes to V_j and u' = (w - sum_{i<j} V_i t_i) / rho - gamma q replaces u in ys and
+// in the global vector W (for the next gather).
+template <typename TV, int RB>
+__device__ void p_update2(const VRows<TV>& V, cplx<TV>* ys, const cplx<TV>* ws, int rows, int cnt, int64_t n0,
+                          int64_t N, int R, int R1, int j, const int* act, const cplx<TV>* sv, const cplx<TV>* tv,
+                          const TV* invr, const cplx<TV>* gam, cplx<TV>* __restrict__ W) {
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    if (b >= R) break;
+    if (!act[b]) continue;
+    const cplx<TV>* sb = sv + b * R1;
+    const cplx<TV>* tb = tv + b * R1;
+    const TV ir = invr[b];
+    const cplx<TV> gm = gam[b];
+    cplx<TV>* vj = V.at(j, b);
+    for (int t = threadIdx.x; t < cnt; t += kPT) {
+      cplx<TV> x = ys[b * rows + t], y = ws[b * rows + t];
+      int i = 0;
+      for (; i + 3 < j; i += 4) {
+        cplx<TV> v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = V.at(i + q, b)[t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const cplx<TV> a = sb[i + q], c = tb[i + q];
+          x.re = fma(-v[q].re, a.re, fma(v[q].im, a.im, x.re));
+          x.im = fma(-v[q].re, a.im, fma(-v[q].im, a.re, x.im));
+          y.re = fma(-v[q].re, c.re, fma(v[q].im, c.im, y.re));
+          y.im = fma(-v[q].re, c.im, fma(-v[q].im, c.re, y.im));
+        }
+      }
+      for (; i < j; ++i) {
+        const cplx<TV> v = V.at(i, b)[t];
+        const cplx<TV> a = sb[i], c = tb[i];
+        x.re = fma(-v.re, a.re, fma(v.im, a.im, x.re));
+        x.im = fma(-v.re, a.im, fma(-v.im, a.re, x.im));
+        y.re = fma(-v.re, c.re, fma(v.im, c.im, y.re));
+        y.im = fma(-v.re, c.im, fma(-v.im, c.re, y.im));
+      }
+      const cplx<TV> q = ir * x;
+      vj[t] = q;
+      const cplx<TV> un = ir * y - q * gm;
+      ys[b * rows + t] = un;
+      W[(int64_t)b * N + n0 + t] = un;
+    }
   }
 }
 
@@ -258,50 +334,6 @@ __device__ void p_norm_partials(const T* nrm, int R, int G, T* __restrict__ part
   }
 }
 
-// ys[b] -= sum_{i <= j} V_i[b] h[b][i] over the CTA's rows, for active b.  With W non-null the
-// result also goes to the global vector and the squared norms of the CTA's rows go to partn.
-template <typename TV, int RB>
-__device__ void p_update(const VRows<TV>& V, cplx<TV>* ys, int rows, int cnt, int64_t n0, int64_t N, int R, int R1,
-                         int j, const int* act, const cplx<TV>* h, cplx<TV>* __restrict__ W, TV* __restrict__ partn,
-                         int G, TV (*red)[RB]) {
-  TV nrm[RB];
-#pragma unroll
-  for (int b = 0; b < RB; ++b) nrm[b] = 0;
-#pragma unroll
-  for (int b = 0; b < RB; ++b) {
-    if (b >= R) break;
-    if (!act[b]) continue;
-    const cplx<TV>* hb = h + b * R1;
-    for (int t = threadIdx.x; t < cnt; t += kPT) {
-      cplx<TV> x = ys[b * rows + t];
-      int i = 0;
-      for (; i + 3 <= j; i += 4) {
-        cplx<TV> v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = V.at(i + u, b)[t];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const cplx<TV> hh = hb[i + u];
-          x.re = fma(-v[u].re, hh.re, fma(v[u].im, hh.im, x.re));
-          x.im = fma(-v[u].re, hh.im, fma(-v[u].im, hh.re, x.im));
-        }
-      }
-      for (; i <= j; ++i) {
-        const cplx<TV> v0 = V.at(i, b)[t];
-        const cplx<TV> hh = hb[i];
-        x.re = fma(-v0.re, hh.re, fma(v0.im, hh.im, x.re));
-        x.im = fma(-v0.re, hh.im, fma(-v0.im, hh.re, x.im));
-      }
-      ys[b * rows + t] = x;
-      if (W) {
-        W[(int64_t)b * N + n0 + t] = x;
-        nrm[b] = fma(x.re, x.re, fma(x.im, x.im, nrm[b]));
-      }
-    }
-  }
-  if (W) p_norm_partials<TV, RB>(nrm, R, G, partn, red);
-}
-
 // The CTA's slice of E: values, column map, row descriptors, and the gathered vector entries.
 template <typename TV, typename TE>
 struct ESlice {
@@ -314,22 +346,19 @@ struct ESlice {
 };
 
 // Rows of the CTA times A = I + E for the R right-hand sides of `src`.
-// mode 0 (Arnoldi): x = ys * inv (the normalised v_j, stored in V_j), ys = x + inv * E src.
+// mode 0 (Arnoldi): ws = u + E u for the pending vector u (own rows in ys, all rows in src).
 // mode 1 (residual): ys = W = B - (Y + E Y), squared norms to partn.
 template <typename TV, typename TE, int RB>
 __device__ void p_product(int mode, const PArgs& a, const ESlice<TV, TE>& S, const cplx<TV>* __restrict__ src,
-                          cplx<TV>* ys, int cnt, int64_t n0, const VRows<TV>& V, int j, const int* act,
-                          const TV* inv, const cplx<TV>* __restrict__ B, cplx<TV>* __restrict__ W,
-                          TV (*red)[RB]) {
+                          cplx<TV>* ys, cplx<TV>* ws, int cnt, int64_t n0, const int* act,
+                          const cplx<TV>* __restrict__ B, cplx<TV>* __restrict__ W, TV (*red)[RB]) {
   const int R = a.P.R;
   const int64_t N = a.P.N;
   bool on[RB];
-  TV sc[RB];
   TV nrm[RB];
 #pragma unroll
   for (int b = 0; b < RB; ++b) {
     on[b] = b < R && (mode == 1 || act[b]);
-    sc[b] = b < R ? inv[b] : TV(0);
     nrm[b] = 0;
   }
   if (S.xg) {
@@ -401,9 +430,7 @@ __device__ void p_product(int mode, const PArgs& a, const ESlice<TV, TE>& S, con
     for (int b = 0; b < RB; ++b) {
       if (!on[b]) continue;
       if (mode == 0) {
-        const cplx<TV> x = sc[b] * ys[b * a.rows + t];
-        V.at(j, b)[t] = x;
-        ys[b * a.rows + t] = x + sc[b] * acc[b];
+        ws[b * a.rows + t] = ys[b * a.rows + t] + acc[b];
       } else {
         const cplx<TV> y = src[(int64_t)b * N + n];  // own row of Y, written by this CTA
         const cplx<TV> r = B[(int64_t)b * N + n] - (y + acc[b]);
@@ -430,9 +457,10 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
   C* W = (C*)a.W;
 
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const PLayout L = persist_layout(RB, R, RS, a.rows, sizeof(C), sizeof(TE), a.vsm, a.esm, a.emax, a.cmax);
-  C* h1 = reinterpret_cast<C*>(sm_raw + L.h1);         // [RB][R1] first-pass coefficients
-  C* h2 = reinterpret_cast<C*>(sm_raw + L.h2);         // [RB][R1] second-pass coefficients
+  const int hown = (R1 + G - 1) / G;  // rows of the unrotated Hessenberg matrix this CTA owns, at most
+  const PLayout L = persist_layout(RB, R, RS, a.rows, hown, sizeof(C), sizeof(TE), a.vsm, a.esm, a.emax, a.cmax);
+  C* h1 = reinterpret_cast<C*>(sm_raw + L.h1);         // [RB][R1] sums Q^H u, with |u|^2 last
+  C* h2 = reinterpret_cast<C*>(sm_raw + L.h2);         // [RB][R1] sums Q^H w, with u^H w last
   c128* yv = reinterpret_cast<c128*>(sm_raw + L.yv);   // [RB][RS] back-solve / coefficients
   C* part1 = (C*)a.part1;
   C* part2 = (C*)a.part2;
@@ -440,8 +468,10 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
   C* gg = reinterpret_cast<C*>(sm_raw + L.gg);         // [RB][R1] rotated residual
   C* sn = reinterpret_cast<C*>(sm_raw + L.sn);         // [RB][RS] rotation sines
   C* colv = reinterpret_cast<C*>(sm_raw + L.col);      // [RB][R1] Hessenberg column
+  C* hrs = reinterpret_cast<C*>(sm_raw + L.hr);        // [RB][hown][RS] own rows, unrotated
   TV* cs = reinterpret_cast<TV*>(sm_raw + L.cs);       // [RB][RS] rotation cosines
-  C* ys = reinterpret_cast<C*>(sm_raw + L.ys);         // [RB][rows]
+  C* ys = reinterpret_cast<C*>(sm_raw + L.ys);         // [RB][rows] pending vector u (own rows)
+  C* ws = reinterpret_cast<C*>(sm_raw + L.ws);         // [RB][rows] w = A u (own rows)
   VRows<TV> V;
   V.R = R;
   if (a.vsm) {
@@ -482,10 +512,11 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
     }
   }
   __shared__ double bnorm[RB], resid[RB];
-  __shared__ TV inv[RB], nrm2[RB];
+  __shared__ TV nrm2[RB], rho_s[RB], invr[RB];
+  __shared__ C gam[RB];
   __shared__ TV red[kPWarps][RB];
   __shared__ int act[RB], jl[RB];
-  __shared__ int s_j, s_iters, s_done, s_conv, s_numeric, s_cycles, s_ok;
+  __shared__ int s_j, s_jmax, s_iters, s_done, s_conv, s_numeric, s_cycles, s_ok;
   __shared__ unsigned s_epoch;
   if (threadIdx.x == 0) {
     s_epoch = 0;
@@ -496,7 +527,6 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
   }
   if (threadIdx.x < RB) {
     act[threadIdx.x] = 0;
-    inv[threadIdx.x] = 0;
     jl[threadIdx.x] = 0;
   }
   __syncthreads();
@@ -545,7 +575,7 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
       if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
     }
     // ---- residual W = B - A Y on the CTA's rows, its squared norms
-    p_product<TV, TE, RB>(1, a, S, Y, ys, cnt, n0, V, 0, act, inv, B, W, red);
+    p_product<TV, TE, RB>(1, a, S, Y, ys, ws, cnt, n0, act, B, W, red);
     if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
     // ---- start of a cycle (every CTA)
     if (wp < R) {
@@ -563,7 +593,6 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
       const bool ac = isfinite(res) && res > P.tol;
       if (!isfinite(res)) s_numeric = 1;
       act[b] = ac ? 1 : 0;
-      inv[b] = beta > 0.0 ? (TV)(1.0 / beta) : TV(0);
       gg[b * R1] = mkc<TV>((TV)beta, TV(0));
     }
     __syncthreads();
@@ -572,100 +601,164 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
       for (int b = 0; b < R; ++b) any |= act[b];
       s_conv = any ? 0 : 1;
       s_j = 0;
+      s_jmax = min(RS, a.max_iter - s_iters);
       s_done = (!any || s_iters >= a.max_iter) ? 1 : 0;
       if (!first) s_cycles += 1;
     }
     __syncthreads();
     first = false;
     if (s_conv || s_numeric || s_iters >= a.max_iter) break;
-    // ---- Arnoldi steps
+    // ---- Arnoldi steps (u_0 = the residual, in ys and W), then the closing pass
     while (!s_done) {
       const int j = s_j;
-      // A: v_j and u = A v_j on own rows, first dots
-      p_product<TV, TE, RB>(0, a, S, W, ys, cnt, n0, V, j, act, inv, B, W, red);
+      const bool closing = j >= s_jmax;
+      // A: w = A u_j on own rows, partial dots
+      if (!closing) p_product<TV, TE, RB>(0, a, S, W, ys, ws, cnt, n0, act, B, W, red);
       __syncthreads();
-      p_dots<TV>(V, ys, a.rows, cnt, R, R1, j, G, act, part1);
+      p_dots2<TV>(V, ys, ws, a.rows, cnt, R, R1, j, G, act, closing, part1, part2);
       if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
-      // B: h1, u -= V h1, second dots
-      p_reduce<TV>(part1, G, R, R1, j, act, h1);
+      // B1: sums (s and |u|^2 in h1, t and u^H w in h2) and the first-pass coefficients of
+      // column j-1, formed at the previous step by the owners of their rows
+      p_reduce2<TV>(part1, part2, G, R, R1, j, act, closing, h1, h2);
+      const c128* hc_prev = ((j - 1) & 1) ? P.hc2 : P.hc;
+      c128* hc_next = (j & 1) ? P.hc2 : P.hc;
+      for (int k = threadIdx.x; k < R * j; k += kPT) {
+        const int b = k / j, i = k % j;
+        if (act[b]) colv[b * R1 + i] = ccast<TV>(ldcg_c<double>(hc_prev + (int64_t)b * R1 + i));
+      }
       __syncthreads();
-      p_update<TV, RB>(V, ys, a.rows, cnt, n0, N, R, R1, j, act, h1, nullptr, nullptr, G, red);
-      __syncthreads();
-      p_dots<TV>(V, ys, a.rows, cnt, R, R1, j, G, act, part2);
-      if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
-      // C: h2, w = u - V h2 to global, squared norms
-      p_reduce<TV>(part2, G, R, R1, j, act, h2);
-      __syncthreads();
-      p_update<TV, RB>(V, ys, a.rows, cnt, n0, N, R, R1, j, act, h2, W, partn, G, red);
-      if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
-      // D: norms, Hessenberg column, rotations, residual estimate (every CTA, same values)
+      // B2: the unrotated column j-1 (first-pass coefficients + s, subdiagonal rho), with
+      // rho = |u - Q s| = sqrt(|u|^2 - |s|^2) and gamma = q_j^H w / rho = (u^H w - s^H t) / rho^2
+      for (int k = threadIdx.x; k < R * j; k += kPT) {
+        const int b = k / j, i = k % j;
+        if (act[b]) colv[b * R1 + i] = colv[b * R1 + i] + h1[b * R1 + i];
+      }
       if (wp < R && act[wp]) {
-        const TV t = sum_g_d<TV>(partn + (int64_t)wp * G, G, lane);
-        if (lane == 0) nrm2[wp] = t;
-      }
-      for (int k = threadIdx.x; k < R * (j + 1); k += kPT) {
-        const int b = k / (j + 1), i = k % (j + 1);
-        if (act[b]) colv[b * R1 + i] = h1[b * R1 + i] + h2[b * R1 + i];
+        const int b = wp;
+        TV ss = 0, gr = 0, gi = 0;
+        for (int i = lane; i < j; i += 32) {
+          const C sv = h1[b * R1 + i];
+          ss += sv.re * sv.re + sv.im * sv.im;
+          if (!closing) {
+            const C p = cmulc(sv, h2[b * R1 + i]);
+            gr += p.re;
+            gi += p.im;
+          }
+        }
+        ss = warp_sum(ss);
+        gr = warp_sum(gr);
+        gi = warp_sum(gi);
+        if (lane == 0) {
+          const TV al = h1[b * R1 + j].re - ss;
+          const TV rho = !isfinite(al) ? al : (al > TV(0) ? sqrt(al) : TV(0));
+          rho_s[b] = rho;
+          const TV ir = rho > TV(0) ? TV(1) / rho : TV(0);
+          invr[b] = ir;
+          if (!closing) gam[b] = (ir * ir) * (h2[b * R1 + j] - mkc<TV>(gr, gi));
+          if (j >= 1) colv[b * R1 + j] = mkc<TV>(rho, TV(0));
+        }
       }
       __syncthreads();
+      // B3: rows k = blockIdx.x + m G (m < hown) of the unrotated matrix belong to this CTA and
+      // live in its shared memory: store their entries of column j-1, and form their first-pass
+      // coefficients of column j, (t_k - (H s)_k) / rho, and gamma - s_{j-1} for row j
+      if ((int)blockIdx.x <= j) {
+        const int nown = (j - (int)blockIdx.x) / G + 1;
+        for (int pr = wp; pr < nown * R; pr += kPWarps) {
+          const int m = pr / R, b = pr % R;
+          const int k = (int)blockIdx.x + m * G;
+          if (!act[b]) continue;
+          C* hr = hrs + ((int64_t)b * hown + m) * RS;
+          if (j >= 1 && lane == 0) hr[j - 1] = colv[b * R1 + k];
+          if (closing) continue;
+          if (k < j) {
+            TV cr = 0, ci = 0;
+            for (int i = (k > 0 ? k - 1 : 0) + lane; i < j; i += 32) {
+              const C h = i == j - 1 ? colv[b * R1 + k] : hr[i];
+              const C sv = h1[b * R1 + i];
+              cr += h.re * sv.re - h.im * sv.im;
+              ci += h.re * sv.im + h.im * sv.re;
+            }
+            cr = warp_sum(cr);
+            ci = warp_sum(ci);
+            if (lane == 0)
+              hc_next[(int64_t)b * R1 + k] = ccast<double>(invr[b] * (h2[b * R1 + k] - mkc<TV>(cr, ci)));
+          } else if (lane == 0) {
+            hc_next[(int64_t)b * R1 + k] = ccast<double>(j >= 1 ? gam[b] - h1[b * R1 + j - 1] : gam[b]);
+          }
+        }
+      }
+      __syncthreads();
+      // B4: rotations of column j-1, residual estimate and activity (every CTA, same values)
       if (threadIdx.x < R && act[threadIdx.x]) {
         const int b = threadIdx.x;
-        C* col = colv + b * R1;
-        const TV h = sqrt(nrm2[b]);
-        for (int i = 0; i < j; ++i) {
-          const C x0 = col[i], x1 = col[i + 1];
-          const C s = sn[b * RS + i];
-          const TV c = cs[b * RS + i];
-          col[i] = c * x0 + s * x1;
-          col[i + 1] = mkc<TV>(-s.re, s.im) * x0 + c * x1;
-        }
-        const C x = col[j];
-        const TV ax2 = x.re * x.re + x.im * x.im;
-        const TV aa = sqrt(ax2);
-        const TV nu = sqrt(ax2 + h * h);
-        const TV inu = TV(1) / nu;
-        TV c;
-        C sv;
-        if (aa == TV(0)) {
-          c = TV(0);
-          sv = mkc<TV>(1, 0);
+        const TV h = rho_s[b];
+        if (j >= 1) {
+          const int l = j - 1;
+          C* col = colv + b * R1;
+          for (int i = 0; i < l; ++i) {
+            const C x0 = col[i], x1 = col[i + 1];
+            const C sg = sn[b * RS + i];
+            const TV c = cs[b * RS + i];
+            col[i] = c * x0 + sg * x1;
+            col[i + 1] = mkc<TV>(-sg.re, sg.im) * x0 + c * x1;
+          }
+          const C x = col[l];
+          const TV ax2 = x.re * x.re + x.im * x.im;
+          const TV aa = sqrt(ax2);
+          const TV nu = sqrt(ax2 + h * h);
+          const TV inu = TV(1) / nu;
+          TV c;
+          C sv;
+          if (aa == TV(0)) {
+            c = TV(0);
+            sv = mkc<TV>(1, 0);
+          } else {
+            c = aa * inu;
+            const TV f = h * inu / aa;
+            sv = mkc<TV>(x.re * f, x.im * f);
+          }
+          cs[b * RS + l] = c;
+          sn[b * RS + l] = sv;
+          col[l] = c * x + h * sv;
+          const C gl = gg[b * R1 + l];
+          gg[b * R1 + l + 1] = mkc<TV>(-sv.re, sv.im) * gl;
+          gg[b * R1 + l] = c * gl;
+          // |g_{l+1}| = |s_l| |g_l| with |s_l| = h / nu
+          const double res = resid[b] * (double)(h * inu);
+          resid[b] = res;
+          jl[b] = j;
+          if (!isfinite(h) || !isfinite(res)) {
+            s_numeric = 1;
+            act[b] = 0;
+          } else if (res <= P.tol || h == TV(0)) {
+            act[b] = 0;
+          }
         } else {
-          c = aa * inu;
-          const TV f = h * inu / aa;
-          sv = mkc<TV>(x.re * f, x.im * f);
+          gg[b * R1] = mkc<TV>(h, TV(0));
+          if (!isfinite(h)) s_numeric = 1;
+          if (!(h > TV(0)) || !isfinite(h)) act[b] = 0;
         }
-        cs[b * RS + j] = c;
-        sn[b * RS + j] = sv;
-        col[j] = c * x + h * sv;
-        const C gj = gg[b * R1 + j];
-        gg[b * R1 + j + 1] = mkc<TV>(-sv.re, sv.im) * gj;
-        gg[b * R1 + j] = c * gj;
-        // |g_{j+1}| = |s_j| |g_j| with |s_j| = h / nu
-        const double res = resid[b] * (double)(h * inu);
-        resid[b] = res;
-        jl[b] = j + 1;
-        if (!isfinite(h) || !isfinite(res)) {
-          s_numeric = 1;
-          act[b] = 0;
-        } else if (res <= P.tol || h == TV(0)) {
-          act[b] = 0;
-        }
-        inv[b] = h > TV(0) ? TV(1) / h : TV(0);
       }
       __syncthreads();
-      if (blockIdx.x == 0)
-        for (int k = threadIdx.x; k < R * (j + 1); k += kPT) {
-          const int b = k / (j + 1), i = k % (j + 1);
-          if (jl[b] == j + 1) P.H[(int64_t)b * R1 * RS + i * RS + j] = ccast<double>(colv[b * R1 + i]);
+      if (blockIdx.x == 0 && j >= 1)
+        for (int k = threadIdx.x; k < R * j; k += kPT) {
+          const int b = k / j, i = k % j;
+          if (jl[b] == j) P.H[(int64_t)b * R1 * RS + i * RS + j - 1] = ccast<double>(colv[b * R1 + i]);
         }
       if (threadIdx.x == 0) {
         int any = 0;
         for (int b = 0; b < R; ++b) any |= act[b];
         s_j = j + 1;
-        s_iters += 1;
-        s_done = (!any || j + 1 >= RS || s_iters >= a.max_iter) ? 1 : 0;
+        if (j >= 1) s_iters += 1;
+        s_done = (!any || closing) ? 1 : 0;
       }
       __syncthreads();
+      if (s_done) break;
+      // B5: q_j to V_j and the next pending vector (own rows and W), then the barrier that makes
+      // W whole for the next gather
+      p_update2<TV, RB>(V, ys, ws, a.rows, cnt, n0, N, R, R1, j, act, h1, h2, invr, gam, W);
+      if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
     }
     if (!ok) break;
   }
@@ -704,11 +797,12 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   SWM_CK(cudaFuncGetAttributes(&fa, fn));
   const size_t limit = (size_t)std::max(0, ctx->smem_optin - (int)fa.sharedSizeBytes - 1024);
   const size_t cb = sizeof(cplx<TV>), eb = sizeof(TE);
-  // V in shared memory when it fits (it is read four times a step); then as large an E slice as
+  // V in shared memory when it fits (it is read twice a step); then as large an E slice as
   // the rest holds (column map + gathered vector about a third of the E entries: the rows of a
   // wire share their column map).  A CTA whose slice is larger reads E from global memory.
-  const int vsm = persist_layout(RB, R, restart, prows, cb, eb, 1, 0, 0, 0).total <= limit ? 1 : 0;
-  const size_t base = persist_layout(RB, R, restart, prows, cb, eb, vsm, 1, 0, 0).total + 64;
+  const int hown = (int)ceil_div(restart + 1, G);
+  const int vsm = persist_layout(RB, R, restart, prows, hown, cb, eb, 1, 0, 0, 0).total <= limit ? 1 : 0;
+  const size_t base = persist_layout(RB, R, restart, prows, hown, cb, eb, vsm, 1, 0, 0).total + 64;
   const int64_t mean_e = ceil_div(ctx->offd.nval, G);
   int64_t emax = 0, cmax = 0;
   if (base < limit) {
@@ -717,7 +811,7 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   }
   const int esm = emax >= mean_e && emax > 0 ? 1 : 0;
   if (!esm) emax = cmax = 0;
-  const size_t smem = persist_layout(RB, R, restart, prows, cb, eb, vsm, esm, emax, cmax).total;
+  const size_t smem = persist_layout(RB, R, restart, prows, hown, cb, eb, vsm, esm, emax, cmax).total;
   if (smem > limit) return SWM_OK;
   int occ = 0;
   SWM_CK(allow_max_dyn_smem(fn, ctx->smem_optin));
