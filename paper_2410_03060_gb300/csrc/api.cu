@@ -65,23 +65,96 @@ static void release_all(swm_ctx* ctx) {
 
 namespace {
 
-// Per-wire input checks; flags: 1 NaN/Inf, 2 non-unit direction, 4 length, 8 radius, 16 segments.
-__global__ void k_validate(int64_t nw, const double* __restrict__ c, const double* __restrict__ t,
-                           const double* __restrict__ L, const double* __restrict__ a, const int32_t* __restrict__ ns,
-                           int* __restrict__ flags, int* __restrict__ max_ns) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nw) return;
-  int f = 0;
-  for (int d = 0; d < 3; ++d)
-    if (!isfinite(c[3 * i + d]) || !isfinite(t[3 * i + d])) f |= 1;
-  if (!isfinite(L[i]) || !isfinite(a[i])) f |= 1;
-  const double tn = t[3 * i] * t[3 * i] + t[3 * i + 1] * t[3 * i + 1] + t[3 * i + 2] * t[3 * i + 2];
-  if (!(fabs(tn - 1.0) <= 2e-9)) f |= 2;
-  if (!(L[i] > 0.0)) f |= 4;
-  if (!(a[i] > 0.0)) f |= 8;
-  if (ns[i] < 2 || ns[i] > kMaxSeg) f |= 16;
-  if (f) atomicOr(flags, f);
-  atomicMax(max_ns, ns[i]);
+// One pass over the caller's wires: copy them into the context's buffers (when the caller's are
+// device buffers; host inputs were copied before), check them, and per CTA the bounding box of the
+// centres, the check flags (1 NaN/Inf, 2 non-unit direction, 4 length, 8 radius, 16 segments) and
+// the largest segment count, part[blk][8] = {min xyz, max xyz, flags, max ns}.
+constexpr int kIngestThreads = 256;
+__global__ void __launch_bounds__(kIngestThreads) k_ingest(int64_t nw, const double* __restrict__ sc,
+                                                           const double* __restrict__ st,
+                                                           const double* __restrict__ sL,
+                                                           const double* __restrict__ sa,
+                                                           const int32_t* __restrict__ sns, int copy, double* c,
+                                                           double* t, double* L, double* a, int32_t* ns,
+                                                           double* __restrict__ part) {
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int f = 0, mns = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x) {
+    double cc[3], tt[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cc[d] = sc[3 * i + d];
+      tt[d] = st[3 * i + d];
+    }
+    const double Li = sL[i], ai = sa[i];
+    const int ni = sns[i];
+    if (copy) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        c[3 * i + d] = cc[d];
+        t[3 * i + d] = tt[d];
+      }
+      L[i] = Li;
+      a[i] = ai;
+      ns[i] = ni;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (!isfinite(cc[d]) || !isfinite(tt[d])) f |= 1;
+      mn[d] = fmin(mn[d], cc[d]);
+      mx[d] = fmax(mx[d], cc[d]);
+    }
+    if (!isfinite(Li) || !isfinite(ai)) f |= 1;
+    const double tn = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
+    if (!(fabs(tn - 1.0) <= 2e-9)) f |= 2;
+    if (!(Li > 0.0)) f |= 4;
+    if (!(ai > 0.0)) f |= 8;
+    if (ni < 2 || ni > kMaxSeg) f |= 16;
+    mns = max(mns, ni);
+  }
+  __shared__ double s[8][kIngestThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+      mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+    }
+    f |= __shfl_xor_sync(0xffffffffu, f, o);
+    mns = max(mns, __shfl_xor_sync(0xffffffffu, mns, o));
+  }
+  if (lane == 0) {
+    for (int d = 0; d < 3; ++d) {
+      s[d][w] = mn[d];
+      s[3 + d][w] = mx[d];
+    }
+    s[6][w] = (double)f;
+    s[7][w] = (double)mns;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int d = threadIdx.x;
+    double v = s[d][0];
+    for (int k = 1; k < kIngestThreads / 32; ++k) {
+      const double x = s[d][k];
+      v = d < 3 ? fmin(v, x) : d < 6 ? fmax(v, x) : d == 6 ? (double)((int)v | (int)x) : fmax(v, x);
+    }
+    part[blockIdx.x * 8 + d] = v;
+  }
+}
+
+// The CTA partials of k_ingest combined: res[8] = {min xyz, max xyz, flags, max ns}.
+__global__ void k_ingest_final(const double* __restrict__ part, int np, double* __restrict__ res) {
+  if (threadIdx.x < 8) {
+    const int d = threadIdx.x;
+    double v = part[d];
+    for (int k = 1; k < np; ++k) {
+      const double x = part[k * 8 + d];
+      v = d < 3 ? fmin(v, x) : d < 6 ? fmax(v, x) : d == 6 ? (double)((int)v | (int)x) : fmax(v, x);
+    }
+    res[d] = v;
+  }
 }
 
 // Internal [R][N] currents (any precision) -> caller [R][N] complex128 in caller unknown order.
@@ -250,26 +323,32 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_L, sizeof(double) * nw));
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_a, sizeof(double) * nw));
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_ns, sizeof(int32_t) * nw));
-  SWM_TRY(copy_in(ctx, ctx->u_c, centres, sizeof(double) * 3 * nw, mem_kind));
-  SWM_TRY(copy_in(ctx, ctx->u_t, dirs, sizeof(double) * 3 * nw, mem_kind));
-  SWM_TRY(copy_in(ctx, ctx->u_L, lengths, sizeof(double) * nw, mem_kind));
-  SWM_TRY(copy_in(ctx, ctx->u_a, radii, sizeof(double) * nw, mem_kind));
-  SWM_TRY(copy_in(ctx, ctx->u_ns, nseg, sizeof(int32_t) * nw, mem_kind));
+  if (mem_kind == SWM_HOST) {  // device inputs are copied by k_ingest itself
+    SWM_TRY(copy_in(ctx, ctx->u_c, centres, sizeof(double) * 3 * nw, mem_kind));
+    SWM_TRY(copy_in(ctx, ctx->u_t, dirs, sizeof(double) * 3 * nw, mem_kind));
+    SWM_TRY(copy_in(ctx, ctx->u_L, lengths, sizeof(double) * nw, mem_kind));
+    SWM_TRY(copy_in(ctx, ctx->u_a, radii, sizeof(double) * nw, mem_kind));
+    SWM_TRY(copy_in(ctx, ctx->u_ns, nseg, sizeof(int32_t) * nw, mem_kind));
+  }
+  const bool dev = mem_kind == SWM_DEVICE;
   std::vector<Buf> tmp;
-  int* flags = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&flags, 2 * sizeof(int)));
-  SWM_CK(cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx->stream));
-  k_validate<<<(unsigned)ceil_div(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a,
-                                                                   ctx->u_ns, flags, flags + 1);
+  const int np = (int)std::min<int64_t>(ceil_div(nw, kIngestThreads), 2 * std::max(ctx->nsm, 1));
+  double* part = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * 8 * (np + 1)));
+  double* res = part + 8 * np;
+  k_ingest<<<(unsigned)np, kIngestThreads, 0, ctx->stream>>>(
+      nw, dev ? centres : ctx->u_c, dev ? dirs : ctx->u_t, dev ? lengths : ctx->u_L, dev ? radii : ctx->u_a,
+      dev ? nseg : ctx->u_ns, dev ? 1 : 0, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a, ctx->u_ns, part);
   SWM_LAUNCHED();
-  double* bb = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&bb, sizeof(double) * 6));
-  SWM_TRY(cloud_bbox_async(ctx, bb, tmp));
-  int hf[2] = {0, 0};
-  SWM_CK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, ctx->stream));
-  SWM_CK(cudaMemcpyAsync(ctx->bbox, bb, sizeof(ctx->bbox), cudaMemcpyDeviceToHost, ctx->stream));
+  k_ingest_final<<<1, 32, 0, ctx->stream>>>(part, np, res);
+  SWM_LAUNCHED();
+  SWM_TRY(ensure_poll_slots(ctx));
+  double* hres = reinterpret_cast<double*>(static_cast<char*>(ctx->pinned_state) + kIngestSlotOffset);
+  SWM_CK(cudaMemcpyAsync(hres, res, sizeof(double) * 8, cudaMemcpyDeviceToHost, ctx->stream));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   dfree_group(ctx, tmp);
+  for (int d = 0; d < 6; ++d) ctx->bbox[d] = hres[d];
+  const int hf[2] = {(int)hres[6], (int)hres[7]};
   if (hf[0]) {
     std::string m = "invalid cloud:";
     if (hf[0] & 1) m += " non-finite value;";
@@ -484,8 +563,9 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
     SWM_CK(cudaMemcpyAsync(obs_dev, obs, sizeof(double) * 2 * n_obs, cudaMemcpyHostToDevice, ctx->stream));
     stride = 2;
   }
-  const size_t sb = ctx->prec == SWM_C64 ? far_field_f32_scratch_bytes(ctx->nw, npairs)
-                                        : far_field_scratch_bytes(ctx->nw, npairs);
+  const size_t sb = ctx->prec == SWM_C64
+                        ? far_field_f32_scratch_bytes(ctx->nw, npairs, mono ? R : n_obs)
+                        : far_field_scratch_bytes(ctx->nw, npairs);
   void* scratch = nullptr;
   SWM_TRY(dalloc(ctx, tmp, &scratch, sb));
   double* sig = nullptr;

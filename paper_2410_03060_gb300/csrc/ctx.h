@@ -236,7 +236,6 @@ int build_pattern(swm_ctx* ctx);
 // copy n device int64 values to the host with one synchronisation
 int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst);
 // launch the bounding-box reduction of the caller centres into out6 (device)
-int cloud_bbox_async(swm_ctx* ctx, double* out6, std::vector<Buf>& tmp);
 // caller-order unknown offsets, made on first use
 int ensure_user_offsets(swm_ctx* ctx);
 // precond.cu: read the build's deferred device flags and counters
@@ -254,7 +253,7 @@ int build_precond(swm_ctx* ctx);
 // rhs_ff.cu: a4 + a7
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* inc_dev);
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs);
-size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs);
+size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs, int n_obs);
 int prepare_far_field(swm_ctx* ctx);
 int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_stride, bool mono, double* sigma,
                          void* scratch, size_t scratch_bytes);
@@ -286,8 +285,10 @@ inline cudaError_t allow_max_dyn_smem(const void* fn, int smem_optin) {
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)fa.sharedSizeBytes);
 }
-// two pinned host slots (kPollSlotBytes in all) for polling the solvers' device state
-constexpr size_t kPollSlotBytes = 128;
+// pinned host memory of a context: two slots (128 bytes in all) for polling the solvers' device
+// state, then the 64-byte result of the cloud checks
+constexpr size_t kPollSlotBytes = 256;
+constexpr size_t kIngestSlotOffset = 128;
 int ensure_poll_slots(swm_ctx* ctx);
 int apply_minv(swm_ctx* ctx, const void* Y);
 // gcr.cu: the paper's GCR solver (alternative to GMRES)

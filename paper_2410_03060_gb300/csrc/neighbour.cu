@@ -21,47 +21,6 @@ struct Grid {
   int nx, ny, nz;
 };
 
-__global__ void k_bbox_partial(const double* __restrict__ c, int64_t nw, double* __restrict__ part) {
-  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double v = c[3 * i + d];
-      mn[d] = fmin(mn[d], v);
-      mx[d] = fmax(mx[d], v);
-    }
-  }
-  __shared__ double s[6][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    for (int o = 16; o > 0; o >>= 1) {
-      mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
-      mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
-    }
-    if (lane == 0) {
-      s[d][w] = mn[d];
-      s[3 + d][w] = mx[d];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    const int d = threadIdx.x;
-    double v = s[d][0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = d < 3 ? fmin(v, s[d][k]) : fmax(v, s[d][k]);
-    part[blockIdx.x * 6 + d] = v;
-  }
-}
-
-__global__ void k_bbox_final(const double* __restrict__ part, int np, double* __restrict__ out) {
-  if (threadIdx.x < 6) {
-    const int d = threadIdx.x;
-    double v = part[d];
-    for (int k = 1; k < np; ++k) v = d < 3 ? fmin(v, part[k * 6 + d]) : fmax(v, part[k * 6 + d]);
-    out[d] = v;
-  }
-}
-
 __device__ __forceinline__ int cell_coord(double v, double v0, double h, int n) {
   int i = (int)floor((v - v0) / h);
   return min(max(i, 0), n - 1);
@@ -314,18 +273,6 @@ int alloc_layout(swm_ctx* ctx, Layout& lay, int32_t* K, int32_t* colpos) {
 }
 
 }  // namespace
-
-int cloud_bbox_async(swm_ctx* ctx, double* out6, std::vector<Buf>& tmp) {
-  const int64_t nw = ctx->nw;
-  const int nbb = (int)std::min<int64_t>(1024, nblk(nw, 256));
-  double* part = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * 6 * nbb));
-  k_bbox_partial<<<nbb, 256, 0, ctx->stream>>>(ctx->u_c, nw, part);
-  SWM_LAUNCHED();
-  k_bbox_final<<<1, 32, 0, ctx->stream>>>(part, nbb, out6);
-  SWM_LAUNCHED();
-  return SWM_OK;
-}
 
 int ensure_user_offsets(swm_ctx* ctx) {
   if (ctx->uoff) return SWM_OK;

@@ -214,15 +214,17 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial(Geo geo, int64_t nw,
   out[2] = mkc(F[4], F[5]);
 }
 
-// One warp per (incidence, observation) pair: sum the chunk partials, then sigma.
-__global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict__ partial, int n_obs,
-                             const double* __restrict__ obs, int obs_stride, int mono, double* __restrict__ sigma) {
+// One warp per (incidence, observation) pair: sum the chunk partials, then sigma.  Partial (c, e)
+// is at partial + (c * cstride + e * estride) * 3.
+__global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict__ partial, int64_t cstride,
+                             int64_t estride, int n_obs, const double* __restrict__ obs, int obs_stride, int mono,
+                             double* __restrict__ sigma) {
   const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (e >= npairs) return;
   double F[6] = {0, 0, 0, 0, 0, 0};
   for (int c = lane; c < nchunks; c += 32) {
-    const c128* in = partial + ((int64_t)c * npairs + e) * 3;
+    const c128* in = partial + ((int64_t)c * cstride + e * estride) * 3;
     for (int d = 0; d < 3; ++d) {
       F[2 * d] += in[d].re;
       F[2 * d + 1] += in[d].im;
@@ -240,17 +242,16 @@ __global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict
 }
 
 // Per-wire data of the float32 far field: the centre in cycles, c k / (2 pi), split into a float
-// and its float remainder, the direction and the length.
+// and its float remainder, the direction, the rooftop half-width D = L / n and the first rooftop
+// centre s_1 = -L / 2 + D.
 struct FFWire {
-  float ch[3], cl[3], t[3], L;
+  float ch[3], cl[3], t[3], D, s1, pad;
 };
-constexpr int kFFChunkMax = 64;   // wires per chunk of the float32 far field
-constexpr int kFFCurMax = 1024;   // staged currents per chunk
 
 __global__ void k_ff_wires(int64_t nw, const double* __restrict__ cx, const double* __restrict__ cy,
                            const double* __restrict__ cz, const double* __restrict__ tx, const double* __restrict__ ty,
-                           const double* __restrict__ tz, const double* __restrict__ Ls, double k,
-                           FFWire* __restrict__ out) {
+                           const double* __restrict__ tz, const double* __restrict__ Ls,
+                           const int32_t* __restrict__ ns, double k, FFWire* __restrict__ out) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= nw) return;
   const double s = k / (2.0 * kPi);
@@ -263,33 +264,106 @@ __global__ void k_ff_wires(int64_t nw, const double* __restrict__ cx, const doub
   w.t[0] = (float)tx[p];
   w.t[1] = (float)ty[p];
   w.t[2] = (float)tz[p];
-  w.L = (float)Ls[p];
+  const double D = Ls[p] / ns[p];
+  w.D = (float)D;
+  w.s1 = (float)(-0.5 * Ls[p] + D);
+  w.pad = 0.f;
   out[p] = w;
+}
+
+// Observation frame of the float32 far field, formed once per observation: the direction r, split
+// into float hi/lo parts for the centre phase and in float64, and theta_hat, phi_hat in float64
+// for the final projection.
+struct FFObs {
+  double r[3], th[3], ph[3];
+  float rhi[3], rlo[3];
+};
+
+__global__ void k_ff_obs(int n, const double* __restrict__ obs, int obs_stride, FFObs* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  FFObs f;
+  obs_frame(obs, obs_stride, o, f.r, f.th, f.ph);
+  for (int i = 0; i < 3; ++i) {
+    f.rhi[i] = (float)f.r[i];
+    f.rlo[i] = (float)(f.r[i] - (double)f.rhi[i]);
+  }
+  out[o] = f;
+}
+
+// Sum of the chunk partials of each (incidence, observation) pair (one warp each, partial[c][e][3],
+// complex64: the partials are float32 sums), four float accumulators per lane and component, then
+// sigma in float64 with the frames of k_ff_obs.
+__global__ void k_far_reduce_f32(int64_t npairs, int nchunks, const c64* __restrict__ partial, int n_obs, int mono,
+                                 const FFObs* __restrict__ frames, double* __restrict__ sigma) {
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= npairs) return;
+  float A[4][6];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 6; ++d) A[a][d] = 0.f;
+  int c = lane;
+  for (; c + 96 < nchunks; c += 128) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const c64* in = partial + ((int64_t)(c + 32 * a) * npairs + e) * 3;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const c64 v = in[d];
+        A[a][2 * d] += v.re;
+        A[a][2 * d + 1] += v.im;
+      }
+    }
+  }
+  for (; c < nchunks; c += 32) {
+    const c64* in = partial + ((int64_t)c * npairs + e) * 3;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const c64 v = in[d];
+      A[0][2 * d] += v.re;
+      A[0][2 * d + 1] += v.im;
+    }
+  }
+  double F[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) F[d] = (double)warp_sum((A[0][d] + A[1][d]) + (A[2][d] + A[3][d]));
+  if (lane != 0) return;
+  const FFObs& f = frames[mono ? (int)e : (int)(e % n_obs)];
+  const double tr = f.th[0] * F[0] + f.th[1] * F[2] + f.th[2] * F[4];
+  const double ti = f.th[0] * F[1] + f.th[1] * F[3] + f.th[2] * F[5];
+  const double pr = f.ph[0] * F[0] + f.ph[1] * F[2] + f.ph[2] * F[4];
+  const double pi = f.ph[0] * F[1] + f.ph[1] * F[3] + f.ph[2] * F[5];
+  sigma[2 * e] = (tr * tr + ti * ti) / kFourPi;
+  sigma[2 * e + 1] = (pr * pr + pi * pi) / kFourPi;
 }
 
 // float32 far field.  The centre phase k r.c = 2 pi (r . c k / 2 pi) is formed modulo one cycle
 // from the hi/lo splits of r and of the centre in cycles: each hi*hi product is split exactly
 // into p + e with an FMA, and p - rint(p) is exact, so the phase keeps ~1e-7 cycles however far
-// the wire is from the origin.
+// the wire is from the origin.  The currents' progression along a wire is summed in Horner form,
+// sum_l J_l z0 q^l = z0 (J_0 + q (J_1 + q (...))).  One thread per (incidence, observation) pair
+// and chunk of wires; the CTA stages the chunk's wire data (and, with one incidence, its currents)
+// in shared memory.  Partials partial[chunk][e][3], complex64.
+constexpr int kFFChunkMax = 64;   // wires per chunk of the float32 far field
+constexpr int kFFCurMax = 1024;   // staged currents per chunk
 __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __restrict__ wires,
                                                                 const int32_t* __restrict__ ns,
                                                                 const int64_t* __restrict__ off, int64_t nw, int64_t N,
                                                                 float k, int n_rhs, const c64* __restrict__ cur,
-                                                                int n_obs, const double* __restrict__ obs,
-                                                                int obs_stride, int mono, int64_t chunk,
-                                                                c128* __restrict__ partial) {
+                                                                int n_obs, const FFObs* __restrict__ frames, int mono,
+                                                                int64_t chunk, c64* __restrict__ partial) {
   const int64_t npairs = mono ? n_rhs : (int64_t)n_rhs * n_obs;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t p0 = blockIdx.y * chunk, p1 = min(nw, p0 + chunk);
   const int64_t ec = e < npairs ? e : npairs - 1;  // threads past the end help stage, then leave
   const int r = mono ? (int)ec : (int)(ec / n_obs);
   const int o = mono ? (int)ec : (int)(ec % n_obs);
-  double rh[3], th[3], ph[3];
-  obs_frame(obs, obs_stride, o, rh, th, ph);
   float rhi[3], rlo[3];
   for (int i = 0; i < 3; ++i) {
-    rhi[i] = (float)rh[i];
-    rlo[i] = (float)(rh[i] - (double)rhi[i]);
+    rhi[i] = frames[o].rhi[i];
+    rlo[i] = frames[o].rlo[i];
   }
   const float two_pi = 6.28318530717958647692f;
   // the chunk's wires and their currents, staged once per CTA
@@ -324,21 +398,22 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
     }
     fr -= rintf(fr);
     const int n = sn[q];
-    const float D = w.L / (float)n;
     const float beta = k * (rhi[0] * w.t[0] + rhi[1] * w.t[1] + rhi[2] * w.t[2]);
-    const float s1 = -0.5f * w.L + D;
     float sa, ca, sb, cb;
-    __sincosf(fmaf(two_pi, fr, beta * s1), &sa, &ca);
-    __sincosf(beta * D, &sb, &cb);
-    const float sc = sinc_f(0.5f * beta * D);
+    __sincosf(fmaf(two_pi, fr, beta * w.s1), &sa, &ca);
+    __sincosf(beta * w.D, &sb, &cb);
+    const float sc = sinc_f(0.5f * beta * w.D);
     const c64* Jp = stage_cur ? sJ + soff[q] : J + soff[q];
-    c64 z = mkc(ca, sa), acc = mkc(0.f, 0.f);
     const c64 rat = mkc(cb, sb);
-    for (int l = 0; l < n - 1; ++l) {
-      cfma(acc, Jp[l], z);
-      z = z * rat;
+    c64 h = Jp[n - 2];
+    for (int l = n - 3; l >= 0; --l) {
+      const c64 Jl = Jp[l];
+      const c64 hv = h;
+      h.re = fmaf(hv.re, rat.re, fmaf(-hv.im, rat.im, Jl.re));
+      h.im = fmaf(hv.re, rat.im, fmaf(hv.im, rat.re, Jl.im));
     }
-    const float amp = D * sc * sc;
+    const c64 acc = mkc(ca, sa) * h;
+    const float amp = w.D * sc * sc;
     const float Sr = amp * acc.re, Si = amp * acc.im;
     F[0] = fmaf(w.t[0], Sr, F[0]);
     F[1] = fmaf(w.t[0], Si, F[1]);
@@ -347,10 +422,10 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
     F[4] = fmaf(w.t[2], Sr, F[4]);
     F[5] = fmaf(w.t[2], Si, F[5]);
   }
-  c128* out = partial + ((int64_t)blockIdx.y * npairs + e) * 3;
-  out[0] = mkc((double)F[0], (double)F[1]);
-  out[1] = mkc((double)F[2], (double)F[3]);
-  out[2] = mkc((double)F[4], (double)F[5]);
+  c64* out = partial + ((int64_t)blockIdx.y * npairs + e) * 3;
+  out[0] = mkc(F[0], F[1]);
+  out[1] = mkc(F[2], F[3]);
+  out[2] = mkc(F[4], F[5]);
 }
 
 }  // namespace
@@ -365,11 +440,22 @@ static void ff_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& chun
   nchunks = ceil_div(nw, chunk);
 }
 
+// Launch shape of the float32 far field: that of the float64 one, with at most kFFChunkMax wires
+// per chunk (the size of the CTA's staging arrays).
+static void ff32_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& chunk) {
+  ff_shape(nw, npairs, nchunks, chunk);
+  if (chunk > kFFChunkMax) {
+    chunk = kFFChunkMax;
+    nchunks = ceil_div(nw, chunk);
+  }
+}
+
+
 int prepare_far_field(swm_ctx* ctx) {
   if (ctx->prec != SWM_C64) return SWM_OK;
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->ffw, sizeof(FFWire) * ctx->nw));
   k_ff_wires<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, ctx->stream>>>(ctx->nw, ctx->cx, ctx->cy, ctx->cz, ctx->tx,
-                                                                        ctx->ty, ctx->tz, ctx->L, ctx->k,
+                                                                        ctx->ty, ctx->tz, ctx->L, ctx->ns, ctx->k,
                                                                         (FFWire*)ctx->ffw);
   SWM_LAUNCHED();
   return SWM_OK;
@@ -380,20 +466,21 @@ int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_str
   const int R = ctx->n_rhs;
   const int64_t npairs = mono ? R : (int64_t)R * n_obs;
   int64_t nchunks, chunk;
-  ff_shape(ctx->nw, npairs, nchunks, chunk);
-  if (chunk > kFFChunkMax) {
-    chunk = kFFChunkMax;
-    nchunks = ceil_div(ctx->nw, chunk);
-  }
-  if ((size_t)nchunks * npairs * 3 * sizeof(c128) > scratch_bytes)
+  ff32_shape(ctx->nw, npairs, nchunks, chunk);
+  const size_t part_bytes = (size_t)nchunks * npairs * 3 * sizeof(c64);
+  if (part_bytes + sizeof(FFObs) * (size_t)n_obs > scratch_bytes)
     return ctx->fail(SWM_EINVAL, "far field: scratch too small");
+  c64* part = (c64*)scratch;
+  FFObs* frames = reinterpret_cast<FFObs*>((char*)scratch + part_bytes);  // part_bytes is a multiple of 8
+  k_ff_obs<<<(unsigned)ceil_div(n_obs, 128), 128, 0, ctx->stream>>>(n_obs, obs, obs_stride, frames);
+  SWM_LAUNCHED();
   dim3 grid((unsigned)ceil_div(npairs, kFFThreads), (unsigned)nchunks);
   k_far_partial_f32<<<grid, kFFThreads, 0, ctx->stream>>>((const FFWire*)ctx->ffw, ctx->ns, ctx->off, ctx->nw, ctx->N,
-                                                          (float)ctx->k, R, (const c64*)ctx->Xv, n_obs, obs,
-                                                          obs_stride, mono, chunk, (c128*)scratch);
+                                                          (float)ctx->k, R, (const c64*)ctx->Xv, n_obs, frames, mono,
+                                                          chunk, part);
   SWM_LAUNCHED();
-  k_far_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, ctx->stream>>>(npairs, (int)nchunks, (c128*)scratch,
-                                                                              n_obs, obs, obs_stride, mono, sigma);
+  k_far_reduce_f32<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, ctx->stream>>>(npairs, (int)nchunks, part, n_obs,
+                                                                                  mono, frames, sigma);
   SWM_LAUNCHED();
   return SWM_OK;
 }
@@ -423,11 +510,10 @@ int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out
   return SWM_OK;
 }
 
-size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs) {
+size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs, int n_obs) {
   int64_t nchunks, chunk;
-  ff_shape(nw, npairs, nchunks, chunk);
-  if (chunk > kFFChunkMax) nchunks = ceil_div(nw, kFFChunkMax);
-  return (size_t)nchunks * npairs * 3 * sizeof(c128);
+  ff32_shape(nw, npairs, nchunks, chunk);
+  return (size_t)nchunks * npairs * 3 * sizeof(c64) + sizeof(FFObs) * (size_t)n_obs;
 }
 
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs) {
@@ -480,8 +566,8 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
     *err = std::string("far field launch: ") + cudaGetErrorString(e);
     return SWM_ECUDA;
   }
-  k_far_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, st>>>(npairs, (int)nchunks, part, n_obs, obs,
-                                                                     obs_stride, mono, sigma);
+  k_far_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, st>>>(npairs, (int)nchunks, part, npairs, 1, n_obs,
+                                                                     obs, obs_stride, mono, sigma);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("far field reduce launch: ") + cudaGetErrorString(e);
