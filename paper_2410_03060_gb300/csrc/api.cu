@@ -144,17 +144,18 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(int64_t nw, const dou
   }
 }
 
-// The CTA partials of k_ingest combined: res[8] = {min xyz, max xyz, flags, max ns}.
-__global__ void k_ingest_final(const double* __restrict__ part, int np, double* __restrict__ res) {
-  if (threadIdx.x < 8) {
-    const int d = threadIdx.x;
-    double v = part[d];
-    for (int k = 1; k < np; ++k) {
-      const double x = part[k * 8 + d];
-      v = d < 3 ? fmin(v, x) : d < 6 ? fmax(v, x) : d == 6 ? (double)((int)v | (int)x) : fmax(v, x);
-    }
-    res[d] = v;
-  }
+// The CTA partials of k_ingest combined: res[8] = {min xyz, max xyz, flags, max ns}, warp d for
+// field d (all of a lane's partials loaded together, then a shuffle tree).
+__global__ void __launch_bounds__(256) k_ingest_final(const double* __restrict__ part, int np, double* __restrict__ res) {
+  const int d = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto comb = [d](double v, double x) {
+    return d < 3 ? fmin(v, x) : d < 6 ? fmax(v, x) : d == 6 ? (double)((int)v | (int)x) : fmax(v, x);
+  };
+  double v = part[d];  // np >= 1
+  for (int k = lane; k < np; k += 32) v = comb(v, part[k * 8 + d]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = comb(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) res[d] = v;
 }
 
 // Internal [R][N] currents (any precision) -> caller [R][N] complex128 in caller unknown order.
@@ -340,7 +341,7 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
       nw, dev ? centres : ctx->u_c, dev ? dirs : ctx->u_t, dev ? lengths : ctx->u_L, dev ? radii : ctx->u_a,
       dev ? nseg : ctx->u_ns, dev ? 1 : 0, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a, ctx->u_ns, part);
   SWM_LAUNCHED();
-  k_ingest_final<<<1, 32, 0, ctx->stream>>>(part, np, res);
+  k_ingest_final<<<1, 256, 0, ctx->stream>>>(part, np, res);
   SWM_LAUNCHED();
   SWM_TRY(ensure_poll_slots(ctx));
   double* hres = reinterpret_cast<double*>(static_cast<char*>(ctx->pinned_state) + kIngestSlotOffset);

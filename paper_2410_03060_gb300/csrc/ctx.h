@@ -234,7 +234,7 @@ void dfree_group(swm_ctx* ctx, std::vector<Buf>& group);
 // neighbour.cu: a0 + a1 (sort by cell, numbering, S-NFC pattern, layouts)
 int build_pattern(swm_ctx* ctx);
 // copy n device int64 values to the host with one synchronisation
-int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst);
+int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst, std::vector<Buf>& tmp);
 // launch the bounding-box reduction of the caller centres into out6 (device)
 // caller-order unknown offsets, made on first use
 int ensure_user_offsets(swm_ctx* ctx);
