@@ -177,6 +177,21 @@ int copy_in(swm_ctx* ctx, void* dst, const void* src, size_t bytes, int kind) {
   return SWM_OK;
 }
 
+// A small host input copied to the device through the context's pinned staging area (no staged
+// pageable copy); inputs that do not fit are copied directly.
+int upload(swm_ctx* ctx, void* dst, const void* src, size_t bytes, size_t* used) {
+  SWM_TRY(ensure_poll_slots(ctx));
+  if (*used + bytes <= kPinnedUpBytes) {
+    char* stage = static_cast<char*>(ctx->pinned_state) + kPinnedUpOffset + *used;
+    std::memcpy(stage, src, bytes);
+    SWM_CK(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *used += (bytes + 15) & ~size_t(15);
+    return SWM_OK;
+  }
+  SWM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return SWM_OK;
+}
+
 int set_device(swm_ctx* ctx) {
   SWM_CK(cudaSetDevice(ctx->device));
   return SWM_OK;
@@ -474,8 +489,9 @@ static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, in
   SWM_TRY(dalloc(ctx, S, (void**)&frames, sizeof(double) * 6 * n_inc));
   std::vector<double> fh;
   frames_host(inc, n_inc, fh);
-  SWM_CK(cudaMemcpyAsync(ctx->inc_dev, inc, sizeof(double) * 3 * n_inc, cudaMemcpyHostToDevice, ctx->stream));
-  SWM_CK(cudaMemcpyAsync(frames, fh.data(), sizeof(double) * 6 * n_inc, cudaMemcpyHostToDevice, ctx->stream));
+  size_t staged = 0;
+  SWM_TRY(upload(ctx, ctx->inc_dev, inc, sizeof(double) * 3 * n_inc, &staged));
+  SWM_TRY(upload(ctx, frames, fh.data(), sizeof(double) * 6 * n_inc, &staged));
   ctx->phase_begin(swm_ctx::PH_RHS);
   SWM_TRY(compute_rhs(ctx, n_inc, frames));
   ctx->phase_end(swm_ctx::PH_RHS);
@@ -561,7 +577,8 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
   int stride = 3;
   if (!mono) {
     SWM_TRY(dalloc(ctx, tmp, (void**)&obs_dev, sizeof(double) * 2 * n_obs));
-    SWM_CK(cudaMemcpyAsync(obs_dev, obs, sizeof(double) * 2 * n_obs, cudaMemcpyHostToDevice, ctx->stream));
+    size_t staged = 0;
+    SWM_TRY(upload(ctx, obs_dev, obs, sizeof(double) * 2 * n_obs, &staged));
     stride = 2;
   }
   const size_t sb = ctx->prec == SWM_C64

@@ -285,10 +285,20 @@ inline cudaError_t allow_max_dyn_smem(const void* fn, int smem_optin) {
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)fa.sharedSizeBytes);
 }
-// pinned host memory of a context: two slots (128 bytes in all) for polling the solvers' device
-// state, then the 64-byte result of the cloud checks
-constexpr size_t kPollSlotBytes = 256;
+// pinned host memory of a context (small copies without a staged pageable copy): two slots (128
+// bytes in all) for polling the solvers' device state, 64 bytes for the cloud checks and the
+// pattern sizes, the persistent solve's state and abort flag, up to kPinnedResidMax float64 values
+// read back (relative residuals, build counters), and a staging area for small uploads
+// (incidences, observation angles).  Every entry point ends with a stream synchronisation, so an
+// area is never rewritten while a copy from it is pending.
+constexpr size_t kPollSlotBytes = 65536;
 constexpr size_t kIngestSlotOffset = 128;
+constexpr size_t kPersistStateOffset = 192;
+constexpr size_t kPersistAbortOffset = 240;
+constexpr size_t kPinnedResidOffset = 256;
+constexpr size_t kPinnedUpOffset = 32768;
+constexpr size_t kPinnedUpBytes = kPollSlotBytes - kPinnedUpOffset;
+constexpr int kPinnedResidMax = (int)((kPinnedUpOffset - kPinnedResidOffset) / sizeof(double));
 int ensure_poll_slots(swm_ctx* ctx);
 int apply_minv(swm_ctx* ctx, const void* Y);
 // gcr.cu: the paper's GCR solver (alternative to GMRES)

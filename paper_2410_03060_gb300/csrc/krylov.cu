@@ -784,10 +784,10 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   int cycles = 0;
   // small systems: the whole solve as one persistent cooperative kernel
   bool persisted = false;
+  SWM_TRY(ensure_poll_slots(ctx));
   {
     PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0};
     SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
-    if (persisted) cycles = hs.cycles;
   }
   const dim3 g_rows((unsigned)ceil_div(N * kG, kRows), R);
   const dim3 g_chunk((unsigned)P.nchunk, R);
@@ -939,8 +939,10 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, U, first ? 1 : 0);
     SWM_LAUNCHED();
     first = false;
-    SWM_CK(cudaMemcpyAsync(&hs, P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    KState* hpin = reinterpret_cast<KState*>(static_cast<char*>(ctx->pinned_state) + kPersistStateOffset);
+    SWM_CK(cudaMemcpyAsync(hpin, P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
     SWM_CK(cudaStreamSynchronize(st));
+    hs = *hpin;
     if (hs.all_conv || hs.numeric || hs.iters >= max_iter) break;
     // the cycle's Arnoldi steps and its closing pass
     const int steps = std::min(restart, max_iter - hs.iters) + 1;
@@ -967,18 +969,30 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     SWM_LAUNCHED();
     ++cycles;
   }
-  if (hs_out) *hs_out = hs;
   if (y_out) {  // inner solve of the refinement: the result stays in y-space
+    if (persisted) {
+      SWM_CK(cudaStreamSynchronize(st));
+      SWM_TRY(persist_result(ctx, &hs));
+    }
+    if (hs_out) *hs_out = hs;
     *y_out = Y;
     dfree_group(ctx, tmp);
     if (hs.numeric) return ctx->fail(SWM_ECUDA, "GMRES produced a non-finite value");
     return hs.all_conv ? SWM_OK : SWM_ENOTCONV;
   }
-  // x = M^-1 y
+  // x = M^-1 y, then one synchronisation for the residuals (and the persistent solve's state)
   SWM_TRY(apply_minv(ctx, Y));
   std::vector<double> res(R);
-  SWM_CK(cudaMemcpyAsync(res.data(), P.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  double* rpin = reinterpret_cast<double*>(static_cast<char*>(ctx->pinned_state) + kPinnedResidOffset);
+  const bool rp = R <= kPinnedResidMax;
+  SWM_CK(cudaMemcpyAsync(rp ? rpin : res.data(), P.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
   SWM_CK(cudaStreamSynchronize(st));
+  if (rp) std::memcpy(res.data(), rpin, sizeof(double) * R);
+  if (persisted) {
+    SWM_TRY(persist_result(ctx, &hs));
+    cycles = hs.cycles;
+  }
+  if (hs_out) *hs_out = hs;
   dfree_group(ctx, tmp);
   double mx = 0.0;
   for (double v : res) mx = std::max(mx, v);

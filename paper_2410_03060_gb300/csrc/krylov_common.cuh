@@ -79,8 +79,11 @@ struct PBuffers {
 constexpr int kPersistMaxR = 8;  // right-hand sides of one persistent solve
 
 // Runs the whole restarted GMRES as one cooperative kernel when the system is small enough
-// (sets *done); otherwise leaves *done false and launches nothing.
+// (sets *done); otherwise leaves *done false and launches nothing.  The final state is read back
+// asynchronously: after the stream's next synchronisation persist_result() gives it (and
+// SWM_ETIMEOUT if a grid barrier ran out of time).
 template <typename TV, typename TE>
 int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& B, int max_iter, KState* hs, bool* done);
+int persist_result(swm_ctx* ctx, KState* hs);
 
 }  // namespace swm

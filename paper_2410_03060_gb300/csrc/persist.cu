@@ -1,6 +1,7 @@
 // Persistent cooperative GMRES (the whole restarted solve in one launch) for small systems.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "krylov_common.cuh"
 
@@ -845,12 +846,23 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   SWM_CK(cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kPT), args, smem, st));
   ctx->prof_end(SWM_K_GMRES);
   SWM_LAUNCHED();
-  PSync hsync{};
-  SWM_CK(cudaMemcpyAsync(hs, P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
-  SWM_CK(cudaMemcpyAsync(&hsync, Bf.sync, sizeof(PSync), cudaMemcpyDeviceToHost, st));
-  SWM_CK(cudaStreamSynchronize(st));
-  if (hsync.abort) return ctx->fail(SWM_ETIMEOUT, "GMRES: a grid barrier of the persistent solve timed out");
+  // the final state and the abort flag go to pinned memory; the caller reads them after its next
+  // synchronisation (persist_result)
+  SWM_TRY(ensure_poll_slots(ctx));
+  char* pin = static_cast<char*>(ctx->pinned_state);
+  SWM_CK(cudaMemcpyAsync(pin + kPersistStateOffset, P.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  SWM_CK(cudaMemcpyAsync(pin + kPersistAbortOffset, &Bf.sync->abort, sizeof(int), cudaMemcpyDeviceToHost, st));
   *done = true;
+  (void)hs;
+  return SWM_OK;
+}
+
+int persist_result(swm_ctx* ctx, KState* hs) {
+  const char* pin = static_cast<const char*>(ctx->pinned_state);
+  std::memcpy(hs, pin + kPersistStateOffset, sizeof(KState));
+  int abort = 0;
+  std::memcpy(&abort, pin + kPersistAbortOffset, sizeof(int));
+  if (abort) return ctx->fail(SWM_ETIMEOUT, "GMRES: a grid barrier of the persistent solve timed out");
   return SWM_OK;
 }
 

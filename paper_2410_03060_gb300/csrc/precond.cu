@@ -3,6 +3,7 @@
 // E_pq = Z_pq Z_qq^-1 for the kept off-diagonal blocks; E is stored (layout `offd`) so that each
 // Krylov step is one block-sparse product plus the identity, and x = M^-1 y at the end.
 #include <algorithm>
+#include <cstring>
 
 #include <cuda_bf16.h>
 
@@ -230,11 +231,15 @@ int make_e16(swm_ctx* ctx) {
 }
 
 int finish_build(swm_ctx* ctx) {
+  SWM_TRY(ensure_poll_slots(ctx));
+  char* pin = static_cast<char*>(ctx->pinned_state) + kPinnedResidOffset;
+  SWM_CK(cudaMemcpyAsync(pin, ctx->d_evals, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaMemcpyAsync(pin + 8, ctx->d_sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
   unsigned long long evals = 0;
   int sing = 0;
-  SWM_CK(cudaMemcpyAsync(&evals, ctx->d_evals, sizeof(evals), cudaMemcpyDeviceToHost, ctx->stream));
-  SWM_CK(cudaMemcpyAsync(&sing, ctx->d_sing, sizeof(sing), cudaMemcpyDeviceToHost, ctx->stream));
-  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(&evals, pin, sizeof(evals));
+  std::memcpy(&sing, pin + 8, sizeof(sing));
   ctx->stats.fill_evals = (int64_t)evals;
   if (sing) return ctx->fail(SWM_EINVAL, "a self block is singular (degenerate wire geometry?)");
   return SWM_OK;
