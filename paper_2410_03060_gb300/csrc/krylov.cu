@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "ctx.h"
@@ -41,36 +42,6 @@ constexpr int kMaxChunk = 2048;  // rows per CTA of the Gram-Schmidt kernels, at
 template <typename T>
 __device__ __forceinline__ bool finite_c(cplx<T> z) {
   return isfinite((double)z.re) && isfinite((double)z.im);
-}
-
-// Residual of the current y, the first vector of a cycle: U = B - (Y + E Y).
-template <typename TV, typename TE>
-__global__ void __launch_bounds__(kRows) k_residual(KPtr P, const int32_t* __restrict__ rowwire,
-                                                    const int64_t* __restrict__ off, Layout lay,
-                                                    const TE* __restrict__ E, const cplx<TV>* __restrict__ B,
-                                                    const cplx<TV>* __restrict__ Y, cplx<TV>* __restrict__ U) {
-  const int64_t n = (blockIdx.x * (int64_t)kRows + threadIdx.x) / kG;
-  const int sub = threadIdx.x % kG;
-  const int r = blockIdx.y;
-  const int64_t N = P.N;
-  const bool row_ok = n < N;
-  const cplx<TV>* src = Y + (int64_t)r * N;
-  cplx<TV> acc = mkc<TV>(0, 0);
-  if (row_ok) {
-    const int64_t p = rowwire[n];
-    const int i = (int)(n - off[p]);
-    const int K = lay.K[p];
-    const int64_t vb = lay.rowbase[p] + (int64_t)i * K;
-    const int32_t* cm = lay.colmap + lay.cmbase[p];
-    for (int c = sub; c < K; c += kG) cfma(acc, ELoad<TV, TE>::ld(E + vb + c), src[cm[c]]);
-  }
-#pragma unroll
-  for (int o = kG / 2; o > 0; o >>= 1) {
-    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
-    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
-  }
-  if (!row_ok || sub != 0) return;
-  U[(int64_t)r * N + n] = B[(int64_t)r * N + n] - (src[n] + acc);
 }
 
 // Last CTA of right-hand side r to arrive at the end of a pass.
@@ -122,11 +93,14 @@ __device__ __forceinline__ double sum_partials_d(const double* __restrict__ base
 // Product w = u + E u for the active right-hand sides, streaming: one scalar row per group of eight
 // lanes, RB right-hand sides sharing every read of E, no shared memory and no barrier, so many
 // rows' loads are in flight.
-template <typename TV, typename TE, int RB>
+// With RES (the residual at the start of a cycle) every right-hand side takes part, the source
+// is Y and the result W = B - (y + E y).
+template <typename TV, typename TE, int RB, bool RES = false>
 __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restrict__ rinfo,
                                                 const int32_t* __restrict__ colmap, const TE* __restrict__ E,
-                                                const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Wv) {
-  if (P.st->cycle_done || P.st->j >= P.st->jmax) return;
+                                                const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Wv,
+                                                const cplx<TV>* __restrict__ B = nullptr) {
+  if (!RES && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   const int r0 = blockIdx.y * RB;
   const int nr = min(RB, P.R - r0);
   const int64_t N = P.N;
@@ -136,7 +110,7 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
   bool any = false;
 #pragma unroll
   for (int b = 0; b < RB; ++b) {
-    act[b] = b < nr && P.active[r0 + b];
+    act[b] = b < nr && (RES || P.active[r0 + b]);
     any |= act[b];
   }
   if (!any) return;  // the same for the whole CTA
@@ -180,7 +154,7 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
     for (int b = 0; b < RB; ++b) {
       if (b >= nr) break;
       const int64_t o = (int64_t)(r0 + b) * N + n;
-      if (act[b]) Wv[o] = U[o] + acc[b];
+      if (act[b]) Wv[o] = RES ? B[o] - (U[o] + acc[b]) : U[o] + acc[b];
     }
   }
 }
@@ -189,9 +163,9 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
 // [R][N]) copied to right-hand-side minor order Xt[N][R] through shared-memory tiles of 32 rows x
 // 32 right-hand sides, so that the product below reads the values of all right-hand sides at a
 // column as one contiguous run.
-template <typename TV>
+template <typename TV, bool RES = false>
 __global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Xt) {
-  if (P.st->cycle_done || P.st->j >= P.st->jmax) return;
+  if (!RES && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   __shared__ cplx<TV> tile[32][33];
   const int64_t n0 = (int64_t)blockIdx.x * 32;
   const int r0 = blockIdx.y * 32;
@@ -214,18 +188,19 @@ __global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __res
 // values of the gathered column as one contiguous run of Xt.  A CTA covers 32 rows; its results go
 // through shared memory so that w is written right-hand-side major as runs of 32 consecutive rows.
 constexpr int kTileRows = 32;
-template <typename TV, typename TE, int RB>
+template <typename TV, typename TE, int RB, bool RES = false>
 __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restrict__ rinfo,
                                                 const int32_t* __restrict__ colmap, const TE* __restrict__ E,
-                                                const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ Wv) {
-  if (P.st->cycle_done || P.st->j >= P.st->jmax) return;
+                                                const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ Wv,
+                                                const cplx<TV>* __restrict__ B = nullptr) {
+  if (!RES && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   __shared__ cplx<TV> ys[kTileRows][RB + 1];
   const int64_t N = P.N;
   const int R = P.R;
   const int64_t n0 = (int64_t)blockIdx.x * kTileRows;
   const int lr = (int)(threadIdx.x % RB);  // right-hand side within the block
   const int r = blockIdx.y * RB + lr;
-  const bool on = r < R && P.active[r];
+  const bool on = r < R && (RES || P.active[r]);
   constexpr int kGroups = 256 / RB;  // rows per pass
   for (int t = (int)(threadIdx.x / RB); t < kTileRows; t += kGroups) {
     const int64_t n = n0 + t;
@@ -256,8 +231,9 @@ __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restric
   const int64_t n = n0 + lane;
   for (int b = w; b < RB; b += 8) {
     const int rr = blockIdx.y * RB + b;
-    if (rr >= R || n >= N || !P.active[rr]) continue;
-    Wv[(int64_t)rr * N + n] = ys[lane][b];
+    if (rr >= R || n >= N || (!RES && !P.active[rr])) continue;
+    const int64_t o = (int64_t)rr * N + n;
+    Wv[o] = RES ? B[o] - ys[lane][b] : ys[lane][b];
   }
 }
 
@@ -549,6 +525,7 @@ __global__ void __launch_bounds__(kRows) k_cycle_start(KPtr P, const cplx<TV>* _
   const int cnt = (int)min((int64_t)P.chunk, P.N - n0);
   const cplx<TV>* w = U + (int64_t)r * P.N + n0;
   double s = 0.0;
+#pragma unroll 4
   for (int t = threadIdx.x; t < cnt; t += kRows) s += (double)w[t].re * w[t].re + (double)w[t].im * w[t].im;
   __shared__ double red[kRows / 32];
   s = warp_sum(s);
@@ -789,7 +766,6 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0};
     SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
   }
-  const dim3 g_rows((unsigned)ceil_div(N * kG, kRows), R);
   const dim3 g_chunk((unsigned)P.nchunk, R);
   const bool multi = R > 1;
   const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
@@ -798,27 +774,35 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   // the first time its shape is solved, and kept.
   constexpr int kMinor = 32;
   int rb = multi ? 8 : 1;
-  auto launch_product = [&](cudaStream_t s, int b) -> int {
+  // res: the residual U = B - A Y of a cycle's start in the same form (every right-hand side)
+  auto product = [&](cudaStream_t s, int b, auto res_tag) -> int {
+    constexpr bool RS = decltype(res_tag)::value;
+    const cplx<TV>* src = RS ? Y : U;
+    cplx<TV>* dst = RS ? U : Wv;
     const dim3 gsp((unsigned)ceil_div(N * kG, kRows), (unsigned)ceil_div(R, std::min(b, 16)));
     switch (b) {
-      case 1: k_spmv<TV, TE, 1><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
-      case 4: k_spmv<TV, TE, 4><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
-      case 16: k_spmv<TV, TE, 16><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
+      case 1: k_spmv<TV, TE, 1, RS><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, src, dst, Bv); break;
+      case 4: k_spmv<TV, TE, 4, RS><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, src, dst, Bv); break;
+      case 16: k_spmv<TV, TE, 16, RS><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, src, dst, Bv); break;
       case kMinor: {
-        k_rhs_minor<TV><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, U, ws->Xt);
+        k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, src, ws->Xt);
         SWM_LAUNCHED();
         const unsigned gx = (unsigned)ceil_div(N, kTileRows);
         if (R >= 24)
-          k_spmv_t<TV, TE, 32><<<dim3(gx, (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, Wv);
+          k_spmv_t<TV, TE, 32, RS><<<dim3(gx, (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E,
+                                                                                       ws->Xt, dst, Bv);
         else
-          k_spmv_t<TV, TE, 16><<<dim3(gx, (unsigned)ceil_div(R, 16)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E, ws->Xt, Wv);
+          k_spmv_t<TV, TE, 16, RS><<<dim3(gx, (unsigned)ceil_div(R, 16)), 256, 0, s>>>(P, ri, ctx->offd.colmap, E,
+                                                                                       ws->Xt, dst, Bv);
         break;
       }
-      default: k_spmv<TV, TE, 8><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, U, Wv); break;
+      default: k_spmv<TV, TE, 8, RS><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, src, dst, Bv); break;
     }
     SWM_LAUNCHED();
     return SWM_OK;
   };
+  auto launch_product = [&](cudaStream_t s, int b) { return product(s, b, std::false_type{}); };
+  auto launch_residual = [&](cudaStream_t s, int b) { return product(s, b, std::true_type{}); };
   const size_t dots_smem = 2 * sizeof(cplx<TV>) * (size_t)P.chunk;
   if (dots_smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_dots<TV>, ctx->smem_optin));
   // back substitution stages the triangle in shared memory when it fits
@@ -857,8 +841,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     } else {
       // first cycle's residual and start (the loop below repeats them; both are idempotent), then
       // each candidate product once untimed and once timed; the product is idempotent
-      k_residual<TV, TE><<<g_rows, kRows, 0, st>>>(P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, U);
-      SWM_LAUNCHED();
+      SWM_TRY(launch_residual(st, rb));
       k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, U, first ? 1 : 0);
       SWM_LAUNCHED();
       cudaEvent_t e0, e1;
@@ -933,9 +916,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   while (!persisted) {
     // residual of the current y and the start of a cycle
     ctx->prof_begin(SWM_K_APPLY);
-    k_residual<TV, TE><<<g_rows, kRows, 0, st>>>(P, ctx->rowwire, ctx->off, ctx->offd, E, Bv, Y, U);
+    SWM_TRY(launch_residual(st, rb));
     ctx->prof_end(SWM_K_APPLY);
-    SWM_LAUNCHED();
     k_cycle_start<TV><<<g_chunk, kRows, 0, st>>>(P, U, first ? 1 : 0);
     SWM_LAUNCHED();
     first = false;
