@@ -3,13 +3,57 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
 #include "ctx.h"
 
 namespace swm {
+
+namespace {
+std::mutex g_fn_mutex;
+std::map<std::pair<const void*, int>, size_t> g_fn_static;              // (kernel, device) -> static smem
+std::map<std::tuple<const void*, int, int, size_t>, int> g_fn_occupancy;  // (kernel, device, threads, smem)
+}  // namespace
+
+cudaError_t allow_max_dyn_smem(const void* fn, int smem_optin, size_t* static_bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_fn_mutex);
+  auto it = g_fn_static.find({fn, dev});
+  if (it == g_fn_static.end()) {
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    it = g_fn_static.emplace(std::make_pair(fn, dev), (size_t)fa.sharedSizeBytes).first;
+  }
+  if (static_bytes) *static_bytes = it->second;
+  return cudaSuccess;
+}
+
+cudaError_t occupancy_cached(const void* fn, int threads, size_t smem, int* blocks) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_fn_mutex);
+  const auto key = std::make_tuple(fn, dev, threads, smem);
+  auto it = g_fn_occupancy.find(key);
+  if (it == g_fn_occupancy.end()) {
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    it = g_fn_occupancy.emplace(key, b).first;
+  }
+  *blocks = it->second;
+  return cudaSuccess;
+}
 
 int dalloc(swm_ctx* ctx, std::vector<Buf>& group, void** out, size_t bytes) {
   bytes = std::max<size_t>((bytes + 255) / 256 * 256, 256);

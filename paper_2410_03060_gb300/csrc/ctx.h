@@ -279,12 +279,14 @@ int norms_of_b(swm_ctx* ctx, const void* B, bool f64, double* bnorm_dev);
 // (smem_optin less its static shared memory).  Always the same value for a kernel, so contexts
 // driven from several host threads do not undo each other's setting of this process-wide
 // attribute; a launch that asks for less is unaffected.
-inline cudaError_t allow_max_dyn_smem(const void* fn, int smem_optin) {
-  cudaFuncAttributes fa{};
-  const cudaError_t e = cudaFuncGetAttributes(&fa, fn);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)fa.sharedSizeBytes);
-}
+// Sets a kernel's dynamic shared-memory limit to all the device allows beside its static shared
+// memory.  The attribute is process-wide and every caller sets the same value, so contexts on
+// concurrent host threads cannot undo one another; it is set once per kernel and device (api.cu
+// keeps the table) and the kernel's static shared memory is returned through *static_bytes.
+cudaError_t allow_max_dyn_smem(const void* fn, int smem_optin, size_t* static_bytes = nullptr);
+// Resident CTAs per SM of a kernel at a block size and dynamic shared memory, queried once per
+// kernel, device and shape.
+cudaError_t occupancy_cached(const void* fn, int threads, size_t smem, int* blocks);
 // pinned host memory of a context (small copies without a staged pageable copy): two slots (128
 // bytes in all) for polling the solvers' device state, 64 bytes for the cloud checks and the
 // pattern sizes, the persistent solve's state and abort flag, up to kPinnedResidMax float64 values

@@ -794,9 +794,9 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   const int G = (int)ceil_div(N, prows);
   const int RB = R == 1 ? 1 : kPersistMaxR;
   const void* fn = R == 1 ? (const void*)k_gmres_persist<TV, TE, 1> : (const void*)k_gmres_persist<TV, TE, kPersistMaxR>;
-  cudaFuncAttributes fa{};
-  SWM_CK(cudaFuncGetAttributes(&fa, fn));
-  const size_t limit = (size_t)std::max(0, ctx->smem_optin - (int)fa.sharedSizeBytes - 1024);
+  size_t static_smem = 0;
+  SWM_CK(allow_max_dyn_smem(fn, ctx->smem_optin, &static_smem));
+  const size_t limit = (size_t)std::max(0, ctx->smem_optin - (int)static_smem - 1024);
   const size_t cb = sizeof(cplx<TV>), eb = sizeof(TE);
   // V in shared memory when it fits (it is read twice a step); then as large an E slice as
   // the rest holds (column map + gathered vector about a third of the E entries: the rows of a
@@ -815,8 +815,7 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   const size_t smem = persist_layout(RB, R, restart, prows, hown, cb, eb, vsm, esm, emax, cmax).total;
   if (smem > limit) return SWM_OK;
   int occ = 0;
-  SWM_CK(allow_max_dyn_smem(fn, ctx->smem_optin));
-  SWM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPT, smem));
+  SWM_CK(occupancy_cached(fn, kPT, smem, &occ));
   if (occ < 1 || G > occ * ctx->nsm) return SWM_OK;
   PArgs pa{};
   pa.P = P;
