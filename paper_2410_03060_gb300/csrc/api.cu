@@ -341,6 +341,12 @@ void swm_destroy(swm_ctx* ctx) {
   if (ctx->pinned_state) cudaFreeHost(ctx->pinned_state);
   if (ctx->gm_exec) cudaGraphExecDestroy(ctx->gm_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  for (auto ev : ctx->side_ev)
+    if (ev) cudaEventDestroy(ev);
   release_all(ctx);
   cudaStreamSynchronize(ctx->stream);
   delete ctx;
@@ -369,6 +375,7 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   if (mem_kind != SWM_HOST && mem_kind != SWM_DEVICE) return ctx->fail(SWM_EINVAL, "bad mem_kind");
   SWM_TRY(set_device(ctx));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->side) SWM_CK(cudaStreamSynchronize(ctx->side));
   dfree_group(ctx, ctx->solve_bufs);
   dfree_group(ctx, ctx->build_bufs);
   dfree_group(ctx, ctx->pattern_bufs);
@@ -436,6 +443,7 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
     return ctx->fail(SWM_EINVAL, "bad precision");
   SWM_TRY(set_device(ctx));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->side) SWM_CK(cudaStreamSynchronize(ctx->side));  // idle unless an earlier build failed midway
   dfree_group(ctx, ctx->solve_bufs);
   dfree_group(ctx, ctx->build_bufs);
   ctx->built = ctx->solved = false;
@@ -464,11 +472,33 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   }
   ctx->stats.pattern_reused = reuse ? 1 : 0;
   ctx->phase_end(swm_ctx::PH_NEIGHBOUR);
+  // The self blocks and their inverses run on a second stream beside the mutual blocks (they
+  // touch disjoint parts of Z); E is formed once both are done.  A profiled self-block or inverse
+  // class stays on the context's stream so that its events time it.
+  SWM_TRY(fill_alloc(ctx));
+  SWM_TRY(precond_alloc(ctx));
+  const bool side = ctx->prof_cls != SWM_K_FILL_SELF && ctx->prof_cls != SWM_K_INVERT;
+  if (side && !ctx->side) {
+    SWM_CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    SWM_CK(cudaEventCreateWithFlags(&ctx->side_ev[0], cudaEventDisableTiming));
+    SWM_CK(cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming));
+  }
+  cudaStream_t s2 = side ? ctx->side : ctx->stream;
   ctx->phase_begin(swm_ctx::PH_FILL);
-  SWM_TRY(fill_blocks(ctx));
+  if (side) {
+    SWM_CK(cudaEventRecord(ctx->side_ev[0], ctx->stream));
+    SWM_CK(cudaStreamWaitEvent(s2, ctx->side_ev[0], 0));
+  }
+  SWM_TRY(fill_self(ctx, s2));
+  SWM_TRY(precond_invert(ctx, s2));
+  SWM_TRY(fill_mutual(ctx));
   ctx->phase_end(swm_ctx::PH_FILL);
   ctx->phase_begin(swm_ctx::PH_PRECOND);
-  SWM_TRY(build_precond(ctx));
+  if (side) {
+    SWM_CK(cudaEventRecord(ctx->side_ev[1], s2));
+    SWM_CK(cudaStreamWaitEvent(ctx->stream, ctx->side_ev[1], 0));
+  }
+  SWM_TRY(precond_form_E(ctx));
   if (ctx->bf16) SWM_TRY(make_e16(ctx));
   ctx->phase_end(swm_ctx::PH_PRECOND);
   SWM_TRY(prepare_far_field(ctx));

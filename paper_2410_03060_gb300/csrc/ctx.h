@@ -137,6 +137,8 @@ struct swm_ctx {
   cudaGraphExec_t gm_exec = nullptr;      // captured chunk of GMRES steps and its argument key
   std::vector<unsigned char> gm_key;
   cudaStream_t cap_stream = nullptr;      // private stream for graph capture
+  cudaStream_t side = nullptr;            // second stream of the build (self blocks and their inverses)
+  cudaEvent_t side_ev[2] = {nullptr, nullptr};  // fork and join of the side stream
   // systems with at least this many unknowns run the Arnoldi step as a streaming product plus
   // separate dots (bandwidth); smaller ones as one fused kernel (latency).  SWM_SPLIT_ROWS overrides.
   int64_t split_rows = int64_t(1) << 19;
@@ -247,9 +249,13 @@ int exclusive_scan_i32_to_i64(swm_ctx* ctx, const int32_t* in, int64_t* out, int
 int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const int* is64, int64_t* const* out,
                          int64_t n);
 // fill.cu: a2 + a3
-int fill_blocks(swm_ctx* ctx);
+int fill_alloc(swm_ctx* ctx);
+int fill_self(swm_ctx* ctx, cudaStream_t s);
+int fill_mutual(swm_ctx* ctx);
 // precond.cu: a5
-int build_precond(swm_ctx* ctx);
+int precond_alloc(swm_ctx* ctx);
+int precond_invert(swm_ctx* ctx, cudaStream_t s);
+int precond_form_E(swm_ctx* ctx);
 // rhs_ff.cu: a4 + a7
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* inc_dev);
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs);

@@ -716,25 +716,37 @@ int launch_fill(swm_ctx* ctx, const GLTable& gl, unsigned long long* evals) {
   return SWM_OK;
 }
 
-int fill_blocks(swm_ctx* ctx) {
-  static const GLTable gl = make_gl();
-  const int64_t nw = ctx->nw;
+// Z and the evaluation counter, allocated and cleared on the context's stream.
+int fill_alloc(swm_ctx* ctx) {
   const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Z, esz * std::max<int64_t>(1, ctx->full.nval)));
   SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->d_evals, sizeof(unsigned long long)));
   SWM_CK(cudaMemsetAsync(ctx->d_evals, 0, sizeof(unsigned long long), ctx->stream));
+  return SWM_OK;
+}
+
+// The self blocks (diagonal of Z), on stream s.
+int fill_self(swm_ctx* ctx, cudaStream_t s) {
+  static const GLTable gl = make_gl();
+  const int64_t nw = ctx->nw;
   int S = 2;
   while (S < ctx->max_ns) S <<= 1;
   const unsigned grid_self = (unsigned)ceil_div(nw, kSelfThreads / S);
   ctx->prof_begin(SWM_K_FILL_SELF);
   if (ctx->prec == SWM_C128)
-    k_self_blocks<double, double><<<grid_self, kSelfThreads, 0, ctx->stream>>>(
+    k_self_blocks<double, double><<<grid_self, kSelfThreads, 0, s>>>(
         nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b, ctx->full, S, reinterpret_cast<c128*>(ctx->Z));
   else
-    k_self_blocks<float, float><<<grid_self, kSelfThreads, 0, ctx->stream>>>(
+    k_self_blocks<float, float><<<grid_self, kSelfThreads, 0, s>>>(
         nw, ctx->L, ctx->a, ctx->ns, ctx->k, gl, ctx->diag_b, ctx->full, S, reinterpret_cast<c64*>(ctx->Z));
   ctx->prof_end(SWM_K_FILL_SELF);
   SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+// The mutual blocks (off-diagonal of Z), on the context's stream.
+int fill_mutual(swm_ctx* ctx) {
+  static const GLTable gl = make_gl();
   if (ctx->prec == SWM_C128) {
     SWM_TRY((launch_fill<double, double>(ctx, gl, ctx->d_evals)));
   } else if (ctx->nup > 0) {

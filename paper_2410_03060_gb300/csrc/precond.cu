@@ -176,40 +176,46 @@ __global__ void k_form_E(int64_t nb, const int32_t* __restrict__ col, const int6
 
 }  // namespace
 
-int build_precond(swm_ctx* ctx) {
-  const int64_t nw = ctx->nw;
+// M^-1, E and the singularity flag, allocated and cleared on the context's stream.
+int precond_alloc(swm_ctx* ctx) {
   const size_t esz = ctx->prec == SWM_C128 ? sizeof(c128) : sizeof(c64);
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Minv, esz * std::max<int64_t>(1, ctx->nminv)));
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->Zp, esz * std::max<int64_t>(1, ctx->offd.nval)));
   SWM_TRY(dalloc(ctx, ctx->build_bufs, (void**)&ctx->d_sing, sizeof(int)));
   SWM_CK(cudaMemsetAsync(ctx->d_sing, 0, sizeof(int), ctx->stream));
+  return SWM_OK;
+}
+
+// M^-1 = blockdiag(Z_pp)^-1 from the self blocks, on stream s.
+int precond_invert(swm_ctx* ctx, cudaStream_t s) {
+  const int64_t nw = ctx->nw;
   const unsigned g1 = (unsigned)ceil_div(nw, 4);
+  ctx->prof_begin(SWM_K_INVERT);
+  if (ctx->prec == SWM_C128)
+    k_invert_self_entries<double, double><<<g1, 128, 0, s>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
+                                                             ctx->minv_off, (c128*)ctx->Minv, ctx->d_sing);
+  else
+    k_invert_self<float, float><<<g1, 128, 0, s>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c64*)ctx->Z,
+                                                   ctx->minv_off, (c64*)ctx->Minv, ctx->d_sing);
+  ctx->prof_end(SWM_K_INVERT);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+// E = Z M^-1 off the diagonal, on the context's stream (after the fill and the inversion).
+int precond_form_E(swm_ctx* ctx) {
   const unsigned g2 = (unsigned)std::max<int64_t>(1, ceil_div(ctx->nb * 32, 256));
-  if (ctx->prec == SWM_C128) {
-    ctx->prof_begin(SWM_K_INVERT);
-    k_invert_self_entries<double, double><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c128*)ctx->Z,
-                                                               ctx->minv_off, (c128*)ctx->Minv, ctx->d_sing);
-    ctx->prof_end(SWM_K_INVERT);
-    SWM_LAUNCHED();
-    ctx->prof_begin(SWM_K_FORM_E);
+  ctx->prof_begin(SWM_K_FORM_E);
+  if (ctx->prec == SWM_C128)
     k_form_E<double><<<g2, 256, 0, ctx->stream>>>(ctx->nb, ctx->col, ctx->bt, ctx->m, ctx->full, ctx->offd,
                                                   (const c128*)ctx->Z, ctx->minv_off, (const c128*)ctx->Minv,
                                                   (c128*)ctx->Zp);
-    ctx->prof_end(SWM_K_FORM_E);
-    SWM_LAUNCHED();
-  } else {
-    ctx->prof_begin(SWM_K_INVERT);
-    k_invert_self<float, float><<<g1, 128, 0, ctx->stream>>>(nw, ctx->m, ctx->diag_b, ctx->full, (const c64*)ctx->Z,
-                                                             ctx->minv_off, (c64*)ctx->Minv, ctx->d_sing);
-    ctx->prof_end(SWM_K_INVERT);
-    SWM_LAUNCHED();
-    ctx->prof_begin(SWM_K_FORM_E);
+  else
     k_form_E<float><<<g2, 256, 0, ctx->stream>>>(ctx->nb, ctx->col, ctx->bt, ctx->m, ctx->full, ctx->offd,
                                                  (const c64*)ctx->Z, ctx->minv_off, (const c64*)ctx->Minv,
                                                  (c64*)ctx->Zp);
-    ctx->prof_end(SWM_K_FORM_E);
-    SWM_LAUNCHED();
-  }
+  ctx->prof_end(SWM_K_FORM_E);
+  SWM_LAUNCHED();
   return SWM_OK;
 }
 
