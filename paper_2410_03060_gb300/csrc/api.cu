@@ -458,6 +458,11 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->prec = precision == SWM_BF16 ? SWM_C64 : precision;
   ctx->bf16 = precision == SWM_BF16;
   ctx->E16 = nullptr;
+  if (!ctx->side) {  // the build's second stream (pattern column maps, self blocks, far-field data)
+    SWM_CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    SWM_CK(cudaEventCreateWithFlags(&ctx->side_ev[0], cudaEventDisableTiming));
+    SWM_CK(cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming));
+  }
   ctx->phase_begin(swm_ctx::PH_NEIGHBOUR);
   if (!reuse) {
     dfree_group(ctx, ctx->pattern_bufs);
@@ -477,12 +482,8 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   // class stays on the context's stream so that its events time it.
   SWM_TRY(fill_alloc(ctx));
   SWM_TRY(precond_alloc(ctx));
+  SWM_TRY(far_field_alloc(ctx));  // every buffer the second stream writes exists before the fork
   const bool side = ctx->prof_cls != SWM_K_FILL_SELF && ctx->prof_cls != SWM_K_INVERT;
-  if (side && !ctx->side) {
-    SWM_CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
-    SWM_CK(cudaEventCreateWithFlags(&ctx->side_ev[0], cudaEventDisableTiming));
-    SWM_CK(cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming));
-  }
   cudaStream_t s2 = side ? ctx->side : ctx->stream;
   ctx->phase_begin(swm_ctx::PH_FILL);
   if (side) {
@@ -491,6 +492,7 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   }
   SWM_TRY(fill_self(ctx, s2));
   SWM_TRY(precond_invert(ctx, s2));
+  SWM_TRY(prepare_far_field(ctx, s2));
   SWM_TRY(fill_mutual(ctx));
   ctx->phase_end(swm_ctx::PH_FILL);
   ctx->phase_begin(swm_ctx::PH_PRECOND);
@@ -501,7 +503,6 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   SWM_TRY(precond_form_E(ctx));
   if (ctx->bf16) SWM_TRY(make_e16(ctx));
   ctx->phase_end(swm_ctx::PH_PRECOND);
-  SWM_TRY(prepare_far_field(ctx));
   SWM_TRY(finish_build(ctx));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->phase_collect();

@@ -260,7 +260,8 @@ int precond_form_E(swm_ctx* ctx);
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* inc_dev);
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs);
 size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs, int n_obs);
-int prepare_far_field(swm_ctx* ctx);
+int far_field_alloc(swm_ctx* ctx);
+int prepare_far_field(swm_ctx* ctx, cudaStream_t s);
 int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_stride, bool mono, double* sigma,
                          void* scratch, size_t scratch_bytes);
 int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64, const void* cur, int64_t nw,

@@ -445,20 +445,31 @@ int build_pattern(swm_ctx* ctx) {
   ctx->prof_end(SWM_K_PAIRS);
   SWM_LAUNCHED();
 
-  // --- diagonal blocks and column positions, transpose map, upper-triangle block list, layouts
-  k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, cpf, cpo);
-  SWM_LAUNCHED();
+  // --- diagonal blocks and column positions, then (both need them) the transpose map with the
+  // upper-triangle block list, and the column maps on the build's second stream when it exists
   // the S-NFC pattern is symmetric, so the blocks above the diagonal are half the off-diagonal ones
   ctx->nup = (ctx->nb - nw) / 2;
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->bt, sizeof(int64_t) * ctx->nb));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->ublk, sizeof(int64_t) * std::max<int64_t>(1, ctx->nup)));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->full.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->full.ncm)));
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->offd.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->offd.ncm)));
+  k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, cpf, cpo);
+  SWM_LAUNCHED();
+  cudaStream_t s2 = ctx->side ? ctx->side : st;
+  if (ctx->side) {
+    SWM_CK(cudaEventRecord(ctx->side_ev[0], st));
+    SWM_CK(cudaStreamWaitEvent(s2, ctx->side_ev[0], 0));
+  }
+  // column maps: positions (k_row_meta), offsets and multiplicities
+  k_colmap<<<nblk(nw, 256), 256, 0, s2>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, ctx->full, ctx->offd);
+  SWM_LAUNCHED();
   k_transpose_and_upper<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, ctx->diag_b, ubase, ctx->bt,
                                                        ctx->ublk);
   SWM_LAUNCHED();
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->full.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->full.ncm)));
-  SWM_TRY(dalloc(ctx, B, (void**)&ctx->offd.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->offd.ncm)));
-  k_colmap<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, ctx->full, ctx->offd);
-  SWM_LAUNCHED();
+  if (ctx->side) {
+    SWM_CK(cudaEventRecord(ctx->side_ev[1], s2));
+    SWM_CK(cudaStreamWaitEvent(st, ctx->side_ev[1], 0));
+  }
   ctx->m = m;
   dfree_group(ctx, tmp);
   return SWM_OK;

@@ -451,10 +451,17 @@ static void ff32_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& ch
 }
 
 
-int prepare_far_field(swm_ctx* ctx) {
+// The per-wire data of the float32 far field: allocated on the context's stream (before the build
+// forks its second stream), filled on stream s.
+int far_field_alloc(swm_ctx* ctx) {
   if (ctx->prec != SWM_C64) return SWM_OK;
   SWM_TRY(dalloc(ctx, ctx->build_bufs, &ctx->ffw, sizeof(FFWire) * ctx->nw));
-  k_ff_wires<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, ctx->stream>>>(ctx->nw, ctx->cx, ctx->cy, ctx->cz, ctx->tx,
+  return SWM_OK;
+}
+
+int prepare_far_field(swm_ctx* ctx, cudaStream_t s) {
+  if (ctx->prec != SWM_C64) return SWM_OK;
+  k_ff_wires<<<(unsigned)ceil_div(ctx->nw, 256), 256, 0, s>>>(ctx->nw, ctx->cx, ctx->cy, ctx->cz, ctx->tx,
                                                                         ctx->ty, ctx->tz, ctx->L, ctx->ns, ctx->k,
                                                                         (FFWire*)ctx->ffw);
   SWM_LAUNCHED();
