@@ -691,6 +691,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     PSync* sync;          // persistent solve: barrier state and partial sums over its CTAs
     c128 *pp1, *pp2;
     double* ppn;
+    bool sync_clean;      // the barrier state is zero
   };
   const int64_t key[4] = {R, N, restart, (int64_t)sizeof(TV)};
   Workspace* ws = reinterpret_cast<Workspace*>(ctx->kry_ws);
@@ -745,26 +746,30 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   cplx<TV> *Y = ws->Y, *W0 = ws->W0, *W1 = ws->W1, *V = ws->V;
   // per-kernel path: W0 holds the pending vector u, W1 the product w = A u
   cplx<TV> *U = W0, *Wv = W1;
-  SWM_CK(cudaMemsetAsync(P.st, 0, sizeof(KState), st));
-  SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));
-  // with an initial guess the tolerance stays relative to |b|, so |b| is measured first
+  // with an initial guess y0 = M x0 is copied in and, the tolerance staying relative to |b|, |b|
+  // is measured first; otherwise (and for the refinement's correction) y starts at zero
   const bool given_b = ctx->guess && !y_out;
-  if (y_out)  // inner solve of the refinement: the correction starts from zero
-    SWM_CK(cudaMemsetAsync(Y, 0, sizeof(cplx<TV>) * R * N, st));
-  else
+  if (given_b) {
     SWM_TRY(init_y(ctx, Y, sizeof(TV) == sizeof(double)));
-  if (given_b) SWM_TRY(norms_of_b(ctx, ctx->Bv, sizeof(TV) == sizeof(double), P.bnorm));
+    SWM_TRY(norms_of_b(ctx, ctx->Bv, sizeof(TV) == sizeof(double), P.bnorm));
+  }
   (void)S;
 
   const cplx<TV>* Bv = (const cplx<TV>*)ctx->Bv;
   KState hs{};
   int cycles = 0;
-  // small systems: the whole solve as one persistent cooperative kernel
+  // small systems: the whole solve as one persistent cooperative kernel, which clears y itself
   bool persisted = false;
   SWM_TRY(ensure_poll_slots(ctx));
   {
-    PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0};
+    PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0, given_b ? 0 : 1,
+                &ws->sync_clean};
     SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
+  }
+  if (!persisted) {
+    SWM_CK(cudaMemsetAsync(P.st, 0, sizeof(KState), st));
+    SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));
+    if (!given_b) SWM_CK(cudaMemsetAsync(Y, 0, sizeof(cplx<TV>) * R * N, st));
   }
   const dim3 g_chunk((unsigned)P.nchunk, R);
   const bool multi = R > 1;
@@ -954,7 +959,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   if (y_out) {  // inner solve of the refinement: the result stays in y-space
     if (persisted) {
       SWM_CK(cudaStreamSynchronize(st));
-      SWM_TRY(persist_result(ctx, &hs));
+      SWM_TRY(persist_result(ctx, &hs, &ws->sync_clean));
     }
     if (hs_out) *hs_out = hs;
     *y_out = Y;
@@ -971,7 +976,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   SWM_CK(cudaStreamSynchronize(st));
   if (rp) std::memcpy(res.data(), rpin, sizeof(double) * R);
   if (persisted) {
-    SWM_TRY(persist_result(ctx, &hs));
+    SWM_TRY(persist_result(ctx, &hs, &ws->sync_clean));
     cycles = hs.cycles;
   }
   if (hs_out) *hs_out = hs;

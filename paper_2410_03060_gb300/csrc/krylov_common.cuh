@@ -66,7 +66,8 @@ struct ELoad<float, __nv_bfloat162> {
 struct PSync {
   unsigned count;  // arrivals at grid barriers since the launch
   int abort;       // a barrier ran out of time
-  int pad[30];
+  unsigned exits;  // CTAs that have left the kernel (the last one clears count and exits)
+  int pad[29];
 };
 struct PBuffers {
   PSync* sync;
@@ -75,6 +76,8 @@ struct PBuffers {
   const void* B;
   void *Y, *W, *V;
   int bnorm_given;              // P.bnorm already holds |b| (solve from an initial guess)
+  int y_zero;                   // Y starts at zero (the kernel clears it)
+  bool* sync_clean;             // the barrier state is zero (else it is cleared before the launch)
 };
 constexpr int kPersistMaxR = 8;  // right-hand sides of one persistent solve
 
@@ -84,6 +87,6 @@ constexpr int kPersistMaxR = 8;  // right-hand sides of one persistent solve
 // SWM_ETIMEOUT if a grid barrier ran out of time).
 template <typename TV, typename TE>
 int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& B, int max_iter, KState* hs, bool* done);
-int persist_result(swm_ctx* ctx, KState* hs);
+int persist_result(swm_ctx* ctx, KState* hs, bool* sync_clean);
 
 }  // namespace swm

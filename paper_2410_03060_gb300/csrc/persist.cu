@@ -62,6 +62,7 @@ struct PArgs {
   int vsm, esm;            // V / E slices in shared memory
   int64_t emax, cmax;      // largest E and column-map slice of a CTA (entries)
   int bnorm_given;         // P.bnorm holds |b| (else the first residual norm is |b|)
+  int y_zero;              // Y starts at zero: each CTA clears its rows and the first residual is B
 };
 
 // Byte offsets of the shared-memory arrays of the persistent kernel.
@@ -444,6 +445,31 @@ __device__ void p_product(int mode, const PArgs& a, const ESlice<TV, TE>& S, con
   if (mode == 1) p_norm_partials<TV, RB>(nrm, R, a.G, (TV*)a.partn, red);
 }
 
+// The first residual when Y starts at zero: the CTA's rows of Y cleared, ys = W = B on its rows,
+// squared norms to partn (no product).
+template <typename TV, int RB>
+__device__ void p_residual_zero(const PArgs& a, cplx<TV>* ys, int cnt, int64_t n0, const cplx<TV>* __restrict__ B,
+                                cplx<TV>* __restrict__ Y, cplx<TV>* __restrict__ W, TV (*red)[RB]) {
+  const int R = a.P.R;
+  const int64_t N = a.P.N;
+  TV nrm[RB];
+#pragma unroll
+  for (int b = 0; b < RB; ++b) nrm[b] = 0;
+  for (int t = threadIdx.x; t < cnt; t += kPT) {
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      if (b >= R) break;
+      const int64_t row = (int64_t)b * N + n0 + t;
+      const cplx<TV> r = B[row];
+      Y[row] = mkc<TV>(0, 0);
+      ys[b * a.rows + t] = r;
+      W[row] = r;
+      nrm[b] = fma(r.re, r.re, fma(r.im, r.im, nrm[b]));
+    }
+  }
+  p_norm_partials<TV, RB>(nrm, R, a.G, (TV*)a.partn, red);
+}
+
 template <typename TV, typename TE, int RB>
 __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
   using C = cplx<TV>;
@@ -576,7 +602,10 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
       if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
     }
     // ---- residual W = B - A Y on the CTA's rows, its squared norms
-    p_product<TV, TE, RB>(1, a, S, Y, ys, ws, cnt, n0, act, B, W, red);
+    if (first && a.y_zero)
+      p_residual_zero<TV, RB>(a, ys, cnt, n0, B, Y, W, red);
+    else
+      p_product<TV, TE, RB>(1, a, S, Y, ys, ws, cnt, n0, act, B, W, red);
     if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
     // ---- start of a cycle (every CTA)
     if (wp < R) {
@@ -763,6 +792,16 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
     }
     if (!ok) break;
   }
+  // ---- the last CTA to leave clears the barrier counter for the next launch (every other CTA has
+  // passed its last barrier); after a timeout the host clears the state instead
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&a.sync->exits, 1u) == gridDim.x - 1) {
+      a.sync->count = 0;
+      a.sync->exits = 0;
+      __threadfence();
+    }
+  }
   // ---- results (CTA 0)
   if (blockIdx.x == 0 && ok) {
     if (threadIdx.x < R) {
@@ -839,7 +878,9 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   pa.emax = emax;
   pa.cmax = cmax;
   pa.bnorm_given = Bf.bnorm_given;
-  SWM_CK(cudaMemsetAsync(Bf.sync, 0, sizeof(PSync), st));
+  pa.y_zero = Bf.y_zero;
+  if (!*Bf.sync_clean) SWM_CK(cudaMemsetAsync(Bf.sync, 0, sizeof(PSync), st));
+  *Bf.sync_clean = false;  // until persist_result has seen the launch end without a timeout
   void* args[] = {&pa};
   ctx->prof_begin(SWM_K_GMRES);
   SWM_CK(cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kPT), args, smem, st));
@@ -856,12 +897,13 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   return SWM_OK;
 }
 
-int persist_result(swm_ctx* ctx, KState* hs) {
+int persist_result(swm_ctx* ctx, KState* hs, bool* sync_clean) {
   const char* pin = static_cast<const char*>(ctx->pinned_state);
   std::memcpy(hs, pin + kPersistStateOffset, sizeof(KState));
   int abort = 0;
   std::memcpy(&abort, pin + kPersistAbortOffset, sizeof(int));
   if (abort) return ctx->fail(SWM_ETIMEOUT, "GMRES: a grid barrier of the persistent solve timed out");
+  *sync_clean = true;
   return SWM_OK;
 }
 
