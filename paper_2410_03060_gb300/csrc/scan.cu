@@ -1,4 +1,5 @@
-// Exclusive prefix sums on the device (tile sums, one-CTA scan of the tile sums, tile rescan).
+// Exclusive prefix sums on the device (tile sums, then a tile rescan that forms its prefix of the
+// tile sums itself, or with many tiles a one-CTA scan of the tile sums between the two).
 #include "common.cuh"
 #include "ctx.h"
 
@@ -39,12 +40,16 @@ __device__ int64_t block_incl_scan(int64_t v, int64_t* total) {
 
 template <typename TIn>
 __global__ void k_tile_sums(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ sums) {
-  const int64_t base = (int64_t)blockIdx.x * kTile;
-  int64_t s = 0;
-  for (int t = threadIdx.x; t < kTile; t += kScanThreads) {
-    int64_t i = base + t;
-    if (i < n) s += (int64_t)in[i];
+  const int64_t base = (int64_t)blockIdx.x * kTile + threadIdx.x;
+  int64_t v[kScanItems];
+#pragma unroll
+  for (int u = 0; u < kScanItems; ++u) {  // all of a thread's loads in flight together
+    const int64_t i = base + (int64_t)u * kScanThreads;
+    v[u] = i < n ? (int64_t)in[i] : 0;
   }
+  int64_t s = 0;
+#pragma unroll
+  for (int u = 0; u < kScanItems; ++u) s += v[u];
   int64_t tot;
   block_incl_scan(s, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
@@ -88,6 +93,43 @@ __global__ void k_tile_rescan(const TIn* __restrict__ in, int64_t n, const int64
     run += v[t];
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = sums[gridDim.x];
+}
+
+// Tile rescan for at most kPrefixMaxTiles tiles: each CTA sums the tile sums before its own (loads
+// in flight together) instead of a separate scan of the tile sums; the last CTA writes the total.
+constexpr int64_t kPrefixMaxTiles = 4 * kScanThreads;
+template <typename TIn>
+__global__ void k_tile_rescan_prefix(const TIn* __restrict__ in, int64_t n, const int64_t* __restrict__ sums,
+                                     int64_t* __restrict__ out) {
+  int64_t pv[kPrefixMaxTiles / kScanThreads];
+#pragma unroll
+  for (int u = 0; u < (int)(kPrefixMaxTiles / kScanThreads); ++u) {
+    const int64_t i = threadIdx.x + (int64_t)u * kScanThreads;
+    pv[u] = i < (int64_t)blockIdx.x ? sums[i] : 0;
+  }
+  int64_t ps = 0;
+#pragma unroll
+  for (int u = 0; u < (int)(kPrefixMaxTiles / kScanThreads); ++u) ps += pv[u];
+  int64_t pre;
+  block_incl_scan(ps, &pre);
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    int64_t i = base + t;
+    v[t] = i < n ? (int64_t)in[i] : 0;
+    s += v[t];
+  }
+  int64_t tot;
+  int64_t run = block_incl_scan(s, &tot) - s + pre;
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    int64_t i = base + t;
+    if (i < n) out[i] = run;
+    run += v[t];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = pre + tot;
 }
 
 // Whole scan in one CTA of kSingleThreads for short arrays (one launch instead of three).  Each
@@ -176,9 +218,13 @@ int scan_impl(swm_ctx* ctx, const TIn* in, int64_t* out, int64_t n, int64_t* tot
   SWM_TRY(dalloc(ctx, tmp, (void**)&sums, sizeof(int64_t) * (nt + 1)));
   k_tile_sums<TIn><<<(unsigned)nt, kScanThreads, 0, ctx->stream>>>(in, n, sums);
   SWM_LAUNCHED();
-  k_scan_sums<<<1, kScanThreads, 0, ctx->stream>>>(sums, nt);
-  SWM_LAUNCHED();
-  k_tile_rescan<TIn><<<(unsigned)nt, kScanThreads, 0, ctx->stream>>>(in, n, sums, out);
+  if (nt <= kPrefixMaxTiles) {
+    k_tile_rescan_prefix<TIn><<<(unsigned)nt, kScanThreads, 0, ctx->stream>>>(in, n, sums, out);
+  } else {
+    k_scan_sums<<<1, kScanThreads, 0, ctx->stream>>>(sums, nt);
+    SWM_LAUNCHED();
+    k_tile_rescan<TIn><<<(unsigned)nt, kScanThreads, 0, ctx->stream>>>(in, n, sums, out);
+  }
   SWM_LAUNCHED();
   if (total_host) {
     SWM_CK(cudaMemcpyAsync(total_host, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
