@@ -38,49 +38,46 @@ __global__ void k_cell_ids(const double* __restrict__ c, int64_t nw, Grid g, int
   atomicAdd(&cnt[id], 1);
 }
 
+// Each wire into a free slot of its cell's range (the cell count, counted down, numbers the slots).
 __global__ void k_scatter_unordered(const int32_t* __restrict__ cid, int64_t nw, const int64_t* __restrict__ cstart,
-                                    int32_t* __restrict__ fill, int32_t* __restrict__ tmp) {
+                                    int32_t* __restrict__ cnt, int32_t* __restrict__ tmp) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nw) return;
   const int id = cid[i];
-  const int64_t pos = cstart[id] + atomicAdd(&fill[id], 1);
+  const int64_t pos = cstart[id] + atomicSub(&cnt[id], 1) - 1;
   tmp[pos] = (int32_t)i;
 }
 
 // Deterministic order inside a cell: a wire's rank is the number of wires of its cell with a
-// smaller caller index.
-__global__ void k_rank_in_cell(const int32_t* __restrict__ cid, int64_t nw, const int64_t* __restrict__ cstart,
-                               const int32_t* __restrict__ tmp, int32_t* __restrict__ perm,
-                               int32_t* __restrict__ iperm, int32_t* __restrict__ cid_sorted) {
+// smaller caller index.  Wire i goes to position s + rank: the permutation, its inverse, the sorted
+// cell ids, and the wire's geometry written in internal order (m = segments - 1 unknowns).
+__global__ void k_rank_and_place(const int32_t* __restrict__ cid, int64_t nw, const int64_t* __restrict__ cstart,
+                                 const int32_t* __restrict__ tmp, int32_t* __restrict__ perm,
+                                 int32_t* __restrict__ iperm, int32_t* __restrict__ cid_sorted,
+                                 const double* __restrict__ uc, const double* __restrict__ ut,
+                                 const double* __restrict__ uL, const double* __restrict__ ua,
+                                 const int32_t* __restrict__ uns, double* cx, double* cy, double* cz, double* tx,
+                                 double* ty, double* tz, double* L, double* a, int32_t* ns, int32_t* m) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nw) return;
   const int id = cid[i];
   const int64_t s = cstart[id], e = cstart[id + 1];
   int64_t r = 0;
   for (int64_t t = s; t < e; ++t) r += (tmp[t] < (int32_t)i);
-  perm[s + r] = (int32_t)i;
-  iperm[i] = (int32_t)(s + r);
-  cid_sorted[s + r] = id;
-}
-
-__global__ void k_gather_geometry(int64_t nw, const int32_t* __restrict__ perm, const double* __restrict__ uc,
-                                  const double* __restrict__ ut, const double* __restrict__ uL,
-                                  const double* __restrict__ ua, const int32_t* __restrict__ uns,
-                                  double* cx, double* cy, double* cz, double* tx, double* ty, double* tz, double* L,
-                                  double* a, int32_t* ns, int32_t* m) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= nw) return;
-  const int64_t u = perm[p];
-  cx[p] = uc[3 * u];
-  cy[p] = uc[3 * u + 1];
-  cz[p] = uc[3 * u + 2];
-  tx[p] = ut[3 * u];
-  ty[p] = ut[3 * u + 1];
-  tz[p] = ut[3 * u + 2];
-  L[p] = uL[u];
-  a[p] = ua[u];
-  ns[p] = uns[u];
-  m[p] = uns[u] - 1;
+  const int64_t p = s + r;
+  perm[p] = (int32_t)i;
+  iperm[i] = (int32_t)p;
+  cid_sorted[p] = id;
+  cx[p] = uc[3 * i];
+  cy[p] = uc[3 * i + 1];
+  cz[p] = uc[3 * i + 2];
+  tx[p] = ut[3 * i];
+  ty[p] = ut[3 * i + 1];
+  tz[p] = ut[3 * i + 2];
+  L[p] = uL[i];
+  a[p] = ua[i];
+  ns[p] = uns[i];
+  m[p] = uns[i] - 1;
 }
 
 __global__ void k_user_m(int64_t nw, const int32_t* __restrict__ uns, int32_t* __restrict__ um) {
@@ -356,35 +353,31 @@ int build_pattern(swm_ctx* ctx) {
   const int64_t ncell = nx * ny * nz;
 
   // --- bin and renumber by (cell, caller index)
-  int32_t *cid = nullptr, *cnt = nullptr, *fill = nullptr, *tmpidx = nullptr, *cid_s = nullptr;
+  int32_t *cid = nullptr, *cnt = nullptr, *tmpidx = nullptr, *cid_s = nullptr;
   int64_t* cstart = nullptr;
   SWM_TRY(dalloc(ctx, tmp, (void**)&cid, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&cnt, sizeof(int32_t) * ncell));
-  SWM_TRY(dalloc(ctx, tmp, (void**)&fill, sizeof(int32_t) * ncell));
   SWM_TRY(dalloc(ctx, tmp, (void**)&tmpidx, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&cid_s, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, tmp, (void**)&cstart, sizeof(int64_t) * (ncell + 1)));
   SWM_CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ncell, st));
-  SWM_CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * ncell, st));
   k_cell_ids<<<nblk(nw, 256), 256, 0, st>>>(ctx->u_c, nw, g, cid, cnt);
   SWM_LAUNCHED();
   SWM_TRY(exclusive_scan_i32_to_i64(ctx, cnt, cstart, ncell, nullptr));
-  k_scatter_unordered<<<nblk(nw, 256), 256, 0, st>>>(cid, nw, cstart, fill, tmpidx);
+  k_scatter_unordered<<<nblk(nw, 256), 256, 0, st>>>(cid, nw, cstart, cnt, tmpidx);
   SWM_LAUNCHED();
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->perm, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->iperm, sizeof(int32_t) * nw));
-  k_rank_in_cell<<<nblk(nw, 256), 256, 0, st>>>(cid, nw, cstart, tmpidx, ctx->perm, ctx->iperm, cid_s);
-  SWM_LAUNCHED();
 
-  // --- geometry in internal order, numbering of unknowns (a0)
+  // --- order inside cells, geometry in internal order, numbering of unknowns (a0)
   double** geo[8] = {&ctx->cx, &ctx->cy, &ctx->cz, &ctx->tx, &ctx->ty, &ctx->tz, &ctx->L, &ctx->a};
   for (auto pp : geo) SWM_TRY(dalloc(ctx, B, (void**)pp, sizeof(double) * nw));
   int32_t* m = nullptr;
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->ns, sizeof(int32_t) * nw));
   SWM_TRY(dalloc(ctx, B, (void**)&m, sizeof(int32_t) * nw));
-  k_gather_geometry<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->perm, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a,
-                                                   ctx->u_ns, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty,
-                                                   ctx->tz, ctx->L, ctx->a, ctx->ns, m);
+  k_rank_and_place<<<nblk(nw, 256), 256, 0, st>>>(cid, nw, cstart, tmpidx, ctx->perm, ctx->iperm, cid_s, ctx->u_c,
+                                                  ctx->u_t, ctx->u_L, ctx->u_a, ctx->u_ns, ctx->cx, ctx->cy, ctx->cz,
+                                                  ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->a, ctx->ns, m);
   SWM_LAUNCHED();
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->off, sizeof(int64_t) * (nw + 1)));  // scanned with the row counts below
   ctx->uoff = nullptr;  // caller-order offsets are made on first use (ensure_user_offsets)
