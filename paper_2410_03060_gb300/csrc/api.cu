@@ -112,15 +112,20 @@ namespace {
 // One pass over the caller's wires: copy them into the context's buffers (when the caller's are
 // device buffers; host inputs were copied before), check them, and per CTA the bounding box of the
 // centres, the check flags (1 NaN/Inf, 2 non-unit direction, 4 length, 8 radius, 16 segments) and
-// the largest segment count, part[blk][8] = {min xyz, max xyz, flags, max ns}.
+// the largest segment count, part[blk][8] = {min xyz, max xyz, flags, max ns}.  The last CTA to
+// arrive combines the partials into res[8] (warp d for field d) and clears the arrival counter.
 constexpr int kIngestThreads = 256;
+__device__ __forceinline__ double ingest_comb(int d, double v, double x) {
+  return d < 3 ? fmin(v, x) : d < 6 ? fmax(v, x) : d == 6 ? (double)((int)v | (int)x) : fmax(v, x);
+}
 __global__ void __launch_bounds__(kIngestThreads) k_ingest(int64_t nw, const double* __restrict__ sc,
                                                            const double* __restrict__ st,
                                                            const double* __restrict__ sL,
                                                            const double* __restrict__ sa,
                                                            const int32_t* __restrict__ sns, int copy, double* c,
                                                            double* t, double* L, double* a, int32_t* ns,
-                                                           double* __restrict__ part) {
+                                                           double* __restrict__ part, unsigned* __restrict__ arrivals,
+                                                           double* __restrict__ res) {
   double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   int f = 0, mns = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x) {
@@ -157,6 +162,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(int64_t nw, const dou
     mns = max(mns, ni);
   }
   __shared__ double s[8][kIngestThreads / 32];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -180,26 +186,22 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(int64_t nw, const dou
   if (threadIdx.x < 8) {
     const int d = threadIdx.x;
     double v = s[d][0];
-    for (int k = 1; k < kIngestThreads / 32; ++k) {
-      const double x = s[d][k];
-      v = d < 3 ? fmin(v, x) : d < 6 ? fmax(v, x) : d == 6 ? (double)((int)v | (int)x) : fmax(v, x);
-    }
+    for (int k = 1; k < kIngestThreads / 32; ++k) v = ingest_comb(d, v, s[d][k]);
     part[blockIdx.x * 8 + d] = v;
   }
-}
-
-// The CTA partials of k_ingest combined: res[8] = {min xyz, max xyz, flags, max ns}, warp d for
-// field d (all of a lane's partials loaded together, then a shuffle tree).
-__global__ void __launch_bounds__(256) k_ingest_final(const double* __restrict__ part, int np, double* __restrict__ res) {
-  const int d = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto comb = [d](double v, double x) {
-    return d < 3 ? fmin(v, x) : d < 6 ? fmax(v, x) : d == 6 ? (double)((int)v | (int)x) : fmax(v, x);
-  };
-  double v = part[d];  // np >= 1
-  for (int k = lane; k < np; k += 32) v = comb(v, part[k * 8 + d]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  // last CTA: warp d combines field d over all CTAs' partials
+  const int d = w;
+  double v = __ldcg(part + d);
+  for (int k = lane; k < (int)gridDim.x; k += 32) v = ingest_comb(d, v, __ldcg(part + k * 8 + d));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = comb(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = ingest_comb(d, v, __shfl_xor_sync(0xffffffffu, v, o));
   if (lane == 0) res[d] = v;
+  if (threadIdx.x == 0) *arrivals = 0;
 }
 
 // Internal [R][N] currents (any precision) -> caller [R][N] complex128 in caller unknown order.
@@ -339,6 +341,7 @@ void swm_destroy(swm_ctx* ctx) {
   for (auto ev : ctx->poll_ev)
     if (ev) cudaEventDestroy(ev);
   if (ctx->pinned_state) cudaFreeHost(ctx->pinned_state);
+  if (ctx->d_arrive) cudaFree(ctx->d_arrive);
   if (ctx->gm_exec) cudaGraphExecDestroy(ctx->gm_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->side) {
@@ -400,14 +403,17 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   const bool dev = mem_kind == SWM_DEVICE;
   std::vector<Buf> tmp;
   const int np = (int)std::min<int64_t>(ceil_div(nw, kIngestThreads), 2 * std::max(ctx->nsm, 1));
+  if (!ctx->d_arrive) {  // the arrival counter of k_ingest: zero, and left zero by every launch
+    SWM_CK(cudaMalloc((void**)&ctx->d_arrive, sizeof(unsigned)));
+    SWM_CK(cudaMemsetAsync(ctx->d_arrive, 0, sizeof(unsigned), ctx->stream));
+  }
   double* part = nullptr;
   SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * 8 * (np + 1)));
   double* res = part + 8 * np;
   k_ingest<<<(unsigned)np, kIngestThreads, 0, ctx->stream>>>(
       nw, dev ? centres : ctx->u_c, dev ? dirs : ctx->u_t, dev ? lengths : ctx->u_L, dev ? radii : ctx->u_a,
-      dev ? nseg : ctx->u_ns, dev ? 1 : 0, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a, ctx->u_ns, part);
-  SWM_LAUNCHED();
-  k_ingest_final<<<1, 256, 0, ctx->stream>>>(part, np, res);
+      dev ? nseg : ctx->u_ns, dev ? 1 : 0, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a, ctx->u_ns, part, ctx->d_arrive,
+      res);
   SWM_LAUNCHED();
   SWM_TRY(ensure_poll_slots(ctx));
   double* hres = reinterpret_cast<double*>(static_cast<char*>(ctx->pinned_state) + kIngestSlotOffset);

@@ -124,6 +124,7 @@ struct swm_ctx {
   unsigned long long* d_evals = nullptr;  // fill evaluation counter (device)
   int* d_sing = nullptr;                  // singular self block flag (device)
   void* pinned_state = nullptr;           // two pinned slots for the Krylov state poll
+  unsigned* d_arrive = nullptr;           // arrival counter of the cloud-check kernel (kept zero)
   int solver = 0;                         // SWM_SOLVER_GMRES or SWM_SOLVER_GCR
   // right-hand sides per block of the fused multi-incidence GMRES step, measured per system shape
   // (N, n_rhs, vector and matrix entry sizes, chunk, restart)
@@ -236,7 +237,6 @@ void dfree_group(swm_ctx* ctx, std::vector<Buf>& group);
 // neighbour.cu: a0 + a1 (sort by cell, numbering, S-NFC pattern, layouts)
 int build_pattern(swm_ctx* ctx);
 // copy n device int64 values to the host with one synchronisation
-int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst, std::vector<Buf>& tmp);
 // launch the bounding-box reduction of the caller centres into out6 (device)
 // caller-order unknown offsets, made on first use
 int ensure_user_offsets(swm_ctx* ctx);
@@ -247,7 +247,7 @@ int exclusive_scan_i64(swm_ctx* ctx, const int64_t* in, int64_t* out, int64_t n,
 int exclusive_scan_i32_to_i64(swm_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host);
 // up to six scans of the same length (one launch when short); inputs int64 (is64) or int32
 int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const int* is64, int64_t* const* out,
-                         int64_t n);
+                         int64_t n, int64_t* totals = nullptr);
 // fill.cu: a2 + a3
 int fill_alloc(swm_ctx* ctx);
 int fill_self(swm_ctx* ctx, cudaStream_t s);

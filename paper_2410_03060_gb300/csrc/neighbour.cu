@@ -261,14 +261,6 @@ __global__ void k_colmap(int64_t nw, const int64_t* __restrict__ row_ptr, const 
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, ceil_div(n, t)); }
 
-constexpr int kMaxRead = 8;
-struct Ptrs8 {
-  const int64_t* p[kMaxRead];
-};
-__global__ void k_gather_i64(Ptrs8 p, int n, int64_t* __restrict__ out) {
-  if ((int)threadIdx.x < n) out[threadIdx.x] = *p.p[threadIdx.x];
-}
-
 int alloc_layout(swm_ctx* ctx, Layout& lay, int32_t* K, int32_t* colpos) {
   lay.K = K;
   lay.colpos = colpos;
@@ -293,23 +285,6 @@ int ensure_user_offsets(swm_ctx* ctx) {
   k_uoff_by_internal<<<nblk(nw, 256), 256, 0, ctx->stream>>>(nw, ctx->perm, ctx->uoff_user, ctx->uoff);
   SWM_LAUNCHED();
   dfree_group(ctx, tmp);
-  return SWM_OK;
-}
-
-int read_i64(swm_ctx* ctx, int n, const int64_t* const* src, int64_t* dst, std::vector<Buf>& tmp) {
-  if (n > kMaxRead) return ctx->fail(SWM_EINVAL, "read_i64: too many values");
-  // one gather kernel and one copy to pinned memory instead of a copy per value
-  Ptrs8 p{};
-  for (int i = 0; i < n; ++i) p.p[i] = src[i];
-  int64_t* d = nullptr;
-  SWM_TRY(dalloc(ctx, tmp, (void**)&d, sizeof(int64_t) * kMaxRead));
-  k_gather_i64<<<1, 32, 0, ctx->stream>>>(p, n, d);
-  SWM_LAUNCHED();
-  SWM_TRY(ensure_poll_slots(ctx));
-  int64_t* h = reinterpret_cast<int64_t*>(static_cast<char*>(ctx->pinned_state) + kIngestSlotOffset);
-  SWM_CK(cudaMemcpyAsync(h, d, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
-  SWM_CK(cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i < n; ++i) dst[i] = h[i];
   return SWM_OK;
 }
 
@@ -411,13 +386,15 @@ int build_pattern(swm_ctx* ctx) {
     const int is64[8] = {0, 0, 1, 1, 0, 1, 0, 1};
     int64_t* out[8] = {ctx->off, ctx->row_ptr, ubase, ctx->full.rowbase, ctx->full.cmbase, ctx->offd.rowbase,
                        ctx->offd.cmbase, ctx->minv_off};
-    SWM_TRY(exclusive_scan_multi(ctx, 8, in, is64, out, nw));
-  }
-  {
-    const int64_t* src[7] = {ctx->off + nw, ctx->row_ptr + nw, ctx->full.rowbase + nw, ctx->full.cmbase + nw,
-                             ctx->offd.rowbase + nw, ctx->offd.cmbase + nw, ctx->minv_off + nw};
-    int64_t v[7];
-    SWM_TRY(read_i64(ctx, 7, src, v, tmp));
+    // the totals side by side, read back with one copy to pinned memory
+    int64_t* tot = nullptr;
+    SWM_TRY(dalloc(ctx, tmp, (void**)&tot, sizeof(int64_t) * 8));
+    SWM_TRY(exclusive_scan_multi(ctx, 8, in, is64, out, nw, tot));
+    SWM_TRY(ensure_poll_slots(ctx));
+    int64_t* h = reinterpret_cast<int64_t*>(static_cast<char*>(ctx->pinned_state) + kIngestSlotOffset);
+    SWM_CK(cudaMemcpyAsync(h, tot, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
+    SWM_CK(cudaStreamSynchronize(st));
+    const int64_t v[7] = {h[0], h[1], h[3], h[4], h[5], h[6], h[7]};  // totals[2] (upper blocks) unused
     ctx->N = v[0];
     ctx->nb = v[1];
     ctx->full.nval = v[2];

@@ -240,6 +240,7 @@ struct MultiScanArgs {
   int is64[kMaxMultiScan];
   int64_t* out[kMaxMultiScan];
   int narr;
+  int64_t* totals;  // optional: the totals side by side, totals[k] = out[k][n]
 };
 
 // Several exclusive scans of the same short length, one CTA per array.
@@ -249,20 +250,28 @@ __global__ void __launch_bounds__(kSingleThreads) k_scan_multi(MultiScanArgs a, 
     cta_scan_short<int64_t>((const int64_t*)a.in[k], n, a.out[k]);
   else
     cta_scan_short<int32_t>((const int32_t*)a.in[k], n, a.out[k]);
+  if (a.totals && threadIdx.x == 0) a.totals[k] = a.out[k][n];  // written by this thread
+}
+
+// The totals of long scans side by side.
+__global__ void k_scan_totals(MultiScanArgs a, int64_t n) {
+  if ((int)threadIdx.x < a.narr) a.totals[threadIdx.x] = a.out[threadIdx.x][n];
 }
 
 }  // namespace
 
 int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const int* is64, int64_t* const* out,
-                         int64_t n) {
-  if (n <= kSingleMax && n > 0 && narr <= kMaxMultiScan) {
-    MultiScanArgs a{};
-    a.narr = narr;
-    for (int k = 0; k < narr; ++k) {
-      a.in[k] = in[k];
-      a.is64[k] = is64[k];
-      a.out[k] = out[k];
-    }
+                         int64_t n, int64_t* totals) {
+  if (narr > kMaxMultiScan) return ctx->fail(SWM_EINVAL, "exclusive_scan_multi: too many arrays");
+  MultiScanArgs a{};
+  a.narr = narr;
+  a.totals = totals;
+  for (int k = 0; k < narr; ++k) {
+    a.in[k] = in[k];
+    a.is64[k] = is64[k];
+    a.out[k] = out[k];
+  }
+  if (n <= kSingleMax && n > 0) {
     k_scan_multi<<<narr, kSingleThreads, 0, ctx->stream>>>(a, n);
     SWM_LAUNCHED();
     return SWM_OK;
@@ -272,6 +281,10 @@ int exclusive_scan_multi(swm_ctx* ctx, int narr, const void* const* in, const in
       SWM_TRY(scan_impl<int64_t>(ctx, (const int64_t*)in[k], out[k], n, nullptr));
     else
       SWM_TRY(scan_impl<int32_t>(ctx, (const int32_t*)in[k], out[k], n, nullptr));
+  }
+  if (totals) {
+    k_scan_totals<<<1, 32, 0, ctx->stream>>>(a, n);
+    SWM_LAUNCHED();
   }
   return SWM_OK;
 }
