@@ -244,10 +244,21 @@ __global__ void k_transpose_and_upper(int64_t nw, const int64_t* __restrict__ ro
 }
 
 // Column maps of both layouts (with and without the diagonal blocks), one thread per block-row.
+// Column maps of both layouts, and for the Krylov kernels each scalar row's wire and its 16-byte
+// descriptor in the off-diagonal layout (first value, first column-map entry, length).
 __global__ void k_colmap(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                         const int32_t* __restrict__ m, const int64_t* __restrict__ off, Layout a, Layout b2) {
+                         const int32_t* __restrict__ m, const int64_t* __restrict__ off, Layout a, Layout b2,
+                         int32_t* __restrict__ rowwire, RowInfo* __restrict__ rinfo) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= nw) return;
+  {
+    const int K = b2.K[p];
+    const int64_t o0 = off[p], o1 = off[p + 1];
+    for (int64_t n = o0; n < o1; ++n) {
+      rowwire[n] = (int32_t)p;
+      rinfo[n] = RowInfo{b2.rowbase[p] + (n - o0) * K, (int32_t)b2.cmbase[p], K};
+    }
+  }
   for (int64_t b = row_ptr[p]; b < row_ptr[p + 1]; ++b) {
     const int32_t q = col[b];
     const int32_t ca = a.colpos[b], cb = b2.colpos[b];
@@ -423,6 +434,9 @@ int build_pattern(swm_ctx* ctx) {
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->ublk, sizeof(int64_t) * std::max<int64_t>(1, ctx->nup)));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->full.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->full.ncm)));
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->offd.colmap, sizeof(int32_t) * std::max<int64_t>(1, ctx->offd.ncm)));
+  if (ctx->offd.ncm > INT32_MAX) return ctx->fail(SWM_EINVAL, "column map too large for 32-bit offsets");
+  SWM_TRY(dalloc(ctx, B, (void**)&ctx->rowwire, sizeof(int32_t) * std::max<int64_t>(1, ctx->N)));
+  SWM_TRY(dalloc(ctx, B, &ctx->rowinfo, sizeof(RowInfo) * std::max<int64_t>(1, ctx->N)));
   k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, cpf, cpo);
   SWM_LAUNCHED();
   cudaStream_t s2 = ctx->side ? ctx->side : st;
@@ -430,8 +444,9 @@ int build_pattern(swm_ctx* ctx) {
     SWM_CK(cudaEventRecord(ctx->side_ev[0], st));
     SWM_CK(cudaStreamWaitEvent(s2, ctx->side_ev[0], 0));
   }
-  // column maps: positions (k_row_meta), offsets and multiplicities
-  k_colmap<<<nblk(nw, 256), 256, 0, s2>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, ctx->full, ctx->offd);
+  // column maps (positions from k_row_meta, offsets, multiplicities) and the row descriptors
+  k_colmap<<<nblk(nw, 256), 256, 0, s2>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, ctx->full, ctx->offd,
+                                          ctx->rowwire, (RowInfo*)ctx->rowinfo);
   SWM_LAUNCHED();
   k_transpose_and_upper<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, ctx->diag_b, ubase, ctx->bt,
                                                        ctx->ublk);
