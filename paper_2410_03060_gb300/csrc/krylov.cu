@@ -763,7 +763,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   SWM_TRY(ensure_poll_slots(ctx));
   {
     PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0, given_b ? 0 : 1,
-                &ws->sync_clean};
+                &ws->sync_clean, y_out ? nullptr : ctx->Xv};
     SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
   }
   if (!persisted) {
@@ -967,8 +967,9 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     if (hs.numeric) return ctx->fail(SWM_ECUDA, "GMRES produced a non-finite value");
     return hs.all_conv ? SWM_OK : SWM_ENOTCONV;
   }
-  // x = M^-1 y, then one synchronisation for the residuals (and the persistent solve's state)
-  SWM_TRY(apply_minv(ctx, Y));
+  // x = M^-1 y (the persistent solve forms it itself), then one synchronisation for the residuals
+  // (and the persistent solve's state)
+  if (!persisted) SWM_TRY(apply_minv(ctx, Y));
   std::vector<double> res(R);
   double* rpin = reinterpret_cast<double*>(static_cast<char*>(ctx->pinned_state) + kPinnedResidOffset);
   const bool rp = R <= kPinnedResidMax;

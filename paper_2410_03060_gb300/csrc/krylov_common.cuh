@@ -78,6 +78,7 @@ struct PBuffers {
   int bnorm_given;              // P.bnorm already holds |b| (solve from an initial guess)
   int y_zero;                   // Y starts at zero (the kernel clears it)
   bool* sync_clean;             // the barrier state is zero (else it is cleared before the launch)
+  void* X;                      // non-null: the kernel also forms x = M^-1 y there
 };
 constexpr int kPersistMaxR = 8;  // right-hand sides of one persistent solve
 

@@ -63,6 +63,13 @@ struct PArgs {
   int64_t emax, cmax;      // largest E and column-map slice of a CTA (entries)
   int bnorm_given;         // P.bnorm holds |b| (else the first residual norm is |b|)
   int y_zero;              // Y starts at zero: each CTA clears its rows and the first residual is B
+  int do_minv;             // at the end, X = M^-1 Y on the CTA's rows
+  const int32_t* rowwire;  // scalar row -> wire
+  const int64_t* off;      // first unknown of each wire
+  const int32_t* mw;       // unknowns per wire
+  const int64_t* minv_off; // M^-1 block of each wire (row-major m x m)
+  const void* Minv;
+  void* X;
 };
 
 // Byte offsets of the shared-memory arrays of the persistent kernel.
@@ -792,6 +799,24 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
     }
     if (!ok) break;
   }
+  // ---- x = M^-1 y on the CTA's rows: the loop left after the grid barrier of a cycle's start, so
+  // every row of y is final (read through L2: rows of a wire can belong to the next CTA)
+  if (ok && a.do_minv) {
+    const C* Mi = (const C*)a.Minv;
+    C* X = (C*)a.X;
+    for (int k = threadIdx.x; k < R * cnt; k += kPT) {
+      const int b = k / cnt, t = k % cnt;
+      const int64_t n = n0 + t;
+      const int p = a.rowwire[n];
+      const int64_t o = a.off[p];
+      const int i = (int)(n - o), mp = a.mw[p];
+      const C* row = Mi + a.minv_off[p] + (int64_t)i * mp;
+      const C* y = Y + (int64_t)b * N + o;
+      C acc = mkc<TV>(0, 0);
+      for (int l = 0; l < mp; ++l) cfma(acc, row[l], ldcg_c<TV>(y + l));
+      X[(int64_t)b * N + n] = acc;
+    }
+  }
   // ---- the last CTA to leave clears the barrier counter for the next launch (every other CTA has
   // passed its last barrier); after a timeout the host clears the state instead
   if (threadIdx.x == 0) {
@@ -879,6 +904,13 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   pa.cmax = cmax;
   pa.bnorm_given = Bf.bnorm_given;
   pa.y_zero = Bf.y_zero;
+  pa.do_minv = Bf.X ? 1 : 0;
+  pa.rowwire = ctx->rowwire;
+  pa.off = ctx->off;
+  pa.mw = ctx->m;
+  pa.minv_off = ctx->minv_off;
+  pa.Minv = ctx->Minv;
+  pa.X = Bf.X;
   if (!*Bf.sync_clean) SWM_CK(cudaMemsetAsync(Bf.sync, 0, sizeof(PSync), st));
   *Bf.sync_clean = false;  // until persist_result has seen the launch end without a timeout
   void* args[] = {&pa};
