@@ -573,8 +573,14 @@ static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, in
   size_t staged = 0;
   SWM_TRY(upload(ctx, ctx->inc_dev, inc, sizeof(double) * 3 * n_inc, &staged));
   SWM_TRY(upload(ctx, frames, fh.data(), sizeof(double) * 6 * n_inc, &staged));
+  // GMRES from zero forms b itself when it runs as the persistent solve (each CTA its rows, in its
+  // first residual); every other path gets it from the RHS kernel here or in the solver
+  const bool defer_rhs = !ctx->bf16 && ctx->solver == SWM_SOLVER_GMRES && !x0;
   ctx->phase_begin(swm_ctx::PH_RHS);
-  SWM_TRY(compute_rhs(ctx, n_inc, frames));
+  if (defer_rhs)
+    ctx->rhs_frames = frames;
+  else
+    SWM_TRY(compute_rhs(ctx, n_inc, frames));
   ctx->phase_end(swm_ctx::PH_RHS);
   ctx->guess = nullptr;
   if (x0) {
@@ -608,6 +614,7 @@ static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, in
                                            : gmres_solve(ctx, tol, restart, max_iter);
   ctx->phase_end(swm_ctx::PH_SOLVE);
   ctx->guess = nullptr;
+  ctx->rhs_frames = nullptr;
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->phase_collect();
   ctx->prof_flush();

@@ -125,6 +125,7 @@ struct swm_ctx {
   int* d_sing = nullptr;                  // singular self block flag (device)
   void* pinned_state = nullptr;           // two pinned slots for the Krylov state poll
   unsigned* d_arrive = nullptr;           // arrival counter of the cloud-check kernel (kept zero)
+  const double* rhs_frames = nullptr;     // b not yet formed: the solver forms it from these frames
   int solver = 0;                         // SWM_SOLVER_GMRES or SWM_SOLVER_GCR
   // right-hand sides per block of the fused multi-incidence GMRES step, measured per system shape
   // (N, n_rhs, vector and matrix entry sizes, chunk, restart)

@@ -763,9 +763,11 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   SWM_TRY(ensure_poll_slots(ctx));
   {
     PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0, given_b ? 0 : 1,
-                &ws->sync_clean, y_out ? nullptr : ctx->Xv};
+                &ws->sync_clean, y_out ? nullptr : ctx->Xv, y_out ? nullptr : ctx->rhs_frames};
     SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
   }
+  if (!persisted && !y_out && ctx->rhs_frames) SWM_TRY(compute_rhs(ctx, R, ctx->rhs_frames));
+  if (!y_out) ctx->rhs_frames = nullptr;
   if (!persisted) {
     SWM_CK(cudaMemsetAsync(P.st, 0, sizeof(KState), st));
     SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));

@@ -79,6 +79,7 @@ struct PBuffers {
   int y_zero;                   // Y starts at zero (the kernel clears it)
   bool* sync_clean;             // the barrier state is zero (else it is cleared before the launch)
   void* X;                      // non-null: the kernel also forms x = M^-1 y there
+  const double* frames;         // non-null: B is not formed yet; the kernel forms it (incidence frames)
 };
 constexpr int kPersistMaxR = 8;  // right-hand sides of one persistent solve
 

@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "krylov_common.cuh"
+#include "rhs_entry.cuh"
 
 namespace swm {
 
@@ -70,6 +71,9 @@ struct PArgs {
   const int64_t* minv_off; // M^-1 block of each wire (row-major m x m)
   const void* Minv;
   void* X;
+  const double* frames;    // non-null: the first residual forms B (and stores it) from these frames
+  double k;
+  RhsGeo geo;
 };
 
 // Byte offsets of the shared-memory arrays of the persistent kernel.
@@ -453,9 +457,9 @@ __device__ void p_product(int mode, const PArgs& a, const ESlice<TV, TE>& S, con
 }
 
 // The first residual when Y starts at zero: the CTA's rows of Y cleared, ys = W = B on its rows,
-// squared norms to partn (no product).
+// squared norms to partn (no product).  With a.frames the CTA forms its rows of B first.
 template <typename TV, int RB>
-__device__ void p_residual_zero(const PArgs& a, cplx<TV>* ys, int cnt, int64_t n0, const cplx<TV>* __restrict__ B,
+__device__ void p_residual_zero(const PArgs& a, cplx<TV>* ys, int cnt, int64_t n0, cplx<TV>* B,
                                 cplx<TV>* __restrict__ Y, cplx<TV>* __restrict__ W, TV (*red)[RB]) {
   const int R = a.P.R;
   const int64_t N = a.P.N;
@@ -463,11 +467,23 @@ __device__ void p_residual_zero(const PArgs& a, cplx<TV>* ys, int cnt, int64_t n
 #pragma unroll
   for (int b = 0; b < RB; ++b) nrm[b] = 0;
   for (int t = threadIdx.x; t < cnt; t += kPT) {
+    int64_t p = 0;
+    int l = 0;
+    if (a.frames) {
+      p = a.rowwire[n0 + t];
+      l = (int)(n0 + t - a.off[p]);
+    }
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
       if (b >= R) break;
       const int64_t row = (int64_t)b * N + n0 + t;
-      const cplx<TV> r = B[row];
+      cplx<TV> r;
+      if (a.frames) {
+        r = rhs_entry<TV>(a.geo, p, l, a.frames + 6 * b, a.k);
+        B[row] = r;
+      } else {
+        r = B[row];
+      }
       Y[row] = mkc<TV>(0, 0);
       ys[b * a.rows + t] = r;
       W[row] = r;
@@ -610,7 +626,7 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
     }
     // ---- residual W = B - A Y on the CTA's rows, its squared norms
     if (first && a.y_zero)
-      p_residual_zero<TV, RB>(a, ys, cnt, n0, B, Y, W, red);
+      p_residual_zero<TV, RB>(a, ys, cnt, n0, (C*)a.B, Y, W, red);
     else
       p_product<TV, TE, RB>(1, a, S, Y, ys, ws, cnt, n0, act, B, W, red);
     if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
@@ -911,6 +927,9 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   pa.minv_off = ctx->minv_off;
   pa.Minv = ctx->Minv;
   pa.X = Bf.X;
+  pa.frames = Bf.frames;
+  pa.k = ctx->k;
+  pa.geo = RhsGeo{ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns};
   if (!*Bf.sync_clean) SWM_CK(cudaMemsetAsync(Bf.sync, 0, sizeof(PSync), st));
   *Bf.sync_clean = false;  // until persist_result has seen the launch end without a timeout
   void* args[] = {&pa};

@@ -11,74 +11,23 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "rhs_entry.cuh"
 
 namespace swm {
 
 namespace {
 
-// x mod 2 pi in float64 (two-constant Cody-Waite split), result in [-pi, pi].
-__device__ __forceinline__ double reduce_2pi(double x) {
-  const double inv2pi = 0.15915494309189535;
-  const double c1 = 6.28318530717958623;      // 2 pi rounded to double
-  const double c2 = 2.4492935982947064e-16;   // 2 pi - c1
-  const double n = rint(x * inv2pi);
-  return fma(-n, c2, fma(-n, c1, x));
-}
-
-__device__ __forceinline__ double sinc_d(double z) { return fabs(z) < 1e-8 ? 1.0 - z * z / 6.0 : sin(z) / z; }
-// sin(z)/z in float: Taylor series to z^6 on |z| <= 0.5 (truncation below 2e-8 relative), else
-// sinf(z)/z; the fast __sinf is avoided because its error is absolute, not relative.
-__device__ __forceinline__ float sinc_f(float z) {
-  const float z2 = z * z;
-  if (z2 <= 0.25f) return 1.0f + z2 * (-1.0f / 6.0f + z2 * (1.0f / 120.0f + z2 * (-1.0f / 5040.0f)));
-  return sinf(z) / z;
-}
-
-// One thread per (wire, incidence).  frames: per incidence khat[3], e[3].
+// One thread per (unknown, incidence).  frames: per incidence khat[3], e[3].
 template <typename TV>
-__global__ void k_rhs(int64_t nw, int n_inc, const double* __restrict__ cx, const double* __restrict__ cy,
-                      const double* __restrict__ cz, const double* __restrict__ tx, const double* __restrict__ ty,
-                      const double* __restrict__ tz, const double* __restrict__ Ls, const int32_t* __restrict__ ns,
-                      const int64_t* __restrict__ off, int64_t N, double k, const double* __restrict__ frames,
+__global__ void k_rhs(int64_t N, int n_inc, RhsGeo g, const int32_t* __restrict__ rowwire,
+                      const int64_t* __restrict__ off, double k, const double* __restrict__ frames,
                       cplx<TV>* __restrict__ B) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= nw * n_inc) return;
-  const int64_t p = e % nw;
-  const int r = (int)(e / nw);
-  const double* f = frames + 6 * r;
-  const double kt = f[0] * tx[p] + f[1] * ty[p] + f[2] * tz[p];
-  const double et = f[3] * tx[p] + f[4] * ty[p] + f[5] * tz[p];
-  const double ph0 = -k * (f[0] * cx[p] + f[1] * cy[p] + f[2] * cz[p]);
-  const int n = ns[p];
-  const double D = Ls[p] / n;
-  const double beta = -k * kt;  // exp(j beta s)
-  const double s1 = -0.5 * Ls[p] + D;
-  cplx<TV>* out = B + (int64_t)r * N + off[p];
-  if constexpr (sizeof(TV) == 8) {
-    const double sc = sinc_d(0.5 * beta * D);
-    const double amp = et * D * sc * sc;
-    double sa, ca, sb, cb;
-    sincos(ph0 + beta * s1, &sa, &ca);
-    sincos(beta * D, &sb, &cb);
-    c128 z = mkc(amp * ca, amp * sa);
-    const c128 rat = mkc(cb, sb);
-    for (int l = 0; l < n - 1; ++l) {
-      out[l] = z;
-      z = z * rat;
-    }
-  } else {
-    const float sc = sinc_f((float)(0.5 * beta * D));
-    const float amp = (float)(et * D) * sc * sc;
-    float sa, ca, sb, cb;
-    sincosf((float)reduce_2pi(ph0 + beta * s1), &sa, &ca);
-    sincosf((float)(beta * D), &sb, &cb);
-    c64 z = mkc(amp * ca, amp * sa);
-    const c64 rat = mkc(cb, sb);
-    for (int l = 0; l < n - 1; ++l) {
-      out[l] = z;
-      z = z * rat;
-    }
-  }
+  if (e >= N * n_inc) return;
+  const int64_t n = e % N;
+  const int r = (int)(e / N);
+  const int64_t p = rowwire[n];
+  B[(int64_t)r * N + n] = rhs_entry<TV>(g, p, (int)(n - off[p]), frames + 6 * r, k);
 }
 
 // Geometry access: structure-of-arrays (internal) or caller arrays (centres/dirs as nw x 3).
@@ -493,26 +442,28 @@ int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_str
 }
 
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
-  const int64_t tot = ctx->nw * (int64_t)n_inc;
+  SWM_TRY(ensure_rowinfo(ctx));
+  const int64_t tot = ctx->N * (int64_t)n_inc;
   const unsigned grid = (unsigned)ceil_div(tot, 256);
+  const RhsGeo g{ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns};
   ctx->prof_begin(SWM_K_RHS);
   if (ctx->prec == SWM_C128)
-    k_rhs<double><<<grid, 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz,
-                                                 ctx->L, ctx->ns, ctx->off, ctx->N, ctx->k, frames_dev,
+    k_rhs<double><<<grid, 256, 0, ctx->stream>>>(ctx->N, n_inc, g, ctx->rowwire, ctx->off, ctx->k, frames_dev,
                                                  (c128*)ctx->Bv);
   else
-    k_rhs<float><<<grid, 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz,
-                                                ctx->L, ctx->ns, ctx->off, ctx->N, ctx->k, frames_dev, (c64*)ctx->Bv);
+    k_rhs<float><<<grid, 256, 0, ctx->stream>>>(ctx->N, n_inc, g, ctx->rowwire, ctx->off, ctx->k, frames_dev,
+                                                (c64*)ctx->Bv);
   ctx->prof_end(SWM_K_RHS);
   SWM_LAUNCHED();
   return SWM_OK;
 }
 
 int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out) {
-  const int64_t tot = ctx->nw * (int64_t)n_inc;
-  k_rhs<double><<<(unsigned)ceil_div(tot, 256), 256, 0, ctx->stream>>>(ctx->nw, n_inc, ctx->cx, ctx->cy, ctx->cz,
-                                                                     ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns,
-                                                                     ctx->off, ctx->N, ctx->k, frames_dev, out);
+  SWM_TRY(ensure_rowinfo(ctx));
+  const int64_t tot = ctx->N * (int64_t)n_inc;
+  const RhsGeo g{ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns};
+  k_rhs<double><<<(unsigned)ceil_div(tot, 256), 256, 0, ctx->stream>>>(ctx->N, n_inc, g, ctx->rowwire, ctx->off,
+                                                                     ctx->k, frames_dev, out);
   SWM_LAUNCHED();
   return SWM_OK;
 }
