@@ -141,7 +141,7 @@ def cpu_baseline(n_wires=1000):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, mid workload, from one ncu capture of
 # the kernel's current code (profiles/gmres_persist_mid.md)
-MEASURED_TRAFFIC = {("gmres", "c64"): 3.978e6}
+MEASURED_TRAFFIC = {("gmres", "c64"): 6.393e6}
 
 
 # ---------------------------------------------------------------------------------- ranks
@@ -186,12 +186,14 @@ def kernel_roofline(cls, st, prof_ms, launches, prec, n_rhs, pk, clocks):
         # row descriptors and the gathered vector u, then the delayed Gram-Schmidt: dots over
         # V_0..V_{j-1}, u, w and the update reading them and writing V_j and the next u; the closing
         # pass of a cycle reads V_0..V_{j-1} and u; per restart cycle: the residual product and the
-        # update of y by the basis.
+        # update of y by the basis; once: b formed from the wire geometry (centre, direction, length,
+        # segment count) and written, and x = M^-1 y (the inverse blocks, y read, x written).
         mat = st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N
         vec = N * esz * n_rhs
         per_solve = sum(mat + vec + (2 * j + 6) * vec for j in st["_steps"])
         per_solve += sum((c + 1) * vec for c in st["_cycle_len"])
         per_solve += (st["restarts"] + 1) * (mat + 3 * vec) + sum(st["_cycle_len"]) * vec
+        per_solve += nw * (7 * 8 + 4) + vec + st["nminv"] * esz + 2 * vec
         work = per_solve * st["_cycles_mult"]
         return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
                 "unit": "GB/s", "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms,

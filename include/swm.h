@@ -116,8 +116,10 @@ typedef struct swm_stats {
   int pattern_reused;      /* 1 if the last build kept the previous S-NFC pattern (same cloud and
                               r_c, e.g. a frequency sweep) and only refilled the values */
   int step_rhs_block;      /* incidences sharing each read of the blocks in the last solve's
-                              per-kernel GMRES step (1, or 4 / 8 / 16 as timed on the system the
-                              first time a shape was solved on this context) */
+                              per-kernel GMRES product (1, 4, 8 or 16, or 32 for the
+                              incidence-minor form, as timed on the system the first time a shape
+                              was solved on this context) */
+  int64_t nminv;           /* stored entries of the self-block inverses (sum over wires of m_p^2) */
 } swm_stats;
 
 /* kernel classes for swm_profile */
@@ -128,12 +130,13 @@ typedef struct swm_stats {
 #define SWM_K_INVERT 4      /* self-block inverses */
 #define SWM_K_FORM_E 5      /* Z_pq Z_qq^-1 */
 #define SWM_K_RHS 6         /* right-hand sides */
-#define SWM_K_APPLY 7       /* block-sparse product (fused with the first Gram-Schmidt pass when
-                               N < 2^19), and the residual product at each restart */
-#define SWM_K_DOTS 8        /* first Gram-Schmidt pass when it runs on its own (N >= 2^19);
-                               below that it is part of SWM_K_APPLY */
-#define SWM_K_UPDATE 9      /* second Gram-Schmidt pass */
-#define SWM_K_FINISH 10     /* norm, Hessenberg column, rotation */
+#define SWM_K_APPLY 7       /* block-sparse product w = A u of each Arnoldi step (with the transpose
+                               to incidence-minor order when that form runs), and the residual
+                               b - A y at each restart */
+#define SWM_K_DOTS 8        /* dots of the delayed Gram-Schmidt (Q^H u, Q^H w, |u|^2, u^H w) with the
+                               Hessenberg column, rotation and residual estimate they complete */
+#define SWM_K_UPDATE 9      /* update of the delayed Gram-Schmidt (q_j and the next vector) */
+#define SWM_K_FINISH 10     /* unused (kept so that class numbers stay as they were) */
 #define SWM_K_FAR 11        /* far field: partial sums and their reduction to RCS */
 #define SWM_K_GMRES 12      /* the whole solve as one persistent cooperative kernel (systems below
                                SWM_SPLIT_ROWS unknowns with at most 8 right-hand sides); the
@@ -141,9 +144,8 @@ typedef struct swm_stats {
 
 /* Create a context on CUDA device `device` that issues all work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context.
- * Environment: SWM_SPLIT_ROWS (default 524288) -- systems with at least this many unknowns run
- * each GMRES step as a streaming block-sparse product plus separate dot products, smaller ones
- * as one fused kernel; SWM_PERSIST (default 1) -- 0 solves small systems with one launch per
+ * Environment: SWM_SPLIT_ROWS (default 524288) -- systems with at least this many unknowns never
+ * run the persistent solve; SWM_PERSIST (default 1) -- 0 solves small systems with one launch per
  * kernel of each GMRES step instead of the persistent cooperative kernel;
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the
  * persistent solve wait for n arrivals that never come, so each wait runs out (after 1 s) and the

@@ -518,6 +518,7 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->stats.nnz = ctx->full.nval;
   ctx->stats.nnz_offd = ctx->offd.nval;
   ctx->stats.ncm_offd = ctx->offd.ncm;
+  ctx->stats.nminv = ctx->nminv;
   ctx->built = true;
   ctx->prof_flush();
   return SWM_OK;

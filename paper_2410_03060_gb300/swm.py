@@ -40,7 +40,7 @@ class swm_stats(C.Structure):
                 ("ms_rcs", C.c_double), ("kernel_launches", C.c_int64), ("fill_evals", C.c_int64),
                 ("nnz_offd", C.c_int64), ("ncm_offd", C.c_int64), ("prof_ms", C.c_double),
                 ("prof_launches", C.c_int64), ("pattern_reused", C.c_int),
-                ("step_rhs_block", C.c_int)]
+                ("step_rhs_block", C.c_int), ("nminv", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
