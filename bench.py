@@ -237,10 +237,8 @@ def run_ours(args):
     ctx = swm.swm_create(local)
 
     def step(prec=prec_id, inputs=dev, out=sigma):
-        swm.swm_set_cloud(ctx, *inputs)
-        swm.swm_build(ctx, K0, R_C, prec)
-        swm.swm_solve(ctx, inc, TOL, RESTART, 1000)
-        swm.swm_rcs_bistatic(ctx, obs, out)
+        # set_cloud, build, solve and the bistatic RCS in one C-ABI call (swm_run)
+        swm.swm_run(ctx, *inputs, K0, R_C, prec, inc, obs, out, TOL, RESTART, 1000)
 
     for _ in range(args.warmup):
         step()

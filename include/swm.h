@@ -251,6 +251,18 @@ int swm_net_train_step(swm_net* net, swm_ctx* ctx, int n_inc, const double* inc,
  * n_inc x n_obs x 2 float64 (theta- and phi-received), memory of kind out_kind. */
 int swm_rcs_bistatic(swm_ctx* ctx, int n_obs, const double* obs, double* sigma_out, int out_kind);
 
+/* The whole path in one call: swm_set_cloud, swm_build, swm_solve (no currents_out) and
+ * swm_rcs_bistatic with the same arguments, meanings and results as those calls made in turn (the
+ * paper has no counterpart; this is an entry point of this library).  It synchronises the host only
+ * where it needs device results (the cloud's bounding box, the pattern sizes, the RCS): the build's
+ * checks and the solver's final state are read after the last synchronisation, so a singular self
+ * block is reported (SWM_EINVAL) after the solve and RCS have run on it.  Returns the first error,
+ * else the solve's status (SWM_OK or SWM_ENOTCONV).  Statistics as after the separate calls. */
+int swm_run(swm_ctx* ctx, int64_t nw, const double* centres, const double* dirs, const double* lengths,
+            const double* radii, const int32_t* nseg, int mem_kind, double k, double r_c, int precision, int n_inc,
+            const double* inc, double tol, int restart, int max_iter, int n_obs, const double* obs,
+            double* sigma_out, int out_kind);
+
 /* Monostatic RCS (Sec. III-B): each incidence observed back along its arrival direction.
  * sigma_out receives n_inc x 2 float64, memory of kind out_kind. */
 int swm_rcs_monostatic(swm_ctx* ctx, double* sigma_out, int out_kind);

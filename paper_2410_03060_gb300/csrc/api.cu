@@ -224,14 +224,16 @@ int copy_in(swm_ctx* ctx, void* dst, const void* src, size_t bytes, int kind) {
 }
 
 // A small host input copied to the device through the context's pinned staging area (no staged
-// pageable copy); inputs that do not fit are copied directly.
-int upload(swm_ctx* ctx, void* dst, const void* src, size_t bytes, size_t* used) {
+// pageable copy); inputs that do not fit are copied directly.  ctx->up_used is the part of the area
+// whose copies may still be pending: every entry point that ends with a synchronisation clears it
+// when it starts, and swm_run (which synchronises only at its end) clears it once for all its steps.
+int upload(swm_ctx* ctx, void* dst, const void* src, size_t bytes) {
   SWM_TRY(ensure_poll_slots(ctx));
-  if (*used + bytes <= kPinnedUpBytes) {
-    char* stage = static_cast<char*>(ctx->pinned_state) + kPinnedUpOffset + *used;
+  if (ctx->up_used + bytes <= kPinnedUpBytes) {
+    char* stage = static_cast<char*>(ctx->pinned_state) + kPinnedUpOffset + ctx->up_used;
     std::memcpy(stage, src, bytes);
     SWM_CK(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    *used += (bytes + 15) & ~size_t(15);
+    ctx->up_used += (bytes + 15) & ~size_t(15);
     return SWM_OK;
   }
   SWM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -510,8 +512,10 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   if (ctx->bf16) SWM_TRY(make_e16(ctx));
   ctx->phase_end(swm_ctx::PH_PRECOND);
   SWM_TRY(finish_build(ctx));
-  SWM_CK(cudaStreamSynchronize(ctx->stream));
-  ctx->phase_collect();
+  if (!ctx->fused) {
+    SWM_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->phase_collect();
+  }
   SWM_CK(cudaGetLastError());
   ctx->stats.n = ctx->N;
   ctx->stats.nb = ctx->nb;
@@ -520,7 +524,7 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
   ctx->stats.ncm_offd = ctx->offd.ncm;
   ctx->stats.nminv = ctx->nminv;
   ctx->built = true;
-  ctx->prof_flush();
+  if (!ctx->fused) ctx->prof_flush();
   return SWM_OK;
 }
 
@@ -558,7 +562,7 @@ static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, in
   for (int i = 0; i < 3 * n_inc; ++i)
     if (!std::isfinite(inc[i])) return ctx->fail(SWM_EINVAL, "non-finite incidence angle");
   SWM_TRY(set_device(ctx));
-  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  if (!ctx->fused) SWM_CK(cudaStreamSynchronize(ctx->stream));  // inside swm_run the stream orders it
   dfree_group(ctx, ctx->solve_bufs);
   ctx->solved = false;
   ctx->n_rhs = n_inc;
@@ -571,9 +575,9 @@ static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, in
   SWM_TRY(dalloc(ctx, S, (void**)&frames, sizeof(double) * 6 * n_inc));
   std::vector<double> fh;
   frames_host(inc, n_inc, fh);
-  size_t staged = 0;
-  SWM_TRY(upload(ctx, ctx->inc_dev, inc, sizeof(double) * 3 * n_inc, &staged));
-  SWM_TRY(upload(ctx, frames, fh.data(), sizeof(double) * 6 * n_inc, &staged));
+  if (!ctx->fused) ctx->up_used = 0;  // the stream was synchronised above
+  SWM_TRY(upload(ctx, ctx->inc_dev, inc, sizeof(double) * 3 * n_inc));
+  SWM_TRY(upload(ctx, frames, fh.data(), sizeof(double) * 6 * n_inc));
   // GMRES from zero forms b itself when it runs as the persistent solve (each CTA its rows, in its
   // first residual); every other path gets it from the RHS kernel here or in the solver
   const bool defer_rhs = !ctx->bf16 && ctx->solver == SWM_SOLVER_GMRES && !x0;
@@ -616,9 +620,11 @@ static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, in
   ctx->phase_end(swm_ctx::PH_SOLVE);
   ctx->guess = nullptr;
   ctx->rhs_frames = nullptr;
-  SWM_CK(cudaStreamSynchronize(ctx->stream));
-  ctx->phase_collect();
-  ctx->prof_flush();
+  if (!ctx->fused) {
+    SWM_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->phase_collect();
+    ctx->prof_flush();
+  }
   if (rc < 0) return rc;
   ctx->stats.n_rhs = n_inc;
   ctx->solved = true;
@@ -658,6 +664,7 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
       if (!std::isfinite(obs[i])) return ctx->fail(SWM_EINVAL, "non-finite observation angle");
   }
   SWM_TRY(set_device(ctx));
+  if (!ctx->fused) ctx->up_used = 0;  // the previous entry point ended with a synchronisation
   ctx->phase_begin(swm_ctx::PH_RCS);
   const int R = ctx->n_rhs;
   const int64_t npairs = mono ? R : (int64_t)R * n_obs;
@@ -666,8 +673,7 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
   int stride = 3;
   if (!mono) {
     SWM_TRY(dalloc(ctx, tmp, (void**)&obs_dev, sizeof(double) * 2 * n_obs));
-    size_t staged = 0;
-    SWM_TRY(upload(ctx, obs_dev, obs, sizeof(double) * 2 * n_obs, &staged));
+    SWM_TRY(upload(ctx, obs_dev, obs, sizeof(double) * 2 * n_obs));
     stride = 2;
   }
   const size_t sb = ctx->prec == SWM_C64
@@ -709,6 +715,50 @@ int swm_rcs_bistatic(swm_ctx* ctx, int n_obs, const double* obs, double* sigma_o
 
 int swm_rcs_monostatic(swm_ctx* ctx, double* sigma_out, int out_kind) {
   return rcs_common(ctx, 0, nullptr, true, sigma_out, out_kind);
+}
+
+int swm_run(swm_ctx* ctx, int64_t nw, const double* centres, const double* dirs, const double* lengths,
+            const double* radii, const int32_t* nseg, int mem_kind, double k, double r_c, int precision, int n_inc,
+            const double* inc, double tol, int restart, int max_iter, int n_obs, const double* obs,
+            double* sigma_out, int out_kind) {
+  if (!ctx) return SWM_EINVAL;
+  int rc = swm_set_cloud(ctx, nw, centres, dirs, lengths, radii, nseg, mem_kind);
+  if (rc < 0) return rc;
+  // the host needs nothing from the build's end or the solve until the RCS is read back
+  ctx->fused = true;
+  ctx->build_check_pending = false;
+  ctx->pend.active = false;
+  ctx->up_used = 0;  // swm_set_cloud ended with a synchronisation
+  rc = swm_build(ctx, k, r_c, precision);
+  int solve_rc = SWM_OK;
+  if (rc >= 0) {
+    solve_rc = swm_solve(ctx, n_inc, inc, tol, restart, max_iter, nullptr, SWM_HOST);
+    if (solve_rc >= 0) rc = swm_rcs_bistatic(ctx, n_obs, obs, sigma_out, out_kind);
+    else rc = solve_rc;
+  }
+  ctx->fused = false;
+  // every later check after one synchronisation (the RCS call ended with one unless it failed)
+  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess && rc >= 0) rc = ctx->fail(SWM_ECUDA, std::string("swm_run: ") + cudaGetErrorString(e));
+  ctx->phase_collect();
+  ctx->prof_flush();
+  if (ctx->build_check_pending) {
+    ctx->build_check_pending = false;
+    const int bc = finish_build_check(ctx);
+    if (bc < 0) {
+      ctx->built = ctx->solved = false;
+      return bc;
+    }
+  }
+  if (ctx->pend.active) {
+    solve_rc = finish_solve(ctx);
+    if (solve_rc < 0) {
+      ctx->solved = false;
+      return solve_rc;
+    }
+  }
+  if (rc < 0) return rc;
+  return solve_rc;
 }
 
 int swm_get_stats(const swm_ctx* ctx, swm_stats* out) {

@@ -126,6 +126,16 @@ struct swm_ctx {
   void* pinned_state = nullptr;           // two pinned slots for the Krylov state poll
   unsigned* d_arrive = nullptr;           // arrival counter of the cloud-check kernel (kept zero)
   const double* rhs_frames = nullptr;     // b not yet formed: the solver forms it from these frames
+  // swm_run: the build's and the persistent solve's final read-backs are left in pinned memory and
+  // checked after the run's last synchronisation
+  bool fused = false;
+  bool build_check_pending = false;
+  size_t up_used = 0;  // bytes of the pinned staging area with copies possibly pending
+  struct PendingSolve {
+    bool active = false;
+    int R = 0;
+    bool* sync_clean = nullptr;
+  } pend;
   int solver = 0;                         // SWM_SOLVER_GMRES or SWM_SOLVER_GCR
   // right-hand sides per block of the fused multi-incidence GMRES step, measured per system shape
   // (N, n_rhs, vector and matrix entry sizes, chunk, restart)
@@ -243,6 +253,8 @@ int build_pattern(swm_ctx* ctx);
 int ensure_user_offsets(swm_ctx* ctx);
 // precond.cu: read the build's deferred device flags and counters
 int finish_build(swm_ctx* ctx);
+int finish_build_check(swm_ctx* ctx);
+int finish_solve(swm_ctx* ctx);
 // scan.cu
 int exclusive_scan_i64(swm_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);
 int exclusive_scan_i32_to_i64(swm_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host);
@@ -304,7 +316,8 @@ cudaError_t occupancy_cached(const void* fn, int threads, size_t smem, int* bloc
 constexpr size_t kPollSlotBytes = 65536;
 constexpr size_t kIngestSlotOffset = 128;
 constexpr size_t kPersistStateOffset = 192;
-constexpr size_t kPersistAbortOffset = 240;
+constexpr size_t kPersistAbortOffset = 224;
+constexpr size_t kBuildCountersOffset = 232;  // fill evaluations (8 bytes) and the singular flag (4)
 constexpr size_t kPinnedResidOffset = 256;
 constexpr size_t kPinnedUpOffset = 32768;
 constexpr size_t kPinnedUpBytes = kPollSlotBytes - kPinnedUpOffset;

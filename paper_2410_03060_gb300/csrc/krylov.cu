@@ -975,6 +975,16 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   std::vector<double> res(R);
   double* rpin = reinterpret_cast<double*>(static_cast<char*>(ctx->pinned_state) + kPinnedResidOffset);
   const bool rp = R <= kPinnedResidMax;
+  if (persisted && rp && ctx->fused && !hs_out) {
+    // inside swm_run: the residuals and the solver state are read after the run's last
+    // synchronisation (finish_solve)
+    SWM_CK(cudaMemcpyAsync(rpin, P.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    ctx->pend.active = true;
+    ctx->pend.R = R;
+    ctx->pend.sync_clean = &ws->sync_clean;
+    dfree_group(ctx, tmp);
+    return SWM_OK;
+  }
   SWM_CK(cudaMemcpyAsync(rp ? rpin : res.data(), P.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
   SWM_CK(cudaStreamSynchronize(st));
   if (rp) std::memcpy(res.data(), rpin, sizeof(double) * R);
@@ -1077,6 +1087,22 @@ int apply_minv(swm_ctx* ctx, const void* Y) {
                                                         (const c64*)ctx->Minv, (const c64*)Y, (c64*)ctx->Xv);
   SWM_LAUNCHED();
   return SWM_OK;
+}
+
+int finish_solve(swm_ctx* ctx) {
+  ctx->pend.active = false;
+  KState hs{};
+  SWM_TRY(persist_result(ctx, &hs, ctx->pend.sync_clean));
+  const double* rpin = reinterpret_cast<const double*>(static_cast<const char*>(ctx->pinned_state) +
+                                                       kPinnedResidOffset);
+  double mx = 0.0;
+  for (int r = 0; r < ctx->pend.R; ++r) mx = std::max(mx, rpin[r]);
+  ctx->stats.iterations = hs.iters;
+  ctx->stats.restarts = hs.cycles;
+  ctx->stats.rel_residual = mx;
+  ctx->stats.converged = hs.all_conv ? 1 : 0;
+  if (hs.numeric) return ctx->fail(SWM_ECUDA, "GMRES produced a non-finite value");
+  return hs.all_conv ? SWM_OK : SWM_ENOTCONV;
 }
 
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter) {

@@ -236,12 +236,23 @@ int make_e16(swm_ctx* ctx) {
   return SWM_OK;
 }
 
+// The build's counters (fill evaluations, singular self block) to pinned memory; checked here, or
+// inside swm_run after its last synchronisation.
 int finish_build(swm_ctx* ctx) {
   SWM_TRY(ensure_poll_slots(ctx));
-  char* pin = static_cast<char*>(ctx->pinned_state) + kPinnedResidOffset;
+  char* pin = static_cast<char*>(ctx->pinned_state) + kBuildCountersOffset;
   SWM_CK(cudaMemcpyAsync(pin, ctx->d_evals, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
   SWM_CK(cudaMemcpyAsync(pin + 8, ctx->d_sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->fused) {
+    ctx->build_check_pending = true;
+    return SWM_OK;
+  }
   SWM_CK(cudaStreamSynchronize(ctx->stream));
+  return finish_build_check(ctx);
+}
+
+int finish_build_check(swm_ctx* ctx) {
+  const char* pin = static_cast<const char*>(ctx->pinned_state) + kBuildCountersOffset;
   unsigned long long evals = 0;
   int sing = 0;
   std::memcpy(&evals, pin, sizeof(evals));

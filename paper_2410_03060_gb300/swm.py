@@ -58,6 +58,8 @@ _SIGS = {
     "swm_solve": (C.c_int, [_P, C.c_int, _P, C.c_double, C.c_int, C.c_int, _P, C.c_int]),
     "swm_rcs_bistatic": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "swm_rcs_monostatic": (C.c_int, [_P, _P, C.c_int]),
+    "swm_run": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _P,
+                          C.c_double, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int]),
     "swm_get_stats": (C.c_int, [_P, C.POINTER(swm_stats)]),
     "swm_profile": (C.c_int, [_P, C.c_int]),
     "swm_get_pattern": (C.c_int, [_P, _P]),
@@ -346,6 +348,26 @@ def swm_rcs_monostatic(ctx: Ctx, sigma_out) -> int:
     n_inc = swm_get_stats(ctx)["n_rhs"]
     ps, kind, _ = _out_ptr(sigma_out, np.float64, (n_inc, 2), "sigma_out")
     return _check(ctx, load().swm_rcs_monostatic(ctx.handle, ps, kind))
+
+
+def swm_run(ctx: Ctx, centres, dirs, lengths, radii, nseg, k: float, r_c: float, precision: int, inc, obs,
+            sigma_out, tol: float = 1e-6, restart: int = 50, max_iter: int = 1000) -> int:
+    """swm_set_cloud, swm_build, swm_solve and swm_rcs_bistatic in one call (synchronising only
+    where the host needs device results); sigma_out as for swm_rcs_bistatic."""
+    nw = len(lengths)
+    pc, k1, a1 = _ptr(centres, np.float64, (nw, 3), "centres")
+    pt, k2, a2 = _ptr(dirs, np.float64, (nw, 3), "dirs")
+    pl, k3, a3 = _ptr(lengths, np.float64, (nw,), "lengths")
+    pr, k4, a4 = _ptr(radii, np.float64, (nw,), "radii")
+    pn, k5, a5 = _ptr(nseg, np.int32, (nw,), "nseg")
+    if len({k1, k2, k3, k4, k5}) != 1:
+        raise TypeError("swm_run: all cloud inputs must be host arrays or all device tensors")
+    inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+    obs = np.ascontiguousarray(np.atleast_2d(obs), dtype=np.float64)
+    ps, kind, _ = _out_ptr(sigma_out, np.float64, (inc.shape[0], obs.shape[0], 2), "sigma_out")
+    return _check(ctx, load().swm_run(ctx.handle, nw, pc, pt, pl, pr, pn, k1, float(k), float(r_c), int(precision),
+                                      inc.shape[0], inc.ctypes.data_as(C.c_void_p), float(tol), int(restart),
+                                      int(max_iter), obs.shape[0], obs.ctypes.data_as(C.c_void_p), ps, kind))
 
 
 def swm_get_stats(ctx: Ctx) -> dict:
