@@ -105,7 +105,8 @@ struct RowCounts {
 };
 
 // mode 0: count kept partners per wire (and the sizes in RowCounts); mode 1: write them (sorted)
-// into col.  One warp per wire: lanes 0..8 look up the nine (z, y) rows of three cells around the
+// into col, with the position of each row's diagonal block and every block's first column in the
+// full layout and in the layout without the diagonal block (-1 for the diagonal).  One warp per wire: lanes 0..8 look up the nine (z, y) rows of three cells around the
 // wire's cell at once (each a contiguous range of the renumbered wires), a warp scan lays the
 // ranges end to end, and the warp tests 32 candidates per pass, so a wire costs about three
 // dependent memory round trips whatever its cell occupancy.  Candidates are visited in increasing
@@ -113,7 +114,8 @@ struct RowCounts {
 __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double* __restrict__ cy,
                         const double* __restrict__ cz, const int32_t* __restrict__ cid, const int64_t* __restrict__ cstart,
                         Grid g, double rc2, int dense, int mode, RowCounts rc, const int32_t* __restrict__ m,
-                        const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col) {
+                        const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col, int64_t* __restrict__ diag_b,
+                        int32_t* __restrict__ colpos_f, int32_t* __restrict__ colpos_o) {
   const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (p >= nw) return;
@@ -150,6 +152,10 @@ __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double*
   int64_t count = 0;
   int32_t msum = 0, nup = 0;  // this lane's kept m_q and kept q > p (counting pass)
   const int64_t base = mode ? row_ptr[p] : 0;
+  // writing pass: running offsets of the kept blocks' columns in the full layout and in the layout
+  // without the diagonal block (whose m_p columns the second one skips)
+  int32_t kf = 0, mp_seen = 0;
+  const int32_t mp_w = mode ? m[p] : 0;
   for (int64_t fb = 0; fb < total; fb += 32) {
     const int64_t f = fb + lane;
     bool keep = false;
@@ -170,7 +176,28 @@ __global__ void k_pairs(int64_t nw, const double* __restrict__ cx, const double*
       }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (mode && keep) col[base + count + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
+    if (mode) {
+      // column positions: exclusive warp scan of m_q over the kept lanes (in q order)
+      const int32_t mq = keep ? m[q] : 0;
+      int32_t incl = mq;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const unsigned dmask = __ballot_sync(0xffffffffu, keep && q == p);
+      if (keep) {
+        const int64_t b = base + count + __popc(bal & ((1u << lane) - 1u));
+        col[b] = (int32_t)q;
+        const int32_t pf = kf + incl - mq;
+        colpos_f[b] = pf;
+        const bool diag_before = mp_seen || (dmask & ((1u << lane) - 1u));
+        colpos_o[b] = q == p ? -1 : pf - (diag_before ? mp_w : 0);
+        if (q == p) diag_b[p] = b;
+      }
+      kf += __shfl_sync(0xffffffffu, incl, 31);
+      if (dmask) mp_seen = 1;
+    }
     if (!mode && keep) {
       msum += m[q];
       nup += q > p ? 1 : 0;
@@ -205,28 +232,6 @@ __device__ __forceinline__ int64_t find_in_row(const int32_t* __restrict__ col, 
       e = mid;
   }
   return b;
-}
-
-// Diagonal block and column positions of every block in both layouts.
-__global__ void k_row_meta(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ m, int64_t* __restrict__ diag_b, int32_t* __restrict__ colpos_f,
-                           int32_t* __restrict__ colpos_o) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= nw) return;
-  const int64_t b0 = row_ptr[p], b1 = row_ptr[p + 1];
-  diag_b[p] = find_in_row(col, b0, b1, (int32_t)p);
-  int32_t kf = 0, ko = 0;
-  for (int64_t b = b0; b < b1; ++b) {
-    const int32_t mq = m[col[b]];
-    colpos_f[b] = kf;
-    kf += mq;
-    if (col[b] == (int32_t)p) {
-      colpos_o[b] = -1;
-    } else {
-      colpos_o[b] = ko;
-      ko += mq;
-    }
-  }
 }
 
 __global__ void k_transpose_and_upper(int64_t nw, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -389,7 +394,8 @@ int build_pattern(swm_ctx* ctx) {
   RowCounts rcs{rcnt, ucnt, Kf, Ko, ent_f, ent_o, msq};
   ctx->prof_begin(SWM_K_PAIRS);
   k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
-                                              ctx->dense ? 1 : 0, 0, rcs, m, nullptr, nullptr);
+                                              ctx->dense ? 1 : 0, 0, rcs, m, nullptr, nullptr, nullptr, nullptr,
+                                              nullptr);
   ctx->prof_end(SWM_K_PAIRS);
   SWM_LAUNCHED();
   {
@@ -422,12 +428,14 @@ int build_pattern(swm_ctx* ctx) {
   ctx->offd.colpos = cpo;
   ctx->prof_begin(SWM_K_PAIRS);
   k_pairs<<<nblk(nw * 32, 256), 256, 0, st>>>(nw, ctx->cx, ctx->cy, ctx->cz, cid_s, cstart, g, rc2,
-                                              ctx->dense ? 1 : 0, 1, rcs, m, ctx->row_ptr, ctx->col);
+                                              ctx->dense ? 1 : 0, 1, rcs, m, ctx->row_ptr, ctx->col, ctx->diag_b,
+                                              cpf, cpo);
   ctx->prof_end(SWM_K_PAIRS);
   SWM_LAUNCHED();
 
-  // --- diagonal blocks and column positions, then (both need them) the transpose map with the
-  // upper-triangle block list, and the column maps on the build's second stream when it exists
+  // --- the transpose map with the upper-triangle block list, and the column maps on the build's
+  // second stream when it exists (both need the diagonal blocks and column positions that the
+  // writing pass of k_pairs produced)
   // the S-NFC pattern is symmetric, so the blocks above the diagonal are half the off-diagonal ones
   ctx->nup = (ctx->nb - nw) / 2;
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->bt, sizeof(int64_t) * ctx->nb));
@@ -437,14 +445,12 @@ int build_pattern(swm_ctx* ctx) {
   if (ctx->offd.ncm > INT32_MAX) return ctx->fail(SWM_EINVAL, "column map too large for 32-bit offsets");
   SWM_TRY(dalloc(ctx, B, (void**)&ctx->rowwire, sizeof(int32_t) * std::max<int64_t>(1, ctx->N)));
   SWM_TRY(dalloc(ctx, B, &ctx->rowinfo, sizeof(RowInfo) * std::max<int64_t>(1, ctx->N)));
-  k_row_meta<<<nblk(nw, 256), 256, 0, st>>>(nw, ctx->row_ptr, ctx->col, m, ctx->diag_b, cpf, cpo);
-  SWM_LAUNCHED();
   cudaStream_t s2 = ctx->side ? ctx->side : st;
   if (ctx->side) {
     SWM_CK(cudaEventRecord(ctx->side_ev[0], st));
     SWM_CK(cudaStreamWaitEvent(s2, ctx->side_ev[0], 0));
   }
-  // column maps (positions from k_row_meta, offsets, multiplicities) and the row descriptors
+  // column maps (positions from the writing pass, offsets, multiplicities) and the row descriptors
   k_colmap<<<nblk(nw, 256), 256, 0, s2>>>(nw, ctx->row_ptr, ctx->col, m, ctx->off, ctx->full, ctx->offd,
                                           ctx->rowwire, (RowInfo*)ctx->rowinfo);
   SWM_LAUNCHED();
