@@ -217,6 +217,17 @@ __global__ void k_to_user(int64_t N, int R, const int32_t* __restrict__ rowwire,
 
 
 
+// The device address of host memory the GPU can read and write in place (page-locked, registered
+// or allocated by CUDA), else null.
+void* device_view(const void* host) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int copy_in(swm_ctx* ctx, void* dst, const void* src, size_t bytes, int kind) {
   SWM_CK(cudaMemcpyAsync(dst, src, bytes, kind == SWM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          ctx->stream));
@@ -395,14 +406,26 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_L, sizeof(double) * nw));
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_a, sizeof(double) * nw));
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_ns, sizeof(int32_t) * nw));
-  if (mem_kind == SWM_HOST) {  // device inputs are copied by k_ingest itself
+  // Device inputs, and host inputs in page-locked memory (which the GPU reads in place over the
+  // host link), are copied by k_ingest itself; other host inputs are copied in first.
+  const void* src[5] = {centres, dirs, lengths, radii, nseg};
+  bool dev = mem_kind == SWM_DEVICE;
+  if (!dev) {
+    bool pinned = true;
+    for (int i = 0; i < 5 && pinned; ++i) {
+      void* dp = device_view(src[i]);
+      if (dp) src[i] = dp;
+      else pinned = false;
+    }
+    dev = pinned;
+  }
+  if (!dev) {
     SWM_TRY(copy_in(ctx, ctx->u_c, centres, sizeof(double) * 3 * nw, mem_kind));
     SWM_TRY(copy_in(ctx, ctx->u_t, dirs, sizeof(double) * 3 * nw, mem_kind));
     SWM_TRY(copy_in(ctx, ctx->u_L, lengths, sizeof(double) * nw, mem_kind));
     SWM_TRY(copy_in(ctx, ctx->u_a, radii, sizeof(double) * nw, mem_kind));
     SWM_TRY(copy_in(ctx, ctx->u_ns, nseg, sizeof(int32_t) * nw, mem_kind));
   }
-  const bool dev = mem_kind == SWM_DEVICE;
   std::vector<Buf> tmp;
   const int np = (int)std::min<int64_t>(ceil_div(nw, kIngestThreads), 2 * std::max(ctx->nsm, 1));
   if (!ctx->d_arrive) {  // the arrival counter of k_ingest: zero, and left zero by every launch
@@ -413,9 +436,10 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * 8 * (np + 1)));
   double* res = part + 8 * np;
   k_ingest<<<(unsigned)np, kIngestThreads, 0, ctx->stream>>>(
-      nw, dev ? centres : ctx->u_c, dev ? dirs : ctx->u_t, dev ? lengths : ctx->u_L, dev ? radii : ctx->u_a,
-      dev ? nseg : ctx->u_ns, dev ? 1 : 0, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a, ctx->u_ns, part, ctx->d_arrive,
-      res);
+      nw, dev ? (const double*)src[0] : ctx->u_c, dev ? (const double*)src[1] : ctx->u_t,
+      dev ? (const double*)src[2] : ctx->u_L, dev ? (const double*)src[3] : ctx->u_a,
+      dev ? (const int32_t*)src[4] : ctx->u_ns, dev ? 1 : 0, ctx->u_c, ctx->u_t, ctx->u_L, ctx->u_a, ctx->u_ns, part,
+      ctx->d_arrive, res);
   SWM_LAUNCHED();
   SWM_TRY(ensure_poll_slots(ctx));
   double* hres = reinterpret_cast<double*>(static_cast<char*>(ctx->pinned_state) + kIngestSlotOffset);
@@ -681,11 +705,11 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
                         : far_field_scratch_bytes(ctx->nw, npairs);
   void* scratch = nullptr;
   SWM_TRY(dalloc(ctx, tmp, &scratch, sb));
-  double* sig = nullptr;
-  if (out_kind == SWM_DEVICE)
-    sig = sigma_out;
-  else
-    SWM_TRY(dalloc(ctx, tmp, (void**)&sig, sizeof(double) * 2 * npairs));
+  // the RCS goes straight to the caller's buffer when the GPU can write it (device memory, or
+  // page-locked host memory written in place over the host link)
+  double* sig = out_kind == SWM_DEVICE ? sigma_out : (double*)device_view(sigma_out);
+  const bool sig_direct = sig != nullptr;
+  if (!sig_direct) SWM_TRY(dalloc(ctx, tmp, (void**)&sig, sizeof(double) * 2 * npairs));
   std::string err;
   ctx->prof_begin(SWM_K_FAR);
   int rc;
@@ -699,7 +723,7 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
   }
   ctx->prof_end(SWM_K_FAR);
   if (rc < 0) return rc;
-  if (out_kind == SWM_HOST)
+  if (!sig_direct)
     SWM_CK(cudaMemcpyAsync(sigma_out, sig, sizeof(double) * 2 * npairs, cudaMemcpyDeviceToHost, ctx->stream));
   ctx->phase_end(swm_ctx::PH_RCS);
   SWM_CK(cudaStreamSynchronize(ctx->stream));
