@@ -147,6 +147,7 @@ typedef struct swm_stats {
  * Environment: SWM_SPLIT_ROWS (default 524288) -- systems with at least this many unknowns never
  * run the persistent solve; SWM_PERSIST (default 1) -- 0 solves small systems with one launch per
  * kernel of each GMRES step instead of the persistent cooperative kernel;
+ * SWM_PERSIST_CTAS (default 0 = one per SM) -- CTAs of the persistent solve, at most one per SM;
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the
  * persistent solve wait for n arrivals that never come, so each wait runs out (after 1 s) and the
  * solve returns SWM_ETIMEOUT; all read when the context is created. */

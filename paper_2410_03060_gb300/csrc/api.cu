@@ -327,6 +327,7 @@ int swm_create(swm_ctx** out, int device, void* cuda_stream) {
   ctx->stream = (cudaStream_t)cuda_stream;
   if (const char* e = std::getenv("SWM_SPLIT_ROWS")) ctx->split_rows = std::max<long long>(0, std::atoll(e));
   if (const char* e = std::getenv("SWM_PERSIST")) ctx->persist = std::atoi(e) != 0;
+  if (const char* e = std::getenv("SWM_PERSIST_CTAS")) ctx->persist_ctas = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("SWM_TEST_BARRIER_EXTRA")) ctx->test_barrier_extra = std::max(0, std::atoi(e));
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||

@@ -160,6 +160,7 @@ struct swm_ctx {
   // test hook (SWM_TEST_BARRIER_EXTRA): grid barriers of the persistent solve wait for this many
   // arrivals more than there are CTAs, so every wait runs out and the solve reports SWM_ETIMEOUT
   int test_barrier_extra = 0;
+  int persist_ctas = 0;                   // CTAs of the persistent solve (0: one per SM)
   int nsm = 0;
   int coop = 0;
   int smem_optin = 0;  // shared memory a CTA may opt in to (bytes)

@@ -867,7 +867,8 @@ int gmres_persistent(swm_ctx* ctx, const KPtr& P, const PBuffers& Bf, int max_it
   cudaStream_t st = ctx->stream;
   const int R = P.R, restart = P.restart;
   const int64_t N = P.N;
-  const int prows = (int)(ceil_div(ceil_div(std::max<int64_t>(N, 1), ctx->nsm > 0 ? ctx->nsm : 1), 32) * 32);
+  const int ctas = ctx->persist_ctas > 0 ? std::min(ctx->persist_ctas, std::max(ctx->nsm, 1)) : std::max(ctx->nsm, 1);
+  const int prows = (int)(ceil_div(ceil_div(std::max<int64_t>(N, 1), ctas), 32) * 32);
   if (!(ctx->persist && ctx->coop && Bf.sync && R <= kPersistMaxR && N > 0 && N < ctx->split_rows &&
         prows <= kPersistMaxRowsPerThread * kPT))
     return SWM_OK;
