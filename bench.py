@@ -52,7 +52,12 @@ def peaks():
 
 # ---------------------------------------------------------------------------------- helpers
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 50 ms while the timed region runs.
+
+    start() returns once nvidia-smi has written its first sample, so the sampler is running when
+    the timed region begins; mark() notes where the timed region starts in its output, and stop()
+    keeps the samples after the mark (the last one before it if the region was shorter than the
+    sampling period, flagged by "samples": 0)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -68,10 +73,25 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None and self._lines() == 0:
+            time.sleep(0.02)
+        self.mark0 = 0
+
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for line in f if line.strip())
+        except OSError:
+            return 0
+
+    def mark(self):
+        self.mark0 = self._lines()
 
     def stop(self):
         if self.proc is None:
@@ -81,9 +101,14 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = [line for line in open(self.path) if line.strip()]
+        mark0 = getattr(self, "mark0", 0)
+        during = lines[mark0:]
+        if not during:
+            during = lines[max(0, mark0 - 1):mark0]
+        sm, smax, reasons = [], [], set()
+        for line in during:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -97,7 +122,7 @@ class ClockSampler:
                     reasons.add(n)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(lines) - mark0, "reasons": sorted(reasons)}
 
 
 def rcs_db_error(s, ref, floor_db=30.0):
@@ -270,6 +295,7 @@ def run_ours(args):
     l0 = swm.swm_get_stats(ctx)["kernel_launches"]
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.mark()
     evs = []
     for _ in range(args.steps):
         flush.zero_()
