@@ -44,6 +44,7 @@ constexpr int kPWarps = kPT / 32;
 constexpr int kPersistMaxRowsPerThread = 4;
 constexpr unsigned long long kBarrierNs = 1000000000ull;  // 1 s
 constexpr unsigned kBarrierMaxPolls = 1u << 26;            // second bound on a wait (>= 1.3 s of sleeps)
+constexpr int kPLanesPerRow = 4;                         // lanes per row of the persistent product
 
 struct PArgs {
   KPtr P;                  // st, jlast, resid, H, coef, R, restart, N, tol
@@ -129,30 +130,33 @@ __device__ __forceinline__ cplx<double> ldcg_c<double>(const cplx<double>* p) {
 }
 
 // Grid barrier with a time limit.  Returns false (in every thread of the CTA) if this CTA gave up
-// or saw another CTA give up.
+// or saw another CTA give up.  Thread 0 arrives with an acquire-release add on the counter (its
+// release covers the CTA's writes before the __syncthreads); the arrival that completes the
+// barrier has acquired every earlier one, the others poll the counter with acquire loads.
 __device__ bool grid_sync(PSync* s, unsigned G, unsigned* epoch, int* ok_sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned target = (*epoch + 1u) * G;
     *epoch += 1u;
-    __threadfence();
-    atomicAdd(&s->count, 1u);
+    unsigned prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&s->count) : "memory");
     int ok = 1;
-    const unsigned long long t0 = global_ns();
-    unsigned polls = 0;
-    while (ld_acquire_u32(&s->count) < target) {
-      if (*(volatile int*)&s->abort) {
-        ok = 0;
-        break;
+    if (prev + 1u != target) {
+      const unsigned long long t0 = global_ns();
+      unsigned polls = 0;
+      while (ld_acquire_u32(&s->count) < target) {
+        if (*(volatile int*)&s->abort) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > kBarrierNs || ++polls > kBarrierMaxPolls) {
+          atomicExch(&s->abort, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
       }
-      if (global_ns() - t0 > kBarrierNs || ++polls > kBarrierMaxPolls) {
-        atomicExch(&s->abort, 1);
-        ok = 0;
-        break;
-      }
-      __nanosleep(20);
     }
-    __threadfence();
     *ok_sm = ok;
   }
   __syncthreads();
@@ -375,69 +379,74 @@ __device__ void p_product(int mode, const PArgs& a, const ESlice<TV, TE>& S, con
     nrm[b] = 0;
   }
   if (S.xg) {
-    // gather src at the column-map slice: every load in flight at once
-#pragma unroll 4
-    for (int q = threadIdx.x; q < S.clen; q += kPT) {
-      const int64_t col = S.cm[q];
+    // gather src at the column-map slice: a thread's GB entries (all right-hand sides) are loaded
+    // before any is stored, so they are in flight together
+    constexpr int GB = RB >= 8 ? 1 : 8 / RB;
+    for (int q0 = threadIdx.x; q0 < S.clen; q0 += GB * kPT) {
+      int col[GB];
 #pragma unroll
-      for (int b = 0; b < RB; ++b)
-        if (on[b]) S.xg[b * S.cstride + q] = ldcg_c<TV>(src + (int64_t)b * N + col);
+      for (int u = 0; u < GB; ++u) {
+        const int q = q0 + u * kPT;
+        col[u] = q < S.clen ? S.cm[q] : -1;
+      }
+      cplx<TV> v[GB][RB];
+#pragma unroll
+      for (int u = 0; u < GB; ++u)
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+          v[u][b] = (col[u] >= 0 && on[b]) ? ldcg_c<TV>(src + (int64_t)b * N + col[u]) : mkc<TV>(0, 0);
+#pragma unroll
+      for (int u = 0; u < GB; ++u)
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+          if (col[u] >= 0 && on[b]) S.xg[b * S.cstride + q0 + u * kPT] = v[u][b];
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < cnt; t += kPT) {
-    const RowInfo ri = S.ri[t];
-    const TE* e = S.e + (ri.vb - S.ebase);
+  // four lanes per row, each taking every fourth entry, so that the rows of a dense part of the
+  // cloud spread over the CTA's threads; passes over the rows are warp-uniform (quad sums below)
+  const int lane = threadIdx.x & 31, sub = lane & (kPLanesPerRow - 1);
+  constexpr int rows_per_warp = 32 / kPLanesPerRow;
+  for (int base = (int)(threadIdx.x >> 5) * rows_per_warp; base < cnt; base += kPWarps * rows_per_warp) {
+    const int t = base + lane / kPLanesPerRow;
+    const bool live = t < cnt;
     cplx<TV> acc[RB];
 #pragma unroll
     for (int b = 0; b < RB; ++b) acc[b] = mkc<TV>(0, 0);
-    if (S.xg) {
-      const cplx<TV>* xq = S.xg + (ri.cmb - S.cbase);
-      int c = 0;
-      for (; c + 1 < ri.K; c += 2) {
-        const cplx<TV> e0 = ELoad<TV, TE>::ld(e + c), e1 = ELoad<TV, TE>::ld(e + c + 1);
+    if (live) {
+      const RowInfo ri = S.ri[t];
+      const TE* e = S.e + (ri.vb - S.ebase);
+      if (S.xg) {
+        const cplx<TV>* xq = S.xg + (ri.cmb - S.cbase);
+#pragma unroll 2
+        for (int c = sub; c < ri.K; c += kPLanesPerRow) {
+          const cplx<TV> ev = ELoad<TV, TE>::ld(e + c);
 #pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) {
-            cfma(acc[b], e0, xq[b * S.cstride + c]);
-            cfma(acc[b], e1, xq[b * S.cstride + c + 1]);
-          }
-      }
-      if (c < ri.K) {
-        const cplx<TV> e0 = ELoad<TV, TE>::ld(e + c);
-#pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) cfma(acc[b], e0, xq[b * S.cstride + c]);
-      }
-    } else {
-      const int32_t* cm = S.cm + (ri.cmb - S.cbase);
-      int c = 0;
-      for (; c + 3 < ri.K; c += 4) {
-        cplx<TV> ev[4];
-        int64_t col[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          ev[u] = ELoad<TV, TE>::ld(e + c + u);
-          col[u] = cm[c + u];
+          for (int b = 0; b < RB; ++b)
+            if (on[b]) cfma(acc[b], ev, xq[b * S.cstride + c]);
         }
+      } else {
+        const int32_t* cm = S.cm + (ri.cmb - S.cbase);
+#pragma unroll 2
+        for (int c = sub; c < ri.K; c += kPLanesPerRow) {
+          const cplx<TV> ev = ELoad<TV, TE>::ld(e + c);
+          const int64_t col = cm[c];
 #pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) {
-            cplx<TV> x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = ldcg_c<TV>(src + (int64_t)b * N + col[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) cfma(acc[b], ev[u], x[u]);
-          }
-      }
-      for (; c < ri.K; ++c) {
-        const cplx<TV> ev = ELoad<TV, TE>::ld(e + c);
-        const int64_t col = cm[c];
-#pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (on[b]) cfma(acc[b], ev, ldcg_c<TV>(src + (int64_t)b * N + col));
+          for (int b = 0; b < RB; ++b)
+            if (on[b]) cfma(acc[b], ev, ldcg_c<TV>(src + (int64_t)b * N + col));
+        }
       }
     }
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      if (b >= R) break;
+#pragma unroll
+      for (int o = 1; o < kPLanesPerRow; o <<= 1) {
+        acc[b].re += __shfl_xor_sync(0xffffffffu, acc[b].re, o);
+        acc[b].im += __shfl_xor_sync(0xffffffffu, acc[b].im, o);
+      }
+    }
+    if (!live || sub != 0) continue;
     const int64_t n = n0 + t;
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
@@ -672,10 +681,16 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
       if (!(ok = grid_sync(a.sync, a.arrivals, &s_epoch, &s_ok))) break;
       // B1: sums (s and |u|^2 in h1, t and u^H w in h2) and the first-pass coefficients of
       // column j-1, formed at the previous step by the owners of their rows
-      p_reduce2<TV>(part1, part2, G, R, R1, j, act, closing, h1, h2);
       const c128* hc_prev = ((j - 1) & 1) ? P.hc2 : P.hc;
       c128* hc_next = (j & 1) ? P.hc2 : P.hc;
-      for (int k = threadIdx.x; k < R * j; k += kPT) {
+      // a thread's first entry of column j-1 is loaded before the sums, so the two loads share
+      // one round trip to L2
+      const bool pre = j > 0 && (int)threadIdx.x < R * j && act[threadIdx.x / j];
+      const c128 hpre = pre ? ldcg_c<double>(hc_prev + (int64_t)(threadIdx.x / j) * R1 + threadIdx.x % j)
+                            : mkc(0.0, 0.0);
+      p_reduce2<TV>(part1, part2, G, R, R1, j, act, closing, h1, h2);
+      if (pre) colv[(threadIdx.x / j) * R1 + threadIdx.x % j] = ccast<TV>(hpre);
+      for (int k = threadIdx.x + kPT; k < R * j; k += kPT) {
         const int b = k / j, i = k % j;
         if (act[b]) colv[b * R1 + i] = ccast<TV>(ldcg_c<double>(hc_prev + (int64_t)b * R1 + i));
       }
@@ -686,6 +701,9 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
         const int b = k / j, i = k % j;
         if (act[b]) colv[b * R1 + i] = colv[b * R1 + i] + h1[b * R1 + i];
       }
+      // the activity before this step's rotations, for B3 (which runs beside them)
+      unsigned actm = 0;
+      for (int b = 0; b < R; ++b) actm |= act[b] ? 1u << b : 0u;
       if (wp < R && act[wp]) {
         const int b = wp;
         TV ss = 0, gr = 0, gi = 0;
@@ -712,15 +730,16 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
         }
       }
       __syncthreads();
-      // B3: rows k = blockIdx.x + m G (m < hown) of the unrotated matrix belong to this CTA and
-      // live in its shared memory: store their entries of column j-1, and form their first-pass
-      // coefficients of column j, (t_k - (H s)_k) / rho, and gamma - s_{j-1} for row j
-      if ((int)blockIdx.x <= j) {
+      // B3 (all warps but the last): rows k = blockIdx.x + m G (m < hown) of the unrotated matrix
+      // belong to this CTA and live in its shared memory: store their entries of column j-1, and
+      // form their first-pass coefficients of column j, (t_k - (H s)_k) / rho, and gamma - s_{j-1}
+      // for row j.  B3 reads the unrotated column, which B4 leaves in place.
+      if ((int)blockIdx.x <= j && wp < kPWarps - 1) {
         const int nown = (j - (int)blockIdx.x) / G + 1;
-        for (int pr = wp; pr < nown * R; pr += kPWarps) {
+        for (int pr = wp; pr < nown * R; pr += kPWarps - 1) {
           const int m = pr / R, b = pr % R;
           const int k = (int)blockIdx.x + m * G;
-          if (!act[b]) continue;
+          if (!((actm >> b) & 1u)) continue;
           C* hr = hrs + ((int64_t)b * hown + m) * RS;
           if (j >= 1 && lane == 0) hr[j - 1] = colv[b * R1 + k];
           if (closing) continue;
@@ -741,22 +760,25 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
           }
         }
       }
-      __syncthreads();
-      // B4: rotations of column j-1, residual estimate and activity (every CTA, same values)
-      if (threadIdx.x < R && act[threadIdx.x]) {
-        const int b = threadIdx.x;
+      // B4 (lanes of the last warp, beside B3): rotations of column j-1, residual estimate and
+      // activity (every CTA, same values); CTA 0 stores the rotated column to H
+      if (wp == kPWarps - 1 && lane < R && act[lane]) {
+        const int b = lane;
         const TV h = rho_s[b];
         if (j >= 1) {
           const int l = j - 1;
-          C* col = colv + b * R1;
+          const C* col = colv + b * R1;
+          c128* Hc = P.H + (int64_t)b * R1 * RS + l;
+          const bool keep = blockIdx.x == 0;
+          C xr = col[0];  // entry i of the column, rotated by the rotations before i
           for (int i = 0; i < l; ++i) {
-            const C x0 = col[i], x1 = col[i + 1];
+            const C x0 = xr, x1 = col[i + 1];
             const C sg = sn[b * RS + i];
             const TV c = cs[b * RS + i];
-            col[i] = c * x0 + sg * x1;
-            col[i + 1] = mkc<TV>(-sg.re, sg.im) * x0 + c * x1;
+            if (keep) Hc[(int64_t)i * RS] = ccast<double>(c * x0 + sg * x1);
+            xr = mkc<TV>(-sg.re, sg.im) * x0 + c * x1;
           }
-          const C x = col[l];
+          const C x = xr;
           const TV ax2 = x.re * x.re + x.im * x.im;
           const TV aa = sqrt(ax2);
           const TV nu = sqrt(ax2 + h * h);
@@ -773,7 +795,7 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
           }
           cs[b * RS + l] = c;
           sn[b * RS + l] = sv;
-          col[l] = c * x + h * sv;
+          if (keep) Hc[(int64_t)l * RS] = ccast<double>(c * x + h * sv);
           const C gl = gg[b * R1 + l];
           gg[b * R1 + l + 1] = mkc<TV>(-sv.re, sv.im) * gl;
           gg[b * R1 + l] = c * gl;
@@ -794,20 +816,16 @@ __global__ void __launch_bounds__(kPT, 1) k_gmres_persist(PArgs a) {
         }
       }
       __syncthreads();
-      if (blockIdx.x == 0 && j >= 1)
-        for (int k = threadIdx.x; k < R * j; k += kPT) {
-          const int b = k / j, i = k % j;
-          if (jl[b] == j) P.H[(int64_t)b * R1 * RS + i * RS + j - 1] = ccast<double>(colv[b * R1 + i]);
-        }
+      // every thread reads the new activity (thread 0 keeps the counters)
+      int any = 0;
+      for (int b = 0; b < R; ++b) any |= act[b];
+      const bool done = !any || closing;
       if (threadIdx.x == 0) {
-        int any = 0;
-        for (int b = 0; b < R; ++b) any |= act[b];
         s_j = j + 1;
         if (j >= 1) s_iters += 1;
-        s_done = (!any || closing) ? 1 : 0;
+        s_done = done ? 1 : 0;
       }
-      __syncthreads();
-      if (s_done) break;
+      if (done) break;
       // B5: q_j to V_j and the next pending vector (own rows and W), then the barrier that makes
       // W whole for the next gather
       p_update2<TV, RB>(V, ys, ws, a.rows, cnt, n0, N, R, R1, j, act, h1, h2, invr, gam, W);
