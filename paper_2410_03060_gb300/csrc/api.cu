@@ -702,7 +702,7 @@ static int rcs_common(swm_ctx* ctx, int n_obs, const double* obs, bool mono, dou
     stride = 2;
   }
   const size_t sb = ctx->prec == SWM_C64
-                        ? far_field_f32_scratch_bytes(ctx->nw, npairs, mono ? R : n_obs)
+                        ? far_field_f32_scratch_bytes(ctx, npairs, mono ? R : n_obs)
                         : far_field_scratch_bytes(ctx->nw, npairs);
   void* scratch = nullptr;
   SWM_TRY(dalloc(ctx, tmp, &scratch, sb));

@@ -273,7 +273,7 @@ int precond_form_E(swm_ctx* ctx);
 // rhs_ff.cu: a4 + a7
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* inc_dev);
 size_t far_field_scratch_bytes(int64_t nw, int64_t npairs);
-size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs, int n_obs);
+size_t far_field_f32_scratch_bytes(const swm_ctx* ctx, int64_t npairs, int n_obs);
 int far_field_alloc(swm_ctx* ctx);
 int prepare_far_field(swm_ctx* ctx, cudaStream_t s);
 int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_stride, bool mono, double* sigma,

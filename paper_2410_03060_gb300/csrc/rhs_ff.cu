@@ -295,6 +295,53 @@ __global__ void k_far_reduce_f32(int64_t npairs, int nchunks, const c64* __restr
 // sum_l J_l z0 q^l = z0 (J_0 + q (J_1 + q (...))).  One thread per (incidence, observation) pair
 // and chunk of wires; the CTA stages the chunk's wire data (and, with one incidence, its currents)
 // in shared memory.  Partials partial[chunk][e][3], complex64.
+// One wire's factors for one observation: the centre phase (split in cycles) and the first
+// rooftop's offset as z0 = e^{i(2 pi fr + beta s1)}, the ratio of consecutive rooftops
+// e^{i beta D}, and the amplitude D sinc^2(beta D / 2), beta = k r.t.
+struct FFTerm {
+  c64 z0, rat;
+  float amp;
+};
+__device__ __forceinline__ FFTerm ff_term(const FFWire& w, const float* rhi, const float* rlo, float k) {
+  const float two_pi = 6.28318530717958647692f;
+  float fr = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float pr = rhi[i] * w.ch[i];
+    const float er = fmaf(rhi[i], w.ch[i], -pr);
+    fr += pr - rintf(pr);
+    fr += er + rhi[i] * w.cl[i] + rlo[i] * w.ch[i];
+  }
+  fr -= rintf(fr);
+  const float beta = k * (rhi[0] * w.t[0] + rhi[1] * w.t[1] + rhi[2] * w.t[2]);
+  float sa, ca, sb, cb;
+  __sincosf(fmaf(two_pi, fr, beta * w.s1), &sa, &ca);
+  __sincosf(beta * w.D, &sb, &cb);
+  const float sc = sinc_f(0.5f * beta * w.D);
+  FFTerm t;
+  t.z0 = mkc(ca, sa);
+  t.rat = mkc(cb, sb);
+  t.amp = w.D * sc * sc;
+  return t;
+}
+// h = h * rat + J_l (one Horner step of sum_l J_l rat^l)
+__device__ __forceinline__ void horner_step(c64& h, c64 rat, c64 Jl) {
+  const c64 hv = h;
+  h.re = fmaf(hv.re, rat.re, fmaf(-hv.im, rat.im, Jl.re));
+  h.im = fmaf(hv.re, rat.im, fmaf(hv.im, rat.re, Jl.im));
+}
+// F += t_w amp z0 h
+__device__ __forceinline__ void ff_accumulate(float* F, const FFWire& w, const FFTerm& t, c64 h) {
+  const c64 acc = t.z0 * h;
+  const float Sr = t.amp * acc.re, Si = t.amp * acc.im;
+  F[0] = fmaf(w.t[0], Sr, F[0]);
+  F[1] = fmaf(w.t[0], Si, F[1]);
+  F[2] = fmaf(w.t[1], Sr, F[2]);
+  F[3] = fmaf(w.t[1], Si, F[3]);
+  F[4] = fmaf(w.t[2], Sr, F[4]);
+  F[5] = fmaf(w.t[2], Si, F[5]);
+}
+
 constexpr int kFFChunkMax = 64;   // wires per chunk of the float32 far field
 constexpr int kFFCurMax = 1024;   // staged currents per chunk
 __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __restrict__ wires,
@@ -314,7 +361,6 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
     rhi[i] = frames[o].rhi[i];
     rlo[i] = frames[o].rlo[i];
   }
-  const float two_pi = 6.28318530717958647692f;
   // the chunk's wires and their currents, staged once per CTA
   __shared__ FFWire sw[kFFChunkMax];
   __shared__ int sn[kFFChunkMax];
@@ -335,41 +381,28 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial_f32(const FFWire* __
   if (e >= npairs) return;
   const c64* J = cur + (int64_t)r * N + o0;
   float F[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int q = 0; q < nwc; ++q) {
-    const FFWire& w = sw[q];
-    float fr = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float pr = rhi[i] * w.ch[i];
-      const float er = fmaf(rhi[i], w.ch[i], -pr);
-      fr += pr - rintf(pr);
-      fr += er + rhi[i] * w.cl[i] + rlo[i] * w.ch[i];
+  // two wires per pass: their phases, sincos and Horner sums are independent chains
+  int q = 0;
+  for (; q + 1 < nwc; q += 2) {
+    FFTerm a = ff_term(sw[q], rhi, rlo, k), b = ff_term(sw[q + 1], rhi, rlo, k);
+    const int na = sn[q], nb = sn[q + 1];
+    const c64* Ja = stage_cur ? sJ + soff[q] : J + soff[q];
+    const c64* Jb = stage_cur ? sJ + soff[q + 1] : J + soff[q + 1];
+    c64 ha = Ja[na - 2], hb = Jb[nb - 2];
+    for (int l = max(na, nb) - 3; l >= 0; --l) {
+      if (l <= na - 3) horner_step(ha, a.rat, Ja[l]);
+      if (l <= nb - 3) horner_step(hb, b.rat, Jb[l]);
     }
-    fr -= rintf(fr);
-    const int n = sn[q];
-    const float beta = k * (rhi[0] * w.t[0] + rhi[1] * w.t[1] + rhi[2] * w.t[2]);
-    float sa, ca, sb, cb;
-    __sincosf(fmaf(two_pi, fr, beta * w.s1), &sa, &ca);
-    __sincosf(beta * w.D, &sb, &cb);
-    const float sc = sinc_f(0.5f * beta * w.D);
-    const c64* Jp = stage_cur ? sJ + soff[q] : J + soff[q];
-    const c64 rat = mkc(cb, sb);
-    c64 h = Jp[n - 2];
-    for (int l = n - 3; l >= 0; --l) {
-      const c64 Jl = Jp[l];
-      const c64 hv = h;
-      h.re = fmaf(hv.re, rat.re, fmaf(-hv.im, rat.im, Jl.re));
-      h.im = fmaf(hv.re, rat.im, fmaf(hv.im, rat.re, Jl.im));
-    }
-    const c64 acc = mkc(ca, sa) * h;
-    const float amp = w.D * sc * sc;
-    const float Sr = amp * acc.re, Si = amp * acc.im;
-    F[0] = fmaf(w.t[0], Sr, F[0]);
-    F[1] = fmaf(w.t[0], Si, F[1]);
-    F[2] = fmaf(w.t[1], Sr, F[2]);
-    F[3] = fmaf(w.t[1], Si, F[3]);
-    F[4] = fmaf(w.t[2], Sr, F[4]);
-    F[5] = fmaf(w.t[2], Si, F[5]);
+    ff_accumulate(F, sw[q], a, ha);
+    ff_accumulate(F, sw[q + 1], b, hb);
+  }
+  if (q < nwc) {
+    const FFTerm a = ff_term(sw[q], rhi, rlo, k);
+    const int na = sn[q];
+    const c64* Ja = stage_cur ? sJ + soff[q] : J + soff[q];
+    c64 ha = Ja[na - 2];
+    for (int l = na - 3; l >= 0; --l) horner_step(ha, a.rat, Ja[l]);
+    ff_accumulate(F, sw[q], a, ha);
   }
   c64* out = partial + ((int64_t)blockIdx.y * npairs + e) * 3;
   out[0] = mkc(F[0], F[1]);
@@ -389,14 +422,22 @@ static void ff_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& chun
   nchunks = ceil_div(nw, chunk);
 }
 
-// Launch shape of the float32 far field: that of the float64 one, with at most kFFChunkMax wires
-// per chunk (the size of the CTA's staging arrays).
-static void ff32_shape(int64_t nw, int64_t npairs, int64_t& nchunks, int64_t& chunk) {
-  ff_shape(nw, npairs, nchunks, chunk);
-  if (chunk > kFFChunkMax) {
-    chunk = kFFChunkMax;
-    nchunks = ceil_div(nw, chunk);
-  }
+// Launch shape of the float32 far field: one wave of CTAs (`slots` = resident CTAs per SM x SMs,
+// whose warps hide each other's sincos and Horner latencies), chunks of at least 8 wires and at
+// most kFFChunkMax (the size of the CTA's staging arrays).
+static void ff32_shape(int64_t nw, int64_t npairs, int64_t slots, int64_t& nchunks, int64_t& chunk) {
+  const int64_t gx = ceil_div(npairs, kFFThreads);
+  nchunks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nw, 8), ceil_div(std::max<int64_t>(slots, 1), gx)));
+  nchunks = std::min<int64_t>(nchunks, 65535);
+  chunk = std::min<int64_t>(ceil_div(nw, nchunks), kFFChunkMax);
+  nchunks = ceil_div(nw, chunk);
+}
+
+// Resident CTAs of the float32 far-field kernel on the whole GPU.
+static int64_t ff32_slots(const swm_ctx* ctx) {
+  int occ = 0;
+  if (occupancy_cached((const void*)k_far_partial_f32, kFFThreads, 0, &occ) != cudaSuccess || occ < 1) occ = 8;
+  return (int64_t)occ * std::max(ctx->nsm, 1);
 }
 
 
@@ -422,7 +463,7 @@ int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_str
   const int R = ctx->n_rhs;
   const int64_t npairs = mono ? R : (int64_t)R * n_obs;
   int64_t nchunks, chunk;
-  ff32_shape(ctx->nw, npairs, nchunks, chunk);
+  ff32_shape(ctx->nw, npairs, ff32_slots(ctx), nchunks, chunk);
   const size_t part_bytes = (size_t)nchunks * npairs * 3 * sizeof(c64);
   if (part_bytes + sizeof(FFObs) * (size_t)n_obs > scratch_bytes)
     return ctx->fail(SWM_EINVAL, "far field: scratch too small");
@@ -468,9 +509,9 @@ int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out
   return SWM_OK;
 }
 
-size_t far_field_f32_scratch_bytes(int64_t nw, int64_t npairs, int n_obs) {
+size_t far_field_f32_scratch_bytes(const swm_ctx* ctx, int64_t npairs, int n_obs) {
   int64_t nchunks, chunk;
-  ff32_shape(nw, npairs, nchunks, chunk);
+  ff32_shape(ctx->nw, npairs, ff32_slots(ctx), nchunks, chunk);
   return (size_t)nchunks * npairs * 3 * sizeof(c64) + sizeof(FFObs) * (size_t)n_obs;
 }
 
