@@ -370,7 +370,7 @@ def run_ours(args):
         roof["peak_source"] = "of measured (MEASURED_PEAKS.json)" if roof["unit"] == "GB/s" else roof.get("note")
     if roof is not None:
         # DRAM bytes per launch from one ncu capture of this kernel at this workload
-        # (profiles/k_step_mid_traffic.md); null for a kernel without a capture of its current code
+        # (profiles/gmres_persist_mid.md); null for a kernel without a capture of its current code
         roof["traffic"] = MEASURED_TRAFFIC.get((dominant, args.precision))
         roof["kernel"] = dominant
     out = {

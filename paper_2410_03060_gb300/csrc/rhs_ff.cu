@@ -241,8 +241,8 @@ __global__ void k_ff_obs(int n, const double* __restrict__ obs, int obs_stride, 
 }
 
 // Sum of the chunk partials of each (incidence, observation) pair (one warp each, partial[c][e][3],
-// complex64: the partials are float32 sums), four float accumulators per lane and component, then
-// sigma in float64 with the frames of k_ff_obs.
+// complex64: the partials are float32 sums), four float accumulators per lane and component in a
+// fixed order, then sigma in float64 with the frames of k_ff_obs.
 __global__ void k_far_reduce_f32(int64_t npairs, int nchunks, const c64* __restrict__ partial, int n_obs, int mono,
                                  const FFObs* __restrict__ frames, double* __restrict__ sigma) {
   const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -253,27 +253,23 @@ __global__ void k_far_reduce_f32(int64_t npairs, int nchunks, const c64* __restr
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int d = 0; d < 6; ++d) A[a][d] = 0.f;
-  int c = lane;
-  for (; c + 96 < nchunks; c += 128) {
+  // a lane's next eight chunks are loaded together (one round trip to L2 per 256 chunks)
+  for (int c0 = 0; c0 < nchunks; c0 += 256) {
+    c64 v[8][3];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const c64* in = partial + ((int64_t)(c + 32 * a) * npairs + e) * 3;
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + lane + 32 * u;
+      const c64* in = partial + ((int64_t)c * npairs + e) * 3;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[u][d] = c < nchunks ? in[d] : mkc(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const c64 v = in[d];
-        A[a][2 * d] += v.re;
-        A[a][2 * d + 1] += v.im;
+        A[u & 3][2 * d] += v[u][d].re;
+        A[u & 3][2 * d + 1] += v[u][d].im;
       }
-    }
-  }
-  for (; c < nchunks; c += 32) {
-    const c64* in = partial + ((int64_t)c * npairs + e) * 3;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const c64 v = in[d];
-      A[0][2 * d] += v.re;
-      A[0][2 * d + 1] += v.im;
-    }
   }
   double F[6];
 #pragma unroll
