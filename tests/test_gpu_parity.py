@@ -154,6 +154,25 @@ def test_far_field_stateless_matches_oracle():
     assert np.max(np.abs(sig.cpu().numpy() - ref)) / np.max(ref) < 1e-10
 
 
+def test_c64_far_field_many_chunks_matches_oracle():
+    """The float32 far field where each pair's wire range is cut into more than 256 chunks (its
+    reduction then takes several batches per lane): bistatic and monostatic RCS of the solved
+    complex64 currents against the oracle's far field of the same currents."""
+    cl = cloud_uniform_cube(6000, 40.0, seed=77)
+    inc = np.array([[0.3, 0.2, 0.0], [2.0, 4.5, 1.0]])
+    obs = np.array([[0.4, 0.1], [1.0, 2.0], [1.6, 3.3], [2.2, 4.4], [3.0, 5.9]])
+    out = run_gpu(cl, K, 1.0, C64, inc, obs=obs, tol=1e-4, mono=True)
+    try:
+        X = out["currents"]
+        ref = O.rcs_bistatic(cl, K, X, obs)
+        assert np.max(np.abs(out["sigma"] - ref)) / np.max(ref) < 1e-4
+        ref_m = O.rcs_monostatic(cl, K, X, inc)
+        assert np.max(np.abs(out["sigma_mono"] - ref_m)) / np.max(ref_m) < 1e-4
+    finally:
+        from paper_2410_03060_gb300 import swm
+        swm.swm_destroy(out["ctx"])
+
+
 def _rhat(obs):
     th, ph = obs[:, 0], obs[:, 1]
     return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
