@@ -494,8 +494,8 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
   const cplx<TV> gm = ccast<TV>(P.gam[r]);
   __syncthreads();
   const int64_t N = P.N;
-  const int64_t n0 = (int64_t)blockIdx.x * P.chunk;
-  const int cnt = (int)min((int64_t)P.chunk, N - n0);
+  const int64_t n0 = (int64_t)blockIdx.x * P.uchunk;
+  const int cnt = (int)min((int64_t)P.uchunk, N - n0);
   cplx<TV>* u = U + (int64_t)r * N + n0;
   const cplx<TV>* w = Wv + (int64_t)r * N + n0;
   cplx<TV>* vj = V + ((int64_t)j * P.R + r) * N + n0;
@@ -675,10 +675,13 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   P.N = N;
   P.tol = tol;
   P.max_iter = max_iter;
-  // rows per CTA of the Gram-Schmidt kernels: about 16 CTAs per SM over all right-hand sides, at
-  // least kRows and at most kMaxChunk rows (the dots stage a chunk of u and w in shared memory)
-  P.chunk = (int)std::min<int64_t>(
-      kMaxChunk, std::max<int64_t>(kRows, ceil_div(ceil_div(N * R, 16 * std::max(ctx->nsm, 1)), kRows) * kRows));
+  // rows per CTA of the Gram-Schmidt kernels, at least kRows and at most kMaxChunk (the dots stage
+  // a chunk of u and w in shared memory): the update about 16 CTAs per SM over all right-hand
+  // sides; the dots about 4, so that the last CTA of each right-hand side adds fewer partial sums
+  const int64_t nsm = std::max(ctx->nsm, 1);
+  P.uchunk = (int)std::min<int64_t>(kMaxChunk, std::max<int64_t>(kRows, ceil_div(ceil_div(N * R, 16 * nsm), kRows) * kRows));
+  P.nuchunk = (int)ceil_div(N, P.uchunk);
+  P.chunk = (int)std::min<int64_t>(kMaxChunk, std::max<int64_t>(kRows, ceil_div(ceil_div(N * R, 4 * nsm), kRows) * kRows));
   P.nchunk = (int)ceil_div(N, P.chunk);
   const int R1 = restart + 1;
   // The workspace persists across solves of the same size, so buffer addresses (and the captured
@@ -773,7 +776,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     SWM_CK(cudaMemsetAsync(P.counter, 0, sizeof(unsigned) * (R + 1), st));
     if (!given_b) SWM_CK(cudaMemsetAsync(Y, 0, sizeof(cplx<TV>) * R * N, st));
   }
-  const dim3 g_chunk((unsigned)P.nchunk, R);
+  const dim3 g_chunk((unsigned)P.nchunk, R), g_uchunk((unsigned)P.nuchunk, R);
   const bool multi = R > 1;
   const RowInfo* ri = (const RowInfo*)ctx->rowinfo;
   // The product: k_spmv with 1, 4, 8 or 16 right-hand sides sharing each read of E, or (kMinor)
@@ -832,7 +835,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       ctx->prof_end(SWM_K_DOTS);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_UPDATE);
-      k_update<TV><<<g_chunk, kRows, 0, s>>>(P, U, Wv, V);
+      k_update<TV><<<g_uchunk, kRows, 0, s>>>(P, U, Wv, V);
       ctx->prof_end(SWM_K_UPDATE);
       SWM_LAUNCHED();
     }

@@ -40,7 +40,8 @@ struct KPtr {
   c128* coef;         // [R][restart]
   c128* part;         // [R][2 (restart + 1)][nchunk]
   double* partn;      // [R][nchunk]
-  int R, restart, nchunk, chunk;
+  int R, restart, nchunk, chunk;  // rows per CTA of the dots and cycle-start kernels
+  int nuchunk, uchunk;             // rows per CTA of the update
   int max_iter;
   int64_t N;
   double tol;
