@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kRows) k_backsolve(KPtr P, int smem_tri) {
 }
 
 // Y += V coef, in the precision of the vectors (float64 arithmetic issues far slower than float32
-// on this GPU, and the complex64 path stores y in complex64 anyway).
+// on GB300, and the complex64 path stores y in complex64 anyway).
 template <typename TV>
 __global__ void __launch_bounds__(256) k_update_y(KPtr P, const cplx<TV>* __restrict__ V, cplx<TV>* __restrict__ Y) {
   const int r = blockIdx.y;

@@ -18,8 +18,8 @@ namespace {
 // chunk of rows and keeps in shared memory, when they fit: its slice of the current Krylov
 // vector, its rows of the basis V, and its rows of E with their column map and row descriptors
 // (loaded once).  The product first gathers the vector at the CTA's column-map slice (the rows
-// of one wire share their block-row's column map) into shared memory, all loads in flight at
-// once, and then forms each row's sum from shared memory.  The basis is orthogonalised by
+// of one wire share their block-row's column map) into shared memory, each thread's loads issued
+// together, and then forms each row's sum from shared memory, four lanes per row.  The basis is orthogonalised by
 // classical Gram-Schmidt with its second pass delayed by one step (as in the per-kernel solve),
 // so one Arnoldi step is two phases separated by two grid barriers:
 //   A: w = A u_j for the pending vector u_j (own rows), partial dots s = Q^H u_j, |u_j|^2,
@@ -34,7 +34,7 @@ namespace {
 // CTAs reach identical decisions and run identical barrier sequences.  The dot
 // products, their sums over the CTAs (in a fixed pairwise order), the rotations and the
 // triangular solve run in the precision of the vectors: float64 on the complex128 path, float32 on
-// the complex64 path, whose vectors carry float32 rounding anyway (on this GPU a float64 warp
+// the complex64 path, whose vectors carry float32 rounding anyway (on GB300 a float64 warp
 // instruction issues about sixteen times slower than a float32 one, which would otherwise set
 // the step time).  The initial residual norm and the relative residual estimate are float64.
 // A barrier waits at most kBarrierNs; a CTA that gives up raises an abort flag that the other

@@ -17,7 +17,7 @@ namespace {
 
 // Gauss-Jordan inversion with partial pivoting of Z_pp in precision R, one warp per wire, the
 // lanes spread over the (row, column) entries of each elimination step: the float64 form (a
-// lane-per-column sweep would chain m float64 operations per lane, slow on this GPU's float64 pipe).
+// lane-per-column sweep would chain m float64 operations per lane, slow on GB300's float64 pipe).
 template <typename R, typename TV>
 __global__ void __launch_bounds__(128) k_invert_self_entries(int64_t nw, const int32_t* __restrict__ m,
                                                     const int64_t* __restrict__ diag_b, Layout lay,
