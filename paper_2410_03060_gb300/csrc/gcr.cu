@@ -72,22 +72,37 @@ __device__ double block_sum(double v) {
   return t;
 }
 
-// Sum of n partials with stride `stride` by one warp, in a fixed order.
+// Sum of n partials with stride `stride` by one warp, in a fixed order, eight loads per lane in
+// flight (the last batch predicated).
 __device__ c128 warp_sum_partials(const c128* __restrict__ base, int stride, int n) {
   const int lane = threadIdx.x & 31;
-  double re = 0.0, im = 0.0;
-  for (int c = lane; c < n; c += 32) {
-    const double2 v = __ldcg(reinterpret_cast<const double2*>(base + (int64_t)c * stride));
-    re += v.x;
-    im += v.y;
+  double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+  for (int c = lane; c < n; c += 8 * 32) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = c + u * 32;
+      v[u] = i < n ? __ldcg(reinterpret_cast<const double2*>(base + (int64_t)i * stride)) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      re[u & 3] += v[u].x;
+      im[u & 3] += v[u].y;
+    }
   }
-  return mkc(warp_sum(re), warp_sum(im));
+  return mkc(warp_sum((re[0] + re[1]) + (re[2] + re[3])), warp_sum((im[0] + im[1]) + (im[2] + im[3])));
 }
 __device__ double warp_sum_partials_d(const double* __restrict__ base, int n) {
   const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int c = lane; c < n; c += 32) s += __ldcg(base + c);
-  return warp_sum(s);
+  double a[4] = {0, 0, 0, 0};
+  for (int c = lane; c < n; c += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = c + u * 32 < n ? __ldcg(base + c + u * 32) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u & 3] += v[u];
+  }
+  return warp_sum((a[0] + a[1]) + (a[2] + a[3]));
 }
 
 // Partial dots conj(Q_i) . w over the CTA's rows for i < j (one warp per i), to part.
