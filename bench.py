@@ -101,9 +101,15 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         lines = [line for line in open(self.path) if line.strip()]
-        mark0 = getattr(self, "mark0", 0)
+        os.unlink(self.path)
+        return self.summarise(lines, getattr(self, "mark0", 0))
+
+    @staticmethod
+    def summarise(lines, mark0):
+        """Median SM clock, max clock and active slowdown reasons of the samples after the mark
+        (the last one before it when the region was shorter than the sampling period)."""
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         during = lines[mark0:]
         if not during:
             during = lines[max(0, mark0 - 1):mark0]
@@ -120,7 +126,6 @@ class ClockSampler:
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
-        os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(lines) - mark0, "reasons": sorted(reasons)}
 
