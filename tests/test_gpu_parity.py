@@ -14,7 +14,8 @@ import pytest
 
 import oracle as O
 from gpu_helpers import K, assert_rcs_db, block_errors, run_gpu
-from synth import CONFIGS, Cloud, cloud_small, cloud_uniform_cube, observations_phi_cut
+from synth import (CONFIGS, Cloud, cloud_mid, cloud_small, cloud_uniform_cube, incidences_single_minus_z,
+                   observations_phi_cut)
 
 pytestmark = pytest.mark.gpu
 
@@ -171,6 +172,58 @@ def test_c64_far_field_many_chunks_matches_oracle():
     finally:
         from paper_2410_03060_gb300 import swm
         swm.swm_destroy(out["ctx"])
+
+
+def test_mid_workload_at_full_size_sampled_parity():
+    """The benchmark's workload at full size (10,000 wires, 51,397 unknowns) in its configuration:
+    device inputs through swm_run, complex64, r_c 3, GMRES(50) to 1e-6, 720 observations.  Checked
+    against the oracle: the pattern bit for bit, the right-hand side, 40 sampled blocks, the
+    residual b - Z x of the GPU currents on 60 sampled block-rows of the oracle's Z, and the RCS
+    against the oracle's far field of the same currents."""
+    import torch
+    from paper_2410_03060_gb300 import swm
+
+    cl = cloud_mid(seed=1)
+    r_c = 3.0
+    inc, obs = incidences_single_minus_z(), observations_phi_cut(720)
+    m, off = O.numbering(cl.nseg)
+    N = int(off[-1])
+    pairs_ref = O.neighbour_pairs(cl.centres, r_c)
+    b_ref = O.rhs(cl, K, inc)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+           (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
+    sig = torch.zeros((1, len(obs), 2), dtype=torch.float64, device="cuda")
+    ctx = swm.swm_create(0)
+    try:
+        assert swm.swm_run(ctx, *dev, K, r_c, C64, inc, obs, sig, 1e-6, 50, 1000) == 0
+        torch.cuda.synchronize()
+        sigma = sig.cpu().numpy()
+        assert np.array_equal(swm.swm_get_pattern(ctx), pairs_ref)
+        b_gpu = swm.swm_get_rhs(ctx).T
+        assert np.max(np.abs(b_gpu - b_ref)) / np.max(np.abs(b_ref)) < 2e-6
+        rng = np.random.default_rng(8)
+        sample = pairs_ref[rng.choice(len(pairs_ref), 40, replace=False)]
+        err, where = block_errors(ctx, cl, K, sample, scaled=True)
+        assert err < BLOCK_TOL_SCALED[C64], (err, where)
+        # the currents of the same built system (the solve is deterministic)
+        cur = np.zeros((1, N), dtype=np.complex128)
+        assert swm.swm_solve(ctx, inc, 1e-6, 50, 1000, cur) == 0
+        X = cur.T
+    finally:
+        swm.swm_destroy(ctx)
+    wires = rng.choice(cl.nw, 60, replace=False)
+    r2 = b2 = 0.0
+    for p in wires:
+        rows = slice(int(off[p]), int(off[p + 1]))
+        acc = b_ref[rows, 0].copy()
+        for q in pairs_ref[pairs_ref[:, 0] == p, 1]:
+            acc -= O.block(cl, K, int(p), int(q)) @ X[int(off[q]):int(off[q + 1]), 0]
+        r2 += float(np.sum(np.abs(acc) ** 2))
+        b2 += float(np.sum(np.abs(b_ref[rows, 0]) ** 2))
+    assert math.sqrt(r2 / b2) < 1e-3, math.sqrt(r2 / b2)
+    s_ref = O.rcs_bistatic(cl, K, X, obs)
+    assert np.max(np.abs(sigma - s_ref)) / np.max(s_ref) < 1e-4
+    assert_rcs_db(sigma[0, :, 0], s_ref[0, :, 0], db=0.1)
 
 
 def _rhat(obs):
