@@ -42,11 +42,12 @@ FOUR_PI = 4.0 * math.pi
 ETA0 = 376.730313668  # free-space impedance (ohm) = mu0 * c
 NQ_FAR = 4
 NQ_NEAR = 8
+PAIRS_BRUTE_MAX = 20000  # clouds up to this size test every pair; larger ones take k-d tree candidates
 SELF_NQ = 8
 RISE, FALL = 0, 1
 
 __all__ = [
-    "FOUR_PI", "ETA0", "NQ_FAR", "NQ_NEAR", "SELF_NQ", "RISE", "FALL",
+    "FOUR_PI", "ETA0", "NQ_FAR", "NQ_NEAR", "PAIRS_BRUTE_MAX", "SELF_NQ", "RISE", "FALL",
     "gauss_legendre_01", "numbering", "vertex_positions", "green",
     "segment_distance", "mutual_order", "mutual_segment_integrals",
     "convolution_poly", "static_antiderivative", "self_offset_integrals", "self_segment_integrals",
@@ -293,7 +294,7 @@ def neighbour_pairs(centres: np.ndarray, r_c: float) -> np.ndarray:
     nw = c.shape[0]
     rc2 = r_c * r_c
     out = []
-    if nw <= 20000:
+    if nw <= PAIRS_BRUTE_MAX:
         cand_rows = None
     else:
         from scipy.spatial import cKDTree  # library range search proposes candidates only

@@ -363,6 +363,67 @@ def test_neighbour_pairs_brute_force_with_exact_ties():
     assert len(ties) > 0  # the inclusive test is exercised
 
 
+def test_neighbour_pairs_kdtree_branch_on_a_lattice_with_exact_ties():
+    """Clouds above PAIRS_BRUTE_MAX wires take the k-d tree branch of the pair search (Eq. neardef):
+    checked against an independent enumeration on an integer lattice.  The centres are distinct
+    lattice sites scaled by 1/4 (exact in binary), so every squared distance is exact and the pairs
+    at exactly r_c (offsets of squared length 9 lattice units, e.g. (3,0,0) and (2,2,1)) must be
+    kept; the reference looks each site's lattice offsets of squared length <= 9 up in a table."""
+    rng = np.random.default_rng(23)
+    side = 36
+    nw = O.PAIRS_BRUTE_MAX + 1500
+    sites = rng.choice(side ** 3, size=nw, replace=False)
+    ijk = np.stack([sites // (side * side), (sites // side) % side, sites % side], axis=1)
+    c = ijk.astype(np.float64) * 0.25
+    r_c = 0.75  # 3 lattice units
+    got = O.neighbour_pairs(c, r_c)
+    assert nw > O.PAIRS_BRUTE_MAX
+    where = {tuple(v): i for i, v in enumerate(ijk.tolist())}
+    offs = [(a, b, d) for a in range(-3, 4) for b in range(-3, 4) for d in range(-3, 4) if a * a + b * b + d * d <= 9]
+    ref = []
+    for p, (i, j, k) in enumerate(ijk.tolist()):
+        for a, b, d in offs:
+            q = where.get((i + a, j + b, k + d))
+            if q is not None:
+                ref.append((p, q))
+    ref = np.array(sorted(ref), dtype=np.int64)
+    assert got.shape == ref.shape and np.array_equal(got, ref)
+    d2 = np.sum((ijk[got[:, 0]] - ijk[got[:, 1]]) ** 2, axis=1)
+    assert np.count_nonzero(d2 == 9) > 1000  # the inclusive test is exercised many times
+
+
+def test_block_jacobi_inverts_each_wires_self_block():
+    """block_jacobi (the block-diagonal preconditioner named after Eq. neardef) holds, for every
+    wire p of a cloud with mixed segment counts, the inverse of the diagonal block of the assembled
+    Z at that wire's unknowns: Z[off_p:off_p+1, off_p:off_p+1] M_p = I.  With r_c below every
+    pair distance, Z is block-diagonal, so the right-preconditioned operator Z M^-1 is the identity
+    and GMRES converges to the LU solution in a single iteration."""
+    rng = np.random.default_rng(24)
+    nw = 9
+    centres = rng.uniform(-2.0, 2.0, size=(nw, 3))
+    dirs = rng.standard_normal((nw, 3))
+    lengths = rng.uniform(0.3, 0.6, size=nw)
+    nseg = np.array([2, 3, 4, 5, 6, 7, 8, 11, 16], dtype=np.int32)
+    cl = _cloud(centres, dirs, lengths, nseg)
+    m, off = O.numbering(cl.nseg)
+    Z = O.assemble(cl, K, None, sparse=False)
+    Mi = O.block_jacobi(cl, K)
+    assert len(Mi) == nw
+    for p in range(nw):
+        a, b = off[p], off[p + 1]
+        assert Mi[p].shape == (m[p], m[p])
+        I = np.eye(m[p])
+        assert np.max(np.abs(Z[a:b, a:b] @ Mi[p] - I)) < 1e-10
+        assert np.max(np.abs(Mi[p] @ Z[a:b, a:b] - I)) < 1e-10
+    dmin = min(np.linalg.norm(centres[p] - centres[q]) for p in range(nw) for q in range(p))
+    Zb = O.assemble(cl, K, 0.5 * dmin, sparse=True)
+    b = O.rhs(cl, K, np.array([[0.4, 0.7, 0.2]]))[:, 0]
+    x, it, rel = O.gmres(Zb, b, Mi, off, tol=1e-12, restart=10)
+    assert it == 1 and rel <= 1e-12
+    x_lu = O.solve_lu(Zb.toarray(), b)
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-12
+
+
 def test_sparse_equals_dense_when_rc_covers_cloud():
     cl = _tiny_cloud(seed=14, nw=10)
     Zd = O.assemble(cl, K, None, sparse=False)
