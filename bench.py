@@ -2,15 +2,19 @@
 """Throughput of the sparsified thin-wire MoM hot path on GB300: unknowns x incidences solved per
 second, RCS checked against the plain FP64 path.
 
-One step = the whole hot path on one cloud: load the wire cloud, S-NFC neighbour search, block
-fill, block-Jacobi preconditioner, right-hand side, GMRES(50) to 1e-6, and the 720-angle bistatic
-RCS.  Workload: 10,000 wires (lengths U[0.3, 0.6] wavelengths, <= 0.08-wavelength segments,
-radius 1e-3, Gaussian centres sigma = 30 wavelengths, random directions), r_c = 3 wavelengths, one
-plane wave arriving from +z, theta-polarised.  Inputs are seeded and synthetic.
+One step = the whole hot path on one cloud through one C-ABI call (swm_run): load the wire cloud,
+S-NFC neighbour search, block fill, block-Jacobi preconditioner, right-hand sides, GMRES(50) to
+1e-6 for every incidence, RCS.  Headline workload (the largest single-GPU configuration):
+1,000,000 wires in 8 Gaussian clusters (sigma 40 wavelengths) in a 600-wavelength cube, lengths
+U[0.3, 0.6] wavelengths, <= 0.08-wavelength segments, radius 1e-3, random directions, r_c = 3
+wavelengths, 37 monostatic incidences (theta 0..180 degrees in 5-degree steps), monostatic RCS.
+The 10,000-wire single-incidence workload (720-angle bistatic RCS) is measured beside it.  Inputs
+are seeded and synthetic.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own cloud (seed 1 + rank): weak scaling, no data-path
-collective; the timing is the max over ranks.  ``--impl reference`` times the FP64 CPU oracle.
+collective; the timing is the max over ranks.  ``--impl reference`` times the FP64 CPU oracle on
+the host cores (a bounded sample of the same workload).
 """
 from __future__ import annotations
 
@@ -136,42 +140,130 @@ def rcs_db_error(s, ref, floor_db=30.0):
     return float(np.max(np.abs(10 * np.log10(s[keep] / ref[keep]))))
 
 
-def slab_sample(cloud, n_target):
-    """The wires of the centre slab |x| < w holding about n_target wires (local density kept)."""
-    x = np.abs(cloud.centres[:, 0])
-    w = np.sort(x)[min(len(x) - 1, n_target)]
-    return cloud.subset(np.nonzero(x < w)[0])
+# ---------------------------------------------------------------------------------- workloads
+# The headline workload is the largest single-GPU configuration: 1,000,000 wires in 8 Gaussian
+# clusters, 37 monostatic incidences, GMRES(50) to 1e-6, monostatic RCS.  The 10,000-wire
+# single-incidence workload with its 720-angle bistatic RCS is measured beside it.
+WORKLOADS = {
+    "learned": dict(cloud=lambda seed: cloud_learned(seed=3 + seed), r_c=3.0, n_inc=37, n_obs=0,
+                    text="learned: 1,000,000 wires in 8 Gaussian clusters (sigma 40) in a 600-wavelength cube, "
+                         "lengths U[0.3, 0.6], r_c 3, 37 monostatic incidences (theta 0..180 deg, 5 deg), "
+                         "GMRES(50) 1e-6, monostatic RCS"),
+    "mid": dict(cloud=lambda seed: cloud_mid(seed=seed), r_c=3.0, n_inc=1, n_obs=N_OBS,
+                text="mid: 10,000 wires, Gaussian sigma 30, r_c 3, GMRES(50) 1e-6, 1 incidence, "
+                     "720-angle bistatic RCS"),
+}
 
 
-def oracle_step(cloud, inc, obs):
-    """The whole path on the FP64 CPU oracle (test infrastructure, timed as the CPU baseline)."""
+def workload_inputs(name, rank=0):
+    w = WORKLOADS[name]
+    cl = w["cloud"](rank_seed(rank))
+    inc = incidences_single_minus_z() if w["n_inc"] == 1 else incidences_monostatic(w["n_inc"])
+    obs = observations_phi_cut(w["n_obs"]) if w["n_obs"] else None
+    return cl, inc, obs
+
+
+def ball_sample(cloud, n_target, seed=0):
+    """The n_target wires nearest to a randomly drawn wire of the cloud (local density kept; the
+    centre is drawn with the wires' own distribution, so the sample's density is typical)."""
+    rng = np.random.default_rng(seed)
+    c0 = cloud.centres[rng.integers(0, cloud.nw)]
+    d = np.linalg.norm(cloud.centres - c0, axis=1)
+    return cloud.subset(np.sort(np.argsort(d)[:min(cloud.nw, n_target)]))
+
+
+def _oracle_blocks(args):
+    """Worker: the oracle's blocks of the given (p, q) pairs and the inverses of the given wires'
+    self blocks."""
     import oracle as O
 
-    Z = O.assemble(cloud, K0, R_C, sparse=True)
-    Mi = O.block_jacobi(cloud, K0)
+    cloud, k, pairs, rows = args
+    blocks = [O.block(cloud, k, int(p), int(q)) for p, q in pairs]
+    return blocks, O.block_jacobi(cloud.subset(rows), k)
+
+
+def oracle_step(cloud, inc, obs, r_c, pool=None, n_chunks=1):
+    """The whole path on the FP64 CPU oracle (test infrastructure, timed as the CPU baseline):
+    pairs, blocks, block-Jacobi, RHS, GMRES per incidence, RCS.  The blocks and the self-block
+    inverses are computed in ``pool`` (the oracle's own functions, rows split over the workers).
+    Returns (rcs, build seconds, seconds of the per-incidence part)."""
+    import scipy.sparse as sp
+
+    import oracle as O
+
+    t0 = time.perf_counter()
+    pairs = O.neighbour_pairs(cloud.centres, r_c)
     m, off = O.numbering(cloud.nseg)
+    nw = cloud.nw
+    bounds = np.linspace(0, nw, n_chunks + 1).astype(np.int64)
+    rowpos = np.searchsorted(pairs[:, 0], bounds)
+    jobs = [(cloud, K0, pairs[rowpos[i]:rowpos[i + 1]], np.arange(bounds[i], bounds[i + 1]))
+            for i in range(n_chunks)]
+    res = list(pool.map(_oracle_blocks, jobs)) if pool is not None else [_oracle_blocks(j) for j in jobs]
+    rows, cols, vals, Mi = [], [], [], []
+    for (blocks, minv), job in zip(res, jobs):
+        Mi += minv
+        for (p, q), Zb in zip(job[2], blocks):
+            rr, cc = np.meshgrid(off[p] + np.arange(m[p]), off[q] + np.arange(m[q]), indexing="ij")
+            rows.append(rr.ravel())
+            cols.append(cc.ravel())
+            vals.append(Zb.ravel())
+    N = int(off[-1])
+    Z = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
+    t1 = time.perf_counter()
     b = O.rhs(cloud, K0, inc)
     X = np.zeros_like(b)
     for i in range(b.shape[1]):
         X[:, i], _, _ = O.gmres(Z, b[:, i], Mi, off, TOL, RESTART, 1000)
-    return O.rcs_bistatic(cloud, K0, X, obs)
+    sig = O.rcs_bistatic(cloud, K0, X, obs) if obs is not None else O.rcs_monostatic(cloud, K0, X, inc)
+    t2 = time.perf_counter()
+    return sig, t1 - t0, t2 - t1
 
 
-def cpu_baseline(n_wires=1000):
-    cl = slab_sample(cloud_mid(), n_wires)
-    inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
-    t = time.perf_counter()
-    oracle_step(cl, inc, obs)
-    dt = time.perf_counter() - t
-    return {"value": cl.n_unknowns * inc.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"centre slab of the 10,000-wire cloud: {cl.nw} wires, N={cl.n_unknowns}, full path "
-                      f"(pairs, fill, block-Jacobi, RHS, GMRES(50) 1e-6, 720-angle RCS) in {dt:.1f} s; "
-                      f"single-threaded NumPy"}
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch, mid workload, from one ncu capture of
-# the kernel's current code (profiles/gmres_persist_mid.md)
-MEASURED_TRAFFIC = {("gmres", "c64"): 6.392e6}
+def oracle_pool(cores):
+    """Process pool for the oracle (spawned workers, one BLAS thread each)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    return cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
+
+
+def cpu_oracle_sample(name, n_target, cores, steps=1, warmup=0):
+    """The oracle on a bounded sample of workload ``name``: the wires nearest a random wire of the
+    cloud, one incidence; with several incidences in the workload the per-incidence part is
+    extrapolated (build once + n_inc x one incidence's RHS, GMRES and RCS)."""
+    w = WORKLOADS[name]
+    cl_full, inc_full, obs = workload_inputs(name)
+    cl = ball_sample(cl_full, n_target)
+    inc = inc_full[:1]
+    n_inc = inc_full.shape[0]
+    with oracle_pool(cores) as pool:
+        for _ in range(warmup):
+            oracle_step(cl, inc, obs, w["r_c"], pool, cores)
+        tb, ts = [], []
+        for _ in range(max(1, steps)):
+            _, b, s = oracle_step(cl, inc, obs, w["r_c"], pool, cores)
+            tb.append(b)
+            ts.append(s)
+    t_build, t_inc = float(np.mean(tb)), float(np.mean(ts))
+    t_step = t_build + n_inc * t_inc
+    value = cl.n_unknowns * n_inc / t_step
+    sample = (f"{cl.nw} wires nearest a random wire of the {cl_full.nw:,}-wire cloud (N={cl.n_unknowns}), the "
+              f"whole path on the FP64 NumPy oracle (blocks and self-block inverses on {cores} processes, GMRES "
+              f"in one): build {t_build:.2f} s, one incidence's RHS + GMRES(50) 1e-6 + RCS {t_inc:.3f} s")
+    if n_inc > 1:
+        sample += f"; EXTRAPOLATED to {n_inc} incidences as build + {n_inc} x one incidence"
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "extrapolated": n_inc > 1, "seconds_per_step": t_step}
 
 
 # ---------------------------------------------------------------------------------- ranks
@@ -195,105 +287,127 @@ def aggregate_over_ranks(times_ms, units, device, world):
 
 
 # ---------------------------------------------------------------------------------- our arm
-def kernel_roofline(cls, st, prof_ms, launches, prec, n_rhs, pk, clocks):
-    """Achieved algorithmic rate of one kernel class over the timed region."""
+def solve_steps(iterations, restart):
+    """Arnoldi step indices j of one solve and the lengths of its restart cycles."""
+    steps_j, cycles = [], []
+    it = iterations
+    while it > 0:
+        c = min(restart, it)
+        steps_j += list(range(c))
+        cycles.append(c)
+        it -= c
+    return steps_j, cycles
+
+
+def class_bytes(cls, st, prec, n_rhs, restart):
+    """Algorithmic bytes of one solve for a kernel class of the per-kernel GMRES step.
+    Product: E values, column map and row descriptors once per block of incidences sharing a
+    read, u read and w written per incidence, and per restart cycle the residual product
+    (B and y read, W written); the transpose to incidence-minor order is not counted.  Delayed
+    Gram-Schmidt at step j: dots read Q_<j, u and w ((j + 2) vectors; the closing pass of a cycle
+    Q_<j and u), update reads Q_<j, u, w and writes q_j and the next u ((j + 4) vectors)."""
     esz = 16 if prec == "c128" else 8
-    N, nw = st["n"], st["nw"]
+    N, R = st["n"], n_rhs
+    vec = R * N * esz
+    steps_j, cycles = solve_steps(st["iterations"], restart)
+    if cls == "apply":
+        rbs = st["step_rhs_block"]
+        rb = (32 if R >= 24 else 16) if rbs == 32 else max(1, rbs)
+        nblk = -(-R // rb)
+        mat = (st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N) * nblk
+        return len(steps_j) * (mat + 2 * vec) + (len(cycles) + 1) * (mat + 3 * vec)
+    if cls == "dots":
+        return sum((j + 2) * vec for j in steps_j) + sum((c + 1) * vec for c in cycles)
+    if cls == "update":
+        return sum((j + 4) * vec for j in steps_j)
+    if cls == "gmres":
+        # the persistent solve: product and delayed Gram-Schmidt as above, b formed from the wire
+        # geometry, restart products, y update by the basis, x = M^-1 y
+        mat = st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N
+        b = sum(mat + vec + (2 * j + 6) * vec for j in steps_j) + sum((c + 1) * vec for c in cycles)
+        b += (st["restarts"] + 1) * (mat + 3 * vec) + sum(cycles) * vec
+        b += st["nw"] * (7 * 8 + 4) + vec + st["nminv"] * esz + 2 * vec
+        return b
+    return None
+
+
+def fp32_peak_tflops(pk):
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    return N_SM * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per_step_units=None):
+    """Achieved algorithmic rate of one kernel class over ``steps`` profiled steps."""
     if prof_ms <= 0 or launches <= 0:
         return None
     per_launch_ms = prof_ms / launches
-    if cls == "apply":
-        # per Arnoldi step: E values + column map + x, y and V rows + row metadata, plus the V rows
-        # read by the fused first Gram-Schmidt pass; per restart: the residual product (+ b)
-        mat = st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 4 * N + 28 * nw
-        vec = N * esz * n_rhs
-        per_solve = sum(mat + 3 * vec + (j + 1) * vec for j in st["_steps"]) + (st["restarts"] + 1) * (mat + 3 * vec)
-        work = per_solve * st["_cycles_mult"]
-        return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
-                "unit": "GB/s", "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms}
-    if cls == "gmres":
-        # the persistent solve, one launch per solve.  Per Arnoldi step j: E values + column map +
-        # row descriptors and the gathered vector u, then the delayed Gram-Schmidt: dots over
-        # V_0..V_{j-1}, u, w and the update reading them and writing V_j and the next u; the closing
-        # pass of a cycle reads V_0..V_{j-1} and u; per restart cycle: the residual product and the
-        # update of y by the basis; once: b formed from the wire geometry (centre, direction, length,
-        # segment count) and written, and x = M^-1 y (the inverse blocks, y read, x written).
-        mat = st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N
-        vec = N * esz * n_rhs
-        per_solve = sum(mat + vec + (2 * j + 6) * vec for j in st["_steps"])
-        per_solve += sum((c + 1) * vec for c in st["_cycle_len"])
-        per_solve += (st["restarts"] + 1) * (mat + 3 * vec) + sum(st["_cycle_len"]) * vec
-        per_solve += nw * (7 * 8 + 4) + vec + st["nminv"] * esz + 2 * vec
-        work = per_solve * st["_cycles_mult"]
-        return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
-                "unit": "GB/s", "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms,
-                "note": "latency-bound at this size (E and the basis stay on chip or in L2)"}
-    if cls in ("dots", "update", "finish"):
-        vec = N * esz * n_rhs
-        work = sum((j + 1) * vec + 2 * vec for j in st["_steps"]) * st["_cycles_mult"]
-        return {"bound": "hbm", "achieved": work / (prof_ms * 1e-3) / 1e9, "peak": pk.get("hbm_gbs", 6800.0),
-                "unit": "GB/s", "per_launch_bytes": work / max(1, len(st["_steps"])), "per_launch_ms": per_launch_ms}
     if cls == "fill_mutual":
-        flops = st["fill_evals"] * FP32_FLOPS_PER_EVAL
-        mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = N_SM * 128 * 2 * mhz * 1e6 / 1e12 if prec == "c64" else 1.25
-        return {"bound": "alu", "achieved": flops / (per_launch_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "per_launch_flops": flops, "per_launch_ms": per_launch_ms,
-                "note": ("FP32 peak = 152 SMs x 128 lanes x 2 flops x max SM clock" if prec == "c64"
-                         else "nominal FP64 peak")}
-    return {"bound": "other", "per_launch_ms": per_launch_ms}
+        flops = st["fill_evals"] * FP32_FLOPS_PER_EVAL * steps
+        peak = fp32_peak_tflops(pk) if prec != "c128" else 1.25
+        ach = flops / (prof_ms * 1e-3) / 1e12
+        return {"kernel": "k_mutual_blocks_f32" if prec != "c128" else "k_mutual_blocks<double>", "bound": "alu",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "per_launch_flops": flops / launches, "per_launch_ms": per_launch_ms,
+                "peak_source": ("FP32 peak = 152 SMs x 128 lanes x 2 flops x max SM clock" if prec != "c128"
+                                else "nominal FP64 peak"),
+                "flops_per_eval": FP32_FLOPS_PER_EVAL, "evals_per_launch": st["fill_evals"]}
+    b = class_bytes(cls, st, prec, n_rhs, restart)
+    if b is None:
+        return {"kernel": cls, "bound": "other", "per_launch_ms": per_launch_ms}
+    work = b * steps
+    ach = work / (prof_ms * 1e-3) / 1e9
+    peak = pk.get("hbm_gbs", 6800.0)
+    names = {"apply": "k_spmv_t (+ k_rhs_minor) / k_spmv: block-sparse product",
+             "dots": "k_dots: delayed Gram-Schmidt inner products",
+             "update": "k_update: delayed Gram-Schmidt update",
+             "gmres": "k_gmres_persist: persistent GMRES solve"}
+    return {"kernel": names.get(cls, cls), "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_source": "of measured (MEASURED_PEAKS.json copy bandwidth)",
+            "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms}
 
 
-def run_ours(args):
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel's
+# current code, keyed by (workload, kernel class, precision); the capture and its scaling are
+# recorded with the profile summaries.  A class without a capture of its current code reports null.
+MEASURED_TRAFFIC = {}
+
+PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "apply", "dots", "update", "far",
+                   "gmres"]
+
+
+def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps=None):
+    """Time workload ``name`` through swm_run (device inputs), then: the class shares (one
+    profiled step per class), the dominant and the named classes' rooflines (a separate profiled
+    pass), the end-to-end step from pinned host buffers, and the plain FP64 path (its RCS gates the
+    fast path).  Returns the record and the summed units."""
     import torch
     import torch.distributed as dist
 
     from paper_2410_03060_gb300 import swm
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOADS[name]
+    cl, inc, obs = workload_inputs(name, rank)
+    R, N = inc.shape[0], cl.n_unknowns
     prec_id = swm.SWM_C64 if args.precision == "c64" else swm.SWM_C128
-    cl = cloud_mid(seed=rank_seed(rank))
-    inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
-    N = cl.n_unknowns
+    restart = args.restart
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
            (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
-    sigma = torch.zeros((1, N_OBS, 2), dtype=torch.float64, device="cuda")
+    shape = (R, 2) if obs is None else (R, obs.shape[0], 2)
+    sigma = torch.zeros(shape, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     ctx = swm.swm_create(local)
+    K = steps or args.steps
 
-    def step(prec=prec_id, inputs=dev, out=sigma):
-        # set_cloud, build, solve and the bistatic RCS in one C-ABI call (swm_run)
-        swm.swm_run(ctx, *inputs, K0, R_C, prec, inc, obs, out, TOL, RESTART, 1000)
+    def step(c=None, prec=prec_id, inputs=dev, out=sigma):
+        rc = swm.swm_run(c or ctx, *inputs, K0, w["r_c"], prec, inc, obs, out, TOL, restart, 2000)
+        if rc != 0:
+            raise RuntimeError(f"swm_run returned {rc} (not converged)")
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    st0 = swm.swm_get_stats(ctx)
-    # accuracy gate against the plain FP64 path (untimed)
-    s_fast = sigma.cpu().numpy()[0, :, 0].copy()
-    sig64 = torch.zeros_like(sigma)
-    step(prec=swm.SWM_C128, out=sig64)
-    torch.cuda.synchronize()
-    err_db = rcs_db_error(s_fast, sig64.cpu().numpy()[0, :, 0])
 
-    # dominant kernel class: one profiled step per class (untimed)
-    classes = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "rhs", "apply", "update", "finish", "far",
-               "gmres"]
-    share = {}
-    for c in classes:
-        swm.swm_profile(ctx, c)
-        step()
-        torch.cuda.synchronize()
-        share[c] = swm.swm_get_stats(ctx)["prof_ms"]
-    dominant = max(share, key=share.get)
-    swm.swm_profile(ctx, dominant)
-
-    # timed region
+    # timed region: K steps, nothing profiled
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -302,7 +416,7 @@ def run_ours(args):
     clocks.start()
     clocks.mark()
     evs = []
-    for _ in range(args.steps):
+    for _ in range(K):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -313,94 +427,152 @@ def run_ours(args):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     st = swm.swm_get_stats(ctx)
-    launches = (st["kernel_launches"] - l0) // max(1, args.steps)
-    ms_step = float(np.mean(ms))
-    prof_ms, prof_n = st["prof_ms"], st["prof_launches"]
+    launches = (st["kernel_launches"] - l0) // max(1, K)
+    s_fast = sigma.cpu().numpy().copy()
+
+    # class shares: one profiled step per class (untimed)
+    share, prof = {}, {}
+    for c in PROFILE_CLASSES:
+        swm.swm_profile(ctx, c)
+        step()
+        torch.cuda.synchronize()
+        s = swm.swm_get_stats(ctx)
+        share[c] = s["prof_ms"]
+        prof[c] = (s["prof_ms"], s["prof_launches"])
     swm.swm_profile(ctx, "none")
-
-    # e2e through the public API with pinned host buffers (copies inside the timed region)
-    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in
-               (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
-    sig_host = torch.zeros((1, N_OBS, 2), dtype=torch.float64).pin_memory().numpy()
-    e2e_steps = max(1, min(args.steps, 50))
-    e2e = []
-    for _ in range(e2e_steps):
+    dominant = max(share, key=share.get)
+    # roofline pass of the dominant class: a few profiled steps of their own
+    rsteps = max(1, min(3, K))
+    swm.swm_profile(ctx, dominant)
+    for _ in range(rsteps):
         flush.zero_()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        step(inputs=host_in, out=sig_host)
-        torch.cuda.synchronize()
-        e2e.append(time.perf_counter() - t)
-    e2e_ms = 1e3 * float(np.mean(e2e))
-    h2d = int(sum(a.nbytes for a in host_in))
-    d2h = int(sig_host.nbytes)
-
-    # plain FP64 path on the same GPU
-    f64 = []
-    for _ in range(max(1, min(args.steps, 20))):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        step(prec=swm.SWM_C128, out=sig64)
-        b.record()
-        f64.append((a, b))
+        step()
     torch.cuda.synchronize()
-    ms64 = float(np.mean([a.elapsed_time(b) for a, b in f64]))
+    s = swm.swm_get_stats(ctx)
+    swm.swm_profile(ctx, "none")
+    pk = peaks()
+    roof = roofline_of(dominant, st, s["prof_ms"], s["prof_launches"], args.precision, R, restart, rsteps, pk)
+    if roof is not None:
+        roof["class"] = dominant
+        roof["profiled_steps"] = rsteps
+        roof["traffic"] = MEASURED_TRAFFIC.get((name, dominant, args.precision))
+    extra_roofs = {}
+    for c in ("fill_mutual", "apply", "dots", "update"):
+        if c != dominant and prof[c][1] > 0:
+            extra_roofs[c] = roofline_of(c, st, prof[c][0], prof[c][1], args.precision, R, restart, 1, pk)
+
+    rec = {"workload": w["text"], "nw": cl.nw, "unknowns": N, "incidences": R, "blocks": st["nb"],
+           "ms_per_step": ms_step, "value_local": N * R / (ms_step * 1e-3), "gpu_launches": int(launches),
+           "iterations": st["iterations"], "restarts": st["restarts"], "rel_residual": st["rel_residual"],
+           "step_rhs_block": st["step_rhs_block"],
+           "phase_ms": {k: st[k] for k in ("ms_neighbour", "ms_fill", "ms_precond", "ms_rhs", "ms_solve", "ms_rcs")},
+           "kernel_ms_per_step": share, "roofline": roof, "rooflines_other": extra_roofs, "clocks": clk}
+
+    if with_e2e:
+        # end to end through the public API: pinned host inputs read in place, RCS written to a
+        # pinned host buffer, inside the timed region
+        host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in
+                   (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
+        sig_host = torch.zeros(shape, dtype=torch.float64).pin_memory().numpy()
+        e2e = []
+        for _ in range(max(1, min(K, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            step(inputs=host_in, out=sig_host)
+            torch.cuda.synchronize()
+            e2e.append(time.perf_counter() - t)
+        rec["e2e_ms"] = 1e3 * float(np.mean(e2e))
+        rec["h2d"] = int(sum(a.nbytes for a in host_in))
+        rec["d2h"] = int(sig_host.nbytes)
     swm.swm_destroy(ctx)
+    del flush
+    torch.cuda.empty_cache()
+
+    if with_fp64:
+        # the plain FP64 path on the same cloud: its RCS gates the fast path; a few steps timed
+        ctx64 = swm.swm_create(local)
+        sig64 = torch.zeros_like(sigma)
+        step(c=ctx64, prec=swm.SWM_C128, out=sig64)
+        torch.cuda.synchronize()
+        f64 = []
+        for _ in range(max(1, min(K, 3))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step(c=ctx64, prec=swm.SWM_C128, out=sig64)
+            b.record()
+            f64.append((a, b))
+        torch.cuda.synchronize()
+        ms64 = float(np.mean([a.elapsed_time(b) for a, b in f64]))
+        s64 = sig64.cpu().numpy()
+        swm.swm_destroy(ctx64)
+        torch.cuda.empty_cache()
+        rec["ms64"] = ms64
+        rec["rcs_err_db_vs_fp64"] = rcs_db_error(s_fast[..., 0], s64[..., 0])
+        rec["rcs_rel_l2_vs_fp64"] = float(np.linalg.norm(s_fast[..., 0] - s64[..., 0]) / np.linalg.norm(s64[..., 0]))
+    return rec, N * R
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    name = args.workload if args.workload in WORKLOADS else "learned"
+    rec, units = measure(name, args, local, world, rank)
+    side = None
+    if name == "learned" and not args.no_mid:
+        side, _ = measure("mid", args, local, world, rank, with_e2e=False, with_fp64=True,
+                          steps=max(args.steps, 200))
 
     # max over ranks, units over all ranks
-    (ms_step, e2e_ms, ms64), total_units = aggregate_over_ranks([ms_step, e2e_ms, ms64], N * inc.shape[0],
-                                                                "cuda", world)
+    (ms_step, e2e_ms, ms64), total_units = aggregate_over_ranks([rec["ms_per_step"], rec["e2e_ms"], rec["ms64"]],
+                                                                units, "cuda", world)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    pk = peaks()
-    # reconstruct the Arnoldi step indices of one solve for the Gram-Schmidt byte counts
-    it = st["iterations"]
-    steps_j, cycle_len = [], []
-    while it > 0:
-        c = min(RESTART, it)
-        steps_j += list(range(c))
-        cycle_len.append(c)
-        it -= c
-    st["_steps"] = steps_j
-    st["_cycle_len"] = cycle_len
-    st["_cycles_mult"] = args.steps
-    roof = kernel_roofline(dominant, st, prof_ms, prof_n, args.precision, 1, pk, clk)
-    if roof and roof.get("peak"):
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["peak_source"] = "of measured (MEASURED_PEAKS.json)" if roof["unit"] == "GB/s" else roof.get("note")
-    if roof is not None:
-        # DRAM bytes per launch from one ncu capture of this kernel at this workload
-        # (profiles/gmres_persist_mid.md); null for a kernel without a capture of its current code
-        roof["traffic"] = MEASURED_TRAFFIC.get((dominant, args.precision))
-        roof["kernel"] = dominant
     out = {
         "metric": METRIC, "value": total_units / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64" if args.precision == "c64" else "c128",
         "data": "synthetic (seeded wire clouds)",
-        "config": {"workload": "mid: 10,000 wires, Gaussian sigma 30, r_c 3, GMRES(50) 1e-6, 1 incidence, "
-                               "720-angle bistatic RCS", "nw": cl.nw, "unknowns": N, "blocks": st["nb"],
-                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+        "config": {"workload": rec["workload"], "nw": rec["nw"], "unknowns": rec["unknowns"],
+                   "incidences": rec["incidences"], "blocks": rec["blocks"], "precision": args.precision,
+                   "restart": args.restart, "tol": TOL,
+                   "l2": "inputs larger than L2 (E and the Krylov basis are GBs); a 256 MB write also flushes "
+                         "L2 between steps",
                    "parallelism": f"{world} independent clouds (one per GPU)"},
-        "gpu_launches": int(launches),
-        "e2e": {"value": total_units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "rcs_err_db_vs_fp64": err_db,
+        "gpu_launches": rec["gpu_launches"],
+        "e2e": {"value": total_units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": rec["h2d"],
+                "d2h_bytes_per_step": rec["d2h"], "ms_per_step": e2e_ms,
+                "path": "swm_run from page-locked host buffers (inputs read and RCS written in place)"},
+        "rcs_err_db_vs_fp64": rec["rcs_err_db_vs_fp64"],
+        "rcs_rel_l2_vs_fp64": rec["rcs_rel_l2_vs_fp64"],
         "fp64_path": {"value": total_units / (ms64 * 1e-3), "ms_per_step": ms64,
                       "speedup_of_value": ms64 / ms_step},
-        "iterations": st["iterations"],
-        "phase_ms": {k: st[k] for k in ("ms_neighbour", "ms_fill", "ms_precond", "ms_rhs", "ms_solve", "ms_rcs")},
-        "kernel_share_ms_per_step": share,
-        "roofline": roof,
-        "clocks": clk,
+        "iterations": rec["iterations"], "restarts": rec["restarts"], "rel_residual": rec["rel_residual"],
+        "step_rhs_block": rec["step_rhs_block"],
+        "phase_ms": rec["phase_ms"],
+        "kernel_share_ms_per_step": rec["kernel_ms_per_step"],
+        "roofline": rec["roofline"],
+        "rooflines_other": rec["rooflines_other"],
+        "clocks": rec["clocks"],
     }
+    if side is not None:
+        out["mid"] = {k: side[k] for k in ("workload", "unknowns", "ms_per_step", "value_local", "iterations",
+                                           "gpu_launches", "rcs_err_db_vs_fp64", "ms64", "roofline", "clocks")}
+        out["mid"]["fp64_speedup"] = side["ms64"] / side["ms_per_step"]
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
+        cores = host_cores()
+        out["cpu_baseline"] = cpu_oracle_sample(name, min(30000, 600 * cores), cores)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -731,29 +903,26 @@ def run_batch(args):
 
 # ---------------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (the paper has no code) on the host cores, on a bounded
+    sample of the same workload, same metric and unit."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # sample size keeps the whole run within a few minutes (about 8 ms of oracle time per wire)
-    n_wires = int(min(1000, max(100, 150.0 / ((args.steps + args.warmup) * 0.008))))
-    cl = slab_sample(cloud_mid(), n_wires)
-    inc, obs = incidences_single_minus_z(), observations_phi_cut(N_OBS)
-    for _ in range(args.warmup):
-        oracle_step(cl, inc, obs)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(cl, inc, obs)
-    dt = (time.perf_counter() - t0) / max(1, args.steps)
-    v = cl.n_unknowns * inc.shape[0] / dt
-    sample = (f"centre slab of the 10,000-wire cloud: {cl.nw} wires, N={cl.n_unknowns}; full path on the FP64 "
-              f"NumPy oracle, single-threaded")
+    name = args.workload if args.workload in WORKLOADS else "learned"
+    cores = host_cores()
+    # sample size keeps the whole run within a few minutes: about 20 ms of oracle time per wire and
+    # core-second, (steps + warmup) oracle steps
+    per_step_s = 150.0 / (args.steps + args.warmup)
+    n_wires = int(min(30000, max(200, per_step_s * cores / 0.02)))
+    cb = cpu_oracle_sample(name, n_wires, cores, steps=args.steps, warmup=args.warmup)
+    v = cb["value"]
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded wire clouds)",
-        "config": {"workload": "mid (sampled): 10,000-wire cloud statistics, r_c 3, GMRES(50) 1e-6, 1 incidence, "
-                               "720-angle bistatic RCS", "nw": cl.nw, "unknowns": cl.n_unknowns},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": cb["seconds_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded wire clouds)",
+        "config": {"workload": WORKLOADS[name]["text"] + " (bounded sample, see cpu_baseline.sample)"},
+        "cpu_baseline": cb,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -761,12 +930,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["mid"] + sorted(SCALE), default="mid")
+    ap.add_argument("--workload", choices=sorted(set(WORKLOADS) | set(SCALE)), default="learned",
+                    help="learned (the headline) or mid; precision and batching0 print scale records")
+    ap.add_argument("--no-mid", action="store_true", help="skip the 10,000-wire side measurement")
     ap.add_argument("--inc", type=int, default=0, help="incidences of a larger workload (default: its own)")
     ap.add_argument("--restart", type=int, default=RESTART)
     ap.add_argument("--nw", type=int, default=0, help="wire count of a larger workload (default: its own)")
@@ -780,9 +951,11 @@ def main():
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--compare-precisions", action="store_true",
                     help="larger workload: time the float64, complex64 and bfloat16-refinement paths")
+    ap.add_argument("--scale", action="store_true",
+                    help="print a scale record (kernel classes, rooflines) of a larger workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.workload != "mid" and args.impl == "ours":
+    if (args.scale or args.compare_precisions or args.workload not in WORKLOADS) and args.impl == "ours":
         if args.compare_precisions:
             run_compare(args)
         else:

@@ -115,10 +115,11 @@ typedef struct swm_stats {
   int64_t prof_launches;   /* launches of the profiled kernel class */
   int pattern_reused;      /* 1 if the last build kept the previous S-NFC pattern (same cloud and
                               r_c, e.g. a frequency sweep) and only refilled the values */
-  int step_rhs_block;      /* incidences sharing each read of the blocks in the last solve's
-                              per-kernel GMRES product (1, 4, 8 or 16, or 32 for the
-                              incidence-minor form, as timed on the system the first time a shape
-                              was solved on this context) */
+  int step_rhs_block;      /* form of the last solve's per-kernel GMRES product: incidences
+                              sharing each read of the blocks (1, 4, 8 or 16), 32 for the
+                              incidence-minor form, 64 for the wire-tiled form (a CTA per group
+                              of wires, every incidence sharing its reads of E); as timed on the
+                              system the first time a shape was solved on this context */
   int64_t nminv;           /* stored entries of the self-block inverses (sum over wires of m_p^2) */
 } swm_stats;
 
@@ -148,6 +149,9 @@ typedef struct swm_stats {
  * run the persistent solve; SWM_PERSIST (default 1) -- 0 solves small systems with one launch per
  * kernel of each GMRES step instead of the persistent cooperative kernel;
  * SWM_PERSIST_CTAS (default 0 = one per SM) -- CTAs of the persistent solve, at most one per SM;
+ * SWM_PRODUCT_FORM (default 0 = timed choice) -- with several incidences, the per-kernel GMRES
+ * product form to use instead of timing them: 4, 8 or 16 incidences per read of E, 32 the
+ * incidence-minor form (12 or more incidences), 64 the wire-tiled form;
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the
  * persistent solve wait for n arrivals that never come, so each wait runs out (after 1 s) and the
  * solve returns SWM_ETIMEOUT; all read when the context is created. */
@@ -181,7 +185,8 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
 
 /* Build the S-NFC system (Sec. II-B): neighbour search with coupling radius r_c (r_c <= 0 or
  * infinite = entire coupling, every block kept), fill of every kept block at wavenumber k > 0
- * (Eqs. (5)-(8)), and the block-Jacobi preconditioner.  precision is SWM_C128 or SWM_C64.
+ * (Eqs. (5)-(8)), and the block-Jacobi preconditioner.  precision is SWM_C128, SWM_C64 or SWM_BF16
+ * (see their definitions above; SWM_BF16 also stores Z M^-1 rounded to complex bfloat16).
  * The pattern depends on the cloud and r_c only: a build with the same r_c as the previous one
  * on the same cloud (a frequency sweep: only k changes) keeps the pattern, its index arrays and
  * the wire order, and refills the values (swm_stats.pattern_reused = 1).
@@ -253,7 +258,8 @@ int swm_net_train_step(swm_net* net, swm_ctx* ctx, int n_inc, const double* inc,
 int swm_rcs_bistatic(swm_ctx* ctx, int n_obs, const double* obs, double* sigma_out, int out_kind);
 
 /* The whole path in one call: swm_set_cloud, swm_build, swm_solve (no currents_out) and
- * swm_rcs_bistatic with the same arguments, meanings and results as those calls made in turn (the
+ * swm_rcs_bistatic -- or, with n_obs = 0 and obs = NULL, swm_rcs_monostatic (sigma_out then
+ * n_inc x 2) -- with the same arguments, meanings and results as those calls made in turn (the
  * paper has no counterpart; this is an entry point of this library).  It synchronises the host only
  * where it needs device results (the cloud's bounding box, the pattern sizes, the RCS): the build's
  * checks and the solver's final state are read after the last synchronisation, so a singular self
@@ -292,6 +298,7 @@ int swm_get_rhs(swm_ctx* ctx, double* re_im_out);
  *   unknown offsets off_p (off_0 = 0, off_{p+1} = off_p + nseg_p - 1);
  *   currents n_rhs x N complex128 (interleaved); obs n_obs x 2 (theta, phi);
  *   sigma_out n_rhs x n_obs x 2 float64 (theta- and phi-received).
+ * SWM_EINVAL if any pointer is not device (or managed) memory.
  * Runs on `cuda_stream` and returns when sigma_out is complete.  Allocates device scratch of
  * about 48 * n_rhs * n_obs * ceil(nw / 256) bytes with cudaMallocAsync and frees it before
  * returning.  Error text (if any) is returned by swm_stateless_error(). */
@@ -315,9 +322,12 @@ int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const do
  * Limits and rules:
  *   - n_rhs * n_obs <= 174762 (48 bytes of scratch per incidence-observation pair); larger
  *     requests return SWM_EINVAL with the sizes in swm_stateless_error().
- *   - The stream's device must be the current device.  The first call on each device looks up
- *     the array's device address (cudaGetSymbolAddress) with that device current; make that
- *     first call before any stream capture.
+ *   - The stream's device must be the current device, in its primary context (the runtime's
+ *     default): the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and keeps it for later calls.
+ *   - Every call reads the unknown count off[nw] back to the host and synchronises its stream
+ *     before returning, so a call cannot be captured into a CUDA graph.
+ *   - Every array must be device memory (SWM_EINVAL otherwise), as for swm_far_field.
  *   - All calls share the one array, and it keeps the last call's contents.  Each call writes
  *     every partial sum it later reads, so nothing has to start at zero; but calls that can
  *     overlap on the GPU (other streams, other host threads) race on the array and must be

@@ -305,6 +305,20 @@ void frames_host(const double* inc, int n, std::vector<double>& out) {
 
 void set_stateless_error(const std::string& msg) { g_stateless_err = msg; }
 
+// True if every pointer is device (or managed) memory that the current device can address; the
+// stateless far-field entry points take device pointers only.
+bool all_device_memory(const void* const* ptrs, int n) {
+  for (int i = 0; i < n; ++i) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptrs[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+  }
+  return true;
+}
+
 }  // namespace swm
 
 using namespace swm;
@@ -329,6 +343,7 @@ int swm_create(swm_ctx** out, int device, void* cuda_stream) {
   if (const char* e = std::getenv("SWM_PERSIST")) ctx->persist = std::atoi(e) != 0;
   if (const char* e = std::getenv("SWM_PERSIST_CTAS")) ctx->persist_ctas = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("SWM_TEST_BARRIER_EXTRA")) ctx->test_barrier_extra = std::max(0, std::atoi(e));
+  if (const char* e = std::getenv("SWM_PRODUCT_FORM")) ctx->product_form = std::max(0, std::atoi(e));
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
@@ -758,7 +773,9 @@ int swm_run(swm_ctx* ctx, int64_t nw, const double* centres, const double* dirs,
   int solve_rc = SWM_OK;
   if (rc >= 0) {
     solve_rc = swm_solve(ctx, n_inc, inc, tol, restart, max_iter, nullptr, SWM_HOST);
-    if (solve_rc >= 0) rc = swm_rcs_bistatic(ctx, n_obs, obs, sigma_out, out_kind);
+    if (solve_rc >= 0)
+      rc = (n_obs == 0 && obs == nullptr) ? swm_rcs_monostatic(ctx, sigma_out, out_kind)
+                                          : swm_rcs_bistatic(ctx, n_obs, obs, sigma_out, out_kind);
     else rc = solve_rc;
   }
   ctx->fused = false;
@@ -913,6 +930,13 @@ int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const do
       !currents || !obs || !sigma_out || !(k > 0.0)) {
     g_stateless_err = "swm_far_field: bad argument";
     return SWM_EINVAL;
+  }
+  {
+    const void* ptrs[8] = {centres, dirs, lengths, nseg, off, currents, obs, sigma_out};
+    if (!all_device_memory(ptrs, 8)) {
+      g_stateless_err = "swm_far_field: every array must be device memory";
+      return SWM_EINVAL;
+    }
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int64_t N = 0;

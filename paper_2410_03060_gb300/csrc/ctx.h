@@ -160,6 +160,8 @@ struct swm_ctx {
   // test hook (SWM_TEST_BARRIER_EXTRA): grid barriers of the persistent solve wait for this many
   // arrivals more than there are CTAs, so every wait runs out and the solve reports SWM_ETIMEOUT
   int test_barrier_extra = 0;
+  int product_form = 0;                   // many right-hand sides: 0 = timed choice, else that form
+                                          // (4, 8, 16, 32 incidence-minor, 64 wire-tiled)
   int persist_ctas = 0;                   // CTAs of the persistent solve (0: one per SM)
   int nsm = 0;
   int coop = 0;
@@ -286,6 +288,8 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
                      std::string* err);
 // incidence frames on the host: k_hat (propagation, = -arrival) then polarisation e, 6 doubles each
 void frames_host(const double* inc, int n, std::vector<double>& out);
+// true if every pointer is device or managed memory (api.cu)
+bool all_device_memory(const void* const* ptrs, int n);
 // error text reported by swm_stateless_error() (api.cu)
 void set_stateless_error(const std::string& msg);
 // krylov.cu: a6
@@ -329,6 +333,9 @@ int apply_minv(swm_ctx* ctx, const void* Y);
 int gcr_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
 // krylov.cu: GMRES on the bfloat16 copy of E (inner solve of the refinement); y-space result
 int gmres_inner_bf16(swm_ctx* ctx, double tol, int restart, int max_iter, void** y_out, int* iters);
+// Rr = B - (Y + E Y) for every right-hand side in float64 vectors with the complex64 E, one read of
+// E shared by all right-hand sides (wire-tiled product, krylov.cu)
+int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr);
 // rhs_ff.cu: right-hand sides in float64 into `out` ([n_inc][N], internal order)
 int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out);
 // refine.cu: float64 iterative refinement around bfloat16-storage GMRES (precision SWM_BF16)

@@ -237,6 +237,114 @@ __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restric
   }
 }
 
+// Product with many right-hand sides, wire-tiled: w = u + E u read and written right-hand-side
+// major, with no transposed copy of u.  A CTA takes WB consecutive wires (block-rows of E) and RG
+// right-hand sides, one thread per (wire, right-hand side): it accumulates the m_p rows of its wire
+// over the wire's K_p columns.  The columns of one block are consecutive unknowns, so the values a
+// thread gathers from u come in short runs (one per block) that the L1 cache serves after the first
+// load; the entries of E are the same address for every thread of a wire (one transaction per
+// warp).  Rows are taken eight at a time (a wire has at most SWM_MAX_SEG - 1 rows).  The results go
+// through shared memory so that w is written as one run of the tile's consecutive rows per
+// right-hand side.  With RES (the residual at the start of a cycle) every right-hand side takes
+// part, the source is Y and the result W = B - (y + E y).
+constexpr int kWireMaxRows = SWM_MAX_SEG - 1;
+template <typename TV, typename TE, bool RES = false>
+__global__ void __launch_bounds__(256) k_spmv_w(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
+                                                const TE* __restrict__ E, const cplx<TV>* __restrict__ U,
+                                                cplx<TV>* __restrict__ Wv, const cplx<TV>* __restrict__ B, int RG,
+                                                int WB, int ystride) {
+  if (!RES && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+  extern __shared__ __align__(16) unsigned char sm_w[];
+  cplx<TV>* ys = reinterpret_cast<cplx<TV>*>(sm_w);  // [RG][ystride]
+  const int64_t N = P.N;
+  const int64_t p0 = (int64_t)blockIdx.x * WB;
+  const int64_t pe = min(p0 + (int64_t)WB, nw);
+  const int r0 = blockIdx.y * RG;
+  const int nr = min(RG, P.R - r0);
+  const int64_t n0 = off[p0];
+  const int rows = (int)(off[pe] - n0);
+  const int pl = (int)threadIdx.x / RG, rl = (int)threadIdx.x % RG;
+  const int64_t p = p0 + pl;
+  const int r = r0 + rl;
+  if (pl < WB && p < pe && rl < nr && (RES || P.active[r])) {
+    const int64_t op = off[p];
+    const int m = (int)(off[p + 1] - op);
+    const int K = lay.K[p];
+    const TE* Ep = E + lay.rowbase[p];
+    const int32_t* cm = lay.colmap + lay.cmbase[p];
+    const cplx<TV>* Ur = U + (int64_t)r * N;
+    cplx<TV>* yr = ys + (int64_t)rl * ystride + (op - n0);
+    for (int i0 = 0; i0 < m; i0 += 8) {
+      const int mm = min(8, m - i0);
+      const TE* Ei = Ep + (int64_t)i0 * K;
+      cplx<TV> acc[8];
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) acc[ii] = mkc<TV>(0, 0);
+      int k = 0;
+      for (; k + 3 < K; k += 4) {
+        int32_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = cm[k + u];
+        cplx<TV> x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = Ur[c[u]];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii)
+          if (ii < mm) {
+            cplx<TV> e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = ELoad<TV, TE>::ld(Ei + (int64_t)ii * K + k + u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cfma(acc[ii], e[u], x[u]);
+          }
+      }
+      for (; k < K; ++k) {
+        const cplx<TV> x = Ur[cm[k]];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii)
+          if (ii < mm) cfma(acc[ii], ELoad<TV, TE>::ld(Ei + (int64_t)ii * K + k), x);
+      }
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii)
+        if (ii < mm) yr[i0 + ii] = acc[ii];
+    }
+  }
+  __syncthreads();
+  // write: warp w takes right-hand sides w, w + nwarps, ...; its lanes take the tile's rows
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+  for (int b = w; b < nr; b += nwp) {
+    const int rr = r0 + b;
+    if (!RES && !P.active[rr]) continue;
+    const cplx<TV>* yb = ys + (int64_t)b * ystride;
+    for (int t = lane; t < rows; t += 32) {
+      const int64_t o = (int64_t)rr * N + n0 + t;
+      const cplx<TV> v = U[o] + yb[t];
+      Wv[o] = RES ? B[o] - v : v;
+    }
+  }
+}
+
+// Tile shape of k_spmv_w for R right-hand sides: RG right-hand sides per CTA (all of them up to
+// 64, else balanced groups of at most 64), WB = 256 / RG wires per CTA, and the odd row stride of
+// its shared-memory results.
+struct WireTile {
+  int RG, WB, ystride;
+  unsigned gx, gy;
+  size_t smem;
+};
+template <typename TV>
+WireTile wire_tile(int R, int64_t nw) {
+  WireTile t{};
+  const int groups = (int)ceil_div(R, 64);
+  t.RG = (int)ceil_div(R, groups);
+  t.WB = std::max(1, 256 / t.RG);
+  t.ystride = (t.WB * kWireMaxRows) | 1;
+  t.gx = (unsigned)ceil_div(nw, t.WB);
+  t.gy = (unsigned)ceil_div(R, t.RG);
+  t.smem = sizeof(cplx<TV>) * (size_t)t.RG * t.ystride;
+  return t;
+}
+
 // Arrival of one right-hand side at the end of the dots pass of step j; the last one advances the
 // step (and counts the Hessenberg column it completed) and ends the cycle when nothing is active
 // or the closing pass is done.
@@ -783,7 +891,11 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   // the right-hand-side-minor form; with several right-hand sides the form is timed on this system
   // the first time its shape is solved, and kept.
   constexpr int kMinor = 32;
+  constexpr int kWire = 64;  // k_spmv_w: wire-tiled, right-hand-side major, no transposed copy
   int rb = multi ? 8 : 1;
+  const WireTile wt = wire_tile<TV>(R, ctx->nw);
+  if (multi && wt.smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, false>, ctx->smem_optin));
+  if (multi && wt.smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, true>, ctx->smem_optin));
   // res: the residual U = B - A Y of a cycle's start in the same form (every right-hand side)
   auto product = [&](cudaStream_t s, int b, auto res_tag) -> int {
     constexpr bool RS = decltype(res_tag)::value;
@@ -806,6 +918,10 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
                                                                                        ws->Xt, dst, Bv);
         break;
       }
+      case kWire:
+        k_spmv_w<TV, TE, RS><<<dim3(wt.gx, wt.gy), 256, wt.smem, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, dst,
+                                                                      Bv, wt.RG, wt.WB, wt.ystride);
+        break;
       default: k_spmv<TV, TE, 8, RS><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, src, dst, Bv); break;
     }
     SWM_LAUNCHED();
@@ -846,7 +962,10 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     int found = 0;
     for (const auto& t : ctx->tuned)
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
-    if (found) {
+    const int forced = ctx->product_form;
+    if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || (forced == kMinor && ws->Xt)) {
+      rb = forced;
+    } else if (found) {
       rb = found;
     } else {
       // first cycle's residual and start (the loop below repeats them; both are idempotent), then
@@ -858,7 +977,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int b : {4, 8, 16, kMinor}) {
+      for (int b : {4, 8, 16, kMinor, kWire}) {
         if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
         if (b == kMinor && !ws->Xt) continue;
         SWM_TRY(launch_product(st, b));
@@ -888,14 +1007,14 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   if (use_graph) {
     struct Key {
       KPtr P;
-      const void* ptr[7];
+      const void* ptr[8];
       Layout lay;
       unsigned gx, gy, bits;
     } key;
     std::memset(&key, 0, sizeof(key));
     key.P = P;
-    const void* ptrs[7] = {ctx->rowinfo, ctx->offd.colmap, E, U, Wv, V, ws->Xt};
-    for (int i = 0; i < 7; ++i) key.ptr[i] = ptrs[i];
+    const void* ptrs[8] = {ctx->rowinfo, ctx->offd.colmap, E, U, Wv, V, ws->Xt, ctx->off};
+    for (int i = 0; i < 8; ++i) key.ptr[i] = ptrs[i];
     key.lay = ctx->offd;
     key.gx = g_chunk.x;
     key.gy = g_chunk.y;
@@ -1112,6 +1231,19 @@ int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter) {
   if (ctx->prec == SWM_C128)
     return gmres_impl<double, c128>(ctx, (const c128*)ctx->Zp, tol, restart, max_iter, nullptr, nullptr);
   return gmres_impl<float, c64>(ctx, (const c64*)ctx->Zp, tol, restart, max_iter, nullptr, nullptr);
+}
+
+int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr) {
+  KPtr P{};
+  P.R = ctx->n_rhs;
+  P.N = ctx->N;
+  const WireTile wt = wire_tile<double>(P.R, ctx->nw);
+  if (wt.smem > 48 * 1024)
+    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c64, true>, ctx->smem_optin));
+  k_spmv_w<double, c64, true><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
+      P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, Rr, B, wt.RG, wt.WB, wt.ystride);
+  SWM_LAUNCHED();
+  return SWM_OK;
 }
 
 int gmres_inner_bf16(swm_ctx* ctx, double tol, int restart, int max_iter, void** y_out, int* iters) {

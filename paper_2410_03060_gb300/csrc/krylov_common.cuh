@@ -47,13 +47,21 @@ struct KPtr {
   double tol;
 };
 
-// Entry of E as the vector type: complex128 / complex64 storage as is, complex bfloat16 storage
-// (one __nv_bfloat162 per entry, real part first) widened to complex64.
+// Entry of E as the vector type: complex128 / complex64 storage as is, complex64 storage widened to
+// complex128 (the float64 residual of the refinement), complex bfloat16 storage (one
+// __nv_bfloat162 per entry, real part first) widened to complex64.
 template <typename TV, typename TE>
 struct ELoad;
 template <typename TV>
 struct ELoad<TV, cplx<TV>> {
   static __device__ __forceinline__ cplx<TV> ld(const cplx<TV>* p) { return *p; }
+};
+template <>
+struct ELoad<double, cplx<float>> {
+  static __device__ __forceinline__ cplx<double> ld(const cplx<float>* p) {
+    const cplx<float> v = *p;
+    return mkc<double>(v.re, v.im);
+  }
 };
 template <>
 struct ELoad<float, __nv_bfloat162> {

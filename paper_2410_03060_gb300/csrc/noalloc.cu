@@ -24,8 +24,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 
-// Device address of g_far_scratch on the current device, looked up once per device.  In host
-// code the symbol itself is only a host-side stand-in, never a device address.
+// Device address of g_far_scratch on the current device, looked up once per device (in the
+// device's primary context, the one the CUDA runtime makes current).  In host code the symbol
+// itself is only a host-side stand-in, never a device address.
 int scratch_on_current_device(void** out, std::string* err) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -82,6 +83,13 @@ int far_noalloc_impl(void* cuda_stream, int64_t nw, const double* centres, const
       !currents || !obs || !sigma_out || !(k > 0.0)) {
     msg = "swm_far_field_noalloc: bad argument";
     return SWM_EINVAL;
+  }
+  {
+    const void* ptrs[8] = {centres, dirs, lengths, nseg, off, currents, obs, sigma_out};
+    if (!all_device_memory(ptrs, 8)) {
+      msg = "swm_far_field_noalloc: every array must be device memory";
+      return SWM_EINVAL;
+    }
   }
   const int64_t npairs = (int64_t)n_rhs * n_obs;
   const size_t per_chunk = (size_t)npairs * 3 * sizeof(c128);

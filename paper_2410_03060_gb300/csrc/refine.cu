@@ -68,6 +68,29 @@ __global__ void __launch_bounds__(kT) k_ir_residual(int64_t N, int chunk, const 
   }
 }
 
+// Partial sums of |r|^2 per chunk of rows (the residual formed by the wire-tiled product).
+__global__ void __launch_bounds__(kT) k_ir_norms(int64_t N, int chunk, const c128* __restrict__ Rr,
+                                                 double* __restrict__ part) {
+  const int r = blockIdx.y;
+  const int64_t n0 = (int64_t)blockIdx.x * chunk;
+  const int cnt = (int)min((int64_t)chunk, N - n0);
+  const c128* v = Rr + (int64_t)r * N + n0;
+  double s = 0.0;
+  for (int t = threadIdx.x; t < cnt; t += kT) {
+    const c128 a = v[t];
+    s += a.re * a.re + a.im * a.im;
+  }
+  __shared__ double red[kT / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kT / 32; ++i) t += red[i];
+    part[(int64_t)r * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 // Right-hand side of the inner solve: complex64 r / |r| (0 for converged right-hand sides).
 __global__ void k_ir_scale(int64_t N, const c128* __restrict__ Rr, const double* __restrict__ scale,
                            c64* __restrict__ Bv) {
@@ -143,8 +166,14 @@ int refine_solve(swm_ctx* ctx, const double* frames_dev, double tol, int restart
   bool conv = false;
   while (true) {
     ctx->prof_begin(SWM_K_APPLY);
-    k_ir_residual<<<gres, kT, 0, st>>>(N, chunk, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap, (const c64*)ctx->Zp,
-                                       B64, Y64, Rr, part);
+    if (R > 1) {
+      // several right-hand sides share each read of E (wire-tiled product), then the norms
+      SWM_TRY(residual_f64_wire(ctx, B64, Y64, Rr));
+      k_ir_norms<<<gres, kT, 0, st>>>(N, chunk, Rr, part);
+    } else {
+      k_ir_residual<<<gres, kT, 0, st>>>(N, chunk, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap,
+                                         (const c64*)ctx->Zp, B64, Y64, Rr, part);
+    }
     ctx->prof_end(SWM_K_APPLY);
     SWM_LAUNCHED();
     SWM_CK(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));

@@ -353,7 +353,8 @@ def swm_rcs_monostatic(ctx: Ctx, sigma_out) -> int:
 def swm_run(ctx: Ctx, centres, dirs, lengths, radii, nseg, k: float, r_c: float, precision: int, inc, obs,
             sigma_out, tol: float = 1e-6, restart: int = 50, max_iter: int = 1000) -> int:
     """swm_set_cloud, swm_build, swm_solve and swm_rcs_bistatic in one call (synchronising only
-    where the host needs device results); sigma_out as for swm_rcs_bistatic."""
+    where the host needs device results); sigma_out as for swm_rcs_bistatic.  With ``obs`` None
+    the RCS is monostatic and sigma_out is n_inc x 2, as for swm_rcs_monostatic."""
     nw = len(lengths)
     pc, k1, a1 = _ptr(centres, np.float64, (nw, 3), "centres")
     pt, k2, a2 = _ptr(dirs, np.float64, (nw, 3), "dirs")
@@ -363,11 +364,16 @@ def swm_run(ctx: Ctx, centres, dirs, lengths, radii, nseg, k: float, r_c: float,
     if len({k1, k2, k3, k4, k5}) != 1:
         raise TypeError("swm_run: all cloud inputs must be host arrays or all device tensors")
     inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
-    obs = np.ascontiguousarray(np.atleast_2d(obs), dtype=np.float64)
-    ps, kind, _ = _out_ptr(sigma_out, np.float64, (inc.shape[0], obs.shape[0], 2), "sigma_out")
+    if obs is None:
+        n_obs, pobs = 0, None
+        ps, kind, _ = _out_ptr(sigma_out, np.float64, (inc.shape[0], 2), "sigma_out")
+    else:
+        obs = np.ascontiguousarray(np.atleast_2d(obs), dtype=np.float64)
+        n_obs, pobs = obs.shape[0], obs.ctypes.data_as(C.c_void_p)
+        ps, kind, _ = _out_ptr(sigma_out, np.float64, (inc.shape[0], n_obs, 2), "sigma_out")
     return _check(ctx, load().swm_run(ctx.handle, nw, pc, pt, pl, pr, pn, k1, float(k), float(r_c), int(precision),
                                       inc.shape[0], inc.ctypes.data_as(C.c_void_p), float(tol), int(restart),
-                                      int(max_iter), obs.shape[0], obs.ctypes.data_as(C.c_void_p), ps, kind))
+                                      int(max_iter), n_obs, pobs, ps, kind))
 
 
 def swm_get_stats(ctx: Ctx) -> dict:
@@ -407,19 +413,25 @@ def swm_get_rhs(ctx: Ctx) -> np.ndarray:
 
 
 def swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out, _entry="swm_far_field") -> int:
-    """Stateless far-field RCS; every array a CUDA torch tensor (see include/swm.h)."""
+    """Stateless far-field RCS; every array a CUDA torch tensor (see include/swm.h).  Host arrays
+    are refused (the C entry point takes device pointers only)."""
     nw = lengths.shape[0]
     n_rhs, n_obs = currents.shape[0], obs.shape[0]
-    args = [_ptr(centres, np.float64, (nw, 3), "centres")[0], _ptr(dirs, np.float64, (nw, 3), "dirs")[0],
-            _ptr(lengths, np.float64, (nw,), "lengths")[0], _ptr(nseg, np.int32, (nw,), "nseg")[0],
-            _ptr(off, np.int64, (nw + 1,), "off")[0]]
-    pc = _ptr(currents, np.complex128, None, "currents")[0]
-    po = _ptr(obs, np.float64, (n_obs, 2), "obs")[0]
-    ps = _ptr(sigma_out, np.float64, (n_rhs, n_obs, 2), "sigma_out")[0]
+    conv = [_ptr(centres, np.float64, (nw, 3), "centres"), _ptr(dirs, np.float64, (nw, 3), "dirs"),
+            _ptr(lengths, np.float64, (nw,), "lengths"), _ptr(nseg, np.int32, (nw,), "nseg"),
+            _ptr(off, np.int64, (nw + 1,), "off"), _ptr(currents, np.complex128, None, "currents"),
+            _ptr(obs, np.float64, (n_obs, 2), "obs"), _ptr(sigma_out, np.float64, (n_rhs, n_obs, 2), "sigma_out")]
+    names = ("centres", "dirs", "lengths", "nseg", "off", "currents", "obs", "sigma_out")
+    for name, (_, kind, _) in zip(names, conv):
+        if kind != SWM_DEVICE:
+            raise TypeError(f"{_entry}: {name} must be a CUDA tensor (device memory)")
+    keep = [c[2] for c in conv]  # the converted objects stay alive until the call returns
+    ptrs = [c[0] for c in conv]
     if stream is None:
         stream = _torch_stream_handle()
     lib = load()
-    rc = getattr(lib, _entry)(C.c_void_p(stream), nw, *args, float(k), n_rhs, pc, n_obs, po, ps)
+    rc = getattr(lib, _entry)(C.c_void_p(stream), nw, *ptrs[:5], float(k), n_rhs, ptrs[5], n_obs, ptrs[6], ptrs[7])
+    del keep
     if rc < 0:
         raise SwmError(rc, lib.swm_stateless_error().decode())
     return rc

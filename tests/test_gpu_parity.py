@@ -155,6 +155,34 @@ def test_far_field_stateless_matches_oracle():
     assert np.max(np.abs(sig.cpu().numpy() - ref)) / np.max(ref) < 1e-10
 
 
+def test_far_field_stateless_refuses_host_memory():
+    """The stateless far field takes device pointers only: the binding refuses host arrays, and the
+    C entry point itself returns SWM_EINVAL when one of its pointers is host memory."""
+    import ctypes as C
+
+    import torch
+    from paper_2410_03060_gb300 import swm
+
+    cl = _mixed_cloud(seed=9)
+    m, off = O.numbering(cl.nseg)
+    cur = np.ones((1, off[-1]), dtype=np.complex128)
+    obs = np.array([[0.3, 0.2]])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sig = torch.zeros((1, 1, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        swm.swm_far_field(None, t(cl.centres), t(cl.dirs), t(cl.lengths), t(cl.nseg), t(off), K, cur, t(obs), sig)
+    dev = [t(cl.centres), t(cl.dirs), t(cl.lengths), t(cl.nseg), t(off), t(cur), t(obs)]
+    host_obs = np.ascontiguousarray(obs)
+    lib = swm.load()
+    for entry in ("swm_far_field", "swm_far_field_noalloc"):
+        rc = getattr(lib, entry)(C.c_void_p(torch.cuda.current_stream().cuda_stream), cl.nw,
+                                 *[C.c_void_p(a.data_ptr()) for a in dev[:5]], float(K), 1,
+                                 C.c_void_p(dev[5].data_ptr()), 1, host_obs.ctypes.data_as(C.c_void_p),
+                                 C.c_void_p(sig.data_ptr()))
+        assert rc == swm.SWM_EINVAL
+        assert "device memory" in lib.swm_stateless_error().decode()
+
+
 def test_c64_far_field_many_chunks_matches_oracle():
     """The float32 far field where each pair's wire range is cut into more than 256 chunks (its
     reduction then takes several batches per lane): bistatic and monostatic RCS of the solved
@@ -229,6 +257,50 @@ def test_mid_workload_at_full_size_sampled_parity():
 def _rhat(obs):
     th, ph = obs[:, 0], obs[:, 1]
     return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+
+
+# ------------------------------------------------------------------------------------- units
+def test_scaled_currents_convert_to_amperes_and_ohms():
+    """The ABI returns jt, the solution of the paper's system multiplied by j omega mu0 (Sec. II-A,
+    Eq. TW_EFIE_MOM); its header states the physical current as I = jt / (j omega mu0) =
+    -j jt / (k eta0) and Z_phys = j k eta0 Z.  Checked on the GPU's own outputs: (1) the GPU's
+    self block of a half-wave dipole, so converted, gives an input impedance (delta gap at the
+    centre vertex) in the textbook band for a = 1e-3 wavelength; (2) the power the converted
+    currents take from a plane wave of 1 V/m, sigma_ext = eta0 Re(I^H b), equals the power they
+    scatter, (1/4 pi) times the integral of the GPU's bistatic RCS over the sphere (optical
+    theorem for a lossless conductor), on a small dense cloud."""
+    import json
+    import os
+    from paper_2410_03060_gb300 import swm
+    from synth import cloud_single
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "textbook_values.json")))
+    band = g["halfwave_dipole_input_impedance_thin_ohm"]["band_radius_1e-3"]
+    dip = cloud_single(0.5, 16)
+    out = run_gpu(dip, K, 3.0, C128, np.array([[math.pi / 2, 0.0, 0.0]]))
+    try:
+        Zs = swm.swm_get_block(out["ctx"], 0, 0, 15, 15)
+    finally:
+        swm.swm_destroy(out["ctx"])
+    zin = 1j * K * O.ETA0 / np.linalg.inv(Zs)[7, 7]
+    assert band["R"][0] <= zin.real <= band["R"][1] and band["X"][0] <= zin.imag <= band["X"][1], zin
+
+    cl = cloud_uniform_cube(6, 1.2, seed=41, length=0.47, nseg=8)
+    inc = np.array([[0.6, 0.3, 0.4]])
+    nt, nph = 32, 64
+    xg, wg = np.polynomial.legendre.leggauss(nt)
+    th = np.arccos(xg)
+    obs = np.array([[t, 2 * math.pi * j / nph] for t in th for j in range(nph)])
+    out = run_gpu(cl, K, 0.0, C128, inc, obs=obs, tol=1e-12)
+    try:
+        I_amp = -1j * out["currents"][:, 0] / (K * O.ETA0)
+        sig_ext = O.ETA0 * float(np.real(np.vdot(I_amp, out["rhs"][:, 0])))
+        s = out["sigma"][0].sum(axis=1).reshape(nt, nph)
+        sig_sca = float(np.sum(wg[:, None] * s) * (2 * math.pi / nph)) / (4 * math.pi)
+    finally:
+        swm.swm_destroy(out["ctx"])
+    assert sig_ext > 0
+    assert abs(sig_ext - sig_sca) / sig_sca < 1e-3, (sig_ext, sig_sca)
 
 
 # ------------------------------------------------------------------------------------- edge cases
@@ -321,6 +393,18 @@ def test_run_equals_separate_calls(prec):
                 assert st[key] == ref["stats"][key], key
             if ctx is not ref["ctx"]:
                 swm.swm_destroy(ctx)
+        # monostatic form (no observation list): the RCS of swm_rcs_monostatic after the same solve
+        incm = np.array([[0.3, 0.1, 0.2], [1.2, 2.0, 0.0], [2.9, 4.0, 1.0]])
+        refm = run_gpu(cl, K, 0.9, prec, incm, tol=tol, max_iter=500, mono=True)
+        try:
+            ctx = swm.swm_create(0)
+            sm = np.zeros((3, 2))
+            rc = swm.swm_run(ctx, cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg, K, 0.9, prec, incm, None, sm,
+                             tol=tol, max_iter=500)
+            assert rc == refm["rc"] and np.array_equal(sm, refm["sigma_mono"])
+            swm.swm_destroy(ctx)
+        finally:
+            swm.swm_destroy(refm["ctx"])
         ctx = swm.swm_create(0)
         bad = cl.dirs.copy()
         bad[3] *= 1.5
@@ -404,6 +488,37 @@ def test_split_step_path_matches_oracle(monkeypatch):
             s_ref = O.rcs_bistatic(cl, K, X, obs)
             for i in range(inc.shape[0]):
                 assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
+
+
+@pytest.mark.parametrize("form", [4, 8, 16, 32, 64])
+def test_every_product_form_matches_oracle(monkeypatch, form):
+    """Each form of the many-incidence product, forced (SWM_PRODUCT_FORM) on the large-system GMRES
+    step: 4/8/16 incidences per read of E, 32 the incidence-minor form, 64 the wire-tiled form.
+    A cloud with every segment count 2..16 (wires of up to 15 rows, two row groups in the
+    wire-tiled form) and ragged tiles; 37 and 70 incidences (one group of 37, two groups of 35 in
+    the wire-tiled form); currents against the oracle's LU solution and the RCS within 0.1 dB."""
+    from paper_2410_03060_gb300 import swm
+
+    monkeypatch.setenv("SWM_SPLIT_ROWS", "0")
+    monkeypatch.setenv("SWM_PRODUCT_FORM", str(form))
+    cl = _mixed_cloud(nw=61, side=3.0, seed=45)
+    obs = observations_phi_cut(24)
+    g = np.random.default_rng(8)
+    many = lambda n: np.stack([g.uniform(0, np.pi, n), g.uniform(0, 2 * np.pi, n), g.uniform(0, np.pi, n)], 1)
+    for n_inc in (37, 70):
+        inc = many(n_inc)
+        Z = O.assemble(cl, K, 1.2, sparse=False)
+        X = O.solve_lu(Z, O.rhs(cl, K, inc))
+        s_ref = O.rcs_bistatic(cl, K, X, obs)
+        for prec, tol in ((C128, 1e-5), (C64, 1e-3)):
+            out = run_gpu(cl, K, 1.2, prec, inc, obs=obs, tol=1e-11 if prec == C128 else 1e-6)
+            try:
+                assert out["stats"]["step_rhs_block"] == form
+                assert np.linalg.norm(out["currents"] - X) / np.linalg.norm(X) < tol
+                for i in range(n_inc):
+                    assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
+            finally:
+                swm.swm_destroy(out["ctx"])
 
 
 def test_per_kernel_step_path_matches_oracle(monkeypatch):
