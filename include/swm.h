@@ -337,6 +337,46 @@ int swm_far_field_noalloc(void* cuda_stream, int64_t nw, const double* centres, 
                           int n_rhs, const double* currents, int n_obs, const double* obs,
                           double* sigma_out);
 
+/* Received far-field components of given currents (Sec. III-A), same arguments as swm_far_field
+ * but comp_out receives n_rhs x n_obs x 2 complex128 (interleaved re, im): theta_hat . F and
+ * phi_hat . F at each observation, F the radiation vector of the currents, so that
+ * sigma = |component|^2 / (4 pi).  The components add over disjoint sets of wires: a cloud split
+ * over ranks sums them (one all-reduce) and forms sigma afterwards.  Device memory only
+ * (SWM_EINVAL otherwise); scratch as swm_far_field. */
+int swm_far_components(void* cuda_stream, int64_t nw, const double* centres, const double* dirs,
+                       const double* lengths, const int32_t* nseg, const int64_t* off, double k, int n_rhs,
+                       const double* currents, int n_obs, const double* obs, double* comp_out);
+
+/* Building blocks of a Krylov solve driven from outside the library on a cloud split over ranks
+ * (Sec. II-B: the S-NFC system couples only wires within r_c, so a rank holding its own wires and
+ * the wires within r_c of them -- its halo -- has everything its rows need).  All vectors are
+ * n_rhs x N complex128 (interleaved re, im), N the context's unknowns, the caller's unknown order.
+ * Each call needs a built context, runs on the context's stream, computes in float64 arithmetic
+ * with the stored values, and returns when its output is complete.
+ *
+ * swm_apply: y = A x with A = Z M^-1 = I + E (E = Z blockdiag(Z_pp)^-1 as stored by swm_build),
+ *   the operator of the right-preconditioned iteration; every row of the context (a halo wire's
+ *   rows lack the couplings outside the context and are to be discarded by the caller).
+ *   x and y of kinds x_kind / y_kind (SWM_HOST or SWM_DEVICE).
+ * swm_precond_apply: x = M^-1 y = blockdiag(Z_pp)^-1 y, wire by wire (the block-diagonal
+ *   preconditioner named after Eq. neardef).
+ * swm_rhs: the right-hand sides b (Eq. (4)) of n_inc incidences (host list as in swm_solve). */
+int swm_apply(swm_ctx* ctx, int n_rhs, const double* x, int x_kind, double* y, int y_kind);
+int swm_precond_apply(swm_ctx* ctx, int n_rhs, const double* y, int y_kind, double* x, int x_kind);
+int swm_rhs(swm_ctx* ctx, int n_inc, const double* inc, double* b_out, int out_kind);
+
+/* Vector algebra of classical Gram-Schmidt on device vectors (no counterpart in the paper; the
+ * paper's Krylov solver needs it, Sec. II-B).  Q is k or more vectors of n_rhs x n complex128,
+ * contiguous (vector i at Q + 2 i n_rhs n doubles); v, out n_rhs x n.  Device memory only
+ * (SWM_EINVAL otherwise); k * n_rhs <= 65535.
+ * swm_vec_dots: out[i][r] = sum_n conj(Q[i][r][n]) v[r][n], k x n_rhs complex128 to host memory
+ *   (partial sums over chunks of rows added in a fixed order).
+ * swm_vec_axpy: v[r] -= sum over i < k of coef[i][r] Q[i][r], coef k x n_rhs complex128 (host).
+ * swm_vec_scale: out[r] = a[r] v[r], a n_rhs float64 (host). */
+int swm_vec_dots(swm_ctx* ctx, int64_t n, int k, int n_rhs, const double* Q, const double* v, double* out);
+int swm_vec_axpy(swm_ctx* ctx, int64_t n, int k, int n_rhs, const double* Q, const double* coef, double* v);
+int swm_vec_scale(swm_ctx* ctx, int64_t n, int n_rhs, const double* a, const double* v, double* out);
+
 /* Message of the last failed stateless call on this host thread ("" if none). */
 const char* swm_stateless_error(void);
 

@@ -922,19 +922,22 @@ int swm_get_rhs(swm_ctx* ctx, double* re_im_out) {
 
 const char* swm_stateless_error(void) { return g_stateless_err.c_str(); }
 
-int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const double* dirs, const double* lengths,
-                  const int32_t* nseg, const int64_t* off, double k, int n_rhs, const double* currents, int n_obs,
-                  const double* obs, double* sigma_out) {
+// The stateless far field: sigma, or with `components` the received components theta_hat . F and
+// phi_hat . F (two complex numbers per pair), which sum over disjoint sets of wires.
+static int far_field_common(void* cuda_stream, int64_t nw, const double* centres, const double* dirs,
+                            const double* lengths, const int32_t* nseg, const int64_t* off, double k, int n_rhs,
+                            const double* currents, int n_obs, const double* obs, double* sigma_out, bool components) {
   g_stateless_err.clear();
+  const std::string who = components ? "swm_far_components: " : "swm_far_field: ";
   if (nw < 1 || n_rhs < 1 || n_obs < 1 || n_rhs > 65535 || !centres || !dirs || !lengths || !nseg || !off ||
       !currents || !obs || !sigma_out || !(k > 0.0)) {
-    g_stateless_err = "swm_far_field: bad argument";
+    g_stateless_err = who + "bad argument";
     return SWM_EINVAL;
   }
   {
     const void* ptrs[8] = {centres, dirs, lengths, nseg, off, currents, obs, sigma_out};
     if (!all_device_memory(ptrs, 8)) {
-      g_stateless_err = "swm_far_field: every array must be device memory";
+      g_stateless_err = who + "every array must be device memory";
       return SWM_EINVAL;
     }
   }
@@ -942,7 +945,7 @@ int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const do
   int64_t N = 0;
   if (cudaMemcpyAsync(&N, off + nw, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
-    g_stateless_err = "swm_far_field: cannot read off[nw]";
+    g_stateless_err = who + "cannot read off[nw]";
     return SWM_ECUDA;
   }
   const int64_t npairs = (int64_t)n_rhs * n_obs;
@@ -950,19 +953,33 @@ int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const do
   void* scratch = nullptr;
   if (cudaMallocAsync(&scratch, sb, st) != cudaSuccess) {
     cudaGetLastError();
-    g_stateless_err = "swm_far_field: scratch allocation failed";
+    g_stateless_err = who + "scratch allocation failed";
     return SWM_ENOMEM;
   }
   int rc = far_field_launch(st, nullptr, false, true, currents, nw, N, centres, dirs, nullptr, nullptr, nullptr,
                             nullptr, nullptr, nullptr, lengths, nseg, off, false, k, n_rhs, n_obs, obs, 2, false,
-                            sigma_out, scratch, sb, &g_stateless_err);
+                            sigma_out, scratch, sb, &g_stateless_err, components);
   cudaFreeAsync(scratch, st);
   if (rc < 0) return rc;
   if (cudaStreamSynchronize(st) != cudaSuccess) {
-    g_stateless_err = std::string("swm_far_field: ") + cudaGetErrorString(cudaGetLastError());
+    g_stateless_err = who + cudaGetErrorString(cudaGetLastError());
     return SWM_ECUDA;
   }
   return SWM_OK;
+}
+
+int swm_far_field(void* cuda_stream, int64_t nw, const double* centres, const double* dirs, const double* lengths,
+                  const int32_t* nseg, const int64_t* off, double k, int n_rhs, const double* currents, int n_obs,
+                  const double* obs, double* sigma_out) {
+  return far_field_common(cuda_stream, nw, centres, dirs, lengths, nseg, off, k, n_rhs, currents, n_obs, obs,
+                          sigma_out, false);
+}
+
+int swm_far_components(void* cuda_stream, int64_t nw, const double* centres, const double* dirs,
+                       const double* lengths, const int32_t* nseg, const int64_t* off, double k, int n_rhs,
+                       const double* currents, int n_obs, const double* obs, double* comp_out) {
+  return far_field_common(cuda_stream, nw, centres, dirs, lengths, nseg, off, k, n_rhs, currents, n_obs, obs,
+                          comp_out, true);
 }
 
 }  // extern "C"

@@ -285,7 +285,7 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
                      const double* cz, const double* tx, const double* ty, const double* tz, const double* Ls,
                      const int32_t* ns, const int64_t* off, bool soa, double k, int n_rhs, int n_obs,
                      const double* obs, int obs_stride, bool mono, double* sigma, void* scratch, size_t scratch_bytes,
-                     std::string* err);
+                     std::string* err, bool components = false);
 // incidence frames on the host: k_hat (propagation, = -arrival) then polarisation e, 6 doubles each
 void frames_host(const double* inc, int n, std::vector<double>& out);
 // true if every pointer is device or managed memory (api.cu)
@@ -336,6 +336,9 @@ int gmres_inner_bf16(swm_ctx* ctx, double tol, int restart, int max_iter, void**
 // Rr = B - (Y + E Y) for every right-hand side in float64 vectors with the complex64 E, one read of
 // E shared by all right-hand sides (wire-tiled product, krylov.cu)
 int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr);
+// Y = X + E X for R right-hand sides in float64 arithmetic with the stored E (complex128 or
+// complex64), internal order, every right-hand side (krylov.cu)
+int product_f64(swm_ctx* ctx, int R, const c128* X, c128* Y);
 // rhs_ff.cu: right-hand sides in float64 into `out` ([n_inc][N], internal order)
 int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out);
 // refine.cu: float64 iterative refinement around bfloat16-storage GMRES (precision SWM_BF16)

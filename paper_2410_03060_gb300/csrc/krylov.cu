@@ -237,23 +237,28 @@ __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restric
   }
 }
 
-// Product with many right-hand sides, wire-tiled: w = u + E u read and written right-hand-side
-// major, with no transposed copy of u.  A CTA takes WB consecutive wires (block-rows of E) and RG
-// right-hand sides, one thread per (wire, right-hand side): it accumulates the m_p rows of its wire
-// over the wire's K_p columns.  The columns of one block are consecutive unknowns, so the values a
-// thread gathers from u come in short runs (one per block) that the L1 cache serves after the first
-// load; the entries of E are the same address for every thread of a wire (one transaction per
-// warp).  Rows are taken eight at a time (a wire has at most SWM_MAX_SEG - 1 rows).  The results go
-// through shared memory so that w is written as one run of the tile's consecutive rows per
-// right-hand side.  With RES (the residual at the start of a cycle) every right-hand side takes
-// part, the source is Y and the result W = B - (y + E y).
+// Product with many right-hand sides, wire-tiled: w = u + E u.  A CTA takes WB consecutive wires
+// (block-rows of E) and RG right-hand sides, one thread per (wire, right-hand side): it
+// accumulates all m_p rows of its wire over the wire's K_p columns, so each gathered value of u
+// serves every row of the wire from a register.  The gathers read Xt, u right-hand-side minor
+// ([N][R], XT), where the threads of a wire (consecutive right-hand sides) read consecutive
+// addresses, or, without XT, u itself (right-hand-side major; each thread's gathers are then a
+// short run per block, but the lanes of a warp read R-apart lines).  The entries of E are the same
+// address for every thread of a wire (one transaction per warp).  Rows are taken eight at a time
+// (a wire has at most SWM_MAX_SEG - 1 rows).  The results go through shared memory so that w is
+// written right-hand-side major as one run of the tile's consecutive rows per right-hand side.
+// MODE kStepW: a GMRES step (active right-hand sides only); kResW: the residual at the start of a
+// cycle, every right-hand side, source Y, result W = B - (y + E y); kPlainW: every right-hand side,
+// W = u + E u (the product on its own, for callers outside GMRES).
 constexpr int kWireMaxRows = SWM_MAX_SEG - 1;
-template <typename TV, typename TE, bool RES = false>
+constexpr int kStepW = 0, kResW = 1, kPlainW = 2;
+template <typename TV, typename TE, int MODE = kStepW, bool XT = false>
 __global__ void __launch_bounds__(256) k_spmv_w(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
                                                 const TE* __restrict__ E, const cplx<TV>* __restrict__ U,
-                                                cplx<TV>* __restrict__ Wv, const cplx<TV>* __restrict__ B, int RG,
-                                                int WB, int ystride) {
-  if (!RES && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+                                                const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ Wv,
+                                                const cplx<TV>* __restrict__ B, int RG, int WB, int ystride) {
+  constexpr bool RES = MODE == kResW, ALL = MODE != kStepW;
+  if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   extern __shared__ __align__(16) unsigned char sm_w[];
   cplx<TV>* ys = reinterpret_cast<cplx<TV>*>(sm_w);  // [RG][ystride]
   const int64_t N = P.N;
@@ -266,13 +271,15 @@ __global__ void __launch_bounds__(256) k_spmv_w(KPtr P, const int64_t* __restric
   const int pl = (int)threadIdx.x / RG, rl = (int)threadIdx.x % RG;
   const int64_t p = p0 + pl;
   const int r = r0 + rl;
-  if (pl < WB && p < pe && rl < nr && (RES || P.active[r])) {
+  if (pl < WB && p < pe && rl < nr && (ALL || P.active[r])) {
     const int64_t op = off[p];
     const int m = (int)(off[p + 1] - op);
     const int K = lay.K[p];
     const TE* Ep = E + lay.rowbase[p];
     const int32_t* cm = lay.colmap + lay.cmbase[p];
-    const cplx<TV>* Ur = U + (int64_t)r * N;
+    // gathered value of column c for this right-hand side
+    const cplx<TV>* xs = XT ? Xt + r : U + (int64_t)r * N;
+    const int64_t xstride = XT ? P.R : 1;
     cplx<TV>* yr = ys + (int64_t)rl * ystride + (op - n0);
     for (int i0 = 0; i0 < m; i0 += 8) {
       const int mm = min(8, m - i0);
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(256) k_spmv_w(KPtr P, const int64_t* __restric
         for (int u = 0; u < 4; ++u) c[u] = cm[k + u];
         cplx<TV> x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = Ur[c[u]];
+        for (int u = 0; u < 4; ++u) x[u] = xs[(int64_t)c[u] * xstride];
 #pragma unroll
         for (int ii = 0; ii < 8; ++ii)
           if (ii < mm) {
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(256) k_spmv_w(KPtr P, const int64_t* __restric
           }
       }
       for (; k < K; ++k) {
-        const cplx<TV> x = Ur[cm[k]];
+        const cplx<TV> x = xs[(int64_t)cm[k] * xstride];
 #pragma unroll
         for (int ii = 0; ii < 8; ++ii)
           if (ii < mm) cfma(acc[ii], ELoad<TV, TE>::ld(Ei + (int64_t)ii * K + k), x);
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(256) k_spmv_w(KPtr P, const int64_t* __restric
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwp = blockDim.x >> 5;
   for (int b = w; b < nr; b += nwp) {
     const int rr = r0 + b;
-    if (!RES && !P.active[rr]) continue;
+    if (!ALL && !P.active[rr]) continue;
     const cplx<TV>* yb = ys + (int64_t)b * ystride;
     for (int t = lane; t < rows; t += 32) {
       const int64_t o = (int64_t)rr * N + n0 + t;
@@ -607,20 +614,42 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
   cplx<TV>* u = U + (int64_t)r * N + n0;
   const cplx<TV>* w = Wv + (int64_t)r * N + n0;
   cplx<TV>* vj = V + ((int64_t)j * P.R + r) * N + n0;
-  for (int t = threadIdx.x; t < cnt; t += kRows) {
-    cplx<TV> x = u[t], y = w[t];
-#pragma unroll 4
-    for (int i = 0; i < j; ++i) {
-      const cplx<TV> v = V[((int64_t)i * P.R + r) * N + n0 + t];
-      const cplx<TV> a = ss[i], b = ts[i];
-      x.re = fma(-v.re, a.re, fma(v.im, a.im, x.re));
-      x.im = fma(-v.re, a.im, fma(-v.im, a.re, x.im));
-      y.re = fma(-v.re, b.re, fma(v.im, b.im, y.re));
-      y.im = fma(-v.re, b.im, fma(-v.im, b.re, y.im));
+  // four rows per thread (kRows apart, so every load is coalesced) and two basis vectors per
+  // pass: eight independent loads in flight per thread
+  constexpr int kQ = 4;
+  for (int t0 = threadIdx.x; t0 < cnt; t0 += kQ * kRows) {
+    cplx<TV> x[kQ], y[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int t = t0 + q * kRows;
+      x[q] = t < cnt ? u[t] : mkc<TV>(0, 0);
+      y[q] = t < cnt ? w[t] : mkc<TV>(0, 0);
     }
-    const cplx<TV> q = ih * x;
-    vj[t] = q;
-    u[t] = ih * y - q * gm;
+    const cplx<TV>* vb = V + (int64_t)r * N + n0 + t0;
+#pragma unroll 2
+    for (int i = 0; i < j; ++i) {
+      const cplx<TV>* vi = vb + (int64_t)i * P.R * N;
+      cplx<TV> v[kQ];
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) v[q] = t0 + q * kRows < cnt ? vi[q * kRows] : mkc<TV>(0, 0);
+      const cplx<TV> a = ss[i], b = ts[i];
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        x[q].re = fma(-v[q].re, a.re, fma(v[q].im, a.im, x[q].re));
+        x[q].im = fma(-v[q].re, a.im, fma(-v[q].im, a.re, x[q].im));
+        y[q].re = fma(-v[q].re, b.re, fma(v[q].im, b.im, y[q].re));
+        y[q].im = fma(-v[q].re, b.im, fma(-v[q].im, b.re, y[q].im));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int t = t0 + q * kRows;
+      if (t < cnt) {
+        const cplx<TV> qv = ih * x[q];
+        vj[t] = qv;
+        u[t] = ih * y[q] - qv * gm;
+      }
+    }
   }
 }
 
@@ -894,8 +923,12 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   constexpr int kWire = 64;  // k_spmv_w: wire-tiled, right-hand-side major, no transposed copy
   int rb = multi ? 8 : 1;
   const WireTile wt = wire_tile<TV>(R, ctx->nw);
-  if (multi && wt.smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, false>, ctx->smem_optin));
-  if (multi && wt.smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, true>, ctx->smem_optin));
+  if (multi && wt.smem > 48 * 1024) {
+    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kStepW, false>, ctx->smem_optin));
+    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kResW, false>, ctx->smem_optin));
+    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kStepW, true>, ctx->smem_optin));
+    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kResW, true>, ctx->smem_optin));
+  }
   // res: the residual U = B - A Y of a cycle's start in the same form (every right-hand side)
   auto product = [&](cudaStream_t s, int b, auto res_tag) -> int {
     constexpr bool RS = decltype(res_tag)::value;
@@ -919,8 +952,17 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
         break;
       }
       case kWire:
-        k_spmv_w<TV, TE, RS><<<dim3(wt.gx, wt.gy), 256, wt.smem, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, dst,
-                                                                      Bv, wt.RG, wt.WB, wt.ystride);
+        if (ws->Xt) {
+          // the gathers read u right-hand-side minor: transposed first
+          k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, src,
+                                                                                                        ws->Xt);
+          SWM_LAUNCHED();
+          k_spmv_w<TV, TE, RS ? kResW : kStepW, true><<<dim3(wt.gx, wt.gy), 256, wt.smem, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, dst, Bv, wt.RG, wt.WB, wt.ystride);
+        } else {
+          k_spmv_w<TV, TE, RS ? kResW : kStepW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB, wt.ystride);
+        }
         break;
       default: k_spmv<TV, TE, 8, RS><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, src, dst, Bv); break;
     }
@@ -1041,7 +1083,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       ctx->gm_key = kv;
     }
   }
-  const int launches_per_step = (rb == kMinor ? 2 : 1) + 2;
+  const int launches_per_step = (rb == kMinor || (rb == kWire && ws->Xt) ? 2 : 1) + 2;
   while (!persisted) {
     // residual of the current y and the start of a cycle
     ctx->prof_begin(SWM_K_APPLY);
@@ -1239,9 +1281,29 @@ int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr) {
   P.N = ctx->N;
   const WireTile wt = wire_tile<double>(P.R, ctx->nw);
   if (wt.smem > 48 * 1024)
-    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c64, true>, ctx->smem_optin));
-  k_spmv_w<double, c64, true><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
-      P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, Rr, B, wt.RG, wt.WB, wt.ystride);
+    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c64, kResW, false>, ctx->smem_optin));
+  k_spmv_w<double, c64, kResW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
+      P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, nullptr, Rr, B, wt.RG, wt.WB, wt.ystride);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+
+int product_f64(swm_ctx* ctx, int R, const c128* X, c128* Y) {
+  KPtr P{};
+  P.R = R;
+  P.N = ctx->N;
+  const WireTile wt = wire_tile<double>(R, ctx->nw);
+  if (ctx->prec == SWM_C128) {
+    if (wt.smem > 48 * 1024)
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c128, kPlainW, false>, ctx->smem_optin));
+    k_spmv_w<double, c128, kPlainW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
+        P, ctx->off, ctx->offd, ctx->nw, (const c128*)ctx->Zp, X, nullptr, Y, nullptr, wt.RG, wt.WB, wt.ystride);
+  } else {
+    if (wt.smem > 48 * 1024)
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c64, kPlainW, false>, ctx->smem_optin));
+    k_spmv_w<double, c64, kPlainW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
+        P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, X, nullptr, Y, nullptr, wt.RG, wt.WB, wt.ystride);
+  }
   SWM_LAUNCHED();
   return SWM_OK;
 }

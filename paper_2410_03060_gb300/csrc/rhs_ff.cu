@@ -163,11 +163,12 @@ __global__ void __launch_bounds__(kFFThreads) k_far_partial(Geo geo, int64_t nw,
   out[2] = mkc(F[4], F[5]);
 }
 
-// One warp per (incidence, observation) pair: sum the chunk partials, then sigma.  Partial (c, e)
+// One warp per (incidence, observation) pair: sum the chunk partials, then sigma (or, with comp,
+// the received components theta_hat . F and phi_hat . F as two complex numbers).  Partial (c, e)
 // is at partial + (c * cstride + e * estride) * 3.
 __global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict__ partial, int64_t cstride,
                              int64_t estride, int n_obs, const double* __restrict__ obs, int obs_stride, int mono,
-                             double* __restrict__ sigma) {
+                             double* __restrict__ sigma, int comp = 0) {
   const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (e >= npairs) return;
@@ -186,6 +187,13 @@ __global__ void k_far_reduce(int64_t npairs, int nchunks, const c128* __restrict
   obs_frame(obs, obs_stride, o, rh, th, ph);
   const double tr = th[0] * F[0] + th[1] * F[2] + th[2] * F[4], ti = th[0] * F[1] + th[1] * F[3] + th[2] * F[5];
   const double pr = ph[0] * F[0] + ph[1] * F[2] + ph[2] * F[4], pi = ph[0] * F[1] + ph[1] * F[3] + ph[2] * F[5];
+  if (comp) {
+    sigma[4 * e] = tr;
+    sigma[4 * e + 1] = ti;
+    sigma[4 * e + 2] = pr;
+    sigma[4 * e + 3] = pi;
+    return;
+  }
   sigma[2 * e] = (tr * tr + ti * ti) / kFourPi;
   sigma[2 * e + 1] = (pr * pr + pi * pi) / kFourPi;
 }
@@ -524,7 +532,7 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
                      const double* cz, const double* tx, const double* ty, const double* tz, const double* Ls,
                      const int32_t* ns, const int64_t* off, bool soa, double k, int n_rhs, int n_obs,
                      const double* obs, int obs_stride, bool mono, double* sigma, void* scratch, size_t scratch_bytes,
-                     std::string* err) {
+                     std::string* err, bool components) {
   const int64_t npairs = mono ? n_rhs : (int64_t)n_rhs * n_obs;
   int64_t nchunks, chunk;
   ff_shape(nw, npairs, nchunks, chunk);
@@ -562,7 +570,8 @@ int far_field_launch(cudaStream_t st, int64_t* launches, bool cur_c64, bool f64,
     return SWM_ECUDA;
   }
   k_far_reduce<<<(unsigned)ceil_div(npairs * 32, 256), 256, 0, st>>>(npairs, (int)nchunks, part, npairs, 1, n_obs,
-                                                                     obs, obs_stride, mono, sigma);
+                                                                     obs, obs_stride, mono, sigma,
+                                                                     components ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("far field reduce launch: ") + cudaGetErrorString(e);

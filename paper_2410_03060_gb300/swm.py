@@ -69,6 +69,13 @@ _SIGS = {
     "swm_far_field_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P, C.c_int, _P,
                                          _P]),
     "swm_stateless_error": (C.c_char_p, []),
+    "swm_far_components": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P, C.c_int, _P, _P]),
+    "swm_apply": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int]),
+    "swm_precond_apply": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int]),
+    "swm_rhs": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
+    "swm_vec_dots": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, _P, _P, _P]),
+    "swm_vec_axpy": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, _P, _P, _P]),
+    "swm_vec_scale": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, _P]),
     "swm_solve_guess": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _P, C.c_int]),
     "swm_net_num_params": (C.c_int64, []),
     "swm_net_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
@@ -417,10 +424,12 @@ def swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, s
     are refused (the C entry point takes device pointers only)."""
     nw = lengths.shape[0]
     n_rhs, n_obs = currents.shape[0], obs.shape[0]
+    out_conv = (_ptr(sigma_out, np.complex128, (n_rhs, n_obs, 2), "comp_out") if _entry == "swm_far_components"
+                else _ptr(sigma_out, np.float64, (n_rhs, n_obs, 2), "sigma_out"))
     conv = [_ptr(centres, np.float64, (nw, 3), "centres"), _ptr(dirs, np.float64, (nw, 3), "dirs"),
             _ptr(lengths, np.float64, (nw,), "lengths"), _ptr(nseg, np.int32, (nw,), "nseg"),
             _ptr(off, np.int64, (nw + 1,), "off"), _ptr(currents, np.complex128, None, "currents"),
-            _ptr(obs, np.float64, (n_obs, 2), "obs"), _ptr(sigma_out, np.float64, (n_rhs, n_obs, 2), "sigma_out")]
+            _ptr(obs, np.float64, (n_obs, 2), "obs"), out_conv]
     names = ("centres", "dirs", "lengths", "nseg", "off", "currents", "obs", "sigma_out")
     for name, (_, kind, _) in zip(names, conv):
         if kind != SWM_DEVICE:
@@ -435,6 +444,76 @@ def swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, s
     if rc < 0:
         raise SwmError(rc, lib.swm_stateless_error().decode())
     return rc
+
+
+def swm_far_components(stream, centres, dirs, lengths, nseg, off, k, currents, obs, comp_out) -> int:
+    """Received far-field components theta_hat . F and phi_hat . F of the given currents
+    (n_rhs x n_obs x 2 complex128, CUDA tensors throughout, see include/swm.h); they add over
+    disjoint sets of wires."""
+    return swm_far_field(stream, centres, dirs, lengths, nseg, off, k, currents, obs, comp_out,
+                         _entry="swm_far_components")
+
+
+def _dev_c128(x, shape, name):
+    if not _is_torch(x):
+        raise TypeError(f"{name}: need a CUDA tensor")
+    return _ptr(x, np.complex128, shape, name)[0]
+
+
+def swm_apply(ctx: Ctx, x, y) -> int:
+    """y = (I + E) x = Z M^-1 x for every local row (n_rhs x N complex128, caller order)."""
+    n = swm_get_stats(ctx)["n"]
+    R = x.shape[0]
+    px, kx, _ = _ptr(x, np.complex128, (R, n), "x")
+    py, ky, _ = _out_ptr(y, np.complex128, (R, n), "y")
+    return _check(ctx, load().swm_apply(ctx.handle, R, px, kx, py, ky))
+
+
+def swm_precond_apply(ctx: Ctx, y, x) -> int:
+    """x = M^-1 y, the self-block inverses wire by wire (n_rhs x N complex128, caller order)."""
+    n = swm_get_stats(ctx)["n"]
+    R = y.shape[0]
+    py, ky, _ = _ptr(y, np.complex128, (R, n), "y")
+    px, kx, _ = _out_ptr(x, np.complex128, (R, n), "x")
+    return _check(ctx, load().swm_precond_apply(ctx.handle, R, py, ky, px, kx))
+
+
+def swm_rhs(ctx: Ctx, inc, b_out) -> int:
+    """Right-hand sides (Eq. (4)) of the built system for the given incidences, n_inc x N."""
+    inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+    n = swm_get_stats(ctx)["n"]
+    pb, kb, _ = _out_ptr(b_out, np.complex128, (inc.shape[0], n), "b_out")
+    return _check(ctx, load().swm_rhs(ctx.handle, inc.shape[0], inc.ctypes.data_as(C.c_void_p), pb, kb))
+
+
+def swm_vec_dots(ctx: Ctx, Vb, k: int, w) -> np.ndarray:
+    """(k x n_rhs) complex inner products Vb[i][r]^H w[r] for i < k; Vb (>= k, n_rhs, n) and w
+    (n_rhs, n) CUDA complex128 tensors."""
+    R, n = w.shape
+    if Vb.shape[0] < k or tuple(Vb.shape[1:]) != (R, n) or not Vb.is_contiguous():
+        raise ValueError("swm_vec_dots: basis shape")
+    out = np.zeros((k, R), dtype=np.complex128)
+    _check(ctx, load().swm_vec_dots(ctx.handle, n, int(k), R, C.c_void_p(Vb.data_ptr()), _dev_c128(w, (R, n), "w"),
+                                    out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def swm_vec_axpy(ctx: Ctx, Vb, k: int, coef, v) -> int:
+    """v[r] -= sum over i < k of coef[i][r] Vb[i][r] (coef host k x n_rhs complex)."""
+    R, n = v.shape
+    if Vb.shape[0] < k or tuple(Vb.shape[1:]) != (R, n) or not Vb.is_contiguous():
+        raise ValueError("swm_vec_axpy: basis shape")
+    c = np.ascontiguousarray(coef, dtype=np.complex128).reshape(k, R)
+    return _check(ctx, load().swm_vec_axpy(ctx.handle, n, int(k), R, C.c_void_p(Vb.data_ptr()),
+                                           c.ctypes.data_as(C.c_void_p), _dev_c128(v, (R, n), "v")))
+
+
+def swm_vec_scale(ctx: Ctx, a, v, out) -> int:
+    """out[r] = a[r] v[r] (a host float64 per right-hand side)."""
+    R, n = v.shape
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(R)
+    return _check(ctx, load().swm_vec_scale(ctx.handle, n, R, a.ctypes.data_as(C.c_void_p), _dev_c128(v, (R, n), "v"),
+                                            _dev_c128(out, (R, n), "out")))
 
 
 def swm_far_field_noalloc(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out) -> int:
