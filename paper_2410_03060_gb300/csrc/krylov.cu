@@ -240,115 +240,178 @@ __global__ void __launch_bounds__(256) k_spmv_t(KPtr P, const RowInfo* __restric
 // Product with many right-hand sides, wire-tiled: w = u + E u.  A CTA takes WB consecutive wires
 // (block-rows of E) and RG right-hand sides, one thread per (wire, right-hand side): it
 // accumulates all m_p rows of its wire over the wire's K_p columns, so each gathered value of u
-// serves every row of the wire from a register.  The gathers read Xt, u right-hand-side minor
-// ([N][R], XT), where the threads of a wire (consecutive right-hand sides) read consecutive
-// addresses, or, without XT, u itself (right-hand-side major; each thread's gathers are then a
-// short run per block, but the lanes of a warp read R-apart lines).  The entries of E are the same
+// serves every row of the wire from a register, and writes its rows itself (a short run per
+// thread; no shared memory and no barrier, so nothing waits for the slowest wire of the CTA).  The
+// gathers read Xt, u right-hand-side minor ([N][R], XT), where the threads of a wire (consecutive
+// right-hand sides) read consecutive addresses, or, without XT, u itself (right-hand-side major).
+// The column map is loaded one group of four ahead of its gathers.  The entries of E are the same
 // address for every thread of a wire (one transaction per warp).  Rows are taken eight at a time
-// (a wire has at most SWM_MAX_SEG - 1 rows).  The results go through shared memory so that w is
-// written right-hand-side major as one run of the tile's consecutive rows per right-hand side.
+// (a wire has at most SWM_MAX_SEG - 1 rows).
 // MODE kStepW: a GMRES step (active right-hand sides only); kResW: the residual at the start of a
 // cycle, every right-hand side, source Y, result W = B - (y + E y); kPlainW: every right-hand side,
 // W = u + E u (the product on its own, for callers outside GMRES).
-constexpr int kWireMaxRows = SWM_MAX_SEG - 1;
 constexpr int kStepW = 0, kResW = 1, kPlainW = 2;
-template <typename TV, typename TE, int MODE = kStepW, bool XT = false>
-__global__ void __launch_bounds__(256) k_spmv_w(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
-                                                const TE* __restrict__ E, const cplx<TV>* __restrict__ U,
-                                                const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ Wv,
-                                                const cplx<TV>* __restrict__ B, int RG, int WB, int ystride) {
+template <typename TV, typename TE, int MODE = kStepW, bool XT = false, int MINB = sizeof(TV) == 4 ? 4 : 2>
+__global__ void __launch_bounds__(256, MINB) k_spmv_w(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
+                                                   const TE* __restrict__ E, const cplx<TV>* __restrict__ U,
+                                                   const cplx<TV>* __restrict__ Xt, cplx<TV>* __restrict__ Wv,
+                                                   const cplx<TV>* __restrict__ B, int RG, int WB) {
   constexpr bool RES = MODE == kResW, ALL = MODE != kStepW;
   if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
-  extern __shared__ __align__(16) unsigned char sm_w[];
-  cplx<TV>* ys = reinterpret_cast<cplx<TV>*>(sm_w);  // [RG][ystride]
   const int64_t N = P.N;
   const int64_t p0 = (int64_t)blockIdx.x * WB;
-  const int64_t pe = min(p0 + (int64_t)WB, nw);
   const int r0 = blockIdx.y * RG;
-  const int nr = min(RG, P.R - r0);
-  const int64_t n0 = off[p0];
-  const int rows = (int)(off[pe] - n0);
   const int pl = (int)threadIdx.x / RG, rl = (int)threadIdx.x % RG;
   const int64_t p = p0 + pl;
   const int r = r0 + rl;
-  if (pl < WB && p < pe && rl < nr && (ALL || P.active[r])) {
-    const int64_t op = off[p];
-    const int m = (int)(off[p + 1] - op);
-    const int K = lay.K[p];
-    const TE* Ep = E + lay.rowbase[p];
-    const int32_t* cm = lay.colmap + lay.cmbase[p];
-    // gathered value of column c for this right-hand side
-    const cplx<TV>* xs = XT ? Xt + r : U + (int64_t)r * N;
-    const int64_t xstride = XT ? P.R : 1;
-    cplx<TV>* yr = ys + (int64_t)rl * ystride + (op - n0);
-    for (int i0 = 0; i0 < m; i0 += 8) {
-      const int mm = min(8, m - i0);
-      const TE* Ei = Ep + (int64_t)i0 * K;
-      cplx<TV> acc[8];
+  if (pl >= WB || p >= nw || r >= P.R || !(ALL || P.active[r])) return;
+  const int64_t op = off[p];
+  const int m = (int)(off[p + 1] - op);
+  const int K = lay.K[p];
+  const TE* Ep = E + lay.rowbase[p];
+  const int32_t* cm = lay.colmap + lay.cmbase[p];
+  // gathered value of column c for this right-hand side
+  const cplx<TV>* xs = XT ? Xt + r : U + (int64_t)r * N;
+  const int64_t xstride = XT ? P.R : 1;
+  const int64_t orow = (int64_t)r * N + op;
+  for (int i0 = 0; i0 < m; i0 += 8) {
+    const int mm = min(8, m - i0);
+    const TE* Ei = Ep + (int64_t)i0 * K;
+    cplx<TV> acc[8];
 #pragma unroll
-      for (int ii = 0; ii < 8; ++ii) acc[ii] = mkc<TV>(0, 0);
-      int k = 0;
-      for (; k + 3 < K; k += 4) {
-        int32_t c[4];
+    for (int ii = 0; ii < 8; ++ii) acc[ii] = mkc<TV>(0, 0);
+    const int K4 = K & ~3;
+    int32_t c[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = cm[k + u];
-        cplx<TV> x[4];
+    for (int u = 0; u < 4; ++u) c[u] = u < K4 ? cm[u] : 0;
+    for (int k = 0; k < K4; k += 4) {
+      cplx<TV> x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = xs[(int64_t)c[u] * xstride];
+      for (int u = 0; u < 4; ++u) x[u] = xs[(int64_t)c[u] * xstride];
+      // the next group's columns while these gathers are in flight
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii)
-          if (ii < mm) {
-            cplx<TV> e[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = ELoad<TV, TE>::ld(Ei + (int64_t)ii * K + k + u);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) cfma(acc[ii], e[u], x[u]);
-          }
-      }
-      for (; k < K; ++k) {
-        const cplx<TV> x = xs[(int64_t)cm[k] * xstride];
-#pragma unroll
-        for (int ii = 0; ii < 8; ++ii)
-          if (ii < mm) cfma(acc[ii], ELoad<TV, TE>::ld(Ei + (int64_t)ii * K + k), x);
-      }
+      for (int u = 0; u < 4; ++u) c[u] = k + 4 + u < K4 ? cm[k + 4 + u] : 0;
 #pragma unroll
       for (int ii = 0; ii < 8; ++ii)
-        if (ii < mm) yr[i0 + ii] = acc[ii];
+        if (ii < mm) {
+          cplx<TV> e[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) e[u] = ELoad<TV, TE>::ld(Ei + (int64_t)ii * K + k + u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cfma(acc[ii], e[u], x[u]);
+        }
     }
+    for (int k = K4; k < K; ++k) {
+      const cplx<TV> x = xs[(int64_t)cm[k] * xstride];
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii)
+        if (ii < mm) cfma(acc[ii], ELoad<TV, TE>::ld(Ei + (int64_t)ii * K + k), x);
+    }
+#pragma unroll
+    for (int ii = 0; ii < 8; ++ii)
+      if (ii < mm) {
+        const int64_t o = orow + i0 + ii;
+        const cplx<TV> v = U[o] + acc[ii];
+        Wv[o] = RES ? B[o] - v : v;
+      }
   }
-  __syncthreads();
-  // write: warp w takes right-hand sides w, w + nwarps, ...; its lanes take the tile's rows
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwp = blockDim.x >> 5;
-  for (int b = w; b < nr; b += nwp) {
-    const int rr = r0 + b;
-    if (!ALL && !P.active[rr]) continue;
-    const cplx<TV>* yb = ys + (int64_t)b * ystride;
-    for (int t = lane; t < rows; t += 32) {
-      const int64_t o = (int64_t)rr * N + n0 + t;
-      const cplx<TV> v = U[o] + yb[t];
-      Wv[o] = RES ? B[o] - v : v;
+}
+
+// The same product with the gathers of u staged asynchronously: each thread copies the values it
+// needs for a chunk of kWCh columns from Xt (right-hand-side minor) into its own shared-memory slots
+// with cp.async (no registers held while the copies are in flight), one chunk ahead of the chunk it
+// multiplies, so about 2 kWCh gathers per thread are in flight instead of four.  A thread reads
+// only the slots it wrote itself, so no barrier is needed: waiting for its own copy groups suffices.
+constexpr int kWCh = 8;
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+template <typename TE, int MODE = kStepW>
+__global__ void __launch_bounds__(256, 4) k_spmv_wa(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
+                                                    const TE* __restrict__ E, const c64* __restrict__ U,
+                                                    const c64* __restrict__ Xt, c64* __restrict__ Wv,
+                                                    const c64* __restrict__ B, int RG, int WB) {
+  constexpr bool RES = MODE == kResW, ALL = MODE != kStepW;
+  if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+  __shared__ c64 xs_sm[2][kWCh][256];
+  const int64_t N = P.N;
+  const int64_t p0 = (int64_t)blockIdx.x * WB;
+  const int r0 = blockIdx.y * RG;
+  const int tid = threadIdx.x;
+  const int pl = tid / RG, rl = tid % RG;
+  const int64_t p = p0 + pl;
+  const int r = r0 + rl;
+  if (pl >= WB || p >= nw || r >= P.R || !(ALL || P.active[r])) return;
+  const int64_t op = off[p];
+  const int m = (int)(off[p + 1] - op);
+  const int K = lay.K[p];
+  const TE* Ep = E + lay.rowbase[p];
+  const int32_t* cm = lay.colmap + lay.cmbase[p];
+  const c64* xs = Xt + r;
+  const int64_t R = P.R;
+  const int64_t orow = (int64_t)r * N + op;
+  const int nch = (K + kWCh - 1) / kWCh;
+  auto issue = [&](int ch) {
+    const int k0 = ch * kWCh;
+#pragma unroll
+    for (int u = 0; u < kWCh; ++u)
+      if (k0 + u < K) cp_async8(&xs_sm[ch & 1][u][tid], xs + (int64_t)cm[k0 + u] * R);
+    cp_async_commit();
+  };
+  for (int i0 = 0; i0 < m; i0 += 8) {
+    const int mm = min(8, m - i0);
+    const TE* Ei = Ep + (int64_t)i0 * K;
+    c64 acc[8];
+#pragma unroll
+    for (int ii = 0; ii < 8; ++ii) acc[ii] = mkc<float>(0, 0);
+    if (nch > 0) issue(0);
+    for (int ch = 0; ch < nch; ++ch) {
+      if (ch + 1 < nch) {
+        issue(ch + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      const int k0 = ch * kWCh;
+      const int kn = min(kWCh, K - k0);
+#pragma unroll
+      for (int u = 0; u < kWCh; ++u) {
+        if (u >= kn) break;
+        const c64 x = xs_sm[ch & 1][u][tid];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii)
+          if (ii < mm) cfma(acc[ii], ELoad<float, TE>::ld(Ei + (int64_t)ii * K + k0 + u), x);
+      }
     }
+#pragma unroll
+    for (int ii = 0; ii < 8; ++ii)
+      if (ii < mm) {
+        const int64_t o = orow + i0 + ii;
+        const c64 v = U[o] + acc[ii];
+        Wv[o] = RES ? B[o] - v : v;
+      }
   }
 }
 
 // Tile shape of k_spmv_w for R right-hand sides: RG right-hand sides per CTA (all of them up to
-// 64, else balanced groups of at most 64), WB = 256 / RG wires per CTA, and the odd row stride of
-// its shared-memory results.
+// 64, else balanced groups of at most 64) and WB = 256 / RG wires per CTA.
 struct WireTile {
-  int RG, WB, ystride;
+  int RG, WB;
   unsigned gx, gy;
-  size_t smem;
 };
-template <typename TV>
-WireTile wire_tile(int R, int64_t nw) {
+inline WireTile wire_tile(int R, int64_t nw) {
   WireTile t{};
   const int groups = (int)ceil_div(R, 64);
   t.RG = (int)ceil_div(R, groups);
   t.WB = std::max(1, 256 / t.RG);
-  t.ystride = (t.WB * kWireMaxRows) | 1;
   t.gx = (unsigned)ceil_div(nw, t.WB);
   t.gy = (unsigned)ceil_div(R, t.RG);
-  t.smem = sizeof(cplx<TV>) * (size_t)t.RG * t.ystride;
   return t;
 }
 
@@ -510,9 +573,9 @@ __device__ void dots_tail(const KPtr& P, int j, int r, bool closing) {
 // and w are staged in shared memory; the warps take (i, row slice) items, q_j standing for u itself,
 // with the rows split into S slices while j + 1 < 8 so that every warp streams, and eight loads in
 // flight per lane.  Slice sums are added in a fixed order (results do not depend on timing).
-template <typename TV>
+template <typename TV, typename TQ = cplx<TV>>
 __global__ void __launch_bounds__(kRows) k_dots(KPtr P, const cplx<TV>* __restrict__ U,
-                                                const cplx<TV>* __restrict__ Wv, const cplx<TV>* __restrict__ V) {
+                                                const cplx<TV>* __restrict__ Wv, const TQ* __restrict__ V) {
   if (P.st->cycle_done) return;
   const int j = P.st->j, r = blockIdx.y;
   const bool closing = j >= P.st->jmax;
@@ -541,13 +604,23 @@ __global__ void __launch_bounds__(kRows) k_dots(KPtr P, const cplx<TV>* __restri
   for (int item = wp; item < (j + 1) * S; item += kWarps) {
     const int i = item / S, sl = item % S;
     const int lo = sl * len, hi = min(cnt, lo + len);
-    const cplx<TV>* vi = i < j ? V + ((int64_t)i * P.R + r) * P.N + n0 : u_sm;
+    // q_i from the basis, or (i == j) the pending vector u itself from shared memory; a basis in
+    // the vector type is read through one pointer, a half-precision one converted on load
+    constexpr bool full = std::is_same<TQ, cplx<TV>>::value;
+    const TQ* vq = V + ((int64_t)i * P.R + r) * P.N + n0;  // i <= j <= restart: inside the basis
+    const cplx<TV>* vi = full ? (i < j ? reinterpret_cast<const cplx<TV>*>(vq) : u_sm) : u_sm;
+    const bool own = i >= j;
+    const float qsi = P.qsi;
+    auto ldv = [&](int t) -> cplx<TV> {
+      if constexpr (full) return vi[t];
+      else return own ? u_sm[t] : QStore<TV, TQ>::ld(vq + t, qsi);
+    };
     cplx<TV> a = mkc<TV>(0, 0), b = mkc<TV>(0, 0);
     int t = lo + lane;
     for (; t + 224 < hi; t += 256) {
       cplx<TV> v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = vi[t + 32 * k];
+      for (int k = 0; k < 8; ++k) v[k] = ldv(t + 32 * k);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const cplx<TV> x = u_sm[t + 32 * k];
@@ -561,7 +634,7 @@ __global__ void __launch_bounds__(kRows) k_dots(KPtr P, const cplx<TV>* __restri
       }
     }
     for (; t < hi; t += 32) {
-      const cplx<TV> v = vi[t], x = u_sm[t];
+      const cplx<TV> v = ldv(t), x = u_sm[t];
       a.re = fma(v.re, x.re, fma(v.im, x.im, a.re));
       a.im = fma(v.re, x.im, fma(-v.im, x.re, a.im));
       if (!closing) {
@@ -593,9 +666,9 @@ __global__ void __launch_bounds__(kRows) k_dots(KPtr P, const cplx<TV>* __restri
 // Update of step j (after its dots): q_j = (u - Q s) / rho goes to V_j and the next pending vector
 // u' = (w - Q t) / rho - gamma q_j (the first Gram-Schmidt pass of A q_j) replaces u, in one read of
 // Q_{<j}; one thread per row.
-template <typename TV>
+template <typename TV, typename TQ = cplx<TV>>
 __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__ U, const cplx<TV>* __restrict__ Wv,
-                                                  cplx<TV>* __restrict__ V) {
+                                                  TQ* __restrict__ V) {
   if (P.st->cycle_done) return;
   const int j = P.st->j - 1, r = blockIdx.y;
   if (!P.active[r]) return;
@@ -613,7 +686,8 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
   const int cnt = (int)min((int64_t)P.uchunk, N - n0);
   cplx<TV>* u = U + (int64_t)r * N + n0;
   const cplx<TV>* w = Wv + (int64_t)r * N + n0;
-  cplx<TV>* vj = V + ((int64_t)j * P.R + r) * N + n0;
+  TQ* vj = V + ((int64_t)j * P.R + r) * N + n0;
+  const float qs = P.qs, qsi = P.qsi;
   // four rows per thread (kRows apart, so every load is coalesced) and two basis vectors per
   // pass: eight independent loads in flight per thread
   constexpr int kQ = 4;
@@ -625,13 +699,14 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
       x[q] = t < cnt ? u[t] : mkc<TV>(0, 0);
       y[q] = t < cnt ? w[t] : mkc<TV>(0, 0);
     }
-    const cplx<TV>* vb = V + (int64_t)r * N + n0 + t0;
+    const TQ* vb = V + (int64_t)r * N + n0 + t0;
 #pragma unroll 2
     for (int i = 0; i < j; ++i) {
-      const cplx<TV>* vi = vb + (int64_t)i * P.R * N;
+      const TQ* vi = vb + (int64_t)i * P.R * N;
       cplx<TV> v[kQ];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) v[q] = t0 + q * kRows < cnt ? vi[q * kRows] : mkc<TV>(0, 0);
+      for (int q = 0; q < kQ; ++q)
+        v[q] = t0 + q * kRows < cnt ? QStore<TV, TQ>::ld(vi + q * kRows, qsi) : mkc<TV>(0, 0);
       const cplx<TV> a = ss[i], b = ts[i];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
@@ -646,7 +721,7 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
       const int t = t0 + q * kRows;
       if (t < cnt) {
         const cplx<TV> qv = ih * x[q];
-        vj[t] = qv;
+        QStore<TV, TQ>::st(vj + t, qv, qs);
         u[t] = ih * y[q] - qv * gm;
       }
     }
@@ -751,8 +826,8 @@ __global__ void __launch_bounds__(kRows) k_backsolve(KPtr P, int smem_tri) {
 
 // Y += V coef, in the precision of the vectors (float64 arithmetic issues far slower than float32
 // on GB300, and the complex64 path stores y in complex64 anyway).
-template <typename TV>
-__global__ void __launch_bounds__(256) k_update_y(KPtr P, const cplx<TV>* __restrict__ V, cplx<TV>* __restrict__ Y) {
+template <typename TV, typename TQ = cplx<TV>>
+__global__ void __launch_bounds__(256) k_update_y(KPtr P, const TQ* __restrict__ V, cplx<TV>* __restrict__ Y) {
   const int r = blockIdx.y;
   const int jl = P.jlast[r];
   if (jl == 0) return;
@@ -763,7 +838,7 @@ __global__ void __launch_bounds__(256) k_update_y(KPtr P, const cplx<TV>* __rest
   if (n >= P.N) return;
   cplx<TV> acc = mkc<TV>(0, 0);
 #pragma unroll 4
-  for (int i = 0; i < jl; ++i) cfma(acc, V[((int64_t)i * P.R + r) * P.N + n], cf[i]);
+  for (int i = 0; i < jl; ++i) cfma(acc, QStore<TV, TQ>::ld(V + ((int64_t)i * P.R + r) * P.N + n, P.qsi), cf[i]);
   Y[(int64_t)r * P.N + n] = Y[(int64_t)r * P.N + n] + acc;
 }
 
@@ -798,8 +873,9 @@ __global__ void k_rowwire(int64_t nw, const int64_t* __restrict__ off, Layout la
 
 // Restarted GMRES on A = I + E with E stored as TE.  With y_out the result stays in y-space
 // (*y_out = the workspace's y, no M^-1 and no statistics); otherwise x = M^-1 y goes to ctx->Xv.
-template <typename TV, typename TE>
+template <typename TV, typename TE, typename TQ = cplx<TV>>
 int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter, void** y_out, KState* hs_out) {
+  constexpr bool kFullBasis = std::is_same<TQ, cplx<TV>>::value;
   cudaStream_t st = ctx->stream;
   const int R = ctx->n_rhs;
   const int64_t N = ctx->N;
@@ -812,6 +888,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   P.N = N;
   P.tol = tol;
   P.max_iter = max_iter;
+  P.qs = kFullBasis ? 1.f : (float)std::sqrt((double)std::max<int64_t>(1, N));
+  P.qsi = 1.f / P.qs;
   // rows per CTA of the Gram-Schmidt kernels, at least kRows and at most kMaxChunk (the dots stage
   // a chunk of u and w in shared memory): the update about 16 CTAs per SM over all right-hand
   // sides; the dots about 4, so that the last CTA of each right-hand side adds fewer partial sums
@@ -826,14 +904,15 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   struct Workspace {
     int64_t key[4];
     KPtr P;
-    cplx<TV> *Y, *W0, *W1, *V;
+    cplx<TV> *Y, *W0, *W1;
+    TQ* V;                // the basis, in the vector type or half precision
     cplx<TV>* Xt;         // many right-hand sides: the pending vectors right-hand-side minor, [N][R]
     PSync* sync;          // persistent solve: barrier state and partial sums over its CTAs
     c128 *pp1, *pp2;
     double* ppn;
     bool sync_clean;      // the barrier state is zero
   };
-  const int64_t key[4] = {R, N, restart, (int64_t)sizeof(TV)};
+  const int64_t key[4] = {R, N, restart, (int64_t)(sizeof(TV) + 64 * sizeof(TQ))};
   Workspace* ws = reinterpret_cast<Workspace*>(ctx->kry_ws);
   if (!ws || std::memcmp(ws->key, key, sizeof(key)) != 0 || ctx->kry_ws_bytes != sizeof(Workspace)) {
     dfree_group(ctx, ctx->kry_bufs);
@@ -867,7 +946,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     SWM_TRY(dalloc(ctx, K, (void**)&ws->Y, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W0, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W1, sizeof(cplx<TV>) * R * N));
-    SWM_TRY(dalloc(ctx, K, (void**)&ws->V, sizeof(cplx<TV>) * (size_t)R1 * R * N));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->V, sizeof(TQ) * (size_t)R1 * R * N));
     if (R >= kMinorR) SWM_TRY(dalloc(ctx, K, (void**)&ws->Xt, sizeof(cplx<TV>) * (size_t)R * N));
     if (R <= kPersistMaxR && ctx->nsm > 0) {
       SWM_TRY(dalloc(ctx, K, (void**)&ws->sync, sizeof(PSync)));
@@ -883,7 +962,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     P.tol = tol_now;
     P.max_iter = max_iter_now;
   }
-  cplx<TV> *Y = ws->Y, *W0 = ws->W0, *W1 = ws->W1, *V = ws->V;
+  cplx<TV> *Y = ws->Y, *W0 = ws->W0, *W1 = ws->W1;
+  TQ* V = ws->V;
   // per-kernel path: W0 holds the pending vector u, W1 the product w = A u
   cplx<TV> *U = W0, *Wv = W1;
   // with an initial guess y0 = M x0 is copied in and, the tolerance staying relative to |b|, |b|
@@ -904,7 +984,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   {
     PBuffers pb{ws->sync, ws->pp1, ws->pp2, ws->ppn, E, Bv, Y, W0, V, given_b ? 1 : 0, given_b ? 0 : 1,
                 &ws->sync_clean, y_out ? nullptr : ctx->Xv, y_out ? nullptr : ctx->rhs_frames};
-    SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
+    // the persistent solve keeps its basis in the vector type
+    if (kFullBasis) SWM_TRY((gmres_persistent<TV, TE>(ctx, P, pb, max_iter, &hs, &persisted)));
   }
   if (!persisted && !y_out && ctx->rhs_frames) SWM_TRY(compute_rhs(ctx, R, ctx->rhs_frames));
   if (!y_out) ctx->rhs_frames = nullptr;
@@ -922,13 +1003,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   constexpr int kMinor = 32;
   constexpr int kWire = 64;  // k_spmv_w: wire-tiled, right-hand-side major, no transposed copy
   int rb = multi ? 8 : 1;
-  const WireTile wt = wire_tile<TV>(R, ctx->nw);
-  if (multi && wt.smem > 48 * 1024) {
-    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kStepW, false>, ctx->smem_optin));
-    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kResW, false>, ctx->smem_optin));
-    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kStepW, true>, ctx->smem_optin));
-    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<TV, TE, kResW, true>, ctx->smem_optin));
-  }
+  const WireTile wt = wire_tile(R, ctx->nw);
   // res: the residual U = B - A Y of a cycle's start in the same form (every right-hand side)
   auto product = [&](cudaStream_t s, int b, auto res_tag) -> int {
     constexpr bool RS = decltype(res_tag)::value;
@@ -951,17 +1026,43 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
                                                                                        ws->Xt, dst, Bv);
         break;
       }
+      case kWire + 2:  // gathers staged by cp.async (complex64 vectors, incidence-minor copy)
+        if constexpr (std::is_same<TV, float>::value) {
+          if (ws->Xt) {
+            k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, src,
+                                                                                                          ws->Xt);
+            SWM_LAUNCHED();
+            k_spmv_wa<TE, RS ? kResW : kStepW><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+                P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, dst, Bv, wt.RG, wt.WB);
+            break;
+          }
+        }
+        k_spmv_w<TV, TE, RS ? kResW : kStepW, false><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+            P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB);
+        break;
+      case kWire + 1:  // the same with five CTAs per SM (fewer registers)
+        if (ws->Xt) {
+          k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, src,
+                                                                                                        ws->Xt);
+          SWM_LAUNCHED();
+          k_spmv_w<TV, TE, RS ? kResW : kStepW, true, 5><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, dst, Bv, wt.RG, wt.WB);
+        } else {
+          k_spmv_w<TV, TE, RS ? kResW : kStepW, false, 5><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB);
+        }
+        break;
       case kWire:
         if (ws->Xt) {
           // the gathers read u right-hand-side minor: transposed first
           k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, src,
                                                                                                         ws->Xt);
           SWM_LAUNCHED();
-          k_spmv_w<TV, TE, RS ? kResW : kStepW, true><<<dim3(wt.gx, wt.gy), 256, wt.smem, s>>>(
-              P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, dst, Bv, wt.RG, wt.WB, wt.ystride);
+          k_spmv_w<TV, TE, RS ? kResW : kStepW, true><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, dst, Bv, wt.RG, wt.WB);
         } else {
-          k_spmv_w<TV, TE, RS ? kResW : kStepW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, s>>>(
-              P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB, wt.ystride);
+          k_spmv_w<TV, TE, RS ? kResW : kStepW, false><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB);
         }
         break;
       default: k_spmv<TV, TE, 8, RS><<<gsp, kRows, 0, s>>>(P, ri, ctx->offd.colmap, E, src, dst, Bv); break;
@@ -972,7 +1073,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   auto launch_product = [&](cudaStream_t s, int b) { return product(s, b, std::false_type{}); };
   auto launch_residual = [&](cudaStream_t s, int b) { return product(s, b, std::true_type{}); };
   const size_t dots_smem = 2 * sizeof(cplx<TV>) * (size_t)P.chunk;
-  if (dots_smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_dots<TV>, ctx->smem_optin));
+  if (dots_smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_dots<TV, TQ>, ctx->smem_optin));
   // back substitution stages the triangle in shared memory when it fits
   size_t bs_smem = sizeof(c128) * (size_t)restart * restart;
   if (bs_smem > 160 * 1024) bs_smem = 0;
@@ -989,11 +1090,11 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       SWM_TRY(launch_product(s, rb));
       ctx->prof_end(SWM_K_APPLY);
       ctx->prof_begin(SWM_K_DOTS);
-      k_dots<TV><<<g_chunk, kRows, dots_smem, s>>>(P, U, Wv, V);
+      k_dots<TV, TQ><<<g_chunk, kRows, dots_smem, s>>>(P, U, Wv, V);
       ctx->prof_end(SWM_K_DOTS);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_UPDATE);
-      k_update<TV><<<g_uchunk, kRows, 0, s>>>(P, U, Wv, V);
+      k_update<TV, TQ><<<g_uchunk, kRows, 0, s>>>(P, U, Wv, V);
       ctx->prof_end(SWM_K_UPDATE);
       SWM_LAUNCHED();
     }
@@ -1005,7 +1106,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     for (const auto& t : ctx->tuned)
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
     const int forced = ctx->product_form;
-    if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || (forced == kMinor && ws->Xt)) {
+    if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || forced == kWire + 1 ||
+        forced == kWire + 2 || (forced == kMinor && ws->Xt)) {
       rb = forced;
     } else if (found) {
       rb = found;
@@ -1060,7 +1162,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     key.lay = ctx->offd;
     key.gx = g_chunk.x;
     key.gy = g_chunk.y;
-    key.bits = (unsigned)(sizeof(TV) * 64 + sizeof(TE) + 4096 * rb);
+    key.bits = (unsigned)(sizeof(TV) * 64 + sizeof(TE) + 4096 * rb + (kFullBasis ? 0 : 1u << 24));
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
     std::vector<unsigned char> kv(kb, kb + sizeof(key));
     if (!ctx->gm_exec || kv != ctx->gm_key) {
@@ -1083,7 +1185,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       ctx->gm_key = kv;
     }
   }
-  const int launches_per_step = (rb == kMinor || (rb == kWire && ws->Xt) ? 2 : 1) + 2;
+  const int launches_per_step = (rb == kMinor || (rb >= kWire && ws->Xt) ? 2 : 1) + 2;
   while (!persisted) {
     // residual of the current y and the start of a cycle
     ctx->prof_begin(SWM_K_APPLY);
@@ -1118,7 +1220,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     }
     k_backsolve<<<(unsigned)R, kRows, bs_smem, st>>>(P, bs_smem > 0 ? 1 : 0);
     SWM_LAUNCHED();
-    k_update_y<TV><<<dim3((unsigned)ceil_div(N, 256), R), 256, 0, st>>>(P, V, Y);
+    k_update_y<TV, TQ><<<dim3((unsigned)ceil_div(N, 256), R), 256, 0, st>>>(P, V, Y);
     SWM_LAUNCHED();
     ++cycles;
   }
@@ -1279,11 +1381,9 @@ int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr) {
   KPtr P{};
   P.R = ctx->n_rhs;
   P.N = ctx->N;
-  const WireTile wt = wire_tile<double>(P.R, ctx->nw);
-  if (wt.smem > 48 * 1024)
-    SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c64, kResW, false>, ctx->smem_optin));
-  k_spmv_w<double, c64, kResW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
-      P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, nullptr, Rr, B, wt.RG, wt.WB, wt.ystride);
+  const WireTile wt = wire_tile(P.R, ctx->nw);
+  k_spmv_w<double, c64, kResW, false><<<dim3(wt.gx, wt.gy), 256, 0, ctx->stream>>>(
+      P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, nullptr, Rr, B, wt.RG, wt.WB);
   SWM_LAUNCHED();
   return SWM_OK;
 }
@@ -1292,26 +1392,22 @@ int product_f64(swm_ctx* ctx, int R, const c128* X, c128* Y) {
   KPtr P{};
   P.R = R;
   P.N = ctx->N;
-  const WireTile wt = wire_tile<double>(R, ctx->nw);
-  if (ctx->prec == SWM_C128) {
-    if (wt.smem > 48 * 1024)
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c128, kPlainW, false>, ctx->smem_optin));
-    k_spmv_w<double, c128, kPlainW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
-        P, ctx->off, ctx->offd, ctx->nw, (const c128*)ctx->Zp, X, nullptr, Y, nullptr, wt.RG, wt.WB, wt.ystride);
-  } else {
-    if (wt.smem > 48 * 1024)
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_w<double, c64, kPlainW, false>, ctx->smem_optin));
-    k_spmv_w<double, c64, kPlainW, false><<<dim3(wt.gx, wt.gy), 256, wt.smem, ctx->stream>>>(
-        P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, X, nullptr, Y, nullptr, wt.RG, wt.WB, wt.ystride);
-  }
+  const WireTile wt = wire_tile(R, ctx->nw);
+  if (ctx->prec == SWM_C128)
+    k_spmv_w<double, c128, kPlainW, false><<<dim3(wt.gx, wt.gy), 256, 0, ctx->stream>>>(
+        P, ctx->off, ctx->offd, ctx->nw, (const c128*)ctx->Zp, X, nullptr, Y, nullptr, wt.RG, wt.WB);
+  else
+    k_spmv_w<double, c64, kPlainW, false><<<dim3(wt.gx, wt.gy), 256, 0, ctx->stream>>>(
+        P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, X, nullptr, Y, nullptr, wt.RG, wt.WB);
   SWM_LAUNCHED();
   return SWM_OK;
 }
 
 int gmres_inner_bf16(swm_ctx* ctx, double tol, int restart, int max_iter, void** y_out, int* iters) {
   KState hs{};
-  const int rc = gmres_impl<float, __nv_bfloat162>(ctx, (const __nv_bfloat162*)ctx->E16, tol, restart, max_iter,
-                                                   y_out, &hs);
+  // the inner solve only needs a few digits: its basis is stored in half precision
+  const int rc = gmres_impl<float, __nv_bfloat162, __half2>(ctx, (const __nv_bfloat162*)ctx->E16, tol, restart,
+                                                            max_iter, y_out, &hs);
   *iters = hs.iters;
   return rc;
 }

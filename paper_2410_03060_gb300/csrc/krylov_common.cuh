@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "ctx.h"
@@ -45,6 +46,28 @@ struct KPtr {
   int max_iter;
   int64_t N;
   double tol;
+  float qs, qsi;  // scale of a basis stored in half precision (sqrt(N)) and its inverse, else 1
+};
+
+// Storage of the Krylov basis: in the vector type, or as complex half (one __half2 per entry,
+// 4 bytes) scaled by qs = sqrt(N), so that the entries of a unit vector are of order one and stay
+// in the normal range of half precision.
+template <typename TV, typename TQ>
+struct QStore;
+template <typename TV>
+struct QStore<TV, cplx<TV>> {
+  static __device__ __forceinline__ cplx<TV> ld(const cplx<TV>* p, float) { return *p; }
+  static __device__ __forceinline__ void st(cplx<TV>* p, cplx<TV> v, float) { *p = v; }
+};
+template <>
+struct QStore<float, __half2> {
+  static __device__ __forceinline__ cplx<float> ld(const __half2* p, float inv) {
+    const float2 f = __half22float2(*p);
+    return mkc<float>(f.x * inv, f.y * inv);
+  }
+  static __device__ __forceinline__ void st(__half2* p, cplx<float> v, float s) {
+    *p = __floats2half2_rn(v.re * s, v.im * s);
+  }
 };
 
 // Entry of E as the vector type: complex128 / complex64 storage as is, complex64 storage widened to
