@@ -599,7 +599,11 @@ def run_scale(args):
 
     w = SCALE[args.workload]
     torch.cuda.set_device(0)
-    cl = w["cloud"](nw=args.nw) if args.nw else w["cloud"]()
+    if args.nw and args.workload == "learned" and args.same_density:
+        # a smaller cloud with the full cloud's wire density (cluster sigma scaled with nw^(1/3))
+        cl = cloud_learned(nw=args.nw, sigma=40.0 * (args.nw / 1e6) ** (1.0 / 3.0))
+    else:
+        cl = w["cloud"](nw=args.nw) if args.nw else w["cloud"]()
     n_inc = args.inc or w["n_inc"]
     inc = incidences_monostatic(n_inc)
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
@@ -901,6 +905,53 @@ def run_batch(args):
         swm.swm_destroy(c)
 
 
+def run_block(args):
+    """Block GMRES against independent GMRES on batching snapshots: per snapshot, the library's
+    swm_solve (independent GMRES per incidence, the incidences sharing every read of E) and the
+    block GMRES of paper_2410_03060_gb300.dist (one Krylov space per group of up to --block-size
+    incidences, its vector algebra in the library's kernels, its small dense algebra on the host),
+    both complex128 to 1e-6.  Prints a JSON line of kind "block_gmres" (a measurement record)."""
+    import torch
+
+    from paper_2410_03060_gb300 import dist, swm
+
+    torch.cuda.set_device(0)
+    n_inc = args.inc or 181
+    inc = incidences_monostatic(n_inc)
+    rows = []
+    for i in range(args.snapshots):
+        cl = cloud_batching_snapshot(i)
+        ctx = swm.swm_create(0)
+        swm.swm_set_cloud(ctx, cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)
+        swm.swm_build(ctx, K0, R_C, swm.SWM_C128)
+        swm.swm_solve(ctx, inc, TOL, args.restart, 2000)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        swm.swm_solve(ctx, inc, TOL, args.restart, 2000)
+        torch.cuda.synchronize()
+        t_ind = time.perf_counter() - t
+        it_ind = swm.swm_get_stats(ctx)["iterations"]
+        owner = np.zeros(cl.nw, dtype=np.int64)
+        plan = dist.Plan(cl.centres, cl.nseg, owner, 0, R_C)
+        its, t_blk = [], 0.0
+        for g0 in range(0, n_inc, args.block_size):
+            sub = inc[g0:g0 + args.block_size]
+            ops = dist.SwmOps(ctx, plan, sub.shape[0])
+            b = dist.gather_rhs_own(ops, sub)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            y, it, rel = dist.dist_block_gmres(ops, dist.LocalComm(), plan, b, TOL, args.block_restart, 2000)
+            torch.cuda.synchronize()
+            t_blk += time.perf_counter() - t
+            its.append(int(it))
+        swm.swm_destroy(ctx)
+        rows.append({"snapshot": i, "nw": cl.nw, "unknowns": cl.n_unknowns, "independent_iterations": it_ind,
+                     "independent_ms": 1e3 * t_ind, "block_iterations": its, "block_ms": 1e3 * t_blk})
+    print(json.dumps({"kind": "block_gmres", "incidences": n_inc, "block_size": args.block_size,
+                      "block_restart": args.block_restart, "restart": args.restart, "tol": TOL, "precision": "c128",
+                      "snapshots": rows}))
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle (the paper has no code) on the host cores, on a bounded
@@ -941,9 +992,15 @@ def main():
     ap.add_argument("--inc", type=int, default=0, help="incidences of a larger workload (default: its own)")
     ap.add_argument("--restart", type=int, default=RESTART)
     ap.add_argument("--nw", type=int, default=0, help="wire count of a larger workload (default: its own)")
+    ap.add_argument("--same-density", action="store_true",
+                    help="with --nw on the learned workload: scale the cluster width to keep the wire density")
     ap.add_argument("--batch", action="store_true",
                     help="the 64-snapshot batching workload, snapshots spread over --streams contexts")
     ap.add_argument("--snapshots", type=int, default=64)
+    ap.add_argument("--block", action="store_true",
+                    help="with --batch: block GMRES against independent GMRES on the first --snapshots snapshots")
+    ap.add_argument("--block-size", type=int, default=32)
+    ap.add_argument("--block-restart", type=int, default=10)
     ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--warm-start", action="store_true",
                     help="mid workload with and without the learned warm start (trains the network first)")
@@ -960,6 +1017,9 @@ def main():
             run_compare(args)
         else:
             run_scale(args)
+        return
+    if args.batch and args.block and args.impl == "ours":
+        run_block(args)
         return
     if args.batch and args.impl == "ours":
         run_batch(args)

@@ -117,9 +117,10 @@ typedef struct swm_stats {
                               r_c, e.g. a frequency sweep) and only refilled the values */
   int step_rhs_block;      /* form of the last solve's per-kernel GMRES product: incidences
                               sharing each read of the blocks (1, 4, 8 or 16), 32 for the
-                              incidence-minor form, 64 for the wire-tiled form (a CTA per group
-                              of wires, every incidence sharing its reads of E); as timed on the
-                              system the first time a shape was solved on this context */
+                              incidence-minor form, 64, 65 or 67 for the wire-tiled forms (a CTA
+                              per group of wires, every incidence sharing its reads of E); as
+                              timed on the system the first time a shape was solved on this
+                              context */
   int64_t nminv;           /* stored entries of the self-block inverses (sum over wires of m_p^2) */
 } swm_stats;
 
@@ -151,7 +152,8 @@ typedef struct swm_stats {
  * SWM_PERSIST_CTAS (default 0 = one per SM) -- CTAs of the persistent solve, at most one per SM;
  * SWM_PRODUCT_FORM (default 0 = timed choice) -- with several incidences, the per-kernel GMRES
  * product form to use instead of timing them: 4, 8 or 16 incidences per read of E, 32 the
- * incidence-minor form (12 or more incidences), 64 the wire-tiled form;
+ * incidence-minor form (12 or more incidences), 64 the wire-tiled form (65: the same with five
+ * CTAs per SM; 67: two incidences per thread and the tile's E in shared memory);
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the
  * persistent solve wait for n arrivals that never come, so each wait runs out (after 1 s) and the
  * solve returns SWM_ETIMEOUT; all read when the context is created. */
@@ -376,6 +378,15 @@ int swm_rhs(swm_ctx* ctx, int n_inc, const double* inc, double* b_out, int out_k
 int swm_vec_dots(swm_ctx* ctx, int64_t n, int k, int n_rhs, const double* Q, const double* v, double* out);
 int swm_vec_axpy(swm_ctx* ctx, int64_t n, int k, int n_rhs, const double* Q, const double* coef, double* v);
 int swm_vec_scale(swm_ctx* ctx, int64_t n, int n_rhs, const double* a, const double* v, double* out);
+
+/* Block forms of the same algebra, for block GMRES (one Krylov space shared by S right-hand
+ * sides): Q is K vectors of length n (contiguous, vector a at Q + 2 a n doubles), W is S vectors.
+ * swm_vec_gram: out[a][b] = sum_n conj(Q[a][n]) W[b][n], K x S complex128 to host memory (partial
+ *   sums over chunks of 2048 rows added in a fixed order, float64 throughout).
+ * swm_vec_gemm: W[b] -= sum over a < K of Q[a] C[a][b], C K x S complex128 (host).
+ * Device memory only (SWM_EINVAL otherwise). */
+int swm_vec_gram(swm_ctx* ctx, int64_t n, int K, int S, const double* Q, const double* W, double* out);
+int swm_vec_gemm(swm_ctx* ctx, int64_t n, int K, int S, const double* Q, const double* C, double* W);
 
 /* Message of the last failed stateless call on this host thread ("" if none). */
 const char* swm_stateless_error(void);

@@ -161,7 +161,7 @@ struct swm_ctx {
   // arrivals more than there are CTAs, so every wait runs out and the solve reports SWM_ETIMEOUT
   int test_barrier_extra = 0;
   int product_form = 0;                   // many right-hand sides: 0 = timed choice, else that form
-                                          // (4, 8, 16, 32 incidence-minor, 64 wire-tiled)
+                                          // (4, 8, 16, 32 incidence-minor, 64, 65, 67 wire-tiled)
   int persist_ctas = 0;                   // CTAs of the persistent solve (0: one per SM)
   int nsm = 0;
   int coop = 0;
@@ -334,8 +334,9 @@ int gcr_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
 // krylov.cu: GMRES on the bfloat16 copy of E (inner solve of the refinement); y-space result
 int gmres_inner_bf16(swm_ctx* ctx, double tol, int restart, int max_iter, void** y_out, int* iters);
 // Rr = B - (Y + E Y) for every right-hand side in float64 vectors with the complex64 E, one read of
-// E shared by all right-hand sides (wire-tiled product, krylov.cu)
-int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr);
+// E shared by all right-hand sides (wire-tiled product, krylov.cu); with Yt (R x N scratch) the
+// gathers read y right-hand-side minor
+int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr, c128* Yt);
 // Y = X + E X for R right-hand sides in float64 arithmetic with the stored E (complex128 or
 // complex64), internal order, every right-hand side (krylov.cu)
 int product_f64(swm_ctx* ctx, int R, const c128* X, c128* Y);

@@ -125,6 +125,61 @@ __global__ void k_vec_scale(int64_t n, const double* __restrict__ a, const c128*
   out[(int64_t)r * n + t] = mkc(a[r] * x.re, a[r] * x.im);
 }
 
+// Block Gram matrix partials: part[c][a][b] = sum over the rows of chunk c of conj(Q[a][n]) W[b][n]
+// for a < K, b < S, by 16 x 16 tiles (a CTA per chunk and tile); the chunk's rows are staged in
+// shared memory 64 at a time and each thread accumulates one (a, b) entry.
+constexpr int kGT = 16, kGRows = 64, kGChunk = 2048;
+__global__ void __launch_bounds__(kGT* kGT) k_vec_gram(int64_t n, int K, int S, const c128* __restrict__ Q,
+                                                       const c128* __restrict__ W, c128* __restrict__ part) {
+  __shared__ c128 qs[kGT][kGRows + 1], ws[kGT][kGRows + 1];
+  const int ta = blockIdx.y, tb = blockIdx.z;
+  const int a = threadIdx.x / kGT, b = threadIdx.x % kGT;
+  const int64_t n0 = (int64_t)blockIdx.x * kGChunk, n1 = min(n, n0 + kGChunk);
+  double re = 0.0, im = 0.0;
+  for (int64_t m0 = n0; m0 < n1; m0 += kGRows) {
+    for (int e = threadIdx.x; e < kGT * kGRows; e += kGT * kGT) {
+      const int row = e / kGRows, t = e % kGRows;
+      const int64_t nn = m0 + t;
+      const int ga = ta * kGT + row, gb = tb * kGT + row;
+      qs[row][t] = (ga < K && nn < n1) ? Q[(int64_t)ga * n + nn] : mkc(0.0, 0.0);
+      ws[row][t] = (gb < S && nn < n1) ? W[(int64_t)gb * n + nn] : mkc(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int t = 0; t < kGRows; ++t) {
+      const c128 x = qs[a][t], y = ws[b][t];
+      re += x.re * y.re + x.im * y.im;
+      im += x.re * y.im - x.im * y.re;
+    }
+    __syncthreads();
+  }
+  const int ga = ta * kGT + a, gb = tb * kGT + b;
+  if (ga < K && gb < S) part[((int64_t)blockIdx.x * K + ga) * S + gb] = mkc(re, im);
+}
+
+// W[b][n] -= sum over a < K of Q[a][n] C[a][b] (C on the device, K x S), 16 outputs per thread.
+__global__ void k_vec_gemm(int64_t n, int K, int S, const c128* __restrict__ Q, const c128* __restrict__ C,
+                           c128* __restrict__ W) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b0 = blockIdx.y * kGT;
+  if (t >= n) return;
+  c128 acc[kGT];
+#pragma unroll
+  for (int b = 0; b < kGT; ++b) acc[b] = mkc(0.0, 0.0);
+  for (int a = 0; a < K; ++a) {
+    const c128 q = Q[(int64_t)a * n + t];
+#pragma unroll
+    for (int b = 0; b < kGT; ++b)
+      if (b0 + b < S) cfma(acc[b], q, C[(int64_t)a * S + b0 + b]);
+  }
+#pragma unroll
+  for (int b = 0; b < kGT; ++b)
+    if (b0 + b < S) {
+      c128& w = W[(int64_t)(b0 + b) * n + t];
+      w = w - acc[b];
+    }
+}
+
 bool is_device(const void* p) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -308,6 +363,61 @@ int swm_vec_scale(swm_ctx* ctx, int64_t n, int n_rhs, const double* a, const dou
   SWM_TRY(dalloc(ctx, tmp, (void**)&ad, sizeof(double) * n_rhs));
   SWM_CK(cudaMemcpyAsync(ad, a, sizeof(double) * n_rhs, cudaMemcpyHostToDevice, ctx->stream));
   k_vec_scale<<<dim3((unsigned)ceil_div(n, kT), n_rhs), kT, 0, ctx->stream>>>(n, ad, (const c128*)v, (c128*)out);
+  SWM_LAUNCHED();
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, tmp);
+  return SWM_OK;
+}
+
+int swm_vec_gram(swm_ctx* ctx, int64_t n, int K, int S, const double* Q, const double* W, double* out) {
+  if (!ctx) return SWM_EINVAL;
+  ctx->err.clear();
+  if (n < 0 || K < 1 || S < 1 || K > 65535 * kGT || S > 65535 * kGT || !Q || !W || !out)
+    return ctx->fail(SWM_EINVAL, "swm_vec_gram: bad argument");
+  if (!is_device(Q) || !is_device(W)) return ctx->fail(SWM_EINVAL, "swm_vec_gram: vectors must be device memory");
+  SWM_TRY(dev_of(ctx));
+  const int64_t nch = std::max<int64_t>(1, ceil_div(n, kGChunk));
+  std::vector<Buf> tmp;
+  c128* part = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(c128) * nch * K * S));
+  if (n > 0) {
+    k_vec_gram<<<dim3((unsigned)nch, (unsigned)ceil_div(K, kGT), (unsigned)ceil_div(S, kGT)), kGT * kGT, 0,
+                 ctx->stream>>>(n, K, S, (const c128*)Q, (const c128*)W, part);
+    SWM_LAUNCHED();
+  } else {
+    SWM_CK(cudaMemsetAsync(part, 0, sizeof(c128) * K * S, ctx->stream));
+  }
+  std::vector<c128> hp((size_t)nch * K * S);
+  SWM_CK(cudaMemcpyAsync(hp.data(), part, sizeof(c128) * hp.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  SWM_CK(cudaStreamSynchronize(ctx->stream));
+  dfree_group(ctx, tmp);
+  const int64_t KS = (int64_t)K * S;
+  for (int64_t e = 0; e < KS; ++e) {
+    double re = 0.0, im = 0.0;
+    for (int64_t c = 0; c < nch; ++c) {
+      re += hp[(size_t)(c * KS + e)].re;
+      im += hp[(size_t)(c * KS + e)].im;
+    }
+    out[2 * e] = re;
+    out[2 * e + 1] = im;
+  }
+  return SWM_OK;
+}
+
+int swm_vec_gemm(swm_ctx* ctx, int64_t n, int K, int S, const double* Q, const double* C, double* W) {
+  if (!ctx) return SWM_EINVAL;
+  ctx->err.clear();
+  if (n < 0 || K < 1 || S < 1 || S > 65535 * kGT || !Q || !C || !W)
+    return ctx->fail(SWM_EINVAL, "swm_vec_gemm: bad argument");
+  if (!is_device(Q) || !is_device(W)) return ctx->fail(SWM_EINVAL, "swm_vec_gemm: vectors must be device memory");
+  if (n == 0) return SWM_OK;
+  SWM_TRY(dev_of(ctx));
+  std::vector<Buf> tmp;
+  c128* cd = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&cd, sizeof(c128) * K * S));
+  SWM_CK(cudaMemcpyAsync(cd, C, sizeof(c128) * K * S, cudaMemcpyHostToDevice, ctx->stream));
+  k_vec_gemm<<<dim3((unsigned)ceil_div(n, kT), (unsigned)ceil_div(S, kGT)), kT, 0, ctx->stream>>>(
+      n, K, S, (const c128*)Q, cd, (c128*)W);
   SWM_LAUNCHED();
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   dfree_group(ctx, tmp);

@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
 // 32 right-hand sides, so that the product below reads the values of all right-hand sides at a
 // column as one contiguous run.
 template <typename TV, bool RES = false>
-__global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Xt) {
+__global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Xt,
+                                                   int xst = 0) {
   if (!RES && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   __shared__ cplx<TV> tile[32][33];
   const int64_t n0 = (int64_t)blockIdx.x * 32;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __res
   for (int k = ty; k < 32; k += 8) {
     const int64_t n = n0 + k;
     const int r = r0 + tx;
-    if (r < P.R && n < P.N) Xt[n * P.R + r] = tile[tx][k];
+    if (r < P.R && n < P.N) Xt[n * (xst > 0 ? xst : P.R) + r] = tile[tx][k];
   }
 }
 
@@ -317,86 +318,138 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_w(KPtr P, const int64_t* __r
   }
 }
 
-// The same product with the gathers of u staged asynchronously: each thread copies the values it
-// needs for a chunk of kWCh columns from Xt (right-hand-side minor) into its own shared-memory slots
-// with cp.async (no registers held while the copies are in flight), one chunk ahead of the chunk it
-// multiplies, so about 2 kWCh gathers per thread are in flight instead of four.  A thread reads
-// only the slots it wrote itself, so no barrier is needed: waiting for its own copy groups suffices.
-constexpr int kWCh = 8;
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+// The product with two right-hand sides per thread and the tile's E in shared memory.  Thread
+// (wire, pair q) takes right-hand sides 2q and 2q + 1 of its group: each entry of E it reads serves
+// both, and their gathered values are one 16-byte load from Xt, whose rows are padded to an even
+// length xst.  The CTA first copies the E rows of its wires into shared memory (coalesced, each row
+// padded to an even length so that two consecutive entries are one 16-byte load), then every thread
+// multiplies; tiles whose E exceeds the shared-memory budget read E from global memory instead.
+constexpr int kWpSmemBytes = 40 * 1024;
+template <typename TE, bool SM>
+__device__ __forceinline__ void e_pair(const TE* Eg, const c64* Es, int64_t idx, c64& e0, c64& e1) {
+  if constexpr (SM) {
+    const float4 v = *reinterpret_cast<const float4*>(Es + idx);
+    e0 = mkc<float>(v.x, v.y);
+    e1 = mkc<float>(v.z, v.w);
+  } else {
+    e0 = ELoad<float, TE>::ld(Eg + idx);
+    e1 = ELoad<float, TE>::ld(Eg + idx + 1);
+  }
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-template <typename TE, int MODE = kStepW>
-__global__ void __launch_bounds__(256, 4) k_spmv_wa(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
-                                                    const TE* __restrict__ E, const c64* __restrict__ U,
-                                                    const c64* __restrict__ Xt, c64* __restrict__ Wv,
-                                                    const c64* __restrict__ B, int RG, int WB) {
-  constexpr bool RES = MODE == kResW, ALL = MODE != kStepW;
-  if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
-  __shared__ c64 xs_sm[2][kWCh][256];
-  const int64_t N = P.N;
-  const int64_t p0 = (int64_t)blockIdx.x * WB;
-  const int r0 = blockIdx.y * RG;
-  const int tid = threadIdx.x;
-  const int pl = tid / RG, rl = tid % RG;
-  const int64_t p = p0 + pl;
-  const int r = r0 + rl;
-  if (pl >= WB || p >= nw || r >= P.R || !(ALL || P.active[r])) return;
-  const int64_t op = off[p];
-  const int m = (int)(off[p + 1] - op);
-  const int K = lay.K[p];
-  const TE* Ep = E + lay.rowbase[p];
-  const int32_t* cm = lay.colmap + lay.cmbase[p];
-  const c64* xs = Xt + r;
-  const int64_t R = P.R;
-  const int64_t orow = (int64_t)r * N + op;
-  const int nch = (K + kWCh - 1) / kWCh;
-  auto issue = [&](int ch) {
-    const int k0 = ch * kWCh;
-#pragma unroll
-    for (int u = 0; u < kWCh; ++u)
-      if (k0 + u < K) cp_async8(&xs_sm[ch & 1][u][tid], xs + (int64_t)cm[k0 + u] * R);
-    cp_async_commit();
-  };
+template <typename TE, int MODE, bool SM>
+__device__ __forceinline__ void wp_rows(const KPtr& P, int64_t N, int m, int K, int estr, const TE* Eg, const c64* Es,
+                                        const int32_t* __restrict__ cm, const c64* __restrict__ xs, int xst,
+                                        const c64* __restrict__ U, c64* __restrict__ Wv, const c64* __restrict__ B,
+                                        int64_t orow, bool wa, bool wb) {
+  constexpr bool RES = MODE == kResW;
   for (int i0 = 0; i0 < m; i0 += 8) {
     const int mm = min(8, m - i0);
-    const TE* Ei = Ep + (int64_t)i0 * K;
-    c64 acc[8];
+    c64 a0[8], a1[8];
 #pragma unroll
-    for (int ii = 0; ii < 8; ++ii) acc[ii] = mkc<float>(0, 0);
-    if (nch > 0) issue(0);
-    for (int ch = 0; ch < nch; ++ch) {
-      if (ch + 1 < nch) {
-        issue(ch + 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      const int k0 = ch * kWCh;
-      const int kn = min(kWCh, K - k0);
+    for (int ii = 0; ii < 8; ++ii) a0[ii] = a1[ii] = mkc<float>(0, 0);
+    const int K2 = K & ~1;
+    for (int k = 0; k < K2; k += 2) {
+      const int32_t c0 = cm[k], c1 = cm[k + 1];
+      const float4 x0 = *reinterpret_cast<const float4*>(xs + (int64_t)c0 * xst);
+      const float4 x1 = *reinterpret_cast<const float4*>(xs + (int64_t)c1 * xst);
 #pragma unroll
-      for (int u = 0; u < kWCh; ++u) {
-        if (u >= kn) break;
-        const c64 x = xs_sm[ch & 1][u][tid];
+      for (int ii = 0; ii < 8; ++ii)
+        if (ii < mm) {
+          c64 e0, e1;
+          e_pair<TE, SM>(Eg, Es, (int64_t)(i0 + ii) * estr + k, e0, e1);
+          cfma(a0[ii], e0, mkc<float>(x0.x, x0.y));
+          cfma(a1[ii], e0, mkc<float>(x0.z, x0.w));
+          cfma(a0[ii], e1, mkc<float>(x1.x, x1.y));
+          cfma(a1[ii], e1, mkc<float>(x1.z, x1.w));
+        }
+    }
+    if (K2 < K) {
+      const float4 x0 = *reinterpret_cast<const float4*>(xs + (int64_t)cm[K2] * xst);
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii)
-          if (ii < mm) cfma(acc[ii], ELoad<float, TE>::ld(Ei + (int64_t)ii * K + k0 + u), x);
-      }
+      for (int ii = 0; ii < 8; ++ii)
+        if (ii < mm) {
+          const c64 e0 = SM ? Es[(int64_t)(i0 + ii) * estr + K2] : ELoad<float, TE>::ld(Eg + (int64_t)(i0 + ii) * estr + K2);
+          cfma(a0[ii], e0, mkc<float>(x0.x, x0.y));
+          cfma(a1[ii], e0, mkc<float>(x0.z, x0.w));
+        }
     }
 #pragma unroll
     for (int ii = 0; ii < 8; ++ii)
       if (ii < mm) {
-        const int64_t o = orow + i0 + ii;
-        const c64 v = U[o] + acc[ii];
-        Wv[o] = RES ? B[o] - v : v;
+        if (wa) {
+          const int64_t o = orow + i0 + ii;
+          const c64 v = U[o] + a0[ii];
+          Wv[o] = RES ? B[o] - v : v;
+        }
+        if (wb) {
+          const int64_t o = orow + N + i0 + ii;
+          const c64 v = U[o] + a1[ii];
+          Wv[o] = RES ? B[o] - v : v;
+        }
       }
   }
+}
+template <typename TE, int MODE = kStepW>
+__global__ void __launch_bounds__(256, 3) k_spmv_wp(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
+                                                    const TE* __restrict__ E, const c64* __restrict__ U,
+                                                    const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
+                                                    const c64* __restrict__ B, int RQ, int WB) {
+  constexpr bool ALL = MODE != kStepW;
+  if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+  extern __shared__ __align__(16) unsigned char sm_wp[];
+  c64* Es = reinterpret_cast<c64*>(sm_wp);
+  __shared__ int soff[33], sK[32], sm_m[32];
+  __shared__ int64_t sbase[32];
+  __shared__ bool fits;
+  const int64_t N = P.N;
+  const int64_t p0 = (int64_t)blockIdx.x * WB;
+  const int nwt = (int)min((int64_t)WB, nw - p0);
+  if (threadIdx.x < nwt) {
+    const int64_t p = p0 + threadIdx.x;
+    sK[threadIdx.x] = lay.K[p];
+    sm_m[threadIdx.x] = (int)(off[p + 1] - off[p]);
+    sbase[threadIdx.x] = lay.rowbase[p];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int w = 0; w < nwt; ++w) {
+      soff[w] = o;
+      o += sm_m[w] * (sK[w] + (sK[w] & 1));
+    }
+    soff[nwt] = o;
+    fits = (size_t)o * sizeof(c64) <= kWpSmemBytes;
+  }
+  __syncthreads();
+  if (fits) {
+    // E rows of the tile, each padded to an even length (the pad entry is zero)
+    for (int w = 0; w < nwt; ++w) {
+      const int K = sK[w], K2 = K + (K & 1), cnt = sm_m[w] * K2;
+      const TE* src = E + sbase[w];
+      c64* dst = Es + soff[w];
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = e / K2, k = e - i * K2;
+        dst[e] = k < K ? ELoad<float, TE>::ld(src + (int64_t)i * K + k) : mkc<float>(0, 0);
+      }
+    }
+    __syncthreads();
+  }
+  const int pl = (int)threadIdx.x / RQ, q = (int)threadIdx.x % RQ;
+  if (pl >= nwt) return;
+  const int ra = blockIdx.y * 2 * RQ + 2 * q, rb = ra + 1;
+  if (ra >= P.R) return;
+  const bool wa = ALL || P.active[ra];
+  const bool wb = rb < P.R && (ALL || P.active[rb]);
+  if (!wa && !wb) return;
+  const int64_t p = p0 + pl;
+  const int K = sK[pl], m = sm_m[pl];
+  const int32_t* cm = lay.colmap + lay.cmbase[p];
+  const c64* xs = Xt + ra;
+  const int64_t orow = (int64_t)ra * N + off[p];
+  if (fits)
+    wp_rows<TE, MODE, true>(P, N, m, K, K + (K & 1), nullptr, Es + soff[pl], cm, xs, xst, U, Wv, B, orow, wa, wb);
+  else
+    wp_rows<TE, MODE, false>(P, N, m, K, K, E + sbase[pl], nullptr, cm, xs, xst, U, Wv, B, orow, wa, wb);
 }
 
 // Tile shape of k_spmv_w for R right-hand sides: RG right-hand sides per CTA (all of them up to
@@ -665,8 +718,11 @@ __global__ void __launch_bounds__(kRows) k_dots(KPtr P, const cplx<TV>* __restri
 
 // Update of step j (after its dots): q_j = (u - Q s) / rho goes to V_j and the next pending vector
 // u' = (w - Q t) / rho - gamma q_j (the first Gram-Schmidt pass of A q_j) replaces u, in one read of
-// Q_{<j}; one thread per row.
-template <typename TV, typename TQ = cplx<TV>>
+// Q_{<j}.  A thread takes KQ rows (kRows apart, so every load is coalesced) and reads BI basis
+// vectors per pass: KQ * BI independent loads issued before their multiply-adds.  Two rows and
+// four vectors measured fastest on the 1M-wire, 37-incidence workload (339 ms per step against
+// 355 ms for four rows and two vectors, 398 ms for 4 x 4 and 634 ms for 8 x 2).
+template <typename TV, typename TQ = cplx<TV>, int KQ = 2, int BI = 4>
 __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__ U, const cplx<TV>* __restrict__ Wv,
                                                   TQ* __restrict__ V) {
   if (P.st->cycle_done) return;
@@ -688,38 +744,53 @@ __global__ void __launch_bounds__(kRows) k_update(KPtr P, cplx<TV>* __restrict__
   const cplx<TV>* w = Wv + (int64_t)r * N + n0;
   TQ* vj = V + ((int64_t)j * P.R + r) * N + n0;
   const float qs = P.qs, qsi = P.qsi;
-  // four rows per thread (kRows apart, so every load is coalesced) and two basis vectors per
-  // pass: eight independent loads in flight per thread
-  constexpr int kQ = 4;
-  for (int t0 = threadIdx.x; t0 < cnt; t0 += kQ * kRows) {
-    cplx<TV> x[kQ], y[kQ];
+  const int64_t vstride = (int64_t)P.R * N;
+  for (int t0 = threadIdx.x; t0 < cnt; t0 += KQ * kRows) {
+    cplx<TV> x[KQ], y[KQ];
+    bool ok[KQ];
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) {
+    for (int q = 0; q < KQ; ++q) {
       const int t = t0 + q * kRows;
-      x[q] = t < cnt ? u[t] : mkc<TV>(0, 0);
-      y[q] = t < cnt ? w[t] : mkc<TV>(0, 0);
+      ok[q] = t < cnt;
+      x[q] = ok[q] ? u[t] : mkc<TV>(0, 0);
+      y[q] = ok[q] ? w[t] : mkc<TV>(0, 0);
     }
     const TQ* vb = V + (int64_t)r * N + n0 + t0;
-#pragma unroll 2
-    for (int i = 0; i < j; ++i) {
-      const TQ* vi = vb + (int64_t)i * P.R * N;
-      cplx<TV> v[kQ];
+    int i = 0;
+    for (; i + BI <= j; i += BI) {
+      cplx<TV> v[BI][KQ];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q)
-        v[q] = t0 + q * kRows < cnt ? QStore<TV, TQ>::ld(vi + q * kRows, qsi) : mkc<TV>(0, 0);
-      const cplx<TV> a = ss[i], b = ts[i];
+      for (int b = 0; b < BI; ++b)
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        x[q].re = fma(-v[q].re, a.re, fma(v[q].im, a.im, x[q].re));
-        x[q].im = fma(-v[q].re, a.im, fma(-v[q].im, a.re, x[q].im));
-        y[q].re = fma(-v[q].re, b.re, fma(v[q].im, b.im, y[q].re));
-        y[q].im = fma(-v[q].re, b.im, fma(-v[q].im, b.re, y[q].im));
+        for (int q = 0; q < KQ; ++q)
+          v[b][q] = ok[q] ? QStore<TV, TQ>::ld(vb + (int64_t)(i + b) * vstride + q * kRows, qsi) : mkc<TV>(0, 0);
+#pragma unroll
+      for (int b = 0; b < BI; ++b) {
+        const cplx<TV> a = ss[i + b], c = ts[i + b];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+          x[q].re = fma(-v[b][q].re, a.re, fma(v[b][q].im, a.im, x[q].re));
+          x[q].im = fma(-v[b][q].re, a.im, fma(-v[b][q].im, a.re, x[q].im));
+          y[q].re = fma(-v[b][q].re, c.re, fma(v[b][q].im, c.im, y[q].re));
+          y[q].im = fma(-v[b][q].re, c.im, fma(-v[b][q].im, c.re, y[q].im));
+        }
+      }
+    }
+    for (; i < j; ++i) {
+      const cplx<TV> a = ss[i], c = ts[i];
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        const cplx<TV> v = ok[q] ? QStore<TV, TQ>::ld(vb + (int64_t)i * vstride + q * kRows, qsi) : mkc<TV>(0, 0);
+        x[q].re = fma(-v.re, a.re, fma(v.im, a.im, x[q].re));
+        x[q].im = fma(-v.re, a.im, fma(-v.im, a.re, x[q].im));
+        y[q].re = fma(-v.re, c.re, fma(v.im, c.im, y[q].re));
+        y[q].im = fma(-v.re, c.im, fma(-v.im, c.re, y[q].im));
       }
     }
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) {
+    for (int q = 0; q < KQ; ++q) {
       const int t = t0 + q * kRows;
-      if (t < cnt) {
+      if (ok[q]) {
         const cplx<TV> qv = ih * x[q];
         QStore<TV, TQ>::st(vj + t, qv, qs);
         u[t] = ih * y[q] - qv * gm;
@@ -947,7 +1018,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W0, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->W1, sizeof(cplx<TV>) * R * N));
     SWM_TRY(dalloc(ctx, K, (void**)&ws->V, sizeof(TQ) * (size_t)R1 * R * N));
-    if (R >= kMinorR) SWM_TRY(dalloc(ctx, K, (void**)&ws->Xt, sizeof(cplx<TV>) * (size_t)R * N));
+    // rows padded to an even length (16-byte aligned pairs of right-hand sides)
+    if (R >= kMinorR) SWM_TRY(dalloc(ctx, K, (void**)&ws->Xt, sizeof(cplx<TV>) * (size_t)(R + (R & 1)) * N));
     if (R <= kPersistMaxR && ctx->nsm > 0) {
       SWM_TRY(dalloc(ctx, K, (void**)&ws->sync, sizeof(PSync)));
       SWM_TRY(dalloc(ctx, K, (void**)&ws->pp1, sizeof(c128) * (size_t)R * R1 * ctx->nsm));
@@ -1004,6 +1076,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   constexpr int kWire = 64;  // k_spmv_w: wire-tiled, right-hand-side major, no transposed copy
   int rb = multi ? 8 : 1;
   const WireTile wt = wire_tile(R, ctx->nw);
+
   // res: the residual U = B - A Y of a cycle's start in the same form (every right-hand side)
   auto product = [&](cudaStream_t s, int b, auto res_tag) -> int {
     constexpr bool RS = decltype(res_tag)::value;
@@ -1026,14 +1099,18 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
                                                                                        ws->Xt, dst, Bv);
         break;
       }
-      case kWire + 2:  // gathers staged by cp.async (complex64 vectors, incidence-minor copy)
+      case kWire + 3:  // two right-hand sides per thread, E of the tile in shared memory
         if constexpr (std::is_same<TV, float>::value) {
           if (ws->Xt) {
-            k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, src,
-                                                                                                          ws->Xt);
+            const int xst = R + (R & 1);
+            const int RQ = std::min(32, (int)ceil_div(R, 2));
+            const int WBp = std::max(1, 256 / RQ);
+            k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(
+                P, src, ws->Xt, xst);
             SWM_LAUNCHED();
-            k_spmv_wa<TE, RS ? kResW : kStepW><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
-                P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, dst, Bv, wt.RG, wt.WB);
+            k_spmv_wp<TE, RS ? kResW : kStepW>
+                <<<dim3((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(R, 2 * RQ)), 256, kWpSmemBytes, s>>>(
+                    P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, xst, dst, Bv, RQ, WBp);
             break;
           }
         }
@@ -1107,7 +1184,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
     const int forced = ctx->product_form;
     if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || forced == kWire + 1 ||
-        forced == kWire + 2 || (forced == kMinor && ws->Xt)) {
+        forced == kWire + 3 || (forced == kMinor && ws->Xt)) {
       rb = forced;
     } else if (found) {
       rb = found;
@@ -1121,7 +1198,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int b : {4, 8, 16, kMinor, kWire}) {
+      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3}) {
         if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
         if (b == kMinor && !ws->Xt) continue;
         SWM_TRY(launch_product(st, b));
@@ -1377,13 +1454,22 @@ int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter) {
   return gmres_impl<float, c64>(ctx, (const c64*)ctx->Zp, tol, restart, max_iter, nullptr, nullptr);
 }
 
-int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr) {
+int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr, c128* Yt) {
   KPtr P{};
   P.R = ctx->n_rhs;
   P.N = ctx->N;
   const WireTile wt = wire_tile(P.R, ctx->nw);
-  k_spmv_w<double, c64, kResW, false><<<dim3(wt.gx, wt.gy), 256, 0, ctx->stream>>>(
-      P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, nullptr, Rr, B, wt.RG, wt.WB);
+  if (Yt) {
+    // y right-hand-side minor first, so that the gathers of a wire's threads are contiguous
+    k_rhs_minor<double, true><<<dim3((unsigned)ceil_div(P.N, 32), (unsigned)ceil_div(P.R, 32)), 256, 0,
+                                ctx->stream>>>(P, Y, Yt);
+    SWM_LAUNCHED();
+    k_spmv_w<double, c64, kResW, true><<<dim3(wt.gx, wt.gy), 256, 0, ctx->stream>>>(
+        P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, Yt, Rr, B, wt.RG, wt.WB);
+  } else {
+    k_spmv_w<double, c64, kResW, false><<<dim3(wt.gx, wt.gy), 256, 0, ctx->stream>>>(
+        P, ctx->off, ctx->offd, ctx->nw, (const c64*)ctx->Zp, Y, nullptr, Rr, B, wt.RG, wt.WB);
+  }
   SWM_LAUNCHED();
   return SWM_OK;
 }

@@ -139,6 +139,8 @@ int refine_solve(swm_ctx* ctx, const double* frames_dev, double tol, int restart
   SWM_TRY(dalloc(ctx, S, (void**)&B64, sizeof(c128) * R * N));
   SWM_TRY(dalloc(ctx, S, (void**)&Y64, sizeof(c128) * R * N));
   SWM_TRY(dalloc(ctx, S, (void**)&Rr, sizeof(c128) * R * N));
+  c128* Yt = nullptr;  // y right-hand-side minor for the residual's gathers (several right-hand sides)
+  if (R > 1) SWM_TRY(dalloc(ctx, S, (void**)&Yt, sizeof(c128) * R * N));
   SWM_TRY(dalloc(ctx, S, (void**)&part, sizeof(double) * (size_t)R * nchunk));
   SWM_TRY(dalloc(ctx, S, (void**)&dscale, sizeof(double) * R));
   SWM_TRY(dalloc(ctx, S, (void**)&dgain, sizeof(double) * R));
@@ -168,7 +170,7 @@ int refine_solve(swm_ctx* ctx, const double* frames_dev, double tol, int restart
     ctx->prof_begin(SWM_K_APPLY);
     if (R > 1) {
       // several right-hand sides share each read of E (wire-tiled product), then the norms
-      SWM_TRY(residual_f64_wire(ctx, B64, Y64, Rr));
+      SWM_TRY(residual_f64_wire(ctx, B64, Y64, Rr, Yt));
       k_ir_norms<<<gres, kT, 0, st>>>(N, chunk, Rr, part);
     } else {
       k_ir_residual<<<gres, kT, 0, st>>>(N, chunk, (const RowInfo*)ctx->rowinfo, ctx->offd.colmap,

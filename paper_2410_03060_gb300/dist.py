@@ -324,6 +324,90 @@ def dist_gmres(ops, comm, plan, b_own, tol=1e-6, restart=50, max_iter=1000, hist
             y = ops.axpy(Vb, j, -coef, y)
 
 
+def _block_qr(ops, comm, W):
+    """W = V Rf with V orthonormal (columns = the block's vectors) by Cholesky QR twice: the Gram
+    matrix is summed over the ranks, its Cholesky factor inverted on the host (at most a few tens
+    of columns).  Returns (V, Rf) or (None, None) when the block is numerically rank deficient."""
+    Rf = np.eye(ops.n_rhs, dtype=np.complex128)
+    V = W
+    for _ in range(2):
+        G = comm.allreduce_sum(ops.gram(ops.as_basis(V), 1, V))  # G[a, b] = V_a^H V_b
+        G = 0.5 * (G + G.conj().T)
+        try:
+            L = np.linalg.cholesky(G)
+        except np.linalg.LinAlgError:
+            return None, None
+        Rk = L.conj().T  # V = Vn Rk
+        if np.min(np.abs(np.diag(Rk))) <= 1e-13 * np.max(np.abs(np.diag(Rk))):
+            return None, None
+        V = ops.gemm(ops.as_basis(V), 1, -np.linalg.inv(Rk), ops.zeros())  # 0 - V (-Rk^-1)
+        Rf = Rk @ Rf
+    return V, Rf
+
+
+def dist_block_gmres(ops, comm, plan, b_own, tol=1e-6, restart=10, max_iter=1000, history=None):
+    """Restarted block GMRES (one Krylov space shared by all n_rhs right-hand sides of ``ops``),
+    right block-Jacobi preconditioned like :func:`dist_gmres`: block Arnoldi with classical block
+    Gram-Schmidt and a second pass (block inner products summed over the ranks), Cholesky QR twice
+    for each new block, and the block Hessenberg least-squares problem solved on the host.  Every
+    right-hand side stops at the first cycle boundary after all of them meet tol (their columns
+    share the space).  Returns (y_own, block iterations, relative residuals)."""
+    R = ops.n_rhs
+    bn = np.sqrt(comm.allreduce_sum(ops.norms2(b_own)))
+    bn = np.where(bn > 0, bn, 1.0)
+    y = ops.zeros()
+    it = 0
+
+    def product(v_own):
+        sends = {s: ops.take(v_own, idx) for s, idx in plan.send.items()}
+        got = _exchange(comm, plan, sends, R)
+        return ops.apply(v_own, {s: (plan.recv[s], vals) for s, vals in got.items()})
+
+    while True:
+        r = ops.sub(b_own, product(y))
+        rn = np.sqrt(comm.allreduce_sum(ops.norms2(r)))
+        rel = rn / bn
+        if history is not None:
+            history.append(rel.copy())
+        if not (rel > tol).any() or it >= max_iter:
+            return y, it, rel
+        V0, beta = _block_qr(ops, comm, r)
+        if V0 is None:
+            return y, it, rel
+        Vb = ops.basis(restart + 1)
+        ops.put(Vb, 0, V0)
+        H = np.zeros(((restart + 1) * R, restart * R), dtype=np.complex128)
+        rhs = np.zeros(((restart + 1) * R, R), dtype=np.complex128)
+        rhs[:R] = beta
+        Z, j = None, 0
+        while j < restart and it < max_iter:
+            W = product(ops.get(Vb, j))
+            h = comm.allreduce_sum(ops.gram(Vb, j + 1, W))  # ((j+1) R) x R
+            W = ops.gemm(Vb, j + 1, h, W)
+            h2 = comm.allreduce_sum(ops.gram(Vb, j + 1, W))
+            W = ops.gemm(Vb, j + 1, h2, W)
+            H[:(j + 1) * R, j * R:(j + 1) * R] = h + h2
+            Vn, Rn = _block_qr(ops, comm, W)
+            if Vn is None:  # the block space stopped growing: solve with what there is
+                j += 1
+                it += 1
+                Z = np.linalg.lstsq(H[:(j + 1) * R, :j * R], rhs[:(j + 1) * R], rcond=None)[0]
+                break
+            H[(j + 1) * R:(j + 2) * R, j * R:(j + 1) * R] = Rn
+            j += 1
+            it += 1
+            Hj = H[:(j + 1) * R, :j * R]
+            Z = np.linalg.lstsq(Hj, rhs[:(j + 1) * R], rcond=None)[0]
+            est = np.linalg.norm(rhs[:(j + 1) * R] - Hj @ Z, axis=0) / bn
+            if j < restart:
+                ops.put(Vb, j, Vn)
+            if not (est > tol).any():
+                break
+        if Z is not None and j > 0:
+            # y += sum over blocks i of V_i Z_i, Z_i the rows i R .. (i+1) R of Z
+            y = ops.gemm(Vb, j, -Z[:j * R], y)
+
+
 # ------------------------------------------------------------------------------------ device ops
 class SwmOps:
     """The numerical steps of :func:`dist_gmres` on one rank, in the library's kernels: a context
@@ -388,6 +472,20 @@ class SwmOps:
         self._lib().swm_vec_scale(self.ctx, np.asarray(a, dtype=np.float64), v, out)
         return out
 
+    def as_basis(self, v):
+        return v.unsqueeze(0)
+
+    def gram(self, Vb, k, w):
+        """((k n_rhs) x n_rhs) inner products of every basis vector of the first k blocks with
+        every vector of w."""
+        return self._lib().swm_vec_gram(self.ctx, Vb, k, w)
+
+    def gemm(self, Vb, k, C, w):
+        """w - (first k blocks of Vb) C, C of (k n_rhs) x n_rhs."""
+        out = w.clone()
+        self._lib().swm_vec_gemm(self.ctx, Vb, k, C, out)
+        return out
+
 
 def gather_rhs_own(ops, inc):
     """Owned rows of the right-hand sides (Eq. (4)) of the rank's wires."""
@@ -412,11 +510,12 @@ def currents_own(ops, y_own):
 
 
 def solve_partitioned(comm, centres, dirs, lengths, radii, nseg, k, r_c, inc, obs, tol=1e-6, restart=50,
-                      max_iter=1000, device=0):
+                      max_iter=1000, device=0, block=False):
     """One rank's share of the whole path on a cloud split over ``comm``: partition (every rank the
     same), its context with owned and halo wires, build, distributed GMRES, x = M^-1 y, and the
-    bistatic RCS from the far-field components summed over the ranks.  Returns (x_own (n_rhs x
-    n_own, numpy), global ids of the owned wires, sigma (n_rhs x n_obs x 2), iterations)."""
+    bistatic RCS from the far-field components summed over the ranks; with ``block`` the solve is
+    block GMRES over all incidences.  Returns (x_own (n_rhs x n_own, numpy), global ids of the owned
+    wires, sigma (n_rhs x n_obs x 2), iterations)."""
     import torch
 
     from . import swm
@@ -432,7 +531,7 @@ def solve_partitioned(comm, centres, dirs, lengths, radii, nseg, k, r_c, inc, ob
         inc = np.atleast_2d(np.asarray(inc, dtype=np.float64))
         ops = SwmOps(ctx, plan, inc.shape[0])
         b = gather_rhs_own(ops, inc)
-        y, it, rel = dist_gmres(ops, comm, plan, b, tol, restart, max_iter)
+        y, it, rel = (dist_block_gmres if block else dist_gmres)(ops, comm, plan, b, tol, restart, max_iter)
         x = currents_own(ops, y)
         no = plan.n_own_wires
         off = torch.from_numpy(plan.off[:no + 1].copy()).cuda()

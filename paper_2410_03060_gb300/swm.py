@@ -76,6 +76,8 @@ _SIGS = {
     "swm_vec_dots": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, _P, _P, _P]),
     "swm_vec_axpy": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, _P, _P, _P]),
     "swm_vec_scale": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, _P]),
+    "swm_vec_gram": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, _P, _P, _P]),
+    "swm_vec_gemm": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, _P, _P, _P]),
     "swm_solve_guess": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _P, C.c_int]),
     "swm_net_num_params": (C.c_int64, []),
     "swm_net_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
@@ -514,6 +516,28 @@ def swm_vec_scale(ctx: Ctx, a, v, out) -> int:
     a = np.ascontiguousarray(a, dtype=np.float64).reshape(R)
     return _check(ctx, load().swm_vec_scale(ctx.handle, n, R, a.ctypes.data_as(C.c_void_p), _dev_c128(v, (R, n), "v"),
                                             _dev_c128(out, (R, n), "out")))
+
+
+def swm_vec_gram(ctx: Ctx, Vb, k: int, w) -> np.ndarray:
+    """((k S) x S) complex inner products conj(Q[a]) . w[b] of the first k S vectors of Vb
+    (a (>= k, S, n) CUDA complex128 tensor) with the S vectors of w (S, n)."""
+    S, n = w.shape
+    if Vb.shape[0] < k or tuple(Vb.shape[1:]) != (S, n) or not Vb.is_contiguous():
+        raise ValueError("swm_vec_gram: basis shape")
+    out = np.zeros((k * S, S), dtype=np.complex128)
+    _check(ctx, load().swm_vec_gram(ctx.handle, n, int(k * S), S, C.c_void_p(Vb.data_ptr()), _dev_c128(w, (S, n), "w"),
+                                    out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def swm_vec_gemm(ctx: Ctx, Vb, k: int, coef, w) -> int:
+    """w[b] -= sum over a < k S of Q[a] coef[a][b] (coef host (k S) x S complex)."""
+    S, n = w.shape
+    if Vb.shape[0] < k or tuple(Vb.shape[1:]) != (S, n) or not Vb.is_contiguous():
+        raise ValueError("swm_vec_gemm: basis shape")
+    c = np.ascontiguousarray(coef, dtype=np.complex128).reshape(k * S, S)
+    return _check(ctx, load().swm_vec_gemm(ctx.handle, n, int(k * S), S, C.c_void_p(Vb.data_ptr()),
+                                           c.ctypes.data_as(C.c_void_p), _dev_c128(w, (S, n), "w")))
 
 
 def swm_far_field_noalloc(stream, centres, dirs, lengths, nseg, off, k, currents, obs, sigma_out) -> int:

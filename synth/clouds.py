@@ -123,12 +123,13 @@ def cloud_precision(seed: int = 3, nw: int = 200_000) -> Cloud:
     return _make(centres, dirs, lengths, _nseg_for(lengths), "precision")
 
 
-def cloud_learned(seed: int = 4, nw: int = 1_000_000, n_clusters: int = 8) -> Cloud:
-    """1,000,000 wires in 8 Gaussian clusters (sigma 40) whose centres are uniform in [-180, 180]^3."""
+def cloud_learned(seed: int = 4, nw: int = 1_000_000, n_clusters: int = 8, sigma: float = 40.0) -> Cloud:
+    """1,000,000 wires in 8 Gaussian clusters (sigma 40) whose centres are uniform in [-180, 180]^3.
+    A smaller ``nw`` with sigma = 40 (nw / 1e6)^(1/3) keeps the wire density of the full cloud."""
     rng = np.random.default_rng(seed)
     cc = rng.uniform(-180.0, 180.0, size=(n_clusters, 3))
     which = rng.integers(0, n_clusters, size=nw)
-    centres = cc[which] + rng.normal(0.0, 40.0, size=(nw, 3))
+    centres = cc[which] + rng.normal(0.0, sigma, size=(nw, 3))
     dirs = _unit_directions(rng, nw)
     lengths = rng.uniform(0.3, 0.6, size=nw)
     return _make(centres, dirs, lengths, _nseg_for(lengths), "learned")

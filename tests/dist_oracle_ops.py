@@ -59,6 +59,17 @@ class OracleOps:
     def scale(self, v, a):
         return np.asarray(a)[:, None] * v
 
+    def as_basis(self, v):
+        return v[None]
+
+    def gram(self, Vb, k, w):
+        Q = Vb[:k].reshape(-1, Vb.shape[-1])
+        return np.conj(Q) @ w.T
+
+    def gemm(self, Vb, k, C, w):
+        Q = Vb[:k].reshape(-1, Vb.shape[-1])
+        return w - (Q.T @ C).T
+
     def rhs_own(self, inc):
         return O.rhs(self.local, self.k, inc).T[:, :self.plan.n_own].copy()
 
@@ -80,7 +91,7 @@ class OracleOps:
         return np.stack([Ft, Fp], axis=2)
 
 
-def run_rank(comm, cloud, k, r_c, inc, obs, tol, restart, max_iter=500):
+def run_rank(comm, cloud, k, r_c, inc, obs, tol, restart, max_iter=500, block=False):
     """One rank's whole partitioned solve with oracle operators: (global wire ids owned, currents
     n_rhs x n_own, sigma n_rhs x n_obs x 2, iterations)."""
     from paper_2410_03060_gb300 import dist
@@ -89,7 +100,8 @@ def run_rank(comm, cloud, k, r_c, inc, obs, tol, restart, max_iter=500):
     plan = dist.Plan(cloud.centres, cloud.nseg, owner, comm.rank, r_c)
     ops = OracleOps(cloud, plan, k, r_c, inc.shape[0])
     b = ops.rhs_own(inc)
-    y, it, rel = dist.dist_gmres(ops, comm, plan, b, tol, restart, max_iter)
+    solver = dist.dist_block_gmres if block else dist.dist_gmres
+    y, it, rel = solver(ops, comm, plan, b, tol, restart, max_iter)
     x = ops.currents_own(y)
     comp = comm.allreduce_sum(ops.far_components(x, obs))
     sigma = np.abs(comp) ** 2 / (4.0 * math.pi)

@@ -148,3 +148,24 @@ def test_partitioned_gmres_on_two_gloo_ranks():
     assert np.linalg.norm(X2 - X1) / np.linalg.norm(X1) < 1e-10
     assert np.allclose(out[0][2], one[2], rtol=1e-9, atol=1e-14)
     assert np.array_equal(out[0][2], out[1][2])  # every rank holds the same RCS
+
+
+def test_block_gmres_one_and_two_ranks_match_lu():
+    """Restarted block GMRES (one Krylov space shared by the incidences), on one rank and split
+    over two thread ranks, against the oracle's LU solution; with several restart cycles."""
+    cl = _cloud()
+    r_c = 1.5
+    g = np.random.default_rng(9)
+    inc = np.stack([g.uniform(0, np.pi, 6), g.uniform(0, 2 * np.pi, 6), g.uniform(0, np.pi, 6)], 1)
+    obs = observations_phi_cut(12)
+    X_lu = O.solve_lu(O.assemble(cl, K, r_c, sparse=False), O.rhs(cl, K, inc))
+    one = run_rank(dist.LocalComm(), cl, K, r_c, inc, obs, 1e-11, 4, block=True)
+    X1 = to_global(cl, [one[:2]])
+    assert np.linalg.norm(X1 - X_lu) / np.linalg.norm(X_lu) < 1e-9
+    res = _threads(2, lambda comm: run_rank(comm, cl, K, r_c, inc, obs, 1e-11, 4, block=True))
+    X2 = to_global(cl, [r[:2] for r in res])
+    assert np.linalg.norm(X2 - X1) / np.linalg.norm(X1) < 1e-9
+    # the block space contains every incidence's own Krylov space: no more block iterations than
+    # the independent GMRES needs
+    ind = run_rank(dist.LocalComm(), cl, K, r_c, inc, obs, 1e-11, 4)
+    assert one[3] <= ind[3]

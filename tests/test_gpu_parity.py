@@ -490,11 +490,11 @@ def test_split_step_path_matches_oracle(monkeypatch):
                 assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
 
 
-@pytest.mark.parametrize("form", [4, 8, 16, 32, 64, 65, 66])
+@pytest.mark.parametrize("form", [4, 8, 16, 32, 64, 65, 67])
 def test_every_product_form_matches_oracle(monkeypatch, form):
     """Each form of the many-incidence product, forced (SWM_PRODUCT_FORM) on the large-system GMRES
     step: 4/8/16 incidences per read of E, 32 the incidence-minor form, 64 and 65 the wire-tiled
-    form (65: five CTAs per SM; 66: gathers staged by cp.async).
+    form (65: five CTAs per SM; 67: two incidences per thread, E of the tile in shared memory).
     A cloud with every segment count 2..16 (wires of up to 15 rows, two row groups in the
     wire-tiled form) and ragged tiles; 37 and 70 incidences (one group of 37, two groups of 35 in
     the wire-tiled form); currents against the oracle's LU solution and the RCS within 0.1 dB."""
