@@ -316,6 +316,9 @@ def class_bytes(cls, st, prec, n_rhs, restart):
         nblk = -(-R // rb)
         mat = (st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N) * nblk
         return len(steps_j) * (mat + 2 * vec) + (len(cycles) + 1) * (mat + 3 * vec)
+    if cls == "transpose":
+        # the copy of u (and of y at each restart) to incidence-minor order: read and written once
+        return (len(steps_j) + len(cycles) + 1) * 2 * vec
     if cls == "dots":
         return sum((j + 2) * vec for j in steps_j) + sum((c + 1) * vec for c in cycles)
     if cls == "update":
@@ -357,7 +360,8 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
     work = b * steps
     ach = work / (prof_ms * 1e-3) / 1e9
     peak = pk.get("hbm_gbs", 6800.0)
-    names = {"apply": "k_spmv_t (+ k_rhs_minor) / k_spmv: block-sparse product",
+    names = {"apply": "k_spmv_wp / k_spmv_w / k_spmv_t / k_spmv (form timed per shape): block-sparse product",
+             "transpose": "k_rhs_minor_all: pending vectors to incidence-minor order",
              "dots": "k_dots: delayed Gram-Schmidt inner products",
              "update": "k_update: delayed Gram-Schmidt update",
              "gmres": "k_gmres_persist: persistent GMRES solve"}
@@ -371,8 +375,8 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
 # recorded with the profile summaries.  A class without a capture of its current code reports null.
 MEASURED_TRAFFIC = {}
 
-PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "apply", "dots", "update", "far",
-                   "gmres"]
+PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "apply", "transpose", "dots", "update",
+                   "far", "gmres"]
 
 
 def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps=None):
@@ -459,7 +463,7 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
         roof["profiled_steps"] = rsteps
         roof["traffic"] = MEASURED_TRAFFIC.get((name, dominant, args.precision))
     extra_roofs = {}
-    for c in ("fill_mutual", "apply", "dots", "update"):
+    for c in ("fill_mutual", "apply", "transpose", "dots", "update"):
         if c != dominant and prof[c][1] > 0:
             extra_roofs[c] = roofline_of(c, st, prof[c][0], prof[c][1], args.precision, R, restart, 1, pk)
 

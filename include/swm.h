@@ -140,6 +140,9 @@ typedef struct swm_stats {
 #define SWM_K_UPDATE 9      /* update of the delayed Gram-Schmidt (q_j and the next vector) */
 #define SWM_K_FINISH 10     /* unused (kept so that class numbers stay as they were) */
 #define SWM_K_FAR 11        /* far field: partial sums and their reduction to RCS */
+#define SWM_K_TRANSPOSE 13  /* copy of the pending vectors to incidence-minor order before the
+                               wire-tiled product with two incidences per thread (form 67); the
+                               APPLY class then times the product kernel alone */
 #define SWM_K_GMRES 12      /* the whole solve as one persistent cooperative kernel (systems below
                                SWM_SPLIT_ROWS unknowns with at most 8 right-hand sides); the
                                per-step classes 7-10 then launch nothing */

@@ -814,7 +814,7 @@ int swm_get_stats(const swm_ctx* ctx, swm_stats* out) {
 
 int swm_profile(swm_ctx* ctx, int kernel_class) {
   if (!ctx) return SWM_EINVAL;
-  if (kernel_class < SWM_K_NONE || kernel_class > SWM_K_GMRES) return ctx->fail(SWM_EINVAL, "bad kernel class");
+  if (kernel_class < SWM_K_NONE || kernel_class > SWM_K_TRANSPOSE) return ctx->fail(SWM_EINVAL, "bad kernel class");
   SWM_TRY(set_device(ctx));
   SWM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->prof_flush();

@@ -163,6 +163,29 @@ __global__ void __launch_bounds__(kRows) k_spmv(KPtr P, const RowInfo* __restric
 // [R][N]) copied to right-hand-side minor order Xt[N][R] through shared-memory tiles of 32 rows x
 // 32 right-hand sides, so that the product below reads the values of all right-hand sides at a
 // column as one contiguous run.
+// The same copy for all right-hand sides at once, T rows per CTA: each warp loads whole runs of T
+// consecutive entries of one right-hand side, and the CTA's output Xt[n0 .. n0 + T)[0 .. xst) is one
+// contiguous block written in order (the padding column of an odd R is written as zero).
+template <typename TV, bool RES = false>
+__global__ void __launch_bounds__(256) k_rhs_minor_all(KPtr P, const cplx<TV>* __restrict__ U,
+                                                       cplx<TV>* __restrict__ Xt, int xst, int T) {
+  if (!RES && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+  extern __shared__ __align__(16) unsigned char sm_tr[];
+  cplx<TV>* tile = reinterpret_cast<cplx<TV>*>(sm_tr);  // [T][xst + 1]
+  const int ts = xst + 1;
+  const int64_t n0 = (int64_t)blockIdx.x * T;
+  const int cnt = (int)min((int64_t)T, P.N - n0);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+  for (int r = wp; r < P.R; r += nwp) {
+    const cplx<TV>* u = U + (int64_t)r * P.N + n0;
+    for (int t = lane; t < cnt; t += 32) tile[t * ts + r] = u[t];
+  }
+  __syncthreads();
+  cplx<TV>* out = Xt + n0 * xst;
+  for (int t = wp; t < cnt; t += nwp)
+    for (int r = lane; r < xst; r += 32) out[(int64_t)t * xst + r] = r < P.R ? tile[t * ts + r] : mkc<TV>(0, 0);
+}
+
 template <typename TV, bool RES = false>
 __global__ void __launch_bounds__(256) k_rhs_minor(KPtr P, const cplx<TV>* __restrict__ U, cplx<TV>* __restrict__ Xt,
                                                    int xst = 0) {
@@ -389,6 +412,7 @@ __device__ __forceinline__ void wp_rows(const KPtr& P, int64_t N, int m, int K, 
       }
   }
 }
+constexpr int kWpMaxWires = 32;  // wires per CTA of k_spmv_wp, at most
 template <typename TE, int MODE = kStepW>
 __global__ void __launch_bounds__(256, 3) k_spmv_wp(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
                                                     const TE* __restrict__ E, const c64* __restrict__ U,
@@ -398,12 +422,12 @@ __global__ void __launch_bounds__(256, 3) k_spmv_wp(KPtr P, const int64_t* __res
   if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   extern __shared__ __align__(16) unsigned char sm_wp[];
   c64* Es = reinterpret_cast<c64*>(sm_wp);
-  __shared__ int soff[33], sK[32], sm_m[32];
-  __shared__ int64_t sbase[32];
+  __shared__ int soff[kWpMaxWires + 1], sK[kWpMaxWires], sm_m[kWpMaxWires];
+  __shared__ int64_t sbase[kWpMaxWires];
   __shared__ bool fits;
   const int64_t N = P.N;
   const int64_t p0 = (int64_t)blockIdx.x * WB;
-  const int nwt = (int)min((int64_t)WB, nw - p0);
+  const int nwt = (int)min((int64_t)min(WB, kWpMaxWires), nw - p0);
   if (threadIdx.x < nwt) {
     const int64_t p = p0 + threadIdx.x;
     sK[threadIdx.x] = lay.K[p];
@@ -1101,12 +1125,19 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       }
       case kWire + 3:  // two right-hand sides per thread, E of the tile in shared memory
         if constexpr (std::is_same<TV, float>::value) {
-          if (ws->Xt) {
+          if (ws->Xt && R <= 256) {  // the transposing copy keeps T rows x (R + 1) in <= 48 KB
             const int xst = R + (R & 1);
             const int RQ = std::min(32, (int)ceil_div(R, 2));
-            const int WBp = std::max(1, 256 / RQ);
-            k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(
-                P, src, ws->Xt, xst);
+            // at most 32 wires: the kernel's per-wire tables in shared memory hold 32
+            const int WBp = std::max(1, std::min(kWpMaxWires, 256 / RQ));
+            // all right-hand sides of T rows per CTA (T x (xst + 1) entries in shared memory, <= 48 KB)
+            const int T = std::max(8, std::min(64, (int)((48 * 1024 / sizeof(cplx<TV>)) / (xst + 1)) / 8 * 8));
+            ctx->prof_end(SWM_K_APPLY);
+            ctx->prof_begin(SWM_K_TRANSPOSE);
+            k_rhs_minor_all<TV, RS><<<(unsigned)ceil_div(N, T), 256, sizeof(cplx<TV>) * T * (xst + 1), s>>>(
+                P, src, ws->Xt, xst, T);
+            ctx->prof_end(SWM_K_TRANSPOSE);
+            ctx->prof_begin(SWM_K_APPLY);
             SWM_LAUNCHED();
             k_spmv_wp<TE, RS ? kResW : kStepW>
                 <<<dim3((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(R, 2 * RQ)), 256, kWpSmemBytes, s>>>(
@@ -1224,7 +1255,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   }
   ctx->stats.step_rhs_block = rb;
   const bool use_graph = !persisted && ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_DOTS &&
-                         ctx->prof_cls != SWM_K_UPDATE;
+                         ctx->prof_cls != SWM_K_UPDATE && ctx->prof_cls != SWM_K_TRANSPOSE;
   if (use_graph) {
     struct Key {
       KPtr P;

@@ -392,7 +392,7 @@ def swm_get_stats(ctx: Ctx) -> dict:
 
 
 SWM_K = {"none": 0, "pairs": 1, "fill_self": 2, "fill_mutual": 3, "invert": 4, "form_e": 5, "rhs": 6,
-         "apply": 7, "dots": 8, "update": 9, "finish": 10, "far": 11, "gmres": 12}
+         "apply": 7, "dots": 8, "update": 9, "finish": 10, "far": 11, "gmres": 12, "transpose": 13}
 
 
 def swm_profile(ctx: Ctx, kernel_class) -> int:

@@ -206,8 +206,10 @@ def test_mid_workload_at_full_size_sampled_parity():
     """The benchmark's workload at full size (10,000 wires, 51,397 unknowns) in its configuration:
     device inputs through swm_run, complex64, r_c 3, GMRES(50) to 1e-6, 720 observations.  Checked
     against the oracle: the pattern bit for bit, the right-hand side, 40 sampled blocks, the
-    residual b - Z x of the GPU currents on 60 sampled block-rows of the oracle's Z, and the RCS
-    against the oracle's far field of the same currents."""
+    residual b - Z x of the GPU currents on 60 sampled block-rows of the oracle's Z (below 1e-4: the
+    GMRES tolerance 1e-6 plus the complex64 fill error, about 1e-5 here), the RCS against the
+    oracle's far field of the same currents, and the RCS against the same cloud run on the
+    float64 path within 0.1 dB (the method's accuracy criterion)."""
     import torch
     from paper_2410_03060_gb300 import swm
 
@@ -223,9 +225,12 @@ def test_mid_workload_at_full_size_sampled_parity():
     sig = torch.zeros((1, len(obs), 2), dtype=torch.float64, device="cuda")
     ctx = swm.swm_create(0)
     try:
+        sig64 = torch.zeros_like(sig)
+        assert swm.swm_run(ctx, *dev, K, r_c, C128, inc, obs, sig64, 1e-6, 50, 1000) == 0
         assert swm.swm_run(ctx, *dev, K, r_c, C64, inc, obs, sig, 1e-6, 50, 1000) == 0
         torch.cuda.synchronize()
         sigma = sig.cpu().numpy()
+        assert_rcs_db(sigma[0, :, 0], sig64.cpu().numpy()[0, :, 0], db=0.1)
         assert np.array_equal(swm.swm_get_pattern(ctx), pairs_ref)
         b_gpu = swm.swm_get_rhs(ctx).T
         assert np.max(np.abs(b_gpu - b_ref)) / np.max(np.abs(b_ref)) < 2e-6
@@ -248,7 +253,7 @@ def test_mid_workload_at_full_size_sampled_parity():
             acc -= O.block(cl, K, int(p), int(q)) @ X[int(off[q]):int(off[q + 1]), 0]
         r2 += float(np.sum(np.abs(acc) ** 2))
         b2 += float(np.sum(np.abs(b_ref[rows, 0]) ** 2))
-    assert math.sqrt(r2 / b2) < 1e-3, math.sqrt(r2 / b2)
+    assert math.sqrt(r2 / b2) < 1e-4, math.sqrt(r2 / b2)
     s_ref = O.rcs_bistatic(cl, K, X, obs)
     assert np.max(np.abs(sigma - s_ref)) / np.max(s_ref) < 1e-4
     assert_rcs_db(sigma[0, :, 0], s_ref[0, :, 0], db=0.1)
@@ -605,16 +610,18 @@ def test_persistent_barrier_wait_runs_out_and_reports_etimeout(monkeypatch):
         swm.swm_destroy(out["ctx"])
 
 
-def test_contexts_on_concurrent_host_threads():
+def test_contexts_on_concurrent_host_threads(monkeypatch):
     """Contexts driven from several host threads at once (each on its own stream, with systems of
     different sizes, so their kernels ask for different amounts of shared memory) give the same
-    currents as when run one after the other."""
+    currents as when run one after the other.  The product form is fixed (its timed choice could
+    differ under the contention of concurrent runs, and two forms add in different orders)."""
     import threading
 
     import torch
 
     from paper_2410_03060_gb300 import swm
 
+    monkeypatch.setenv("SWM_PRODUCT_FORM", "8")
     # up to 150k unknowns: the fused step kernel then asks for more than 48 KB of shared memory
     clouds = [cloud_uniform_cube(n, (n / 0.02) ** (1 / 3), seed=90 + i)
               for i, n in enumerate((30000, 26000, 12000, 3000))]
