@@ -54,7 +54,7 @@ __all__ = [
     "assemble_block", "mutual_block", "self_block", "block",
     "neighbour_pairs", "block_pattern", "assemble", "block_jacobi",
     "incidence_frames", "triangle_ft", "rhs", "far_field", "rcs_from_far_field",
-    "rcs_bistatic", "rcs_monostatic", "solve_lu", "gmres", "gcr", "solve",
+    "rcs_bistatic", "rcs_monostatic", "solve_lu", "gmres", "gcr", "bicgstab", "solve",
 ]
 
 
@@ -603,10 +603,85 @@ def gcr(A, b: np.ndarray, Minv_blocks, off, tol: float = 1e-6, restart: int = 50
                 break
 
 
+def bicgstab(A, b: np.ndarray, Minv_blocks, off, tol: float = 1e-6, max_iter: int = 1000, x0=None,
+             history=None):
+    """BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput. 13 (1992) 631) with right block-Jacobi
+    preconditioning, in float64, for one right-hand side of A x = b: a short-recurrence Krylov
+    solver for the block-diagonally preconditioned system of Sec. II-B, whose cost per step is two
+    products and a fixed number of vector operations (no basis is stored).
+
+    On the right-preconditioned system (A M^-1) y = b, x = M^-1 y, starting from y = 0, r = b and
+    the shadow residual rh = r; each iteration (two products):
+        rho = rh^H r,  beta = (rho / rho_prev) (alpha / omega),  p = r + beta (p - omega v),
+        v = A M^-1 p,  alpha = rho / (rh^H v),  s = r - alpha v,
+        t = A M^-1 s,  omega = (t^H s) / (t^H t),  y += alpha p + omega s,  r = s - omega t.
+    The iteration stops when the recursive residual |r| <= tol |b|; the true residual b - A x is
+    then formed, and if it still exceeds tol |b| (the recursion drifted) the method restarts from
+    it with rh = r.  A breakdown (rho, rh^H v or t^H t equal to zero) restarts the same way.
+    Returns (x, iterations, true relative residual); ``history`` receives |r|/|b| after every
+    iteration."""
+    b = np.asarray(b, dtype=np.complex128)
+    N = b.shape[0]
+
+    def Minv(v):
+        z = np.empty_like(v)
+        for p, Mi in enumerate(Minv_blocks):
+            z[off[p]:off[p + 1]] = Mi @ v[off[p]:off[p + 1]]
+        return z
+
+    def op(v):
+        return A @ Minv(v)
+
+    bnorm = np.linalg.norm(b)
+    x = np.zeros(N, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    if bnorm == 0.0:
+        return x, 0, 0.0
+    y = np.zeros(N, dtype=np.complex128)  # x = x_start + M^-1 y
+    x_start = x.copy()
+    it = 0
+    while True:
+        r = b - A @ (x_start + Minv(y))
+        rel = np.linalg.norm(r) / bnorm
+        if rel <= tol or it >= max_iter:
+            return x_start + Minv(y), it, rel
+        rh = r.copy()
+        rho_prev = alpha = omega = 1.0 + 0.0j
+        p = np.zeros(N, dtype=np.complex128)
+        v = np.zeros(N, dtype=np.complex128)
+        while it < max_iter:
+            rho = np.vdot(rh, r)
+            if rho == 0.0:
+                break
+            beta = (rho / rho_prev) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+            v = op(p)
+            rv = np.vdot(rh, v)
+            if rv == 0.0:
+                break
+            alpha = rho / rv
+            s = r - alpha * v
+            t = op(s)
+            tt = np.vdot(t, t).real
+            if tt == 0.0:
+                y = y + alpha * p
+                it += 1
+                break
+            omega = np.vdot(t, s) / tt
+            y = y + alpha * p + omega * s
+            r = s - omega * t
+            rho_prev = rho
+            it += 1
+            rel = np.linalg.norm(r) / bnorm
+            if history is not None:
+                history.append(rel)
+            if rel <= tol or omega == 0.0:
+                break
+
+
 def solve(cloud, k: float, inc: np.ndarray, r_c: float | None = None, method: str = "lu",
           tol: float = 1e-6, restart: int = 50, max_iter: int = 1000):
-    """Currents jt (N x n_inc) of Z jt = b for each incidence.  ``method`` 'lu', 'gmres' or
-    'gcr'."""
+    """Currents jt (N x n_inc) of Z jt = b for each incidence.  ``method`` 'lu', 'gmres', 'gcr' or
+    'bicgstab'."""
     Z = assemble(cloud, k, r_c, sparse=(method != "lu"))
     b = rhs(cloud, k, inc)
     if method == "lu":
@@ -616,7 +691,10 @@ def solve(cloud, k: float, inc: np.ndarray, r_c: float | None = None, method: st
     X = np.zeros_like(b)
     its = []
     for i in range(b.shape[1]):
-        krylov = gcr if method == "gcr" else gmres
-        X[:, i], it, rel = krylov(Z, b[:, i], Mi, off, tol, restart, max_iter)
+        if method == "bicgstab":
+            X[:, i], it, rel = bicgstab(Z, b[:, i], Mi, off, tol, max_iter)
+        else:
+            krylov = gcr if method == "gcr" else gmres
+            X[:, i], it, rel = krylov(Z, b[:, i], Mi, off, tol, restart, max_iter)
         its.append(it)
     return X, {"iterations": its}

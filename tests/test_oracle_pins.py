@@ -476,6 +476,70 @@ def test_gcr_matches_lu_and_restarts():
         assert np.linalg.norm(b - Z @ x) / np.linalg.norm(b) < 1e-11
 
 
+def test_bicgstab_matches_lu_and_terminates_on_two_eigenvalues():
+    """BiCGSTAB (the short-recurrence solver of the block-diagonally preconditioned system of
+    Sec. II-B): the LU solution of a cloud's sparsified system; one iteration when the
+    right-preconditioned operator is the identity (Z block-diagonal, exact block inverses); and at
+    most two iterations on an operator with two distinct eigenvalues (its residual polynomial of
+    degree two vanishes on both)."""
+    cl = cloud_uniform_cube(40, 4.0, seed=16)
+    inc = np.array([[0.0, 0.0, 0.0]])
+    Z = O.assemble(cl, K, 2.0, sparse=True)
+    b = O.rhs(cl, K, inc)[:, 0]
+    x_lu = O.solve_lu(Z, b)
+    m, off = O.numbering(cl.nseg)
+    Mi = O.block_jacobi(cl, K)
+    x, it, rel = O.bicgstab(Z, b, Mi, off, tol=1e-12)
+    assert rel <= 1e-12 and it > 1
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-10
+    assert np.linalg.norm(b - Z @ x) / np.linalg.norm(b) < 1e-11
+    # tolerance 1e-6: the true residual is below it, in fewer iterations
+    x6, it6, rel6 = O.bicgstab(Z, b, Mi, off, tol=1e-6)
+    assert np.linalg.norm(b - Z @ x6) / np.linalg.norm(b) <= 1e-6 and it6 < it
+    # identity operator: Z block-diagonal (r_c below every pair distance), M^-1 its exact inverse
+    d = np.linalg.norm(cl.centres[:, None] - cl.centres[None], axis=2)
+    dmin = d[np.triu_indices(cl.nw, 1)].min()
+    Zb = O.assemble(cl, K, 0.5 * dmin, sparse=True)
+    xb, itb, relb = O.bicgstab(Zb, b, Mi, off, tol=1e-12)
+    assert itb == 1 and relb < 1e-12
+    assert np.linalg.norm(xb - O.solve_lu(Zb.toarray(), b)) / np.linalg.norm(xb) < 1e-12
+    # two distinct eigenvalues, no preconditioner (1 x 1 identity blocks)
+    rng = np.random.default_rng(5)
+    n = 12
+    V = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 4 * np.eye(n)
+    D = np.where(np.arange(n) % 2 == 0, 1.5 + 0.5j, -0.7 + 2.0j)
+    A = V @ np.diag(D) @ np.linalg.inv(V)
+    rhs2 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ones = [np.eye(1)] * n
+    x2, it2, rel2 = O.bicgstab(A, rhs2, ones, np.arange(n + 1), tol=1e-10)
+    assert it2 <= 2 and rel2 <= 1e-10
+    assert np.linalg.norm(x2 - np.linalg.solve(A, rhs2)) / np.linalg.norm(x2) < 1e-9
+
+
+def test_bicgstab_first_step_is_galerkin_then_minimal_residual():
+    """One BiCGSTAB iteration from zero is the BiCG step (the new residual s = b - alpha A b is
+    orthogonal to the shadow residual b) followed by the one-dimensional minimal-residual step
+    (r = s - omega A s of least norm): both conditions solved independently (the orthogonality
+    by its scalar equation, the least-norm step by numpy's least squares) give the oracle's first
+    iterate."""
+    rng = np.random.default_rng(6)
+    n = 15
+    A = np.eye(n) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ones = [np.eye(1)] * n
+    x1, it1, _ = O.bicgstab(A, b, ones, np.arange(n + 1), tol=1e-300, max_iter=1)
+    assert it1 == 1
+    Ab = A @ b
+    alpha = (b.conj() @ b) / (b.conj() @ Ab)
+    s = b - alpha * Ab
+    assert abs(b.conj() @ s) < 1e-12 * np.linalg.norm(b) ** 2
+    t = A @ s
+    omega = np.linalg.lstsq(t[:, None], s, rcond=None)[0][0]
+    r1 = s - omega * t
+    assert np.linalg.norm(b - A @ x1 - r1) < 1e-12 * np.linalg.norm(b)
+    assert np.linalg.norm(x1 - (alpha * b + omega * s)) < 1e-12 * np.linalg.norm(x1)
+
+
 def test_gcr_residual_is_the_krylov_least_squares_minimum():
     """After k steps (no restart) the GCR iterate is x_k = M^-1 z_k with z_k minimising
     |b - A M^-1 z| over the Krylov space K_k(A M^-1, b): checked against that definition solved by
