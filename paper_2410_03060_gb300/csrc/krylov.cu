@@ -476,6 +476,149 @@ __global__ void __launch_bounds__(256, 3) k_spmv_wp(KPtr P, const int64_t* __res
     wp_rows<TE, MODE, false>(P, N, m, K, K, E + sbase[pl], nullptr, cm, xs, xst, U, Wv, B, orow, wa, wb);
 }
 
+// The product with packed FP32x2 arithmetic.  As k_spmv_wp, thread (wire, pair q) accumulates
+// right-hand sides 2q and 2q + 1 of every row of its wire, but the two right-hand sides sit in the
+// two halves of each packed operation: the real parts of both in one register pair, the imaginary
+// parts in another, so one complex multiply-add of an E entry into both right-hand sides is four
+// FFMA2.  The CTA copies its tile's E (one contiguous range, the wires being consecutive) into
+// shared memory with each entry expanded to (re, re, im, im), so one 16-byte load gives the two
+// packed operands; it copies the tile's column map too.  The row loop is unrolled to the largest
+// row count of the warp's wires (warp-uniform, rows beyond a wire's own are predicated off), and
+// the gathered values of the next column pair are loaded while the current pair is multiplied.
+constexpr int kWmSmemE = 48 * 1024;  // expanded E entries (16 bytes each)
+constexpr int kWmSmemC = 4 * 1024;   // column-map entries
+__device__ __forceinline__ void wm_xsplit(const float4 v, float2& xr, float2& xi, float2& nxi) {
+  xr = make_float2(v.x, v.z);
+  xi = make_float2(v.y, v.w);
+  nxi = make_float2(-v.y, -v.w);
+}
+__device__ __forceinline__ void wm_fma(float2& ar, float2& ai, const float4 e, const float2 xr, const float2 xi,
+                                       const float2 nxi) {
+  const float2 er = make_float2(e.x, e.y), ei = make_float2(e.z, e.w);
+  ar = __ffma2_rn(er, xr, ar);
+  ar = __ffma2_rn(ei, nxi, ar);
+  ai = __ffma2_rn(er, xi, ai);
+  ai = __ffma2_rn(ei, xr, ai);
+}
+template <int MODE, int MW>
+__device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, const float4* __restrict__ Es,
+                                        const int32_t* __restrict__ cms, const c64* __restrict__ xs, int xst,
+                                        const c64* __restrict__ U, c64* __restrict__ Wv, const c64* __restrict__ B,
+                                        int64_t orow, bool wa, bool wb) {
+  constexpr bool RES = MODE == kResW;
+  float2 ar[MW], ai[MW];
+#pragma unroll
+  for (int ii = 0; ii < MW; ++ii) ar[ii] = ai[ii] = make_float2(0.f, 0.f);
+  float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+  if (K > 0) {
+    x0 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[0] * xst));
+    x1 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[K > 1 ? 1 : 0] * xst));
+  }
+  const float4* er = Es + (int64_t)i0 * K;
+  for (int k = 0; k < K; k += 2) {
+    float4 n0 = x0, n1 = x1;
+    if (k + 2 < K) {
+      n0 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[k + 2] * xst));
+      n1 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[k + 3 < K ? k + 3 : k + 2] * xst));
+    }
+    const bool two = k + 1 < K;
+    float2 xr0, xi0, nxi0, xr1, xi1, nxi1;
+    wm_xsplit(x0, xr0, xi0, nxi0);
+    wm_xsplit(x1, xr1, xi1, nxi1);
+#pragma unroll
+    for (int ii = 0; ii < MW; ++ii)
+      if (ii < mm) {
+        wm_fma(ar[ii], ai[ii], er[ii * K + k], xr0, xi0, nxi0);
+        if (two) wm_fma(ar[ii], ai[ii], er[ii * K + k + 1], xr1, xi1, nxi1);
+      }
+    x0 = n0;
+    x1 = n1;
+  }
+#pragma unroll
+  for (int ii = 0; ii < MW; ++ii)
+    if (ii < mm) {
+      if (wa) {
+        const int64_t o = orow + i0 + ii;
+        const c64 v = U[o] + mkc<float>(ar[ii].x, ai[ii].x);
+        Wv[o] = RES ? B[o] - v : v;
+      }
+      if (wb) {
+        const int64_t o = orow + N + i0 + ii;
+        const c64 v = U[o] + mkc<float>(ar[ii].y, ai[ii].y);
+        Wv[o] = RES ? B[o] - v : v;
+      }
+    }
+}
+template <typename TE, int MODE = kStepW, int MINB = 3>
+__global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
+                                                    const TE* __restrict__ E, const c64* __restrict__ U,
+                                                    const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
+                                                    const c64* __restrict__ B, int RQ, int WB) {
+  constexpr bool ALL = MODE != kStepW;
+  if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+  extern __shared__ __align__(16) unsigned char sm_wm[];
+  float4* Es = reinterpret_cast<float4*>(sm_wm);
+  int32_t* Cs = reinterpret_cast<int32_t*>(sm_wm + kWmSmemE);
+  __shared__ int sK[kWpMaxWires], sm_m[kWpMaxWires], seo[kWpMaxWires], sco[kWpMaxWires];
+  const int64_t N = P.N;
+  const int64_t p0 = (int64_t)blockIdx.x * WB;
+  const int nwt = (int)min((int64_t)min(WB, kWpMaxWires), nw - p0);
+  // the tile's E entries and column-map entries are contiguous ranges
+  const int64_t e0 = lay.rowbase[p0], c0 = lay.cmbase[p0];
+  const int64_t ne = lay.rowbase[p0 + nwt] - e0, nc = lay.cmbase[p0 + nwt] - c0;
+  const bool fits = ne * (int64_t)sizeof(float4) <= kWmSmemE && nc * (int64_t)sizeof(int32_t) <= kWmSmemC;
+  if (threadIdx.x < nwt) {
+    const int64_t p = p0 + threadIdx.x;
+    sK[threadIdx.x] = lay.K[p];
+    sm_m[threadIdx.x] = (int)(off[p + 1] - off[p]);
+    seo[threadIdx.x] = (int)(lay.rowbase[p] - e0);
+    sco[threadIdx.x] = (int)(lay.cmbase[p] - c0);
+  }
+  if (fits) {
+    const int ne4 = (int)ne, nc4 = (int)nc;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < ne4; e += blockDim.x) {
+      const c64 v = ELoad<float, TE>::ld(E + e0 + e);
+      Es[e] = make_float4(v.re, v.re, v.im, v.im);
+    }
+    for (int c = threadIdx.x; c < nc4; c += blockDim.x) Cs[c] = lay.colmap[c0 + c];
+  }
+  __syncthreads();
+  const int pl = (int)threadIdx.x / RQ, q = (int)threadIdx.x % RQ;
+  const int ra = blockIdx.y * 2 * RQ + 2 * q, rb = ra + 1;
+  const bool valid = pl < nwt && ra < P.R;
+  // warp-uniform row bound: the largest row count among the warp's wires
+  const int mw = __reduce_max_sync(0xffffffffu, valid ? sm_m[pl] : 0);
+  if (!valid) return;
+  const bool wa = ALL || P.active[ra];
+  const bool wb = rb < P.R && (ALL || P.active[rb]);
+  if (!wa && !wb) return;
+  const int64_t p = p0 + pl;
+  const int K = sK[pl], m = sm_m[pl];
+  const c64* xs = Xt + ra;
+  const int64_t orow = (int64_t)ra * N + off[p];
+  if (!fits) {
+    wp_rows<TE, MODE, false>(P, N, m, K, K, E + lay.rowbase[p], nullptr, lay.colmap + lay.cmbase[p], xs, xst, U,
+                             Wv, B, orow, wa, wb);
+    return;
+  }
+  const float4* er = Es + seo[pl];
+  const int32_t* cms = Cs + sco[pl];
+  switch (mw) {
+    case 1: wm_rows<MODE, 1>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 2: wm_rows<MODE, 2>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 3: wm_rows<MODE, 3>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 4: wm_rows<MODE, 4>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 5: wm_rows<MODE, 5>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 6: wm_rows<MODE, 6>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 7: wm_rows<MODE, 7>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    default:
+      for (int i0 = 0; i0 < m; i0 += 8)
+        wm_rows<MODE, 8>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
+      break;
+  }
+}
+
 // Tile shape of k_spmv_w for R right-hand sides: RG right-hand sides per CTA (all of them up to
 // 64, else balanced groups of at most 64) and WB = 256 / RG wires per CTA.
 struct WireTile {
@@ -1148,6 +1291,34 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
         k_spmv_w<TV, TE, RS ? kResW : kStepW, false><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
             P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB);
         break;
+      case kWire + 4:  // packed FP32x2 arithmetic, E expanded and the column map in shared memory
+      case kWire + 5:  // the same with four CTAs per SM (fewer registers)
+        if constexpr (std::is_same<TV, float>::value) {
+          if (ws->Xt && R <= 256) {
+            const int xst = R + (R & 1);
+            const int RQ = std::min(32, (int)ceil_div(R, 2));
+            const int WBp = std::max(1, std::min(kWpMaxWires, 256 / RQ));
+            const int T = std::max(8, std::min(64, (int)((48 * 1024 / sizeof(cplx<TV>)) / (xst + 1)) / 8 * 8));
+            ctx->prof_end(SWM_K_APPLY);
+            ctx->prof_begin(SWM_K_TRANSPOSE);
+            k_rhs_minor_all<TV, RS><<<(unsigned)ceil_div(N, T), 256, sizeof(cplx<TV>) * T * (xst + 1), s>>>(
+                P, src, ws->Xt, xst, T);
+            ctx->prof_end(SWM_K_TRANSPOSE);
+            ctx->prof_begin(SWM_K_APPLY);
+            SWM_LAUNCHED();
+            const dim3 g((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(R, 2 * RQ));
+            if (b == kWire + 4)
+              k_spmv_wm<TE, RS ? kResW : kStepW, 3><<<g, 256, kWmSmemE + kWmSmemC, s>>>(
+                  P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, xst, dst, Bv, RQ, WBp);
+            else
+              k_spmv_wm<TE, RS ? kResW : kStepW, 4><<<g, 256, kWmSmemE + kWmSmemC, s>>>(
+                  P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, xst, dst, Bv, RQ, WBp);
+            break;
+          }
+        }
+        k_spmv_w<TV, TE, RS ? kResW : kStepW, false><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+            P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB);
+        break;
       case kWire + 1:  // the same with five CTAs per SM (fewer registers)
         if (ws->Xt) {
           k_rhs_minor<TV, RS><<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(R, 32)), 256, 0, s>>>(P, src,
@@ -1180,6 +1351,14 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   };
   auto launch_product = [&](cudaStream_t s, int b) { return product(s, b, std::false_type{}); };
   auto launch_residual = [&](cudaStream_t s, int b) { return product(s, b, std::true_type{}); };
+  if constexpr (std::is_same<TV, float>::value) {
+    if (multi && ws->Xt) {
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 3>, ctx->smem_optin));
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 3>, ctx->smem_optin));
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 4>, ctx->smem_optin));
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 4>, ctx->smem_optin));
+    }
+  }
   const size_t dots_smem = 2 * sizeof(cplx<TV>) * (size_t)P.chunk;
   if (dots_smem > 48 * 1024) SWM_CK(allow_max_dyn_smem((const void*)k_dots<TV, TQ>, ctx->smem_optin));
   // back substitution stages the triangle in shared memory when it fits
@@ -1215,7 +1394,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
     const int forced = ctx->product_form;
     if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || forced == kWire + 1 ||
-        forced == kWire + 3 || (forced == kMinor && ws->Xt)) {
+        forced == kWire + 3 || forced == kWire + 4 || forced == kWire + 5 || (forced == kMinor && ws->Xt)) {
       rb = forced;
     } else if (found) {
       rb = found;
@@ -1229,7 +1408,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3}) {
+      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3, kWire + 4, kWire + 5}) {
         if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
         if (b == kMinor && !ws->Xt) continue;
         SWM_TRY(launch_product(st, b));

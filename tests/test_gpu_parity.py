@@ -495,23 +495,26 @@ def test_split_step_path_matches_oracle(monkeypatch):
                 assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
 
 
-@pytest.mark.parametrize("form", [4, 8, 16, 32, 64, 65, 67])
+@pytest.mark.parametrize("form", [4, 8, 16, 32, 64, 65, 67, 68, 69])
 def test_every_product_form_matches_oracle(monkeypatch, form):
     """Each form of the many-incidence product, forced (SWM_PRODUCT_FORM) on the large-system GMRES
     step: 4/8/16 incidences per read of E, 32 the incidence-minor form, 64 and 65 the wire-tiled
-    form (65: five CTAs per SM; 67: two incidences per thread, E of the tile in shared memory).
-    A cloud with every segment count 2..16 (wires of up to 15 rows, two row groups in the
-    wire-tiled form) and ragged tiles; 37 and 70 incidences (one group of 37, two groups of 35 in
-    the wire-tiled form); currents against the oracle's LU solution and the RCS within 0.1 dB."""
+    form (65: five CTAs per SM; 67: two incidences per thread, E of the tile in shared memory;
+    68 and 69: the same with packed FP32x2 arithmetic, three and four CTAs per SM).
+    Clouds with every segment count 2..16 (wires of up to 15 rows, two row groups in the
+    wire-tiled form) and ragged tiles, one dense (a tile's E exceeds the shared-memory budget, so
+    the forms that stage it read it from global memory) and one sparse (it fits); 37 and 70
+    incidences (one group of 37, two groups of 35 in the wire-tiled form); currents against the
+    oracle's LU solution and the RCS within 0.1 dB."""
     from paper_2410_03060_gb300 import swm
 
     monkeypatch.setenv("SWM_SPLIT_ROWS", "0")
     monkeypatch.setenv("SWM_PRODUCT_FORM", str(form))
-    cl = _mixed_cloud(nw=61, side=3.0, seed=45)
     obs = observations_phi_cut(24)
     g = np.random.default_rng(8)
     many = lambda n: np.stack([g.uniform(0, np.pi, n), g.uniform(0, 2 * np.pi, n), g.uniform(0, np.pi, n)], 1)
-    for n_inc in (37, 70):
+    for cl, n_inc in ((_mixed_cloud(nw=61, side=3.0, seed=45), 37), (_mixed_cloud(nw=61, side=3.0, seed=45), 70),
+                      (_mixed_cloud(nw=150, side=9.0, seed=46), 37)):
         inc = many(n_inc)
         Z = O.assemble(cl, K, 1.2, sparse=False)
         X = O.solve_lu(Z, O.rhs(cl, K, inc))
