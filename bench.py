@@ -299,13 +299,41 @@ def solve_steps(iterations, restart):
     return steps_j, cycles
 
 
-def class_bytes(cls, st, prec, n_rhs, restart):
+def class_bytes_bicgstab(cls, st, prec, n_rhs):
+    """Algorithmic bytes of one BiCGSTAB solve per kernel class.  A step: two products (E, column
+    map and row descriptors once for all incidences, the source read and the image written), the
+    two direction updates with their incidence-minor copies (p = r + beta (p - omega v): r, p, v
+    read, p and its copy written; s = r - alpha v: r, v read, s and its copy written), the inner
+    products (rh^H v; t^H s and t^H t) and y += alpha p + omega s, r = s - omega t with rh^H r and
+    |r| (y, p, s, t, rh read, y and r written).  Each true-residual check: y copied to
+    incidence-minor order, the residual product (b read as well) and |r|."""
+    esz = 16 if prec == "c128" else 8
+    N, R = st["n"], n_rhs
+    vec = R * N * esz
+    steps = st["iterations"]
+    checks = st["restarts"] + 2
+    mat = st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N
+    xt = prec != "c128" and R >= 2
+    if cls == "apply":
+        return steps * 2 * (mat + 2 * vec) + checks * (mat + 3 * vec)
+    if cls == "transpose":
+        return steps * ((5 + 4) * vec if xt else (4 + 3) * vec) + (checks * 2 * vec if xt else 0)
+    if cls == "dots":
+        return steps * 4 * vec + checks * vec
+    if cls == "update":
+        return steps * 7 * vec
+    return None
+
+
+def class_bytes(cls, st, prec, n_rhs, restart, solver="gmres"):
     """Algorithmic bytes of one solve for a kernel class of the per-kernel GMRES step.
     Product: E values, column map and row descriptors once per block of incidences sharing a
     read, u read and w written per incidence, and per restart cycle the residual product
     (B and y read, W written); the transpose to incidence-minor order is not counted.  Delayed
     Gram-Schmidt at step j: dots read Q_<j, u and w ((j + 2) vectors; the closing pass of a cycle
     Q_<j and u), update reads Q_<j, u, w and writes q_j and the next u ((j + 4) vectors)."""
+    if solver == "bicgstab":
+        return class_bytes_bicgstab(cls, st, prec, n_rhs)
     esz = 16 if prec == "c128" else 8
     N, R = st["n"], n_rhs
     vec = R * N * esz
@@ -339,7 +367,7 @@ def fp32_peak_tflops(pk):
     return N_SM * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per_step_units=None):
+def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per_step_units=None, solver="gmres"):
     """Achieved algorithmic rate of one kernel class over ``steps`` profiled steps."""
     if prof_ms <= 0 or launches <= 0:
         return None
@@ -354,7 +382,7 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
                 "peak_source": ("FP32 peak = 152 SMs x 128 lanes x 2 flops x max SM clock" if prec != "c128"
                                 else "nominal FP64 peak"),
                 "flops_per_eval": FP32_FLOPS_PER_EVAL, "evals_per_launch": st["fill_evals"]}
-    b = class_bytes(cls, st, prec, n_rhs, restart)
+    b = class_bytes(cls, st, prec, n_rhs, restart, solver)
     if b is None:
         return {"kernel": cls, "bound": "other", "per_launch_ms": per_launch_ms}
     work = b * steps
@@ -379,7 +407,14 @@ PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "app
                    "far", "gmres"]
 
 
-def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps=None):
+def workload_text(name, solver, restart):
+    t = WORKLOADS[name]["text"]
+    if solver == "bicgstab":
+        return t.replace("GMRES(50) 1e-6", "BiCGSTAB 1e-6 (true residual)")
+    return t.replace("GMRES(50)", f"GMRES({restart})")
+
+
+def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps=None, solver=None):
     """Time workload ``name`` through swm_run (device inputs), then: the class shares (one
     profiled step per class), the dominant and the named classes' rooflines (a separate profiled
     pass), the end-to-end step from pinned host buffers, and the plain FP64 path (its RCS gates the
@@ -390,6 +425,7 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
     from paper_2410_03060_gb300 import swm
 
     w = WORKLOADS[name]
+    solver = solver or args.solver
     cl, inc, obs = workload_inputs(name, rank)
     R, N = inc.shape[0], cl.n_unknowns
     prec_id = swm.SWM_C64 if args.precision == "c64" else swm.SWM_C128
@@ -400,6 +436,7 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
     sigma = torch.zeros(shape, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     ctx = swm.swm_create(local)
+    swm.swm_set_solver(ctx, solver)
     K = steps or args.steps
 
     def step(c=None, prec=prec_id, inputs=dev, out=sigma):
@@ -457,7 +494,8 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
     s = swm.swm_get_stats(ctx)
     swm.swm_profile(ctx, "none")
     pk = peaks()
-    roof = roofline_of(dominant, st, s["prof_ms"], s["prof_launches"], args.precision, R, restart, rsteps, pk)
+    roof = roofline_of(dominant, st, s["prof_ms"], s["prof_launches"], args.precision, R, restart, rsteps, pk,
+                       solver=solver)
     if roof is not None:
         roof["class"] = dominant
         roof["profiled_steps"] = rsteps
@@ -465,9 +503,10 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
     extra_roofs = {}
     for c in ("fill_mutual", "apply", "transpose", "dots", "update"):
         if c != dominant and prof[c][1] > 0:
-            extra_roofs[c] = roofline_of(c, st, prof[c][0], prof[c][1], args.precision, R, restart, 1, pk)
+            extra_roofs[c] = roofline_of(c, st, prof[c][0], prof[c][1], args.precision, R, restart, 1, pk,
+                                         solver=solver)
 
-    rec = {"workload": w["text"], "nw": cl.nw, "unknowns": N, "incidences": R, "blocks": st["nb"],
+    rec = {"workload": workload_text(name, solver, restart), "solver": solver, "nw": cl.nw, "unknowns": N, "incidences": R, "blocks": st["nb"],
            "ms_per_step": ms_step, "value_local": N * R / (ms_step * 1e-3), "gpu_launches": int(launches),
            "iterations": st["iterations"], "restarts": st["restarts"], "rel_residual": st["rel_residual"],
            "step_rhs_block": st["step_rhs_block"],
@@ -498,6 +537,7 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
     if with_fp64:
         # the plain FP64 path on the same cloud: its RCS gates the fast path; a few steps timed
         ctx64 = swm.swm_create(local)
+        swm.swm_set_solver(ctx64, solver)
         sig64 = torch.zeros_like(sigma)
         step(c=ctx64, prec=swm.SWM_C128, out=sig64)
         torch.cuda.synchronize()
@@ -534,7 +574,7 @@ def run_ours(args):
     side = None
     if name == "learned" and not args.no_mid:
         side, _ = measure("mid", args, local, world, rank, with_e2e=False, with_fp64=True,
-                          steps=max(args.steps, 200))
+                          steps=max(args.steps, 200), solver="gmres")
 
     # max over ranks, units over all ranks
     (ms_step, e2e_ms, ms64), total_units = aggregate_over_ranks([rec["ms_per_step"], rec["e2e_ms"], rec["ms64"]],
@@ -550,7 +590,8 @@ def run_ours(args):
         "data": "synthetic (seeded wire clouds)",
         "config": {"workload": rec["workload"], "nw": rec["nw"], "unknowns": rec["unknowns"],
                    "incidences": rec["incidences"], "blocks": rec["blocks"], "precision": args.precision,
-                   "restart": args.restart, "tol": TOL,
+                   "solver": rec["solver"], "restart": args.restart if rec["solver"] == "gmres" else None,
+                   "tol": TOL,
                    "l2": "inputs larger than L2 (E and the Krylov basis are GBs); a 256 MB write also flushes "
                          "L2 between steps",
                    "parallelism": f"{world} independent clouds (one per GPU)"},
@@ -613,6 +654,7 @@ def run_scale(args):
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cl.centres, cl.dirs, cl.lengths, cl.radii, cl.nseg)]
     mono = torch.zeros((n_inc, 2), dtype=torch.float64, device="cuda")
     ctx = swm.swm_create(0)
+    swm.swm_set_solver(ctx, args.solver)
     restart = args.restart
 
     def step():
@@ -625,7 +667,7 @@ def run_scale(args):
     step()
     torch.cuda.synchronize()
     res = {}
-    for cls in ("fill_mutual", "apply", "dots", "update", "finish", "far", "pairs", "fill_self"):
+    for cls in ("fill_mutual", "apply", "transpose", "dots", "update", "far", "pairs", "fill_self"):
         swm.swm_profile(ctx, cls)
         step()
         torch.cuda.synchronize()
@@ -641,57 +683,19 @@ def run_scale(args):
         ts.append(time.perf_counter() - t)
     st = swm.swm_get_stats(ctx)
     pk = peaks()
-    mhz = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = N_SM * 128 * 2 * mhz * 1e6 / 1e12
-    fill_ms, _ = res["fill_mutual"]
-    fill_tf = st["fill_evals"] * FP32_FLOPS_PER_EVAL / (fill_ms * 1e-3) / 1e12
-    # block-sparse product: E (+ column map, row descriptors) once per block of right-hand sides
-    # sharing a read, u read and w written per right-hand side; a transpose to incidence-minor
-    # order is implementation traffic, not counted
-    esz, N, R = 8, st["n"], n_inc
-    it = st["iterations"]
-    steps_j, closing_j = [], []
-    while it > 0:
-        c = min(restart, it)
-        steps_j += list(range(c))
-        closing_j.append(c)
-        it -= c
-    rbs = st["step_rhs_block"]
-    rb = (32 if R >= 24 else 16) if rbs == 32 else max(1, rbs)
-    nblk = -(-R // rb) if R > 1 else 1
-    mat = (st["nnz_offd"] * esz + st["ncm_offd"] * 4 + 16 * N) * nblk
-    apply_bytes = sum(mat + 2 * R * N * esz for _ in steps_j)
-    apply_ms, apply_n = res["apply"]
-    # the residual products of the restarts are timed with the class too: count their bytes
-    apply_bytes += (st["restarts"] + 1) * (st["nnz_offd"] * esz + st["ncm_offd"] * 4) * R
-    gbs = apply_bytes / (apply_ms * 1e-3) / 1e9
-    # delayed Gram-Schmidt: dots read Q_<j, u, w; update reads them and writes q_j, u; the closing
-    # dots of a cycle read Q_<j and u
-    gs_bytes = sum((2 * j + 6) * R * N * esz for j in steps_j) + sum((j + 1) * R * N * esz for j in closing_j)
-    gs_ms = res["dots"][0] + res["update"][0]
-    gs_gbs = gs_bytes / (gs_ms * 1e-3) / 1e9
+    roofs = {c: roofline_of(c, st, res[c][0], res[c][1], "c64", n_inc, restart, 1, pk, solver=args.solver)
+             for c in ("fill_mutual", "apply", "transpose", "dots", "update") if res[c][1] > 0}
+    N = st["n"]
     out = {
         "kind": "scale", "workload": args.workload, "description": w["text"], "nw": cl.nw, "unknowns": N,
-        "blocks": st["nb"], "nnz": st["nnz"], "incidences": n_inc, "restart": restart, "iterations": st["iterations"],
-        "converged": st["converged"], "rel_residual": st["rel_residual"], "rc": rc,
+        "blocks": st["nb"], "nnz": st["nnz"], "incidences": n_inc, "solver": args.solver, "restart": restart,
+        "iterations": st["iterations"], "restarts": st["restarts"], "converged": st["converged"],
+        "rel_residual": st["rel_residual"], "rc": rc,
         "ms_per_step": 1e3 * float(np.median(ts)),
         "value": N * n_inc / float(np.median(ts)), "unit": UNIT,
         "phase_ms": {k: st[k] for k in ("ms_neighbour", "ms_fill", "ms_precond", "ms_rhs", "ms_solve", "ms_rcs")},
-        "fill_roofline": {"bound": "alu", "kernel": "k_mutual_blocks<float>", "evals": st["fill_evals"],
-                          "flops_per_eval": FP32_FLOPS_PER_EVAL, "ms": fill_ms, "achieved": fill_tf,
-                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": fill_tf / fp32_peak,
-                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"},
-        "apply_roofline": {"bound": "hbm",
-                           "kernel": "k_rhs_minor + k_spmv_t (block-sparse product, one lane per incidence)"
-                           if rbs == 32 else "k_spmv (block-sparse product, %d incidences per read of E)" % rb,
-                           "launches": apply_n, "ms": apply_ms, "bytes": apply_bytes, "achieved": gbs,
-                           "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                           "frac": gbs / pk.get("hbm_gbs", 6800.0), "peak_source": "of measured (MEASURED_PEAKS.json)"},
-        "gs_roofline": {"bound": "hbm", "kernel": "k_dots + k_update (delayed Gram-Schmidt)", "ms": gs_ms,
-                        "bytes": gs_bytes, "achieved": gs_gbs, "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                        "frac": gs_gbs / pk.get("hbm_gbs", 6800.0),
-                        "peak_source": "of measured (MEASURED_PEAKS.json)"},
-        "step_rhs_block": rbs,
+        "rooflines": roofs,
+        "step_rhs_block": st["step_rhs_block"],
         "kernel_ms_per_step": {k: v[0] for k, v in res.items()},
     }
     print(json.dumps(out))
@@ -995,6 +999,8 @@ def main():
     ap.add_argument("--no-mid", action="store_true", help="skip the 10,000-wire side measurement")
     ap.add_argument("--inc", type=int, default=0, help="incidences of a larger workload (default: its own)")
     ap.add_argument("--restart", type=int, default=RESTART)
+    ap.add_argument("--solver", choices=["gmres", "bicgstab"], default="bicgstab",
+                    help="Krylov method of the solve (GMRES(restart) or BiCGSTAB)")
     ap.add_argument("--nw", type=int, default=0, help="wire count of a larger workload (default: its own)")
     ap.add_argument("--same-density", action="store_true",
                     help="with --nw on the learned workload: scale the cluster width to keep the wire density")

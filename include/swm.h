@@ -205,9 +205,16 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision);
  * SWM_SOLVER_GCR -- restarted GCR, the method the paper names (Sec. II-B, after Eq. neardef):
  * per step one product, two Gram-Schmidt passes over the stored images A p_i, and an update of
  * the iterate and of the residual, whose norm is then exact; it stores two bases (p_i and A p_i).
+ * SWM_SOLVER_BICGSTAB -- BiCGSTAB (van der Vorst 1992), a short-recurrence alternative for the
+ * same preconditioned system: per step two products and a fixed number of vector passes (no
+ * basis, so `restart` is ignored); max_iter counts its steps (two products each).  It stops when
+ * the recursive residual meets tol, then forms the true residual b - Z x and restarts from it
+ * where that is still above tol; the reported residuals are the true ones.  Not used with
+ * precision SWM_BF16, whose refinement runs GMRES inside.
  * Applies to the following swm_solve calls of this context; SWM_EINVAL for another value. */
 #define SWM_SOLVER_GMRES 0
 #define SWM_SOLVER_GCR 1
+#define SWM_SOLVER_BICGSTAB 2
 int swm_set_solver(swm_ctx* ctx, int method);
 
 /* Solve Z jt = b for n_inc >= 1 incidences (Eq. (4) right-hand sides), inc = n_inc x 3 float64

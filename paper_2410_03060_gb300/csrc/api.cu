@@ -570,7 +570,8 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
 
 int swm_set_solver(swm_ctx* ctx, int method) {
   if (!ctx) return SWM_EINVAL;
-  if (method != SWM_SOLVER_GMRES && method != SWM_SOLVER_GCR) return ctx->fail(SWM_EINVAL, "bad solver");
+  if (method != SWM_SOLVER_GMRES && method != SWM_SOLVER_GCR && method != SWM_SOLVER_BICGSTAB)
+    return ctx->fail(SWM_EINVAL, "bad solver");
   ctx->solver = method;
   return SWM_OK;
 }
@@ -655,8 +656,9 @@ static int solve_impl(swm_ctx* ctx, int n_inc, const double* inc, double tol, in
   }
   ctx->phase_begin(swm_ctx::PH_SOLVE);
   int rc = ctx->bf16 ? refine_solve(ctx, frames, tol, restart, max_iter)
-           : ctx->solver == SWM_SOLVER_GCR ? gcr_solve(ctx, tol, restart, max_iter)
-                                           : gmres_solve(ctx, tol, restart, max_iter);
+           : ctx->solver == SWM_SOLVER_GCR      ? gcr_solve(ctx, tol, restart, max_iter)
+           : ctx->solver == SWM_SOLVER_BICGSTAB ? bicgstab_solve(ctx, tol, max_iter)
+                                                : gmres_solve(ctx, tol, restart, max_iter);
   ctx->phase_end(swm_ctx::PH_SOLVE);
   ctx->guess = nullptr;
   ctx->rhs_frames = nullptr;

@@ -294,6 +294,7 @@ bool all_device_memory(const void* const* ptrs, int n);
 void set_stateless_error(const std::string& msg);
 // krylov.cu: a6
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
+int bicgstab_solve(swm_ctx* ctx, double tol, int max_iter);
 // row descriptors of E (built once per build) and x = M^-1 y into ctx->Xv
 int ensure_rowinfo(swm_ctx* ctx);
 // y = y0 (ctx->guess, complex128) or 0 at the start of a solve, in the vector precision

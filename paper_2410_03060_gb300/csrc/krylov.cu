@@ -1557,6 +1557,543 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   return hs.all_conv ? SWM_OK : SWM_ENOTCONV;
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// BiCGSTAB on the same right-preconditioned system A y = b (A = I + E, x = M^-1 y): a
+// short-recurrence Krylov method (van der Vorst 1992) whose step is two products and a fixed
+// number of vector passes, so its cost per step does not grow with the step index as the
+// Gram-Schmidt passes of GMRES do.  Each right-hand side is an independent instance; all share
+// every pass over E.  Per step, with the shadow residual rh:
+//   k_bi_dir (p) : p = r + beta (p - omega v)   (p = r and rh = r after a (re)start)
+//   product      : v = A p
+//   k_bi_rv      : alpha = rho / (rh^H v)
+//   k_bi_dir (s) : s = r - alpha v
+//   product      : t = A s
+//   k_bi_ts      : omega = (t^H s) / (t^H t)
+//   k_bi_xr      : y += alpha p + omega s,  r = s - omega t,  rho' = rh^H r,  |r|;
+//                  beta = (rho' / rho)(alpha / omega)
+// The two direction kernels also write their result right-hand-side minor (Xt) for the product's
+// gathers.  Inner products: each thread sums its run of rows in the vector type (as the GMRES dots
+// do), the CTA's threads and then the CTAs are added in float64, the CTAs in a fixed order by the
+// last CTA of each right-hand side to arrive, which also updates that right-hand side's scalars.  A
+// right-hand side stops when its recursive residual meets tol (or on a breakdown); when none is
+// left the true residual b - A y is formed and those above tol restart from it.
+struct BState {
+  int nactive;  // right-hand sides still iterating
+  int numeric;  // a NaN/Inf appeared
+  int pad[6];
+};
+static_assert(sizeof(BState) == sizeof(KState), "poll slot layout");
+struct BPtr {
+  BState* st;
+  int* active;        // [R] 1 while iterating
+  int* fresh;         // [R] the next direction starts from r (and rh = r)
+  int* its;           // [R] steps taken
+  unsigned* counter;  // [R] CTAs of the current pass that have arrived
+  double* bnorm;      // [R]
+  double* resid;      // [R] relative residual: recursive while iterating, true after a check
+  c128 *rho, *alpha, *omega, *beta;  // [R]
+  c128* part;         // [R][nchunk][2]
+  int64_t N;
+  int R, nchunk, chunk, max_iter;
+  double tol;
+};
+
+__device__ bool bi_last_cta(const BPtr& B, int r) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&B.counter[r], 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+
+// Sums of a CTA (kRows threads) of two complex values, on thread 0.
+__device__ void bi_block_sum2(c128& a, c128& b) {
+  __shared__ double sh[4][kRows / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double v[4] = {warp_sum(a.re), warp_sum(a.im), warp_sum(b.re), warp_sum(b.im)};
+  if (lane == 0)
+    for (int k = 0; k < 4; ++k) sh[k][w] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kRows / 32; ++i) s += sh[k][i];
+      v[k] = s;
+    }
+    a = mkc(v[0], v[1]);
+    b = mkc(v[2], v[3]);
+  }
+}
+
+// The CTA's two partial sums to part[r][chunk]; the last CTA of r returns true with the totals
+// (summed over the chunks in order) on thread 0 and resets the arrival counter.
+__device__ bool bi_reduce2(const BPtr& B, int r, c128 a, c128 b, c128& ta, c128& tb) {
+  bi_block_sum2(a, b);
+  c128* part = B.part + ((int64_t)r * B.nchunk) * 2;
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+  if (!bi_last_cta(B, r)) return false;
+  if (threadIdx.x < 32) {
+    ta = sum_partials_c(part, 2, B.nchunk, threadIdx.x);
+    tb = sum_partials_c(part + 1, 2, B.nchunk, threadIdx.x);
+  }
+  if (threadIdx.x == 0) B.counter[r] = 0;
+  return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ bool finite_z(c128 z) { return isfinite(z.re) && isfinite(z.im); }
+// acc += conj(a) b and n += |b|^2 in the vector type (a thread's run of rows); the sums over
+// threads and CTAs are float64
+template <typename T>
+__device__ __forceinline__ void bi_acc(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+  acc.re = fma(a.re, b.re, fma(a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(-a.im, b.re, acc.im));
+}
+template <typename T>
+__device__ __forceinline__ void bi_nrm(T& acc, cplx<T> b) {
+  acc = fma(b.re, b.re, fma(b.im, b.im, acc));
+}
+__device__ __forceinline__ c128 bi_cdiv(c128 a, c128 b) {
+  const double s = 1.0 / (b.re * b.re + b.im * b.im);
+  return s * cmulc(b, a);
+}
+
+// the product kernels' step state (never done: step 0 of 1) and every right-hand side active for
+// the residual
+__global__ void k_bi_init(KState* k, int* pact, int R) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    KState z{};
+    z.jmax = 1;
+    *k = z;
+  }
+  if (i < R) pact[i] = 1;
+}
+
+__device__ void bi_stop(const BPtr& B, int r, bool numeric) {
+  B.active[r] = 0;
+  atomicSub(&B.st->nactive, 1);
+  if (numeric) B.st->numeric = 1;
+}
+
+// p = r + beta (p - omega v), or p = r and rh = r after a (re)start (SMODE false); s = r - alpha v
+// (SMODE true).  T rows x all right-hand sides per CTA; with XT the result is also written
+// right-hand-side minor, Xt[n][0 .. xst), through a shared-memory tile (inactive right-hand sides
+// and the padding column as zero).
+template <typename TV, bool SMODE, bool XT>
+__global__ void __launch_bounds__(256) k_bi_dir(BPtr B, const cplx<TV>* __restrict__ Rv, cplx<TV>* __restrict__ Rh,
+                                                cplx<TV>* __restrict__ Pv, const cplx<TV>* __restrict__ Vv,
+                                                cplx<TV>* __restrict__ Out, cplx<TV>* __restrict__ Xt, int xst,
+                                                int T) {
+  extern __shared__ __align__(16) unsigned char sm_bi[];
+  cplx<TV>* tile = reinterpret_cast<cplx<TV>*>(sm_bi);  // [T][xst + 1]
+  const int ts = xst + 1;
+  const int64_t N = B.N;
+  const int64_t n0 = (int64_t)blockIdx.x * T;
+  const int cnt = (int)min((int64_t)T, N - n0);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+  for (int r = wp; r < B.R; r += nwp) {
+    const bool act = B.active[r] != 0;
+    const int64_t base = (int64_t)r * N + n0;
+    if (act) {
+      if (SMODE) {
+        const cplx<TV> a = ccast<TV>(B.alpha[r]);
+        for (int t = lane; t < cnt; t += 32) {
+          const cplx<TV> o = Rv[base + t] - a * Vv[base + t];
+          Out[base + t] = o;
+          if (XT) tile[t * ts + r] = o;
+        }
+      } else if (B.fresh[r]) {
+        for (int t = lane; t < cnt; t += 32) {
+          const cplx<TV> o = Rv[base + t];
+          Rh[base + t] = o;
+          Out[base + t] = o;
+          if (XT) tile[t * ts + r] = o;
+        }
+      } else {
+        const cplx<TV> be = ccast<TV>(B.beta[r]), om = ccast<TV>(B.omega[r]);
+        for (int t = lane; t < cnt; t += 32) {
+          const cplx<TV> o = Rv[base + t] + be * (Pv[base + t] - om * Vv[base + t]);
+          Out[base + t] = o;
+          if (XT) tile[t * ts + r] = o;
+        }
+      }
+    } else if (XT) {
+      for (int t = lane; t < cnt; t += 32) tile[t * ts + r] = mkc<TV>(0, 0);
+    }
+  }
+  if (!XT) return;
+  __syncthreads();
+  cplx<TV>* out = Xt + n0 * xst;
+  for (int t = wp; t < cnt; t += nwp)
+    for (int r = lane; r < xst; r += 32) out[(int64_t)t * xst + r] = r < B.R ? tile[t * ts + r] : mkc<TV>(0, 0);
+}
+
+// alpha = rho / (rh^H v)
+template <typename TV>
+__global__ void __launch_bounds__(kRows) k_bi_rv(BPtr B, const cplx<TV>* __restrict__ Rh,
+                                                 const cplx<TV>* __restrict__ Vv) {
+  const int r = blockIdx.y;
+  if (!B.active[r]) return;
+  const int64_t N = B.N, n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(N, n0 + B.chunk);
+  const cplx<TV>* h = Rh + (int64_t)r * N;
+  const cplx<TV>* v = Vv + (int64_t)r * N;
+  cplx<TV> a = mkc<TV>(0, 0);
+#pragma unroll 4
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += kRows) bi_acc(a, h[n], v[n]);
+  c128 rv, dummy;
+  if (!bi_reduce2(B, r, ccast<double>(a), mkc(0.0, 0.0), rv, dummy)) return;
+  B.fresh[r] = 0;
+  const double mag = sqrt(rv.re * rv.re + rv.im * rv.im);
+  if (!finite_z(rv)) {
+    bi_stop(B, r, true);
+  } else if (mag == 0.0) {
+    bi_stop(B, r, false);  // breakdown: the true-residual check restarts it
+  } else {
+    B.alpha[r] = bi_cdiv(B.rho[r], rv);
+  }
+}
+
+// omega = (t^H s) / (t^H t)
+template <typename TV>
+__global__ void __launch_bounds__(kRows) k_bi_ts(BPtr B, const cplx<TV>* __restrict__ Tv,
+                                                 const cplx<TV>* __restrict__ Sv) {
+  const int r = blockIdx.y;
+  if (!B.active[r]) return;
+  const int64_t N = B.N, n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(N, n0 + B.chunk);
+  const cplx<TV>* t = Tv + (int64_t)r * N;
+  const cplx<TV>* s = Sv + (int64_t)r * N;
+  cplx<TV> ts = mkc<TV>(0, 0);
+  TV tt = 0;
+#pragma unroll 4
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += kRows) {
+    const cplx<TV> tv = t[n];
+    bi_acc(ts, tv, s[n]);
+    bi_nrm(tt, tv);
+  }
+  c128 sts, stt;
+  if (!bi_reduce2(B, r, ccast<double>(ts), mkc((double)tt, 0.0), sts, stt)) return;
+  if (!finite_z(sts) || !isfinite(stt.re)) {
+    bi_stop(B, r, true);
+    return;
+  }
+  B.omega[r] = stt.re > 0.0 ? (1.0 / stt.re) * sts : mkc(0.0, 0.0);
+}
+
+// y += alpha p + omega s, r = s - omega t; rho' = rh^H r and |r| decide the next step
+template <typename TV>
+__global__ void __launch_bounds__(kRows) k_bi_xr(BPtr B, cplx<TV>* __restrict__ Y, cplx<TV>* __restrict__ Rv,
+                                                 const cplx<TV>* __restrict__ Rh, const cplx<TV>* __restrict__ Pv,
+                                                 const cplx<TV>* __restrict__ Sv, const cplx<TV>* __restrict__ Tv) {
+  const int r = blockIdx.y;
+  if (!B.active[r]) return;
+  const int64_t N = B.N, n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(N, n0 + B.chunk);
+  const int64_t o = (int64_t)r * N;
+  const cplx<TV> a = ccast<TV>(B.alpha[r]), om = ccast<TV>(B.omega[r]);
+  cplx<TV> hr = mkc<TV>(0, 0);
+  TV rr = 0;
+#pragma unroll 4
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += kRows) {
+    const cplx<TV> sv = Sv[o + n];
+    Y[o + n] = Y[o + n] + a * Pv[o + n] + om * sv;
+    const cplx<TV> rn = sv - om * Tv[o + n];
+    Rv[o + n] = rn;
+    bi_acc(hr, Rh[o + n], rn);
+    bi_nrm(rr, rn);
+  }
+  c128 shr, srr;
+  if (!bi_reduce2(B, r, ccast<double>(hr), mkc((double)rr, 0.0), shr, srr)) return;
+  const int it = ++B.its[r];
+  const double rel = B.bnorm[r] > 0.0 ? sqrt(srr.re) / B.bnorm[r] : 0.0;
+  B.resid[r] = rel;
+  const c128 om64 = B.omega[r];
+  if (!finite_z(shr) || !isfinite(rel)) {
+    bi_stop(B, r, true);
+  } else if (rel <= B.tol || it >= B.max_iter || (om64.re == 0.0 && om64.im == 0.0) ||
+             (shr.re == 0.0 && shr.im == 0.0)) {
+    bi_stop(B, r, false);  // converged by the recursion, out of steps, or a breakdown
+  } else {
+    B.beta[r] = bi_cdiv(shr, B.rho[r]) * bi_cdiv(B.alpha[r], om64);
+    B.rho[r] = shr;
+  }
+}
+
+// True residual check: r holds b - A y; right-hand sides above tol with steps left restart from it
+// (rho = |r|^2, the next direction p = r and rh = r).
+template <typename TV>
+__global__ void __launch_bounds__(kRows) k_bi_check(BPtr B, const cplx<TV>* __restrict__ Rv) {
+  const int r = blockIdx.y;
+  const int64_t N = B.N, n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(N, n0 + B.chunk);
+  const cplx<TV>* v = Rv + (int64_t)r * N;
+  TV rr = 0;
+#pragma unroll 4
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += kRows) bi_nrm(rr, v[n]);
+  c128 srr, dummy;
+  if (!bi_reduce2(B, r, mkc((double)rr, 0.0), mkc(0.0, 0.0), srr, dummy)) return;
+  const double rel = B.bnorm[r] > 0.0 ? sqrt(srr.re) / B.bnorm[r] : 0.0;
+  B.resid[r] = rel;
+  if (!isfinite(rel)) {
+    B.active[r] = 0;
+    B.st->numeric = 1;
+  } else if (rel > B.tol && B.its[r] < B.max_iter) {
+    B.active[r] = 1;
+    B.fresh[r] = 1;
+    B.rho[r] = mkc(srr.re, 0.0);
+    atomicAdd(&B.st->nactive, 1);
+  } else {
+    B.active[r] = 0;
+  }
+}
+
+template <typename TV, typename TE>
+int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
+  cudaStream_t st = ctx->stream;
+  const int R = ctx->n_rhs;
+  const int64_t N = ctx->N;
+  const int64_t nsm = std::max(ctx->nsm, 1);
+  // the right-hand-side-minor copy for the wire-tiled product with two right-hand sides per thread
+  const bool xt = std::is_same<TV, float>::value && R >= 2 && R <= 256;
+  const int xst = R + (R & 1);
+  struct Workspace {
+    int64_t key[4];
+    BPtr B;
+    KState* kst;  // the product kernels' step state: never done
+    int* pact;    // the product kernels' activity flags (all right-hand sides: the residual)
+    cplx<TV> *Y, *Rv, *Rh, *Pv, *Vv, *Sv, *Tv, *Xt;
+  };
+  const int64_t key[4] = {R, N, (int64_t)sizeof(TV), -2};
+  Workspace* ws = reinterpret_cast<Workspace*>(ctx->kry_ws);
+  if (!ws || ctx->kry_ws_bytes != sizeof(Workspace) || std::memcmp(ws->key, key, sizeof(key)) != 0) {
+    dfree_group(ctx, ctx->kry_bufs);
+    std::free(ctx->kry_ws);
+    ctx->kry_ws = nullptr;
+    ws = reinterpret_cast<Workspace*>(std::calloc(1, sizeof(Workspace)));
+    if (!ws) return ctx->fail(SWM_ENOMEM, "host allocation failed");
+    ctx->kry_ws = ws;
+    ctx->kry_ws_bytes = sizeof(Workspace);
+    std::memcpy(ws->key, key, sizeof(key));
+    auto& K = ctx->kry_bufs;
+    BPtr B{};
+    B.N = N;
+    B.R = R;
+    B.chunk = (int)std::min<int64_t>(kMaxChunk, std::max<int64_t>(kRows, ceil_div(ceil_div(N * R, 4 * nsm), kRows) * kRows));
+    B.nchunk = (int)ceil_div(N, B.chunk);
+    SWM_TRY(dalloc(ctx, K, (void**)&B.st, sizeof(BState)));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.active, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.fresh, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.its, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.counter, sizeof(unsigned) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.bnorm, sizeof(double) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.resid, sizeof(double) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.rho, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.alpha, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.omega, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.beta, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.part, sizeof(c128) * 2 * (size_t)R * B.nchunk));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->kst, sizeof(KState)));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->pact, sizeof(int) * R));
+    cplx<TV>** vecs[7] = {&ws->Y, &ws->Rv, &ws->Rh, &ws->Pv, &ws->Vv, &ws->Sv, &ws->Tv};
+    for (auto v : vecs) SWM_TRY(dalloc(ctx, K, (void**)v, sizeof(cplx<TV>) * R * N));
+    if (xt) SWM_TRY(dalloc(ctx, K, (void**)&ws->Xt, sizeof(cplx<TV>) * (size_t)xst * N));
+    ws->B = B;
+  }
+  BPtr B = ws->B;
+  B.tol = tol;
+  B.max_iter = max_iter;
+  cplx<TV> *Y = ws->Y, *Rv = ws->Rv, *Rh = ws->Rh, *Pv = ws->Pv, *Vv = ws->Vv, *Sv = ws->Sv, *Tv = ws->Tv;
+  const cplx<TV>* Bv = (const cplx<TV>*)ctx->Bv;
+  SWM_TRY(ensure_poll_slots(ctx));
+  // product kernels' view: N, R, their step state (never done) and activity flags
+  KPtr P{};
+  P.N = N;
+  P.R = R;
+  P.st = ws->kst;
+  P.active = B.active;
+  KPtr Pall = P;  // residual: every right-hand side
+  Pall.active = ws->pact;
+  k_bi_init<<<(unsigned)ceil_div(R, 256), 256, 0, st>>>(ws->kst, ws->pact, R);
+  SWM_LAUNCHED();
+  SWM_CK(cudaMemsetAsync(B.st, 0, sizeof(BState), st));
+  SWM_CK(cudaMemsetAsync(B.its, 0, sizeof(int) * R, st));
+  SWM_CK(cudaMemsetAsync(B.counter, 0, sizeof(unsigned) * R, st));
+  SWM_CK(cudaMemsetAsync(B.active, 0, sizeof(int) * R, st));
+  SWM_TRY(norms_of_b(ctx, ctx->Bv, sizeof(TV) == sizeof(double), B.bnorm));
+  SWM_TRY(init_y(ctx, Y, sizeof(TV) == sizeof(double)));
+  const WireTile wt = wire_tile(R, ctx->nw);
+  const int RQ = std::min(32, (int)ceil_div(R, 2));
+  const int WBp = std::max(1, std::min(kWpMaxWires, 256 / RQ));
+  const int T = std::max(8, std::min(64, (int)((48 * 1024 / sizeof(cplx<TV>)) / (xst + 1)) / 8 * 8));
+  const size_t dir_smem = xt ? sizeof(cplx<TV>) * T * (xst + 1) : 0;
+  if constexpr (std::is_same<TV, float>::value) {
+    if (xt) {
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 3>, ctx->smem_optin));
+      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 3>, ctx->smem_optin));
+    }
+  }
+  // w = u + E u (active right-hand sides), or with RES w = b - (u + E u) for all of them; with the
+  // right-hand-side-minor copy the source's copy is in Xt already
+  auto product = [&](cudaStream_t s, const cplx<TV>* src, cplx<TV>* dst, auto res_tag) -> int {
+    constexpr bool RS = decltype(res_tag)::value;
+    const KPtr& PP = RS ? Pall : P;
+    if constexpr (std::is_same<TV, float>::value) {
+      if (xt) {
+        const dim3 g((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(R, 2 * RQ));
+        k_spmv_wm<TE, RS ? kResW : kStepW, 3><<<g, 256, kWmSmemE + kWmSmemC, s>>>(
+            PP, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, xst, dst, Bv, RQ, WBp);
+        SWM_LAUNCHED();
+        return SWM_OK;
+      }
+    }
+    k_spmv_w<TV, TE, RS ? kResW : kStepW, false><<<dim3(wt.gx, wt.gy), 256, 0, s>>>(
+        PP, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB);
+    SWM_LAUNCHED();
+    return SWM_OK;
+  };
+  const unsigned gT = (unsigned)ceil_div(N, T);
+  const dim3 gC((unsigned)B.nchunk, R);
+  auto launch_steps = [&](cudaStream_t s, int n) -> int {
+    for (int i = 0; i < n; ++i) {
+      ctx->prof_begin(SWM_K_TRANSPOSE);
+      if (xt)
+        k_bi_dir<TV, false, true><<<gT, 256, dir_smem, s>>>(B, Rv, Rh, Pv, Vv, Pv, ws->Xt, xst, T);
+      else
+        k_bi_dir<TV, false, false><<<gT, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Pv, nullptr, xst, T);
+      ctx->prof_end(SWM_K_TRANSPOSE);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_APPLY);
+      SWM_TRY(product(s, Pv, Vv, std::false_type{}));
+      ctx->prof_end(SWM_K_APPLY);
+      ctx->prof_begin(SWM_K_DOTS);
+      k_bi_rv<TV><<<gC, kRows, 0, s>>>(B, Rh, Vv);
+      ctx->prof_end(SWM_K_DOTS);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_TRANSPOSE);
+      if (xt)
+        k_bi_dir<TV, true, true><<<gT, 256, dir_smem, s>>>(B, Rv, Rh, Pv, Vv, Sv, ws->Xt, xst, T);
+      else
+        k_bi_dir<TV, true, false><<<gT, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Sv, nullptr, xst, T);
+      ctx->prof_end(SWM_K_TRANSPOSE);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_APPLY);
+      SWM_TRY(product(s, Sv, Tv, std::false_type{}));
+      ctx->prof_end(SWM_K_APPLY);
+      ctx->prof_begin(SWM_K_DOTS);
+      k_bi_ts<TV><<<gC, kRows, 0, s>>>(B, Tv, Sv);
+      ctx->prof_end(SWM_K_DOTS);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_UPDATE);
+      k_bi_xr<TV><<<gC, kRows, 0, s>>>(B, Y, Rv, Rh, Pv, Sv, Tv);
+      ctx->prof_end(SWM_K_UPDATE);
+      SWM_LAUNCHED();
+    }
+    return SWM_OK;
+  };
+  // the true residual r = b - A y of every right-hand side and the restart decision
+  auto check = [&]() -> int {
+    if (xt) {
+      k_rhs_minor_all<TV, true><<<gT, 256, dir_smem, st>>>(Pall, Y, ws->Xt, xst, T);
+      SWM_LAUNCHED();
+    }
+    ctx->prof_begin(SWM_K_APPLY);
+    SWM_TRY(product(st, Y, Rv, std::true_type{}));
+    ctx->prof_end(SWM_K_APPLY);
+    k_bi_check<TV><<<gC, kRows, 0, st>>>(B, Rv);
+    SWM_LAUNCHED();
+    return SWM_OK;
+  };
+  constexpr int kChunk = 4;
+  ctx->stats.step_rhs_block = xt ? 68 : 64;
+  const bool use_graph = ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_DOTS &&
+                         ctx->prof_cls != SWM_K_UPDATE && ctx->prof_cls != SWM_K_TRANSPOSE;
+  if (use_graph) {
+    struct Key {
+      BPtr B;
+      const void* ptr[12];
+      Layout lay;
+      int64_t bits;
+    } gk;
+    std::memset(&gk, 0, sizeof(gk));
+    gk.B = B;
+    const void* ptrs[12] = {E, Y, Rv, Rh, Pv, Vv, Sv, Tv, ws->Xt, ctx->off, ws->kst, Bv};
+    for (int i = 0; i < 12; ++i) gk.ptr[i] = ptrs[i];
+    gk.lay = ctx->offd;
+    gk.bits = -(int64_t)(sizeof(TV) * 64 + sizeof(TE));
+    const unsigned char* kb = reinterpret_cast<const unsigned char*>(&gk);
+    std::vector<unsigned char> kv(kb, kb + sizeof(gk));
+    if (!ctx->gm_exec || kv != ctx->gm_key) {
+      if (!ctx->cap_stream) SWM_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+      const int64_t launches0 = ctx->launches;
+      SWM_CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = launch_steps(ctx->cap_stream, kChunk);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+      ctx->launches = launches0;
+      if (rc < 0) return rc;
+      SWM_CK(ce);
+      if (ctx->gm_exec) {
+        cudaGraphExecDestroy(ctx->gm_exec);
+        ctx->gm_exec = nullptr;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&ctx->gm_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SWM_CK(ie);
+      ctx->gm_key = kv;
+    }
+  }
+  const int launches_per_step = 7;
+  KState* slot = reinterpret_cast<KState*>(ctx->pinned_state);
+  BState hs{};
+  int restarts = 0;
+  for (;;) {
+    SWM_TRY(check());
+    BState* hpin = reinterpret_cast<BState*>(static_cast<char*>(ctx->pinned_state) + kPersistStateOffset);
+    SWM_CK(cudaMemcpyAsync(hpin, B.st, sizeof(BState), cudaMemcpyDeviceToHost, st));
+    SWM_CK(cudaStreamSynchronize(st));
+    hs = *hpin;
+    if (hs.nactive <= 0 || hs.numeric) break;
+    ++restarts;
+    // chunks of steps; the host reads the count of chunk c - 1 while chunk c is queued.  Each
+    // right-hand side stops by itself after at most max_iter steps, so the loop ends.
+    for (int c = 0;; ++c) {
+      if (use_graph) {
+        SWM_CK(cudaGraphLaunch(ctx->gm_exec, st));
+        ctx->launches += launches_per_step * kChunk;
+      } else {
+        SWM_TRY(launch_steps(st, kChunk));
+      }
+      SWM_CK(cudaMemcpyAsync(&slot[c & 1], B.st, sizeof(BState), cudaMemcpyDeviceToHost, st));
+      SWM_CK(cudaEventRecord(ctx->poll_ev[c & 1], st));
+      if (c >= 1) {
+        SWM_CK(cudaEventSynchronize(ctx->poll_ev[(c - 1) & 1]));
+        const BState* b = reinterpret_cast<const BState*>(&slot[(c - 1) & 1]);
+        if (b->nactive <= 0 || b->numeric) break;
+      }
+    }
+  }
+  SWM_TRY(apply_minv(ctx, Y));
+  std::vector<double> res(R);
+  std::vector<int> its(R);
+  SWM_CK(cudaMemcpyAsync(res.data(), B.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  SWM_CK(cudaMemcpyAsync(its.data(), B.its, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  SWM_CK(cudaStreamSynchronize(st));
+  double mx = 0.0;
+  int itmax = 0;
+  for (int r = 0; r < R; ++r) {
+    mx = std::max(mx, res[r]);
+    itmax = std::max(itmax, its[r]);
+  }
+  ctx->stats.iterations = itmax;
+  ctx->stats.restarts = std::max(0, restarts - 1);
+  ctx->stats.rel_residual = mx;
+  ctx->stats.converged = (!hs.numeric && mx <= tol) ? 1 : 0;
+  if (hs.numeric) return ctx->fail(SWM_ECUDA, "BiCGSTAB produced a non-finite value");
+  return ctx->stats.converged ? SWM_OK : SWM_ENOTCONV;
+}
+
 }  // namespace
 
 template <typename TV>
@@ -1662,6 +2199,11 @@ int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter) {
   if (ctx->prec == SWM_C128)
     return gmres_impl<double, c128>(ctx, (const c128*)ctx->Zp, tol, restart, max_iter, nullptr, nullptr);
   return gmres_impl<float, c64>(ctx, (const c64*)ctx->Zp, tol, restart, max_iter, nullptr, nullptr);
+}
+
+int bicgstab_solve(swm_ctx* ctx, double tol, int max_iter) {
+  if (ctx->prec == SWM_C128) return bicgstab_impl<double, c128>(ctx, (const c128*)ctx->Zp, tol, max_iter);
+  return bicgstab_impl<float, c64>(ctx, (const c64*)ctx->Zp, tol, max_iter);
 }
 
 int residual_f64_wire(swm_ctx* ctx, const c128* B, const c128* Y, c128* Rr, c128* Yt) {

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 SWM_OK, SWM_ENOTCONV = 0, 1
-SWM_SOLVER_GMRES, SWM_SOLVER_GCR = 0, 1
+SWM_SOLVER_GMRES, SWM_SOLVER_GCR, SWM_SOLVER_BICGSTAB = 0, 1, 2
 SWM_EINVAL, SWM_ENOMEM, SWM_ECUDA, SWM_ESTATE, SWM_ETIMEOUT = -1, -2, -3, -4, -5
 SWM_HOST, SWM_DEVICE = 0, 1
 SWM_C128, SWM_C64, SWM_BF16 = 0, 1, 2
@@ -233,8 +233,10 @@ def swm_build(ctx: Ctx, k: float, r_c: float, precision: int = SWM_C128) -> int:
 
 
 def swm_set_solver(ctx: Ctx, method) -> int:
-    """Krylov method of the following solves: "gmres" / SWM_SOLVER_GMRES or "gcr" / SWM_SOLVER_GCR."""
-    m = {"gmres": SWM_SOLVER_GMRES, "gcr": SWM_SOLVER_GCR}[method] if isinstance(method, str) else int(method)
+    """Krylov method of the following solves: "gmres" / SWM_SOLVER_GMRES, "gcr" / SWM_SOLVER_GCR or
+    "bicgstab" / SWM_SOLVER_BICGSTAB."""
+    m = ({"gmres": SWM_SOLVER_GMRES, "gcr": SWM_SOLVER_GCR, "bicgstab": SWM_SOLVER_BICGSTAB}[method]
+         if isinstance(method, str) else int(method))
     return _check(ctx, load().swm_set_solver(ctx.handle, m))
 
 
