@@ -485,8 +485,11 @@ __global__ void __launch_bounds__(256, 3) k_spmv_wp(KPtr P, const int64_t* __res
 // packed operands; it copies the tile's column map too.  The row loop is unrolled to the largest
 // row count of the warp's wires (warp-uniform, rows beyond a wire's own are predicated off), and
 // the gathered values of the next column pair are loaded while the current pair is multiplied.
-constexpr int kWmSmemE = 48 * 1024;  // expanded E entries (16 bytes each)
-constexpr int kWmSmemC = 4 * 1024;   // column-map entries
+constexpr int kWmSmemC = 4 * 1024;  // column-map entries of a tile
+// E budgets (expanded entries, 16 bytes each) of the two launch shapes: three CTAs per SM with
+// 48 KB (measured faster than 64 KB although more tiles of dense regions fall back to global
+// memory), two with 96 KB (nearly every tile fits, fewer warps)
+constexpr int kWmSmemE3 = 48 * 1024, kWmSmemE2 = 96 * 1024;
 __device__ __forceinline__ void wm_xsplit(const float4 v, float2& xr, float2& xi, float2& nxi) {
   xr = make_float2(v.x, v.z);
   xi = make_float2(v.y, v.w);
@@ -500,11 +503,25 @@ __device__ __forceinline__ void wm_fma(float2& ar, float2& ai, const float4 e, c
   ai = __ffma2_rn(er, xi, ai);
   ai = __ffma2_rn(ei, xr, ai);
 }
-template <int MODE, int MW>
-__device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, const float4* __restrict__ Es,
-                                        const int32_t* __restrict__ cms, const c64* __restrict__ xs, int xst,
-                                        const c64* __restrict__ U, c64* __restrict__ Wv, const c64* __restrict__ B,
-                                        int64_t orow, bool wa, bool wb) {
+// Entries of E as the packed operands (re, re, im, im): from the expanded copy in shared memory,
+// or read from global memory in the storage type and expanded in registers.
+struct EStaged {
+  const float4* p;
+  __device__ __forceinline__ float4 operator[](int64_t i) const { return p[i]; }
+};
+template <typename TE>
+struct EGlobal {
+  const TE* p;
+  __device__ __forceinline__ float4 operator[](int64_t i) const {
+    const c64 v = ELoad<float, TE>::ld(p + i);
+    return make_float4(v.re, v.re, v.im, v.im);
+  }
+};
+template <int MODE, int MW, typename EA>
+__device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, EA Es, const int32_t* __restrict__ cms,
+                                        const c64* __restrict__ xs, int xst, const c64* __restrict__ U,
+                                        c64* __restrict__ Wv, const c64* __restrict__ B, int64_t orow, bool wa,
+                                        bool wb) {
   constexpr bool RES = MODE == kResW;
   float2 ar[MW], ai[MW];
 #pragma unroll
@@ -514,7 +531,8 @@ __device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, const 
     x0 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[0] * xst));
     x1 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[K > 1 ? 1 : 0] * xst));
   }
-  const float4* er = Es + (int64_t)i0 * K;
+  EA er = Es;
+  er.p += (int64_t)i0 * K;
   for (int k = 0; k < K; k += 2) {
     float4 n0 = x0, n1 = x1;
     if (k + 2 < K) {
@@ -549,7 +567,7 @@ __device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, const 
       }
     }
 }
-template <typename TE, int MODE = kStepW, int MINB = 3>
+template <typename TE, int MODE = kStepW, int MINB = 3, int EB = kWmSmemE3>
 __global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
                                                     const TE* __restrict__ E, const c64* __restrict__ U,
                                                     const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
@@ -558,7 +576,7 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __
   if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   extern __shared__ __align__(16) unsigned char sm_wm[];
   float4* Es = reinterpret_cast<float4*>(sm_wm);
-  int32_t* Cs = reinterpret_cast<int32_t*>(sm_wm + kWmSmemE);
+  int32_t* Cs = reinterpret_cast<int32_t*>(sm_wm + EB);
   __shared__ int sK[kWpMaxWires], sm_m[kWpMaxWires], seo[kWpMaxWires], sco[kWpMaxWires];
   const int64_t N = P.N;
   const int64_t p0 = (int64_t)blockIdx.x * WB;
@@ -566,7 +584,7 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __
   // the tile's E entries and column-map entries are contiguous ranges
   const int64_t e0 = lay.rowbase[p0], c0 = lay.cmbase[p0];
   const int64_t ne = lay.rowbase[p0 + nwt] - e0, nc = lay.cmbase[p0 + nwt] - c0;
-  const bool fits = ne * (int64_t)sizeof(float4) <= kWmSmemE && nc * (int64_t)sizeof(int32_t) <= kWmSmemC;
+  const bool fits = ne * (int64_t)sizeof(float4) <= EB && nc * (int64_t)sizeof(int32_t) <= kWmSmemC;
   if (threadIdx.x < nwt) {
     const int64_t p = p0 + threadIdx.x;
     sK[threadIdx.x] = lay.K[p];
@@ -602,7 +620,7 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __
                              Wv, B, orow, wa, wb);
     return;
   }
-  const float4* er = Es + seo[pl];
+  const EStaged er{Es + seo[pl]};
   const int32_t* cms = Cs + sco[pl];
   switch (mw) {
     case 1: wm_rows<MODE, 1>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
@@ -617,6 +635,83 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __
         wm_rows<MODE, 8>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
       break;
   }
+}
+
+// The packed product without shared memory: each thread reads its wire's E (broadcast in L1 to
+// the wire's other threads) and column map from global memory, no staging and no barrier.
+template <typename TE, int MODE = kStepW, int MINB = 3>
+__global__ void __launch_bounds__(256, MINB) k_spmv_wg(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
+                                                    const TE* __restrict__ E, const c64* __restrict__ U,
+                                                    const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
+                                                    const c64* __restrict__ B, int RQ, int WB) {
+  constexpr bool ALL = MODE != kStepW;
+  if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+  const int64_t N = P.N;
+  const int64_t p0 = (int64_t)blockIdx.x * WB;
+  const int pl = (int)threadIdx.x / RQ, q = (int)threadIdx.x % RQ;
+  const int64_t p = p0 + pl;
+  const int ra = blockIdx.y * 2 * RQ + 2 * q, rb = ra + 1;
+  const bool valid = pl < WB && p < nw && ra < P.R;
+  const int64_t op = valid ? off[p] : 0;
+  const int m = valid ? (int)(off[p + 1] - op) : 0;
+  // warp-uniform row bound: the largest row count among the warp's wires
+  const int mw = __reduce_max_sync(0xffffffffu, m);
+  if (!valid) return;
+  const bool wa = ALL || P.active[ra];
+  const bool wb = rb < P.R && (ALL || P.active[rb]);
+  if (!wa && !wb) return;
+  const int K = lay.K[p];
+  const EGlobal<TE> er{E + lay.rowbase[p]};
+  const int32_t* cms = lay.colmap + lay.cmbase[p];
+  const c64* xs = Xt + ra;
+  const int64_t orow = (int64_t)ra * N + op;
+  switch (mw) {
+    case 1: wm_rows<MODE, 1>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 2: wm_rows<MODE, 2>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 3: wm_rows<MODE, 3>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 4: wm_rows<MODE, 4>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 5: wm_rows<MODE, 5>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 6: wm_rows<MODE, 6>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 7: wm_rows<MODE, 7>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    default:
+      for (int i0 = 0; i0 < m; i0 += 8)
+        wm_rows<MODE, 8>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
+      break;
+  }
+}
+
+// Launch of k_spmv_wm in one of its two shapes (three CTAs per SM with the 64 KB E budget, or two
+// with 96 KB), and the shared-memory opt-in of its instances.
+template <typename TE, bool RS>
+int launch_wm(cudaStream_t s, int form, const KPtr& P, swm_ctx* ctx, const TE* E, const c64* src, const c64* Xt,
+              int xst, c64* dst, const c64* Bv, int RQ, int WBp) {
+  const dim3 g((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(P.R, 2 * RQ));
+  constexpr int MODE = RS ? kResW : kStepW;
+  switch (form) {
+    case 68:
+      k_spmv_wm<TE, MODE, 3, kWmSmemE3><<<g, 256, kWmSmemE3 + kWmSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
+                                                                             Xt, xst, dst, Bv, RQ, WBp);
+      break;
+    case 69:
+      k_spmv_wm<TE, MODE, 2, kWmSmemE2><<<g, 256, kWmSmemE2 + kWmSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
+                                                                             Xt, xst, dst, Bv, RQ, WBp);
+      break;
+    case 70:
+      k_spmv_wg<TE, MODE, 3><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, WBp);
+      break;
+    default:
+      k_spmv_wg<TE, MODE, 4><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, WBp);
+      break;
+  }
+  return SWM_OK;  // the caller checks and counts the launch
+}
+template <typename TE>
+int allow_wm(swm_ctx* ctx) {
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 3, kWmSmemE3>, ctx->smem_optin));
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 3, kWmSmemE3>, ctx->smem_optin));
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 2, kWmSmemE2>, ctx->smem_optin));
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 2, kWmSmemE2>, ctx->smem_optin));
+  return SWM_OK;
 }
 
 // Tile shape of k_spmv_w for R right-hand sides: RG right-hand sides per CTA (all of them up to
@@ -1292,7 +1387,9 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
             P, ctx->off, ctx->offd, ctx->nw, E, src, nullptr, dst, Bv, wt.RG, wt.WB);
         break;
       case kWire + 4:  // packed FP32x2 arithmetic, E expanded and the column map in shared memory
-      case kWire + 5:  // the same with four CTAs per SM (fewer registers)
+      case kWire + 5:  // the same with two CTAs per SM and a larger E budget
+      case kWire + 6:  // packed, E and the column map read from global memory (three CTAs per SM)
+      case kWire + 7:  // the same with four CTAs per SM
         if constexpr (std::is_same<TV, float>::value) {
           if (ws->Xt && R <= 256) {
             const int xst = R + (R & 1);
@@ -1306,13 +1403,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
             ctx->prof_end(SWM_K_TRANSPOSE);
             ctx->prof_begin(SWM_K_APPLY);
             SWM_LAUNCHED();
-            const dim3 g((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(R, 2 * RQ));
-            if (b == kWire + 4)
-              k_spmv_wm<TE, RS ? kResW : kStepW, 3><<<g, 256, kWmSmemE + kWmSmemC, s>>>(
-                  P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, xst, dst, Bv, RQ, WBp);
-            else
-              k_spmv_wm<TE, RS ? kResW : kStepW, 4><<<g, 256, kWmSmemE + kWmSmemC, s>>>(
-                  P, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, xst, dst, Bv, RQ, WBp);
+            SWM_TRY((launch_wm<TE, RS>(s, b, P, ctx, E, src, ws->Xt, xst, dst, Bv, RQ, WBp)));
             break;
           }
         }
@@ -1353,10 +1444,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
   auto launch_residual = [&](cudaStream_t s, int b) { return product(s, b, std::true_type{}); };
   if constexpr (std::is_same<TV, float>::value) {
     if (multi && ws->Xt) {
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 3>, ctx->smem_optin));
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 3>, ctx->smem_optin));
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 4>, ctx->smem_optin));
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 4>, ctx->smem_optin));
+      SWM_TRY(allow_wm<TE>(ctx));
     }
   }
   const size_t dots_smem = 2 * sizeof(cplx<TV>) * (size_t)P.chunk;
@@ -1394,7 +1482,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
     const int forced = ctx->product_form;
     if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || forced == kWire + 1 ||
-        forced == kWire + 3 || forced == kWire + 4 || forced == kWire + 5 || (forced == kMinor && ws->Xt)) {
+        forced == kWire + 3 || forced == kWire + 4 || forced == kWire + 5 || forced == kWire + 6 || forced == kWire + 7 || (forced == kMinor && ws->Xt)) {
       rb = forced;
     } else if (found) {
       rb = found;
@@ -1408,7 +1496,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3, kWire + 4, kWire + 5}) {
+      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3, kWire + 4, kWire + 5, kWire + 6, kWire + 7}) {
         if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
         if (b == kMinor && !ws->Xt) continue;
         SWM_TRY(launch_product(st, b));
@@ -1929,11 +2017,12 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
   const int T = std::max(8, std::min(64, (int)((48 * 1024 / sizeof(cplx<TV>)) / (xst + 1)) / 8 * 8));
   const size_t dir_smem = xt ? sizeof(cplx<TV>) * T * (xst + 1) : 0;
   if constexpr (std::is_same<TV, float>::value) {
-    if (xt) {
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 3>, ctx->smem_optin));
-      SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 3>, ctx->smem_optin));
-    }
+    if (xt) SWM_TRY(allow_wm<TE>(ctx));
   }
+  // product form: the packed wire-tiled product in one of its two shapes, or (no copy) the
+  // wire-tiled product reading u in place; with the copy the shape is timed on this system the
+  // first time its size is solved (the product is idempotent) and kept
+  int form = xt ? 68 : 64;
   // w = u + E u (active right-hand sides), or with RES w = b - (u + E u) for all of them; with the
   // right-hand-side-minor copy the source's copy is in Xt already
   auto product = [&](cudaStream_t s, const cplx<TV>* src, cplx<TV>* dst, auto res_tag) -> int {
@@ -1941,9 +2030,7 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
     const KPtr& PP = RS ? Pall : P;
     if constexpr (std::is_same<TV, float>::value) {
       if (xt) {
-        const dim3 g((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(R, 2 * RQ));
-        k_spmv_wm<TE, RS ? kResW : kStepW, 3><<<g, 256, kWmSmemE + kWmSmemC, s>>>(
-            PP, ctx->off, ctx->offd, ctx->nw, E, src, ws->Xt, xst, dst, Bv, RQ, WBp);
+        SWM_TRY((launch_wm<TE, RS>(s, form, PP, ctx, E, src, ws->Xt, xst, dst, Bv, RQ, WBp)));
         SWM_LAUNCHED();
         return SWM_OK;
       }
@@ -2005,8 +2092,48 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
     SWM_LAUNCHED();
     return SWM_OK;
   };
+  if (xt) {
+    const int64_t shape[6] = {N, R, (int64_t)sizeof(TV), (int64_t)sizeof(TE), -3, 0};
+    int found = 0;
+    for (const auto& t : ctx->tuned)
+      if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
+    if (ctx->product_form >= 68 && ctx->product_form <= 71) {
+      form = ctx->product_form;
+    } else if (found) {
+      form = found;
+    } else {
+      // p = b transposed, then each shape once untimed and once timed on it
+      k_rhs_minor_all<TV, true><<<gT, 256, dir_smem, st>>>(Pall, Bv, ws->Xt, xst, T);
+      SWM_LAUNCHED();
+      cudaEvent_t e0, e1;
+      SWM_CK(cudaEventCreate(&e0));
+      SWM_CK(cudaEventCreate(&e1));
+      float best = 0.f;
+      for (int f : {68, 69, 70, 71}) {
+        form = f;
+        SWM_TRY(product(st, Bv, Vv, std::true_type{}));
+        SWM_CK(cudaEventRecord(e0, st));
+        SWM_TRY(product(st, Bv, Vv, std::true_type{}));
+        SWM_CK(cudaEventRecord(e1, st));
+        SWM_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SWM_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best == 0.f || ms < best) {
+          best = ms;
+          found = f;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      form = found;
+      swm_ctx::Tuned t{};
+      std::memcpy(t.shape, shape, sizeof(shape));
+      t.rb = form;
+      ctx->tuned.push_back(t);
+    }
+  }
   constexpr int kChunk = 4;
-  ctx->stats.step_rhs_block = xt ? 68 : 64;
+  ctx->stats.step_rhs_block = form;
   const bool use_graph = ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_DOTS &&
                          ctx->prof_cls != SWM_K_UPDATE && ctx->prof_cls != SWM_K_TRANSPOSE;
   if (use_graph) {

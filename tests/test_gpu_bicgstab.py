@@ -40,9 +40,14 @@ def _many(n, seed):
     return np.stack([g.uniform(0, np.pi, n), g.uniform(0, 2 * np.pi, n), g.uniform(0, np.pi, n)], 1)
 
 
-@pytest.mark.parametrize("n_inc", [1, 9, 37])
-def test_bicgstab_currents_and_rcs_match_oracle_lu(n_inc):
+@pytest.mark.parametrize("n_inc,form", [(1, 0), (9, 0), (37, 68), (37, 69), (37, 70), (37, 71)])
+def test_bicgstab_currents_and_rcs_match_oracle_lu(monkeypatch, n_inc, form):
+    """form: the packed product's shape forced (68/69: E staged in shared memory, three or two CTAs
+    per SM; 70/71: E read from global memory, three or four CTAs per SM), 0 the default."""
     from paper_2410_03060_gb300 import swm
+
+    if form:
+        monkeypatch.setenv("SWM_PRODUCT_FORM", str(form))
 
     obs = observations_phi_cut(48)
     cases = [(cloud_uniform_cube(120, 5.0, seed=61), 2.0)]
@@ -57,6 +62,8 @@ def test_bicgstab_currents_and_rcs_match_oracle_lu(n_inc):
             try:
                 cur, rc, st = _solve(swm, ctx, cl, inc, tol)
                 assert rc == swm.SWM_OK and st["converged"] == 1
+                if form and prec == C64:
+                    assert st["step_rhs_block"] == form
                 assert st["rel_residual"] <= tol
                 assert np.linalg.norm(cur - X) / np.linalg.norm(X) < bound
                 sig = np.zeros((n_inc, len(obs), 2))
