@@ -2230,12 +2230,17 @@ __global__ void k_init_y(int64_t n, const c128* __restrict__ g, cplx<TV>* __rest
 }
 
 // |b_r| per right-hand side (one CTA each, float64), 1 for a zero right-hand side.
+// |b| per right-hand side in two deterministic passes: partial sums of kBnormRows rows per CTA,
+// then the partials of each right-hand side added in order (|b| = 0 is stored as 1).
+constexpr int kBnormRows = 65536;
 template <typename TV>
-__global__ void __launch_bounds__(256) k_bnorm(int64_t N, const cplx<TV>* __restrict__ B, double* __restrict__ out) {
-  const int r = blockIdx.x;
+__global__ void __launch_bounds__(256) k_bnorm_part(int64_t N, const cplx<TV>* __restrict__ B, double* __restrict__ part) {
+  const int r = blockIdx.y;
+  const int64_t n0 = (int64_t)blockIdx.x * kBnormRows, n1 = min(N, n0 + kBnormRows);
+  const cplx<TV>* b = B + (int64_t)r * N;
   double s = 0.0;
-  for (int64_t n = threadIdx.x; n < N; n += 256) {
-    const cplx<TV> v = B[(int64_t)r * N + n];
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += 256) {
+    const cplx<TV> v = b[n];
     s += (double)v.re * v.re + (double)v.im * v.im;
   }
   __shared__ double red[8];
@@ -2245,16 +2250,31 @@ __global__ void __launch_bounds__(256) k_bnorm(int64_t N, const cplx<TV>* __rest
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < 8; ++i) t += red[i];
-    out[r] = t > 0.0 ? sqrt(t) : 1.0;
+    part[(int64_t)r * gridDim.x + blockIdx.x] = t;
   }
+}
+__global__ void k_bnorm_fin(int nchunk, const double* __restrict__ part, double* __restrict__ out) {
+  const int r = blockIdx.x;
+  const double t = sum_partials_d(part + (int64_t)r * nchunk, nchunk, threadIdx.x);
+  if (threadIdx.x == 0) out[r] = t > 0.0 ? sqrt(t) : 1.0;
 }
 
 int norms_of_b(swm_ctx* ctx, const void* B, bool f64, double* bnorm_dev) {
+  const int64_t N = ctx->N;
+  const int R = ctx->n_rhs;
+  const int nchunk = (int)std::max<int64_t>(1, ceil_div(N, kBnormRows));
+  std::vector<Buf> tmp;
+  double* part = nullptr;
+  SWM_TRY(dalloc(ctx, tmp, (void**)&part, sizeof(double) * (size_t)nchunk * R));
+  const dim3 g((unsigned)nchunk, (unsigned)R);
   if (f64)
-    k_bnorm<double><<<(unsigned)ctx->n_rhs, 256, 0, ctx->stream>>>(ctx->N, (const c128*)B, bnorm_dev);
+    k_bnorm_part<double><<<g, 256, 0, ctx->stream>>>(N, (const c128*)B, part);
   else
-    k_bnorm<float><<<(unsigned)ctx->n_rhs, 256, 0, ctx->stream>>>(ctx->N, (const c64*)B, bnorm_dev);
+    k_bnorm_part<float><<<g, 256, 0, ctx->stream>>>(N, (const c64*)B, part);
   SWM_LAUNCHED();
+  k_bnorm_fin<<<(unsigned)R, 32, 0, ctx->stream>>>(nchunk, part, bnorm_dev);
+  SWM_LAUNCHED();
+  dfree_group(ctx, tmp);  // stream order makes the reuse of the scratch safe
   return SWM_OK;
 }
 

@@ -17,17 +17,43 @@ namespace swm {
 
 namespace {
 
-// One thread per (unknown, incidence).  frames: per incidence khat[3], e[3].
+// Right-hand sides, one thread per (wire, incidence; frames: per incidence khat[3], e[3]): the
+// wire's incidence-dependent factors once (float64), then its m entries, each with its own phase
+// ph0 + beta s_l formed in float64 (and, on the complex64 path, reduced mod 2 pi in float64 before
+// the float32 sincos), as rhs_entry does per entry.
 template <typename TV>
-__global__ void k_rhs(int64_t N, int n_inc, RhsGeo g, const int32_t* __restrict__ rowwire,
-                      const int64_t* __restrict__ off, double k, const double* __restrict__ frames,
-                      cplx<TV>* __restrict__ B) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= N * n_inc) return;
-  const int64_t n = e % N;
-  const int r = (int)(e / N);
-  const int64_t p = rowwire[n];
-  B[(int64_t)r * N + n] = rhs_entry<TV>(g, p, (int)(n - off[p]), frames + 6 * r, k);
+__global__ void k_rhs_wire(int64_t nw, RhsGeo g, const int64_t* __restrict__ off, double k,
+                           const double* __restrict__ frames, int64_t N, cplx<TV>* __restrict__ B) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nw) return;
+  const int r = blockIdx.y;
+  const double* f = frames + 6 * r;
+  const double tx = g.tx[p], ty = g.ty[p], tz = g.tz[p];
+  const double kt = f[0] * tx + f[1] * ty + f[2] * tz;
+  const double et = f[3] * tx + f[4] * ty + f[5] * tz;
+  const double ph0 = -k * (f[0] * g.cx[p] + f[1] * g.cy[p] + f[2] * g.cz[p]);
+  const double Lp = g.L[p];
+  const int ns = g.ns[p];
+  const double D = Lp / ns;
+  const double beta = -k * kt;
+  const int64_t o = (int64_t)r * N + off[p];
+  if constexpr (sizeof(TV) == 8) {
+    const double sc = sinc_d(0.5 * beta * D);
+    const double amp = et * D * sc * sc;
+    for (int l = 0; l + 1 < ns; ++l) {
+      double sa, ca;
+      sincos(ph0 + beta * (-0.5 * Lp + (l + 1) * D), &sa, &ca);
+      B[o + l] = mkc(amp * ca, amp * sa);
+    }
+  } else {
+    const float sc = sinc_f((float)(0.5 * beta * D));
+    const float amp = (float)(et * D) * sc * sc;
+    for (int l = 0; l + 1 < ns; ++l) {
+      float sa, ca;
+      sincosf((float)reduce_2pi(ph0 + beta * (-0.5 * Lp + (l + 1) * D)), &sa, &ca);
+      B[o + l] = mkc(amp * ca, amp * sa);
+    }
+  }
 }
 
 // Geometry access: structure-of-arrays (internal) or caller arrays (centres/dirs as nw x 3).
@@ -488,16 +514,15 @@ int far_field_f32_launch(swm_ctx* ctx, int n_obs, const double* obs, int obs_str
 
 int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
   SWM_TRY(ensure_rowinfo(ctx));
-  const int64_t tot = ctx->N * (int64_t)n_inc;
-  const unsigned grid = (unsigned)ceil_div(tot, 256);
   const RhsGeo g{ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns};
+  const dim3 grid((unsigned)ceil_div(ctx->nw, 128), (unsigned)n_inc);
   ctx->prof_begin(SWM_K_RHS);
   if (ctx->prec == SWM_C128)
-    k_rhs<double><<<grid, 256, 0, ctx->stream>>>(ctx->N, n_inc, g, ctx->rowwire, ctx->off, ctx->k, frames_dev,
-                                                 (c128*)ctx->Bv);
+    k_rhs_wire<double><<<grid, 128, 0, ctx->stream>>>(ctx->nw, g, ctx->off, ctx->k, frames_dev, ctx->N,
+                                                      (c128*)ctx->Bv);
   else
-    k_rhs<float><<<grid, 256, 0, ctx->stream>>>(ctx->N, n_inc, g, ctx->rowwire, ctx->off, ctx->k, frames_dev,
-                                                (c64*)ctx->Bv);
+    k_rhs_wire<float><<<grid, 128, 0, ctx->stream>>>(ctx->nw, g, ctx->off, ctx->k, frames_dev, ctx->N,
+                                                     (c64*)ctx->Bv);
   ctx->prof_end(SWM_K_RHS);
   SWM_LAUNCHED();
   return SWM_OK;
@@ -505,10 +530,9 @@ int compute_rhs(swm_ctx* ctx, int n_inc, const double* frames_dev) {
 
 int compute_rhs_f64(swm_ctx* ctx, int n_inc, const double* frames_dev, c128* out) {
   SWM_TRY(ensure_rowinfo(ctx));
-  const int64_t tot = ctx->N * (int64_t)n_inc;
   const RhsGeo g{ctx->cx, ctx->cy, ctx->cz, ctx->tx, ctx->ty, ctx->tz, ctx->L, ctx->ns};
-  k_rhs<double><<<(unsigned)ceil_div(tot, 256), 256, 0, ctx->stream>>>(ctx->N, n_inc, g, ctx->rowwire, ctx->off,
-                                                                     ctx->k, frames_dev, out);
+  const dim3 grid((unsigned)ceil_div(ctx->nw, 128), (unsigned)n_inc);
+  k_rhs_wire<double><<<grid, 128, 0, ctx->stream>>>(ctx->nw, g, ctx->off, ctx->k, frames_dev, ctx->N, out);
   SWM_LAUNCHED();
   return SWM_OK;
 }
