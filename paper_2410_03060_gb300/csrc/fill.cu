@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "rhs_entry.cuh"
 
 namespace swm {
 
@@ -528,6 +529,13 @@ __global__ void __launch_bounds__(kFillThreads, sizeof(R) == 4 ? 3 : 1) k_mutual
 // the exact float64 segment distance only when the wires may be near), then every lane evaluates
 // segment pairs and adds each pair's four contributions straight into the block's entries in shared
 // memory, and finally the warp writes Z_pq and Z_qp = Z_pq^T.
+//
+// Split phase: exp(-j k R) = exp(-j k |D|) exp(-j k (R - |D|)) with D the centre difference.  The
+// block factor exp(-j k |D|) is formed once per block in float64 and applied to the block's entries
+// when they are written; the evaluations take sin and cos of the residual phase k (R - |D|), whose
+// magnitude is at most k (L_p + L_q) / 2 + k a (triangle inequality), so the float32 phase carries
+// no large multiple of 2 pi.  The evaluations of two quadrature points h, h + 1 of wire q run in
+// packed FP32x2 arithmetic.
 
 constexpr int kWarpBlocks = 8;
 constexpr int kFillF32Threads = 256;
@@ -535,10 +543,72 @@ constexpr int kFillF32Threads = 256;
 struct WarpGeo {
   float D[3], tp[3], tq[3];
   float Lp, Lq, a2, tpq, f, sc;
-  int nsp, nsq, nq, item0, acc0;
+  float Dp, Dq, rq;  // segment lengths, 1 / n_s(q)
+  float kd;          // k |D| in float32: the residual phase is k R - kd
+  float2 e0;         // exp(-j k |D|), from float64
+  int nsp, nsq, nq, acc0;
   int Kp, Kq;
   int64_t bpq, bqp;
 };
+
+// Shape integrals of one segment pair (without the 1/(4 pi) D_p D_q factor and without the block
+// factor exp(-j k |D|)).
+template <int NQ>
+__device__ __forceinline__ void seg_pair_x2(const WarpGeo& G, int u, int v, float k, const float* xg, const float* wg,
+                                            SegI<float>& out) {
+  constexpr int NH = NQ / 2;
+  float2 qx[NH], qy[NH], qz[NH], w2[NH], wx2[NH];
+#pragma unroll
+  for (int hp = 0; hp < NH; ++hp) {
+    const float x0 = xg[2 * hp], x1 = xg[2 * hp + 1];
+    const float sq0 = -0.5f * G.Lq + ((float)v + x0) * G.Dq, sq1 = -0.5f * G.Lq + ((float)v + x1) * G.Dq;
+    qx[hp] = make_float2(-sq0 * G.tq[0], -sq1 * G.tq[0]);
+    qy[hp] = make_float2(-sq0 * G.tq[1], -sq1 * G.tq[1]);
+    qz[hp] = make_float2(-sq0 * G.tq[2], -sq1 * G.tq[2]);
+    w2[hp] = make_float2(wg[2 * hp], wg[2 * hp + 1]);
+    wx2[hp] = make_float2(wg[2 * hp] * x0, wg[2 * hp + 1] * x1);
+  }
+  const float2 a2 = make_float2(G.a2, G.a2), k2 = make_float2(k, k), nkd = make_float2(-G.kd, -G.kd);
+  float rrr = 0.f, rri = 0.f, rfr = 0.f, rfi = 0.f, frr = 0.f, fri = 0.f, ffr = 0.f, ffi = 0.f;
+#pragma unroll
+  for (int g = 0; g < NQ; ++g) {
+    const float sp = -0.5f * G.Lp + ((float)u + xg[g]) * G.Dp;
+    const float ex = G.D[0] + sp * G.tp[0], ey = G.D[1] + sp * G.tp[1], ez = G.D[2] + sp * G.tp[2];
+    const float2 ex2 = make_float2(ex, ex), ey2 = make_float2(ey, ey), ez2 = make_float2(ez, ez);
+    float2 Ar = make_float2(0.f, 0.f), As = Ar, Br = Ar, Bs = Ar;
+#pragma unroll
+    for (int hp = 0; hp < NH; ++hp) {
+      const float2 dx = __fadd2_rn(ex2, qx[hp]), dy = __fadd2_rn(ey2, qy[hp]), dz = __fadd2_rn(ez2, qz[hp]);
+      const float2 R2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, a2)));
+      const float2 ri = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+      const float2 th = __ffma2_rn(__fmul2_rn(R2, ri), k2, nkd);
+      float s0, c0, s1, c1;
+      __sincosf(th.x, &s0, &c0);
+      __sincosf(th.y, &s1, &c1);
+      const float2 gr = __fmul2_rn(make_float2(c0, c1), ri), gs = __fmul2_rn(make_float2(s0, s1), ri);
+      Ar = __ffma2_rn(w2[hp], gr, Ar);
+      As = __ffma2_rn(w2[hp], gs, As);
+      Br = __ffma2_rn(wx2[hp], gr, Br);
+      Bs = __ffma2_rn(wx2[hp], gs, Bs);
+    }
+    // G = (cos - j sin) / R: the imaginary parts are minus the sine sums
+    const float ar = Ar.x + Ar.y, ai = -(As.x + As.y), br = Br.x + Br.y, bi = -(Bs.x + Bs.y);
+    const float wr = wg[g] * xg[g], wf = wg[g] - wr;
+    const float cr = ar - br, ci = ai - bi;
+    rrr = fmaf(wr, br, rrr);
+    rri = fmaf(wr, bi, rri);
+    rfr = fmaf(wr, cr, rfr);
+    rfi = fmaf(wr, ci, rfi);
+    frr = fmaf(wf, br, frr);
+    fri = fmaf(wf, bi, fri);
+    ffr = fmaf(wf, cr, ffr);
+    ffi = fmaf(wf, ci, ffi);
+  }
+  out.rr = mkc(rrr, rri);
+  out.rf = mkc(rfr, rfi);
+  out.fr = mkc(frr, fri);
+  out.ff = mkc(ffr, ffi);
+}
 
 __global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
     int64_t nup, const int64_t* __restrict__ ublk, const int32_t* __restrict__ col, const int64_t* __restrict__ bt,
@@ -550,6 +620,7 @@ __global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
   __shared__ float xs4[4], ws4[4], xs8[8], ws8[8];
   __shared__ WarpGeo geo_all[kFillF32Threads / 32][kWarpBlocks];
   __shared__ int pre_all[kFillF32Threads / 32][kWarpBlocks + 1];
+  __shared__ int outs_all[kFillF32Threads / 32][kWarpBlocks + 1];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   if (threadIdx.x < 4) {
     xs4[threadIdx.x] = (float)gl.x4[threadIdx.x];
@@ -562,13 +633,14 @@ __global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
   __syncthreads();  // the only CTA-wide barrier: the quadrature tables
   WarpGeo* geo = geo_all[wl];
   int* pre = pre_all[wl];
+  int* outs = outs_all[wl];
   float2* acc = reinterpret_cast<float2*>(smem) + (size_t)wl * kWarpBlocks * acc_per_block;
   const int64_t b0 = ((int64_t)blockIdx.x * (kFillF32Threads / 32) + wl) * kWarpBlocks;
   if (b0 >= nup) return;  // whole warp
   const int nb_here = (int)min((int64_t)kWarpBlocks, nup - b0);
   const float kf = (float)k;
   // --- set-up, one lane per block
-  int items = 0;
+  int items = 0, nout = 0;
   unsigned long long ev = 0;
   if (lane < nb_here) {
     const int64_t b = ublk[b0 + lane];
@@ -586,15 +658,31 @@ __global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
     const int nsp = ns[p], nsq = ns[q];
     G.Lp = (float)Ls[p];
     G.Lq = (float)Ls[q];
-    const float Dp = G.Lp / nsp, Dq = G.Lq / nsq;
+    G.Dp = G.Lp / nsp;
+    G.Dq = G.Lq / nsq;
+    G.rq = 1.0f / nsq;
     const float ap = (float)as[p], aq = (float)as[q];
     G.a2 = 0.5f * (ap * ap + aq * aq);
     G.tpq = G.tp[0] * G.tq[0] + G.tp[1] * G.tq[1] + G.tp[2] * G.tq[2];
-    G.f = Dp * Dq * (float)(1.0 / kFourPi);
-    G.sc = 1.0f / (kf * kf * Dp * Dq);
+    G.f = G.Dp * G.Dq * (float)(1.0 / kFourPi);
+    G.sc = 1.0f / (kf * kf * G.Dp * G.Dq);
+    // the block's phase k |D| in float64 without a float64 square root or sine (both are long
+    // dependent chains here): |D| = |D|^2 y with y the float32 reciprocal square root refined by
+    // one Newton step in float64 (relative error ~1e-14), k |D| reduced mod 2 pi in float64, and
+    // the factor exp(-j k |D|) from the reduced phase in float32 (|phase| <= pi)
+    const double d2 = Dd[0] * Dd[0] + Dd[1] * Dd[1] + Dd[2] * Dd[2];
+    double y = (double)rsqrtf((float)d2);
+    y = d2 > 0.0 ? y * (1.5 - 0.5 * d2 * y * y) : 0.0;
+    const double kd = k * (d2 * y);
+    G.kd = (float)kd;
+    {
+      float sd, cd;
+      sincosf((float)reduce_2pi(kd), &sd, &cd);
+      G.e0 = make_float2(cd, -sd);
+    }
     // near rule, decided in float64 like the reference: only when the wires may come within
     // the longer segment length (the float32 screen has a wide margin)
-    const float dmax = fmaxf(Dp, Dq);
+    const float dmax = fmaxf(G.Dp, G.Dq);
     const float reach = 0.5f * (G.Lp + G.Lq) + dmax;
     const float cd2 = G.D[0] * G.D[0] + G.D[1] * G.D[1] + G.D[2] * G.D[2];
     int nq = 4;
@@ -611,46 +699,47 @@ __global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
     G.bpq = lay.rowbase[p] + lay.colpos[b];
     G.bqp = lay.rowbase[q] + lay.colpos[bq];
     items = nsp * nsq;
+    nout = (nsp - 1) * (nsq - 1);
     ev = (unsigned long long)items * nq * nq;
     geo[lane] = G;
   }
-  // prefix of items over the batch
-  int incl = items;
+  // prefixes of items and of output entries over the batch
+  int incl = items, oincl = nout;
 #pragma unroll
   for (int o = 1; o < kWarpBlocks; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
+    const int v = __shfl_up_sync(0xffffffffu, incl, o), w = __shfl_up_sync(0xffffffffu, oincl, o);
+    if (lane >= o) {
+      incl += v;
+      oincl += w;
+    }
   }
-  if (lane < kWarpBlocks) pre[lane + 1] = incl;
-  if (lane == 0) pre[0] = 0;
+  if (lane < kWarpBlocks) {
+    pre[lane + 1] = incl;
+    outs[lane + 1] = oincl;
+  }
+  if (lane == 0) {
+    pre[0] = 0;
+    outs[0] = 0;
+  }
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
   if (lane == 0) atomicAdd(evals, ev);
   // clear the accumulators of the batch
   for (int e = lane; e < kWarpBlocks * acc_per_block; e += 32) acc[e] = make_float2(0.f, 0.f);
   __syncwarp();
   const int nitems = pre[nb_here];
+  int bl = 0;  // a lane's items increase, so its block index only moves forward
   for (int it = lane; it < nitems; it += 32) {
-    int bl = 0;
     while (pre[bl + 1] <= it) ++bl;
     const WarpGeo& G = geo[bl];
     const int local = it - pre[bl];
-    const int u = local / G.nsq, v = local % G.nsq;
-    BlockGeo B;
-    for (int c = 0; c < 3; ++c) {
-      B.D[c] = G.D[c];
-      B.tp[c] = G.tp[c];
-      B.tq[c] = G.tq[c];
-    }
-    B.Lp = G.Lp;
-    B.Lq = G.Lq;
-    B.a2 = G.a2;
-    B.nsp = G.nsp;
-    B.nsq = G.nsq;
+    // local / n_s(q) by the float reciprocal: exact for local < 256
+    const int u = (int)(((float)local + 0.5f) * G.rq);
+    const int v = local - u * G.nsq;
     SegI<float> S;
     if (G.nq == 4)
-      seg_pair_f32<4>(B, u, v, kf, xs4, ws4, S);
+      seg_pair_x2<4>(G, u, v, kf, xs4, ws4, S);
     else
-      seg_pair_f32<8>(B, u, v, kf, xs8, ws8, S);
+      seg_pair_x2<8>(G, u, v, kf, xs8, ws8, S);
     const c64 IG = S.rr + S.rf + S.fr + S.ff;
     // segment u rises for basis u and falls for basis u - 1 (same on wire q with v)
     const int mp = G.nsp - 1, mq = G.nsq - 1;
@@ -673,21 +762,16 @@ __global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
     }
   }
   __syncwarp();
-  // write Z_pq and Z_qp = Z_pq^T
-  int outs[kWarpBlocks + 1];
-  outs[0] = 0;
-#pragma unroll
-  for (int bl = 0; bl < kWarpBlocks; ++bl)
-    outs[bl + 1] = outs[bl] + (bl < nb_here ? (geo[bl].nsp - 1) * (geo[bl].nsq - 1) : 0);
+  // write Z_pq and Z_qp = Z_pq^T, each entry times the block factor exp(-j k |D|)
+  int ob = 0;
   for (int e = lane; e < outs[nb_here]; e += 32) {
-    int bl = 0;
-    while (outs[bl + 1] <= e) ++bl;
-    const WarpGeo& G = geo[bl];
+    while (outs[ob + 1] <= e) ++ob;
+    const WarpGeo& G = geo[ob];
     const int mq = G.nsq - 1;
-    const int local = e - outs[bl];
-    const int i = local / mq, jj = local % mq;
-    const float2 z = acc[bl * acc_per_block + i * mq + jj];
-    const c64 zc = mkc(z.x, z.y);
+    const int local = e - outs[ob];
+    const int i = local / mq, jj = local - (local / mq) * mq;
+    const float2 z = acc[ob * acc_per_block + i * mq + jj];
+    const c64 zc = mkc(z.x * G.e0.x - z.y * G.e0.y, z.x * G.e0.y + z.y * G.e0.x);
     Z[G.bpq + (int64_t)i * G.Kp + jj] = zc;
     Z[G.bqp + (int64_t)jj * G.Kq + i] = zc;
   }
