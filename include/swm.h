@@ -160,6 +160,8 @@ typedef struct swm_stats {
  * tile's E in shared memory; 68/69: two incidences per thread in packed FP32x2 arithmetic, E
  * staged in shared memory, three CTAs per SM with 48 KB or two with 96 KB; 70/71: the packed form
  * reading E from global memory, three or four CTAs per SM);
+ * SWM_BICGSTAB_MAJOR (default 0, a test hook) -- 1 keeps BiCGSTAB's vectors incidence-major on the
+ * complex64 path (as on the float64 path and with one incidence) instead of incidence-minor;
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the
  * persistent solve wait for n arrivals that never come, so each wait runs out (after 1 s) and the
  * solve returns SWM_ETIMEOUT; all read when the context is created. */
@@ -210,7 +212,9 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision);
  * the iterate and of the residual, whose norm is then exact; it stores two bases (p_i and A p_i).
  * SWM_SOLVER_BICGSTAB -- BiCGSTAB (van der Vorst 1992), a short-recurrence alternative for the
  * same preconditioned system: per step two products and a fixed number of vector passes (no
- * basis, so `restart` is ignored); max_iter counts its steps (two products each).  It stops when
+ * basis, so `restart` is ignored); max_iter counts its steps (two products each).  On the complex64
+ * path with 2 to 256 incidences its vectors are kept incidence-minor, the layout the product
+ * gathers from.  It stops when
  * the recursive residual meets tol, then forms the true residual b - Z x and restarts from it
  * where that is still above tol; the reported residuals are the true ones.  Not used with
  * precision SWM_BF16, whose refinement runs GMRES inside.

@@ -157,6 +157,9 @@ struct swm_ctx {
   // systems below split_rows with at most 8 right-hand sides solve in one persistent cooperative
   // kernel (SWM_PERSIST=0 turns it off); SM count and cooperative-launch support of the device
   bool persist = true;
+  // test hook (SWM_BICGSTAB_MAJOR=1): BiCGSTAB keeps its vectors incidence-major on the complex64
+  // path too, as it does on the float64 path and with one incidence
+  bool bicg_major = false;
   // test hook (SWM_TEST_BARRIER_EXTRA): grid barriers of the persistent solve wait for this many
   // arrivals more than there are CTAs, so every wait runs out and the solve reports SWM_ETIMEOUT
   int test_barrier_extra = 0;

@@ -517,7 +517,10 @@ struct EGlobal {
     return make_float4(v.re, v.re, v.im, v.im);
   }
 };
-template <int MODE, int MW, typename EA>
+// MINOR: the vectors are incidence-minor like the gathered copy ([N][xst]; U, Wv and B point at
+// incidence ra, orow is the wire's first row) and the thread reads and writes its two incidences
+// of a row as one 16-byte access; otherwise incidence-major ([R][N]; orow = ra N + first row).
+template <int MODE, int MW, typename EA, bool MINOR = false>
 __device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, EA Es, const int32_t* __restrict__ cms,
                                         const c64* __restrict__ xs, int xst, const c64* __restrict__ U,
                                         c64* __restrict__ Wv, const c64* __restrict__ B, int64_t orow, bool wa,
@@ -552,22 +555,39 @@ __device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, EA Es,
     x0 = n0;
     x1 = n1;
   }
+  if constexpr (MINOR) {
+    // both incidences of a row at once (the second may be the padding column or inactive: its
+    // value is written too and never read as a result)
 #pragma unroll
-  for (int ii = 0; ii < MW; ++ii)
-    if (ii < mm) {
-      if (wa) {
-        const int64_t o = orow + i0 + ii;
-        const c64 v = U[o] + mkc<float>(ar[ii].x, ai[ii].x);
-        Wv[o] = RES ? B[o] - v : v;
+    for (int ii = 0; ii < MW; ++ii)
+      if (ii < mm) {
+        const int64_t o = (orow + i0 + ii) * xst;
+        const float4 u = *reinterpret_cast<const float4*>(U + o);
+        float4 v = make_float4(u.x + ar[ii].x, u.y + ai[ii].x, u.z + ar[ii].y, u.w + ai[ii].y);
+        if (RES) {
+          const float4 b = *reinterpret_cast<const float4*>(B + o);
+          v = make_float4(b.x - v.x, b.y - v.y, b.z - v.z, b.w - v.w);
+        }
+        *reinterpret_cast<float4*>(Wv + o) = v;
       }
-      if (wb) {
-        const int64_t o = orow + N + i0 + ii;
-        const c64 v = U[o] + mkc<float>(ar[ii].y, ai[ii].y);
-        Wv[o] = RES ? B[o] - v : v;
+  } else {
+#pragma unroll
+    for (int ii = 0; ii < MW; ++ii)
+      if (ii < mm) {
+        if (wa) {
+          const int64_t o = orow + i0 + ii;
+          const c64 v = U[o] + mkc<float>(ar[ii].x, ai[ii].x);
+          Wv[o] = RES ? B[o] - v : v;
+        }
+        if (wb) {
+          const int64_t o = orow + N + i0 + ii;
+          const c64 v = U[o] + mkc<float>(ar[ii].y, ai[ii].y);
+          Wv[o] = RES ? B[o] - v : v;
+        }
       }
-    }
+  }
 }
-template <typename TE, int MODE = kStepW, int MINB = 3, int EB = kWmSmemE3>
+template <typename TE, int MODE = kStepW, int MINB = 3, int EB = kWmSmemE3, bool MINOR = false>
 __global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
                                                     const TE* __restrict__ E, const c64* __restrict__ U,
                                                     const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
@@ -614,32 +634,40 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wm(KPtr P, const int64_t* __
   const int64_t p = p0 + pl;
   const int K = sK[pl], m = sm_m[pl];
   const c64* xs = Xt + ra;
-  const int64_t orow = (int64_t)ra * N + off[p];
+  const int64_t orow = MINOR ? off[p] : (int64_t)ra * N + off[p];
+  if constexpr (MINOR) {
+    U += ra;
+    Wv += ra;
+    if (B) B += ra;
+  }
   if (!fits) {
-    wp_rows<TE, MODE, false>(P, N, m, K, K, E + lay.rowbase[p], nullptr, lay.colmap + lay.cmbase[p], xs, xst, U,
-                             Wv, B, orow, wa, wb);
+    // the tile's E or column map exceed the budgets: read them from global memory
+    const EGlobal<TE> eg{E + lay.rowbase[p]};
+    const int32_t* cmg = lay.colmap + lay.cmbase[p];
+    for (int i0 = 0; i0 < m; i0 += 8)
+      wm_rows<MODE, 8, EGlobal<TE>, MINOR>(N, i0, min(8, m - i0), K, eg, cmg, xs, xst, U, Wv, B, orow, wa, wb);
     return;
   }
   const EStaged er{Es + seo[pl]};
   const int32_t* cms = Cs + sco[pl];
   switch (mw) {
-    case 1: wm_rows<MODE, 1>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 2: wm_rows<MODE, 2>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 3: wm_rows<MODE, 3>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 4: wm_rows<MODE, 4>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 5: wm_rows<MODE, 5>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 6: wm_rows<MODE, 6>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 7: wm_rows<MODE, 7>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 1: wm_rows<MODE, 1, EStaged, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 2: wm_rows<MODE, 2, EStaged, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 3: wm_rows<MODE, 3, EStaged, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 4: wm_rows<MODE, 4, EStaged, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 5: wm_rows<MODE, 5, EStaged, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 6: wm_rows<MODE, 6, EStaged, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 7: wm_rows<MODE, 7, EStaged, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
     default:
       for (int i0 = 0; i0 < m; i0 += 8)
-        wm_rows<MODE, 8>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
+        wm_rows<MODE, 8, EStaged, MINOR>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
       break;
   }
 }
 
 // The packed product without shared memory: each thread reads its wire's E (broadcast in L1 to
 // the wire's other threads) and column map from global memory, no staging and no barrier.
-template <typename TE, int MODE = kStepW, int MINB = 3>
+template <typename TE, int MODE = kStepW, int MINB = 3, bool MINOR = false>
 __global__ void __launch_bounds__(256, MINB) k_spmv_wg(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
                                                     const TE* __restrict__ E, const c64* __restrict__ U,
                                                     const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
@@ -664,43 +692,50 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wg(KPtr P, const int64_t* __
   const EGlobal<TE> er{E + lay.rowbase[p]};
   const int32_t* cms = lay.colmap + lay.cmbase[p];
   const c64* xs = Xt + ra;
-  const int64_t orow = (int64_t)ra * N + op;
+  const int64_t orow = MINOR ? op : (int64_t)ra * N + op;
+  if constexpr (MINOR) {
+    U += ra;
+    Wv += ra;
+    if (B) B += ra;
+  }
   switch (mw) {
-    case 1: wm_rows<MODE, 1>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 2: wm_rows<MODE, 2>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 3: wm_rows<MODE, 3>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 4: wm_rows<MODE, 4>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 5: wm_rows<MODE, 5>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 6: wm_rows<MODE, 6>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 7: wm_rows<MODE, 7>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 1: wm_rows<MODE, 1, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 2: wm_rows<MODE, 2, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 3: wm_rows<MODE, 3, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 4: wm_rows<MODE, 4, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 5: wm_rows<MODE, 5, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 6: wm_rows<MODE, 6, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 7: wm_rows<MODE, 7, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
     default:
       for (int i0 = 0; i0 < m; i0 += 8)
-        wm_rows<MODE, 8>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
+        wm_rows<MODE, 8, EGlobal<TE>, MINOR>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
       break;
   }
 }
 
 // Launch of k_spmv_wm in one of its two shapes (three CTAs per SM with the 64 KB E budget, or two
 // with 96 KB), and the shared-memory opt-in of its instances.
-template <typename TE, bool RS>
+template <typename TE, bool RS, bool MINOR = false>
 int launch_wm(cudaStream_t s, int form, const KPtr& P, swm_ctx* ctx, const TE* E, const c64* src, const c64* Xt,
               int xst, c64* dst, const c64* Bv, int RQ, int WBp) {
   const dim3 g((unsigned)ceil_div(ctx->nw, WBp), (unsigned)ceil_div(P.R, 2 * RQ));
   constexpr int MODE = RS ? kResW : kStepW;
   switch (form) {
     case 68:
-      k_spmv_wm<TE, MODE, 3, kWmSmemE3><<<g, 256, kWmSmemE3 + kWmSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
-                                                                             Xt, xst, dst, Bv, RQ, WBp);
+      k_spmv_wm<TE, MODE, 3, kWmSmemE3, MINOR><<<g, 256, kWmSmemE3 + kWmSmemC, s>>>(
+          P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, WBp);
       break;
     case 69:
-      k_spmv_wm<TE, MODE, 2, kWmSmemE2><<<g, 256, kWmSmemE2 + kWmSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
-                                                                             Xt, xst, dst, Bv, RQ, WBp);
+      k_spmv_wm<TE, MODE, 2, kWmSmemE2, MINOR><<<g, 256, kWmSmemE2 + kWmSmemC, s>>>(
+          P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, WBp);
       break;
     case 70:
-      k_spmv_wg<TE, MODE, 3><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, WBp);
+      k_spmv_wg<TE, MODE, 3, MINOR><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
+                                                      WBp);
       break;
     default:
-      k_spmv_wg<TE, MODE, 4><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, WBp);
+      k_spmv_wg<TE, MODE, 4, MINOR><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
+                                                      WBp);
       break;
   }
   return SWM_OK;  // the caller checks and counts the launch
@@ -711,6 +746,10 @@ int allow_wm(swm_ctx* ctx) {
   SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 3, kWmSmemE3>, ctx->smem_optin));
   SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 2, kWmSmemE2>, ctx->smem_optin));
   SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 2, kWmSmemE2>, ctx->smem_optin));
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 3, kWmSmemE3, true>, ctx->smem_optin));
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 3, kWmSmemE3, true>, ctx->smem_optin));
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kStepW, 2, kWmSmemE2, true>, ctx->smem_optin));
+  SWM_CK(allow_max_dyn_smem((const void*)k_spmv_wm<TE, kResW, 2, kWmSmemE2, true>, ctx->smem_optin));
   return SWM_OK;
 }
 
@@ -2221,6 +2260,512 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
   return ctx->stats.converged ? SWM_OK : SWM_ENOTCONV;
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// BiCGSTAB on incidence-minor vectors (complex64, two to 256 incidences): every vector is stored
+// [N][xst] (xst = R rounded up to even, the padding column zero) like the product's gathered
+// copy, so the product reads its source in place, writes its image with 16-byte accesses at its
+// own rows, and the direction updates need no transposed copy.  Each vector kernel takes a chunk
+// of rows with all incidences (thread (row lane, incidence)); the per-incidence partial sums of a
+// CTA are added over its row lanes in order, written per chunk, and the last CTA of the pass adds
+// the chunks in order for every incidence and updates that incidence's scalars (float64).
+struct BmPtr {
+  BState* st;
+  int* active;        // [R] 1 while iterating
+  int* fresh;         // [R] the next direction starts from r (and rh = r)
+  int* its;           // [R] steps taken
+  unsigned* counter;  // [1] CTAs of the current pass that have arrived
+  double* bnorm;      // [R]
+  double* resid;      // [R]
+  c128 *rho, *alpha, *omega, *beta;  // [R]
+  c128* part;         // [R][nchunk][2]
+  int64_t N;
+  int R, xst, nchunk, chunk, max_iter;
+  double tol;
+};
+
+// Per-incidence sums a (complex) and b (real part used) of the CTA's rows: the row lanes of each
+// incidence added in order, one partial per chunk; true on every thread of the last CTA to arrive.
+__device__ bool bm_reduce(const BmPtr& B, int c, int rl, int nrl, bool valid, c128 a, c128 b) {
+  __shared__ c128 red[2][256];
+  __shared__ bool last;
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  __syncthreads();
+  if (valid && rl == 0) {
+    c128 sa = mkc(0.0, 0.0), sb = mkc(0.0, 0.0);
+    for (int l = 0; l < nrl; ++l) {
+      sa = sa + red[0][l * B.xst + c];
+      sb = sb + red[1][l * B.xst + c];
+    }
+    c128* part = B.part + ((int64_t)c * B.nchunk + blockIdx.x) * 2;
+    part[0] = sa;
+    part[1] = sb;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(B.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+
+// The last CTA: warp w takes incidences w, w + 8, ...; lane 0 gets the totals.
+template <typename F>
+__device__ void bm_finish(const BmPtr& B, F&& f) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw8 = blockDim.x >> 5;
+  for (int c = w; c < B.R; c += nw8) {
+    const c128* base = B.part + (int64_t)c * B.nchunk * 2;
+    const c128 ta = sum_partials_c(base, 2, B.nchunk, lane);
+    const c128 tb = sum_partials_c(base + 1, 2, B.nchunk, lane);
+    if (lane == 0) f(c, ta, tb);
+  }
+  if (threadIdx.x == 0) *B.counter = 0;
+}
+
+__device__ void bm_stop(const BmPtr& B, int r, bool numeric) {
+  B.active[r] = 0;
+  atomicSub(&B.st->nactive, 1);
+  if (numeric) B.st->numeric = 1;
+}
+
+// p = r + beta (p - omega v), or p = r and rh = r after a (re)start (SMODE false); s = r - alpha v
+// (SMODE true).  Inactive incidences are left as they are.
+template <bool SMODE>
+__global__ void __launch_bounds__(256) k_bm_dir(BmPtr B, const c64* __restrict__ Rv, c64* __restrict__ Rh,
+                                                const c64* __restrict__ Pv, const c64* __restrict__ Vv,
+                                                c64* __restrict__ Out) {
+  const int xst = B.xst, nrl = blockDim.x / xst;
+  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
+  if (rl >= nrl || c >= B.R || !B.active[c]) return;
+  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
+  if (SMODE) {
+    const c64 a = ccast<float>(B.alpha[c]);
+    for (int64_t n = n0 + rl; n < n1; n += nrl) {
+      const int64_t o = n * xst + c;
+      Out[o] = Rv[o] - a * Vv[o];
+    }
+  } else if (B.fresh[c]) {
+    for (int64_t n = n0 + rl; n < n1; n += nrl) {
+      const int64_t o = n * xst + c;
+      const c64 r = Rv[o];
+      Rh[o] = r;
+      Out[o] = r;
+    }
+  } else {
+    const c64 be = ccast<float>(B.beta[c]), om = ccast<float>(B.omega[c]);
+    for (int64_t n = n0 + rl; n < n1; n += nrl) {
+      const int64_t o = n * xst + c;
+      Out[o] = Rv[o] + be * (Pv[o] - om * Vv[o]);
+    }
+  }
+}
+
+// alpha = rho / (rh^H v)
+__global__ void __launch_bounds__(256) k_bm_rv(BmPtr B, const c64* __restrict__ Rh, const c64* __restrict__ Vv) {
+  const int xst = B.xst, nrl = blockDim.x / xst;
+  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
+  const bool valid = rl < nrl && c < B.R && B.active[c];
+  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
+  c64 a = mkc(0.f, 0.f);
+  if (valid)
+#pragma unroll 4
+    for (int64_t n = n0 + rl; n < n1; n += nrl) bi_acc(a, Rh[n * xst + c], Vv[n * xst + c]);
+  if (!bm_reduce(B, c, rl, nrl, valid, ccast<double>(a), mkc(0.0, 0.0))) return;
+  bm_finish(B, [&](int r, c128 rv, c128) {
+    if (!B.active[r]) return;
+    B.fresh[r] = 0;
+    if (!finite_z(rv)) {
+      bm_stop(B, r, true);
+    } else if (rv.re == 0.0 && rv.im == 0.0) {
+      bm_stop(B, r, false);  // breakdown: the true-residual check restarts it
+    } else {
+      B.alpha[r] = bi_cdiv(B.rho[r], rv);
+    }
+  });
+}
+
+// omega = (t^H s) / (t^H t)
+__global__ void __launch_bounds__(256) k_bm_ts(BmPtr B, const c64* __restrict__ Tv, const c64* __restrict__ Sv) {
+  const int xst = B.xst, nrl = blockDim.x / xst;
+  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
+  const bool valid = rl < nrl && c < B.R && B.active[c];
+  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
+  c64 ts = mkc(0.f, 0.f);
+  float tt = 0.f;
+  if (valid)
+#pragma unroll 4
+    for (int64_t n = n0 + rl; n < n1; n += nrl) {
+      const c64 t = Tv[n * xst + c];
+      bi_acc(ts, t, Sv[n * xst + c]);
+      bi_nrm(tt, t);
+    }
+  if (!bm_reduce(B, c, rl, nrl, valid, ccast<double>(ts), mkc((double)tt, 0.0))) return;
+  bm_finish(B, [&](int r, c128 sts, c128 stt) {
+    if (!B.active[r]) return;
+    if (!finite_z(sts) || !isfinite(stt.re)) {
+      bm_stop(B, r, true);
+      return;
+    }
+    B.omega[r] = stt.re > 0.0 ? (1.0 / stt.re) * sts : mkc(0.0, 0.0);
+  });
+}
+
+// y += alpha p + omega s, r = s - omega t; rho' = rh^H r and |r| decide the next step
+__global__ void __launch_bounds__(256) k_bm_xr(BmPtr B, c64* __restrict__ Y, c64* __restrict__ Rv,
+                                               const c64* __restrict__ Rh, const c64* __restrict__ Pv,
+                                               const c64* __restrict__ Sv, const c64* __restrict__ Tv) {
+  const int xst = B.xst, nrl = blockDim.x / xst;
+  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
+  const bool valid = rl < nrl && c < B.R && B.active[c];
+  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
+  c64 hr = mkc(0.f, 0.f);
+  float rr = 0.f;
+  if (valid) {
+    const c64 a = ccast<float>(B.alpha[c]), om = ccast<float>(B.omega[c]);
+#pragma unroll 4
+    for (int64_t n = n0 + rl; n < n1; n += nrl) {
+      const int64_t o = n * xst + c;
+      const c64 sv = Sv[o];
+      Y[o] = Y[o] + a * Pv[o] + om * sv;
+      const c64 rn = sv - om * Tv[o];
+      Rv[o] = rn;
+      bi_acc(hr, Rh[o], rn);
+      bi_nrm(rr, rn);
+    }
+  }
+  if (!bm_reduce(B, c, rl, nrl, valid, ccast<double>(hr), mkc((double)rr, 0.0))) return;
+  bm_finish(B, [&](int r, c128 shr, c128 srr) {
+    if (!B.active[r]) return;
+    const int it = ++B.its[r];
+    const double rel = B.bnorm[r] > 0.0 ? sqrt(srr.re) / B.bnorm[r] : 0.0;
+    B.resid[r] = rel;
+    const c128 om64 = B.omega[r];
+    if (!finite_z(shr) || !isfinite(rel)) {
+      bm_stop(B, r, true);
+    } else if (rel <= B.tol || it >= B.max_iter || (om64.re == 0.0 && om64.im == 0.0) ||
+               (shr.re == 0.0 && shr.im == 0.0)) {
+      bm_stop(B, r, false);  // converged by the recursion, out of steps, or a breakdown
+    } else {
+      B.beta[r] = bi_cdiv(shr, B.rho[r]) * bi_cdiv(B.alpha[r], om64);
+      B.rho[r] = shr;
+    }
+  });
+}
+
+// True residual check: r holds b - A y; incidences above tol with steps left restart from it.
+__global__ void __launch_bounds__(256) k_bm_check(BmPtr B, const c64* __restrict__ Rv) {
+  const int xst = B.xst, nrl = blockDim.x / xst;
+  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
+  const bool valid = rl < nrl && c < B.R;
+  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
+  float rr = 0.f;
+  if (valid)
+#pragma unroll 4
+    for (int64_t n = n0 + rl; n < n1; n += nrl) bi_nrm(rr, Rv[n * xst + c]);
+  if (!bm_reduce(B, c, rl, nrl, valid, mkc((double)rr, 0.0), mkc(0.0, 0.0))) return;
+  bm_finish(B, [&](int r, c128 srr, c128) {
+    const double rel = B.bnorm[r] > 0.0 ? sqrt(srr.re) / B.bnorm[r] : 0.0;
+    B.resid[r] = rel;
+    if (!isfinite(rel)) {
+      B.active[r] = 0;
+      B.st->numeric = 1;
+    } else if (rel > B.tol && B.its[r] < B.max_iter) {
+      B.active[r] = 1;
+      B.fresh[r] = 1;
+      B.rho[r] = mkc(srr.re, 0.0);
+      atomicAdd(&B.st->nactive, 1);
+    } else {
+      B.active[r] = 0;
+    }
+  });
+}
+
+// Incidence-minor [N][xst] to incidence-major [R][N] through shared-memory tiles of T rows.
+__global__ void __launch_bounds__(256) k_minor_to_major(int64_t N, int R, int xst, int T, const c64* __restrict__ X,
+                                                        c64* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char sm_mm[];
+  c64* tile = reinterpret_cast<c64*>(sm_mm);  // [T][xst + 1]
+  const int ts = xst + 1;
+  const int64_t n0 = (int64_t)blockIdx.x * T;
+  const int cnt = (int)min((int64_t)T, N - n0);
+  const c64* in = X + n0 * xst;
+  for (int e = threadIdx.x; e < cnt * xst; e += blockDim.x) tile[(e / xst) * ts + e % xst] = in[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+  for (int r = wp; r < R; r += nwp)
+    for (int t = lane; t < cnt; t += 32) Y[(int64_t)r * N + n0 + t] = tile[t * ts + r];
+}
+
+int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
+  cudaStream_t st = ctx->stream;
+  const int R = ctx->n_rhs;
+  const int64_t N = ctx->N;
+  const int64_t nsm = std::max(ctx->nsm, 1);
+  const int xst = R + (R & 1);
+  struct Workspace {
+    int64_t key[4];
+    BmPtr B;
+    KState* kst;
+    int* pact;
+    c64 *Y, *Rv, *Rh, *Pv, *Vv, *Sv, *Tv, *Bt;
+  };
+  const int64_t key[4] = {R, N, (int64_t)sizeof(float), -4};
+  Workspace* ws = reinterpret_cast<Workspace*>(ctx->kry_ws);
+  const size_t vbytes = sizeof(c64) * (size_t)xst * N;
+  if (!ws || ctx->kry_ws_bytes != sizeof(Workspace) || std::memcmp(ws->key, key, sizeof(key)) != 0) {
+    dfree_group(ctx, ctx->kry_bufs);
+    std::free(ctx->kry_ws);
+    ctx->kry_ws = nullptr;
+    ws = reinterpret_cast<Workspace*>(std::calloc(1, sizeof(Workspace)));
+    if (!ws) return ctx->fail(SWM_ENOMEM, "host allocation failed");
+    ctx->kry_ws = ws;
+    ctx->kry_ws_bytes = sizeof(Workspace);
+    std::memcpy(ws->key, key, sizeof(key));
+    auto& K = ctx->kry_bufs;
+    BmPtr B{};
+    B.N = N;
+    B.R = R;
+    B.xst = xst;
+    // chunks of rows: about four CTAs per SM, at least 2048 rows each
+    B.chunk = (int)std::max<int64_t>(2048, ceil_div(N, 4 * nsm));
+    B.nchunk = (int)ceil_div(N, B.chunk);
+    SWM_TRY(dalloc(ctx, K, (void**)&B.st, sizeof(BState)));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.active, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.fresh, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.its, sizeof(int) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.counter, sizeof(unsigned)));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.bnorm, sizeof(double) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.resid, sizeof(double) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.rho, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.alpha, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.omega, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.beta, sizeof(c128) * R));
+    SWM_TRY(dalloc(ctx, K, (void**)&B.part, sizeof(c128) * 2 * (size_t)R * B.nchunk));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->kst, sizeof(KState)));
+    SWM_TRY(dalloc(ctx, K, (void**)&ws->pact, sizeof(int) * R));
+    c64** vecs[8] = {&ws->Y, &ws->Rv, &ws->Rh, &ws->Pv, &ws->Vv, &ws->Sv, &ws->Tv, &ws->Bt};
+    for (auto v : vecs) {
+      SWM_TRY(dalloc(ctx, K, (void**)v, vbytes));
+      // the padding column (odd R) is read by the product as a second incidence: zero, and never
+      // written with anything but the product of zeros
+      SWM_CK(cudaMemsetAsync(*v, 0, vbytes, st));
+    }
+    ws->B = B;
+  }
+  BmPtr B = ws->B;
+  B.tol = tol;
+  B.max_iter = max_iter;
+  c64 *Y = ws->Y, *Rv = ws->Rv, *Rh = ws->Rh, *Pv = ws->Pv, *Vv = ws->Vv, *Sv = ws->Sv, *Tv = ws->Tv, *Bt = ws->Bt;
+  SWM_TRY(ensure_poll_slots(ctx));
+  KPtr P{};
+  P.N = N;
+  P.R = R;
+  P.st = ws->kst;
+  P.active = B.active;
+  KPtr Pall = P;
+  Pall.active = ws->pact;
+  k_bi_init<<<(unsigned)ceil_div(R, 256), 256, 0, st>>>(ws->kst, ws->pact, R);
+  SWM_LAUNCHED();
+  SWM_CK(cudaMemsetAsync(B.st, 0, sizeof(BState), st));
+  SWM_CK(cudaMemsetAsync(B.its, 0, sizeof(int) * R, st));
+  SWM_CK(cudaMemsetAsync(B.counter, 0, sizeof(unsigned), st));
+  SWM_CK(cudaMemsetAsync(B.active, 0, sizeof(int) * R, st));
+  SWM_TRY(norms_of_b(ctx, ctx->Bv, false, B.bnorm));
+  // b and the start y0 (zero, or M x0 for a guess) to incidence-minor order
+  const int T = std::max(8, std::min(64, (int)((48 * 1024 / sizeof(c64)) / (xst + 1)) / 8 * 8));
+  const size_t tsm = sizeof(c64) * T * (xst + 1);
+  const unsigned gT = (unsigned)ceil_div(N, T);
+  k_rhs_minor_all<float, true><<<gT, 256, tsm, st>>>(Pall, (const c64*)ctx->Bv, Bt, xst, T);
+  SWM_LAUNCHED();
+  if (ctx->guess) {
+    // y0 in incidence-major order in Vv's storage first
+    SWM_TRY(init_y(ctx, Vv, false));
+    k_rhs_minor_all<float, true><<<gT, 256, tsm, st>>>(Pall, Vv, Y, xst, T);
+    SWM_LAUNCHED();
+  } else {
+    SWM_CK(cudaMemsetAsync(Y, 0, vbytes, st));
+  }
+  SWM_TRY(allow_wm<c64>(ctx));
+  const int RQ = std::min(32, (int)ceil_div(R, 2));
+  const int WBp = std::max(1, std::min(kWpMaxWires, 256 / RQ));
+  int form = 71;
+  // v = A u (active incidences) or, RS, v = b - A u (every incidence): u is its own gathered copy
+  auto product = [&](cudaStream_t s, const c64* src, c64* dst, auto res_tag) -> int {
+    constexpr bool RS = decltype(res_tag)::value;
+    SWM_TRY((launch_wm<c64, RS, true>(s, form, RS ? Pall : P, ctx, E, src, src, xst, dst, Bt, RQ, WBp)));
+    SWM_LAUNCHED();
+    return SWM_OK;
+  };
+  {
+    const int64_t shape[6] = {N, R, (int64_t)sizeof(float), (int64_t)sizeof(c64), -4, 0};
+    int found = 0;
+    for (const auto& t : ctx->tuned)
+      if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
+    if (ctx->product_form >= 68 && ctx->product_form <= 71) {
+      form = ctx->product_form;
+    } else if (found) {
+      form = found;
+    } else {
+      // each shape once untimed and once timed on b (the product is idempotent)
+      cudaEvent_t e0, e1;
+      SWM_CK(cudaEventCreate(&e0));
+      SWM_CK(cudaEventCreate(&e1));
+      float best = 0.f;
+      for (int f : {68, 69, 70, 71}) {
+        form = f;
+        SWM_TRY(product(st, Bt, Vv, std::true_type{}));
+        SWM_CK(cudaEventRecord(e0, st));
+        SWM_TRY(product(st, Bt, Vv, std::true_type{}));
+        SWM_CK(cudaEventRecord(e1, st));
+        SWM_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SWM_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best == 0.f || ms < best) {
+          best = ms;
+          found = f;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      form = found;
+      swm_ctx::Tuned t{};
+      std::memcpy(t.shape, shape, sizeof(shape));
+      t.rb = form;
+      ctx->tuned.push_back(t);
+    }
+  }
+  ctx->stats.step_rhs_block = form;
+  const unsigned gC = (unsigned)B.nchunk;
+  auto launch_steps = [&](cudaStream_t s, int n) -> int {
+    for (int i = 0; i < n; ++i) {
+      ctx->prof_begin(SWM_K_TRANSPOSE);
+      k_bm_dir<false><<<gC, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Pv);
+      ctx->prof_end(SWM_K_TRANSPOSE);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_APPLY);
+      SWM_TRY(product(s, Pv, Vv, std::false_type{}));
+      ctx->prof_end(SWM_K_APPLY);
+      ctx->prof_begin(SWM_K_DOTS);
+      k_bm_rv<<<gC, 256, 0, s>>>(B, Rh, Vv);
+      ctx->prof_end(SWM_K_DOTS);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_TRANSPOSE);
+      k_bm_dir<true><<<gC, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Sv);
+      ctx->prof_end(SWM_K_TRANSPOSE);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_APPLY);
+      SWM_TRY(product(s, Sv, Tv, std::false_type{}));
+      ctx->prof_end(SWM_K_APPLY);
+      ctx->prof_begin(SWM_K_DOTS);
+      k_bm_ts<<<gC, 256, 0, s>>>(B, Tv, Sv);
+      ctx->prof_end(SWM_K_DOTS);
+      SWM_LAUNCHED();
+      ctx->prof_begin(SWM_K_UPDATE);
+      k_bm_xr<<<gC, 256, 0, s>>>(B, Y, Rv, Rh, Pv, Sv, Tv);
+      ctx->prof_end(SWM_K_UPDATE);
+      SWM_LAUNCHED();
+    }
+    return SWM_OK;
+  };
+  auto check = [&]() -> int {
+    ctx->prof_begin(SWM_K_APPLY);
+    SWM_TRY(product(st, Y, Rv, std::true_type{}));
+    ctx->prof_end(SWM_K_APPLY);
+    k_bm_check<<<gC, 256, 0, st>>>(B, Rv);
+    SWM_LAUNCHED();
+    return SWM_OK;
+  };
+  constexpr int kChunk = 4;
+  const bool use_graph = ctx->prof_cls != SWM_K_APPLY && ctx->prof_cls != SWM_K_DOTS &&
+                         ctx->prof_cls != SWM_K_UPDATE && ctx->prof_cls != SWM_K_TRANSPOSE;
+  if (use_graph) {
+    struct Key {
+      BmPtr B;
+      const void* ptr[11];
+      Layout lay;
+      int64_t bits;
+    } gk;
+    std::memset(&gk, 0, sizeof(gk));
+    gk.B = B;
+    const void* ptrs[11] = {E, Y, Rv, Rh, Pv, Vv, Sv, Tv, Bt, ctx->off, ws->kst};
+    for (int i = 0; i < 11; ++i) gk.ptr[i] = ptrs[i];
+    gk.lay = ctx->offd;
+    gk.bits = -(int64_t)(1000 + form);
+    const unsigned char* kb = reinterpret_cast<const unsigned char*>(&gk);
+    std::vector<unsigned char> kv(kb, kb + sizeof(gk));
+    if (!ctx->gm_exec || kv != ctx->gm_key) {
+      if (!ctx->cap_stream) SWM_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+      const int64_t launches0 = ctx->launches;
+      SWM_CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = launch_steps(ctx->cap_stream, kChunk);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+      ctx->launches = launches0;
+      if (rc < 0) return rc;
+      SWM_CK(ce);
+      if (ctx->gm_exec) {
+        cudaGraphExecDestroy(ctx->gm_exec);
+        ctx->gm_exec = nullptr;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&ctx->gm_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SWM_CK(ie);
+      ctx->gm_key = kv;
+    }
+  }
+  const int launches_per_step = 7;
+  KState* slot = reinterpret_cast<KState*>(ctx->pinned_state);
+  BState hs{};
+  int restarts = 0;
+  for (;;) {
+    SWM_TRY(check());
+    BState* hpin = reinterpret_cast<BState*>(static_cast<char*>(ctx->pinned_state) + kPersistStateOffset);
+    SWM_CK(cudaMemcpyAsync(hpin, B.st, sizeof(BState), cudaMemcpyDeviceToHost, st));
+    SWM_CK(cudaStreamSynchronize(st));
+    hs = *hpin;
+    if (hs.nactive <= 0 || hs.numeric) break;
+    ++restarts;
+    // chunks of steps; the host reads the count of chunk c - 1 while chunk c is queued.  Each
+    // incidence stops by itself after at most max_iter steps, so the loop ends.
+    for (int c = 0;; ++c) {
+      if (use_graph) {
+        SWM_CK(cudaGraphLaunch(ctx->gm_exec, st));
+        ctx->launches += launches_per_step * kChunk;
+      } else {
+        SWM_TRY(launch_steps(st, kChunk));
+      }
+      SWM_CK(cudaMemcpyAsync(&slot[c & 1], B.st, sizeof(BState), cudaMemcpyDeviceToHost, st));
+      SWM_CK(cudaEventRecord(ctx->poll_ev[c & 1], st));
+      if (c >= 1) {
+        SWM_CK(cudaEventSynchronize(ctx->poll_ev[(c - 1) & 1]));
+        const BState* b = reinterpret_cast<const BState*>(&slot[(c - 1) & 1]);
+        if (b->nactive <= 0 || b->numeric) break;
+      }
+    }
+  }
+  // y back to incidence-major order (in Vv's storage), then x = M^-1 y
+  k_minor_to_major<<<gT, 256, tsm, st>>>(N, R, xst, T, Y, Vv);
+  SWM_LAUNCHED();
+  SWM_TRY(apply_minv(ctx, Vv));
+  std::vector<double> res(R);
+  std::vector<int> its(R);
+  SWM_CK(cudaMemcpyAsync(res.data(), B.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  SWM_CK(cudaMemcpyAsync(its.data(), B.its, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  SWM_CK(cudaStreamSynchronize(st));
+  double mx = 0.0;
+  int itmax = 0;
+  for (int r = 0; r < R; ++r) {
+    mx = std::max(mx, res[r]);
+    itmax = std::max(itmax, its[r]);
+  }
+  ctx->stats.iterations = itmax;
+  ctx->stats.restarts = std::max(0, restarts - 1);
+  ctx->stats.rel_residual = mx;
+  ctx->stats.converged = (!hs.numeric && mx <= tol) ? 1 : 0;
+  if (hs.numeric) return ctx->fail(SWM_ECUDA, "BiCGSTAB produced a non-finite value");
+  return ctx->stats.converged ? SWM_OK : SWM_ENOTCONV;
+}
+
 }  // namespace
 
 template <typename TV>
@@ -2350,6 +2895,9 @@ int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter) {
 
 int bicgstab_solve(swm_ctx* ctx, double tol, int max_iter) {
   if (ctx->prec == SWM_C128) return bicgstab_impl<double, c128>(ctx, (const c128*)ctx->Zp, tol, max_iter);
+  // complex64 with 2 to 256 incidences: the vectors incidence-minor (the headline's form)
+  if (ctx->n_rhs >= 2 && ctx->n_rhs <= 256 && !ctx->bicg_major)
+    return bicgstab_minor(ctx, (const c64*)ctx->Zp, tol, max_iter);
   return bicgstab_impl<float, c64>(ctx, (const c64*)ctx->Zp, tol, max_iter);
 }
 

@@ -40,14 +40,18 @@ def _many(n, seed):
     return np.stack([g.uniform(0, np.pi, n), g.uniform(0, 2 * np.pi, n), g.uniform(0, np.pi, n)], 1)
 
 
-@pytest.mark.parametrize("n_inc,form", [(1, 0), (9, 0), (37, 68), (37, 69), (37, 70), (37, 71)])
-def test_bicgstab_currents_and_rcs_match_oracle_lu(monkeypatch, n_inc, form):
+@pytest.mark.parametrize("n_inc,form,major", [(1, 0, 0), (9, 0, 0), (9, 0, 1), (37, 68, 0), (37, 69, 0), (37, 70, 0),
+                                               (37, 71, 0), (37, 71, 1), (37, 68, 1)])
+def test_bicgstab_currents_and_rcs_match_oracle_lu(monkeypatch, n_inc, form, major):
     """form: the packed product's shape forced (68/69: E staged in shared memory, three or two CTAs
-    per SM; 70/71: E read from global memory, three or four CTAs per SM), 0 the default."""
+    per SM; 70/71: E read from global memory, three or four CTAs per SM), 0 the default; major: the
+    complex64 vectors kept incidence-major (SWM_BICGSTAB_MAJOR) instead of incidence-minor."""
     from paper_2410_03060_gb300 import swm
 
     if form:
         monkeypatch.setenv("SWM_PRODUCT_FORM", str(form))
+    if major:
+        monkeypatch.setenv("SWM_BICGSTAB_MAJOR", "1")
 
     obs = observations_phi_cut(48)
     cases = [(cloud_uniform_cube(120, 5.0, seed=61), 2.0)]
