@@ -182,7 +182,7 @@ def _oracle_blocks(args):
     return blocks, O.block_jacobi(cloud.subset(rows), k)
 
 
-def oracle_step(cloud, inc, obs, r_c, pool=None, n_chunks=1):
+def oracle_step(cloud, inc, obs, r_c, pool=None, n_chunks=1, solver="gmres"):
     """The whole path on the FP64 CPU oracle (test infrastructure, timed as the CPU baseline):
     pairs, blocks, block-Jacobi, RHS, GMRES per incidence, RCS.  The blocks and the self-block
     inverses are computed in ``pool`` (the oracle's own functions, rows split over the workers).
@@ -214,7 +214,10 @@ def oracle_step(cloud, inc, obs, r_c, pool=None, n_chunks=1):
     b = O.rhs(cloud, K0, inc)
     X = np.zeros_like(b)
     for i in range(b.shape[1]):
-        X[:, i], _, _ = O.gmres(Z, b[:, i], Mi, off, TOL, RESTART, 1000)
+        if solver == "bicgstab":
+            X[:, i], _, _ = O.bicgstab(Z, b[:, i], Mi, off, TOL, 1000)
+        else:
+            X[:, i], _, _ = O.gmres(Z, b[:, i], Mi, off, TOL, RESTART, 1000)
     sig = O.rcs_bistatic(cloud, K0, X, obs) if obs is not None else O.rcs_monostatic(cloud, K0, X, inc)
     t2 = time.perf_counter()
     return sig, t1 - t0, t2 - t1
@@ -237,7 +240,7 @@ def oracle_pool(cores):
     return cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
 
 
-def cpu_oracle_sample(name, n_target, cores, steps=1, warmup=0):
+def cpu_oracle_sample(name, n_target, cores, steps=1, warmup=0, solver="gmres"):
     """The oracle on a bounded sample of workload ``name``: the wires nearest a random wire of the
     cloud, one incidence; with several incidences in the workload the per-incidence part is
     extrapolated (build once + n_inc x one incidence's RHS, GMRES and RCS)."""
@@ -248,18 +251,19 @@ def cpu_oracle_sample(name, n_target, cores, steps=1, warmup=0):
     n_inc = inc_full.shape[0]
     with oracle_pool(cores) as pool:
         for _ in range(warmup):
-            oracle_step(cl, inc, obs, w["r_c"], pool, cores)
+            oracle_step(cl, inc, obs, w["r_c"], pool, cores, solver)
         tb, ts = [], []
         for _ in range(max(1, steps)):
-            _, b, s = oracle_step(cl, inc, obs, w["r_c"], pool, cores)
+            _, b, s = oracle_step(cl, inc, obs, w["r_c"], pool, cores, solver)
             tb.append(b)
             ts.append(s)
     t_build, t_inc = float(np.mean(tb)), float(np.mean(ts))
     t_step = t_build + n_inc * t_inc
     value = cl.n_unknowns * n_inc / t_step
+    kry = "BiCGSTAB" if solver == "bicgstab" else "GMRES(50)"
     sample = (f"{cl.nw} wires nearest a random wire of the {cl_full.nw:,}-wire cloud (N={cl.n_unknowns}), the "
-              f"whole path on the FP64 NumPy oracle (blocks and self-block inverses on {cores} processes, GMRES "
-              f"in one): build {t_build:.2f} s, one incidence's RHS + GMRES(50) 1e-6 + RCS {t_inc:.3f} s")
+              f"whole path on the FP64 NumPy oracle (blocks and self-block inverses on {cores} processes, the "
+              f"solve in one): build {t_build:.2f} s, one incidence's RHS + {kry} 1e-6 + RCS {t_inc:.3f} s")
     if n_inc > 1:
         sample += f"; EXTRAPOLATED to {n_inc} incidences as build + {n_inc} x one incidence"
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
@@ -305,8 +309,10 @@ def class_bytes_bicgstab(cls, st, prec, n_rhs):
     two direction updates with their incidence-minor copies (p = r + beta (p - omega v): r, p, v
     read, p and its copy written; s = r - alpha v: r, v read, s and its copy written), the inner
     products (rh^H v; t^H s and t^H t) and y += alpha p + omega s, r = s - omega t with rh^H r and
-    |r| (y, p, s, t, rh read, y and r written).  Each true-residual check: y copied to
-    incidence-minor order, the residual product (b read as well) and |r|."""
+    |r| (y, p, s, t, rh read, y and r written).  Each true-residual check: the residual product
+    (b read as well) and |r|.  With the incidence-minor vectors (complex64, 2-256 incidences) the
+    direction updates write no copy, and b and y are transposed once each; otherwise each update
+    writes the incidence-minor copy and each check copies y."""
     esz = 16 if prec == "c128" else 8
     N, R = st["n"], n_rhs
     vec = R * N * esz
@@ -316,7 +322,10 @@ def class_bytes_bicgstab(cls, st, prec, n_rhs):
     xt = prec != "c128" and R >= 2
     if cls == "apply":
         return steps * 2 * (mat + 2 * vec) + checks * (mat + 3 * vec)
+    minor = xt and 2 <= R <= 256
     if cls == "transpose":
+        if minor:
+            return steps * (4 + 3) * vec
         return steps * ((5 + 4) * vec if xt else (4 + 3) * vec) + (checks * 2 * vec if xt else 0)
     if cls == "dots":
         return steps * 4 * vec + checks * vec
@@ -388,20 +397,30 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
     work = b * steps
     ach = work / (prof_ms * 1e-3) / 1e9
     peak = pk.get("hbm_gbs", 6800.0)
-    names = {"apply": "k_spmv_wp / k_spmv_w / k_spmv_t / k_spmv (form timed per shape): block-sparse product",
+    names = {"apply": "block-sparse product, form %s (k_spmv_wg / k_spmv_wm / k_spmv_wp / k_spmv_w / k_spmv_t / "
+                      "k_spmv, timed per shape)" % st.get("step_rhs_block"),
              "transpose": "k_rhs_minor_all: pending vectors to incidence-minor order",
              "dots": "k_dots: delayed Gram-Schmidt inner products",
              "update": "k_update: delayed Gram-Schmidt update",
              "gmres": "k_gmres_persist: persistent GMRES solve"}
+    if solver == "bicgstab":
+        names.update({"transpose": "k_bm_dir (k_bi_dir): direction updates p and s",
+                      "dots": "k_bm_rv, k_bm_ts (k_bi_rv, k_bi_ts): inner products r^H v, t^H s, t^H t",
+                      "update": "k_bm_xr (k_bi_xr): y and r updates with r^H r and |r|"})
     return {"kernel": names.get(cls, cls), "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_source": "of measured (MEASURED_PEAKS.json copy bandwidth)",
             "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel's
-# current code, keyed by (workload, kernel class, precision); the capture and its scaling are
-# recorded with the profile summaries.  A class without a capture of its current code reports null.
-MEASURED_TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch over the launch's
+# algorithmic bytes, from one ncu capture of the kernel's current code on the 250,000-wire cloud
+# of the same density, keyed by (workload, kernel class, precision, solver); the bench line's
+# traffic is this ratio times its own algorithmic bytes per launch.  The capture is recorded with
+# the profile summaries.  A class without a capture of its current code reports null.
+MEASURED_TRAFFIC = {
+    # k_spmv_wg, complex64, incidence-minor (BiCGSTAB step): 1.0628 GB against 1.0766 GB
+    ("learned", "apply", "c64", "bicgstab"): 1.0628e9 / 1.0766e9,
+}
 
 PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "apply", "transpose", "dots", "update",
                    "far", "gmres"]
@@ -499,7 +518,8 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
     if roof is not None:
         roof["class"] = dominant
         roof["profiled_steps"] = rsteps
-        roof["traffic"] = MEASURED_TRAFFIC.get((name, dominant, args.precision))
+        ratio = MEASURED_TRAFFIC.get((name, dominant, args.precision, solver))
+        roof["traffic"] = ratio * roof["per_launch_bytes"] if ratio and "per_launch_bytes" in roof else None
     extra_roofs = {}
     for c in ("fill_mutual", "apply", "transpose", "dots", "update"):
         if c != dominant and prof[c][1] > 0:
@@ -617,7 +637,7 @@ def run_ours(args):
         out["mid"]["fp64_speedup"] = side["ms64"] / side["ms_per_step"]
     if world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        out["cpu_baseline"] = cpu_oracle_sample(name, min(30000, 600 * cores), cores)
+        out["cpu_baseline"] = cpu_oracle_sample(name, min(30000, 600 * cores), cores, solver=args.solver)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -973,14 +993,14 @@ def run_reference(args):
     # core-second, (steps + warmup) oracle steps
     per_step_s = 150.0 / (args.steps + args.warmup)
     n_wires = int(min(30000, max(200, per_step_s * cores / 0.02)))
-    cb = cpu_oracle_sample(name, n_wires, cores, steps=args.steps, warmup=args.warmup)
+    cb = cpu_oracle_sample(name, n_wires, cores, steps=args.steps, warmup=args.warmup, solver=args.solver)
     v = cb["value"]
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": cb["seconds_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded wire clouds)",
-        "config": {"workload": WORKLOADS[name]["text"] + " (bounded sample, see cpu_baseline.sample)"},
+        "config": {"workload": workload_text(name, args.solver, args.restart) + " (bounded sample, see cpu_baseline.sample)"},
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
