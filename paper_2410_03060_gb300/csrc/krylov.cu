@@ -733,6 +733,32 @@ int launch_wm(cudaStream_t s, int form, const KPtr& P, swm_ctx* ctx, const TE* E
       k_spmv_wg<TE, MODE, 3, MINOR><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
                                                       WBp);
       break;
+    case 72:
+    case 73: {
+      // small CTAs (a few whole warps) so that a CTA's registers come free as soon as its few
+      // wires are done: w wires of RQ threads in 32 ceil(w RQ / 32) threads, w chosen for the
+      // fewest idle lanes
+      int bw = 1, bt = 32;
+      double be = 0.0;
+      for (int w = 1; w <= 8; ++w) {
+        const int t = 32 * (int)ceil_div(w * RQ, 32);
+        if (t > 256) break;
+        const double e = (double)(w * RQ) / t;
+        if (e > be + 1e-9) {
+          be = e;
+          bw = w;
+          bt = t;
+        }
+      }
+      const dim3 gs((unsigned)ceil_div(ctx->nw, bw), g.y);
+      if (form == 72)
+        k_spmv_wg<TE, MODE, 3, MINOR><<<gs, bt, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
+                                                        bw);
+      else
+        k_spmv_wg<TE, MODE, 4, MINOR><<<gs, bt, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
+                                                        bw);
+      break;
+    }
     default:
       k_spmv_wg<TE, MODE, 4, MINOR><<<g, 256, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
                                                       WBp);
@@ -1429,6 +1455,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       case kWire + 5:  // the same with two CTAs per SM and a larger E budget
       case kWire + 6:  // packed, E and the column map read from global memory (three CTAs per SM)
       case kWire + 7:  // the same with four CTAs per SM
+      case kWire + 8:  // the same in small CTAs of a few whole warps (register budget of 70)
+      case kWire + 9:  // the same in small CTAs (register budget of 71)
         if constexpr (std::is_same<TV, float>::value) {
           if (ws->Xt && R <= 256) {
             const int xst = R + (R & 1);
@@ -1521,7 +1549,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
     const int forced = ctx->product_form;
     if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || forced == kWire + 1 ||
-        forced == kWire + 3 || forced == kWire + 4 || forced == kWire + 5 || forced == kWire + 6 || forced == kWire + 7 || (forced == kMinor && ws->Xt)) {
+        forced == kWire + 3 || forced == kWire + 4 || forced == kWire + 5 || forced == kWire + 6 || forced == kWire + 7 || forced == kWire + 8 || forced == kWire + 9 || (forced == kMinor && ws->Xt)) {
       rb = forced;
     } else if (found) {
       rb = found;
@@ -1535,7 +1563,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3, kWire + 4, kWire + 5, kWire + 6, kWire + 7}) {
+      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3, kWire + 4, kWire + 5, kWire + 6, kWire + 7, kWire + 8, kWire + 9}) {
         if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
         if (b == kMinor && !ws->Xt) continue;
         SWM_TRY(launch_product(st, b));
@@ -2136,7 +2164,7 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
     int found = 0;
     for (const auto& t : ctx->tuned)
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
-    if (ctx->product_form >= 68 && ctx->product_form <= 71) {
+    if (ctx->product_form >= 68 && ctx->product_form <= 73) {
       form = ctx->product_form;
     } else if (found) {
       form = found;
@@ -2148,7 +2176,7 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int f : {68, 69, 70, 71}) {
+      for (int f : {68, 69, 70, 71, 72, 73}) {
         form = f;
         SWM_TRY(product(st, Bv, Vv, std::true_type{}));
         SWM_CK(cudaEventRecord(e0, st));
@@ -2601,7 +2629,7 @@ int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
     int found = 0;
     for (const auto& t : ctx->tuned)
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
-    if (ctx->product_form >= 68 && ctx->product_form <= 71) {
+    if (ctx->product_form >= 68 && ctx->product_form <= 73) {
       form = ctx->product_form;
     } else if (found) {
       form = found;
@@ -2611,7 +2639,7 @@ int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int f : {68, 69, 70, 71}) {
+      for (int f : {68, 69, 70, 71, 72, 73}) {
         form = f;
         SWM_TRY(product(st, Bt, Vv, std::true_type{}));
         SWM_CK(cudaEventRecord(e0, st));
