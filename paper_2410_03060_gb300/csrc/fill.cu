@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kFillThreads, sizeof(R) == 4 ? 3 : 1) k_mutual
 // packed FP32x2 arithmetic.
 
 constexpr int kWarpBlocks = 8;
-constexpr int kFillF32Threads = 256;
+constexpr int kFillF32Threads = 64;  // two warps: a CTA retires as soon as its two batches are done
 
 struct WarpGeo {
   float D[3], tp[3], tq[3];
@@ -610,7 +610,7 @@ __device__ __forceinline__ void seg_pair_x2(const WarpGeo& G, int u, int v, floa
   out.ff = mkc(ffr, ffi);
 }
 
-__global__ void __launch_bounds__(kFillF32Threads, 3) k_mutual_blocks_f32(
+__global__ void __launch_bounds__(kFillF32Threads, 12) k_mutual_blocks_f32(
     int64_t nup, const int64_t* __restrict__ ublk, const int32_t* __restrict__ col, const int64_t* __restrict__ bt,
     const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
     const double* __restrict__ tx, const double* __restrict__ ty, const double* __restrict__ tz,
