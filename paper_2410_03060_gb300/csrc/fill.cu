@@ -610,7 +610,7 @@ __device__ __forceinline__ void seg_pair_x2(const WarpGeo& G, int u, int v, floa
   out.ff = mkc(ffr, ffi);
 }
 
-__global__ void __launch_bounds__(kFillF32Threads, 12) k_mutual_blocks_f32(
+__global__ void __launch_bounds__(kFillF32Threads, 16) k_mutual_blocks_f32(
     int64_t nup, const int64_t* __restrict__ ublk, const int32_t* __restrict__ col, const int64_t* __restrict__ bt,
     const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
     const double* __restrict__ tx, const double* __restrict__ ty, const double* __restrict__ tz,

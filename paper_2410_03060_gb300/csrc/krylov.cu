@@ -2368,11 +2368,13 @@ __global__ void __launch_bounds__(256) k_bm_dir(BmPtr B, const c64* __restrict__
   const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
   if (SMODE) {
     const c64 a = ccast<float>(B.alpha[c]);
+#pragma unroll 4
     for (int64_t n = n0 + rl; n < n1; n += nrl) {
       const int64_t o = n * xst + c;
       Out[o] = Rv[o] - a * Vv[o];
     }
   } else if (B.fresh[c]) {
+#pragma unroll 4
     for (int64_t n = n0 + rl; n < n1; n += nrl) {
       const int64_t o = n * xst + c;
       const c64 r = Rv[o];
@@ -2381,6 +2383,7 @@ __global__ void __launch_bounds__(256) k_bm_dir(BmPtr B, const c64* __restrict__
     }
   } else {
     const c64 be = ccast<float>(B.beta[c]), om = ccast<float>(B.omega[c]);
+#pragma unroll 4
     for (int64_t n = n0 + rl; n < n1; n += nrl) {
       const int64_t o = n * xst + c;
       Out[o] = Rv[o] + be * (Pv[o] - om * Vv[o]);
