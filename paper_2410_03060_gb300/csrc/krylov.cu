@@ -2312,31 +2312,6 @@ struct BmPtr {
   double tol;
 };
 
-// Per-incidence sums a (complex) and b (real part used) of the CTA's rows: the row lanes of each
-// incidence added in order, one partial per chunk; true on every thread of the last CTA to arrive.
-__device__ bool bm_reduce(const BmPtr& B, int c, int rl, int nrl, bool valid, c128 a, c128 b) {
-  __shared__ c128 red[2][256];
-  __shared__ bool last;
-  red[0][threadIdx.x] = a;
-  red[1][threadIdx.x] = b;
-  __syncthreads();
-  if (valid && rl == 0) {
-    c128 sa = mkc(0.0, 0.0), sb = mkc(0.0, 0.0);
-    for (int l = 0; l < nrl; ++l) {
-      sa = sa + red[0][l * B.xst + c];
-      sb = sb + red[1][l * B.xst + c];
-    }
-    c128* part = B.part + ((int64_t)c * B.nchunk + blockIdx.x) * 2;
-    part[0] = sa;
-    part[1] = sb;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(B.counter, 1u) == gridDim.x - 1;
-  __syncthreads();
-  return last;
-}
-
 // The last CTA: warp w takes incidences w, w + 8, ...; lane 0 gets the totals.
 template <typename F>
 __device__ void bm_finish(const BmPtr& B, F&& f) {
@@ -2356,52 +2331,122 @@ __device__ void bm_stop(const BmPtr& B, int r, bool numeric) {
   if (numeric) B.st->numeric = 1;
 }
 
-// p = r + beta (p - omega v), or p = r and rh = r after a (re)start (SMODE false); s = r - alpha v
-// (SMODE true).  Inactive incidences are left as they are.
+// Pair-granular forms of the incidence-minor BiCGSTAB passes: thread (row lane, pair q) takes
+// incidences 2q and 2q + 1 (the second may be the padding column) of its rows as one 16-byte
+// access; scalars of inactive or padding halves are zero, so those halves stay finite.
+struct BpRow {
+  int q, rl, nrl;
+  bool valid;
+  int64_t n0, n1;
+};
+__device__ __forceinline__ BpRow bp_row(const BmPtr& B) {
+  BpRow t;
+  const int pq = B.xst >> 1;
+  t.nrl = blockDim.x / pq;
+  t.q = threadIdx.x % pq;
+  t.rl = threadIdx.x / pq;
+  t.valid = t.rl < t.nrl;
+  t.n0 = (int64_t)blockIdx.x * B.chunk;
+  t.n1 = min(B.N, t.n0 + B.chunk);
+  return t;
+}
+__device__ __forceinline__ float4 ld4(const c64* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(c64* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ c64 lo(float4 v) { return mkc(v.x, v.y); }
+__device__ __forceinline__ c64 hi(float4 v) { return mkc(v.z, v.w); }
+__device__ __forceinline__ float4 f4(c64 a, c64 b) { return make_float4(a.re, a.im, b.re, b.im); }
+// Per-incidence sums of the pair passes: a (complex) and b (real) for both halves, the row lanes
+// added in order, one partial per chunk; true on every thread of the last CTA to arrive.
+__device__ bool bp_reduce(const BmPtr& B, const BpRow& t, c128 a0, c128 b0, c128 a1, c128 b1) {
+  __shared__ c128 red[4][256];
+  __shared__ bool last;
+  red[0][threadIdx.x] = a0;
+  red[1][threadIdx.x] = b0;
+  red[2][threadIdx.x] = a1;
+  red[3][threadIdx.x] = b1;
+  __syncthreads();
+  const int pq = B.xst >> 1;
+  if (t.valid && t.rl == 0) {
+    c128 s[4] = {mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0), mkc(0.0, 0.0)};
+    for (int l = 0; l < t.nrl; ++l)
+      for (int k = 0; k < 4; ++k) s[k] = s[k] + red[k][l * pq + t.q];
+    const int c0 = 2 * t.q, c1 = c0 + 1;
+    c128* p0 = B.part + ((int64_t)c0 * B.nchunk + blockIdx.x) * 2;
+    p0[0] = s[0];
+    p0[1] = s[1];
+    if (c1 < B.R) {
+      c128* p1 = B.part + ((int64_t)c1 * B.nchunk + blockIdx.x) * 2;
+      p1[0] = s[2];
+      p1[1] = s[3];
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(B.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+__device__ __forceinline__ bool bp_act(const BmPtr& B, int c) { return c < B.R && B.active[c]; }
+__device__ __forceinline__ c64 bp_sc(const BmPtr& B, const c128* v, int c) {
+  return bp_act(B, c) ? ccast<float>(v[c]) : mkc(0.f, 0.f);
+}
+
+// p = r + beta (p - omega v), or p = r and rh = r for a (re)started incidence (SMODE false);
+// s = r - alpha v (SMODE true).
 template <bool SMODE>
-__global__ void __launch_bounds__(256) k_bm_dir(BmPtr B, const c64* __restrict__ Rv, c64* __restrict__ Rh,
+__global__ void __launch_bounds__(256) k_bp_dir(BmPtr B, const c64* __restrict__ Rv, c64* __restrict__ Rh,
                                                 const c64* __restrict__ Pv, const c64* __restrict__ Vv,
                                                 c64* __restrict__ Out) {
-  const int xst = B.xst, nrl = blockDim.x / xst;
-  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
-  if (rl >= nrl || c >= B.R || !B.active[c]) return;
-  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
+  const BpRow t = bp_row(B);
+  const int c0 = 2 * t.q, c1 = c0 + 1;
+  const bool a0 = bp_act(B, c0), a1 = bp_act(B, c1);
+  if (!t.valid || (!a0 && !a1)) return;
+  const int xst = B.xst;
   if (SMODE) {
-    const c64 a = ccast<float>(B.alpha[c]);
+    const c64 al0 = bp_sc(B, B.alpha, c0), al1 = bp_sc(B, B.alpha, c1);
 #pragma unroll 4
-    for (int64_t n = n0 + rl; n < n1; n += nrl) {
-      const int64_t o = n * xst + c;
-      Out[o] = Rv[o] - a * Vv[o];
+    for (int64_t n = t.n0 + t.rl; n < t.n1; n += t.nrl) {
+      const int64_t o = n * xst + c0;
+      const float4 r = ld4(Rv + o), v = ld4(Vv + o);
+      st4(Out + o, f4(lo(r) - al0 * lo(v), hi(r) - al1 * hi(v)));
     }
-  } else if (B.fresh[c]) {
+    return;
+  }
+  const bool f0 = a0 && B.fresh[c0], f1 = a1 && B.fresh[c1];
+  // a fresh half takes beta = 0 (p = r); its rh is set to r
+  const c64 be0 = f0 ? mkc(0.f, 0.f) : bp_sc(B, B.beta, c0), be1 = f1 ? mkc(0.f, 0.f) : bp_sc(B, B.beta, c1);
+  const c64 om0 = bp_sc(B, B.omega, c0), om1 = bp_sc(B, B.omega, c1);
 #pragma unroll 4
-    for (int64_t n = n0 + rl; n < n1; n += nrl) {
-      const int64_t o = n * xst + c;
-      const c64 r = Rv[o];
-      Rh[o] = r;
-      Out[o] = r;
-    }
-  } else {
-    const c64 be = ccast<float>(B.beta[c]), om = ccast<float>(B.omega[c]);
-#pragma unroll 4
-    for (int64_t n = n0 + rl; n < n1; n += nrl) {
-      const int64_t o = n * xst + c;
-      Out[o] = Rv[o] + be * (Pv[o] - om * Vv[o]);
+  for (int64_t n = t.n0 + t.rl; n < t.n1; n += t.nrl) {
+    const int64_t o = n * xst + c0;
+    const float4 r = ld4(Rv + o), p = ld4(Pv + o), v = ld4(Vv + o);
+    st4(Out + o, f4(lo(r) + be0 * (lo(p) - om0 * lo(v)), hi(r) + be1 * (hi(p) - om1 * hi(v))));
+    if (f0 && f1) {
+      st4(Rh + o, r);
+    } else if (f0) {
+      Rh[o] = lo(r);
+    } else if (f1) {
+      Rh[o + 1] = hi(r);
     }
   }
 }
 
 // alpha = rho / (rh^H v)
-__global__ void __launch_bounds__(256) k_bm_rv(BmPtr B, const c64* __restrict__ Rh, const c64* __restrict__ Vv) {
-  const int xst = B.xst, nrl = blockDim.x / xst;
-  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
-  const bool valid = rl < nrl && c < B.R && B.active[c];
-  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
-  c64 a = mkc(0.f, 0.f);
-  if (valid)
+__global__ void __launch_bounds__(256) k_bp_rv(BmPtr B, const c64* __restrict__ Rh, const c64* __restrict__ Vv) {
+  const BpRow t = bp_row(B);
+  const int c0 = 2 * t.q, c1 = c0 + 1;
+  const bool on = t.valid && (bp_act(B, c0) || bp_act(B, c1));
+  c64 x0 = mkc(0.f, 0.f), x1 = x0;
+  if (on)
 #pragma unroll 4
-    for (int64_t n = n0 + rl; n < n1; n += nrl) bi_acc(a, Rh[n * xst + c], Vv[n * xst + c]);
-  if (!bm_reduce(B, c, rl, nrl, valid, ccast<double>(a), mkc(0.0, 0.0))) return;
+    for (int64_t n = t.n0 + t.rl; n < t.n1; n += t.nrl) {
+      const int64_t o = n * B.xst + c0;
+      const float4 h = ld4(Rh + o), v = ld4(Vv + o);
+      bi_acc(x0, lo(h), lo(v));
+      bi_acc(x1, hi(h), hi(v));
+    }
+  const c128 z = mkc(0.0, 0.0);
+  if (!bp_reduce(B, t, ccast<double>(x0), z, ccast<double>(x1), z)) return;
   bm_finish(B, [&](int r, c128 rv, c128) {
     if (!B.active[r]) return;
     B.fresh[r] = 0;
@@ -2416,21 +2461,23 @@ __global__ void __launch_bounds__(256) k_bm_rv(BmPtr B, const c64* __restrict__ 
 }
 
 // omega = (t^H s) / (t^H t)
-__global__ void __launch_bounds__(256) k_bm_ts(BmPtr B, const c64* __restrict__ Tv, const c64* __restrict__ Sv) {
-  const int xst = B.xst, nrl = blockDim.x / xst;
-  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
-  const bool valid = rl < nrl && c < B.R && B.active[c];
-  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
-  c64 ts = mkc(0.f, 0.f);
-  float tt = 0.f;
-  if (valid)
+__global__ void __launch_bounds__(256) k_bp_ts(BmPtr B, const c64* __restrict__ Tv, const c64* __restrict__ Sv) {
+  const BpRow t = bp_row(B);
+  const int c0 = 2 * t.q, c1 = c0 + 1;
+  const bool on = t.valid && (bp_act(B, c0) || bp_act(B, c1));
+  c64 x0 = mkc(0.f, 0.f), x1 = x0;
+  float y0 = 0.f, y1 = 0.f;
+  if (on)
 #pragma unroll 4
-    for (int64_t n = n0 + rl; n < n1; n += nrl) {
-      const c64 t = Tv[n * xst + c];
-      bi_acc(ts, t, Sv[n * xst + c]);
-      bi_nrm(tt, t);
+    for (int64_t n = t.n0 + t.rl; n < t.n1; n += t.nrl) {
+      const int64_t o = n * B.xst + c0;
+      const float4 tv = ld4(Tv + o), sv = ld4(Sv + o);
+      bi_acc(x0, lo(tv), lo(sv));
+      bi_acc(x1, hi(tv), hi(sv));
+      bi_nrm(y0, lo(tv));
+      bi_nrm(y1, hi(tv));
     }
-  if (!bm_reduce(B, c, rl, nrl, valid, ccast<double>(ts), mkc((double)tt, 0.0))) return;
+  if (!bp_reduce(B, t, ccast<double>(x0), mkc((double)y0, 0.0), ccast<double>(x1), mkc((double)y1, 0.0))) return;
   bm_finish(B, [&](int r, c128 sts, c128 stt) {
     if (!B.active[r]) return;
     if (!finite_z(sts) || !isfinite(stt.re)) {
@@ -2441,30 +2488,40 @@ __global__ void __launch_bounds__(256) k_bm_ts(BmPtr B, const c64* __restrict__ 
   });
 }
 
-// y += alpha p + omega s, r = s - omega t; rho' = rh^H r and |r| decide the next step
-__global__ void __launch_bounds__(256) k_bm_xr(BmPtr B, c64* __restrict__ Y, c64* __restrict__ Rv,
+// y += alpha p + omega s, r = s - omega t for the active halves (an inactive half keeps y, whose
+// scalars are zero, and r, which is not written); rho' = rh^H r and |r| decide the next step
+__global__ void __launch_bounds__(256) k_bp_xr(BmPtr B, c64* __restrict__ Y, c64* __restrict__ Rv,
                                                const c64* __restrict__ Rh, const c64* __restrict__ Pv,
                                                const c64* __restrict__ Sv, const c64* __restrict__ Tv) {
-  const int xst = B.xst, nrl = blockDim.x / xst;
-  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
-  const bool valid = rl < nrl && c < B.R && B.active[c];
-  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
-  c64 hr = mkc(0.f, 0.f);
-  float rr = 0.f;
-  if (valid) {
-    const c64 a = ccast<float>(B.alpha[c]), om = ccast<float>(B.omega[c]);
+  const BpRow t = bp_row(B);
+  const int c0 = 2 * t.q, c1 = c0 + 1;
+  const bool a0 = bp_act(B, c0), a1 = bp_act(B, c1);
+  const bool on = t.valid && (a0 || a1);
+  c64 x0 = mkc(0.f, 0.f), x1 = x0;
+  float y0 = 0.f, y1 = 0.f;
+  if (on) {
+    const c64 al0 = bp_sc(B, B.alpha, c0), al1 = bp_sc(B, B.alpha, c1);
+    const c64 om0 = bp_sc(B, B.omega, c0), om1 = bp_sc(B, B.omega, c1);
 #pragma unroll 4
-    for (int64_t n = n0 + rl; n < n1; n += nrl) {
-      const int64_t o = n * xst + c;
-      const c64 sv = Sv[o];
-      Y[o] = Y[o] + a * Pv[o] + om * sv;
-      const c64 rn = sv - om * Tv[o];
-      Rv[o] = rn;
-      bi_acc(hr, Rh[o], rn);
-      bi_nrm(rr, rn);
+    for (int64_t n = t.n0 + t.rl; n < t.n1; n += t.nrl) {
+      const int64_t o = n * B.xst + c0;
+      const float4 y = ld4(Y + o), p = ld4(Pv + o), s = ld4(Sv + o), tv = ld4(Tv + o), h = ld4(Rh + o);
+      st4(Y + o, f4(lo(y) + al0 * lo(p) + om0 * lo(s), hi(y) + al1 * hi(p) + om1 * hi(s)));
+      const c64 r0 = lo(s) - om0 * lo(tv), r1 = hi(s) - om1 * hi(tv);
+      if (a0 && a1) {
+        st4(Rv + o, f4(r0, r1));
+      } else if (a0) {
+        Rv[o] = r0;
+      } else {
+        Rv[o + 1] = r1;
+      }
+      bi_acc(x0, lo(h), r0);
+      bi_acc(x1, hi(h), r1);
+      bi_nrm(y0, r0);
+      bi_nrm(y1, r1);
     }
   }
-  if (!bm_reduce(B, c, rl, nrl, valid, ccast<double>(hr), mkc((double)rr, 0.0))) return;
+  if (!bp_reduce(B, t, ccast<double>(x0), mkc((double)y0, 0.0), ccast<double>(x1), mkc((double)y1, 0.0))) return;
   bm_finish(B, [&](int r, c128 shr, c128 srr) {
     if (!B.active[r]) return;
     const int it = ++B.its[r];
@@ -2484,16 +2541,19 @@ __global__ void __launch_bounds__(256) k_bm_xr(BmPtr B, c64* __restrict__ Y, c64
 }
 
 // True residual check: r holds b - A y; incidences above tol with steps left restart from it.
-__global__ void __launch_bounds__(256) k_bm_check(BmPtr B, const c64* __restrict__ Rv) {
-  const int xst = B.xst, nrl = blockDim.x / xst;
-  const int c = threadIdx.x % xst, rl = threadIdx.x / xst;
-  const bool valid = rl < nrl && c < B.R;
-  const int64_t n0 = (int64_t)blockIdx.x * B.chunk, n1 = min(B.N, n0 + B.chunk);
-  float rr = 0.f;
-  if (valid)
+__global__ void __launch_bounds__(256) k_bp_check(BmPtr B, const c64* __restrict__ Rv) {
+  const BpRow t = bp_row(B);
+  const int c0 = 2 * t.q;
+  float y0 = 0.f, y1 = 0.f;
+  if (t.valid)
 #pragma unroll 4
-    for (int64_t n = n0 + rl; n < n1; n += nrl) bi_nrm(rr, Rv[n * xst + c]);
-  if (!bm_reduce(B, c, rl, nrl, valid, mkc((double)rr, 0.0), mkc(0.0, 0.0))) return;
+    for (int64_t n = t.n0 + t.rl; n < t.n1; n += t.nrl) {
+      const float4 r = ld4(Rv + n * B.xst + c0);
+      bi_nrm(y0, lo(r));
+      bi_nrm(y1, hi(r));
+    }
+  const c128 z = mkc(0.0, 0.0);
+  if (!bp_reduce(B, t, mkc((double)y0, 0.0), z, mkc((double)y1, 0.0), z)) return;
   bm_finish(B, [&](int r, c128 srr, c128) {
     const double rel = B.bnorm[r] > 0.0 ? sqrt(srr.re) / B.bnorm[r] : 0.0;
     B.resid[r] = rel;
@@ -2670,29 +2730,29 @@ int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
   auto launch_steps = [&](cudaStream_t s, int n) -> int {
     for (int i = 0; i < n; ++i) {
       ctx->prof_begin(SWM_K_TRANSPOSE);
-      k_bm_dir<false><<<gC, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Pv);
+      k_bp_dir<false><<<gC, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Pv);
       ctx->prof_end(SWM_K_TRANSPOSE);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_APPLY);
       SWM_TRY(product(s, Pv, Vv, std::false_type{}));
       ctx->prof_end(SWM_K_APPLY);
       ctx->prof_begin(SWM_K_DOTS);
-      k_bm_rv<<<gC, 256, 0, s>>>(B, Rh, Vv);
+      k_bp_rv<<<gC, 256, 0, s>>>(B, Rh, Vv);
       ctx->prof_end(SWM_K_DOTS);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_TRANSPOSE);
-      k_bm_dir<true><<<gC, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Sv);
+      k_bp_dir<true><<<gC, 256, 0, s>>>(B, Rv, Rh, Pv, Vv, Sv);
       ctx->prof_end(SWM_K_TRANSPOSE);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_APPLY);
       SWM_TRY(product(s, Sv, Tv, std::false_type{}));
       ctx->prof_end(SWM_K_APPLY);
       ctx->prof_begin(SWM_K_DOTS);
-      k_bm_ts<<<gC, 256, 0, s>>>(B, Tv, Sv);
+      k_bp_ts<<<gC, 256, 0, s>>>(B, Tv, Sv);
       ctx->prof_end(SWM_K_DOTS);
       SWM_LAUNCHED();
       ctx->prof_begin(SWM_K_UPDATE);
-      k_bm_xr<<<gC, 256, 0, s>>>(B, Y, Rv, Rh, Pv, Sv, Tv);
+      k_bp_xr<<<gC, 256, 0, s>>>(B, Y, Rv, Rh, Pv, Sv, Tv);
       ctx->prof_end(SWM_K_UPDATE);
       SWM_LAUNCHED();
     }
@@ -2702,7 +2762,7 @@ int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
     ctx->prof_begin(SWM_K_APPLY);
     SWM_TRY(product(st, Y, Rv, std::true_type{}));
     ctx->prof_end(SWM_K_APPLY);
-    k_bm_check<<<gC, 256, 0, st>>>(B, Rv);
+    k_bp_check<<<gC, 256, 0, st>>>(B, Rv);
     SWM_LAUNCHED();
     return SWM_OK;
   };
