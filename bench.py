@@ -418,8 +418,9 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
 # traffic is this ratio times its own algorithmic bytes per launch.  The capture is recorded with
 # the profile summaries.  A class without a capture of its current code reports null.
 MEASURED_TRAFFIC = {
-    # k_spmv_wg, complex64, incidence-minor (BiCGSTAB step): 1.0628 GB against 1.0766 GB
-    ("learned", "apply", "c64", "bicgstab"): 1.0628e9 / 1.0766e9,
+    # k_spmv_wg form 73 (small CTAs), complex64, incidence-minor (BiCGSTAB step): 1.0665 GB
+    # against 1.0766 GB
+    ("learned", "apply", "c64", "bicgstab"): 1.0665e9 / 1.0766e9,
 }
 
 PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "apply", "transpose", "dots", "update",
