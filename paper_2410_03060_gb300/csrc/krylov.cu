@@ -484,7 +484,8 @@ __global__ void __launch_bounds__(256, 3) k_spmv_wp(KPtr P, const int64_t* __res
 // shared memory with each entry expanded to (re, re, im, im), so one 16-byte load gives the two
 // packed operands; it copies the tile's column map too.  The row loop is unrolled to the largest
 // row count of the warp's wires (warp-uniform, rows beyond a wire's own are predicated off), and
-// the gathered values of the next column pair are loaded while the current pair is multiplied.
+// the gathered values of the next column pair are loaded while the current pair is multiplied
+// (their column indices one pair earlier still).
 constexpr int kWmSmemC = 4 * 1024;  // column-map entries of a tile
 // E budgets (expanded entries, 16 bytes each) of the two launch shapes: three CTAs per SM with
 // 48 KB (measured faster than 64 KB although more tiles of dense regions fall back to global
@@ -534,13 +535,24 @@ __device__ __forceinline__ void wm_rows(int64_t N, int i0, int mm, int K, EA Es,
     x0 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[0] * xst));
     x1 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[K > 1 ? 1 : 0] * xst));
   }
+  // column indices one pair further ahead than the gathered values, so that a gather's address
+  // never waits on its column-map load
+  int d0 = 0, d1 = 0;
+  if (K > 2) {
+    d0 = cms[2];
+    d1 = cms[K > 3 ? 3 : 2];
+  }
   EA er = Es;
   er.p += (int64_t)i0 * K;
   for (int k = 0; k < K; k += 2) {
     float4 n0 = x0, n1 = x1;
     if (k + 2 < K) {
-      n0 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[k + 2] * xst));
-      n1 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)cms[k + 3 < K ? k + 3 : k + 2] * xst));
+      n0 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)d0 * xst));
+      n1 = __ldg(reinterpret_cast<const float4*>(xs + (int64_t)d1 * xst));
+      if (k + 4 < K) {
+        d0 = cms[k + 4];
+        d1 = cms[k + 5 < K ? k + 5 : k + 4];
+      }
     }
     const bool two = k + 1 < K;
     float2 xr0, xi0, nxi0, xr1, xi1, nxi1;
