@@ -154,13 +154,13 @@ typedef struct swm_stats {
  * kernel of each GMRES step instead of the persistent cooperative kernel;
  * SWM_PERSIST_CTAS (default 0 = one per SM) -- CTAs of the persistent solve, at most one per SM;
  * SWM_PRODUCT_FORM (default 0 = timed choice) -- with several incidences, the product form of the
- * per-kernel GMRES (and, for 68-73, of BiCGSTAB) to use instead of timing them: 4, 8 or 16
+ * per-kernel GMRES (and, for 68-75, of BiCGSTAB) to use instead of timing them: 4, 8 or 16
  * incidences per read of E, 32 the incidence-minor form (12 or more incidences), 64 the
  * wire-tiled form (65: the same with five CTAs per SM; 67: two incidences per thread and the
  * tile's E in shared memory; 68/69: two incidences per thread in packed FP32x2 arithmetic, E
  * staged in shared memory, three CTAs per SM with 48 KB or two with 96 KB; 70/71: the packed form
  * reading E from global memory, three or four CTAs per SM; 72/73: the same in small CTAs of a
- * few whole warps);
+ * few whole warps; 74/75: small CTAs with E and the column map staged by cp.async);
  * SWM_BICGSTAB_MAJOR (default 0, a test hook) -- 1 keeps BiCGSTAB's vectors incidence-major on the
  * complex64 path (as on the float64 path and with one incidence) instead of incidence-minor;
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the

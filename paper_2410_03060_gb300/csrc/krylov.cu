@@ -725,6 +725,93 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wg(KPtr P, const int64_t* __
   }
 }
 
+// The packed product in small CTAs with the tile's E and column map staged in shared memory as
+// stored (not expanded) by cp.async: each thread issues 16-byte copies of the tile's two
+// contiguous ranges (the 16-byte-aligned span around each; a partial last chunk reads only its
+// own bytes and zero-fills the rest), so the whole tile is in flight at once and the row loop
+// reads E and the column map at shared-memory latency.  A tile whose ranges exceed the budgets
+// reads them from global memory.  E and the column map must start on 16-byte boundaries (the
+// launch checks), so that no chunk reaches before either buffer.
+constexpr int kWaSmemE = 16 * 1024, kWaSmemC = 4 * 1024;
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+template <typename TE, int MODE = kStepW, int MINB = 3, bool MINOR = false>
+__global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
+                                                    const TE* __restrict__ E, const c64* __restrict__ U,
+                                                    const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
+                                                    const c64* __restrict__ B, int RQ, int WB) {
+  constexpr bool ALL = MODE != kStepW;
+  if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
+  extern __shared__ __align__(16) unsigned char sm_wa[];
+  __shared__ int sK[kWpMaxWires], sm_m[kWpMaxWires], seo[kWpMaxWires], sco[kWpMaxWires];
+  const int64_t N = P.N;
+  const int64_t p0 = (int64_t)blockIdx.x * WB;
+  const int nwt = (int)min((int64_t)min(WB, kWpMaxWires), nw - p0);
+  const int64_t e0 = lay.rowbase[p0], c0 = lay.cmbase[p0];
+  const unsigned char* eb = reinterpret_cast<const unsigned char*>(E + e0);
+  const unsigned char* ea = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(eb) & ~(uintptr_t)15);
+  const unsigned char* cb = reinterpret_cast<const unsigned char*>(lay.colmap + c0);
+  const unsigned char* ca = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(cb) & ~(uintptr_t)15);
+  const int64_t enb = reinterpret_cast<const unsigned char*>(E + lay.rowbase[p0 + nwt]) - ea;
+  const int64_t cnb = reinterpret_cast<const unsigned char*>(lay.colmap + lay.cmbase[p0 + nwt]) - ca;
+  const bool fits = enb <= kWaSmemE && cnb <= kWaSmemC;
+  if (threadIdx.x < nwt) {
+    const int64_t p = p0 + threadIdx.x;
+    sK[threadIdx.x] = lay.K[p];
+    sm_m[threadIdx.x] = (int)(off[p + 1] - off[p]);
+    seo[threadIdx.x] = (int)(lay.rowbase[p] - e0);
+    sco[threadIdx.x] = (int)(lay.cmbase[p] - c0);
+  }
+  if (fits) {
+    const int ne = (int)enb, nc = (int)cnb;
+    for (int c = 16 * (int)threadIdx.x; c < ne; c += 16 * (int)blockDim.x) cp_async16(sm_wa + c, ea + c, min(16, ne - c));
+    for (int c = 16 * (int)threadIdx.x; c < nc; c += 16 * (int)blockDim.x)
+      cp_async16(sm_wa + kWaSmemE + c, ca + c, min(16, nc - c));
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  const int pl = (int)threadIdx.x / RQ, q = (int)threadIdx.x % RQ;
+  const int ra = blockIdx.y * 2 * RQ + 2 * q, rb = ra + 1;
+  const bool valid = pl < nwt && ra < P.R;
+  const int mw = __reduce_max_sync(0xffffffffu, valid ? sm_m[pl] : 0);
+  if (!valid) return;
+  const bool wa = ALL || P.active[ra];
+  const bool wb = rb < P.R && (ALL || P.active[rb]);
+  if (!wa && !wb) return;
+  const int64_t p = p0 + pl;
+  const int K = sK[pl], m = sm_m[pl];
+  // E and the column map of the wire: in shared memory at the tile's offsets, else in global memory
+  const TE* ep = fits ? reinterpret_cast<const TE*>(sm_wa + (eb - ea)) + seo[pl] : E + lay.rowbase[p];
+  const int32_t* cms =
+      fits ? reinterpret_cast<const int32_t*>(sm_wa + kWaSmemE + (cb - ca)) + sco[pl] : lay.colmap + lay.cmbase[p];
+  const EGlobal<TE> er{ep};
+  const c64* xs = Xt + ra;
+  const int64_t orow = MINOR ? off[p] : (int64_t)ra * N + off[p];
+  if constexpr (MINOR) {
+    U += ra;
+    Wv += ra;
+    if (B) B += ra;
+  }
+  switch (mw) {
+    case 1: wm_rows<MODE, 1, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 2: wm_rows<MODE, 2, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 3: wm_rows<MODE, 3, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 4: wm_rows<MODE, 4, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 5: wm_rows<MODE, 5, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 6: wm_rows<MODE, 6, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 7: wm_rows<MODE, 7, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    default:
+      for (int i0 = 0; i0 < m; i0 += 8)
+        wm_rows<MODE, 8, EGlobal<TE>, MINOR>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
+      break;
+  }
+}
+
 // Launch of k_spmv_wm in one of its two shapes (three CTAs per SM with the 64 KB E budget, or two
 // with 96 KB), and the shared-memory opt-in of its instances.
 template <typename TE, bool RS, bool MINOR = false>
@@ -746,7 +833,9 @@ int launch_wm(cudaStream_t s, int form, const KPtr& P, swm_ctx* ctx, const TE* E
                                                       WBp);
       break;
     case 72:
-    case 73: {
+    case 73:
+    case 74:
+    case 75: {
       // small CTAs (a few whole warps) so that a CTA's registers come free as soon as its few
       // wires are done: w wires of RQ threads in 32 ceil(w RQ / 32) threads, w chosen for the
       // fewest idle lanes
@@ -763,7 +852,18 @@ int launch_wm(cudaStream_t s, int form, const KPtr& P, swm_ctx* ctx, const TE* E
         }
       }
       const dim3 gs((unsigned)ceil_div(ctx->nw, bw), g.y);
-      if (form == 72)
+      // E and the column map staged by cp.async: the 16-byte spans around the tiles' ranges stay
+      // inside the buffers only if both start on 16-byte boundaries (else form 73)
+      const bool al16 =
+          !(reinterpret_cast<uintptr_t>(E) & 15) && !(reinterpret_cast<uintptr_t>(ctx->offd.colmap) & 15);
+      if ((form == 74 || form == 75) && al16) {
+        if (form == 74)
+          k_spmv_wa<TE, MODE, 3, MINOR><<<gs, bt, kWaSmemE + kWaSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
+                                                                           Xt, xst, dst, Bv, RQ, bw);
+        else
+          k_spmv_wa<TE, MODE, 4, MINOR><<<gs, bt, kWaSmemE + kWaSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
+                                                                           Xt, xst, dst, Bv, RQ, bw);
+      } else if (form == 72)
         k_spmv_wg<TE, MODE, 3, MINOR><<<gs, bt, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
                                                         bw);
       else
@@ -1469,6 +1569,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       case kWire + 7:  // the same with four CTAs per SM
       case kWire + 8:  // the same in small CTAs of a few whole warps (register budget of 70)
       case kWire + 9:  // the same in small CTAs (register budget of 71)
+      case kWire + 10:  // small CTAs, E and the column map staged by cp.async (budget of 70)
+      case kWire + 11:  // the same with the register budget of 71
         if constexpr (std::is_same<TV, float>::value) {
           if (ws->Xt && R <= 256) {
             const int xst = R + (R & 1);
@@ -1561,7 +1663,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
     const int forced = ctx->product_form;
     if (forced == 4 || forced == 8 || forced == 16 || forced == kWire || forced == kWire + 1 ||
-        forced == kWire + 3 || forced == kWire + 4 || forced == kWire + 5 || forced == kWire + 6 || forced == kWire + 7 || forced == kWire + 8 || forced == kWire + 9 || (forced == kMinor && ws->Xt)) {
+        (forced >= kWire + 3 && forced <= kWire + 11) || (forced == kMinor && ws->Xt)) {
       rb = forced;
     } else if (found) {
       rb = found;
@@ -1575,7 +1677,8 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3, kWire + 4, kWire + 5, kWire + 6, kWire + 7, kWire + 8, kWire + 9}) {
+      for (int b : {4, 8, 16, kMinor, kWire, kWire + 1, kWire + 3, kWire + 4, kWire + 5, kWire + 6, kWire + 7,
+                    kWire + 8, kWire + 9, kWire + 10, kWire + 11}) {
         if (b == 16 && ceil_div(R, 16) == ceil_div(R, 8)) continue;  // no fewer reads of E than with 8
         if (b == kMinor && !ws->Xt) continue;
         SWM_TRY(launch_product(st, b));
@@ -2176,7 +2279,7 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
     int found = 0;
     for (const auto& t : ctx->tuned)
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
-    if (ctx->product_form >= 68 && ctx->product_form <= 73) {
+    if (ctx->product_form >= 68 && ctx->product_form <= 75) {
       form = ctx->product_form;
     } else if (found) {
       form = found;
@@ -2188,7 +2291,7 @@ int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int f : {68, 69, 70, 71, 72, 73}) {
+      for (int f : {68, 69, 70, 71, 72, 73, 74, 75}) {
         form = f;
         SWM_TRY(product(st, Bv, Vv, std::true_type{}));
         SWM_CK(cudaEventRecord(e0, st));
@@ -2704,7 +2807,7 @@ int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
     int found = 0;
     for (const auto& t : ctx->tuned)
       if (std::memcmp(t.shape, shape, sizeof(shape)) == 0) found = t.rb;
-    if (ctx->product_form >= 68 && ctx->product_form <= 73) {
+    if (ctx->product_form >= 68 && ctx->product_form <= 75) {
       form = ctx->product_form;
     } else if (found) {
       form = found;
@@ -2714,7 +2817,7 @@ int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
       SWM_CK(cudaEventCreate(&e0));
       SWM_CK(cudaEventCreate(&e1));
       float best = 0.f;
-      for (int f : {68, 69, 70, 71, 72, 73}) {
+      for (int f : {68, 69, 70, 71, 72, 73, 74, 75}) {
         form = f;
         SWM_TRY(product(st, Bt, Vv, std::true_type{}));
         SWM_CK(cudaEventRecord(e0, st));

@@ -42,7 +42,8 @@ def _many(n, seed):
 
 @pytest.mark.parametrize("n_inc,form,major", [(1, 0, 0), (9, 0, 0), (9, 0, 1), (37, 68, 0), (37, 69, 0), (37, 70, 0),
                                                (37, 71, 0), (37, 71, 1), (37, 68, 1),
-                                               (37, 72, 0), (37, 73, 0), (37, 73, 1)])
+                                               (37, 72, 0), (37, 73, 0), (37, 73, 1),
+                                               (37, 74, 0), (37, 75, 0), (37, 75, 1)])
 def test_bicgstab_currents_and_rcs_match_oracle_lu(monkeypatch, n_inc, form, major):
     """form: the packed product's shape forced (68/69: E staged in shared memory, three or two CTAs
     per SM; 70/71: E read from global memory, three or four CTAs per SM; 72/73: the same in small

@@ -495,7 +495,7 @@ def test_split_step_path_matches_oracle(monkeypatch):
                 assert_rcs_db(out["sigma"][i, :, 0], s_ref[i, :, 0], db=0.1)
 
 
-@pytest.mark.parametrize("form", [4, 8, 16, 32, 64, 65, 67, 68, 69, 70, 71, 72, 73])
+@pytest.mark.parametrize("form", [4, 8, 16, 32, 64, 65, 67, 68, 69, 70, 71, 72, 73, 74, 75])
 def test_every_product_form_matches_oracle(monkeypatch, form):
     """Each form of the many-incidence product, forced (SWM_PRODUCT_FORM) on the large-system GMRES
     step: 4/8/16 incidences per read of E, 32 the incidence-minor form, 64 and 65 the wire-tiled
@@ -503,7 +503,7 @@ def test_every_product_form_matches_oracle(monkeypatch, form):
     68 and 69: the same with packed FP32x2 arithmetic, E expanded in shared memory, three CTAs
     per SM with a 48 KB budget and two with 96 KB; 70 and 71: packed, E and the column map read
     from global memory, three and four CTAs per SM; 72 and 73: the same in small CTAs of a few
-    whole warps).
+    whole warps; 74 and 75: small CTAs with E and the column map staged by cp.async).
     Clouds with every segment count 2..16 (wires of up to 15 rows, two row groups in the
     wire-tiled form) and ragged tiles, one dense (a tile's E exceeds the shared-memory budget, so
     the forms that stage it read it from global memory) and one sparse (it fits); 37 and 70
