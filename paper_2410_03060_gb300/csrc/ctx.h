@@ -119,6 +119,7 @@ struct swm_ctx {
   int64_t* ublk = nullptr;     // [nup] blocks (p, q) with q > p
   int64_t* minv_off = nullptr; // [nw + 1] offsets of the m_p x m_p inverse blocks
   int32_t* rowwire = nullptr;  // [N] internal wire of each scalar row
+  int32_t* wperm = nullptr;    // [nw] wire order of the small-CTA product (sorted within windows)
   void* rowinfo = nullptr;     // [N] row descriptors of E (value offset, column-map offset, length)
   int64_t nminv = 0;           // entries of the packed self-block inverses
   unsigned long long* d_evals = nullptr;  // fill evaluation counter (device)
@@ -298,6 +299,7 @@ void set_stateless_error(const std::string& msg);
 // krylov.cu: a6
 int gmres_solve(swm_ctx* ctx, double tol, int restart, int max_iter);
 int bicgstab_solve(swm_ctx* ctx, double tol, int max_iter);
+int build_wire_order(swm_ctx* ctx);
 // row descriptors of E (built once per build) and x = M^-1 y into ctx->Xv
 int ensure_rowinfo(swm_ctx* ctx);
 // y = y0 (ctx->guess, complex128) or 0 at the start of a solve, in the vector precision

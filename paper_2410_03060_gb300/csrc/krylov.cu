@@ -725,14 +725,18 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wg(KPtr P, const int64_t* __
   }
 }
 
-// The packed product in small CTAs with the tile's E and column map staged in shared memory as
-// stored (not expanded) by cp.async: each thread issues 16-byte copies of the tile's two
-// contiguous ranges (the 16-byte-aligned span around each; a partial last chunk reads only its
-// own bytes and zero-fills the rest), so the whole tile is in flight at once and the row loop
-// reads E and the column map at shared-memory latency.  A tile whose ranges exceed the budgets
-// reads them from global memory.  E and the column map must start on 16-byte boundaries (the
-// launch checks), so that no chunk reaches before either buffer.
-constexpr int kWaSmemE = 16 * 1024, kWaSmemC = 4 * 1024;
+// The packed product in small CTAs with each wire's E rows and column map staged in shared memory
+// as stored (not expanded) by cp.async: every thread issues 16-byte copies of the 16-byte-aligned
+// spans around the tile's ranges (a partial last chunk reads only its own bytes and zero-fills the
+// rest), so the whole tile is in flight at once and the row loop reads E and the column map at
+// shared-memory latency.  A tile whose spans exceed the budgets reads them from global memory.
+// E and the column map must start on 16-byte boundaries (the launch checks), so that no span
+// reaches before either buffer.  With an order (perm, nullable) the CTA takes wires perm[p0 + i]
+// instead of p0 + i.
+// The E budget, 22 KB, holds all but about 0.5 % of the work's tiles at three CTAs' register
+// budget (eight CTAs per SM, as many as its registers allow).
+constexpr int kWaSmemE3 = 22 * 1024, kWaSmemC = 4 * 1024;
+constexpr int kWaMaxWires = 8;  // wires per small CTA, at most
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int bytes) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
@@ -740,38 +744,75 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int byt
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
-template <typename TE, int MODE = kStepW, int MINB = 3, bool MINOR = false>
+template <typename TE, int MODE = kStepW, int MINB = 3, bool MINOR = false, int EB = kWaSmemE3>
 __global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
                                                     const TE* __restrict__ E, const c64* __restrict__ U,
                                                     const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
-                                                    const c64* __restrict__ B, int RQ, int WB) {
+                                                    const c64* __restrict__ B, int RQ, int WB,
+                                                    const int32_t* __restrict__ perm) {
   constexpr bool ALL = MODE != kStepW;
   if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   extern __shared__ __align__(16) unsigned char sm_wa[];
-  __shared__ int sK[kWpMaxWires], sm_m[kWpMaxWires], seo[kWpMaxWires], sco[kWpMaxWires];
+  // per wire: its index, K, rows, the aligned starts of its E and column-map spans, their sizes
+  // and offsets in shared memory, and the offsets of its first entries within the spans
+  __shared__ const unsigned char* sea[kWaMaxWires];
+  __shared__ const unsigned char* sca[kWaMaxWires];
+  __shared__ int64_t sp[kWaMaxWires];
+  __shared__ int sK[kWaMaxWires], sm_m[kWaMaxWires], sen[kWaMaxWires], scn[kWaMaxWires];
+  __shared__ int soe[kWaMaxWires], soc[kWaMaxWires], she[kWaMaxWires], shc[kWaMaxWires];
+  __shared__ int sfit;
   const int64_t N = P.N;
   const int64_t p0 = (int64_t)blockIdx.x * WB;
-  const int nwt = (int)min((int64_t)min(WB, kWpMaxWires), nw - p0);
-  const int64_t e0 = lay.rowbase[p0], c0 = lay.cmbase[p0];
-  const unsigned char* eb = reinterpret_cast<const unsigned char*>(E + e0);
-  const unsigned char* ea = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(eb) & ~(uintptr_t)15);
-  const unsigned char* cb = reinterpret_cast<const unsigned char*>(lay.colmap + c0);
-  const unsigned char* ca = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(cb) & ~(uintptr_t)15);
-  const int64_t enb = reinterpret_cast<const unsigned char*>(E + lay.rowbase[p0 + nwt]) - ea;
-  const int64_t cnb = reinterpret_cast<const unsigned char*>(lay.colmap + lay.cmbase[p0 + nwt]) - ca;
-  const bool fits = enb <= kWaSmemE && cnb <= kWaSmemC;
-  if (threadIdx.x < nwt) {
-    const int64_t p = p0 + threadIdx.x;
-    sK[threadIdx.x] = lay.K[p];
-    sm_m[threadIdx.x] = (int)(off[p + 1] - off[p]);
-    seo[threadIdx.x] = (int)(lay.rowbase[p] - e0);
-    sco[threadIdx.x] = (int)(lay.cmbase[p] - c0);
+  const int nwt = (int)min((int64_t)min(WB, kWaMaxWires), nw - p0);
+  if (threadIdx.x < 32) {
+    const int i = threadIdx.x;
+    int en = 0, cn = 0;
+    if (i < nwt) {
+      const int64_t p = perm ? (int64_t)perm[p0 + i] : p0 + i;
+      const unsigned char* eb = reinterpret_cast<const unsigned char*>(E + lay.rowbase[p]);
+      const unsigned char* ea = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(eb) & ~(uintptr_t)15);
+      const unsigned char* cb = reinterpret_cast<const unsigned char*>(lay.colmap + lay.cmbase[p]);
+      const unsigned char* ca = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(cb) & ~(uintptr_t)15);
+      const int K = lay.K[p], m = (int)(off[p + 1] - off[p]);
+      en = (int)(reinterpret_cast<const unsigned char*>(E + lay.rowbase[p] + (int64_t)m * K) - ea);
+      cn = (int)(reinterpret_cast<const unsigned char*>(lay.colmap + lay.cmbase[p] + K) - ca);
+      sp[i] = p;
+      sK[i] = K;
+      sm_m[i] = m;
+      sea[i] = ea;
+      sca[i] = ca;
+      sen[i] = en;
+      scn[i] = cn;
+      she[i] = (int)(eb - ea);
+      shc[i] = (int)(cb - ca);
+    }
+    // offsets of the spans in shared memory: inclusive scans of the 16-byte-rounded sizes
+    int oe = (en + 15) & ~15, oc = (cn + 15) & ~15;
+#pragma unroll
+    for (int o = 1; o < kWaMaxWires; o <<= 1) {
+      const int a = __shfl_up_sync(0xffffffffu, oe, o), b = __shfl_up_sync(0xffffffffu, oc, o);
+      if (i >= o) {
+        oe += a;
+        oc += b;
+      }
+    }
+    if (i < nwt) {
+      soe[i] = oe - ((en + 15) & ~15);
+      soc[i] = EB + oc - ((cn + 15) & ~15);
+    }
+    if (i == kWaMaxWires - 1) sfit = oe <= EB && oc <= kWaSmemC;
   }
+  __syncthreads();
+  const bool fits = sfit;
   if (fits) {
-    const int ne = (int)enb, nc = (int)cnb;
-    for (int c = 16 * (int)threadIdx.x; c < ne; c += 16 * (int)blockDim.x) cp_async16(sm_wa + c, ea + c, min(16, ne - c));
-    for (int c = 16 * (int)threadIdx.x; c < nc; c += 16 * (int)blockDim.x)
-      cp_async16(sm_wa + kWaSmemE + c, ca + c, min(16, nc - c));
+    for (int w = 0; w < nwt; ++w) {
+      const int ne = sen[w], nc = scn[w];
+      const unsigned char *ea = sea[w], *ca = sca[w];
+      for (int c = 16 * (int)threadIdx.x; c < ne; c += 16 * (int)blockDim.x)
+        cp_async16(sm_wa + soe[w] + c, ea + c, min(16, ne - c));
+      for (int c = 16 * (int)threadIdx.x; c < nc; c += 16 * (int)blockDim.x)
+        cp_async16(sm_wa + soc[w] + c, ca + c, min(16, nc - c));
+    }
     cp_async_wait_all();
   }
   __syncthreads();
@@ -783,12 +824,12 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __
   const bool wa = ALL || P.active[ra];
   const bool wb = rb < P.R && (ALL || P.active[rb]);
   if (!wa && !wb) return;
-  const int64_t p = p0 + pl;
+  const int64_t p = sp[pl];
   const int K = sK[pl], m = sm_m[pl];
-  // E and the column map of the wire: in shared memory at the tile's offsets, else in global memory
-  const TE* ep = fits ? reinterpret_cast<const TE*>(sm_wa + (eb - ea)) + seo[pl] : E + lay.rowbase[p];
+  // E and the column map of the wire: in shared memory, else in global memory
+  const TE* ep = fits ? reinterpret_cast<const TE*>(sm_wa + soe[pl] + she[pl]) : E + lay.rowbase[p];
   const int32_t* cms =
-      fits ? reinterpret_cast<const int32_t*>(sm_wa + kWaSmemE + (cb - ca)) + sco[pl] : lay.colmap + lay.cmbase[p];
+      fits ? reinterpret_cast<const int32_t*>(sm_wa + soc[pl] + shc[pl]) : lay.colmap + lay.cmbase[p];
   const EGlobal<TE> er{ep};
   const c64* xs = Xt + ra;
   const int64_t orow = MINOR ? off[p] : (int64_t)ra * N + off[p];
@@ -811,6 +852,56 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __
       break;
   }
 }
+
+// Wire order of the small-CTA product: within each window of kOrderWin consecutive wires (wires
+// near one another in space), the wires sorted by (column pairs, rows), so that the two or three
+// wires sharing a warp run row loops of about the same length.  One CTA per window, a bitonic
+// sort of (key, position) in shared memory; positions past the last wire sort last.
+constexpr int kOrderWin = 2048;
+__global__ void __launch_bounds__(1024) k_wire_order(int64_t nw, const int32_t* __restrict__ K,
+                                                     const int64_t* __restrict__ off, int32_t* __restrict__ perm) {
+  __shared__ unsigned long long key[kOrderWin];
+  const int64_t base = (int64_t)blockIdx.x * kOrderWin;
+  for (int t = threadIdx.x; t < kOrderWin; t += blockDim.x) {
+    const int64_t p = base + t;
+    unsigned hi = 0xffffffffu;
+    if (p < nw) {
+      const unsigned kp = (unsigned)min((K[p] + 1) / 2, 32767);
+      const unsigned mp = (unsigned)min((int64_t)65535, off[p + 1] - off[p]);
+      hi = (kp << 16) | mp;
+    }
+    key[t] = ((unsigned long long)hi << 32) | (unsigned)t;
+  }
+  __syncthreads();
+  for (int k = 2; k <= kOrderWin; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < kOrderWin; t += blockDim.x) {
+        const int o = t ^ j;
+        if (o > t) {
+          const unsigned long long a = key[t], b = key[o];
+          if ((a > b) == ((t & k) == 0)) {
+            key[t] = b;
+            key[o] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < kOrderWin; t += blockDim.x) {
+    const int64_t p = base + t;
+    if (p < nw) perm[p] = (int32_t)(base + (int64_t)(key[t] & 0xffffffffu));
+  }
+}
+}  // namespace
+int build_wire_order(swm_ctx* ctx) {
+  if (ctx->nw <= 0 || ctx->nw > INT32_MAX) return SWM_OK;
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&ctx->wperm, sizeof(int32_t) * ctx->nw));
+  k_wire_order<<<(unsigned)ceil_div(ctx->nw, kOrderWin), 1024, 0, ctx->stream>>>(ctx->nw, ctx->offd.K, ctx->off,
+                                                                                ctx->wperm);
+  SWM_LAUNCHED();
+  return SWM_OK;
+}
+namespace {
 
 // Launch of k_spmv_wm in one of its two shapes (three CTAs per SM with the 64 KB E budget, or two
 // with 96 KB), and the shared-memory opt-in of its instances.
@@ -856,13 +947,13 @@ int launch_wm(cudaStream_t s, int form, const KPtr& P, swm_ctx* ctx, const TE* E
       // inside the buffers only if both start on 16-byte boundaries (else form 73)
       const bool al16 =
           !(reinterpret_cast<uintptr_t>(E) & 15) && !(reinterpret_cast<uintptr_t>(ctx->offd.colmap) & 15);
-      if ((form == 74 || form == 75) && al16) {
+      if ((form == 74 || (form == 75 && ctx->wperm)) && al16) {
         if (form == 74)
-          k_spmv_wa<TE, MODE, 3, MINOR><<<gs, bt, kWaSmemE + kWaSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
-                                                                           Xt, xst, dst, Bv, RQ, bw);
+          k_spmv_wa<TE, MODE, 3, MINOR, kWaSmemE3><<<gs, bt, kWaSmemE3 + kWaSmemC, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, bw, nullptr);
         else
-          k_spmv_wa<TE, MODE, 4, MINOR><<<gs, bt, kWaSmemE + kWaSmemC, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src,
-                                                                           Xt, xst, dst, Bv, RQ, bw);
+          k_spmv_wa<TE, MODE, 3, MINOR, kWaSmemE3><<<gs, bt, kWaSmemE3 + kWaSmemC, s>>>(
+              P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, bw, ctx->wperm);
       } else if (form == 72)
         k_spmv_wg<TE, MODE, 3, MINOR><<<gs, bt, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
                                                         bw);
@@ -1570,7 +1661,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
       case kWire + 8:  // the same in small CTAs of a few whole warps (register budget of 70)
       case kWire + 9:  // the same in small CTAs (register budget of 71)
       case kWire + 10:  // small CTAs, E and the column map staged by cp.async (budget of 70)
-      case kWire + 11:  // the same with the register budget of 71
+      case kWire + 11:  // the same over the wires sorted by loop length within windows
         if constexpr (std::is_same<TV, float>::value) {
           if (ws->Xt && R <= 256) {
             const int xst = R + (R & 1);

@@ -503,7 +503,8 @@ def test_every_product_form_matches_oracle(monkeypatch, form):
     68 and 69: the same with packed FP32x2 arithmetic, E expanded in shared memory, three CTAs
     per SM with a 48 KB budget and two with 96 KB; 70 and 71: packed, E and the column map read
     from global memory, three and four CTAs per SM; 72 and 73: the same in small CTAs of a few
-    whole warps; 74 and 75: small CTAs with E and the column map staged by cp.async).
+    whole warps; 74: small CTAs with E and the column map staged by cp.async; 75: 74 over the wires sorted
+    by loop length within windows).
     Clouds with every segment count 2..16 (wires of up to 15 rows, two row groups in the
     wire-tiled form) and ragged tiles, one dense (a tile's E exceeds the shared-memory budget, so
     the forms that stage it read it from global memory) and one sparse (it fits); 37 and 70
