@@ -414,13 +414,14 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch over the launch's
 # algorithmic bytes, from one ncu capture of the kernel's current code on the 250,000-wire cloud
-# of the same density, keyed by (workload, kernel class, precision, solver); the bench line's
-# traffic is this ratio times its own algorithmic bytes per launch.  The capture is recorded with
-# the profile summaries.  A class without a capture of its current code reports null.
+# of the same density, keyed by (workload, kernel class, precision, solver, product form); the
+# bench line's traffic is this ratio times its own algorithmic bytes per launch.  The capture is
+# recorded with the profile summaries.  A class or form without a capture of its current code
+# reports null.
 MEASURED_TRAFFIC = {
-    # k_spmv_wg form 73 (small CTAs), complex64, incidence-minor (BiCGSTAB step): 1.0665 GB
-    # against 1.0766 GB
-    ("learned", "apply", "c64", "bicgstab"): 1.0665e9 / 1.0766e9,
+    # k_spmv_wa form 75 (small CTAs, wires sorted by loop length, E staged by cp.async),
+    # complex64, incidence-minor (BiCGSTAB step): 1.0597 GB against 1.0766 GB
+    ("learned", "apply", "c64", "bicgstab", 75): 1.0597e9 / 1.0766e9,
 }
 
 PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "apply", "transpose", "dots", "update",
@@ -519,7 +520,7 @@ def measure(name, args, local, world, rank, with_e2e=True, with_fp64=True, steps
     if roof is not None:
         roof["class"] = dominant
         roof["profiled_steps"] = rsteps
-        ratio = MEASURED_TRAFFIC.get((name, dominant, args.precision, solver))
+        ratio = MEASURED_TRAFFIC.get((name, dominant, args.precision, solver, st.get("step_rhs_block")))
         roof["traffic"] = ratio * roof["per_launch_bytes"] if ratio and "per_launch_bytes" in roof else None
     extra_roofs = {}
     for c in ("fill_mutual", "apply", "transpose", "dots", "update"):

@@ -161,7 +161,7 @@ typedef struct swm_stats {
  * staged in shared memory, three CTAs per SM with 48 KB or two with 96 KB; 70/71: the packed form
  * reading E from global memory, three or four CTAs per SM; 72/73: the same in small CTAs of a
  * few whole warps; 74: small CTAs with E and the column map staged by cp.async; 75: 74 over the wires sorted by
- * loop length within windows of 2048);
+ * loop length within windows of 4096);
  * SWM_BICGSTAB_MAJOR (default 0, a test hook) -- 1 keeps BiCGSTAB's vectors incidence-major on the
  * complex64 path (as on the float64 path and with one incidence) instead of incidence-minor;
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the

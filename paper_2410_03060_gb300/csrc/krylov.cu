@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __
 // near one another in space), the wires sorted by (column pairs, rows), so that the two or three
 // wires sharing a warp run row loops of about the same length.  One CTA per window, a bitonic
 // sort of (key, position) in shared memory; positions past the last wire sort last.
-constexpr int kOrderWin = 2048;
+constexpr int kOrderWin = 4096;
 __global__ void __launch_bounds__(1024) k_wire_order(int64_t nw, const int32_t* __restrict__ K,
                                                      const int64_t* __restrict__ off, int32_t* __restrict__ perm) {
   __shared__ unsigned long long key[kOrderWin];
