@@ -397,16 +397,16 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
     work = b * steps
     ach = work / (prof_ms * 1e-3) / 1e9
     peak = pk.get("hbm_gbs", 6800.0)
-    names = {"apply": "block-sparse product, form %s (k_spmv_wg / k_spmv_wm / k_spmv_wp / k_spmv_w / k_spmv_t / "
-                      "k_spmv, timed per shape)" % st.get("step_rhs_block"),
+    names = {"apply": "block-sparse product, form %s (k_spmv_wa / k_spmv_wg / k_spmv_wm / k_spmv_wp / k_spmv_w / "
+                      "k_spmv_t / k_spmv, timed per shape)" % st.get("step_rhs_block"),
              "transpose": "k_rhs_minor_all: pending vectors to incidence-minor order",
              "dots": "k_dots: delayed Gram-Schmidt inner products",
              "update": "k_update: delayed Gram-Schmidt update",
              "gmres": "k_gmres_persist: persistent GMRES solve"}
     if solver == "bicgstab":
-        names.update({"transpose": "k_bm_dir (k_bi_dir): direction updates p and s",
-                      "dots": "k_bm_rv, k_bm_ts (k_bi_rv, k_bi_ts): inner products r^H v, t^H s, t^H t",
-                      "update": "k_bm_xr (k_bi_xr): y and r updates with r^H r and |r|"})
+        names.update({"transpose": "k_bp_dir (k_bi_dir): direction updates p and s",
+                      "dots": "k_bp_rv, k_bp_ts (k_bi_rv, k_bi_ts): inner products r^H v, t^H s, t^H t",
+                      "update": "k_bp_xr (k_bi_xr): y and r updates with r^H r and |r|"})
     return {"kernel": names.get(cls, cls), "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_source": "of measured (MEASURED_PEAKS.json copy bandwidth)",
             "per_launch_bytes": work / launches, "per_launch_ms": per_launch_ms}
@@ -620,7 +620,7 @@ def run_ours(args):
         "gpu_launches": rec["gpu_launches"],
         "e2e": {"value": total_units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": rec["h2d"],
                 "d2h_bytes_per_step": rec["d2h"], "ms_per_step": e2e_ms,
-                "path": "swm_run from page-locked host buffers (inputs read and RCS written in place)"},
+                "path": "swm_run from page-locked host buffers (inputs copied in by DMA, RCS written in place)"},
         "rcs_err_db_vs_fp64": rec["rcs_err_db_vs_fp64"],
         "rcs_rel_l2_vs_fp64": rec["rcs_rel_l2_vs_fp64"],
         "fp64_path": {"value": total_units / (ms64 * 1e-3), "ms_per_step": ms64,

@@ -424,19 +424,11 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_L, sizeof(double) * nw));
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_a, sizeof(double) * nw));
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_ns, sizeof(int32_t) * nw));
-  // Device inputs, and host inputs in page-locked memory (which the GPU reads in place over the
-  // host link), are copied by k_ingest itself; other host inputs are copied in first.
+  // Device inputs are copied by k_ingest itself; host inputs are copied in first by the copy
+  // engines (page-locked ones at the host link's full rate; measured faster than the kernel
+  // reading them in place) and checked where they land.
   const void* src[5] = {centres, dirs, lengths, radii, nseg};
-  bool dev = mem_kind == SWM_DEVICE;
-  if (!dev) {
-    bool pinned = true;
-    for (int i = 0; i < 5 && pinned; ++i) {
-      void* dp = device_view(src[i]);
-      if (dp) src[i] = dp;
-      else pinned = false;
-    }
-    dev = pinned;
-  }
+  const bool dev = mem_kind == SWM_DEVICE;
   if (!dev) {
     SWM_TRY(copy_in(ctx, ctx->u_c, centres, sizeof(double) * 3 * nw, mem_kind));
     SWM_TRY(copy_in(ctx, ctx->u_t, dirs, sizeof(double) * 3 * nw, mem_kind));

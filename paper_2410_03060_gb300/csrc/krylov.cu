@@ -894,7 +894,7 @@ __global__ void __launch_bounds__(1024) k_wire_order(int64_t nw, const int32_t* 
 }
 }  // namespace
 int build_wire_order(swm_ctx* ctx) {
-  if (ctx->nw <= 0 || ctx->nw > INT32_MAX) return SWM_OK;
+  if (ctx->wperm || ctx->nw <= 0 || ctx->nw > INT32_MAX) return SWM_OK;  // built for this pattern
   SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&ctx->wperm, sizeof(int32_t) * ctx->nw));
   k_wire_order<<<(unsigned)ceil_div(ctx->nw, kOrderWin), 1024, 0, ctx->stream>>>(ctx->nw, ctx->offd.K, ctx->off,
                                                                                 ctx->wperm);
@@ -1748,6 +1748,7 @@ int gmres_impl(swm_ctx* ctx, const TE* E, double tol, int restart, int max_iter,
     return SWM_OK;
   };
   if (!persisted && multi) {
+    SWM_TRY(build_wire_order(ctx));  // form 75 (tuned or forced) takes the wires in this order
     const int64_t shape[6] = {N, R, (int64_t)sizeof(TV), (int64_t)sizeof(TE), P.chunk, restart};
     int found = 0;
     for (const auto& t : ctx->tuned)
@@ -2212,6 +2213,7 @@ __global__ void __launch_bounds__(kRows) k_bi_check(BPtr B, const cplx<TV>* __re
 
 template <typename TV, typename TE>
 int bicgstab_impl(swm_ctx* ctx, const TE* E, double tol, int max_iter) {
+  SWM_TRY(build_wire_order(ctx));  // the order of product form 75, once per pattern
   cudaStream_t st = ctx->stream;
   const int R = ctx->n_rhs;
   const int64_t N = ctx->N;
@@ -2794,6 +2796,7 @@ __global__ void __launch_bounds__(256) k_minor_to_major(int64_t N, int R, int xs
 }
 
 int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
+  SWM_TRY(build_wire_order(ctx));  // the order of product form 75, once per pattern
   cudaStream_t st = ctx->stream;
   const int R = ctx->n_rhs;
   const int64_t N = ctx->N;

@@ -463,7 +463,7 @@ int build_pattern(swm_ctx* ctx) {
   }
   ctx->m = m;
   dfree_group(ctx, tmp);
-  return build_wire_order(ctx);
+  return SWM_OK;
 }
 
 }  // namespace swm
