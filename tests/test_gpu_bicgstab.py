@@ -134,3 +134,40 @@ def test_bicgstab_step_limit_identity_and_start_at_solution():
             assert np.linalg.norm(cur - Xf) / np.linalg.norm(Xf) < bound
         finally:
             swm.swm_destroy(ctx)
+
+
+def test_sorted_product_over_several_order_windows(monkeypatch):
+    """Form 75 takes the wires in an order sorted within windows of 4096 wires; a cloud of 9,000
+    wires spans two full windows and a ragged one.  Its complex64 currents and RCS against the
+    float64 path on the same cloud (no oracle LU at 45,000 unknowns), and against form 73 (the
+    cell order): both forms solve the same system, so their currents agree to the tolerance."""
+    from paper_2410_03060_gb300 import swm
+
+    cl = cloud_uniform_cube(9000, 39.0, seed=65)
+    inc = _many(37, 66)
+    obs = observations_phi_cut(24)
+
+    def run(prec, tol, form=None):
+        if form:
+            monkeypatch.setenv("SWM_PRODUCT_FORM", str(form))
+        else:
+            monkeypatch.delenv("SWM_PRODUCT_FORM", raising=False)
+        ctx = _ctx(cl, 2.0, prec)
+        try:
+            cur, rc, st = _solve(swm, ctx, cl, inc, tol)
+            assert rc == swm.SWM_OK and st["converged"] == 1
+            if form:
+                assert st["step_rhs_block"] == form
+            sig = np.zeros((inc.shape[0], len(obs), 2))
+            swm.swm_rcs_bistatic(ctx, obs, sig)
+            return cur, sig
+        finally:
+            swm.swm_destroy(ctx)
+
+    X64, s64 = run(C128, 1e-10)
+    X73, _ = run(C64, 1e-6, 73)
+    X75, s75 = run(C64, 1e-6, 75)
+    assert np.linalg.norm(X75 - X64) / np.linalg.norm(X64) < 1e-4
+    assert np.linalg.norm(X75 - X73) / np.linalg.norm(X64) < 1e-4
+    for i in range(inc.shape[0]):
+        assert_rcs_db(s75[i, :, 0], s64[i, :, 0], db=0.1)
