@@ -160,10 +160,12 @@ typedef struct swm_stats {
  * tile's E in shared memory; 68/69: two incidences per thread in packed FP32x2 arithmetic, E
  * staged in shared memory, three CTAs per SM with 48 KB or two with 96 KB; 70/71: the packed form
  * reading E from global memory, three or four CTAs per SM; 72/73: the same in small CTAs of a
- * few whole warps; 74: small CTAs with E and the column map staged by cp.async; 75: 74 over the wires sorted by
- * loop length within windows of 4096);
+ * few whole warps; 74: small CTAs with E and the column map staged by cp.async; 75: 74 over the
+ * wires sorted by loop length within windows of 4096);
  * SWM_BICGSTAB_MAJOR (default 0, a test hook) -- 1 keeps BiCGSTAB's vectors incidence-major on the
  * complex64 path (as on the float64 path and with one incidence) instead of incidence-minor;
+ * SWM_BICGSTAB_CTAS (default 4, 1-64) -- CTAs per SM of the incidence-minor BiCGSTAB vector passes
+ * (their chunks of rows, at least 2048 rows each);
  * SWM_TEST_BARRIER_EXTRA (default 0, a test hook) -- n > 0 makes every grid barrier of the
  * persistent solve wait for n arrivals that never come, so each wait runs out (after 1 s) and the
  * solve returns SWM_ETIMEOUT; all read when the context is created. */

@@ -345,6 +345,7 @@ int swm_create(swm_ctx** out, int device, void* cuda_stream) {
   if (const char* e = std::getenv("SWM_TEST_BARRIER_EXTRA")) ctx->test_barrier_extra = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("SWM_PRODUCT_FORM")) ctx->product_form = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("SWM_BICGSTAB_MAJOR")) ctx->bicg_major = std::atoi(e) != 0;
+  if (const char* e = std::getenv("SWM_BICGSTAB_CTAS")) ctx->bicg_ctas = std::min(64, std::max(1, std::atoi(e)));
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||

@@ -162,6 +162,8 @@ struct swm_ctx {
   // test hook (SWM_BICGSTAB_MAJOR=1): BiCGSTAB keeps its vectors incidence-major on the complex64
   // path too, as it does on the float64 path and with one incidence
   bool bicg_major = false;
+  // CTAs per SM of the incidence-minor BiCGSTAB vector passes (SWM_BICGSTAB_CTAS, default 4)
+  int bicg_ctas = 4;
   // test hook (SWM_TEST_BARRIER_EXTRA): grid barriers of the persistent solve wait for this many
   // arrivals more than there are CTAs, so every wait runs out and the solve reports SWM_ETIMEOUT
   int test_barrier_extra = 0;

@@ -2826,8 +2826,8 @@ int bicgstab_minor(swm_ctx* ctx, const c64* E, double tol, int max_iter) {
     B.N = N;
     B.R = R;
     B.xst = xst;
-    // chunks of rows: about four CTAs per SM, at least 2048 rows each
-    B.chunk = (int)std::max<int64_t>(2048, ceil_div(N, 4 * nsm));
+    // chunks of rows: about bicg_ctas (4) CTAs per SM, at least 2048 rows each
+    B.chunk = (int)std::max<int64_t>(2048, ceil_div(N, (int64_t)ctx->bicg_ctas * nsm));
     B.nchunk = (int)ceil_div(N, B.chunk);
     SWM_TRY(dalloc(ctx, K, (void**)&B.st, sizeof(BState)));
     SWM_TRY(dalloc(ctx, K, (void**)&B.active, sizeof(int) * R));
