@@ -419,9 +419,8 @@ def roofline_of(cls, st, prof_ms, launches, prec, n_rhs, restart, steps, pk, per
 # recorded with the profile summaries.  A class or form without a capture of its current code
 # reports null.
 MEASURED_TRAFFIC = {
-    # k_spmv_wa form 75 (small CTAs, wires sorted by loop length, E staged by cp.async),
-    # complex64, incidence-minor (BiCGSTAB step): 1.0597 GB against 1.0766 GB
-    ("learned", "apply", "c64", "bicgstab", 75): 1.0597e9 / 1.0766e9,
+    # (form 75's capture, 1.0597 GB against 1.0766 GB, predates its record-based prologue, so the
+    # form reports null until it is captured again)
 }
 
 PROFILE_CLASSES = ["pairs", "fill_self", "fill_mutual", "invert", "form_e", "apply", "transpose", "dots", "update",

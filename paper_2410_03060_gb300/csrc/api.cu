@@ -417,7 +417,7 @@ int swm_set_cloud(swm_ctx* ctx, int64_t nw, const double* centres, const double*
   ctx->built = ctx->solved = false;
   ctx->pattern_ok = false;
   ctx->rowwire = nullptr;
-  ctx->wperm = nullptr;
+  ctx->wrec = nullptr;
   ctx->nw = nw;
   auto& G = ctx->cloud_bufs;
   SWM_TRY(dalloc(ctx, G, (void**)&ctx->u_c, sizeof(double) * 3 * nw));
@@ -511,7 +511,7 @@ int swm_build(swm_ctx* ctx, double k, double r_c, int precision) {
     dfree_group(ctx, ctx->pattern_bufs);
     ctx->pattern_ok = false;
     ctx->rowwire = nullptr;
-    ctx->wperm = nullptr;
+    ctx->wrec = nullptr;
     ctx->uoff = nullptr;
     ctx->uoff_user = nullptr;
     SWM_TRY(build_pattern(ctx));

@@ -119,8 +119,8 @@ struct swm_ctx {
   int64_t* ublk = nullptr;     // [nup] blocks (p, q) with q > p
   int64_t* minv_off = nullptr; // [nw + 1] offsets of the m_p x m_p inverse blocks
   int32_t* rowwire = nullptr;  // [N] internal wire of each scalar row
-  int32_t* wperm = nullptr;    // [nw] wire order of product form 75 (built by the first solve that
-                               // may use it after a pattern build)
+  void* wrec = nullptr;        // [nw] wire records of product form 75 in its order (built by the
+                               // first solve that may use it after a pattern build)
   void* rowinfo = nullptr;     // [N] row descriptors of E (value offset, column-map offset, length)
   int64_t nminv = 0;           // entries of the packed self-block inverses
   unsigned long long* d_evals = nullptr;  // fill evaluation counter (device)

@@ -731,8 +731,10 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wg(KPtr P, const int64_t* __
 // rest), so the whole tile is in flight at once and the row loop reads E and the column map at
 // shared-memory latency.  A tile whose spans exceed the budgets reads them from global memory.
 // E and the column map must start on 16-byte boundaries (the launch checks), so that no span
-// reaches before either buffer.  With an order (perm, nullable) the CTA takes wires perm[p0 + i]
-// instead of p0 + i.
+// reaches before either buffer.  With records (rec, nullable) the CTA takes the wires of
+// rec[p0 + i], in the order the records were written, instead of wires p0 + i; every warp reads
+// the CTA's few records itself and issues its share of the copies, so the only barrier is the one
+// after the copies.
 // The E budget, 22 KB, holds all but about 0.5 % of the work's tiles at three CTAs' register
 // budget (eight CTAs per SM, as many as its registers allow).
 constexpr int kWaSmemE3 = 22 * 1024, kWaSmemC = 4 * 1024;
@@ -744,74 +746,88 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int byt
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
+// A wire of the small-CTA product as its prologue needs it: its index, first E entry and first
+// column-map entry, K and rows (the order build writes one per position, in the product's order).
+struct WaRec {
+  int64_t ebeg, cbeg;
+  int32_t p, K, m, pad;
+};
 template <typename TE, int MODE = kStepW, int MINB = 3, bool MINOR = false, int EB = kWaSmemE3>
 __global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __restrict__ off, Layout lay, int64_t nw,
                                                     const TE* __restrict__ E, const c64* __restrict__ U,
                                                     const c64* __restrict__ Xt, int xst, c64* __restrict__ Wv,
                                                     const c64* __restrict__ B, int RQ, int WB,
-                                                    const int32_t* __restrict__ perm) {
+                                                    const WaRec* __restrict__ rec) {
   constexpr bool ALL = MODE != kStepW;
   if (!ALL && (P.st->cycle_done || P.st->j >= P.st->jmax)) return;
   extern __shared__ __align__(16) unsigned char sm_wa[];
-  // per wire: its index, K, rows, the aligned starts of its E and column-map spans, their sizes
-  // and offsets in shared memory, and the offsets of its first entries within the spans
-  __shared__ const unsigned char* sea[kWaMaxWires];
-  __shared__ const unsigned char* sca[kWaMaxWires];
+  // per wire (written by warp 0, read after the barrier): its index, K, rows, and the offsets of
+  // its E rows and column map in shared memory
   __shared__ int64_t sp[kWaMaxWires];
-  __shared__ int sK[kWaMaxWires], sm_m[kWaMaxWires], sen[kWaMaxWires], scn[kWaMaxWires];
-  __shared__ int soe[kWaMaxWires], soc[kWaMaxWires], she[kWaMaxWires], shc[kWaMaxWires];
-  __shared__ int sfit;
+  __shared__ int sK[kWaMaxWires], sm_m[kWaMaxWires], sE[kWaMaxWires], sC[kWaMaxWires];
   const int64_t N = P.N;
   const int64_t p0 = (int64_t)blockIdx.x * WB;
   const int nwt = (int)min((int64_t)min(WB, kWaMaxWires), nw - p0);
-  if (threadIdx.x < 32) {
-    const int i = threadIdx.x;
-    int en = 0, cn = 0;
-    if (i < nwt) {
-      const int64_t p = perm ? (int64_t)perm[p0 + i] : p0 + i;
-      const unsigned char* eb = reinterpret_cast<const unsigned char*>(E + lay.rowbase[p]);
-      const unsigned char* ea = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(eb) & ~(uintptr_t)15);
-      const unsigned char* cb = reinterpret_cast<const unsigned char*>(lay.colmap + lay.cmbase[p]);
-      const unsigned char* ca = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(cb) & ~(uintptr_t)15);
-      const int K = lay.K[p], m = (int)(off[p + 1] - off[p]);
-      en = (int)(reinterpret_cast<const unsigned char*>(E + lay.rowbase[p] + (int64_t)m * K) - ea);
-      cn = (int)(reinterpret_cast<const unsigned char*>(lay.colmap + lay.cmbase[p] + K) - ca);
-      sp[i] = p;
-      sK[i] = K;
-      sm_m[i] = m;
-      sea[i] = ea;
-      sca[i] = ca;
-      sen[i] = en;
-      scn[i] = cn;
-      she[i] = (int)(eb - ea);
-      shc[i] = (int)(cb - ca);
+  // every warp: lane i < nwt takes wire i (its record, or the layout in the cell order), the spans
+  // and their offsets in shared memory (inclusive scans of the 16-byte-rounded sizes), so that each
+  // warp issues its share of the copies without waiting for another
+  const int lane = threadIdx.x & 31;
+  int64_t p = 0, eoff = 0, coff = 0;
+  int K = 0, m = 0, en = 0, cn = 0, he = 0, hc = 0;
+  const unsigned char *ea = nullptr, *ca = nullptr;
+  if (lane < nwt) {
+    if (rec) {
+      const WaRec r = rec[p0 + lane];
+      p = r.p;
+      eoff = r.ebeg;
+      coff = r.cbeg;
+      K = r.K;
+      m = r.m;
+    } else {
+      p = p0 + lane;
+      eoff = lay.rowbase[p];
+      coff = lay.cmbase[p];
+      K = lay.K[p];
+      m = (int)(off[p + 1] - off[p]);
     }
-    // offsets of the spans in shared memory: inclusive scans of the 16-byte-rounded sizes
-    int oe = (en + 15) & ~15, oc = (cn + 15) & ~15;
-#pragma unroll
-    for (int o = 1; o < kWaMaxWires; o <<= 1) {
-      const int a = __shfl_up_sync(0xffffffffu, oe, o), b = __shfl_up_sync(0xffffffffu, oc, o);
-      if (i >= o) {
-        oe += a;
-        oc += b;
-      }
-    }
-    if (i < nwt) {
-      soe[i] = oe - ((en + 15) & ~15);
-      soc[i] = EB + oc - ((cn + 15) & ~15);
-    }
-    if (i == kWaMaxWires - 1) sfit = oe <= EB && oc <= kWaSmemC;
+    const unsigned char* eb = reinterpret_cast<const unsigned char*>(E + eoff);
+    const unsigned char* cb = reinterpret_cast<const unsigned char*>(lay.colmap + coff);
+    ea = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(eb) & ~(uintptr_t)15);
+    ca = reinterpret_cast<const unsigned char*>(reinterpret_cast<uintptr_t>(cb) & ~(uintptr_t)15);
+    en = (int)(reinterpret_cast<const unsigned char*>(E + eoff + (int64_t)m * K) - ea);
+    cn = (int)(reinterpret_cast<const unsigned char*>(lay.colmap + coff + K) - ca);
+    he = (int)(eb - ea);
+    hc = (int)(cb - ca);
   }
-  __syncthreads();
-  const bool fits = sfit;
+  int oe = (en + 15) & ~15, oc = (cn + 15) & ~15;
+#pragma unroll
+  for (int o = 1; o < kWaMaxWires; o <<= 1) {
+    const int a = __shfl_up_sync(0xffffffffu, oe, o), b = __shfl_up_sync(0xffffffffu, oc, o);
+    if (lane >= o) {
+      oe += a;
+      oc += b;
+    }
+  }
+  const int soe = oe - ((en + 15) & ~15), soc = EB + oc - ((cn + 15) & ~15);
+  const bool fits = __shfl_sync(0xffffffffu, oe, kWaMaxWires - 1) <= EB &&
+                    __shfl_sync(0xffffffffu, oc, kWaMaxWires - 1) <= kWaSmemC;
+  if (threadIdx.x < 32 && lane < nwt) {
+    sp[lane] = p;
+    sK[lane] = K;
+    sm_m[lane] = m;
+    sE[lane] = fits ? soe + he : 0;
+    sC[lane] = fits ? soc + hc : 0;
+  }
   if (fits) {
     for (int w = 0; w < nwt; ++w) {
-      const int ne = sen[w], nc = scn[w];
-      const unsigned char *ea = sea[w], *ca = sca[w];
-      for (int c = 16 * (int)threadIdx.x; c < ne; c += 16 * (int)blockDim.x)
-        cp_async16(sm_wa + soe[w] + c, ea + c, min(16, ne - c));
-      for (int c = 16 * (int)threadIdx.x; c < nc; c += 16 * (int)blockDim.x)
-        cp_async16(sm_wa + soc[w] + c, ca + c, min(16, nc - c));
+      const int ne = __shfl_sync(0xffffffffu, en, w), nc = __shfl_sync(0xffffffffu, cn, w);
+      const int de = __shfl_sync(0xffffffffu, soe, w), dc = __shfl_sync(0xffffffffu, soc, w);
+      const unsigned char* a = reinterpret_cast<const unsigned char*>(
+          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ea), w));
+      const unsigned char* c = reinterpret_cast<const unsigned char*>(
+          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ca), w));
+      for (int x = 16 * (int)threadIdx.x; x < ne; x += 16 * (int)blockDim.x) cp_async16(sm_wa + de + x, a + x, min(16, ne - x));
+      for (int x = 16 * (int)threadIdx.x; x < nc; x += 16 * (int)blockDim.x) cp_async16(sm_wa + dc + x, c + x, min(16, nc - x));
     }
     cp_async_wait_all();
   }
@@ -824,31 +840,30 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __
   const bool wa = ALL || P.active[ra];
   const bool wb = rb < P.R && (ALL || P.active[rb]);
   if (!wa && !wb) return;
-  const int64_t p = sp[pl];
-  const int K = sK[pl], m = sm_m[pl];
+  const int64_t pw = sp[pl];
+  const int Kw = sK[pl], mwr = sm_m[pl];
   // E and the column map of the wire: in shared memory, else in global memory
-  const TE* ep = fits ? reinterpret_cast<const TE*>(sm_wa + soe[pl] + she[pl]) : E + lay.rowbase[p];
-  const int32_t* cms =
-      fits ? reinterpret_cast<const int32_t*>(sm_wa + soc[pl] + shc[pl]) : lay.colmap + lay.cmbase[p];
+  const TE* ep = fits ? reinterpret_cast<const TE*>(sm_wa + sE[pl]) : E + lay.rowbase[pw];
+  const int32_t* cms = fits ? reinterpret_cast<const int32_t*>(sm_wa + sC[pl]) : lay.colmap + lay.cmbase[pw];
   const EGlobal<TE> er{ep};
   const c64* xs = Xt + ra;
-  const int64_t orow = MINOR ? off[p] : (int64_t)ra * N + off[p];
+  const int64_t orow = MINOR ? off[pw] : (int64_t)ra * N + off[pw];
   if constexpr (MINOR) {
     U += ra;
     Wv += ra;
     if (B) B += ra;
   }
   switch (mw) {
-    case 1: wm_rows<MODE, 1, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 2: wm_rows<MODE, 2, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 3: wm_rows<MODE, 3, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 4: wm_rows<MODE, 4, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 5: wm_rows<MODE, 5, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 6: wm_rows<MODE, 6, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
-    case 7: wm_rows<MODE, 7, EGlobal<TE>, MINOR>(N, 0, m, K, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 1: wm_rows<MODE, 1, EGlobal<TE>, MINOR>(N, 0, mwr, Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 2: wm_rows<MODE, 2, EGlobal<TE>, MINOR>(N, 0, mwr, Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 3: wm_rows<MODE, 3, EGlobal<TE>, MINOR>(N, 0, mwr, Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 4: wm_rows<MODE, 4, EGlobal<TE>, MINOR>(N, 0, mwr, Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 5: wm_rows<MODE, 5, EGlobal<TE>, MINOR>(N, 0, mwr, Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 6: wm_rows<MODE, 6, EGlobal<TE>, MINOR>(N, 0, mwr, Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
+    case 7: wm_rows<MODE, 7, EGlobal<TE>, MINOR>(N, 0, mwr, Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb); break;
     default:
-      for (int i0 = 0; i0 < m; i0 += 8)
-        wm_rows<MODE, 8, EGlobal<TE>, MINOR>(N, i0, min(8, m - i0), K, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
+      for (int i0 = 0; i0 < mwr; i0 += 8)
+        wm_rows<MODE, 8, EGlobal<TE>, MINOR>(N, i0, min(8, mwr - i0), Kw, er, cms, xs, xst, U, Wv, B, orow, wa, wb);
       break;
   }
 }
@@ -858,8 +873,9 @@ __global__ void __launch_bounds__(256, MINB) k_spmv_wa(KPtr P, const int64_t* __
 // wires sharing a warp run row loops of about the same length.  One CTA per window, a bitonic
 // sort of (key, position) in shared memory; positions past the last wire sort last.
 constexpr int kOrderWin = 4096;
-__global__ void __launch_bounds__(1024) k_wire_order(int64_t nw, const int32_t* __restrict__ K,
-                                                     const int64_t* __restrict__ off, int32_t* __restrict__ perm) {
+__global__ void __launch_bounds__(1024) k_wire_order(int64_t nw, Layout lay, const int64_t* __restrict__ off,
+                                                     WaRec* __restrict__ rec) {
+  const int32_t* __restrict__ K = lay.K;
   __shared__ unsigned long long key[kOrderWin];
   const int64_t base = (int64_t)blockIdx.x * kOrderWin;
   for (int t = threadIdx.x; t < kOrderWin; t += blockDim.x) {
@@ -888,16 +904,26 @@ __global__ void __launch_bounds__(1024) k_wire_order(int64_t nw, const int32_t* 
       __syncthreads();
     }
   for (int t = threadIdx.x; t < kOrderWin; t += blockDim.x) {
-    const int64_t p = base + t;
-    if (p < nw) perm[p] = (int32_t)(base + (int64_t)(key[t] & 0xffffffffu));
+    const int64_t i = base + t;
+    if (i < nw) {
+      const int64_t p = base + (int64_t)(key[t] & 0xffffffffu);
+      WaRec r;
+      r.ebeg = lay.rowbase[p];
+      r.cbeg = lay.cmbase[p];
+      r.p = (int32_t)p;
+      r.K = K[p];
+      r.m = (int32_t)(off[p + 1] - off[p]);
+      r.pad = 0;
+      rec[i] = r;
+    }
   }
 }
 }  // namespace
 int build_wire_order(swm_ctx* ctx) {
-  if (ctx->wperm || ctx->nw <= 0 || ctx->nw > INT32_MAX) return SWM_OK;  // built for this pattern
-  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, (void**)&ctx->wperm, sizeof(int32_t) * ctx->nw));
-  k_wire_order<<<(unsigned)ceil_div(ctx->nw, kOrderWin), 1024, 0, ctx->stream>>>(ctx->nw, ctx->offd.K, ctx->off,
-                                                                                ctx->wperm);
+  if (ctx->wrec || ctx->nw <= 0 || ctx->nw > INT32_MAX) return SWM_OK;  // built for this pattern
+  SWM_TRY(dalloc(ctx, ctx->pattern_bufs, &ctx->wrec, sizeof(WaRec) * ctx->nw));
+  k_wire_order<<<(unsigned)ceil_div(ctx->nw, kOrderWin), 1024, 0, ctx->stream>>>(
+      ctx->nw, ctx->offd, ctx->off, reinterpret_cast<WaRec*>(ctx->wrec));
   SWM_LAUNCHED();
   return SWM_OK;
 }
@@ -947,13 +973,14 @@ int launch_wm(cudaStream_t s, int form, const KPtr& P, swm_ctx* ctx, const TE* E
       // inside the buffers only if both start on 16-byte boundaries (else form 73)
       const bool al16 =
           !(reinterpret_cast<uintptr_t>(E) & 15) && !(reinterpret_cast<uintptr_t>(ctx->offd.colmap) & 15);
-      if ((form == 74 || (form == 75 && ctx->wperm)) && al16) {
+      if ((form == 74 || (form == 75 && ctx->wrec)) && al16) {
         if (form == 74)
           k_spmv_wa<TE, MODE, 3, MINOR, kWaSmemE3><<<gs, bt, kWaSmemE3 + kWaSmemC, s>>>(
               P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, bw, nullptr);
         else
           k_spmv_wa<TE, MODE, 3, MINOR, kWaSmemE3><<<gs, bt, kWaSmemE3 + kWaSmemC, s>>>(
-              P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, bw, ctx->wperm);
+              P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ, bw,
+              reinterpret_cast<const WaRec*>(ctx->wrec));
       } else if (form == 72)
         k_spmv_wg<TE, MODE, 3, MINOR><<<gs, bt, 0, s>>>(P, ctx->off, ctx->offd, ctx->nw, E, src, Xt, xst, dst, Bv, RQ,
                                                         bw);
